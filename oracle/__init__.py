@@ -1,0 +1,208 @@
+"""FP64 CPU oracle (ctypes wrapper around oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may use it; the library path never does.  It
+shares no code with the CUDA library.  Every function cites the passage of
+arXiv 2507.16022 it follows (see oracle.h).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (portable flags: x86_64 and aarch64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n_int", ctypes.c_int), ("n_ext", ctypes.c_int), ("n_det", ctypes.c_int),
+                ("n_modes", ctypes.c_int), ("n_bins", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("mode_m", ctypes.POINTER(ctypes.c_int)),
+                ("f", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
+                ("psd", ctypes.POINTER(ctypes.c_double)), ("data", ctypes.POINTER(ctypes.c_double)),
+                ("h", ctypes.POINTER(ctypes.c_double)), ("R", ctypes.POINTER(ctypes.c_double)),
+                ("t", ctypes.POINTER(ctypes.c_double)),
+                ("ln_w_int", ctypes.POINTER(ctypes.c_double)),
+                ("ln_w_ext", ctypes.POINTER(ctypes.c_double)),
+                ("u_min", ctypes.c_double)]
+
+
+PAIR_DTYPE = np.dtype([("lnl_marg", "f8"), ("lnl_sq", "f8"), ("lnl_ml_max", "f8"),
+                       ("argmax_o", "i4"), ("n_pass", "i4")])
+
+
+class EvidenceOut(ctypes.Structure):
+    _fields_ = [("ln_z", ctypes.c_double), ("n_eff", ctypes.c_double),
+                ("n_eff_int", ctypes.c_double), ("n_eff_ext", ctypes.c_double),
+                ("max_lnl_ml", ctypes.c_double), ("arg_i", ctypes.c_int64),
+                ("arg_e", ctypes.c_int64), ("arg_o", ctypes.c_int64),
+                ("n_marginalised", ctypes.c_int64)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.or_dist_marg.restype = ctypes.c_double
+            L.or_dist_marg.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.or_lnl_ml.restype = ctypes.c_double
+            L.or_lnl_ml.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.or_default_threads.restype = ctypes.c_int
+            for name in ("or_data_weights", "or_direct_phases", "or_mode_components",
+                         "or_rotate_phases", "or_eval_pairs", "or_eval_grid",
+                         "or_direct_grid_ml", "or_evidence"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+        return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c128(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a
+
+
+class OracleProblem:
+    """Holds contiguous FP64 copies of one workload and the ctypes struct."""
+
+    def __init__(self, bank, ext, event, i_slice=None):
+        h = bank.h if i_slice is None else bank.h[i_slice]
+        lw_i = bank.ln_w if i_slice is None else bank.ln_w[i_slice]
+        self.mode_m = np.ascontiguousarray(bank.mode_m, dtype=np.int32)
+        self.f = np.ascontiguousarray(bank.f, dtype=np.float64)
+        self.w = np.ascontiguousarray(bank.w, dtype=np.float64)
+        self.psd = np.ascontiguousarray(event.psd, dtype=np.float64)
+        self.data = _c128(event.data)
+        self.h = _c128(h)
+        self.R = _c128(ext.R)
+        self.t = np.ascontiguousarray(ext.t, dtype=np.float64)
+        self.ln_w_int = np.ascontiguousarray(lw_i, dtype=np.float64)
+        self.ln_w_ext = np.ascontiguousarray(ext.ln_w, dtype=np.float64)
+        I, M, B = self.h.shape
+        E, D = self.t.shape
+        self.shape = (I, E, D, M, B)
+        self.n_phi = int(event.n_phi)
+        self.u_min = float(event.u_min)
+        self.s = Problem(I, E, D, M, B, self.n_phi,
+                         self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                         _dp(self.f), _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),
+                         _dp(self.h.view(np.float64)), _dp(self.R.view(np.float64)), _dp(self.t),
+                         _dp(self.ln_w_int), _dp(self.ln_w_ext), self.u_min)
+
+    # -- components -------------------------------------------------------
+    def data_weights(self):
+        """Eq. inner_product: c_{d,b} = 4 w conj(d)/S, omega = 4 w / S."""
+        I, E, D, M, B = self.shape
+        c = np.zeros((D, B), np.complex128)
+        om = np.zeros((D, B))
+        lib().or_data_weights(D, B, _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),
+                              _dp(c.view(np.float64)), _dp(om))
+        return c, om
+
+    def direct_phases(self, i, e):
+        """Route O1: (dh_o, hh_o) for o = 0..n_phi-1 by the direct frequency sum."""
+        dh = np.zeros(self.n_phi)
+        hh = np.zeros(self.n_phi)
+        lib().or_direct_phases(ctypes.byref(self.s), ctypes.c_int64(i), ctypes.c_int64(e),
+                               _dp(dh), _dp(hh))
+        return dh, hh
+
+    def mode_components(self, i, e):
+        """Route O2: z_m [M] and H_{mm'} [M, M] (complex)."""
+        I, E, D, M, B = self.shape
+        c, om = self.data_weights()
+        z = np.zeros(M, np.complex128)
+        H = np.zeros((M, M), np.complex128)
+        lib().or_mode_components(ctypes.byref(self.s), _dp(c.view(np.float64)), _dp(om),
+                                 ctypes.c_int64(i), ctypes.c_int64(e), _dp(z.view(np.float64)),
+                                 _dp(H.view(np.float64)))
+        return z, H
+
+    def rotate_phases(self, z, H, n_phi=None):
+        n_phi = self.n_phi if n_phi is None else n_phi
+        M = self.shape[3]
+        z = _c128(z)
+        H = _c128(H)
+        dh = np.zeros(n_phi)
+        hh = np.zeros(n_phi)
+        lib().or_rotate_phases(M, self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               _dp(z.view(np.float64)), _dp(H.view(np.float64)), n_phi,
+                               _dp(dh), _dp(hh))
+        return dh, hh
+
+    # -- evaluation -------------------------------------------------------
+    def eval_pairs(self, pi, pe, threshold=-np.inf, n_threads=0):
+        pi = np.ascontiguousarray(pi, dtype=np.int64)
+        pe = np.ascontiguousarray(pe, dtype=np.int64)
+        out = np.zeros(pi.shape[0], dtype=PAIR_DTYPE)
+        lib().or_eval_pairs(ctypes.byref(self.s), ctypes.c_int64(pi.shape[0]),
+                            pi.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            pe.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            ctypes.c_double(threshold), n_threads,
+                            out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    def eval_grid(self, cut_delta=0.0, n_threads=0):
+        I, E = self.shape[:2]
+        out = np.zeros(I * E, dtype=PAIR_DTYPE)
+        thr = ctypes.c_double(0.0)
+        lib().or_eval_grid(ctypes.byref(self.s), ctypes.c_double(cut_delta), n_threads,
+                           out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(thr))
+        return out.reshape(I, E), thr.value
+
+    def direct_grid_ml(self, n_threads=0):
+        I, E = self.shape[:2]
+        out = np.zeros(I * E)
+        lib().or_direct_grid_ml(ctypes.byref(self.s), n_threads, _dp(out))
+        return out.reshape(I, E)
+
+    def evidence(self, grid):
+        I, E = self.shape[:2]
+        g = np.ascontiguousarray(grid.reshape(-1), dtype=PAIR_DTYPE)
+        ev = EvidenceOut()
+        lpi = np.zeros(I)
+        lpe = np.zeros(E)
+        lib().or_evidence(ctypes.byref(self.s), g.ctypes.data_as(ctypes.c_void_p),
+                          ctypes.byref(ev), _dp(lpi), _dp(lpe))
+        return dict(ln_z=ev.ln_z, n_eff=ev.n_eff, n_eff_int=ev.n_eff_int,
+                    n_eff_ext=ev.n_eff_ext, max_lnl_ml=ev.max_lnl_ml,
+                    arg=(ev.arg_i, ev.arg_e, ev.arg_o), n_marginalised=ev.n_marginalised,
+                    ln_p_int=lpi, ln_p_ext=lpe)
+
+
+def dist_marg(dh, hh, u_min):
+    """Eq. lnl_dist_marginalized (pi(d_L) ~ d_L^2 up to d_max = d0/u_min)."""
+    return lib().or_dist_marg(float(dh), float(hh), float(u_min))
+
+
+def lnl_ml(dh, hh):
+    """Eq. bestfit_lnl."""
+    return lib().or_lnl_ml(float(dh), float(hh))
+
+
+def default_threads():
+    return lib().or_default_threads()

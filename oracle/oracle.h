@@ -1,0 +1,113 @@
+/*
+ * FP64 CPU oracle for the dense (intrinsic x extrinsic) likelihood of the
+ * sampler-free gravitational-wave method (arXiv 2507.16022).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library and includes nothing from it.
+ *
+ * Complex arrays are interleaved (re, im) doubles.  Layouts:
+ *   h      [I][M][B]   bank waveform components h_{i m}(f_b), d_L = d_L^0
+ *   R      [E][D][M]   complex detector response of mode m
+ *   t      [E][D]      arrival time at detector d (s)
+ *   data   [D][B]      detector data d_d(f_b)
+ *   psd    [D][B]      one-sided PSD S_d(f_b)
+ *   f, w   [B]         bin frequencies and quadrature weights
+ *   mode_m [M]         azimuthal number of each mode
+ *
+ * Inner product (Eq. inner_product): <a|b> = sum_d sum_b 4 w_b a b^* / S_d.
+ * Log-likelihood (Eq. lnlike): ln L = Re<d|h> - <h|h>/2.
+ */
+#ifndef DOTPE_ORACLE_H
+#define DOTPE_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct or_problem {
+  int n_int, n_ext, n_det, n_modes, n_bins, n_phi;
+  const int *mode_m;
+  const double *f, *w, *psd, *data;  /* data: complex */
+  const double *h;                   /* complex [I][M][B] */
+  const double *R;                   /* complex [E][D][M] */
+  const double *t;                   /* [E][D] */
+  const double *ln_w_int, *ln_w_ext; /* [I], [E] (may be NULL: zeros) */
+  double u_min;                      /* d_L^0 / d_max of pi(d_L) ~ d_L^2 */
+} or_problem;
+
+/* Per-(i,e) outputs. */
+typedef struct or_pair_out {
+  double lnl_marg;    /* ln Lbar_ie = ln( (1/N_phi) sum_o Lbar_ieo ), -inf if no phase passes */
+  double lnl_sq;      /* ln sum_o Lbar_ieo^2 (for N_eff), -inf if none */
+  double lnl_ml_max;  /* max_o ln L^ML_ieo */
+  int32_t argmax_o;   /* phase index of lnl_ml_max (lowest on ties) */
+  int32_t n_pass;     /* phases that passed the ML cut */
+} or_pair_out;
+
+typedef struct or_evidence_out {
+  double ln_z;        /* Eq. Z_sum */
+  double n_eff, n_eff_int, n_eff_ext; /* Eqs. posterior_element, int_ess, ext_ess */
+  double max_lnl_ml;
+  int64_t arg_i, arg_e, arg_o;
+  int64_t n_marginalised;
+} or_evidence_out;
+
+/* Eq. inner_product folded into per-bin data weights:
+ *   c_{d,b} = 4 w_b conj(d_d(f_b)) / S_d(f_b),  omega_{d,b} = 4 w_b / S_d(f_b). */
+int or_data_weights(int D, int B, const double *w, const double *psd, const double *data,
+                    double *c_out, double *omega_out);
+
+/* Route O1 (plain definition): for one (i, e) build the detector strain of
+ * Eq. h_k at d_L = d_L^0 and phase phi_o = 2 pi o / n_phi, then evaluate
+ * Re<d|h> and <h|h> by the frequency sum.  dh_out, hh_out: [n_phi]. */
+int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, double *hh_out);
+
+/* Route O2 (Eqs. dh_ieo, hh_ieo): per-mode components for one (i, e):
+ *   z_m = sum_d R_{e,d,m} sum_b c_{d,b} e^{-2 pi i f_b t_{e,d}} h_{i m}(f_b)
+ *   H_{m m'} = sum_d R_{e,d,m} R^*_{e,d,m'} <h_{i m}|h_{i m'}>_d
+ * z_out: complex [M]; H_out: complex [M][M]. */
+int or_mode_components(const or_problem *p, const double *c, const double *omega,
+                       int64_t i, int64_t e, double *z_out, double *H_out);
+
+/* Orbital-phase rotation (Phi_m = e^{i m phi}): dh_o = Re sum_m z_m e^{i m phi_o},
+ * hh_o = Re sum_{m m'} H_{m m'} e^{i (m - m') phi_o}. */
+int or_rotate_phases(int M, const int *mode_m, const double *z, const double *H, int n_phi,
+                     double *dh_out, double *hh_out);
+
+/* Eq. bestfit_lnl. */
+double or_lnl_ml(double dh, double hh);
+
+/* Eq. lnl_dist_marginalized with pi(d_L) = 3 d_L^2 / d_max^3 on (0, d_max],
+ * u_min = d_L^0 / d_max: returns ln Lbar(dh, hh). */
+double or_dist_marg(double dh, double hh, double u_min);
+
+/* Full per-pair evaluation (route O2, phase grid, ML cut, distance marginal,
+ * phase average) for an explicit list of pairs.  lnl_ml_threshold: phases
+ * with ln L^ML below it are dropped (pass -INFINITY for no cut). */
+int or_eval_pairs(const or_problem *p, int64_t n_pairs, const int64_t *pi, const int64_t *pe,
+                  double lnl_ml_threshold, int n_threads, or_pair_out *out);
+
+/* Same over the whole I x E grid (out: [I][E]); with cut_delta > 0 the
+ * threshold is max_{ieo} ln L^ML - cut_delta (Eq. coherent_ML_selection),
+ * found in a first pass.  Returns the threshold used via *thr_out. */
+int or_eval_grid(const or_problem *p, double cut_delta, int n_threads, or_pair_out *out,
+                 double *thr_out);
+
+/* Route O1 over the whole grid (no distance marginal): max_o ln L^ML per pair. */
+int or_direct_grid_ml(const or_problem *p, int n_threads, double *lnl_ml_max_out);
+
+/* Evidence and effective sample sizes from per-pair outputs over the full
+ * grid [I][E] (Eq. Z_sum with w_o = 1; Eqs. posterior_element, int_ess, ext_ess).
+ * ln_p_int [I] and ln_p_ext [E] (may be NULL) receive ln sum_{e,o} p_ieo and
+ * ln sum_{i,o} p_ieo. */
+int or_evidence(const or_problem *p, const or_pair_out *grid, or_evidence_out *ev,
+                double *ln_p_int, double *ln_p_ext);
+
+/* Number of hardware threads the oracle will use by default. */
+int or_default_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

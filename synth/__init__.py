@@ -1,0 +1,377 @@
+"""Seeded synthetic workloads for the dense (intrinsic x extrinsic) likelihood.
+
+This module only *makes inputs*: a waveform bank on a compressed frequency
+grid, a set of extrinsic samples (arrival times and complex detector
+responses), a PSD per detector and one event's data (an injected bank member
+plus Gaussian noise).  It contains none of the method's arithmetic (no inner
+products, phase/distance marginalisation or evidence sums); both the FP64
+oracle and the CUDA path consume what it returns.
+
+Physical content, following the paper's decomposition (Sec. IV.A):
+
+* waveform components h_m(f) = A_m f^(-7/6) exp(i Psi_m(f)) with the leading
+  post-Newtonian phase Psi_22 and Psi_m = (m/2) Psi_22,
+* detector responses F_+/F_x (Eqs. response_plus/response_cross) from the
+  textbook detector-tensor contraction in an Earth-fixed frame,
+* arrival times t_k = t_geo + r_k . n_prop / c (Eq. t_at_detector),
+* the strain model h_k = u sum_m h_m R_{k,m} T_k Phi_m (Eq. h_k), used here
+  only to build the injected signal.
+
+The complex response R_{e,d,m} folds the polarisation sum of Eq. h_k into one
+number per (extrinsic sample, detector, mode):
+R = F_+ K+_m(iota) + F_x Kx_m(iota), with K+_m = (Y_lm + (-1)^l Y_l-m)/2 and
+Kx_m = i (Y_lm - (-1)^l Y_l-m)/2 built from spin-weight -2 spherical
+harmonics at azimuth 0.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Physical constants (SI).
+C_LIGHT = 299_792_458.0
+R_EARTH = 6.371e6
+GM_SUN_S = 4.925491025543576e-06  # G M_sun / c^3 in seconds
+
+# Approximate detector vertices (deg) and arm bearings (deg from North towards
+# East).  Exact values are immaterial for a synthetic workload.
+DETECTORS = {
+    "H1": dict(lat=46.455, lon=-119.408, xarm=324.0, yarm=234.0),
+    "L1": dict(lat=30.563, lon=-90.774, xarm=252.3, yarm=162.3),
+    "V1": dict(lat=43.631, lon=10.504, xarm=70.6, yarm=340.6),
+}
+DET_ORDER = ("H1", "L1", "V1")
+PSD_SCALES = (1.0, 1.3, 1.7)
+
+# (l, m) for each supported mode count.  Modes are indexed by azimuthal m.
+MODE_SETS = {
+    1: ((2, 2),),
+    2: ((2, 2), (3, 3)),
+    3: ((2, 2), (3, 3), (4, 4)),
+    4: ((2, 1), (2, 2), (3, 3), (4, 4)),
+}
+
+
+# ----------------------------------------------------------------------------
+# frequency grid, quadrature weights, PSD
+# ----------------------------------------------------------------------------
+def freq_grid(n_bins: int, fmin: float = 20.0, fmax: float = 1024.0):
+    """Log-spaced bins f_b and trapezoid weights w_b (Hz) on them."""
+    f = fmin * (fmax / fmin) ** (np.arange(n_bins) / (n_bins - 1))
+    w = np.empty(n_bins)
+    w[0] = 0.5 * (f[1] - f[0])
+    w[-1] = 0.5 * (f[-1] - f[-2])
+    w[1:-1] = 0.5 * (f[2:] - f[:-2])
+    return f, w
+
+
+def analytic_psd(f: np.ndarray, scale: float = 1.0, f_s: float = 150.0):
+    """Smooth analytic one-sided PSD in whitened units."""
+    r = f / f_s
+    return scale * (r ** -4 + 2.0 + 2.0 * r ** 2)
+
+
+# ----------------------------------------------------------------------------
+# spin-weight -2 spherical harmonics at azimuth 0 (real-valued there)
+# ----------------------------------------------------------------------------
+def sYlm_m2(l: int, m: int, iota):
+    """_{-2}Y_{lm}(iota, phi=0) for the modes used here (closed forms)."""
+    iota = np.asarray(iota, dtype=np.float64)
+    c = np.cos(iota / 2.0)
+    s = np.sin(iota / 2.0)
+    ci = np.cos(iota)
+    si = np.sin(iota)
+    if l == 2 and m == 2:
+        return math.sqrt(5.0 / (64.0 * math.pi)) * (1.0 + ci) ** 2
+    if l == 2 and m == -2:
+        return math.sqrt(5.0 / (64.0 * math.pi)) * (1.0 - ci) ** 2
+    if l == 2 and m == 1:
+        return math.sqrt(5.0 / (16.0 * math.pi)) * si * (1.0 + ci)
+    if l == 2 and m == -1:
+        return math.sqrt(5.0 / (16.0 * math.pi)) * si * (1.0 - ci)
+    if l == 3 and m == 3:
+        return -math.sqrt(21.0 / (2.0 * math.pi)) * c ** 5 * s
+    if l == 3 and m == -3:
+        return math.sqrt(21.0 / (2.0 * math.pi)) * c * s ** 5
+    if l == 4 and m == 4:
+        return 3.0 * math.sqrt(7.0 / math.pi) * c ** 6 * s ** 2
+    if l == 4 and m == -4:
+        return 3.0 * math.sqrt(7.0 / math.pi) * c ** 2 * s ** 6
+    raise ValueError(f"no closed form for (l,m)=({l},{m})")
+
+
+def polarisation_factors(l: int, m: int, iota):
+    """(K+, Kx) such that h_+ = K+ h_lm and h_x = Kx h_lm for this mode."""
+    yp = sYlm_m2(l, m, iota)
+    ym = sYlm_m2(l, -m, iota)
+    sign = (-1.0) ** l
+    kplus = 0.5 * (yp + sign * ym)
+    kcross = 0.5j * (yp - sign * ym)
+    return kplus, kcross
+
+
+# ----------------------------------------------------------------------------
+# detector geometry (Earth-fixed frame; the sky rotates, the Earth does not)
+# ----------------------------------------------------------------------------
+def _unit(lat_deg, lon_deg):
+    la, lo = math.radians(lat_deg), math.radians(lon_deg)
+    return np.array([math.cos(la) * math.cos(lo), math.cos(la) * math.sin(lo), math.sin(la)])
+
+
+def detector_geometry(name: str):
+    """(position r [m], detector tensor D = (x x^T - y y^T)/2)."""
+    g = DETECTORS[name]
+    la, lo = math.radians(g["lat"]), math.radians(g["lon"])
+    east = np.array([-math.sin(lo), math.cos(lo), 0.0])
+    north = np.array([-math.sin(la) * math.cos(lo), -math.sin(la) * math.sin(lo), math.cos(la)])
+
+    def arm(bearing_deg):
+        b = math.radians(bearing_deg)
+        return math.cos(b) * north + math.sin(b) * east
+
+    x, y = arm(g["xarm"]), arm(g["yarm"])
+    tensor = 0.5 * (np.outer(x, x) - np.outer(y, y))
+    return R_EARTH * _unit(g["lat"], g["lon"]), tensor
+
+
+def antenna_patterns(tensor, lat, lon, psi):
+    """F_+, F_x for sources at Earth-fixed (lat, lon) with polarisation psi.
+
+    Polarisation basis (X, Y) transverse to the source direction; F_+ = D:(XX-YY),
+    F_x = D:(XY+YX).  Vectorised over the sample axis.
+    """
+    theta = 0.5 * np.pi - lat  # colatitude
+    phi = lon
+    sph, cph = np.sin(phi), np.cos(phi)
+    sth, cth = np.sin(theta), np.cos(theta)
+    sps, cps = np.sin(psi), np.cos(psi)
+    X = np.stack([sph * cps - sps * cph * cth,
+                  -(cph * cps + sps * sph * cth),
+                  sps * sth], axis=-1)
+    Y = np.stack([-sph * sps - cps * cph * cth,
+                  cph * sps - cps * sph * cth,
+                  cps * sth], axis=-1)
+    fp = np.einsum("ni,ij,nj->n", X, tensor, X) - np.einsum("ni,ij,nj->n", Y, tensor, Y)
+    fc = np.einsum("ni,ij,nj->n", X, tensor, Y) + np.einsum("ni,ij,nj->n", Y, tensor, X)
+    return fp, fc
+
+
+# ----------------------------------------------------------------------------
+# workload containers
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Bank:
+    f: np.ndarray          # [B] Hz
+    w: np.ndarray          # [B] quadrature weights (Hz)
+    mode_m: np.ndarray     # [M] azimuthal numbers
+    mode_l: np.ndarray     # [M]
+    h: np.ndarray          # [I, M, B] complex128
+    ln_w: np.ndarray       # [I] ln(pi/pi') importance weights
+    mchirp: np.ndarray     # [I] Msun (metadata)
+
+
+@dataclasses.dataclass
+class Extrinsic:
+    t: np.ndarray          # [E, D] arrival time at each detector (s)
+    R: np.ndarray          # [E, D, M] complex128 response
+    ln_w: np.ndarray       # [E]
+    lat: np.ndarray
+    lon: np.ndarray
+    psi: np.ndarray
+    cos_iota: np.ndarray
+    t_geo: np.ndarray
+
+
+@dataclasses.dataclass
+class Event:
+    psd: np.ndarray        # [D, B]
+    data: np.ndarray       # [D, B] complex128
+    u_min: float           # d_L^0 / d_max of the distance prior
+    n_phi: int
+    injection: dict        # i, e (if inserted), phi, u, snr
+
+
+# ----------------------------------------------------------------------------
+# generators
+# ----------------------------------------------------------------------------
+def make_bank(rng, n_int, n_modes, n_bins, mc_range=(5.0, 30.0), ratio_max=0.3,
+              ln_w="zero", dtype=np.complex128, fmin=20.0, fmax=1024.0,
+              chunk=8192):
+    """Leading-PN multi-mode bank on log-spaced bins (see module doc)."""
+    f, w = freq_grid(n_bins, fmin, fmax)
+    lm = MODE_SETS[n_modes]
+    mode_l = np.array([l for l, _ in lm], dtype=np.int32)
+    mode_m = np.array([m for _, m in lm], dtype=np.int32)
+    mc = rng.uniform(mc_range[0], mc_range[1], size=n_int)
+    ratios = rng.uniform(0.0, ratio_max, size=(n_int, n_modes))
+    i22 = int(np.nonzero((mode_l == 2) & (mode_m == 2))[0][0])
+    ratios[:, i22] = 1.0
+    # normalise so that a waveform of chirp mass mc_ref has <h22|h22> = 1 on
+    # the first detector's PSD with unit response
+    psd0 = analytic_psd(f, PSD_SCALES[0])
+    norm = math.sqrt(np.sum(4.0 * w * f ** (-7.0 / 3.0) / psd0))
+    mc_ref = 0.5 * (mc_range[0] + mc_range[1])
+    amp22 = (mc / mc_ref) ** (5.0 / 6.0) / norm
+    h = np.empty((n_int, n_modes, n_bins), dtype=dtype)
+    base_amp = f ** (-7.0 / 6.0)
+    for i0 in range(0, n_int, chunk):
+        i1 = min(n_int, i0 + chunk)
+        x = np.pi * GM_SUN_S * mc[i0:i1, None] * f[None, :]
+        psi22 = -0.25 * np.pi + (3.0 / 128.0) * x ** (-5.0 / 3.0)
+        for k, m in enumerate(mode_m):
+            amp = (amp22[i0:i1] * ratios[i0:i1, k])[:, None] * base_amp[None, :]
+            h[i0:i1, k, :] = amp * np.exp(1j * (0.5 * m) * psi22)
+    if ln_w == "zero":
+        lw = np.zeros(n_int)
+    elif ln_w == "random":
+        lw = rng.normal(0.0, 0.5, size=n_int)
+    else:
+        raise ValueError(ln_w)
+    return Bank(f=f, w=w, mode_m=mode_m, mode_l=mode_l, h=h, ln_w=lw, mchirp=mc)
+
+
+def make_extrinsic(rng, n_ext, n_det, bank: Bank, ln_w="zero", t_span=0.010):
+    """Prior draws: isotropic sky, uniform psi, cos(iota), t_geo in +-t_span."""
+    lon = rng.uniform(0.0, 2.0 * np.pi, n_ext)
+    lat = np.arcsin(rng.uniform(-1.0, 1.0, n_ext))
+    psi = rng.uniform(0.0, np.pi, n_ext)
+    cos_iota = rng.uniform(-1.0, 1.0, n_ext)
+    t_geo = rng.uniform(-t_span, t_span, n_ext)
+    return extrinsic_from_params(lat, lon, psi, cos_iota, t_geo, n_det, bank,
+                                 ln_w=(np.zeros(n_ext) if ln_w == "zero"
+                                       else rng.normal(0.0, 0.5, n_ext)))
+
+
+def extrinsic_from_params(lat, lon, psi, cos_iota, t_geo, n_det, bank: Bank, ln_w):
+    n_ext = lat.shape[0]
+    iota = np.arccos(cos_iota)
+    # propagation direction is minus the source direction
+    n_src = np.stack([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.sin(lat)], -1)
+    M = bank.mode_m.shape[0]
+    t = np.empty((n_ext, n_det))
+    R = np.empty((n_ext, n_det, M), dtype=np.complex128)
+    kp = np.empty((n_ext, M), dtype=np.complex128)
+    kx = np.empty((n_ext, M), dtype=np.complex128)
+    for k in range(M):
+        a, b = polarisation_factors(int(bank.mode_l[k]), int(bank.mode_m[k]), iota)
+        kp[:, k] = a
+        kx[:, k] = b
+    for d in range(n_det):
+        r, tensor = detector_geometry(DET_ORDER[d])
+        t[:, d] = t_geo - (n_src @ r) / C_LIGHT
+        fp, fc = antenna_patterns(tensor, lat, lon, psi)
+        R[:, d, :] = fp[:, None] * kp + fc[:, None] * kx
+    return Extrinsic(t=t, R=R, ln_w=np.asarray(ln_w, dtype=np.float64), lat=lat, lon=lon,
+                     psi=psi, cos_iota=cos_iota, t_geo=t_geo)
+
+
+def signal_at_detectors(h_modes, R_dm, t_d, f, mode_m, phi, u):
+    """Eq. h_k: u sum_m h_m R_{d,m} exp(-2 pi i f t_d) exp(i m phi); [D, B]."""
+    ph = np.exp(1j * mode_m * phi)                      # [M]
+    shift = np.exp(-2j * np.pi * f[None, :] * t_d[:, None])   # [D, B]
+    comb = np.einsum("mb,dm,m->db", h_modes, R_dm, ph)
+    return u * comb * shift
+
+
+def network_norm(sig, psd, w):
+    """sum_d sum_b 4 w |s|^2 / S  (only used to scale the injection)."""
+    return float(np.sum(4.0 * w[None, :] * np.abs(sig) ** 2 / psd))
+
+
+def make_event(rng, bank: Bank, ext: Extrinsic, n_det, snr=15.0, n_phi=32,
+               noise=True, inj_i=None, inj_e=None, phi_inj=None, u_min=None):
+    """Event data: bank member inj_i seen through extrinsic sample inj_e.
+
+    If inj_e is None a fresh prior draw is used (not a member of `ext`).
+    The distance is set so that the network optimal SNR equals `snr`.
+    """
+    D = n_det
+    psd = np.stack([analytic_psd(bank.f, PSD_SCALES[d]) for d in range(D)])
+    I = bank.h.shape[0]
+    if inj_i is None:
+        inj_i = int(rng.integers(0, I))
+    if inj_e is None:
+        e1 = make_extrinsic(rng, 1, D, bank)
+        R_dm, t_d = e1.R[0], e1.t[0]
+    else:
+        R_dm, t_d = ext.R[inj_e], ext.t[inj_e]
+    if phi_inj is None:
+        phi_inj = float(rng.uniform(0.0, 2.0 * np.pi))
+    h_modes = np.asarray(bank.h[inj_i], dtype=np.complex128)
+    unit = signal_at_detectors(h_modes, R_dm, t_d, bank.f, bank.mode_m, phi_inj, 1.0)
+    u_inj = snr / math.sqrt(network_norm(unit, psd, bank.w))
+    data = u_inj * unit
+    if noise:
+        sigma = np.sqrt(psd / (4.0 * bank.w[None, :]))
+        data = data + sigma * (rng.standard_normal((D, bank.f.size))
+                               + 1j * rng.standard_normal((D, bank.f.size)))
+    if u_min is None:
+        u_min = default_u_min(bank, D)
+    return Event(psd=psd, data=data, u_min=float(u_min), n_phi=int(n_phi),
+                 injection=dict(i=inj_i, e=inj_e, phi=phi_inj, u=u_inj, snr=snr))
+
+
+def default_u_min(bank: Bank, n_det: int, snr_at_dmax: float = 4.0):
+    """u_min = d0/d_max such that a face-on, optimally oriented waveform of
+    <h22|h22> = 1 reaches network SNR `snr_at_dmax` at d_max."""
+    kp, _ = polarisation_factors(2, 2, 0.0)
+    rho2 = sum(abs(kp) ** 2 / PSD_SCALES[d] for d in range(n_det))
+    return snr_at_dmax / math.sqrt(rho2)
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+WORKLOADS = {
+    # name: (I, E, D, M, B, snr, seed)
+    "cfg1": dict(n_int=1024, n_ext=256, n_det=2, n_modes=3, n_bins=256, snr=15.0, seed=0),
+    "cfg2": dict(n_int=65536, n_ext=4096, n_det=3, n_modes=4, n_bins=512, snr=15.0, seed=2),
+    "cfg3": dict(n_int=1048576, n_ext=2048, n_det=3, n_modes=4, n_bins=384, snr=30.0, seed=3),
+}
+
+
+@dataclasses.dataclass
+class Workload:
+    bank: Bank
+    ext: Extrinsic
+    event: Event
+
+
+def make_workload(n_int, n_ext, n_det, n_modes, n_bins, snr=15.0, seed=0, n_phi=32,
+                  noise=True, insert_injection=False, ln_w="zero", bank_dtype=np.complex128,
+                  phi_inj=None):
+    """Bank + extrinsic set + one event, all from one seeded generator.
+
+    insert_injection=True places the injected extrinsic sample at e = 0 (and,
+    unless phi_inj is given, the injected phase at phi = 0) so that the
+    noiseless likelihood peaks exactly on the grid.
+    """
+    rng = np.random.default_rng(seed)
+    bank = make_bank(rng, n_int, n_modes, n_bins, ln_w=ln_w, dtype=bank_dtype)
+    ext = make_extrinsic(rng, n_ext, n_det, bank, ln_w=ln_w)
+    if insert_injection:
+        ev = make_event(rng, bank, ext, n_det, snr=snr, n_phi=n_phi, noise=noise,
+                        inj_e=0, phi_inj=(0.0 if phi_inj is None else phi_inj))
+    else:
+        ev = make_event(rng, bank, ext, n_det, snr=snr, n_phi=n_phi, noise=noise,
+                        phi_inj=phi_inj)
+    return Workload(bank=bank, ext=ext, event=ev)
+
+
+def named_workload(name: str, **overrides):
+    kw = dict(WORKLOADS[name])
+    kw.update(overrides)
+    return make_workload(**kw)
+
+
+def pair_subsample(rng_seed, n_int, n_ext, frac=0.01, n_max=None):
+    """Seeded uniform (i, e) subsample without replacement, sorted."""
+    rng = np.random.default_rng(rng_seed)
+    n = n_int * n_ext
+    k = max(1, int(round(frac * n)))
+    if n_max is not None:
+        k = min(k, n_max)
+    flat = np.sort(rng.choice(n, size=k, replace=False))
+    return (flat // n_ext).astype(np.int64), (flat % n_ext).astype(np.int64)
