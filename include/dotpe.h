@@ -1,0 +1,220 @@
+/*
+ * dotpe -- dense (intrinsic x extrinsic) gravitational-wave likelihood on one
+ * GB300 GPU (sm_103a), after arXiv 2507.16022 ("Sampler-free gravitational
+ * wave inference using matrix multiplication").
+ *
+ * C ABI.  Every function returns an int status: DOTPE_OK (0) or a negative
+ * DOTPE_E_* code; dotpe_strerror() names the code and
+ * dotpe_last_error_message() (thread-local) gives the detail of the last
+ * failure on the calling thread.  No C++ exception crosses this boundary.
+ * A dotpe_ctx may be used from several host threads; calls are serialised
+ * internally.
+ *
+ * Pointers marked "host or device" are classified with
+ * cudaPointerGetAttributes: device (or managed) pointers are read on the GPU,
+ * anything else is read from host memory.  The library never keeps a
+ * caller's pointer after the call returns: inputs are copied into memory the
+ * context owns.  Complex arrays are interleaved (re, im) doubles.
+ *
+ * Notation (paper Sec. IV): i = intrinsic sample (bank row), e = extrinsic
+ * sample, d = detector, m = azimuthal mode, b = frequency bin, o = phase
+ * index of the regular grid phi_o = 2 pi o / N_phi (w_o = 1, Sec. IV.B).
+ */
+#ifndef DOTPE_H
+#define DOTPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOTPE_ABI_VERSION 1
+
+/* ---- status codes ------------------------------------------------------ */
+#define DOTPE_OK 0
+#define DOTPE_E_INVALID -1     /* bad argument, shape, NaN/Inf input, unknown id */
+#define DOTPE_E_NOMEM -2       /* device or pinned host allocation failed */
+#define DOTPE_E_ADMISSION -3   /* event can never fit the context's HBM budget */
+#define DOTPE_E_NOT_READY -4   /* event not finished yet */
+#define DOTPE_E_TIMEOUT -5     /* a bounded wait (host or device) ran out */
+#define DOTPE_E_DEVICE -6      /* CUDA error; the context may be unusable */
+#define DOTPE_E_NOT_FOUND -7   /* unknown bank or event id */
+#define DOTPE_E_UNSUPPORTED -8 /* valid request this build does not serve */
+
+/* ---- enums ------------------------------------------------------------- */
+/* Arithmetic of the <d|h> GEMM (Eq. dh_ieo).  All accumulate in FP32.
+ *   FP32   : SIMT FFMA path (the plain baseline)
+ *   BF16   : one tcgen05 pass, bf16 operands
+ *   FP16   : one tcgen05 pass, fp16 operands
+ *   BF16X3 : split precision x = hi + lo (both bf16); hi*hi + hi*lo + lo*hi */
+enum { DOTPE_PREC_FP32 = 0, DOTPE_PREC_BF16 = 1, DOTPE_PREC_FP16 = 2, DOTPE_PREC_BF16X3 = 3 };
+
+/* bank waveform element type */
+enum { DOTPE_C128 = 0, DOTPE_C64 = 1 };
+
+/* event flags */
+#define DOTPE_FLAG_STORE_LNL 0x1   /* keep ln Lbar_ie and max_o ln L^ML_ie for dotpe_lnl_blocks */
+#define DOTPE_FLAG_GEMM_ONLY 0x2   /* diagnostics: skip the marginalisation epilogue (result not valid) */
+
+/* event states */
+enum { DOTPE_STATE_QUEUED = 0, DOTPE_STATE_RUNNING = 1, DOTPE_STATE_DONE = 2, DOTPE_STATE_FAILED = 3 };
+
+/* what dotpe_lnl_blocks returns */
+enum {
+  DOTPE_LNL_MARG = 0,   /* ln Lbar_ie = ln (1/N_phi) sum_o Lbar_ieo (Eq. lnl_dist_marginalized) */
+  DOTPE_LNL_ML_MAX = 1, /* max_o ln L^ML_ieo (Eq. bestfit_lnl) */
+  DOTPE_ROW_MARGINAL = 2, /* ln sum_{e,o} w_i w_e Lbar_ieo, one value per i (row e0..e1 ignored) */
+  DOTPE_COL_MARGINAL = 3  /* ln sum_{i,o} w_i w_e Lbar_ieo, one value per e (rows ignored) */
+};
+
+/* ---- structures -------------------------------------------------------- */
+typedef struct dotpe_ctx dotpe_ctx;
+
+typedef struct dotpe_config {
+  int device;                /* CUDA ordinal */
+  uint64_t hbm_budget_bytes; /* device bytes the context may hold for banks + events; 0 = 90% of free */
+  int n_slots;               /* events that may run concurrently on the device (0 = 4) */
+  int flags;                 /* reserved, 0 */
+} dotpe_config;
+
+/* Intrinsic waveform bank on fixed bins (Sec. IV.C; h_{impb} stored on f_b only).
+ * h: host or device, element type h_dtype, layout [n_int][n_modes][n_bins] complex.
+ * f, w_quad: [n_bins] host or device doubles: bin frequencies (Hz) and quadrature
+ * weights such that <a|b> = sum_d sum_b 4 w_quad[b] a b^* / S_d(f_b) (Eq. inner_product).
+ * mode_m: host int [n_modes], azimuthal numbers, each in 1..4, distinct.
+ * ln_w_int: [n_int] host or device, ln(pi/pi') of each sample (Eq. int_weights); NULL = 0. */
+typedef struct dotpe_bank_desc {
+  int64_t n_int;
+  int n_modes;
+  const int *mode_m;
+  int n_bins;
+  const double *f;
+  const double *w_quad;
+  const void *h;
+  int h_dtype;
+  const double *ln_w_int;
+} dotpe_bank_desc;
+
+/* One event: data, PSD, extrinsic samples (Sec. IV.B-E).
+ * Rows [i0, i1) of the bank are used (N_int = i1 - i0).
+ * psd [n_det][n_bins] (double), data [n_det][n_bins] (complex): host or device.
+ * t [n_ext][n_det] (double, s): arrival time at each detector (Eq. t_at_detector).
+ * R [n_ext][n_det][n_modes] (complex): response of mode m at detector d, i.e.
+ *   the factor that multiplies h_m(f) T_d(f) Phi_m in Eq. h_k (polarisation sum folded in).
+ * ln_w_ext [n_ext]: ln w_e (Sec. IV.E); NULL = 0.
+ * u_min = d_L^0 / d_max of the distance prior pi(d_L) ~ d_L^2 on (0, d_max].
+ * cut_delta > 0 enables the coherent-ML selection of Eq. coherent_ML_selection
+ *   (phases with ln L^ML < max - cut_delta are not marginalised); <= 0 disables it.
+ * stream: cudaStream_t the event's work is ordered after (NULL: none). */
+typedef struct dotpe_event_desc {
+  uint64_t bank_id;
+  int64_t i0, i1;
+  int n_det;
+  const double *psd;
+  const double *data;
+  int64_t n_ext;
+  const double *t;
+  const double *R;
+  const double *ln_w_ext;
+  int n_phi;
+  double u_min;
+  double cut_delta;
+  int precision;
+  int flags;
+  void *stream;
+} dotpe_event_desc;
+
+typedef struct dotpe_event_stats {
+  int64_t t_submit_ns, t_admit_ns, t_done_ns; /* host steady clock; 0 if not reached */
+  int64_t n_pairs;                            /* N_int * N_ext */
+  int64_t footprint_bytes;                    /* device bytes held while running */
+  float device_ms;                            /* GPU time from first to last kernel */
+  int precision;
+  int state;
+} dotpe_event_stats;
+
+/* Eq. Z_sum with w_o = 1; Eqs. posterior_element, int_ess, ext_ess; Eq. bestfit_lnl. */
+typedef struct dotpe_evidence_out {
+  double ln_z;              /* ln Z = ln[(1/(N_i N_e N_phi)) sum_ieo w_i w_e Lbar_ieo] */
+  double n_eff, n_eff_int, n_eff_ext;
+  double max_lnl_ml;        /* max over (i,e,o) of ln L^ML */
+  int64_t arg_i, arg_e, arg_o; /* its location (i in bank numbering); lowest (i,e,o) on ties */
+  int64_t n_marginalised;   /* (i,e,o) for which Lbar was evaluated */
+  int64_t n_pairs;
+  double lnl_ml_threshold;  /* the cut applied (running maximum - cut_delta), -inf when off */
+  int32_t device_status;    /* 0, or a DOTPE_E_* raised inside a kernel */
+  int32_t reserved;
+} dotpe_evidence_out;
+
+/* ---- context ----------------------------------------------------------- */
+/* Creates a context on cfg->device (cfg may be NULL: defaults).  Allocates the
+ * distance-marginal lookup table (built on the device) and its streams.
+ * Errors: E_INVALID (bad device), E_DEVICE, E_NOMEM. */
+int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out);
+
+/* Waits for outstanding work, frees every bank/event and the context. */
+int dotpe_destroy(dotpe_ctx *ctx);
+
+const char *dotpe_strerror(int status);
+const char *dotpe_last_error_message(void);
+int dotpe_version(void);
+
+/* Number of SMs and the name of the device the context runs on. */
+int dotpe_device_info(dotpe_ctx *ctx, int *n_sms, char *name, int name_len);
+
+/* ---- bank -------------------------------------------------------------- */
+/* Copies the bank to the device (synchronously) and prepares the operand
+ * planes of every precision: FP32 master, bf16 hi/lo, fp16; rows padded to
+ * a multiple of 64 frequency-pairs.  The caller keeps its buffers.
+ * Errors: E_INVALID (shape, mode numbers, non-finite values), E_NOMEM
+ * (beyond the HBM budget), E_DEVICE. */
+int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *desc, uint64_t *bank_id);
+
+/* Frees a bank.  E_INVALID if an unreleased event still uses it. */
+int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id);
+
+/* ---- events ------------------------------------------------------------ */
+/* Queues one event and returns at once (inputs are copied before return).
+ * The event is admitted as soon as its device footprint fits the free part of
+ * the HBM budget and a slot is free; admitted events run concurrently on the
+ * device.  Errors: E_INVALID, E_NOT_FOUND (bank), E_ADMISSION (footprint larger
+ * than the whole budget), E_NOMEM. */
+int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *desc, uint64_t *event_id);
+
+/* Non-blocking state query; also admits queued events whose memory now fits.
+ * stats may be NULL.  Errors: E_NOT_FOUND. */
+int dotpe_event_poll(dotpe_ctx *ctx, uint64_t event_id, int *state, dotpe_event_stats *stats);
+
+/* Blocks until the event is DONE or FAILED, at most timeout_s seconds
+ * (<= 0: no limit).  Errors: E_TIMEOUT, E_NOT_FOUND, E_DEVICE. */
+int dotpe_event_wait(dotpe_ctx *ctx, uint64_t event_id, double timeout_s);
+
+/* Evidence, effective sample sizes and the ML point of a finished event.
+ * Errors: E_NOT_READY, E_NOT_FOUND, E_DEVICE (device_status set). */
+int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out);
+
+/* Copies a block of per-pair or marginal results into out (host or device),
+ * row-major with leading dimension ld (floats).  LNL_MARG / LNL_ML_MAX need
+ * DOTPE_FLAG_STORE_LNL; i and e are relative to the event's slice.
+ * ROW_MARGINAL writes out[k] for i = i0+k; COL_MARGINAL out[k] for e = e0+k.
+ * Errors: E_NOT_READY, E_NOT_FOUND, E_INVALID (range), E_UNSUPPORTED. */
+int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, int64_t e0,
+                     int64_t e1, int what, float *out, int64_t ld);
+
+/* Frees an event's device state (waits for it if still running). */
+int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id);
+
+/* ---- diagnostics ------------------------------------------------------- */
+/* Evaluates the device distance marginal ln Lbar(dh, hh) (Eq.
+ * lnl_dist_marginalized with pi(d_L) ~ d_L^2, u_min = d0/d_max) for n inputs.
+ * dh, hh, out: host or device float arrays of length n.  Runs the same device
+ * function as the fused epilogue. */
+int dotpe_dist_marg_eval(dotpe_ctx *ctx, int64_t n, const float *dh, const float *hh, float u_min,
+                         float *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOTPE_H */

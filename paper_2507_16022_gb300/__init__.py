@@ -1,0 +1,287 @@
+"""Python binding of libdotpe (dense GW likelihood on GB300, arXiv 2507.16022).
+
+Argument marshalling only: every computation runs in the CUDA library behind
+the C ABI declared in include/dotpe.h.  The functions keep the ABI's names.
+Importing works without a GPU (the library only needs the CUDA runtime to
+load); calls that need a device fail with DotpeError when there is none.
+There is no CPU fallback: if libdotpe.so is missing the import raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdotpe.so")
+
+# ---- constants mirrored from include/dotpe.h ---------------------------------
+DOTPE_OK = 0
+DOTPE_E_INVALID = -1
+DOTPE_E_NOMEM = -2
+DOTPE_E_ADMISSION = -3
+DOTPE_E_NOT_READY = -4
+DOTPE_E_TIMEOUT = -5
+DOTPE_E_DEVICE = -6
+DOTPE_E_NOT_FOUND = -7
+DOTPE_E_UNSUPPORTED = -8
+
+DOTPE_PREC_FP32, DOTPE_PREC_BF16, DOTPE_PREC_FP16, DOTPE_PREC_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
+DOTPE_C128, DOTPE_C64 = 0, 1
+DOTPE_FLAG_STORE_LNL = 0x1
+DOTPE_FLAG_GEMM_ONLY = 0x2
+DOTPE_STATE_QUEUED, DOTPE_STATE_RUNNING, DOTPE_STATE_DONE, DOTPE_STATE_FAILED = 0, 1, 2, 3
+DOTPE_LNL_MARG, DOTPE_LNL_ML_MAX, DOTPE_ROW_MARGINAL, DOTPE_COL_MARGINAL = 0, 1, 2, 3
+
+# Public C symbols (kept in sync with include/dotpe.h by a test).
+SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_message",
+           "dotpe_version", "dotpe_device_info", "dotpe_bank_load", "dotpe_bank_release",
+           "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
+           "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval")
+
+
+class DotpeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+# ---- ctypes mirrors of the ABI structs ------------------------------------------
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class dotpe_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("n_slots", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class dotpe_bank_desc(ctypes.Structure):
+    _fields_ = [("n_int", ctypes.c_int64), ("n_modes", ctypes.c_int),
+                ("mode_m", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int),
+                ("f", _dp), ("w_quad", _dp), ("h", ctypes.c_void_p), ("h_dtype", ctypes.c_int),
+                ("ln_w_int", _dp)]
+
+
+class dotpe_event_desc(ctypes.Structure):
+    _fields_ = [("bank_id", ctypes.c_uint64), ("i0", ctypes.c_int64), ("i1", ctypes.c_int64),
+                ("n_det", ctypes.c_int), ("psd", _dp), ("data", _dp), ("n_ext", ctypes.c_int64),
+                ("t", _dp), ("R", _dp), ("ln_w_ext", _dp), ("n_phi", ctypes.c_int),
+                ("u_min", ctypes.c_double), ("cut_delta", ctypes.c_double),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class dotpe_event_stats(ctypes.Structure):
+    _fields_ = [("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("footprint_bytes", ctypes.c_int64), ("device_ms", ctypes.c_float),
+                ("precision", ctypes.c_int), ("state", ctypes.c_int)]
+
+
+class dotpe_evidence_out(ctypes.Structure):
+    _fields_ = [("ln_z", ctypes.c_double), ("n_eff", ctypes.c_double),
+                ("n_eff_int", ctypes.c_double), ("n_eff_ext", ctypes.c_double),
+                ("max_lnl_ml", ctypes.c_double), ("arg_i", ctypes.c_int64),
+                ("arg_e", ctypes.c_int64), ("arg_o", ctypes.c_int64),
+                ("n_marginalised", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("lnl_ml_threshold", ctypes.c_double), ("device_status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libdotpe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_2507_16022_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    vp, u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
+    sig = {
+        "dotpe_create": ([ctypes.POINTER(dotpe_config), ctypes.POINTER(vp)], ctypes.c_int),
+        "dotpe_destroy": ([vp], ctypes.c_int),
+        "dotpe_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "dotpe_last_error_message": ([], ctypes.c_char_p),
+        "dotpe_version": ([], ctypes.c_int),
+        "dotpe_device_info": ([vp, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p, ctypes.c_int],
+                              ctypes.c_int),
+        "dotpe_bank_load": ([vp, ctypes.POINTER(dotpe_bank_desc), u64p], ctypes.c_int),
+        "dotpe_bank_release": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "dotpe_event_submit": ([vp, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
+        "dotpe_event_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(dotpe_event_stats)], ctypes.c_int),
+        "dotpe_event_wait": ([vp, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
+        "dotpe_evidence": ([vp, ctypes.c_uint64, ctypes.POINTER(dotpe_evidence_out)], ctypes.c_int),
+        "dotpe_lnl_blocks": ([vp, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                              ctypes.c_int64, ctypes.c_int, vp, ctypes.c_int64], ctypes.c_int),
+        "dotpe_event_release": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "dotpe_dist_marg_eval": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != DOTPE_OK:
+        L = load()
+        raise DotpeError(status, f"{L.dotpe_strerror(status).decode()}: "
+                                 f"{L.dotpe_last_error_message().decode()}")
+    return status
+
+
+def _ptr(a, ctype=ctypes.c_double):
+    """Pointer to a contiguous numpy array (host) or an int device address."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.cast(ctypes.c_void_p(a), ctypes.POINTER(ctype))
+    if hasattr(a, "data_ptr"):  # torch tensor
+        return ctypes.cast(ctypes.c_void_p(a.data_ptr()), ctypes.POINTER(ctype))
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _host_c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+# ---- thin wrappers with the ABI's names ---------------------------------------
+def dotpe_create(device=0, hbm_budget_bytes=0, n_slots=0):
+    L = load()
+    cfg = dotpe_config(device, hbm_budget_bytes, n_slots, 0)
+    h = ctypes.c_void_p()
+    _check(L.dotpe_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def dotpe_destroy(ctx):
+    return _check(load().dotpe_destroy(ctx))
+
+
+def dotpe_version():
+    return load().dotpe_version()
+
+
+def dotpe_device_info(ctx):
+    n = ctypes.c_int()
+    buf = ctypes.create_string_buffer(256)
+    _check(load().dotpe_device_info(ctx, ctypes.byref(n), buf, 256))
+    return n.value, buf.value.decode()
+
+
+def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None):
+    """h: [I, M, B] complex128/complex64 numpy array, or a torch tensor on the device
+    (complex128/complex64, contiguous)."""
+    L = load()
+    keep = []
+    if hasattr(h, "data_ptr"):
+        import torch
+        dtype = DOTPE_C128 if h.dtype == torch.complex128 else DOTPE_C64
+        I, M, B = h.shape
+        hp = ctypes.c_void_p(h.data_ptr())
+    else:
+        if h.dtype == np.complex64:
+            h = np.ascontiguousarray(h)
+            dtype = DOTPE_C64
+        else:
+            h = _host_c128(h)
+            dtype = DOTPE_C128
+        I, M, B = h.shape
+        hp = ctypes.c_void_p(h.ctypes.data)
+        keep.append(h)
+    mm = np.ascontiguousarray(mode_m, dtype=np.int32)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    w = np.ascontiguousarray(w_quad, dtype=np.float64)
+    lw = None if ln_w_int is None else np.ascontiguousarray(ln_w_int, dtype=np.float64)
+    desc = dotpe_bank_desc(I, M, mm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), B, _ptr(f), _ptr(w),
+                           hp, dtype, _ptr(lw))
+    bid = ctypes.c_uint64()
+    _check(L.dotpe_bank_load(ctx, ctypes.byref(desc), ctypes.byref(bid)))
+    return bid.value
+
+
+def dotpe_bank_release(ctx, bank_id):
+    return _check(load().dotpe_bank_release(ctx, bank_id))
+
+
+def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
+                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None):
+    """psd [D,B], data [D,B] complex, t [E,D], R [E,D,M] complex, ln_w_ext [E]: numpy (host)
+    or torch tensors (host or device; complex tensors as float64 views are accepted)."""
+    L = load()
+    keep = []
+
+    def arr(a, cplx=False):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            keep.append(a)
+            return _ptr(a)
+        a = _host_c128(a) if cplx else np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return _ptr(a.view(np.float64) if cplx else a)
+
+    D, B = (psd.shape[0], psd.shape[1])
+    E = t.shape[0]
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    desc = dotpe_event_desc(bank_id, i0, i1, D, arr(psd), arr(data, True), E, arr(t), arr(R, True),
+                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st)
+    eid = ctypes.c_uint64()
+    _check(L.dotpe_event_submit(ctx, ctypes.byref(desc), ctypes.byref(eid)))
+    return eid.value
+
+
+def dotpe_event_poll(ctx, event_id):
+    st = ctypes.c_int()
+    s = dotpe_event_stats()
+    _check(load().dotpe_event_poll(ctx, event_id, ctypes.byref(st), ctypes.byref(s)))
+    return st.value, {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def dotpe_event_wait(ctx, event_id, timeout_s=0.0):
+    return _check(load().dotpe_event_wait(ctx, event_id, timeout_s))
+
+
+def dotpe_evidence(ctx, event_id):
+    o = dotpe_evidence_out()
+    _check(load().dotpe_evidence(ctx, event_id, ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def dotpe_lnl_blocks(ctx, event_id, i0, i1, e0, e1, what=DOTPE_LNL_MARG, out=None):
+    """Returns a float32 array (host) unless `out` (numpy or torch) is given."""
+    L = load()
+    if what in (DOTPE_ROW_MARGINAL, DOTPE_COL_MARGINAL):
+        n = (i1 - i0) if what == DOTPE_ROW_MARGINAL else (e1 - e0)
+        shape, ld = (n,), n
+    else:
+        shape, ld = (i1 - i0, e1 - e0), e1 - e0
+    if out is None:
+        out = np.empty(shape, dtype=np.float32)
+    p = ctypes.c_void_p(out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data)
+    _check(L.dotpe_lnl_blocks(ctx, event_id, i0, i1, e0, e1, what, p, ld))
+    return out
+
+
+def dotpe_event_release(ctx, event_id):
+    return _check(load().dotpe_event_release(ctx, event_id))
+
+
+def dotpe_dist_marg_eval(ctx, dh, hh, u_min):
+    dh = np.ascontiguousarray(dh, dtype=np.float32)
+    hh = np.ascontiguousarray(hh, dtype=np.float32)
+    out = np.empty_like(dh)
+    _check(load().dotpe_dist_marg_eval(ctx, dh.size, ctypes.c_void_p(dh.ctypes.data),
+                                       ctypes.c_void_p(hh.ctypes.data), float(u_min),
+                                       ctypes.c_void_p(out.ctypes.data)))
+    return out

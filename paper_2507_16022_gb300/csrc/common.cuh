@@ -1,0 +1,184 @@
+// Internal definitions shared by the dotpe CUDA translation units (sm_103a).
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dotpe.h"
+
+namespace dotpe {
+
+constexpr int MAXM = 4;    // modes per waveform
+constexpr int MAXD = 3;    // detectors (H, L, V)
+constexpr int REC = 16;    // floats per (row or column, detector) cross-term record
+constexpr int MAXPHI = 128;
+constexpr int NPAIR = 6;   // mode pairs (a > b) for MAXM = 4
+
+// Device error codes written into an event's status word (never __trap()).
+enum : int {
+  DEV_OK = 0,
+  DEV_E_NONFINITE = 1,     // NaN/Inf/non-positive PSD in the event inputs
+  DEV_E_TIMEOUT = 2,       // a bounded mbarrier wait ran out
+  DEV_E_SHAPE = 3,
+};
+
+// Everything the fused epilogue needs besides the per-pair GEMM outputs.
+struct EpiParams {
+  int n_modes, n_det, n_phi;
+  int mode_m[MAXM];
+  int npair;                // n_modes (n_modes - 1) / 2
+  int pdelta[NPAIR];        // m_a - m_b of pair p (index into C_delta, 1..3)
+  float u_min;
+  float z_scale;            // accumulator -> <d|h> component scale (times 1 / *g_scale)
+  const float *g_scale;     // device scale applied to the extrinsic operand (null: 1)
+  float cut_delta;          // > 0: coherent-ML selection on
+  float ln_nphi;
+  int64_t n_int, n_ext;     // slice sizes
+  int64_t i_base;           // first bank row of the slice
+  const float *mx;          // [n_int][n_det][REC] row cross-term records (slice-relative)
+  const float *qx;          // [n_ext][n_det][REC] column records
+  const double *lw_int;     // [n_int] slice-relative, may be null
+  const double *lw_ext;     // [n_ext], may be null
+  const float4 *dm_table;   // distance-marginal Hermite table
+  float *ml_running;        // running max of ln L^ML (>= 0)
+  // outputs
+  float4 *tile_part;        // [n_itile * n_etile] (m1, s1, m2, s2) of x = ln(w_i w_e sum_o Lbar)
+  float2 *row_part;         // [n_etile][n_int]
+  float2 *col_part;         // [n_itile][n_ext]
+  float *tile_ml;           // [n_tiles] best ln L^ML in tile
+  long long *tile_arg;      // [n_tiles] packed (i, e, o) of it
+  int *tile_npass;          // [n_tiles]
+  float *lnl_tile;          // optional [n_int][n_ext]
+  float *ml_tile;           // optional [n_int][n_ext]
+  int *status;
+  int gemm_only;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers (mbarrier, TMA, tcgen05)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait: gives up after limit_ns of wall time, records DEV_E_TIMEOUT
+// and returns false.  `abort` (shared) lets one timed-out role stop the others.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *status,
+                                          volatile int *abort, uint64_t limit_ns = 4000000000ull) {
+  if (mbar_try(b, parity)) return true;
+  uint64_t t0 = global_ns();
+  while (true) {
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k)
+      if (mbar_try(b, parity)) return true;
+    if (*abort) return false;
+    if (global_ns() - t0 > limit_ns) {
+      if (status) atomicCAS(status, 0, DEV_E_TIMEOUT);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+// K-major operand tile, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc_k128(const void *p) {
+  uint64_t a = smem_u32(p);
+  return ((a >> 4) & 0x3FFFull) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: D = F32, A/B = bf16 (1) or f16 (0), K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 lanes x 32-bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Order-preserving float max for values >= 0.
+__device__ __forceinline__ void atomic_max_nonneg(float *addr, float v) {
+  atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v));
+}
+
+}  // namespace dotpe

@@ -1,0 +1,923 @@
+// dotpe C ABI and runtime: context, bank residency, event admission by HBM
+// footprint, concurrent event slots (one CUDA stream each), results.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.h"
+
+namespace dotpe {
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_OR_FAIL(expr)                                                                         \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(e_ == cudaErrorMemoryAllocation ? DOTPE_E_NOMEM : DOTPE_E_DEVICE, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+  } while (0)
+
+static int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves one allocation into 256-byte aligned pieces.
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t n) {
+    size_t o = off;
+    off = align256(off + n * sizeof(T));
+    return o;
+  }
+};
+
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Bank {
+  uint64_t id = 0;
+  int64_t I = 0;
+  int M = 0, B = 0, Kpad = 0;
+  int mode_m[MAXM] = {0, 0, 0, 0};
+  double *f = nullptr, *w = nullptr, *lw = nullptr;  // device
+  float *master = nullptr;                           // [M][I][Kpad]
+  __nv_bfloat16 *bf = nullptr;                       // [2][M][I][Kpad] hi, lo
+  __half *hf = nullptr;                              // [M][I][Kpad]
+  float a_scale = 1.f;
+  void *block = nullptr;
+  size_t bytes = 0;
+  int refs = 0;
+};
+
+struct Event {
+  uint64_t id = 0;
+  Bank *bank = nullptr;
+  int state = DOTPE_STATE_QUEUED;
+  int64_t i0 = 0, NI = 0, NE = 0;
+  int D = 0, nphi = 0, prec = 0, flags = 0;
+  double u_min = 0, cut = 0;
+  bool has_lwe = false;
+  // inputs: device copy made at submit
+  void *in_block = nullptr;
+  size_t in_bytes = 0;
+  double *psd = nullptr, *t = nullptr, *lwe = nullptr;
+  double2 *data = nullptr, *R = nullptr;
+  void *in_stage = nullptr;  // pinned host staging of host inputs
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr;
+  // results kept until release
+  void *keep_block = nullptr;
+  size_t keep_bytes = 0;
+  double *ln_p_int = nullptr, *ln_p_ext = nullptr;
+  float *lnl_tile = nullptr, *ml_tile = nullptr;
+  ReduceOut *d_out = nullptr;
+  ReduceOut *h_out = nullptr;  // pinned
+  size_t scratch_bytes = 0;
+  int slot = -1;
+  int64_t t_submit = 0, t_admit = 0;
+  volatile int64_t t_done = 0;
+  float device_ms = -1.f;
+};
+
+}  // namespace dotpe
+
+struct dotpe_ctx {
+  int device = 0;
+  int n_sms = 0;
+  char name[256] = {0};
+  uint64_t budget = 0, used = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> slot_busy;
+  cudaStream_t main_stream = nullptr, input_stream = nullptr;
+  float4 *dm_table = nullptr;
+  std::mutex mu;
+  std::unordered_map<uint64_t, dotpe::Bank *> banks;
+  std::unordered_map<uint64_t, dotpe::Event *> events;
+  std::deque<uint64_t> queue;
+  uint64_t next_id = 1;
+};
+
+namespace dotpe {
+
+static void CUDART_CB mark_done(void *p) {
+  Event *ev = (Event *)p;
+  ev->t_done = now_ns();
+}
+
+// ---------------------------------------------------------------------------
+// footprint of one event's device scratch (freed when the event completes)
+// ---------------------------------------------------------------------------
+struct ScratchLayout {
+  size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, gpack, mx, tile_part, tile_ml, tile_arg,
+      tile_npass, row_part, col_part, ml_running, status, total;
+  int n_itile, n_etile, pack_kind, pack_planes, TI, TE;
+};
+
+static ScratchLayout scratch_layout(const Event &e) {
+  ScratchLayout L{};
+  const Bank &b = *e.bank;
+  const int64_t D = e.D, B = b.B, M = b.M, E = e.NE, NI = e.NI, Kp = b.Kpad;
+  const bool simt = (e.prec == DOTPE_PREC_FP32);
+  L.TI = simt ? SIMT_TI : TC_TI;
+  L.TE = simt ? SIMT_TE : TC_TE;
+  L.n_itile = (int)((NI + L.TI - 1) / L.TI);
+  L.n_etile = (int)((E + L.TE - 1) / L.TE);
+  L.pack_kind = simt ? 0 : (e.prec == DOTPE_PREC_FP16 ? 2 : 1);
+  L.pack_planes = (e.prec == DOTPE_PREC_BF16X3) ? 2 : 1;
+  size_t elem = (L.pack_kind == 0) ? 4 : 2;
+  const int64_t T = (int64_t)L.n_itile * L.n_etile;
+  Carver c;
+  L.c = c.take<float2>(D * B);
+  L.omega = c.take<float>(D * B);
+  L.fh = c.take<float>(B);
+  L.fl = c.take<float>(B);
+  L.th = c.take<float>(E * D);
+  L.tl = c.take<float>(E * D);
+  L.Rf = c.take<float2>(E * D * M);
+  L.qx = c.take<float>(E * D * REC);
+  L.G32 = c.take<float2>(M * E * B);
+  L.gmax = c.take<float>(1);
+  L.gscale = c.take<float>(1);
+  L.gpack = c.take<uint8_t>((size_t)L.pack_planes * M * 2 * E * Kp * elem);
+  L.mx = c.take<float>(NI * D * REC);
+  L.tile_part = c.take<float4>(T);
+  L.tile_ml = c.take<float>(T);
+  L.tile_arg = c.take<long long>(T);
+  L.tile_npass = c.take<int>(T);
+  L.row_part = c.take<float2>((size_t)L.n_etile * NI);
+  L.col_part = c.take<float2>((size_t)L.n_itile * E);
+  L.ml_running = c.take<float>(1);
+  L.status = c.take<int>(1);
+  L.total = c.off;
+  return L;
+}
+
+static size_t keep_bytes_of(const Event &e) {
+  size_t k = align256(sizeof(ReduceOut)) + align256(e.NI * 8) + align256(e.NE * 8);
+  if (e.flags & DOTPE_FLAG_STORE_LNL) k += 2 * align256((size_t)e.NI * e.NE * 4);
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// launch one admitted event on its slot stream
+// ---------------------------------------------------------------------------
+static int run_event(dotpe_ctx *ctx, Event &e) {
+  cudaStream_t st = ctx->streams[e.slot];
+  Bank &b = *e.bank;
+  ScratchLayout L = scratch_layout(e);
+  e.scratch_bytes = L.total;
+  uint8_t *scr = nullptr;
+  CUDA_OR_FAIL(cudaStreamWaitEvent(st, e.ev_inputs, 0));
+  CUDA_OR_FAIL(cudaMallocAsync((void **)&scr, L.total, st));
+  // keep block
+  e.keep_bytes = keep_bytes_of(e);
+  uint8_t *keep = nullptr;
+  CUDA_OR_FAIL(cudaMallocAsync((void **)&keep, e.keep_bytes, st));
+  e.keep_block = keep;
+  {
+    Carver c;
+    e.d_out = (ReduceOut *)(keep + c.take<ReduceOut>(1));
+    e.ln_p_int = (double *)(keep + c.take<double>(e.NI));
+    e.ln_p_ext = (double *)(keep + c.take<double>(e.NE));
+    if (e.flags & DOTPE_FLAG_STORE_LNL) {
+      e.lnl_tile = (float *)(keep + c.take<float>((size_t)e.NI * e.NE));
+      e.ml_tile = (float *)(keep + c.take<float>((size_t)e.NI * e.NE));
+    }
+  }
+  CUDA_OR_FAIL(cudaMemsetAsync(scr + L.gmax, 0, 4, st));
+  CUDA_OR_FAIL(cudaMemsetAsync(scr + L.ml_running, 0, 4, st));
+  CUDA_OR_FAIL(cudaMemsetAsync(scr + L.status, 0, 4, st));
+  CUDA_OR_FAIL(cudaEventRecord(e.ev_start, st));
+
+  int *status = (int *)(scr + L.status);
+  PrepArgs pa;
+  pa.D = e.D; pa.B = b.B; pa.M = b.M; pa.Kpad = b.Kpad; pa.E = e.NE;
+  pa.f = b.f; pa.w = b.w; pa.psd = e.psd; pa.data = e.data; pa.t = e.t; pa.R = e.R;
+  pa.c = (float2 *)(scr + L.c);
+  pa.omega = (float *)(scr + L.omega);
+  pa.fh = (float *)(scr + L.fh);
+  pa.fl = (float *)(scr + L.fl);
+  pa.th = (float *)(scr + L.th);
+  pa.tl = (float *)(scr + L.tl);
+  pa.Rf = (float2 *)(scr + L.Rf);
+  pa.qx = (float *)(scr + L.qx);
+  pa.G32 = (float2 *)(scr + L.G32);
+  pa.gmax = (float *)(scr + L.gmax);
+  pa.gpack = scr + L.gpack;
+  pa.pack_kind = L.pack_kind;
+  pa.pack_planes = L.pack_planes;
+  pa.gscale = (float *)(scr + L.gscale);
+  pa.status = status;
+  launch_prep(pa, st);
+  float *mx = (float *)(scr + L.mx);
+  launch_cross_terms(e.NI, e.i0, b.I, b.M, e.D, b.B, b.Kpad, b.master, pa.omega, mx, ctx->n_sms, st);
+
+  EpiParams P;
+  memset(&P, 0, sizeof(P));
+  P.n_modes = b.M;
+  P.n_det = e.D;
+  P.n_phi = e.nphi;
+  for (int m = 0; m < MAXM; ++m) P.mode_m[m] = m < b.M ? b.mode_m[m] : 0;
+  P.npair = b.M * (b.M - 1) / 2;
+  {
+    int p = 0;
+    for (int a = 1; a < MAXM; ++a)
+      for (int c = 0; c < a; ++c, ++p) P.pdelta[p] = (a < b.M) ? (b.mode_m[a] - b.mode_m[c]) : 0;
+  }
+  P.u_min = (float)e.u_min;
+  P.cut_delta = (float)(e.cut > 0 ? e.cut : 0.0);
+  P.ln_nphi = (float)std::log((double)e.nphi);
+  P.n_int = e.NI;
+  P.n_ext = e.NE;
+  P.i_base = e.i0;
+  P.mx = mx;
+  P.qx = pa.qx;
+  P.lw_int = b.lw ? b.lw + e.i0 : nullptr;
+  P.lw_ext = e.has_lwe ? e.lwe : nullptr;
+  P.dm_table = ctx->dm_table;
+  P.ml_running = (float *)(scr + L.ml_running);
+  P.tile_part = (float4 *)(scr + L.tile_part);
+  P.row_part = (float2 *)(scr + L.row_part);
+  P.col_part = (float2 *)(scr + L.col_part);
+  P.tile_ml = (float *)(scr + L.tile_ml);
+  P.tile_arg = (long long *)(scr + L.tile_arg);
+  P.tile_npass = (int *)(scr + L.tile_npass);
+  P.lnl_tile = e.lnl_tile;
+  P.ml_tile = e.ml_tile;
+  P.status = status;
+  P.gemm_only = (e.flags & DOTPE_FLAG_GEMM_ONLY) ? 1 : 0;
+
+  if (e.prec == DOTPE_PREC_FP32) {
+    P.z_scale = 1.f;
+    P.g_scale = nullptr;
+    SimtArgs g;
+    g.A = b.master;
+    g.Bm = (const float *)pa.gpack;
+    g.I_bank = b.I;
+    g.Kpad = b.Kpad;
+    g.K = 2 * b.B;
+    launch_simt(g, P, st);
+  } else {
+    P.z_scale = 1.f / b.a_scale;
+    P.g_scale = pa.gscale;
+    TcArgs g;
+    memset(&g, 0, sizeof(g));
+    const bool bf = (e.prec != DOTPE_PREC_FP16);
+    g.bf16 = bf;
+    g.kb_per_mode = b.Kpad / 64;
+    g.n_sms = ctx->n_sms;
+    const int64_t a_rows = (bf ? 2 : 1) * (int64_t)b.M * b.I;
+    const int64_t b_rows = (int64_t)L.pack_planes * b.M * 2 * e.NE;
+    if (a_rows >= (1ll << 31) || b_rows >= (1ll << 31))
+      return fail(DOTPE_E_UNSUPPORTED, "operand too large for 32-bit TMA coordinates");
+    CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    void *abase = bf ? (void *)b.bf : (void *)b.hf;
+    if (encode_tmap_2d(&g.mapA, dt, abase, b.Kpad, a_rows, (uint64_t)b.Kpad * 2, 64, TC_TI) ||
+        encode_tmap_2d(&g.mapB, dt, pa.gpack, b.Kpad, b_rows, (uint64_t)b.Kpad * 2, 64, 2 * TC_TE))
+      return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed");
+    g.a_plane_rows = b.M * (int)b.I;
+    g.a_mode_rows = (int)b.I;
+    g.a_row0 = (int)e.i0;
+    g.b_plane_rows = b.M * 2 * (int)e.NE;
+    g.b_mode_rows = 2 * (int)e.NE;
+    if (e.prec == DOTPE_PREC_BF16X3) {
+      g.n_pass = 3;
+      g.pa[0] = 0; g.pb[0] = 0;  // hi * hi
+      g.pa[1] = 0; g.pb[1] = 1;  // hi * lo
+      g.pa[2] = 1; g.pb[2] = 0;  // lo * hi
+    } else {
+      g.n_pass = 1;
+    }
+    int r = launch_tc(g, P, st);
+    if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+  }
+
+  ReduceArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.n_int = e.NI;
+  ra.n_ext = e.NE;
+  ra.n_itile = L.n_itile;
+  ra.n_etile = L.n_etile;
+  ra.n_phi = e.nphi;
+  ra.tile_part = P.tile_part;
+  ra.row_part = P.row_part;
+  ra.col_part = P.col_part;
+  ra.tile_ml = P.tile_ml;
+  ra.tile_arg = P.tile_arg;
+  ra.tile_npass = P.tile_npass;
+  ra.ml_running = P.ml_running;
+  ra.cut_delta = P.cut_delta;
+  ra.ln_p_int = e.ln_p_int;
+  ra.ln_p_ext = e.ln_p_ext;
+  ra.status = status;
+  ra.out = e.d_out;
+  launch_reduce(ra, st);
+  CUDA_OR_FAIL(cudaGetLastError());
+  CUDA_OR_FAIL(cudaMemcpyAsync(e.h_out, e.d_out, sizeof(ReduceOut), cudaMemcpyDeviceToHost, st));
+  CUDA_OR_FAIL(cudaEventRecord(e.ev_end, st));
+  CUDA_OR_FAIL(cudaLaunchHostFunc(st, mark_done, &e));
+  CUDA_OR_FAIL(cudaFreeAsync(scr, st));
+  CUDA_OR_FAIL(cudaFreeAsync(e.in_block, st));
+  e.in_block = nullptr;
+  return DOTPE_OK;
+}
+
+// Admits queued events in order while a slot and budget are available.
+static void progress(dotpe_ctx *ctx) {
+  // retire finished events: free their slot and scratch budget
+  for (auto &kv : ctx->events) {
+    Event &e = *kv.second;
+    if (e.state == DOTPE_STATE_RUNNING) {
+      cudaError_t q = cudaEventQuery(e.ev_end);
+      if (q == cudaSuccess) {
+        e.state = (e.h_out->status == 0) ? DOTPE_STATE_DONE : DOTPE_STATE_FAILED;
+        float ms = -1.f;
+        if (cudaEventElapsedTime(&ms, e.ev_start, e.ev_end) == cudaSuccess) e.device_ms = ms;
+        if (e.t_done == 0) e.t_done = now_ns();
+        ctx->slot_busy[e.slot] = 0;
+        ctx->used -= e.scratch_bytes + e.in_bytes;
+        e.scratch_bytes = 0;
+        e.in_bytes = 0;
+        if (e.in_stage) {
+          cudaFreeHost(e.in_stage);
+          e.in_stage = nullptr;
+        }
+      } else if (q != cudaErrorNotReady) {
+        cudaGetLastError();
+        e.state = DOTPE_STATE_FAILED;
+        ctx->slot_busy[e.slot] = 0;
+      }
+    }
+  }
+  while (!ctx->queue.empty()) {
+    uint64_t id = ctx->queue.front();
+    auto it = ctx->events.find(id);
+    if (it == ctx->events.end()) {
+      ctx->queue.pop_front();
+      continue;
+    }
+    Event &e = *it->second;
+    int slot = -1;
+    for (size_t s = 0; s < ctx->slot_busy.size(); ++s)
+      if (!ctx->slot_busy[s]) {
+        slot = (int)s;
+        break;
+      }
+    if (slot < 0) break;
+    size_t need = scratch_layout(e).total + keep_bytes_of(e);
+    if (ctx->used + need > ctx->budget) break;
+    ctx->queue.pop_front();
+    e.slot = slot;
+    ctx->slot_busy[slot] = 1;
+    ctx->used += need;
+    e.t_admit = now_ns();
+    e.state = DOTPE_STATE_RUNNING;
+    if (run_event(ctx, e) != DOTPE_OK) {
+      e.state = DOTPE_STATE_FAILED;
+      ctx->slot_busy[slot] = 0;
+    }
+  }
+}
+
+static void free_event(dotpe_ctx *ctx, Event *e) {
+  if (e->state == DOTPE_STATE_RUNNING) cudaEventSynchronize(e->ev_end);
+  if (e->keep_block) cudaFree(e->keep_block);
+  if (e->in_block) cudaFree(e->in_block);
+  if (e->in_stage) cudaFreeHost(e->in_stage);
+  if (e->h_out) cudaFreeHost(e->h_out);
+  if (e->ev_inputs) cudaEventDestroy(e->ev_inputs);
+  if (e->ev_start) cudaEventDestroy(e->ev_start);
+  if (e->ev_end) cudaEventDestroy(e->ev_end);
+  size_t give = e->keep_bytes + e->scratch_bytes + e->in_bytes;
+  if (e->state == DOTPE_STATE_QUEUED) give = e->in_bytes;
+  ctx->used = (ctx->used >= give) ? ctx->used - give : 0;
+  if (e->slot >= 0 && e->state == DOTPE_STATE_RUNNING) ctx->slot_busy[e->slot] = 0;
+  if (e->bank) e->bank->refs--;
+  delete e;
+}
+
+}  // namespace dotpe
+
+using namespace dotpe;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *dotpe_strerror(int s) {
+  switch (s) {
+    case DOTPE_OK: return "ok";
+    case DOTPE_E_INVALID: return "invalid argument";
+    case DOTPE_E_NOMEM: return "out of memory";
+    case DOTPE_E_ADMISSION: return "event can never fit the HBM budget";
+    case DOTPE_E_NOT_READY: return "not ready";
+    case DOTPE_E_TIMEOUT: return "timeout";
+    case DOTPE_E_DEVICE: return "CUDA device error";
+    case DOTPE_E_NOT_FOUND: return "not found";
+    case DOTPE_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char *dotpe_last_error_message(void) { return g_last_error.c_str(); }
+
+int dotpe_version(void) { return DOTPE_ABI_VERSION; }
+
+int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
+  if (!out) return fail(DOTPE_E_INVALID, "out is null");
+  *out = nullptr;
+  dotpe_config c;
+  memset(&c, 0, sizeof(c));
+  if (cfg) c = *cfg;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return fail(DOTPE_E_DEVICE, "no CUDA device");
+  }
+  if (c.device < 0 || c.device >= ndev) return fail(DOTPE_E_INVALID, "device %d out of range", c.device);
+  CUDA_OR_FAIL(cudaSetDevice(c.device));
+  cudaDeviceProp prop;
+  CUDA_OR_FAIL(cudaGetDeviceProperties(&prop, c.device));
+  if (prop.major < 10) return fail(DOTPE_E_UNSUPPORTED, "device %s (sm_%d%d) lacks tcgen05", prop.name, prop.major, prop.minor);
+  dotpe_ctx *ctx = new dotpe_ctx();
+  ctx->device = c.device;
+  ctx->n_sms = prop.multiProcessorCount;
+  snprintf(ctx->name, sizeof(ctx->name), "%s", prop.name);
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  ctx->budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
+  int ns = c.n_slots > 0 ? c.n_slots : 4;
+  ctx->streams.resize(ns);
+  ctx->slot_busy.assign(ns, 0);
+  for (int s = 0; s < ns; ++s) cudaStreamCreateWithFlags(&ctx->streams[s], cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&ctx->main_stream, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&ctx->input_stream, cudaStreamNonBlocking);
+  // keep freed stream-ordered memory in the pool for reuse
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c.device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaError_t e = cudaMalloc(&ctx->dm_table, dm_table_elems() * sizeof(float4));
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(DOTPE_E_NOMEM, "table allocation: %s", cudaGetErrorString(e));
+  }
+  launch_build_dm_table(ctx->dm_table, ctx->main_stream);
+  e = cudaStreamSynchronize(ctx->main_stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(ctx->dm_table);
+    delete ctx;
+    return fail(DOTPE_E_DEVICE, "table build: %s", cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return DOTPE_OK;
+}
+
+int dotpe_destroy(dotpe_ctx *ctx) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  cudaSetDevice(ctx->device);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto &kv : ctx->events) free_event(ctx, kv.second);
+    ctx->events.clear();
+    for (auto &kv : ctx->banks) {
+      cudaFree(kv.second->block);
+      delete kv.second;
+    }
+    ctx->banks.clear();
+  }
+  cudaDeviceSynchronize();
+  cudaFree(ctx->dm_table);
+  for (auto s : ctx->streams) cudaStreamDestroy(s);
+  cudaStreamDestroy(ctx->main_stream);
+  cudaStreamDestroy(ctx->input_stream);
+  delete ctx;
+  return DOTPE_OK;
+}
+
+int dotpe_device_info(dotpe_ctx *ctx, int *n_sms, char *name, int name_len) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  if (n_sms) *n_sms = ctx->n_sms;
+  if (name && name_len > 0) snprintf(name, (size_t)name_len, "%s", ctx->name);
+  return DOTPE_OK;
+}
+
+// copies n bytes from a host or device pointer into device memory
+static int copy_in(void *dst, const void *src, size_t n, cudaStream_t st) {
+  if (n == 0) return DOTPE_OK;
+  CUDA_OR_FAIL(cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, st));
+  return DOTPE_OK;
+}
+
+int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id) {
+  if (!ctx || !d || !bank_id) return fail(DOTPE_E_INVALID, "null argument");
+  if (d->n_int < 1 || d->n_modes < 1 || d->n_modes > MAXM || d->n_bins < 2 || !d->mode_m || !d->f || !d->w_quad ||
+      !d->h)
+    return fail(DOTPE_E_INVALID, "bank shape: n_int=%lld n_modes=%d n_bins=%d", (long long)d->n_int, d->n_modes,
+                d->n_bins);
+  if (d->h_dtype != DOTPE_C128 && d->h_dtype != DOTPE_C64) return fail(DOTPE_E_INVALID, "h_dtype");
+  for (int m = 0; m < d->n_modes; ++m) {
+    if (d->mode_m[m] < 1 || d->mode_m[m] > 4) return fail(DOTPE_E_INVALID, "mode_m[%d]=%d not in 1..4", m, d->mode_m[m]);
+    if (m > 0 && d->mode_m[m] <= d->mode_m[m - 1]) return fail(DOTPE_E_INVALID, "mode_m must increase");
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  Bank *b = new Bank();
+  b->I = d->n_int;
+  b->M = d->n_modes;
+  b->B = d->n_bins;
+  b->Kpad = (int)(((2 * (int64_t)d->n_bins + 63) / 64) * 64);
+  for (int m = 0; m < d->n_modes; ++m) b->mode_m[m] = d->mode_m[m];
+  const size_t nel = (size_t)b->M * b->I * b->Kpad;
+  Carver c;
+  size_t o_f = c.take<double>(b->B), o_w = c.take<double>(b->B), o_lw = c.take<double>(b->I);
+  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(nel);
+  size_t o_scal = c.take<float>(4);
+  b->bytes = c.off;
+  if (ctx->used + b->bytes > ctx->budget) {
+    delete b;
+    return fail(DOTPE_E_NOMEM, "bank needs %zu bytes beyond the budget", c.off);
+  }
+  cudaError_t e = cudaMalloc(&b->block, b->bytes);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(DOTPE_E_NOMEM, "bank allocation of %zu bytes: %s", c.off, cudaGetErrorString(e));
+  }
+  uint8_t *base = (uint8_t *)b->block;
+  b->f = (double *)(base + o_f);
+  b->w = (double *)(base + o_w);
+  b->lw = d->ln_w_int ? (double *)(base + o_lw) : nullptr;
+  b->master = (float *)(base + o_master);
+  b->bf = (__nv_bfloat16 *)(base + o_bf);
+  b->hf = (__half *)(base + o_hf);
+  float *scal = (float *)(base + o_scal);  // [0] amax, [1] a_scale, [2] status
+  cudaStream_t st = ctx->main_stream;
+  int rc = DOTPE_OK;
+  auto check = [&](cudaError_t x) {
+    if (x != cudaSuccess && rc == DOTPE_OK) rc = fail(DOTPE_E_DEVICE, "bank load: %s", cudaGetErrorString(x));
+  };
+  check(cudaMemsetAsync(b->master, 0, nel * sizeof(float), st));
+  check(cudaMemsetAsync(scal, 0, 16, st));
+  check(cudaMemcpyAsync(b->f, d->f, b->B * 8, cudaMemcpyDefault, st));
+  check(cudaMemcpyAsync(b->w, d->w_quad, b->B * 8, cudaMemcpyDefault, st));
+  if (d->ln_w_int) check(cudaMemcpyAsync(b->lw, d->ln_w_int, b->I * 8, cudaMemcpyDefault, st));
+  // stream the waveforms through a device staging buffer in row chunks
+  const size_t row_bytes = (size_t)b->M * b->B * (d->h_dtype == DOTPE_C128 ? 16 : 8);
+  const bool hdev = is_device_ptr(d->h);
+  int64_t chunk = (int64_t)((256u << 20) / row_bytes);
+  if (chunk < 1) chunk = 1;
+  void *stage = nullptr;
+  void *pin = nullptr;
+  if (!hdev) {
+    check(cudaMalloc(&stage, (size_t)std::min<int64_t>(chunk, b->I) * row_bytes));
+    check(cudaHostAlloc(&pin, (size_t)std::min<int64_t>(chunk, b->I) * row_bytes, cudaHostAllocDefault));
+  }
+  for (int64_t r0 = 0; r0 < b->I && rc == DOTPE_OK; r0 += chunk) {
+    int64_t rows = std::min<int64_t>(chunk, b->I - r0);
+    const uint8_t *src = (const uint8_t *)d->h + (size_t)r0 * row_bytes;
+    const void *dsrc = src;
+    if (!hdev) {
+      check(cudaStreamSynchronize(st));  // previous chunk done with the pinned buffer
+      memcpy(pin, src, (size_t)rows * row_bytes);
+      check(cudaMemcpyAsync(stage, pin, (size_t)rows * row_bytes, cudaMemcpyHostToDevice, st));
+      dsrc = stage;
+    }
+    launch_bank_to_master(rows, r0, b->I, b->M, b->B, b->Kpad, dsrc, d->h_dtype, b->master, &scal[0],
+                          (int *)&scal[2], st);
+  }
+  launch_master_to_planes((int64_t)nel, b->master, &scal[0], b->bf, b->hf, &scal[1], st);
+  check(cudaGetLastError());
+  check(cudaStreamSynchronize(st));
+  if (stage) cudaFree(stage);
+  if (pin) cudaFreeHost(pin);
+  float hs[4] = {0, 0, 0, 0};
+  if (rc == DOTPE_OK) check(cudaMemcpy(hs, scal, 16, cudaMemcpyDeviceToHost));
+  if (rc == DOTPE_OK && *(int *)&hs[2] != 0) rc = fail(DOTPE_E_INVALID, "bank contains non-finite values");
+  if (rc == DOTPE_OK && !(hs[0] > 0.f)) rc = fail(DOTPE_E_INVALID, "bank is all zero");
+  if (rc != DOTPE_OK) {
+    cudaFree(b->block);
+    delete b;
+    return rc;
+  }
+  b->a_scale = hs[1];
+  b->id = ctx->next_id++;
+  ctx->banks[b->id] = b;
+  ctx->used += b->bytes;
+  *bank_id = b->id;
+  return DOTPE_OK;
+}
+
+int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->banks.find(bank_id);
+  if (it == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)bank_id);
+  if (it->second->refs > 0) return fail(DOTPE_E_INVALID, "bank still used by %d events", it->second->refs);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(it->second->block);
+  ctx->used -= it->second->bytes;
+  delete it->second;
+  ctx->banks.erase(it);
+  return DOTPE_OK;
+}
+
+int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *event_id) {
+  if (!ctx || !d || !event_id) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  auto bit = ctx->banks.find(d->bank_id);
+  if (bit == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)d->bank_id);
+  Bank *b = bit->second;
+  if (d->i0 < 0 || d->i1 <= d->i0 || d->i1 > b->I) return fail(DOTPE_E_INVALID, "slice [%lld,%lld) of %lld rows",
+                                                               (long long)d->i0, (long long)d->i1, (long long)b->I);
+  if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
+  if (d->n_ext < 1) return fail(DOTPE_E_INVALID, "n_ext=%lld", (long long)d->n_ext);
+  if (d->n_phi < 1 || d->n_phi > MAXPHI) return fail(DOTPE_E_INVALID, "n_phi=%d not in 1..%d", d->n_phi, MAXPHI);
+  if (!(d->u_min > 0.0) || !std::isfinite(d->u_min)) return fail(DOTPE_E_INVALID, "u_min must be > 0");
+  if (!d->psd || !d->data || !d->t || !d->R) return fail(DOTPE_E_INVALID, "null input array");
+  if (d->precision < DOTPE_PREC_FP32 || d->precision > DOTPE_PREC_BF16X3)
+    return fail(DOTPE_E_INVALID, "precision %d", d->precision);
+  const int64_t NI = d->i1 - d->i0, NE = d->n_ext;
+  if (d->precision != DOTPE_PREC_FP32 && (2 * (int64_t)b->M * 2 * NE >= (1ll << 31)))
+    return fail(DOTPE_E_UNSUPPORTED, "n_ext too large");
+  Event *e = new Event();
+  e->bank = b;
+  e->i0 = d->i0;
+  e->NI = NI;
+  e->NE = NE;
+  e->D = d->n_det;
+  e->nphi = d->n_phi;
+  e->prec = d->precision;
+  e->flags = d->flags;
+  e->u_min = d->u_min;
+  e->cut = d->cut_delta;
+  e->has_lwe = d->ln_w_ext != nullptr;
+  // footprint check against the whole budget
+  size_t need = scratch_layout(*e).total + keep_bytes_of(*e);
+  Carver c;
+  const int64_t D = e->D, B = b->B, M = b->M;
+  size_t o_psd = c.take<double>(D * B), o_data = c.take<double2>(D * B), o_t = c.take<double>(NE * D);
+  size_t o_R = c.take<double2>(NE * D * M), o_lw = c.take<double>(NE);
+  e->in_bytes = c.off;
+  if (need + e->in_bytes + b->bytes > ctx->budget) {
+    delete e;
+    return fail(DOTPE_E_ADMISSION, "event needs %zu device bytes, budget %llu", need + c.off,
+                (unsigned long long)ctx->budget);
+  }
+  // device copy of the inputs, ordered after the caller's stream
+  cudaStream_t ist = ctx->input_stream;
+  auto cleanup = [&](int rc) {
+    if (e->in_block) cudaFree(e->in_block);
+    if (e->in_stage) cudaFreeHost(e->in_stage);
+    delete e;
+    return rc;
+  };
+  if (cudaMallocAsync(&e->in_block, e->in_bytes, ist) != cudaSuccess) {
+    cudaGetLastError();
+    delete e;
+    return fail(DOTPE_E_NOMEM, "event inputs");
+  }
+  uint8_t *ib = (uint8_t *)e->in_block;
+  e->psd = (double *)(ib + o_psd);
+  e->data = (double2 *)(ib + o_data);
+  e->t = (double *)(ib + o_t);
+  e->R = (double2 *)(ib + o_R);
+  e->lwe = (double *)(ib + o_lw);
+  struct Piece { const void *src; void *dst; size_t n; };
+  Piece pieces[5] = {{d->psd, e->psd, (size_t)(D * B * 8)},
+                     {d->data, e->data, (size_t)(D * B * 16)},
+                     {d->t, e->t, (size_t)(NE * D * 8)},
+                     {d->R, e->R, (size_t)(NE * D * M * 16)},
+                     {d->ln_w_ext, e->lwe, d->ln_w_ext ? (size_t)(NE * 8) : 0}};
+  size_t host_total = 0;
+  for (auto &p : pieces)
+    if (p.n && !is_device_ptr(p.src)) host_total += p.n;
+  if (host_total) {
+    if (cudaHostAlloc(&e->in_stage, host_total, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(fail(DOTPE_E_NOMEM, "pinned staging"));
+    }
+    e->stage_bytes = host_total;
+  }
+  if (d->stream) {
+    cudaEvent_t dep;
+    cudaEventCreateWithFlags(&dep, cudaEventDisableTiming);
+    cudaEventRecord(dep, (cudaStream_t)d->stream);
+    cudaStreamWaitEvent(ist, dep, 0);
+    cudaEventDestroy(dep);
+  }
+  size_t so = 0;
+  for (auto &p : pieces) {
+    if (!p.n) continue;
+    if (is_device_ptr(p.src)) {
+      if (copy_in(p.dst, p.src, p.n, ist) != DOTPE_OK) return cleanup(DOTPE_E_DEVICE);
+    } else {
+      uint8_t *hs = (uint8_t *)e->in_stage + so;
+      memcpy(hs, p.src, p.n);
+      so += p.n;
+      if (copy_in(p.dst, hs, p.n, ist) != DOTPE_OK) return cleanup(DOTPE_E_DEVICE);
+    }
+  }
+  cudaEventCreateWithFlags(&e->ev_inputs, cudaEventDisableTiming);
+  cudaEventCreate(&e->ev_start);
+  cudaEventCreate(&e->ev_end);
+  cudaEventRecord(e->ev_inputs, ist);
+  if (cudaHostAlloc((void **)&e->h_out, sizeof(ReduceOut), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(DOTPE_E_NOMEM, "pinned result"));
+  }
+  memset(e->h_out, 0, sizeof(ReduceOut));
+  e->id = ctx->next_id++;
+  e->t_submit = now_ns();
+  b->refs++;
+  ctx->used += e->in_bytes;
+  ctx->events[e->id] = e;
+  ctx->queue.push_back(e->id);
+  *event_id = e->id;
+  progress(ctx);
+  if (e->state == DOTPE_STATE_FAILED) return fail(DOTPE_E_DEVICE, "launch failed: %s", g_last_error.c_str());
+  return DOTPE_OK;
+}
+
+static void fill_stats(const Event &e, dotpe_event_stats *s) {
+  if (!s) return;
+  s->t_submit_ns = e.t_submit;
+  s->t_admit_ns = e.t_admit;
+  s->t_done_ns = e.t_done;
+  s->n_pairs = e.NI * e.NE;
+  s->footprint_bytes = (int64_t)(e.keep_bytes + scratch_layout(e).total + e.in_bytes);
+  s->device_ms = e.device_ms;
+  s->precision = e.prec;
+  s->state = e.state;
+}
+
+int dotpe_event_poll(dotpe_ctx *ctx, uint64_t event_id, int *state, dotpe_event_stats *stats) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  progress(ctx);
+  auto it = ctx->events.find(event_id);
+  if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+  if (state) *state = it->second->state;
+  fill_stats(*it->second, stats);
+  return DOTPE_OK;
+}
+
+int dotpe_event_wait(dotpe_ctx *ctx, uint64_t event_id, double timeout_s) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  const int64_t t0 = now_ns();
+  while (true) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      cudaSetDevice(ctx->device);
+      progress(ctx);
+      auto it = ctx->events.find(event_id);
+      if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+      int s = it->second->state;
+      if (s == DOTPE_STATE_DONE) return DOTPE_OK;
+      if (s == DOTPE_STATE_FAILED) return fail(DOTPE_E_DEVICE, "event failed (device status %d)", it->second->h_out->status);
+    }
+    if (timeout_s > 0 && (now_ns() - t0) > (int64_t)(timeout_s * 1e9)) return fail(DOTPE_E_TIMEOUT, "event wait");
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out) {
+  if (!ctx || !out) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  progress(ctx);
+  auto it = ctx->events.find(event_id);
+  if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+  Event &e = *it->second;
+  if (e.state == DOTPE_STATE_QUEUED || e.state == DOTPE_STATE_RUNNING) return fail(DOTPE_E_NOT_READY, "event not done");
+  const ReduceOut &r = *e.h_out;
+  memset(out, 0, sizeof(*out));
+  out->ln_z = r.ln_z;
+  out->n_eff = r.n_eff;
+  out->n_eff_int = r.n_eff_int;
+  out->n_eff_ext = r.n_eff_ext;
+  out->max_lnl_ml = r.max_ml;
+  long long a = r.arg;
+  out->arg_o = a % e.nphi;
+  a /= e.nphi;
+  out->arg_e = a % e.NE;
+  out->arg_i = a / e.NE + e.i0;
+  out->n_marginalised = r.n_marg;
+  out->n_pairs = e.NI * e.NE;
+  out->lnl_ml_threshold = r.threshold;
+  out->device_status = r.status;
+  if (r.status == DEV_E_NONFINITE) return fail(DOTPE_E_INVALID, "non-finite or non-positive event input");
+  if (r.status == DEV_E_TIMEOUT) return fail(DOTPE_E_TIMEOUT, "device wait timed out");
+  if (r.status != 0) return fail(DOTPE_E_DEVICE, "device status %d", r.status);
+  return DOTPE_OK;
+}
+
+int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, int64_t e0, int64_t e1, int what,
+                     float *out, int64_t ld) {
+  if (!ctx || !out) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  progress(ctx);
+  auto it = ctx->events.find(event_id);
+  if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+  Event &e = *it->second;
+  if (e.state != DOTPE_STATE_DONE) return fail(DOTPE_E_NOT_READY, "event not done");
+  if (what == DOTPE_LNL_MARG || what == DOTPE_LNL_ML_MAX) {
+    if (!(e.flags & DOTPE_FLAG_STORE_LNL)) return fail(DOTPE_E_UNSUPPORTED, "event ran without DOTPE_FLAG_STORE_LNL");
+    if (i0 < 0 || i1 > e.NI || i1 <= i0 || e0 < 0 || e1 > e.NE || e1 <= e0 || ld < e1 - e0)
+      return fail(DOTPE_E_INVALID, "block range");
+    const float *src = (what == DOTPE_LNL_MARG ? e.lnl_tile : e.ml_tile) + i0 * e.NE + e0;
+    CUDA_OR_FAIL(cudaMemcpy2D(out, ld * 4, src, e.NE * 4, (e1 - e0) * 4, i1 - i0, cudaMemcpyDefault));
+    return DOTPE_OK;
+  }
+  if (what == DOTPE_ROW_MARGINAL || what == DOTPE_COL_MARGINAL) {
+    const bool row = what == DOTPE_ROW_MARGINAL;
+    int64_t a = row ? i0 : e0, z = row ? i1 : e1, n = row ? e.NI : e.NE;
+    if (a < 0 || z > n || z <= a) return fail(DOTPE_E_INVALID, "marginal range");
+    std::vector<double> tmp(z - a);
+    CUDA_OR_FAIL(cudaMemcpy(tmp.data(), (row ? e.ln_p_int : e.ln_p_ext) + a, (z - a) * 8, cudaMemcpyDeviceToHost));
+    std::vector<float> f(z - a);
+    for (size_t k = 0; k < f.size(); ++k) f[k] = (float)tmp[k];
+    CUDA_OR_FAIL(cudaMemcpy(out, f.data(), f.size() * 4, cudaMemcpyDefault));
+    return DOTPE_OK;
+  }
+  return fail(DOTPE_E_INVALID, "what=%d", what);
+}
+
+int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  auto it = ctx->events.find(event_id);
+  if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+  Event *e = it->second;
+  if (e->state == DOTPE_STATE_RUNNING) {
+    cudaEventSynchronize(e->ev_end);
+    progress(ctx);
+  }
+  for (auto q = ctx->queue.begin(); q != ctx->queue.end(); ++q)
+    if (*q == event_id) {
+      ctx->queue.erase(q);
+      break;
+    }
+  ctx->events.erase(it);
+  free_event(ctx, e);
+  progress(ctx);
+  return DOTPE_OK;
+}
+
+int dotpe_dist_marg_eval(dotpe_ctx *ctx, int64_t n, const float *dh, const float *hh, float u_min, float *out) {
+  if (!ctx || !dh || !hh || !out || n < 0) return fail(DOTPE_E_INVALID, "null argument");
+  if (n == 0) return DOTPE_OK;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  float *buf = nullptr;
+  CUDA_OR_FAIL(cudaMalloc(&buf, 3 * n * sizeof(float)));
+  cudaStream_t st = ctx->main_stream;
+  cudaMemcpyAsync(buf, dh, n * 4, cudaMemcpyDefault, st);
+  cudaMemcpyAsync(buf + n, hh, n * 4, cudaMemcpyDefault, st);
+  launch_dist_marg_eval(n, buf, buf + n, u_min, ctx->dm_table, buf + 2 * n, st);
+  cudaMemcpyAsync(out, buf + 2 * n, n * 4, cudaMemcpyDefault, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(DOTPE_E_DEVICE, "%s", cudaGetErrorString(e));
+  return DOTPE_OK;
+}
+
+}  // extern "C"

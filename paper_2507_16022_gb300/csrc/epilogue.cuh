@@ -1,0 +1,169 @@
+// Fused per-pair epilogue shared by the FP32 SIMT and tcgen05 kernels.
+//
+// Given the per-mode components Z_m = sum_b h_{im}(b) G_m[b,e] of one (i,e)
+// pair (Eq. dh_ieo: Re<d|h>(phi) = Re sum_m Z_m e^{i m phi}) and the <h|h>
+// coefficients C_0, C_delta (Eq. hh_ieo: <h|h>(phi) = C_0 + 2 Re sum_delta
+// C_delta e^{i delta phi}), evaluate on the regular phase grid phi_o:
+//   ln L^ML_o   (Eq. bestfit_lnl),
+//   the coherent-ML selection (Eq. coherent_ML_selection) against `thr`,
+//   ln Lbar_o   (Eq. lnl_dist_marginalized, device table),
+//   and the phase sums ln sum_o Lbar_o, ln sum_o Lbar_o^2 (w_o = 1).
+#pragma once
+#include "common.cuh"
+#include "dist_marg.cuh"
+
+namespace dotpe {
+
+struct PairRes {
+  float lsum;   // ln sum_o Lbar_o (-inf if no phase marginalised)
+  float lsum2;  // ln sum_o Lbar_o^2
+  float ml;     // max_o ln L^ML_o
+  int argo;     // its phase index (lowest on ties)
+  int npass;    // phases marginalised
+};
+
+// Phase tables in shared memory: ph_mode[m][o] = (cos, sin)(m_m phi_o) for the
+// waveform's modes, ph_delta[k-1][o] = (cos, sin)(k phi_o), k = 1..3.
+__device__ __forceinline__ void fill_phase_tables(float2 *ph, const EpiParams &P, int tid, int nthreads) {
+  for (int k = tid; k < 7 * MAXPHI; k += nthreads) {
+    int row = k / MAXPHI, o = k % MAXPHI;
+    int mult = row < MAXM ? (row < P.n_modes ? P.mode_m[row] : 0) : (row - MAXM + 1);
+    float s, c;
+    // angle = mult * 2 pi o / n_phi, reduced exactly in integers first
+    int num = (mult * o) % (P.n_phi > 0 ? P.n_phi : 1);
+    sincospif(2.0f * (float)num / (float)P.n_phi, &s, &c);
+    ph[k] = make_float2(c, s);
+  }
+}
+
+// <h|h> coefficients for one pair from the row record (mrec) and column record (qrec):
+// C_0 = sum_d sum_m M_d[m,m] Q_d[m,m];  C_delta = sum_d sum_{a>b, m_a-m_b=delta} M_d[a,b] Q_d[a,b].
+__device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const float *__restrict__ qrec,
+                                          const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
+  C0 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { Cr[k] = 0.f; Ci[k] = 0.f; }
+#pragma unroll
+  for (int d = 0; d < MAXD; ++d) {
+    if (d >= P.n_det) break;
+    const float *mr = mrec + d * REC;
+    const float *qr = qrec + d * REC;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) C0 = fmaf(mr[m], qr[m], C0);
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+      float ar = mr[4 + 2 * p], ai = mr[5 + 2 * p];
+      float br = qr[4 + 2 * p], bi = qr[5 + 2 * p];
+      float hr = ar * br - ai * bi;
+      float hi = ar * bi + ai * br;
+      int dl = P.pdelta[p];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        bool sel = (dl == k + 1);
+        Cr[k] += sel ? hr : 0.f;
+        Ci[k] += sel ? hi : 0.f;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ PairRes pair_eval(const float Zr[MAXM], const float Zi[MAXM], float C0,
+                                             const float Cr[3], const float Ci[3], float thr, bool allow_skip,
+                                             const EpiParams &P, const float2 *__restrict__ ph) {
+  PairRes R;
+  R.lsum = -INFINITY;
+  R.lsum2 = -INFINITY;
+  R.ml = 0.f;
+  R.argo = 0;
+  R.npass = 0;
+  if (allow_skip && thr > 0.f) {
+    // upper bound of max_o ln L^ML: |dh| <= sum |Z_m|, hh >= C_0 - 2 sum |C_delta|
+    float a = 0.f, hmin = C0;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) a += sqrtf(Zr[m] * Zr[m] + Zi[m] * Zi[m]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) hmin -= 2.f * sqrtf(Cr[k] * Cr[k] + Ci[k] * Ci[k]);
+    if (hmin > 0.f && a * a < 2.f * hmin * thr) return R;
+  }
+  const float2 *phm = ph;
+  const float2 *phd = ph + MAXM * MAXPHI;
+  float mx = -INFINITY, s1 = 0.f, s2 = 0.f;
+  float best = -1.f;
+  int argo = 0, npass = 0;
+  for (int o = 0; o < P.n_phi; ++o) {
+    float dh = 0.f;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      float2 cs = phm[m * MAXPHI + o];
+      dh = fmaf(Zr[m], cs.x, fmaf(-Zi[m], cs.y, dh));
+    }
+    float hs = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float2 cs = phd[k * MAXPHI + o];
+      hs = fmaf(Cr[k], cs.x, fmaf(-Ci[k], cs.y, hs));
+    }
+    float hh = fmaf(2.f, hs, C0);
+    float ml = (dh > 0.f && hh > 0.f) ? __fdividef(0.5f * dh * dh, hh) : 0.f;
+    if (ml > best) { best = ml; argo = o; }
+    if (!(ml >= thr)) continue;
+    ++npass;
+    float l = dm_lnlbar(dh, hh, P.u_min, P.dm_table);
+    if (l > mx) {
+      float r = __expf(mx - l);
+      s1 = fmaf(s1, r, 1.f);
+      s2 = fmaf(s2, r * r, 1.f);
+      mx = l;
+    } else {
+      float q = __expf(l - mx);
+      s1 += q;
+      s2 = fmaf(q, q, s2);
+    }
+  }
+  R.ml = best;
+  R.argo = argo;
+  R.npass = npass;
+  if (npass > 0) {
+    R.lsum = mx + __logf(s1);
+    R.lsum2 = 2.f * mx + __logf(s2);
+  }
+  return R;
+}
+
+// Online log-sum-exp accumulator.
+struct Lse {
+  float m, s;
+  __device__ __forceinline__ void init() { m = -INFINITY; s = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    if (x == -INFINITY) return;
+    if (x > m) { s = fmaf(s, __expf(m - x), 1.f); m = x; }
+    else s += __expf(x - m);
+  }
+  __device__ __forceinline__ void merge(float om, float os) {
+    if (om == -INFINITY) return;
+    if (m == -INFINITY) { m = om; s = os; return; }
+    if (om > m) { s = fmaf(s, __expf(m - om), os); m = om; }
+    else s = fmaf(os, __expf(om - m), s);
+  }
+};
+
+__device__ __forceinline__ void warp_merge_lse(Lse &a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float om = __shfl_xor_sync(0xffffffffu, a.m, o);
+    float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+    a.merge(om, os);
+  }
+}
+
+// (value, packed index) max with lowest index on ties
+__device__ __forceinline__ void warp_argmax(float &v, long long &idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    long long oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+}
+
+}  // namespace dotpe

@@ -1,0 +1,368 @@
+// K3: fused <d|h> GEMM on the 5th-generation tensor cores + marginalisation epilogue.
+//
+// Persistent kernel, one CTA per SM, warp-specialised:
+//   warp 0      TMA producer: bank tile A (128 rows x 64 k) and extrinsic tile B
+//               (64 rows = 32 samples x (re, im), 64 k) into a STAGES-deep ring
+//   warp 1      TMEM allocator and tcgen05.mma issuer (one elected lane)
+//   warps 2..5  epilogue: tcgen05.ld of the accumulators, <h|h> coefficients,
+//               phase grid, ML cut, distance marginal, log-sum-exp partials
+// Tile = 128 bank rows x 32 extrinsic samples, all modes: accumulators for mode
+// m live in TMEM columns [buf*256 + 64 m, +64) (two buffers, so the epilogue of
+// tile t overlaps the MMAs of tile t+1).  Per mode the GEMM is the real-ified
+// complex product of Eq. dh_ieo (K = 2B, padded to a multiple of 64); split
+// precision adds passes over hi/lo operand planes into the same accumulator.
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "kernels.h"
+
+namespace dotpe {
+
+namespace {
+constexpr int TI = TC_TI, TE = TC_TE, BN = 2 * TE, BK = 64, ST = 7;
+constexpr int NT = 192;
+constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 512, BUF_COLS = MAXM * BN;
+constexpr int XS_LD = TE + 1;
+static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
+
+struct TcShape {
+  int n_itile, n_etile, kb, n_pass;
+  int pa[3], pb[3];
+  int a_plane_rows, a_mode_rows, a_row0;
+  int b_plane_rows, b_mode_rows;
+};
+
+struct TcTail {
+  float xs[TI * XS_LD];
+  float qs[TE * MAXD * REC];
+  double lwe[TE];
+  float2 ph[7 * MAXPHI];
+  float wm1[4], ws1[4], wm2[4], ws2[4], wml[4];
+  long long warg[4];
+  int wnp[4];
+  uint64_t full[ST], empty[ST], tfull[2], tempty[2], drain;
+  uint32_t tmem_slot;
+  int abort_flag;
+};
+constexpr size_t SMEM_BYTES = 1024 + (size_t)ST * STAGE_BYTES + sizeof(TcTail);
+}  // namespace
+
+template <bool BF16>
+__global__ void __launch_bounds__(NT, 1)
+    tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                    const TcShape S, const EpiParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = base;
+  uint8_t *sB = base + ST * A_BYTES;
+  TcTail &T = *reinterpret_cast<TcTail *>(base + (size_t)ST * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tiles = S.n_itile * S.n_etile;
+  const int M = P.n_modes;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&T.full[s], 1);
+      mbar_init(&T.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&T.tfull[b], 1);
+      mbar_init(&T.tempty[b], 4);
+    }
+    mbar_init(&T.drain, 1);
+    T.abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&mapA);
+    tma_prefetch_desc(&mapB);
+  }
+  if (warp == 1) tmem_alloc(&T.tmem_slot, TMEM_COLS);
+  if (warp >= 2) fill_phase_tables(T.ph, P, threadIdx.x - 64, 128);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = T.tmem_slot;
+  volatile int *abortp = &T.abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      uint32_t q = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int it = t / S.n_etile, et = t % S.n_etile;
+        for (int m = 0; m < M && ok; ++m)
+          for (int p = 0; p < S.n_pass && ok; ++p) {
+            const int arow = S.pa[p] * S.a_plane_rows + m * S.a_mode_rows + S.a_row0 + it * TI;
+            const int brow = S.pb[p] * S.b_plane_rows + m * S.b_mode_rows + et * BN;
+            for (int kb = 0; kb < S.kb; ++kb, ++q) {
+              const int s = q % ST;
+              const uint32_t n = q / ST;
+              if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, P.status, abortp))) break;
+              mbar_expect_tx(&T.full[s], STAGE_BYTES);
+              tma_load_2d(sA + s * A_BYTES, &mapA, &T.full[s], kb * BK, arow);
+              tma_load_2d(sB + s * B_BYTES, &mapB, &T.full[s], kb * BK, brow);
+            }
+          }
+      }
+      if (!ok) {
+        // let copies already in flight land before the CTA exits
+        uint32_t first = q > (uint32_t)ST ? q - ST : 0;
+        for (uint32_t j = first; j < q; ++j) {
+          volatile int no_abort = 0;
+          mbar_wait(&T.full[j % ST], (j / ST) & 1, nullptr, &no_abort, 200000000ull);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
+      uint32_t q = 0, u = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++u) {
+        const int b = u & 1;
+        const uint32_t use = u >> 1;
+        if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, P.status, abortp))) break;
+        tc_fence_after();
+        for (int m = 0; m < M && ok; ++m) {
+          const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
+          for (int p = 0; p < S.n_pass && ok; ++p)
+            for (int kb = 0; kb < S.kb; ++kb, ++q) {
+              const int s = q % ST;
+              const uint32_t n = q / ST;
+              if (!(ok = mbar_wait(&T.full[s], n & 1, P.status, abortp))) break;
+              tc_fence_after();
+              const uint64_t ad = sdesc_k128(sA + s * A_BYTES), bd = sdesc_k128(sB + s * B_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                tc_mma(dcol, ad + 2 * k, bd + 2 * k, idesc, (p | kb | k) ? 1u : 0u);
+              tc_commit(&T.empty[s]);
+            }
+        }
+        if (ok) tc_commit(&T.tfull[b]);
+      }
+      // all MMAs of this CTA complete before TMEM is released
+      tc_commit(&T.drain);
+      volatile int no_abort = 0;
+      mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
+    }
+  } else {
+    // ---------------- epilogue (128 threads, one tile row each) ----------------
+    const int ew = warp - 2;
+    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row = quad * 32 + lane;
+    const int etid = threadIdx.x - 64;
+    const bool store = (P.lnl_tile != nullptr);
+    const float zs = P.z_scale / (P.g_scale ? *P.g_scale : 1.f);
+    float mrec[MAXD * REC];
+    double lwi = 0.0;
+    int cur_it = -1;
+    uint32_t u = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++u) {
+      const int b = u & 1;
+      const uint32_t use = u >> 1;
+      const int it = t / S.n_etile, et = t % S.n_etile;
+      const int64_t i = (int64_t)it * TI + row;
+      const bool vi = i < P.n_int;
+      const int64_t e0 = (int64_t)et * TE;
+      if (it != cur_it) {
+#pragma unroll
+        for (int k = 0; k < MAXD * REC; ++k) mrec[k] = 0.f;
+        const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
+#pragma unroll
+        for (int k = 0; k < MAXD * REC / 4; ++k) {
+          if (vi && k < P.n_det * REC / 4) {
+            float4 v = __ldg(src + k);
+            mrec[4 * k] = v.x; mrec[4 * k + 1] = v.y; mrec[4 * k + 2] = v.z; mrec[4 * k + 3] = v.w;
+          }
+        }
+        lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
+        cur_it = it;
+      }
+      for (int k = etid; k < TE * P.n_det * REC; k += 128) {
+        const int e = k / (P.n_det * REC), qq = k % (P.n_det * REC);
+        T.qs[e * MAXD * REC + qq] = (e0 + e < P.n_ext) ? __ldg(P.qx + (e0 + e) * P.n_det * REC + qq) : 0.f;
+      }
+      for (int k = etid; k < TE; k += 128) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
+      named_bar_sync(1, 128);
+      const float thr = (P.cut_delta > 0.f) ? (*(volatile float *)P.ml_running - P.cut_delta) : -INFINITY;
+      if (!mbar_wait(&T.tfull[b], use & 1, P.status, abortp)) break;
+      tc_fence_after();
+
+      Lse ra, rb;
+      ra.init();
+      rb.init();
+      float best = -1.f;
+      long long barg = 0x7fffffffffffffffLL;
+      int np = 0;
+      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS;
+#pragma unroll 1
+      for (int c = 0; c < TE / 8; ++c) {
+        float z[MAXM][16];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) {
+          if (m < M) tmem_ld16(tbase + m * BN + c * 16, z[m]);
+          else
+#pragma unroll
+            for (int k = 0; k < 16; ++k) z[m][k] = 0.f;
+        }
+        tmem_ld_wait();
+        if (c == TE / 8 - 1) {
+          // accumulators of this buffer are in registers: hand it back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&T.tempty[b]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int el = c * 8 + j;
+          const int64_t e = e0 + el;
+          float x = -INFINITY, x2 = -INFINITY;
+          if (vi && e < P.n_ext) {
+            float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              Zr[m] = z[m][2 * j] * zs;
+              Zi[m] = z[m][2 * j + 1] * zs;
+            }
+            if (P.gemm_only) {
+              float sx = 0.f;
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) sx += Zr[m] + Zi[m];
+              x = sx;
+              x2 = sx;
+            } else {
+              float C0, Cr[3], Ci[3];
+              hh_coeffs(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+              PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph);
+              const float lw = (float)(lwi + T.lwe[el]);
+              x = pr.lsum + lw;
+              x2 = pr.lsum2 + 2.f * lw;
+              np += pr.npass;
+              if (pr.ml > best) {
+                best = pr.ml;
+                barg = (i * P.n_ext + e) * (long long)P.n_phi + pr.argo;
+              }
+              if (store) {
+                P.lnl_tile[i * P.n_ext + e] = pr.lsum - P.ln_nphi;
+                P.ml_tile[i * P.n_ext + e] = pr.ml;
+              }
+            }
+          }
+          T.xs[row * XS_LD + el] = x;
+          ra.add(x);
+          rb.add(x2);
+        }
+      }
+      if (vi) P.row_part[(int64_t)et * P.n_int + i] = make_float2(ra.m, ra.s);
+      warp_merge_lse(ra);
+      warp_merge_lse(rb);
+      warp_argmax(best, barg);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+      if (lane == 0) {
+        T.wm1[ew] = ra.m; T.ws1[ew] = ra.s; T.wm2[ew] = rb.m; T.ws2[ew] = rb.s;
+        T.wml[ew] = best; T.warg[ew] = barg; T.wnp[ew] = np;
+      }
+      named_bar_sync(1, 128);
+      {
+        // column partials: 4 threads per extrinsic sample, 32 rows each
+        const int cc = etid >> 2, qq = etid & 3;
+        Lse a;
+        a.init();
+        for (int r = qq * 32; r < qq * 32 + 32; ++r) a.add(T.xs[r * XS_LD + cc]);
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+          float om = __shfl_xor_sync(0xffffffffu, a.m, o);
+          float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+          a.merge(om, os);
+        }
+        if (qq == 0 && e0 + cc < P.n_ext) P.col_part[(int64_t)it * P.n_ext + e0 + cc] = make_float2(a.m, a.s);
+      }
+      if (etid == 0) {
+        Lse a, bb;
+        a.init();
+        bb.init();
+        float bv = -1.f;
+        long long bi = 0x7fffffffffffffffLL;
+        int n = 0;
+        for (int w = 0; w < 4; ++w) {
+          a.merge(T.wm1[w], T.ws1[w]);
+          bb.merge(T.wm2[w], T.ws2[w]);
+          n += T.wnp[w];
+          if (T.wml[w] > bv || (T.wml[w] == bv && T.warg[w] < bi)) { bv = T.wml[w]; bi = T.warg[w]; }
+        }
+        P.tile_part[t] = make_float4(a.m, a.s, bb.m, bb.s);
+        P.tile_ml[t] = bv;
+        P.tile_arg[t] = bi;
+        P.tile_npass[t] = n;
+        if (bv > 0.f && P.cut_delta > 0.f) atomic_max_nonneg(P.ml_running, bv);
+      }
+      named_bar_sync(1, 128);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t inner, uint64_t rows,
+                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows) {
+  if (!g_encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(map, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -2;
+}
+
+int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
+  TcShape S;
+  S.n_itile = (int)((P.n_int + TI - 1) / TI);
+  S.n_etile = (int)((P.n_ext + TE - 1) / TE);
+  S.kb = g.kb_per_mode;
+  S.n_pass = g.n_pass;
+  for (int k = 0; k < 3; ++k) { S.pa[k] = g.pa[k]; S.pb[k] = g.pb[k]; }
+  S.a_plane_rows = g.a_plane_rows;
+  S.a_mode_rows = g.a_mode_rows;
+  S.a_row0 = g.a_row0;
+  S.b_plane_rows = g.b_plane_rows;
+  S.b_mode_rows = g.b_mode_rows;
+  const int n_tiles = S.n_itile * S.n_etile;
+  int grid = g.n_sms < n_tiles ? g.n_sms : n_tiles;
+  if (grid < 1) grid = 1;
+  cudaError_t err;
+  if (g.bf16) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+      attr = true;
+    }
+    tc_fused_kernel<true><<<grid, NT, SMEM_BYTES, st>>>(g.mapA, g.mapB, S, P);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+      attr = true;
+    }
+    tc_fused_kernel<false><<<grid, NT, SMEM_BYTES, st>>>(g.mapA, g.mapB, S, P);
+  }
+  err = cudaGetLastError();
+  return (int)err;
+}
+
+}  // namespace dotpe

@@ -1,0 +1,104 @@
+// Host-side launchers of the dotpe kernels (internal).
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace dotpe {
+
+struct PrepArgs {
+  int D, B, M, Kpad;
+  int64_t E;
+  // inputs (device)
+  const double *f, *w, *psd;
+  const double2 *data;
+  const double *t;
+  const double2 *R;
+  // outputs (device)
+  float2 *c;
+  float *omega, *fh, *fl, *th, *tl;
+  float2 *Rf;
+  float *qx;
+  float2 *G32;     // [M][E][B]
+  float *gmax;     // 1 float, zeroed
+  void *gpack;     // packed operand planes
+  int pack_kind;   // 0 fp32, 1 bf16, 2 fp16
+  int pack_planes; // 1 or 2 (bf16 hi/lo)
+  float *gscale;   // 1 float out
+  int *status;
+};
+
+void launch_prep(const PrepArgs &a, cudaStream_t st);
+void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
+                        const float *master, const float *omega, float *mx, int n_sms, cudaStream_t st);
+void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, const void *src,
+                           int dtype, float *master, float *amax, int *status, cudaStream_t st);
+void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf, __half *hf,
+                             float *scale_out, cudaStream_t st);
+void launch_build_dm_table(float4 *tab, cudaStream_t st);
+void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
+                           cudaStream_t st);
+size_t dm_table_elems();
+
+// Fused <d|h> GEMM + marginalisation epilogue, FP32 SIMT (plain path).
+struct SimtArgs {
+  const float *A;   // FP32 master [M][I_bank][Kpad]
+  const float *Bm;  // FP32 packed G [M][2E][Kpad]
+  int64_t I_bank;
+  int Kpad, K;      // K = 2B (multiple-of-8 not required)
+};
+constexpr int SIMT_TI = 64, SIMT_TE = 32;
+void launch_simt(const SimtArgs &g, const EpiParams &P, cudaStream_t st);
+
+// Fused tcgen05 kernel.
+constexpr int TC_TI = 128, TC_TE = 32;
+struct TcArgs {
+  CUtensorMap mapA, mapB;
+  int kb_per_mode;   // Kpad / 64
+  int n_pass;
+  int pa[3], pb[3];  // plane index of A and B per pass
+  int a_plane_rows, a_mode_rows, a_row0;
+  int b_plane_rows, b_mode_rows;
+  bool bf16;
+  int n_sms;
+};
+int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st);  // returns cudaError_t as int
+
+// Cross-tile FP64 reduction -> evidence.
+struct ReduceOut {
+  double ln_z, ln_s1, ln_s2, n_eff, n_eff_int, n_eff_ext;
+  double max_ml;
+  long long arg;
+  long long n_marg;
+  double threshold;
+  int status;
+  int pad;
+};
+struct ReduceArgs {
+  int64_t n_int, n_ext;
+  int n_itile, n_etile, n_phi;
+  const float4 *tile_part;
+  const float2 *row_part, *col_part;
+  const float *tile_ml;
+  const long long *tile_arg;
+  const int *tile_npass;
+  const float *ml_running;
+  float cut_delta;
+  double *ln_p_int;  // [n_int] out
+  double *ln_p_ext;  // [n_ext] out
+  double *scratch;   // >= 2 * 1024 doubles
+  const int *status;
+  ReduceOut *out;
+};
+void launch_reduce(const ReduceArgs &a, cudaStream_t st);
+
+// Tensor-map encoding through the driver entry point.
+int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t inner, uint64_t rows,
+                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows);
+
+}  // namespace dotpe

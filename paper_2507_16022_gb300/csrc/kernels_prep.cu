@@ -1,0 +1,396 @@
+// Per-event preparation, bank conversion and the distance-marginal table.
+//
+//  K0  prep_bins / prep_ext   data weights c_{d,b} = 4 w_b conj(d_d(f_b)) / S_d(f_b) and
+//                             omega_{d,b} = 4 w_b / S_d(f_b) (Eq. inner_product) in FP64,
+//                             input validation, FP32 hi/lo splits of f and t
+//  K1  build_G / pack_G       G_m[b,e] = sum_d R_{e,d,m} exp(-2 pi i f_b t_{e,d}) c_{d,b}
+//                             (Eq. dh_ieo with the detector sum folded into G), packed as
+//                             the real-ified K-major operand [(e,re),(e,im)] x [re | im];
+//                             column cross-term records Q_d[e] = R_{e,d,m} R^*_{e,d,m'}
+//                             (Eq. hh_ieo)
+//  K2  cross_terms            row records <h_{im}|h_{im'}>_d = sum_b omega_{d,b} h h'^*
+//  K9  build_dm_table         FP64 Gauss-Legendre table of the distance-marginal remainder
+#include "common.cuh"
+#include "dist_marg.cuh"
+#include "kernels.h"
+
+namespace dotpe {
+
+// ---------------------------------------------------------------------------
+// K0
+// ---------------------------------------------------------------------------
+__global__ void prep_bins_kernel(int D, int B, const double *__restrict__ f, const double *__restrict__ w,
+                                 const double *__restrict__ psd, const double2 *__restrict__ data,
+                                 float2 *__restrict__ c, float *__restrict__ omega, float *__restrict__ fh,
+                                 float *__restrict__ fl, int *status) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < B) {
+    double fb = f[k];
+    float h = (float)fb;
+    fh[k] = h;
+    fl[k] = (float)(fb - (double)h);
+    if (!isfinite(fb) || !isfinite(w[k])) atomicCAS(status, 0, DEV_E_NONFINITE);
+  }
+  if (k >= D * B) return;
+  int b = k % B;
+  double S = psd[k];
+  double2 dk = data[k];
+  if (!(S > 0.0) || !isfinite(S) || !isfinite(dk.x) || !isfinite(dk.y)) {
+    atomicCAS(status, 0, DEV_E_NONFINITE);
+    S = 1.0; dk = make_double2(0.0, 0.0);
+  }
+  double om = 4.0 * w[b] / S;
+  omega[k] = (float)om;
+  float2 cv = make_float2((float)(om * dk.x), (float)(-om * dk.y));
+  c[k] = cv;
+}
+
+__global__ void prep_ext_kernel(int64_t E, int D, int M, const double *__restrict__ t,
+                                const double2 *__restrict__ R, float *__restrict__ th, float *__restrict__ tl,
+                                float2 *__restrict__ Rf, float *__restrict__ qx, int *status) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= E * D) return;
+  double tv = t[k];
+  if (!isfinite(tv)) { atomicCAS(status, 0, DEV_E_NONFINITE); tv = 0.0; }
+  float h = (float)tv;
+  th[k] = h;
+  tl[k] = (float)(tv - (double)h);
+  float2 r[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    double2 v = (m < M) ? R[k * M + m] : make_double2(0.0, 0.0);
+    if (!isfinite(v.x) || !isfinite(v.y)) { atomicCAS(status, 0, DEV_E_NONFINITE); v = make_double2(0.0, 0.0); }
+    r[m] = make_float2((float)v.x, (float)v.y);
+    if (m < M) Rf[k * M + m] = r[m];
+  }
+  // column record of <h|h>: |R_m|^2 and R_a R_b^* for a > b (Eq. hh_ieo)
+  float *q = qx + k * REC;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) q[m] = r[m].x * r[m].x + r[m].y * r[m].y;
+  int p = 0;
+#pragma unroll
+  for (int a = 1; a < MAXM; ++a)
+#pragma unroll
+    for (int b = 0; b < a; ++b, ++p) {
+      q[4 + 2 * p] = r[a].x * r[b].x + r[a].y * r[b].y;
+      q[5 + 2 * p] = r[a].y * r[b].x - r[a].x * r[b].y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1
+// ---------------------------------------------------------------------------
+// exp(-2 pi i f t) with the phase f t formed to ~1e-9 cycles in FP32:
+// exact product of the hi parts (FMA), cross terms of the lo parts.
+__device__ __forceinline__ float2 shift_factor(float fh, float fl, float th, float tl) {
+  float p = fh * th;
+  float e1 = fmaf(fh, th, -p);
+  float e2 = fmaf(fh, tl, fl * th);
+  float n = rintf(p);
+  float q = (p - n) + (e1 + e2);
+  float s, c;
+  sincospif(2.0f * q, &s, &c);
+  return make_float2(c, -s);
+}
+
+__global__ void build_G_kernel(int64_t E, int D, int M, int B, const float *__restrict__ fh,
+                               const float *__restrict__ fl, const float *__restrict__ th,
+                               const float *__restrict__ tl, const float2 *__restrict__ c,
+                               const float2 *__restrict__ Rf, float2 *__restrict__ G /*[M][E][B]*/,
+                               float *__restrict__ gmax) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= E * B) return;
+  int64_t e = k / B;
+  int b = (int)(k % B);
+  float2 g[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) g[m] = make_float2(0.f, 0.f);
+  float f_h = fh[b], f_l = fl[b];
+  for (int d = 0; d < D; ++d) {
+    float2 T = shift_factor(f_h, f_l, th[e * D + d], tl[e * D + d]);
+    float2 cc = c[d * B + b];
+    float2 W = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      if (m >= M) break;
+      float2 r = Rf[(e * D + d) * M + m];
+      g[m].x += r.x * W.x - r.y * W.y;
+      g[m].y += r.x * W.y + r.y * W.x;
+    }
+  }
+  float a = 0.f;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    if (m >= M) break;
+    G[((int64_t)m * E + e) * B + b] = g[m];
+    a = fmaxf(a, fmaxf(fabsf(g[m].x), fabsf(g[m].y)));
+  }
+  atomic_max_nonneg(gmax, a);
+}
+
+__device__ __forceinline__ float pow2_scale(float maxabs) {
+  // 2^-ceil(log2(maxabs)): scaled magnitudes land in (1/2, 1]
+  if (!(maxabs > 0.f) || !isfinite(maxabs)) return 1.0f;
+  int ex;
+  frexpf(maxabs, &ex);
+  return ldexpf(1.0f, -ex);
+}
+
+// Real-ified operand rows: (e, re) = [Gr | -Gi], (e, im) = [Gi | Gr], K padded with zeros.
+// kind: 0 = fp32 plane, 1 = bf16 hi (+ lo if nplanes == 2), 2 = fp16 hi.
+__global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *__restrict__ G,
+                              const float *__restrict__ gmax, int kind, int nplanes, void *__restrict__ out,
+                              float *__restrict__ scale_out) {
+  int64_t total = (int64_t)M * 2 * E * Kpad;
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float sc = (kind == 0) ? 1.0f : pow2_scale(*gmax);
+  if (k == 0 && scale_out) *scale_out = sc;
+  if (k >= total) return;
+  int col = (int)(k % Kpad);
+  int64_t row = k / Kpad;  // m * 2E + 2e + ri
+  int ri = (int)(row & 1);
+  int64_t me = row >> 1;   // m * E + e
+  float v = 0.f;
+  if (col < 2 * B) {
+    int b = col < B ? col : col - B;
+    float2 g = G[me * B + b];
+    if (ri == 0) v = (col < B) ? g.x : -g.y;
+    else v = (col < B) ? g.y : g.x;
+  }
+  v *= sc;
+  if (kind == 0) {
+    ((float *)out)[k] = v;
+  } else if (kind == 1) {
+    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    ((__nv_bfloat16 *)out)[k] = hi;
+    if (nplanes == 2) ((__nv_bfloat16 *)out)[total + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  } else {
+    ((__half *)out)[k] = __float2half_rn(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: row records <h_{im}|h_{im'}>_d  (one warp per bank row)
+// ---------------------------------------------------------------------------
+__global__ void cross_terms_kernel(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
+                                   const float *__restrict__ master /*[M][I_bank][Kpad]*/,
+                                   const float *__restrict__ omega /*[D][B]*/, float *__restrict__ mx) {
+  extern __shared__ float om_s[];
+  for (int k = threadIdx.x; k < D * B; k += blockDim.x) om_s[k] = omega[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp_global; i < n_rows; i += nwarps) {
+    float acc[MAXD][REC];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d)
+#pragma unroll
+      for (int q = 0; q < REC; ++q) acc[d][q] = 0.f;
+    for (int b = lane; b < B; b += 32) {
+      float hr[MAXM], hi[MAXM];
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m) {
+        if (m < M) {
+          const float *row = master + ((int64_t)m * I_bank + row0 + i) * Kpad;
+          hr[m] = __ldg(row + b);
+          hi[m] = __ldg(row + B + b);
+        } else {
+          hr[m] = 0.f; hi[m] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < MAXD; ++d) {
+        if (d >= D) break;
+        float w = om_s[d * B + b];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) acc[d][m] += w * (hr[m] * hr[m] + hi[m] * hi[m]);
+        int p = 0;
+#pragma unroll
+        for (int a = 1; a < MAXM; ++a)
+#pragma unroll
+          for (int c = 0; c < a; ++c, ++p) {
+            // h_a h_c^*
+            acc[d][4 + 2 * p] += w * (hr[a] * hr[c] + hi[a] * hi[c]);
+            acc[d][5 + 2 * p] += w * (hi[a] * hr[c] - hr[a] * hi[c]);
+          }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) {
+      if (d >= D) break;
+#pragma unroll
+      for (int q = 0; q < REC; ++q) {
+        float v = acc[d][q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == q) mx[(i * D + d) * REC + q] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bank conversion (load time)
+// ---------------------------------------------------------------------------
+// complex [rows][M][B] (double2 or float2) -> FP32 master [M][I_bank][Kpad] rows [re | im]
+template <typename CT>
+__global__ void bank_to_master_kernel(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad,
+                                      const CT *__restrict__ src, float *__restrict__ master,
+                                      float *__restrict__ amax, int *status) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= rows * M * B) return;
+  int b = (int)(k % B);
+  int64_t rm = k / B;
+  int m = (int)(rm % M);
+  int64_t r = rm / M;
+  CT v = src[k];
+  float re = (float)v.x, im = (float)v.y;
+  if (!isfinite(re) || !isfinite(im)) { atomicCAS(status, 0, DEV_E_NONFINITE); re = 0.f; im = 0.f; }
+  float *row = master + ((int64_t)m * I_bank + row0 + r) * Kpad;
+  row[b] = re;
+  row[B + b] = im;
+  atomic_max_nonneg(amax, fmaxf(fabsf(re), fabsf(im)));
+}
+template __global__ void bank_to_master_kernel<double2>(int64_t, int64_t, int64_t, int, int, int, const double2 *,
+                                                        float *, float *, int *);
+template __global__ void bank_to_master_kernel<float2>(int64_t, int64_t, int64_t, int, int, int, const float2 *,
+                                                       float *, float *, int *);
+
+__global__ void master_to_planes_kernel(int64_t n, const float *__restrict__ master, const float *__restrict__ amax,
+                                        __nv_bfloat16 *__restrict__ bf /*[2][n]*/, __half *__restrict__ hf,
+                                        float *__restrict__ scale_out) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float sc = pow2_scale(*amax);
+  if (k == 0) *scale_out = sc;
+  if (k >= n) return;
+  float v = master[k] * sc;
+  __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  bf[k] = hi;
+  bf[n + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  hf[k] = __float2half_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// K9: distance-marginal table (FP64)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double mu_d(double y) {
+  double r = sqrt(y * y + 4.0);
+  return y >= 0.0 ? 0.5 * (y + r) : 2.0 / (r - y);
+}
+
+// K(y, sigma) = ln E[(s+t)^-4] + 4 ln(s + mu(y)), t ~ N(y,1) truncated at 0, s = e^sigma.
+__device__ double dm_K_exact(double y, double sig) {
+  // 8-point Gauss-Legendre on composite panels (published nodes/weights)
+  const double gx[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+  const double gw[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+  const double s = exp(sig);
+  // weight w(t) = exp(-(t-y)^2/2 + c) with c = y^2/2 for y < 0 (no underflow near t = 0)
+  const bool neg = y < 0.0;
+  const double T = neg ? fmin(40.0, 40.0 / fmax(-y, 1.0)) + 1.0 : y + 9.0;
+  const double wneg = neg ? 1.0 / fmax(-y, 1.0) : 1e30;
+  double num = 0.0, t = 0.0;
+  int guard = 0;
+  while (t < T && guard < 4000) {
+    double hwid = fmin(0.5, 0.5 * (s + t));
+    hwid = fmin(hwid, wneg);
+    hwid = fmin(hwid, T - t);
+    double cen = t + 0.5 * hwid, hl = 0.5 * hwid, acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      for (int sg = -1; sg <= 1; sg += 2) {
+        double tt = cen + sg * hl * gx[j];
+        double lw = neg ? (-0.5 * tt * tt + tt * y) : (-0.5 * (tt - y) * (tt - y));
+        double g = s + tt;
+        double g2 = g * g;
+        acc += gw[j] * exp(lw) / (g2 * g2);
+      }
+    }
+    num += acc * hl;
+    t += hwid;
+    ++guard;
+  }
+  const double SQ2PI = 2.5066282746310002;
+  double den = neg ? SQ2PI * 0.5 * erfcx(-y * 0.70710678118654752) : SQ2PI * (1.0 - 0.5 * erfc(y * 0.70710678118654752));
+  return log(num / den) + 4.0 * log(s + mu_d(y));
+}
+
+__global__ void build_dm_table_kernel(float4 *__restrict__ tab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= DM_NY * DM_NS) return;
+  int iy = k % DM_NY, is = k / DM_NY;
+  double y = (double)DM_Y0 + (double)DM_DY * iy;
+  double sg = (double)DM_S0 + (double)DM_DS * is;
+  const double h = 1e-3;
+  double f = dm_K_exact(y, sg);
+  double fyp = dm_K_exact(y + h, sg), fym = dm_K_exact(y - h, sg);
+  double fsp = dm_K_exact(y, sg + h), fsm = dm_K_exact(y, sg - h);
+  double fpp = dm_K_exact(y + h, sg + h), fpm = dm_K_exact(y + h, sg - h);
+  double fmp = dm_K_exact(y - h, sg + h), fmm = dm_K_exact(y - h, sg - h);
+  double fy = (fyp - fym) / (2 * h), fs = (fsp - fsm) / (2 * h);
+  double fys = (fpp - fpm - fmp + fmm) / (4 * h * h);
+  tab[k] = make_float4((float)f, (float)(fy * DM_DY), (float)(fs * DM_DS), (float)(fys * DM_DY * DM_DS));
+}
+
+__global__ void dist_marg_eval_kernel(int64_t n, const float *__restrict__ dh, const float *__restrict__ hh,
+                                      float u_min, const float4 *__restrict__ tab, float *__restrict__ out) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) out[k] = dm_lnlbar(dh[k], hh[k], u_min, tab);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+void launch_prep(const PrepArgs &a, cudaStream_t st) {
+  prep_bins_kernel<<<nblk((int64_t)a.D * a.B, 256), 256, 0, st>>>(a.D, a.B, a.f, a.w, a.psd, a.data, a.c, a.omega,
+                                                                a.fh, a.fl, a.status);
+  prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, a.th, a.tl, a.Rf, a.qx, a.status);
+  build_G_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.Rf, a.G32,
+                                                       a.gmax);
+  int64_t total = (int64_t)a.M * 2 * a.E * a.Kpad;
+  pack_G_kernel<<<nblk(total, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, a.pack_kind, a.pack_planes,
+                                                  a.gpack, a.gscale);
+}
+
+void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
+                        const float *master, const float *omega, float *mx, int n_sms, cudaStream_t st) {
+  int bs = 256;
+  int64_t warps = (n_rows + 0);
+  int64_t blocks = (warps * 32 + bs - 1) / bs;
+  int64_t cap = (int64_t)n_sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  size_t smem = sizeof(float) * (size_t)D * B;
+  cross_terms_kernel<<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, master, omega, mx);
+}
+
+void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, const void *src,
+                           int dtype, float *master, float *amax, int *status, cudaStream_t st) {
+  int64_t n = rows * M * B;
+  if (dtype == DOTPE_C128)
+    bank_to_master_kernel<double2><<<nblk(n, 256), 256, 0, st>>>(rows, row0, I_bank, M, B, Kpad,
+                                                                 (const double2 *)src, master, amax, status);
+  else
+    bank_to_master_kernel<float2><<<nblk(n, 256), 256, 0, st>>>(rows, row0, I_bank, M, B, Kpad,
+                                                                (const float2 *)src, master, amax, status);
+}
+
+void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf, __half *hf,
+                             float *scale_out, cudaStream_t st) {
+  master_to_planes_kernel<<<nblk(n, 256), 256, 0, st>>>(n, master, amax, bf, hf, scale_out);
+}
+
+void launch_build_dm_table(float4 *tab, cudaStream_t st) {
+  build_dm_table_kernel<<<nblk((int64_t)DM_NY * DM_NS, 64), 64, 0, st>>>(tab);
+}
+
+void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
+                           cudaStream_t st) {
+  dist_marg_eval_kernel<<<nblk(n, 256), 256, 0, st>>>(n, dh, hh, u_min, tab, out);
+}
+
+size_t dm_table_elems() { return (size_t)DM_NY * DM_NS; }
+
+}  // namespace dotpe
