@@ -52,7 +52,14 @@ int or_data_weights(int D, int B, const double *w, const double *psd, const doub
   return 0;
 }
 
-static double phase_of(int n_phi, int o) { return TWO_PI * (double)o / (double)n_phi; }
+/* Phi on the regular grid phi_o = 2 pi o / N_phi: e^{i k phi_o} with the integer
+ * k o reduced modulo N_phi first, so that equal phases give equal values and
+ * ties between grid points are exact. */
+static cplx grid_phase(int k, int o, int n_phi) {
+  long r = ((long)k * (long)o) % n_phi;
+  if (r < 0) r += n_phi;
+  return cexp(I * TWO_PI * (double)r / (double)n_phi);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Route O1: plain definition per (i, e, o)                                  */
@@ -60,7 +67,6 @@ static double phase_of(int n_phi, int o) { return TWO_PI * (double)o / (double)n
 int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, double *hh_out) {
   const int M = p->n_modes, D = p->n_det, B = p->n_bins;
   for (int o = 0; o < p->n_phi; ++o) {
-    double phi = phase_of(p->n_phi, o);
     double dh = 0.0, hh = 0.0;
     for (int d = 0; d < D; ++d) {
       double t = p->t[e * D + d];
@@ -70,7 +76,7 @@ int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, 
         for (int m = 0; m < M; ++m) {
           cplx hm = ld_c(p->h, (i * M + m) * B + b);
           cplx R = ld_c(p->R, (e * D + d) * M + m);
-          cplx Phi = cexp(I * (double)p->mode_m[m] * phi);
+          cplx Phi = grid_phase(p->mode_m[m], o, p->n_phi);
           hk += hm * R * Phi;
         }
         hk *= cexp(-I * TWO_PI * p->f[b] * t);
@@ -148,12 +154,11 @@ int or_mode_components(const or_problem *p, const double *c, const double *omega
 static void rotate(int M, const int *mode_m, const cplx *z, const cplx *H, int n_phi,
                    double *dh_out, double *hh_out) {
   for (int o = 0; o < n_phi; ++o) {
-    double phi = phase_of(n_phi, o);
     cplx dh = 0.0, hh = 0.0;
-    for (int m = 0; m < M; ++m) dh += z[m] * cexp(I * (double)mode_m[m] * phi);
+    for (int m = 0; m < M; ++m) dh += z[m] * grid_phase(mode_m[m], o, n_phi);
     for (int m = 0; m < M; ++m)
       for (int mp = 0; mp < M; ++mp)
-        hh += H[m * M + mp] * cexp(I * (double)(mode_m[m] - mode_m[mp]) * phi);
+        hh += H[m * M + mp] * grid_phase(mode_m[m] - mode_m[mp], o, n_phi);
     dh_out[o] = creal(dh);
     hh_out[o] = creal(hh);
   }
