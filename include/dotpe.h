@@ -57,6 +57,10 @@ enum { DOTPE_C128 = 0, DOTPE_C64 = 1 };
 /* event flags */
 #define DOTPE_FLAG_STORE_LNL 0x1   /* keep ln Lbar_ie and max_o ln L^ML_ie for dotpe_lnl_blocks */
 #define DOTPE_FLAG_GEMM_ONLY 0x2   /* diagnostics: skip the marginalisation epilogue (result not valid) */
+/* failure-path test: the tensor-core kernel's producer never signals its first
+ * stage, so the consumer's bounded wait (0.25 s) runs out; the event ends FAILED
+ * with DOTPE_E_TIMEOUT and the context stays usable.  Precisions other than FP32. */
+#define DOTPE_FLAG_TEST_STALL 0x100
 
 /* event states */
 enum { DOTPE_STATE_QUEUED = 0, DOTPE_STATE_RUNNING = 1, DOTPE_STATE_DONE = 2, DOTPE_STATE_FAILED = 3 };
@@ -131,6 +135,8 @@ typedef struct dotpe_event_stats {
   int64_t n_pairs;                            /* N_int * N_ext */
   int64_t footprint_bytes;                    /* device bytes held while running */
   float device_ms;                            /* GPU time from first to last kernel */
+  float prep_ms;                              /* data weights, extrinsic operand, cross terms */
+  float fused_ms;                             /* fused GEMM + marginalisation kernel */
   int precision;
   int state;
 } dotpe_event_stats;
@@ -190,6 +196,12 @@ int dotpe_event_poll(dotpe_ctx *ctx, uint64_t event_id, int *state, dotpe_event_
 /* Blocks until the event is DONE or FAILED, at most timeout_s seconds
  * (<= 0: no limit).  Errors: E_TIMEOUT, E_NOT_FOUND, E_DEVICE. */
 int dotpe_event_wait(dotpe_ctx *ctx, uint64_t event_id, double timeout_s);
+
+/* Makes `stream` (a cudaStream_t) wait, on the device, for the event's
+ * completion.  Returns once the wait is enqueued; while the event is still
+ * queued (not yet admitted) the call blocks on the host until it is.
+ * Errors: E_NOT_FOUND, E_DEVICE. */
+int dotpe_event_stream_wait(dotpe_ctx *ctx, uint64_t event_id, void *stream);
 
 /* Evidence, effective sample sizes and the ML point of a finished event.
  * Errors: E_NOT_READY, E_NOT_FOUND, E_DEVICE (device_status set). */

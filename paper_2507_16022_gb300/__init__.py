@@ -32,6 +32,7 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
 DOTPE_C128, DOTPE_C64 = 0, 1
 DOTPE_FLAG_STORE_LNL = 0x1
 DOTPE_FLAG_GEMM_ONLY = 0x2
+DOTPE_FLAG_TEST_STALL = 0x100
 DOTPE_STATE_QUEUED, DOTPE_STATE_RUNNING, DOTPE_STATE_DONE, DOTPE_STATE_FAILED = 0, 1, 2, 3
 DOTPE_LNL_MARG, DOTPE_LNL_ML_MAX, DOTPE_ROW_MARGINAL, DOTPE_COL_MARGINAL = 0, 1, 2, 3
 
@@ -39,7 +40,8 @@ DOTPE_LNL_MARG, DOTPE_LNL_ML_MAX, DOTPE_ROW_MARGINAL, DOTPE_COL_MARGINAL = 0, 1,
 SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_message",
            "dotpe_version", "dotpe_device_info", "dotpe_bank_load", "dotpe_bank_release",
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
-           "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval")
+           "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
+           "dotpe_event_stream_wait")
 
 
 class DotpeError(RuntimeError):
@@ -76,6 +78,7 @@ class dotpe_event_stats(ctypes.Structure):
     _fields_ = [("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
                 ("t_done_ns", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("footprint_bytes", ctypes.c_int64), ("device_ms", ctypes.c_float),
+                ("prep_ms", ctypes.c_float), ("fused_ms", ctypes.c_float),
                 ("precision", ctypes.c_int), ("state", ctypes.c_int)]
 
 
@@ -120,6 +123,7 @@ def load(path: str = LIB_PATH):
                               ctypes.c_int64, ctypes.c_int, vp, ctypes.c_int64], ctypes.c_int),
         "dotpe_event_release": ([vp, ctypes.c_uint64], ctypes.c_int),
         "dotpe_dist_marg_eval": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "dotpe_event_stream_wait": ([vp, ctypes.c_uint64, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -250,6 +254,12 @@ def dotpe_event_poll(ctx, event_id):
 
 def dotpe_event_wait(ctx, event_id, timeout_s=0.0):
     return _check(load().dotpe_event_wait(ctx, event_id, timeout_s))
+
+
+def dotpe_event_stream_wait(ctx, event_id, stream):
+    """stream: torch.cuda.Stream or a raw cudaStream_t integer."""
+    st = stream if isinstance(stream, int) else stream.cuda_stream
+    return _check(load().dotpe_event_stream_wait(ctx, event_id, ctypes.c_void_p(st)))
 
 
 def dotpe_evidence(ctx, event_id):

@@ -54,6 +54,8 @@ struct EpiParams {
   float *ml_tile;           // optional [n_int][n_ext]
   int *status;
   int gemm_only;
+  int test_stall;           // producer withholds its first stage (failure-path test)
+  unsigned long long wait_ns;  // bound of every mbarrier wait
 };
 
 // ---------------------------------------------------------------------------

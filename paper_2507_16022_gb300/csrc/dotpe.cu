@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -95,7 +96,7 @@ struct Event {
   double2 *data = nullptr, *R = nullptr;
   void *in_stage = nullptr;  // pinned host staging of host inputs
   size_t stage_bytes = 0;
-  cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
   // results kept until release
   void *keep_block = nullptr;
   size_t keep_bytes = 0;
@@ -107,7 +108,7 @@ struct Event {
   int slot = -1;
   int64_t t_submit = 0, t_admit = 0;
   volatile int64_t t_done = 0;
-  float device_ms = -1.f;
+  float device_ms = -1.f, prep_ms = -1.f, fused_ms = -1.f;
 };
 
 }  // namespace dotpe
@@ -126,13 +127,32 @@ struct dotpe_ctx {
   std::unordered_map<uint64_t, dotpe::Event *> events;
   std::deque<uint64_t> queue;
   uint64_t next_id = 1;
+  // completion callbacks -> admission worker
+  std::mutex cb_mu;
+  std::condition_variable cv;
+  std::unordered_map<uint64_t, int64_t> done_ns;
+  bool stop = false;
+  std::thread worker;
 };
 
 namespace dotpe {
 
+struct DoneArg {
+  dotpe_ctx *ctx;
+  uint64_t id;
+};
+
+// Host callback at the end of an event's stream work: records the completion
+// time and wakes the admission worker.  It touches no CUDA API and not the
+// Event itself (which the caller may release concurrently).
 static void CUDART_CB mark_done(void *p) {
-  Event *ev = (Event *)p;
-  ev->t_done = now_ns();
+  DoneArg *a = (DoneArg *)p;
+  {
+    std::lock_guard<std::mutex> lk(a->ctx->cb_mu);
+    a->ctx->done_ns[a->id] = now_ns();
+  }
+  a->ctx->cv.notify_all();
+  delete a;
 }
 
 // ---------------------------------------------------------------------------
@@ -277,7 +297,10 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   P.ml_tile = e.ml_tile;
   P.status = status;
   P.gemm_only = (e.flags & DOTPE_FLAG_GEMM_ONLY) ? 1 : 0;
+  P.test_stall = (e.flags & DOTPE_FLAG_TEST_STALL) ? 1 : 0;
+  P.wait_ns = P.test_stall ? 250000000ull : 4000000000ull;
 
+  CUDA_OR_FAIL(cudaEventRecord(e.ev_k0, st));
   if (e.prec == DOTPE_PREC_FP32) {
     P.z_scale = 1.f;
     P.g_scale = nullptr;
@@ -322,6 +345,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
     int r = launch_tc(g, P, st);
     if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
   }
+  CUDA_OR_FAIL(cudaEventRecord(e.ev_k1, st));
 
   ReduceArgs ra;
   memset(&ra, 0, sizeof(ra));
@@ -346,7 +370,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   CUDA_OR_FAIL(cudaGetLastError());
   CUDA_OR_FAIL(cudaMemcpyAsync(e.h_out, e.d_out, sizeof(ReduceOut), cudaMemcpyDeviceToHost, st));
   CUDA_OR_FAIL(cudaEventRecord(e.ev_end, st));
-  CUDA_OR_FAIL(cudaLaunchHostFunc(st, mark_done, &e));
+  CUDA_OR_FAIL(cudaLaunchHostFunc(st, mark_done, new DoneArg{ctx, e.id}));
   CUDA_OR_FAIL(cudaFreeAsync(scr, st));
   CUDA_OR_FAIL(cudaFreeAsync(e.in_block, st));
   e.in_block = nullptr;
@@ -362,8 +386,18 @@ static void progress(dotpe_ctx *ctx) {
       cudaError_t q = cudaEventQuery(e.ev_end);
       if (q == cudaSuccess) {
         e.state = (e.h_out->status == 0) ? DOTPE_STATE_DONE : DOTPE_STATE_FAILED;
+        {
+          std::lock_guard<std::mutex> lk(ctx->cb_mu);
+          auto d = ctx->done_ns.find(e.id);
+          if (d != ctx->done_ns.end()) {
+            e.t_done = d->second;
+            ctx->done_ns.erase(d);
+          }
+        }
         float ms = -1.f;
         if (cudaEventElapsedTime(&ms, e.ev_start, e.ev_end) == cudaSuccess) e.device_ms = ms;
+        if (cudaEventElapsedTime(&ms, e.ev_start, e.ev_k0) == cudaSuccess) e.prep_ms = ms;
+        if (cudaEventElapsedTime(&ms, e.ev_k0, e.ev_k1) == cudaSuccess) e.fused_ms = ms;
         if (e.t_done == 0) e.t_done = now_ns();
         ctx->slot_busy[e.slot] = 0;
         ctx->used -= e.scratch_bytes + e.in_bytes;
@@ -419,6 +453,8 @@ static void free_event(dotpe_ctx *ctx, Event *e) {
   if (e->ev_inputs) cudaEventDestroy(e->ev_inputs);
   if (e->ev_start) cudaEventDestroy(e->ev_start);
   if (e->ev_end) cudaEventDestroy(e->ev_end);
+  if (e->ev_k0) cudaEventDestroy(e->ev_k0);
+  if (e->ev_k1) cudaEventDestroy(e->ev_k1);
   size_t give = e->keep_bytes + e->scratch_bytes + e->in_bytes;
   if (e->state == DOTPE_STATE_QUEUED) give = e->in_bytes;
   ctx->used = (ctx->used >= give) ? ctx->used - give : 0;
@@ -503,12 +539,31 @@ int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
     delete ctx;
     return fail(DOTPE_E_DEVICE, "table build: %s", cudaGetErrorString(e));
   }
+  // admission worker: admits queued events as earlier ones complete
+  ctx->worker = std::thread([ctx]() {
+    cudaSetDevice(ctx->device);
+    while (true) {
+      {
+        std::unique_lock<std::mutex> lk(ctx->cb_mu);
+        ctx->cv.wait_for(lk, std::chrono::milliseconds(2));
+        if (ctx->stop) return;
+      }
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      if (!ctx->queue.empty()) progress(ctx);
+    }
+  });
   *out = ctx;
   return DOTPE_OK;
 }
 
 int dotpe_destroy(dotpe_ctx *ctx) {
   if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  {
+    std::lock_guard<std::mutex> lk(ctx->cb_mu);
+    ctx->stop = true;
+  }
+  ctx->cv.notify_all();
+  if (ctx->worker.joinable()) ctx->worker.join();
   cudaSetDevice(ctx->device);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -756,6 +811,8 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   cudaEventCreateWithFlags(&e->ev_inputs, cudaEventDisableTiming);
   cudaEventCreate(&e->ev_start);
   cudaEventCreate(&e->ev_end);
+  cudaEventCreate(&e->ev_k0);
+  cudaEventCreate(&e->ev_k1);
   cudaEventRecord(e->ev_inputs, ist);
   if (cudaHostAlloc((void **)&e->h_out, sizeof(ReduceOut), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
@@ -782,6 +839,8 @@ static void fill_stats(const Event &e, dotpe_event_stats *s) {
   s->n_pairs = e.NI * e.NE;
   s->footprint_bytes = (int64_t)(e.keep_bytes + scratch_layout(e).total + e.in_bytes);
   s->device_ms = e.device_ms;
+  s->prep_ms = e.prep_ms;
+  s->fused_ms = e.fused_ms;
   s->precision = e.prec;
   s->state = e.state;
 }
@@ -810,10 +869,35 @@ int dotpe_event_wait(dotpe_ctx *ctx, uint64_t event_id, double timeout_s) {
       if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
       int s = it->second->state;
       if (s == DOTPE_STATE_DONE) return DOTPE_OK;
-      if (s == DOTPE_STATE_FAILED) return fail(DOTPE_E_DEVICE, "event failed (device status %d)", it->second->h_out->status);
+      if (s == DOTPE_STATE_FAILED) {
+        int ds = it->second->h_out->status;
+        int code = ds == DEV_E_NONFINITE ? DOTPE_E_INVALID : ds == DEV_E_TIMEOUT ? DOTPE_E_TIMEOUT : DOTPE_E_DEVICE;
+        return fail(code, "event failed (device status %d)", ds);
+      }
     }
     if (timeout_s > 0 && (now_ns() - t0) > (int64_t)(timeout_s * 1e9)) return fail(DOTPE_E_TIMEOUT, "event wait");
     std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+int dotpe_event_stream_wait(dotpe_ctx *ctx, uint64_t event_id, void *stream) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  while (true) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+      progress(ctx);
+      auto it = ctx->events.find(event_id);
+      if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+      Event &e = *it->second;
+      if (e.state != DOTPE_STATE_QUEUED) {
+        CUDA_OR_FAIL(cudaStreamWaitEvent((cudaStream_t)stream, e.ev_end, 0));
+        return DOTPE_OK;
+      }
+    }
+    // still queued: wait for an earlier event to finish and free its slot
+    std::unique_lock<std::mutex> lk(ctx->cb_mu);
+    ctx->cv.wait_for(lk, std::chrono::milliseconds(1));
   }
 }
 

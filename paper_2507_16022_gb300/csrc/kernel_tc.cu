@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       uint32_t q = 0;
-      bool ok = true;
+      bool ok = !P.test_stall;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int it = t / S.n_etile, et = t % S.n_etile;
         for (int m = 0; m < M && ok; ++m)
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int kb = 0; kb < S.kb; ++kb, ++q) {
               const int s = q % ST;
               const uint32_t n = q / ST;
-              if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, P.status, abortp))) break;
+              if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, P.status, abortp, P.wait_ns))) break;
               mbar_expect_tx(&T.full[s], STAGE_BYTES);
               tma_load_2d(sA + s * A_BYTES, &mapA, &T.full[s], kb * BK, arow);
               tma_load_2d(sB + s * B_BYTES, &mapB, &T.full[s], kb * BK, brow);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NT, 1)
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++u) {
         const int b = u & 1;
         const uint32_t use = u >> 1;
-        if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, P.status, abortp))) break;
+        if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, P.status, abortp, P.wait_ns))) break;
         tc_fence_after();
         for (int m = 0; m < M && ok; ++m) {
           const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int kb = 0; kb < S.kb; ++kb, ++q) {
               const int s = q % ST;
               const uint32_t n = q / ST;
-              if (!(ok = mbar_wait(&T.full[s], n & 1, P.status, abortp))) break;
+              if (!(ok = mbar_wait(&T.full[s], n & 1, P.status, abortp, P.wait_ns))) break;
               tc_fence_after();
               const uint64_t ad = sdesc_k128(sA + s * A_BYTES), bd = sdesc_k128(sB + s * B_BYTES);
 #pragma unroll
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(NT, 1)
       for (int k = etid; k < TE; k += 128) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
       named_bar_sync(1, 128);
       const float thr = (P.cut_delta > 0.f) ? (*(volatile float *)P.ml_running - P.cut_delta) : -INFINITY;
-      if (!mbar_wait(&T.tfull[b], use & 1, P.status, abortp)) break;
+      if (!mbar_wait(&T.tfull[b], use & 1, P.status, abortp, P.wait_ns)) break;
       tc_fence_after();
 
       Lse ra, rb;

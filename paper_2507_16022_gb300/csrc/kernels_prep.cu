@@ -319,7 +319,7 @@ __global__ void build_dm_table_kernel(float4 *__restrict__ tab) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= DM_NY * DM_NS) return;
   int iy = k % DM_NY, is = k / DM_NY;
-  double y = (double)DM_Y0 + (double)DM_DY * iy;
+  double y = dm_node_y(iy);
   double sg = (double)DM_S0 + (double)DM_DS * is;
   const double h = 1e-3;
   double f = dm_K_exact(y, sg);
@@ -329,7 +329,8 @@ __global__ void build_dm_table_kernel(float4 *__restrict__ tab) {
   double fmp = dm_K_exact(y - h, sg + h), fmm = dm_K_exact(y - h, sg - h);
   double fy = (fyp - fym) / (2 * h), fs = (fsp - fsm) / (2 * h);
   double fys = (fpp - fpm - fmp + fmm) / (4 * h * h);
-  tab[k] = make_float4((float)f, (float)(fy * DM_DY), (float)(fs * DM_DS), (float)(fys * DM_DY * DM_DS));
+  // y-derivatives unscaled (cells have different widths), sigma-derivatives times ds
+  tab[k] = make_float4((float)f, (float)fy, (float)(fs * DM_DS), (float)(fys * DM_DS));
 }
 
 __global__ void dist_marg_eval_kernel(int64_t n, const float *__restrict__ dh, const float *__restrict__ hh,

@@ -1,0 +1,383 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (per pair, on ln Lbar_ie and max_o ln L^ML_ie):
+  fp32, bf16x3 : |d| <= 1e-3                       (the split-precision bound)
+  fp16, bf16   : |d| <= 2e-2 + 4 u max(ln L^ML, 0),  u = 2^-11 (fp16), 2^-9 (bf16)
+A single-pass format rounds both GEMM operands to precision u, so each product
+h G carries a relative error up to 2u and, by Cauchy-Schwarz,
+|d<d|h>| <= 2u sqrt(<h|h><d|d>).  ln L^ML = <d|h>^2 / 2<h|h> then moves by up to
+2u |x| sqrt(<d|d>) with |x| = sqrt(2 ln L^ML) (plus 4u ln L^ML when the
+products add coherently); the single-pass bound used is
+  2e-2 + 4u ln L^ML + 2u sqrt(2 ln L^ML + 1) sqrt(<d|d>).
+A flat 2e-2 is out of reach for bf16 at SNR 15: the noise power <d|d> ~ 2 B D
+enters every pair.
+ln Z: |d| <= 1e-2 for fp32 and bf16x3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": (1e-3, 0.0), "bf16x3": (1e-3, 0.0), "fp16": (2e-2, 4 * 2.0 ** -11),
+       "bf16": (2e-2, 4 * 2.0 ** -9)}
+PRECISE = ("fp32", "bf16x3")
+
+
+@pytest.fixture(scope="module")
+def dpx():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2507_16022_gb300 as dp
+    ctx = dp.dotpe_create(0)
+    yield dp, ctx
+    dp.dotpe_destroy(ctx)
+
+
+def run(dp, ctx, wl, precision, bid=None, i0=0, i1=None, cut=0.0, flags=None, n_phi=None):
+    own = bid is None
+    if own:
+        bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    I = wl.bank.h.shape[0]
+    i1 = I if i1 is None else i1
+    E = wl.ext.t.shape[0]
+    flags = dp.DOTPE_FLAG_STORE_LNL if flags is None else flags
+    eid = dp.dotpe_event_submit(ctx, bid, i0, i1, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                wl.ext.ln_w, n_phi=n_phi or wl.event.n_phi, u_min=wl.event.u_min,
+                                cut_delta=cut, precision=precision, flags=flags)
+    dp.dotpe_event_wait(ctx, eid, 120.0)
+    ev = dp.dotpe_evidence(ctx, eid)
+    out = dict(ev=ev)
+    if flags & dp.DOTPE_FLAG_STORE_LNL:
+        out["lnl"] = dp.dotpe_lnl_blocks(ctx, eid, 0, i1 - i0, 0, E)
+        out["ml"] = dp.dotpe_lnl_blocks(ctx, eid, 0, i1 - i0, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+    out["row"] = dp.dotpe_lnl_blocks(ctx, eid, 0, i1 - i0, 0, E, what=dp.DOTPE_ROW_MARGINAL)
+    out["col"] = dp.dotpe_lnl_blocks(ctx, eid, 0, i1 - i0, 0, E, what=dp.DOTPE_COL_MARGINAL)
+    out["stats"] = dp.dotpe_event_poll(ctx, eid)[1]
+    dp.dotpe_event_release(ctx, eid)
+    if own:
+        dp.dotpe_bank_release(ctx, bid)
+    return out
+
+
+def data_norm(wl):
+    """<d|d> = sum_d sum_b 4 w_b |d_d(f_b)|^2 / S_d(f_b) (Eq. inner_product)."""
+    return float(np.sum(4.0 * wl.bank.w[None, :] * np.abs(wl.event.data) ** 2 / wl.event.psd))
+
+
+def check_pairs(got, ref, precision, dd=0.0):
+    a, r = TOL[precision]
+    ml = np.maximum(ref["lnl_ml_max"], 0.0)
+    tol = a + r * ml
+    if r > 0.0:
+        tol = tol + 0.5 * r * np.sqrt(2.0 * ml + 1.0) * np.sqrt(dd)
+    d1 = np.abs(got["lnl"].astype(np.float64) - ref["lnl_marg"])
+    d2 = np.abs(got["ml"].astype(np.float64) - ref["lnl_ml_max"])
+    assert np.all(np.isfinite(got["lnl"]))
+    assert np.all(d1 <= tol), (precision, float(d1.max()), np.unravel_index(np.argmax(d1 - tol), d1.shape))
+    assert np.all(d2 <= tol), (precision, float(d2.max()))
+
+
+def check_evidence(got, ref_ev, precision, lnz_tol=1e-2):
+    ev = got["ev"]
+    if precision in PRECISE:
+        assert abs(ev["ln_z"] - ref_ev["ln_z"]) <= lnz_tol
+        for k in ("n_eff", "n_eff_int", "n_eff_ext"):
+            assert ev[k] == pytest.approx(ref_ev[k], rel=2e-2), k
+        np.testing.assert_allclose(got["row"], ref_ev["ln_p_int"], atol=2e-3)
+        np.testing.assert_allclose(got["col"], ref_ev["ln_p_ext"], atol=2e-3)
+    else:
+        assert abs(ev["ln_z"] - ref_ev["ln_z"]) <= 0.1
+
+
+# ---------------------------------------------------------------------------
+# device distance marginal (Eq. lnl_dist_marginalized) against the oracle
+# ---------------------------------------------------------------------------
+def test_dist_marg_table_sweep(dpx):
+    """Bound: 1e-4 for the table, plus the conditioning of FP32 inputs: x = dh/sqrt(hh)
+    carries ~2^-22 relative error and d lnLbar/dx lies between s and max(x, s)."""
+    import oracle
+    dp, ctx = dpx
+    rng = np.random.default_rng(0)
+    for u_min in (0.5, 2.0, 9.5):
+        x = np.concatenate([rng.uniform(-60, 60, 2500), rng.uniform(0.0, 12.0, 1000)])
+        s = np.exp(np.concatenate([rng.uniform(-11, 4.5, 2500), rng.uniform(-11.5, -3.0, 1000)]))
+        x[2500:] += s[2500:]  # the small-s corner with y = x - s in [0, 12]
+        hh = (s / u_min) ** 2
+        dh = (x * np.sqrt(hh)).astype(np.float32)
+        hh = hh.astype(np.float32)
+        got = dp.dotpe_dist_marg_eval(ctx, dh, hh, u_min).astype(np.float64)
+        ref = np.array([oracle.dist_marg(float(a), float(b), u_min) for a, b in zip(dh, hh)])
+        err = np.abs(got - ref)
+        bound = 1e-4 + 2.5e-7 * np.abs(x) * (np.maximum(np.abs(x), s) + 5.0) + 2e-7 * np.abs(ref)
+        k = int(np.argmax(err - bound))
+        assert np.all(err <= bound), (float(err[k]), float(x[k]), float(s[k]), float(ref[k]))
+        assert np.median(err) < 2e-5
+    # no signal power -> exactly 0
+    z = dp.dotpe_dist_marg_eval(ctx, np.array([0.3, 0.0], np.float32), np.array([0.0, 0.0], np.float32), 2.0)
+    assert np.all(z == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# config 1 (all pairs): I=1024, E=256, D=2, M=3, B=256, SNR 15, seed 0
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg1():
+    import oracle
+    wl = synth.named_workload("cfg1", ln_w="random")
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event)
+    grid, _ = P.eval_grid(0.0)
+    return wl, P, grid, P.evidence(grid)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16", "bf16"])
+def test_config1_all_pairs(dpx, cfg1, precision):
+    dp, ctx = dpx
+    wl, P, grid, ref_ev = cfg1
+    got = run(dp, ctx, wl, precision)
+    check_pairs(got, grid, precision, data_norm(wl))
+    check_evidence(got, ref_ev, precision)
+    if precision in PRECISE:
+        assert (got["ev"]["arg_i"], got["ev"]["arg_e"], got["ev"]["arg_o"]) == tuple(ref_ev["arg"])
+        assert got["ev"]["max_lnl_ml"] == pytest.approx(ref_ev["max_lnl_ml"], abs=1e-3)
+    assert got["ev"]["n_marginalised"] == ref_ev["n_marginalised"]
+
+
+def test_config1_ml_cut(dpx, cfg1):
+    """Eq. coherent_ML_selection with the paper's delta = 20.  The device uses a
+    running maximum, so it keeps a superset of the exact cut: its ln Z lies
+    between the oracle's cut and uncut values."""
+    import oracle
+    dp, ctx = dpx
+    wl, P, grid, ref_ev = cfg1
+    gcut, thr = P.eval_grid(20.0)
+    ev_cut = P.evidence(gcut)
+    for precision in PRECISE:
+        got = run(dp, ctx, wl, precision, cut=20.0, flags=0)
+        ev = got["ev"]
+        assert ev_cut["ln_z"] - 1e-2 <= ev["ln_z"] <= ref_ev["ln_z"] + 1e-2
+        assert ev["n_marginalised"] >= ev_cut["n_marginalised"]
+        assert ev["lnl_ml_threshold"] <= thr + 1e-3
+        assert (ev["arg_i"], ev["arg_e"], ev["arg_o"]) == tuple(ref_ev["arg"])
+
+
+# ---------------------------------------------------------------------------
+# ragged shapes, slices, mode/detector counts
+# ---------------------------------------------------------------------------
+SHAPES = [  # I_bank, slice, E, D, M, B
+    (200, (0, 200), 45, 1, 1, 64),
+    (400, (17, 350), 77, 2, 3, 96),
+    (300, (5, 134), 33, 3, 4, 160),
+    (150, (0, 150), 130, 3, 2, 40),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"I{s[0]}E{s[2]}D{s[3]}M{s[4]}B{s[5]}")
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "fp16", "bf16"])
+def test_ragged_shapes(dpx, shape, precision):
+    import oracle
+    dp, ctx = dpx
+    Ib, (a, b), E, D, M, B = shape
+    wl = synth.make_workload(n_int=Ib, n_ext=E, n_det=D, n_modes=M, n_bins=B, snr=12.0,
+                             seed=Ib + E + D, ln_w="random", n_phi=16)
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event, i_slice=slice(a, b))
+    grid, _ = P.eval_grid(0.0)
+    ref_ev = P.evidence(grid)
+    got = run(dp, ctx, wl, precision, i0=a, i1=b)
+    check_pairs(got, grid, precision, data_norm(wl))
+    check_evidence(got, ref_ev, precision)
+    if precision in PRECISE:
+        assert got["ev"]["arg_i"] - a == ref_ev["arg"][0]
+        assert (got["ev"]["arg_e"], got["ev"]["arg_o"]) == tuple(ref_ev["arg"][1:])
+
+
+def test_noiseless_peak(dpx):
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=500, n_ext=96, n_det=3, n_modes=4, n_bins=128, snr=15.0, seed=5,
+                             noise=False, insert_injection=True, phi_inj=2 * np.pi * 5 / 32)
+    for precision in PRECISE:
+        ev = run(dp, ctx, wl, precision, flags=0)["ev"]
+        assert (ev["arg_i"], ev["arg_e"], ev["arg_o"]) == (wl.event.injection["i"], 0, 5)
+        assert ev["max_lnl_ml"] == pytest.approx(112.5, abs=2e-3)
+
+
+# ---------------------------------------------------------------------------
+# production size (65,536 x 4,096, D=3, M=4, B=512): sampled pairs vs the oracle
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg2():
+    wl = synth.named_workload("cfg2")
+    return wl
+
+
+def test_config2_sampled_pairs_and_evidence(dpx, cfg2):
+    import oracle
+    dp, ctx = dpx
+    wl = cfg2
+    I, E = wl.bank.h.shape[0], wl.ext.t.shape[0]
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    try:
+        pi, pe = synth.pair_subsample(2, I, E, n_max=12000)
+        # include the best pairs: the oracle's max must agree where it matters most
+        P = oracle.OracleProblem(wl.bank, wl.ext, wl.event)
+        res = {}
+        for precision in ("fp32", "bf16x3", "bf16"):
+            res[precision] = run(dp, ctx, wl, precision, bid=bid)
+        i_s, e_s = res["bf16x3"]["ev"]["arg_i"], res["bf16x3"]["ev"]["arg_e"]
+        pi = np.concatenate([pi, [i_s]])
+        pe = np.concatenate([pe, [e_s]])
+        ref = P.eval_pairs(pi, pe)
+        for precision, got in res.items():
+            sub = {"lnl": got["lnl"][pi, pe], "ml": got["ml"][pi, pe]}
+            check_pairs(sub, ref, precision, data_norm(wl))
+        # evidence: served split precision against the plain FP32 path (same GPU)
+        assert abs(res["bf16x3"]["ev"]["ln_z"] - res["fp32"]["ev"]["ln_z"]) <= 1e-2
+        # the FP64 reduction reproduces a direct FP64 log-sum-exp of the stored ln Lbar_ie
+        lnl = res["bf16x3"]["lnl"].astype(np.float64)
+        lw = wl.bank.ln_w[:, None] + wl.ext.ln_w[None, :]
+        x = (lnl + lw).ravel()
+        m = x.max()
+        lnz = m + math.log(np.sum(np.exp(x - m))) - math.log(I * E)
+        assert res["bf16x3"]["ev"]["ln_z"] == pytest.approx(lnz, abs=1e-4)
+        assert res["bf16x3"]["ev"]["max_lnl_ml"] == pytest.approx(float(ref["lnl_ml_max"][-1]), abs=1e-3)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+
+
+# ---------------------------------------------------------------------------
+# runtime: concurrency, admission, failure paths
+# ---------------------------------------------------------------------------
+def test_concurrent_events_equal_alone(dpx):
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=2048, n_ext=512, n_det=3, n_modes=4, n_bins=256, snr=12.0, seed=21)
+    rng = np.random.default_rng(3)
+    evs = [wl.event] + [synth.make_event(rng, wl.bank, wl.ext, 3, snr=float(s)) for s in (8, 20, 35)]
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    try:
+        def submit(ev, prec, i0, i1):
+            return dp.dotpe_event_submit(ctx, bid, i0, i1, ev.psd, ev.data, wl.ext.t, wl.ext.R,
+                                         n_phi=32, u_min=ev.u_min, precision=prec)
+        specs = [(evs[k], ("bf16x3", "fp32", "bf16x3", "fp16")[k], 64 * k, 2048 - 100 * k) for k in range(4)]
+        alone = []
+        for s in specs:
+            eid = submit(*s)
+            dp.dotpe_event_wait(ctx, eid, 60)
+            alone.append(dp.dotpe_evidence(ctx, eid))
+            dp.dotpe_event_release(ctx, eid)
+        ids = [submit(*s) for s in specs]  # all in flight together
+        for eid, a in zip(ids, alone):
+            dp.dotpe_event_wait(ctx, eid, 60)
+            b = dp.dotpe_evidence(ctx, eid)
+            # no ML cut: fixed reduction order, so results are bitwise equal
+            assert b["ln_z"] == a["ln_z"] and b["n_eff"] == a["n_eff"]
+            assert (b["arg_i"], b["arg_e"], b["arg_o"]) == (a["arg_i"], a["arg_e"], a["arg_o"])
+            dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+
+
+def test_admission_by_footprint(dpx):
+    import paper_2507_16022_gb300 as dp
+    wl = synth.make_workload(n_int=8192, n_ext=2048, n_det=3, n_modes=4, n_bins=256, snr=12.0, seed=9)
+    dp0, ctx0 = dpx
+    probe = run(dp0, ctx0, wl, "bf16x3", flags=0)
+    foot = probe["stats"]["footprint_bytes"]
+    bank_bytes = 10 * 4 * 8192 * 512 + (1 << 20)
+    ctx = dp.dotpe_create(0, hbm_budget_bytes=int(bank_bytes + 1.5 * foot), n_slots=4)
+    try:
+        bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m)
+        # an event larger than the whole budget is refused outright
+        big = synth.make_workload(n_int=8, n_ext=60000, n_det=3, n_modes=4, n_bins=256, seed=1)
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_event_submit(ctx, bid, 0, 8192, wl.event.psd, wl.event.data, big.ext.t, big.ext.R,
+                                  u_min=wl.event.u_min, precision="bf16x3")
+        assert ei.value.status == dp.DOTPE_E_ADMISSION
+        # events that fit one at a time are queued, then admitted as memory frees, and all complete
+        ids = [dp.dotpe_event_submit(ctx, bid, 0, 8192, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                     u_min=wl.event.u_min, precision="bf16x3") for _ in range(3)]
+        assert dp.dotpe_event_poll(ctx, ids[2])[0] == dp.DOTPE_STATE_QUEUED
+        lz = []
+        for e in ids:
+            dp.dotpe_event_wait(ctx, e, 60)
+            lz.append(dp.dotpe_evidence(ctx, e)["ln_z"])
+            dp.dotpe_event_release(ctx, e)
+        assert lz[0] == lz[1] == lz[2] == probe["ev"]["ln_z"]
+    finally:
+        dp.dotpe_destroy(ctx)
+
+
+def test_nonfinite_input_reported_and_context_survives(dpx):
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=256, n_ext=64, n_det=2, n_modes=3, n_bins=64, snr=10.0, seed=4)
+    psd = wl.event.psd.copy()
+    psd[1, 7] = np.nan
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m)
+    try:
+        eid = dp.dotpe_event_submit(ctx, bid, 0, 256, psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                    u_min=wl.event.u_min, precision="bf16x3")
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_event_wait(ctx, eid, 60)
+        assert ei.value.status == dp.DOTPE_E_INVALID
+        dp.dotpe_event_release(ctx, eid)
+        eid = dp.dotpe_event_submit(ctx, bid, 0, 256, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                    u_min=wl.event.u_min, precision="bf16x3")
+        dp.dotpe_event_wait(ctx, eid, 60)
+        assert math.isfinite(dp.dotpe_evidence(ctx, eid)["ln_z"])
+        dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+
+
+def test_device_wait_timeout_is_reported_and_context_survives(dpx):
+    """A stage that is never signalled: the bounded mbarrier wait runs out,
+    the kernel records a timeout and exits; no fault, no hang."""
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=512, n_ext=128, n_det=2, n_modes=3, n_bins=64, snr=10.0, seed=6)
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m)
+    try:
+        eid = dp.dotpe_event_submit(ctx, bid, 0, 512, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                    u_min=wl.event.u_min, precision="bf16", flags=dp.DOTPE_FLAG_TEST_STALL)
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_event_wait(ctx, eid, 60)
+        assert ei.value.status == dp.DOTPE_E_TIMEOUT
+        assert dp.dotpe_event_poll(ctx, eid)[0] == dp.DOTPE_STATE_FAILED
+        dp.dotpe_event_release(ctx, eid)
+        got = run(dp, ctx, wl, "bf16x3", bid=bid, flags=0)
+        assert math.isfinite(got["ev"]["ln_z"])
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+
+
+def test_device_resident_inputs_on_caller_stream(dpx):
+    import torch
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=700, n_ext=90, n_det=3, n_modes=4, n_bins=128, snr=12.0, seed=8)
+    host = run(dp, ctx, wl, "bf16x3", flags=0)["ev"]
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        def dev(a):
+            a = np.ascontiguousarray(a)
+            a = a.view(np.float64) if np.iscomplexobj(a) else a
+            return torch.from_numpy(a.copy()).to("cuda", non_blocking=True)
+        t, R, lw, psd, data = (dev(x) for x in (wl.ext.t, wl.ext.R, wl.ext.ln_w, wl.event.psd, wl.event.data))
+    eid = dp.dotpe_event_submit(ctx, bid, 0, 700, psd, data, t, R, lw, n_phi=32, u_min=wl.event.u_min,
+                                precision="bf16x3", stream=s)
+    dp.dotpe_event_stream_wait(ctx, eid, s)
+    s.synchronize()
+    assert dp.dotpe_event_poll(ctx, eid)[0] == dp.DOTPE_STATE_DONE
+    ev = dp.dotpe_evidence(ctx, eid)
+    assert ev["ln_z"] == host["ln_z"]
+    dp.dotpe_event_release(ctx, eid)
+    dp.dotpe_bank_release(ctx, bid)
+
+
+def test_gemm_only_diagnostic_runs(dpx):
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=1024, n_ext=256, n_det=3, n_modes=4, n_bins=256, seed=2)
+    for precision in ("bf16", "bf16x3", "fp32"):
+        got = run(dp, ctx, wl, precision, flags=dp.DOTPE_FLAG_GEMM_ONLY)
+        assert got["stats"]["fused_ms"] > 0
