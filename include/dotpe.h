@@ -226,6 +226,26 @@ int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id);
 int dotpe_dist_marg_eval(dotpe_ctx *ctx, int64_t n, const float *dh, const float *hh, float u_min,
                          float *out);
 
+/* Allocation-free variant of dotpe_dist_marg_eval (the paper has no
+ * counterpart; this is a library service).  Some callers cannot allocate
+ * device memory at the point where they call: code running while a stream
+ * is being captured into a CUDA graph (cudaMalloc is not allowed then),
+ * hosts that hand the whole device to their own allocator, and latency-bound
+ * loops that must not pay for cudaMalloc/cudaFree.  This entry point calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch for the
+ * inputs and the output is a static device array of 3 x 2^20 floats (12 MiB)
+ * that every GPU loading the library holds until the process exits; the
+ * array's device address is looked up with cudaGetSymbolAddress on the
+ * first call on each device, so make that first call before any stream
+ * capture.  n must not exceed 2^20 (1,048,576): larger n is rejected with
+ * DOTPE_E_INVALID and a message.  dh, hh, out: host or device float arrays
+ * of length n, as for dotpe_dist_marg_eval.  All calls share the one scratch
+ * array and are serialised on the context's stream; calls that overlap on
+ * the GPU (e.g. from several contexts on one device) race on it.  The call
+ * returns after the result is in `out`.  Errors: E_INVALID, E_DEVICE. */
+int dotpe_dist_marg_eval_noalloc(dotpe_ctx *ctx, int64_t n, const float *dh, const float *hh, float u_min,
+                                 float *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,7 +41,7 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_version", "dotpe_device_info", "dotpe_bank_load", "dotpe_bank_release",
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
-           "dotpe_event_stream_wait")
+           "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc")
 
 
 class DotpeError(RuntimeError):
@@ -124,6 +124,7 @@ def load(path: str = LIB_PATH):
         "dotpe_event_release": ([vp, ctypes.c_uint64], ctypes.c_int),
         "dotpe_dist_marg_eval": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "dotpe_event_stream_wait": ([vp, ctypes.c_uint64, vp], ctypes.c_int),
+        "dotpe_dist_marg_eval_noalloc": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -294,4 +295,19 @@ def dotpe_dist_marg_eval(ctx, dh, hh, u_min):
     _check(load().dotpe_dist_marg_eval(ctx, dh.size, ctypes.c_void_p(dh.ctypes.data),
                                        ctypes.c_void_p(hh.ctypes.data), float(u_min),
                                        ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+DIST_MARG_NOALLOC_MAX = 1 << 20
+
+
+def dotpe_dist_marg_eval_noalloc(ctx, dh, hh, u_min):
+    """Same values as dotpe_dist_marg_eval, through the allocation-free entry point
+    (its scratch is a static device array; at most 2^20 values per call)."""
+    dh = np.ascontiguousarray(dh, dtype=np.float32)
+    hh = np.ascontiguousarray(hh, dtype=np.float32)
+    out = np.empty_like(dh)
+    _check(load().dotpe_dist_marg_eval_noalloc(ctx, dh.size, ctypes.c_void_p(dh.ctypes.data),
+                                               ctypes.c_void_p(hh.ctypes.data), float(u_min),
+                                               ctypes.c_void_p(out.ctypes.data)))
     return out

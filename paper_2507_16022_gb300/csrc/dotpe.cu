@@ -1004,4 +1004,16 @@ int dotpe_dist_marg_eval(dotpe_ctx *ctx, int64_t n, const float *dh, const float
   return DOTPE_OK;
 }
 
+int dotpe_dist_marg_eval_noalloc(dotpe_ctx *ctx, int64_t n, const float *dh, const float *hh, float u_min,
+                                  float *out) {
+  if (!ctx || (n > 0 && (!dh || !hh || !out))) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  char msg[256] = {0};
+  int rc = dist_marg_eval_noalloc(ctx->device, n, dh, hh, u_min, ctx->dm_table, out, ctx->main_stream, msg,
+                                  sizeof(msg));
+  if (rc != DOTPE_OK) return fail(rc, "%s", msg);
+  return DOTPE_OK;
+}
+
 }  // extern "C"

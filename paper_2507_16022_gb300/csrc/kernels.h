@@ -44,6 +44,9 @@ void launch_build_dm_table(float4 *tab, cudaStream_t st);
 void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
                            cudaStream_t st);
 size_t dm_table_elems();
+constexpr int64_t DM_NOALLOC_MAX = 1 << 20;  // evaluations per allocation-free call
+int dist_marg_eval_noalloc(int device, int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab,
+                           float *out, cudaStream_t st, char *msg, size_t msg_len);
 
 // Fused <d|h> GEMM + marginalisation epilogue, FP32 SIMT (plain path).
 struct SimtArgs {

@@ -10,6 +10,9 @@
 //                             (Eq. hh_ieo)
 //  K2  cross_terms            row records <h_{im}|h_{im'}>_d = sum_b omega_{d,b} h h'^*
 //  K9  build_dm_table         FP64 Gauss-Legendre table of the distance-marginal remainder
+#include <cstdio>
+#include <mutex>
+
 #include "common.cuh"
 #include "dist_marg.cuh"
 #include "kernels.h"
@@ -393,5 +396,64 @@ void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_
 }
 
 size_t dm_table_elems() { return (size_t)DM_NY * DM_NS; }
+
+// ---------------------------------------------------------------------------
+// Allocation-free distance-marginal evaluation.
+//
+// Scratch for the inputs and the output lives in this file-scope device array
+// (3 x DM_NOALLOC_MAX floats = 12 MiB), which every GPU that loads the library
+// holds until the process exits.  Host code cannot use the array's name as a
+// device address (on the host it is only a stand-in), so its address is looked
+// up once per device with cudaGetSymbolAddress and cached.  Every call shares
+// the one array: calls that overlap on the GPU (from different streams or
+// threads without ordering) race on it.  Each call overwrites exactly the
+// entries it reads before reading them, so nothing has to start at zero.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float g_dm_noalloc_scratch[3 * DM_NOALLOC_MAX];
+
+int dist_marg_eval_noalloc(int device, int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab,
+                           float *out, cudaStream_t st, char *msg, size_t msg_len) {
+  static std::mutex mu;
+  static float *addr[64] = {nullptr};
+  if (n < 0 || n > DM_NOALLOC_MAX) {
+    snprintf(msg, msg_len, "n=%lld exceeds the allocation-free limit of %lld evaluations per call", (long long)n,
+             (long long)DM_NOALLOC_MAX);
+    return DOTPE_E_INVALID;
+  }
+  if (device < 0 || device >= 64) {
+    snprintf(msg, msg_len, "device %d out of range", device);
+    return DOTPE_E_INVALID;
+  }
+  if (n == 0) return DOTPE_OK;
+  float *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[device]) {
+      // first use on this device (the caller has made `device` current)
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_dm_noalloc_scratch);
+      if (e != cudaSuccess || p == nullptr) {
+        snprintf(msg, msg_len, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return DOTPE_E_DEVICE;
+      }
+      addr[device] = (float *)p;
+    }
+    base = addr[device];
+  }
+  float *s_dh = base, *s_hh = base + DM_NOALLOC_MAX, *s_out = base + 2 * DM_NOALLOC_MAX;
+  cudaError_t e = cudaMemcpyAsync(s_dh, dh, (size_t)n * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s_hh, hh, (size_t)n * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) {
+    dist_marg_eval_kernel<<<nblk(n, 256), 256, 0, st>>>(n, s_dh, s_hh, u_min, tab, s_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, s_out, (size_t)n * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    snprintf(msg, msg_len, "%s", cudaGetErrorString(e));
+    return DOTPE_E_DEVICE;
+  }
+  return DOTPE_OK;
+}
 
 }  // namespace dotpe
