@@ -30,6 +30,7 @@ struct EpiParams {
   int mode_m[MAXM];
   int npair;                // n_modes (n_modes - 1) / 2
   int pdelta[NPAIR];        // m_a - m_b of pair p (index into C_delta, 1..3)
+  int consec;               // azimuthal numbers are consecutive: pdelta[p] = a - b
   float u_min;
   float z_scale;            // accumulator -> <d|h> component scale (times 1 / *g_scale)
   const float *g_scale;     // device scale applied to the extrinsic operand (null: 1)

@@ -160,7 +160,7 @@ static void CUDART_CB mark_done(void *p) {
 // ---------------------------------------------------------------------------
 struct ScratchLayout {
   size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, gpack, mx, tile_part, tile_ml, tile_arg,
-      tile_npass, row_part, col_part, ml_running, status, total;
+      tile_npass, row_part, col_part, ml_running, status, red, total;
   int n_itile, n_etile, pack_kind, pack_planes, TI, TE;
 };
 
@@ -199,6 +199,7 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.col_part = c.take<float2>((size_t)L.n_itile * E);
   L.ml_running = c.take<float>(1);
   L.status = c.take<int>(1);
+  L.red = c.take<uint8_t>(reduce_scratch_bytes());
   L.total = c.off;
   return L;
 }
@@ -275,6 +276,9 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
     for (int a = 1; a < MAXM; ++a)
       for (int c = 0; c < a; ++c, ++p) P.pdelta[p] = (a < b.M) ? (b.mode_m[a] - b.mode_m[c]) : 0;
   }
+  P.consec = 1;
+  for (int m = 1; m < b.M; ++m)
+    if (b.mode_m[m] != b.mode_m[m - 1] + 1) P.consec = 0;
   P.u_min = (float)e.u_min;
   P.cut_delta = (float)(e.cut > 0 ? e.cut : 0.0);
   P.ln_nphi = (float)std::log((double)e.nphi);
@@ -365,6 +369,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   ra.ln_p_int = e.ln_p_int;
   ra.ln_p_ext = e.ln_p_ext;
   ra.status = status;
+  ra.scratch = scr + L.red;
   ra.out = e.d_out;
   launch_reduce(ra, st);
   CUDA_OR_FAIL(cudaGetLastError());

@@ -38,6 +38,8 @@ __device__ __forceinline__ void fill_phase_tables(float2 *ph, const EpiParams &P
 
 // <h|h> coefficients for one pair from the row record (mrec) and column record (qrec):
 // C_0 = sum_d sum_m M_d[m,m] Q_d[m,m];  C_delta = sum_d sum_{a>b, m_a-m_b=delta} M_d[a,b] Q_d[a,b].
+// CONSEC: the modes' azimuthal numbers are consecutive, so pair (a, b) has delta = a - b.
+template <bool CONSEC>
 __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const float *__restrict__ qrec,
                                           const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
   C0 = 0.f;
@@ -50,21 +52,35 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
     const float *qr = qrec + d * REC;
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) C0 = fmaf(mr[m], qr[m], C0);
+    int p = 0;
 #pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-      float ar = mr[4 + 2 * p], ai = mr[5 + 2 * p];
-      float br = qr[4 + 2 * p], bi = qr[5 + 2 * p];
-      float hr = ar * br - ai * bi;
-      float hi = ar * bi + ai * br;
-      int dl = P.pdelta[p];
+    for (int a = 1; a < MAXM; ++a)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        bool sel = (dl == k + 1);
-        Cr[k] += sel ? hr : 0.f;
-        Ci[k] += sel ? hi : 0.f;
+      for (int b = 0; b < a; ++b, ++p) {
+        const float ar = mr[4 + 2 * p], ai = mr[5 + 2 * p];
+        const float br = qr[4 + 2 * p], bi = qr[5 + 2 * p];
+        if (CONSEC) {
+          const int k = a - b - 1;
+          Cr[k] = fmaf(ar, br, fmaf(-ai, bi, Cr[k]));
+          Ci[k] = fmaf(ar, bi, fmaf(ai, br, Ci[k]));
+        } else {
+          const float hr = ar * br - ai * bi, hi = ar * bi + ai * br;
+          const int dl = P.pdelta[p];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const bool sel = (dl == k + 1);
+            Cr[k] += sel ? hr : 0.f;
+            Ci[k] += sel ? hi : 0.f;
+          }
+        }
       }
-    }
   }
+}
+
+// Out-of-line distance marginal: it runs for the few phases that pass the ML
+// cut, so it is kept out of the hot loop's instruction stream.
+static __device__ __noinline__ float dm_lnlbar_call(float dh, float hh, float u_min, const float4 *tab) {
+  return dm_lnlbar(dh, hh, u_min, tab);
 }
 
 __device__ __forceinline__ PairRes pair_eval(const float Zr[MAXM], const float Zi[MAXM], float C0,
@@ -90,6 +106,7 @@ __device__ __forceinline__ PairRes pair_eval(const float Zr[MAXM], const float Z
   float mx = -INFINITY, s1 = 0.f, s2 = 0.f;
   float best = -1.f;
   int argo = 0, npass = 0;
+#pragma unroll 2
   for (int o = 0; o < P.n_phi; ++o) {
     float dh = 0.f;
 #pragma unroll
@@ -108,7 +125,7 @@ __device__ __forceinline__ PairRes pair_eval(const float Zr[MAXM], const float Z
     if (ml > best) { best = ml; argo = o; }
     if (!(ml >= thr)) continue;
     ++npass;
-    float l = dm_lnlbar(dh, hh, P.u_min, P.dm_table);
+    float l = dm_lnlbar_call(dh, hh, P.u_min, P.dm_table);
     if (l > mx) {
       float r = __expf(mx - l);
       s1 = fmaf(s1, r, 1.f);

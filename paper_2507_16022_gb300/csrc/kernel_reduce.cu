@@ -1,129 +1,210 @@
-// K6: cross-tile reduction in FP64 (Eq. Z_sum with w_o = 1; Eqs. posterior_element,
-// int_ess, ext_ess).  Each fused-kernel tile left log-sum-exp partials (max, sum) in
-// FP32; they are combined here in double precision.
+// K6: cross-tile reduction (Eq. Z_sum with w_o = 1; Eqs. posterior_element,
+// int_ess, ext_ess).  Each fused-kernel tile left log-sum-exp partials (max, sum)
+// in FP32; they are combined with FP64 accumulation:
 //   ln S1 = ln sum_ieo p_ieo,  ln S2 = ln sum_ieo p_ieo^2,  p_ieo = w_i w_e Lbar_ieo
 //   ln Z  = ln S1 - ln(N_i N_e N_phi)
 //   N_eff = S1^2 / S2, N_eff,int = S1^2 / sum_i P_i^2, N_eff,ext = S1^2 / sum_e P_e^2
+// Two passes per log-sum-exp: the maximum (FP32, exact), then the sum of
+// s * exp(m - max) accumulated in FP64 (the exponentials of FP32 partials are
+// evaluated in FP32: their relative error is that of the partials themselves).
 #include "common.cuh"
 #include "kernels.h"
 
 namespace dotpe {
 
-struct DLse {
-  double m, s;
-  __device__ void init() { m = -INFINITY; s = 0.0; }
-  __device__ void add_ms(double om, double os) {
-    if (om == -INFINITY || !(os > 0.0)) return;
-    if (m == -INFINITY) { m = om; s = os; return; }
-    if (om > m) { s = s * exp(m - om) + os; m = om; }
-    else s += os * exp(om - m);
-  }
-  __device__ double value() const { return (m == -INFINITY) ? -INFINITY : m + log(s); }
-};
+namespace {
+constexpr int RB = 256;  // threads per block
+constexpr int NB = 128;  // blocks of the parallel passes
+constexpr int NSUM = 4;  // quantities reduced in the final pass
+}
 
-// ln P_i over the e-tiles (row partials [n_etile][n_int])
-__global__ void reduce_rows_kernel(int64_t n, int nparts, const float2 *__restrict__ part, double *__restrict__ out) {
+// ln P over partials [nparts][n] (row or column marginal), one thread per entry.
+__global__ void reduce_lines_kernel(int64_t n, int nparts, const float2 *__restrict__ part, double *__restrict__ out) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  DLse a;
-  a.init();
+  float m = -INFINITY;
   for (int p = 0; p < nparts; ++p) {
     float2 v = part[(int64_t)p * n + k];
-    a.add_ms((double)v.x, (double)v.y);
+    if (v.y > 0.f) m = fmaxf(m, v.x);
   }
-  out[k] = a.value();
+  if (m == -INFINITY) {
+    out[k] = -INFINITY;
+    return;
+  }
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) {
+    float2 v = part[(int64_t)p * n + k];
+    if (v.y > 0.f) s += (double)v.y * (double)__expf(v.x - m);
+  }
+  out[k] = (double)m + log(s);
 }
 
-__device__ void block_lse(DLse &a, double *sm, double *ss) {
-  const int t = threadIdx.x;
-  sm[t] = a.m;
-  ss[t] = a.s;
+__device__ __forceinline__ float block_max(float v, float *sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (t < w) {
-      DLse x;
-      x.m = sm[t];
-      x.s = ss[t];
-      x.add_ms(sm[t + w], ss[t + w]);
-      sm[t] = x.m;
-      ss[t] = x.s;
-    }
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) sh[0] = v;
   }
-  a.m = sm[0];
-  a.s = ss[0];
   __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
 }
 
-__global__ void __launch_bounds__(1024) reduce_final_kernel(ReduceArgs a) {
-  __shared__ double sm[1024], ss[1024];
-  __shared__ float bml[1024];
-  __shared__ long long barg[1024];
-  __shared__ long long bnp[1024];
-  const int t = threadIdx.x, nt = blockDim.x;
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+// Pass 1: per-block maxima of the four log-sum-exp inputs (tile m1, tile m2,
+// 2 ln P_i, 2 ln P_e), the argmax and the marginalised count.
+__global__ void __launch_bounds__(RB) reduce_pass1_kernel(ReduceArgs a, float *__restrict__ bmax,
+                                                           float *__restrict__ bml, long long *__restrict__ barg,
+                                                           long long *__restrict__ bnp) {
+  __shared__ float shf[32];
+  __shared__ double shd[32];
+  __shared__ float sv[RB];
+  __shared__ long long sa[RB];
   const int64_t n_tiles = (int64_t)a.n_itile * a.n_etile;
-  DLse s1, s2, ri, ce;
-  s1.init(); s2.init(); ri.init(); ce.init();
-  float best = -1.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float m1 = -INFINITY, m2 = -INFINITY, mr = -INFINITY, mc = -INFINITY, best = -1.f;
   long long arg = 0x7fffffffffffffffLL, np = 0;
-  for (int64_t k = t; k < n_tiles; k += nt) {
+  for (int64_t k = k0; k < n_tiles; k += stride) {
     float4 v = a.tile_part[k];
-    s1.add_ms(v.x, v.y);
-    s2.add_ms(v.z, v.w);
+    if (v.y > 0.f) m1 = fmaxf(m1, v.x);
+    if (v.w > 0.f) m2 = fmaxf(m2, v.z);
     float ml = a.tile_ml[k];
     long long g = a.tile_arg[k];
     if (ml > best || (ml == best && g < arg)) { best = ml; arg = g; }
     np += a.tile_npass[k];
   }
-  for (int64_t k = t; k < a.n_int; k += nt) {
-    double v = a.ln_p_int[k];
-    if (v != -INFINITY) ri.add_ms(2.0 * v, 1.0);
+  for (int64_t k = k0; k < a.n_int; k += stride) mr = fmaxf(mr, (float)(2.0 * a.ln_p_int[k]));
+  for (int64_t k = k0; k < a.n_ext; k += stride) mc = fmaxf(mc, (float)(2.0 * a.ln_p_ext[k]));
+  float r[NSUM] = {m1, m2, mr, mc};
+  for (int q = 0; q < NSUM; ++q) {
+    float v = block_max(r[q], shf);
+    if (threadIdx.x == 0) bmax[q * gridDim.x + blockIdx.x] = v;
   }
-  for (int64_t k = t; k < a.n_ext; k += nt) {
-    double v = a.ln_p_ext[k];
-    if (v != -INFINITY) ce.add_ms(2.0 * v, 1.0);
-  }
-  block_lse(s1, sm, ss);
-  block_lse(s2, sm, ss);
-  block_lse(ri, sm, ss);
-  block_lse(ce, sm, ss);
-  bml[t] = best;
-  barg[t] = arg;
-  bnp[t] = np;
+  sv[threadIdx.x] = best;
+  sa[threadIdx.x] = arg;
   __syncthreads();
-  for (int w = nt / 2; w > 0; w >>= 1) {
-    if (t < w) {
-      if (bml[t + w] > bml[t] || (bml[t + w] == bml[t] && barg[t + w] < barg[t])) {
-        bml[t] = bml[t + w];
-        barg[t] = barg[t + w];
+  for (int w = RB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      if (sv[threadIdx.x + w] > sv[threadIdx.x] ||
+          (sv[threadIdx.x + w] == sv[threadIdx.x] && sa[threadIdx.x + w] < sa[threadIdx.x])) {
+        sv[threadIdx.x] = sv[threadIdx.x + w];
+        sa[threadIdx.x] = sa[threadIdx.x + w];
       }
-      bnp[t] += bnp[t + w];
     }
     __syncthreads();
   }
-  if (t == 0) {
-    ReduceOut o;
-    double l1 = s1.value(), l2 = s2.value();
-    o.ln_s1 = l1;
-    o.ln_s2 = l2;
-    o.ln_z = l1 - log((double)a.n_int) - log((double)a.n_ext) - log((double)a.n_phi);
-    o.n_eff = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - l2);
-    o.n_eff_int = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - ri.value());
-    o.n_eff_ext = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - ce.value());
-    o.max_ml = bml[0];
-    o.arg = barg[0];
-    o.n_marg = bnp[0];
-    o.threshold = (a.cut_delta > 0.f) ? (double)(*a.ml_running) - (double)a.cut_delta : -INFINITY;
-    o.status = *a.status;
-    o.pad = 0;
-    *a.out = o;
+  double npd = block_sum((double)np, shd);  // counts < 2^53
+  if (threadIdx.x == 0) {
+    bml[blockIdx.x] = sv[0];
+    barg[blockIdx.x] = sa[0];
+    bnp[blockIdx.x] = (long long)npd;
   }
 }
 
+// Pass 2: per-block FP64 sums of s * exp(m - M) against the global maxima.
+__global__ void __launch_bounds__(RB) reduce_pass2_kernel(ReduceArgs a, const float *__restrict__ bmax,
+                                                           double *__restrict__ bsum) {
+  __shared__ double shd[32];
+  __shared__ float M[NSUM];
+  if (threadIdx.x < NSUM) {
+    float m = -INFINITY;
+    for (int b = 0; b < (int)gridDim.x; ++b) m = fmaxf(m, bmax[threadIdx.x * gridDim.x + b]);
+    M[threadIdx.x] = m;
+  }
+  __syncthreads();
+  const int64_t n_tiles = (int64_t)a.n_itile * a.n_etile;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double s[NSUM] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t k = k0; k < n_tiles; k += stride) {
+    float4 v = a.tile_part[k];
+    if (v.y > 0.f) s[0] += (double)v.y * (double)__expf(v.x - M[0]);
+    if (v.w > 0.f) s[1] += (double)v.w * (double)__expf(v.z - M[1]);
+  }
+  for (int64_t k = k0; k < a.n_int; k += stride) {
+    double v = a.ln_p_int[k];
+    if (v != -INFINITY) s[2] += exp(2.0 * v - (double)M[2]);
+  }
+  for (int64_t k = k0; k < a.n_ext; k += stride) {
+    double v = a.ln_p_ext[k];
+    if (v != -INFINITY) s[3] += exp(2.0 * v - (double)M[3]);
+  }
+  for (int q = 0; q < NSUM; ++q) {
+    double v = block_sum(s[q], shd);
+    if (threadIdx.x == 0) bsum[q * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+__global__ void reduce_finish_kernel(ReduceArgs a, int nb, const float *__restrict__ bmax, const double *__restrict__ bsum,
+                                     const float *__restrict__ bml, const long long *__restrict__ barg,
+                                     const long long *__restrict__ bnp) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lv[NSUM];
+  for (int q = 0; q < NSUM; ++q) {
+    float m = -INFINITY;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) m = fmaxf(m, bmax[q * nb + b]);
+    for (int b = 0; b < nb; ++b) s += bsum[q * nb + b];  // fixed order: deterministic
+    lv[q] = (m == -INFINITY || !(s > 0.0)) ? -INFINITY : (double)m + log(s);
+  }
+  float best = -1.f;
+  long long arg = 0x7fffffffffffffffLL, np = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (bml[b] > best || (bml[b] == best && barg[b] < arg)) { best = bml[b]; arg = barg[b]; }
+    np += bnp[b];
+  }
+  ReduceOut o;
+  const double l1 = lv[0], l2 = lv[1];
+  o.ln_s1 = l1;
+  o.ln_s2 = l2;
+  o.ln_z = l1 - log((double)a.n_int) - log((double)a.n_ext) - log((double)a.n_phi);
+  o.n_eff = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - l2);
+  o.n_eff_int = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - lv[2]);
+  o.n_eff_ext = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - lv[3]);
+  o.max_ml = best;
+  o.arg = arg;
+  o.n_marg = np;
+  o.threshold = (a.cut_delta > 0.f) ? (double)(*a.ml_running) - (double)a.cut_delta : -INFINITY;
+  o.status = *a.status;
+  o.pad = 0;
+  *a.out = o;
+}
+
+size_t reduce_scratch_bytes() {
+  return (size_t)NB * (NSUM * sizeof(float) + NSUM * sizeof(double) + sizeof(float) + 2 * sizeof(long long)) + 256;
+}
+
 void launch_reduce(const ReduceArgs &a, cudaStream_t st) {
-  reduce_rows_kernel<<<(unsigned)((a.n_int + 255) / 256), 256, 0, st>>>(a.n_int, a.n_etile, a.row_part, a.ln_p_int);
-  reduce_rows_kernel<<<(unsigned)((a.n_ext + 255) / 256), 256, 0, st>>>(a.n_ext, a.n_itile, a.col_part, a.ln_p_ext);
-  reduce_final_kernel<<<1, 1024, 0, st>>>(a);
+  reduce_lines_kernel<<<(unsigned)((a.n_int + 255) / 256), 256, 0, st>>>(a.n_int, a.n_etile, a.row_part, a.ln_p_int);
+  reduce_lines_kernel<<<(unsigned)((a.n_ext + 255) / 256), 256, 0, st>>>(a.n_ext, a.n_itile, a.col_part, a.ln_p_ext);
+  uint8_t *w = (uint8_t *)a.scratch;
+  float *bmax = (float *)w;
+  double *bsum = (double *)(w + NB * NSUM * sizeof(float));
+  float *bml = (float *)(bsum + NB * NSUM);
+  long long *barg = (long long *)(((uintptr_t)(bml + NB) + 7) & ~(uintptr_t)7);
+  long long *bnp = barg + NB;
+  reduce_pass1_kernel<<<NB, RB, 0, st>>>(a, bmax, bml, barg, bnp);
+  reduce_pass2_kernel<<<NB, RB, 0, st>>>(a, bmax, bsum);
+  reduce_finish_kernel<<<1, 32, 0, st>>>(a, NB, bmax, bsum, bml, barg, bnp);
 }
 
 }  // namespace dotpe

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NT) simt_fused_kernel(SimtArgs g, EpiParams P)
           x = sx; x2 = sx; ml = 0.f;
         } else {
           float C0, Cr[3], Ci[3];
-          hh_coeffs(mrec, &qs[el * MAXD * REC], P, C0, Cr, Ci);
+          hh_coeffs<false>(mrec, &qs[el * MAXD * REC], P, C0, Cr, Ci);
           PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, ph);
           float lw = (float)(lwi + lwe[el]);
           x = pr.lsum + lw;

@@ -4,8 +4,10 @@
 //   warp 0      TMA producer: bank tile A (128 rows x 64 k) and extrinsic tile B
 //               (64 rows = 32 samples x (re, im), 64 k) into a STAGES-deep ring
 //   warp 1      TMEM allocator and tcgen05.mma issuer (one elected lane)
-//   warps 2..5  epilogue: tcgen05.ld of the accumulators, <h|h> coefficients,
-//               phase grid, ML cut, distance marginal, log-sum-exp partials
+//   warps 2..9  epilogue (two warps per TMEM lane quadrant, each taking half
+//               of the tile's extrinsic samples): tcgen05.ld of the accumulators,
+//               <h|h> coefficients, phase grid, ML cut, distance marginal,
+//               log-sum-exp partials
 // Tile = 128 bank rows x 32 extrinsic samples, all modes: accumulators for mode
 // m live in TMEM columns [buf*256 + 64 m, +64) (two buffers, so the epilogue of
 // tile t overlaps the MMAs of tile t+1).  Per mode the GEMM is the real-ified
@@ -18,16 +20,26 @@
 namespace dotpe {
 
 namespace {
-constexpr int TI = TC_TI, TE = TC_TE, BN = 2 * TE, BK = 64, ST = 7;
-constexpr int NT = 192;
-constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TI = TC_TI, TE = TC_TE, BN = 2 * TE, BK = 64;
+constexpr int NEPI = 8;              // epilogue warps
+constexpr int NT = (2 + NEPI) * 32;  // 320 threads
+constexpr int EPT = NEPI * 32;       // epilogue threads
+constexpr int EHALF = TE / 2;        // extrinsic samples per epilogue thread and tile
+constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2;
+// Pipeline depth: single pass = 7 stages of {A, B} (24 KB); split precision =
+// 4 stages of {A_hi, A_lo, B_hi, B_lo} (48 KB), whose three MMA groups
+// (hi*hi, hi*lo, lo*hi) share one load of each operand plane.
+template <bool SPLIT> struct Pipe {
+  static constexpr int NPL = SPLIT ? 2 : 1;
+  static constexpr int ST = SPLIT ? 4 : 7;
+  static constexpr uint32_t STAGE = NPL * (A_BYTES + B_BYTES);
+};
 constexpr uint32_t TMEM_COLS = 512, BUF_COLS = MAXM * BN;
 constexpr int XS_LD = TE + 1;
 static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
 
 struct TcShape {
-  int n_itile, n_etile, kb, n_pass;
-  int pa[3], pb[3];
+  int n_itile, n_etile, kb;
   int a_plane_rows, a_mode_rows, a_row0;
   int b_plane_rows, b_mode_rows;
 };
@@ -37,24 +49,40 @@ struct TcTail {
   float qs[TE * MAXD * REC];
   double lwe[TE];
   float2 ph[7 * MAXPHI];
-  float wm1[4], ws1[4], wm2[4], ws2[4], wml[4];
-  long long warg[4];
-  int wnp[4];
-  uint64_t full[ST], empty[ST], tfull[2], tempty[2], drain;
+  float2 rowh[TI];  // second-half row partial of each row
+  float wm1[NEPI], ws1[NEPI], wm2[NEPI], ws2[NEPI], wml[NEPI];
+  long long warg[NEPI];
+  int wnp[NEPI];
+  uint64_t full[7], empty[7], tfull[2], tempty[2], drain;
   uint32_t tmem_slot;
   int abort_flag;
 };
-constexpr size_t SMEM_BYTES = 1024 + (size_t)ST * STAGE_BYTES + sizeof(TcTail);
+template <bool SPLIT>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)Pipe<SPLIT>::ST * Pipe<SPLIT>::STAGE + sizeof(TcTail);
+}
+static_assert(smem_bytes<true>() <= 232448 && smem_bytes<false>() <= 232448, "shared memory budget");
 }  // namespace
 
-template <bool BF16>
+// 32 lanes x 32-bit, 2 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
+  a = __uint_as_float(r0);
+  b = __uint_as_float(r1);
+}
+
+template <bool BF16, bool CONSEC, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const TcShape S, const EpiParams P) {
+  constexpr int ST = Pipe<SPLIT>::ST, NPL = Pipe<SPLIT>::NPL;
+  constexpr uint32_t STAGE_BYTES = Pipe<SPLIT>::STAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // stage s, plane p: A at sA + (s NPL + p) A_BYTES, B at sB + (s NPL + p) B_BYTES
   uint8_t *sA = base;
-  uint8_t *sB = base + ST * A_BYTES;
+  uint8_t *sB = base + ST * NPL * A_BYTES;
   TcTail &T = *reinterpret_cast<TcTail *>(base + (size_t)ST * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = S.n_itile * S.n_etile;
@@ -67,7 +95,7 @@ __global__ void __launch_bounds__(NT, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&T.tfull[b], 1);
-      mbar_init(&T.tempty[b], 4);
+      mbar_init(&T.tempty[b], NEPI);
     }
     mbar_init(&T.drain, 1);
     T.abort_flag = 0;
@@ -78,7 +106,7 @@ __global__ void __launch_bounds__(NT, 1)
     tma_prefetch_desc(&mapB);
   }
   if (warp == 1) tmem_alloc(&T.tmem_slot, TMEM_COLS);
-  if (warp >= 2) fill_phase_tables(T.ph, P, threadIdx.x - 64, 128);
+  if (warp >= 2) fill_phase_tables(T.ph, P, threadIdx.x - 64, EPT);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -92,19 +120,21 @@ __global__ void __launch_bounds__(NT, 1)
       bool ok = !P.test_stall;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int it = t / S.n_etile, et = t % S.n_etile;
-        for (int m = 0; m < M && ok; ++m)
-          for (int p = 0; p < S.n_pass && ok; ++p) {
-            const int arow = S.pa[p] * S.a_plane_rows + m * S.a_mode_rows + S.a_row0 + it * TI;
-            const int brow = S.pb[p] * S.b_plane_rows + m * S.b_mode_rows + et * BN;
-            for (int kb = 0; kb < S.kb; ++kb, ++q) {
-              const int s = q % ST;
-              const uint32_t n = q / ST;
-              if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, P.status, abortp, P.wait_ns))) break;
-              mbar_expect_tx(&T.full[s], STAGE_BYTES);
-              tma_load_2d(sA + s * A_BYTES, &mapA, &T.full[s], kb * BK, arow);
-              tma_load_2d(sB + s * B_BYTES, &mapB, &T.full[s], kb * BK, brow);
+        for (int m = 0; m < M && ok; ++m) {
+          const int arow = m * S.a_mode_rows + S.a_row0 + it * TI;
+          const int brow = m * S.b_mode_rows + et * BN;
+          for (int kb = 0; kb < S.kb; ++kb, ++q) {
+            const int s = q % ST;
+            const uint32_t n = q / ST;
+            if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, P.status, abortp, P.wait_ns))) break;
+            mbar_expect_tx(&T.full[s], STAGE_BYTES);
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+              tma_load_2d(sA + (s * NPL + pl) * A_BYTES, &mapA, &T.full[s], kb * BK, pl * S.a_plane_rows + arow);
+              tma_load_2d(sB + (s * NPL + pl) * B_BYTES, &mapB, &T.full[s], kb * BK, pl * S.b_plane_rows + brow);
             }
           }
+        }
       }
       if (!ok) {
         // let copies already in flight land before the CTA exits
@@ -128,18 +158,24 @@ __global__ void __launch_bounds__(NT, 1)
         tc_fence_after();
         for (int m = 0; m < M && ok; ++m) {
           const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
-          for (int p = 0; p < S.n_pass && ok; ++p)
-            for (int kb = 0; kb < S.kb; ++kb, ++q) {
-              const int s = q % ST;
-              const uint32_t n = q / ST;
-              if (!(ok = mbar_wait(&T.full[s], n & 1, P.status, abortp, P.wait_ns))) break;
-              tc_fence_after();
-              const uint64_t ad = sdesc_k128(sA + s * A_BYTES), bd = sdesc_k128(sB + s * B_BYTES);
+          for (int kb = 0; kb < S.kb; ++kb, ++q) {
+            const int s = q % ST;
+            const uint32_t n = q / ST;
+            if (!(ok = mbar_wait(&T.full[s], n & 1, P.status, abortp, P.wait_ns))) break;
+            tc_fence_after();
+            const uint64_t ah = sdesc_k128(sA + (s * NPL) * A_BYTES), bh = sdesc_k128(sB + (s * NPL) * B_BYTES);
+            const uint64_t al = sdesc_k128(sA + (s * NPL + NPL - 1) * A_BYTES);
+            const uint64_t bl = sdesc_k128(sB + (s * NPL + NPL - 1) * B_BYTES);
 #pragma unroll
-              for (int k = 0; k < BK / 16; ++k)
-                tc_mma(dcol, ad + 2 * k, bd + 2 * k, idesc, (p | kb | k) ? 1u : 0u);
-              tc_commit(&T.empty[s]);
+            for (int k = 0; k < BK / 16; ++k) {
+              tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (kb | k) ? 1u : 0u);
+              if (SPLIT) {
+                tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
+                tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+              }
             }
+            tc_commit(&T.empty[s]);
+          }
         }
         if (ok) tc_commit(&T.tfull[b]);
       }
@@ -149,9 +185,10 @@ __global__ void __launch_bounds__(NT, 1)
       mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
     }
   } else {
-    // ---------------- epilogue (128 threads, one tile row each) ----------------
-    const int ew = warp - 2;
-    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    // ---------------- epilogue (256 threads: one tile row, half the samples each) ----------------
+    const int ew = warp - 2;      // 0..7
+    const int quad = warp & 3;    // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;     // which 16 of the tile's 32 extrinsic samples
     const int row = quad * 32 + lane;
     const int etid = threadIdx.x - 64;
     const bool store = (P.lnl_tile != nullptr);
@@ -181,12 +218,12 @@ __global__ void __launch_bounds__(NT, 1)
         lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
         cur_it = it;
       }
-      for (int k = etid; k < TE * P.n_det * REC; k += 128) {
+      for (int k = etid; k < TE * P.n_det * REC; k += EPT) {
         const int e = k / (P.n_det * REC), qq = k % (P.n_det * REC);
         T.qs[e * MAXD * REC + qq] = (e0 + e < P.n_ext) ? __ldg(P.qx + (e0 + e) * P.n_det * REC + qq) : 0.f;
       }
-      for (int k = etid; k < TE; k += 128) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
-      named_bar_sync(1, 128);
+      for (int k = etid; k < TE; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
+      named_bar_sync(1, EPT);
       const float thr = (P.cut_delta > 0.f) ? (*(volatile float *)P.ml_running - P.cut_delta) : -INFINITY;
       if (!mbar_wait(&T.tfull[b], use & 1, P.status, abortp, P.wait_ns)) break;
       tc_fence_after();
@@ -199,82 +236,83 @@ __global__ void __launch_bounds__(NT, 1)
       int np = 0;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS;
 #pragma unroll 1
-      for (int c = 0; c < TE / 8; ++c) {
-        float z[MAXM][16];
+      for (int j = 0; j < EHALF; ++j) {
+        const int el = half * EHALF + j;
+        const int64_t e = e0 + el;
+        float Zr[MAXM], Zi[MAXM];
 #pragma unroll
         for (int m = 0; m < MAXM; ++m) {
-          if (m < M) tmem_ld16(tbase + m * BN + c * 16, z[m]);
-          else
-#pragma unroll
-            for (int k = 0; k < 16; ++k) z[m][k] = 0.f;
+          if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
+          else { Zr[m] = 0.f; Zi[m] = 0.f; }
         }
         tmem_ld_wait();
-        if (c == TE / 8 - 1) {
-          // accumulators of this buffer are in registers: hand it back to the MMA warp
+        if (j == EHALF - 1) {
+          // this warp's accumulators are in registers: release the buffer to the MMA warp
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&T.tempty[b]);
         }
+        float x = -INFINITY, x2 = -INFINITY;
+        if (vi && e < P.n_ext) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int el = c * 8 + j;
-          const int64_t e = e0 + el;
-          float x = -INFINITY, x2 = -INFINITY;
-          if (vi && e < P.n_ext) {
-            float Zr[MAXM], Zi[MAXM];
+          for (int m = 0; m < MAXM; ++m) {
+            Zr[m] *= zs;
+            Zi[m] *= zs;
+          }
+          if (P.gemm_only) {
+            float sx = 0.f;
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              Zr[m] = z[m][2 * j] * zs;
-              Zi[m] = z[m][2 * j + 1] * zs;
+            for (int m = 0; m < MAXM; ++m) sx += Zr[m] + Zi[m];
+            x = sx;
+            x2 = sx;
+          } else {
+            float C0, Cr[3], Ci[3];
+            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph);
+            const float lw = (float)(lwi + T.lwe[el]);
+            x = pr.lsum + lw;
+            x2 = pr.lsum2 + 2.f * lw;
+            np += pr.npass;
+            if (pr.ml > best) {
+              best = pr.ml;
+              barg = (i * P.n_ext + e) * (long long)P.n_phi + pr.argo;
             }
-            if (P.gemm_only) {
-              float sx = 0.f;
-#pragma unroll
-              for (int m = 0; m < MAXM; ++m) sx += Zr[m] + Zi[m];
-              x = sx;
-              x2 = sx;
-            } else {
-              float C0, Cr[3], Ci[3];
-              hh_coeffs(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
-              PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph);
-              const float lw = (float)(lwi + T.lwe[el]);
-              x = pr.lsum + lw;
-              x2 = pr.lsum2 + 2.f * lw;
-              np += pr.npass;
-              if (pr.ml > best) {
-                best = pr.ml;
-                barg = (i * P.n_ext + e) * (long long)P.n_phi + pr.argo;
-              }
-              if (store) {
-                P.lnl_tile[i * P.n_ext + e] = pr.lsum - P.ln_nphi;
-                P.ml_tile[i * P.n_ext + e] = pr.ml;
-              }
+            if (store) {
+              P.lnl_tile[i * P.n_ext + e] = pr.lsum - P.ln_nphi;
+              P.ml_tile[i * P.n_ext + e] = pr.ml;
             }
           }
-          T.xs[row * XS_LD + el] = x;
-          ra.add(x);
-          rb.add(x2);
         }
+        T.xs[row * XS_LD + el] = x;
+        ra.add(x);
+        rb.add(x2);
       }
-      if (vi) P.row_part[(int64_t)et * P.n_int + i] = make_float2(ra.m, ra.s);
-      warp_merge_lse(ra);
+      if (half == 1) T.rowh[row] = make_float2(ra.m, ra.s);
       warp_merge_lse(rb);
       warp_argmax(best, barg);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
-      if (lane == 0) {
-        T.wm1[ew] = ra.m; T.ws1[ew] = ra.s; T.wm2[ew] = rb.m; T.ws2[ew] = rb.s;
-        T.wml[ew] = best; T.warg[ew] = barg; T.wnp[ew] = np;
-      }
-      named_bar_sync(1, 128);
       {
-        // column partials: 4 threads per extrinsic sample, 32 rows each
-        const int cc = etid >> 2, qq = etid & 3;
+        Lse w = ra;
+        warp_merge_lse(w);
+        if (lane == 0) {
+          T.wm1[ew] = w.m; T.ws1[ew] = w.s; T.wm2[ew] = rb.m; T.ws2[ew] = rb.s;
+          T.wml[ew] = best; T.warg[ew] = barg; T.wnp[ew] = np;
+        }
+      }
+      named_bar_sync(1, EPT);
+      if (half == 0 && vi) {
+        ra.merge(T.rowh[row].x, T.rowh[row].y);
+        P.row_part[(int64_t)et * P.n_int + i] = make_float2(ra.m, ra.s);
+      }
+      {
+        // column partials: 8 threads per extrinsic sample, 16 rows each
+        const int cc = etid >> 3, qq = etid & 7;
         Lse a;
         a.init();
-        for (int r = qq * 32; r < qq * 32 + 32; ++r) a.add(T.xs[r * XS_LD + cc]);
+        for (int r = qq * 16; r < qq * 16 + 16; ++r) a.add(T.xs[r * XS_LD + cc]);
 #pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
+        for (int o = 1; o <= 4; o <<= 1) {
           float om = __shfl_xor_sync(0xffffffffu, a.m, o);
           float os = __shfl_xor_sync(0xffffffffu, a.s, o);
           a.merge(om, os);
@@ -288,7 +326,7 @@ __global__ void __launch_bounds__(NT, 1)
         float bv = -1.f;
         long long bi = 0x7fffffffffffffffLL;
         int n = 0;
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < NEPI; ++w) {
           a.merge(T.wm1[w], T.ws1[w]);
           bb.merge(T.wm2[w], T.ws2[w]);
           n += T.wnp[w];
@@ -300,7 +338,7 @@ __global__ void __launch_bounds__(NT, 1)
         P.tile_npass[t] = n;
         if (bv > 0.f && P.cut_delta > 0.f) atomic_max_nonneg(P.ml_running, bv);
       }
-      named_bar_sync(1, 128);
+      named_bar_sync(1, EPT);
     }
   }
   tc_fence_before();
@@ -335,8 +373,6 @@ int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   S.n_itile = (int)((P.n_int + TI - 1) / TI);
   S.n_etile = (int)((P.n_ext + TE - 1) / TE);
   S.kb = g.kb_per_mode;
-  S.n_pass = g.n_pass;
-  for (int k = 0; k < 3; ++k) { S.pa[k] = g.pa[k]; S.pb[k] = g.pb[k]; }
   S.a_plane_rows = g.a_plane_rows;
   S.a_mode_rows = g.a_mode_rows;
   S.a_row0 = g.a_row0;
@@ -346,20 +382,20 @@ int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   int grid = g.n_sms < n_tiles ? g.n_sms : n_tiles;
   if (grid < 1) grid = 1;
   cudaError_t err;
-  if (g.bf16) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-      attr = true;
-    }
-    tc_fused_kernel<true><<<grid, NT, SMEM_BYTES, st>>>(g.mapA, g.mapB, S, P);
+  auto go = [&](auto kern, size_t smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, NT, smem, st>>>(g.mapA, g.mapB, S, P);
+  };
+  const bool split = g.n_pass == 3;
+  if (split) {
+    if (P.consec) go(tc_fused_kernel<true, true, true>, smem_bytes<true>());
+    else go(tc_fused_kernel<true, false, true>, smem_bytes<true>());
+  } else if (g.bf16) {
+    if (P.consec) go(tc_fused_kernel<true, true, false>, smem_bytes<false>());
+    else go(tc_fused_kernel<true, false, false>, smem_bytes<false>());
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-      attr = true;
-    }
-    tc_fused_kernel<false><<<grid, NT, SMEM_BYTES, st>>>(g.mapA, g.mapB, S, P);
+    if (P.consec) go(tc_fused_kernel<false, true, false>, smem_bytes<false>());
+    else go(tc_fused_kernel<false, false, false>, smem_bytes<false>());
   }
   err = cudaGetLastError();
   return (int)err;

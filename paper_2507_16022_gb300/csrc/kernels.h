@@ -94,11 +94,12 @@ struct ReduceArgs {
   float cut_delta;
   double *ln_p_int;  // [n_int] out
   double *ln_p_ext;  // [n_ext] out
-  double *scratch;   // >= 2 * 1024 doubles
+  void *scratch;     // reduce_scratch_bytes() of device memory
   const int *status;
   ReduceOut *out;
 };
 void launch_reduce(const ReduceArgs &a, cudaStream_t st);
+size_t reduce_scratch_bytes();
 
 // Tensor-map encoding through the driver entry point.
 int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t inner, uint64_t rows,
