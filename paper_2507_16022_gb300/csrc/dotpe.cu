@@ -127,6 +127,7 @@ struct dotpe_ctx {
   std::unordered_map<uint64_t, dotpe::Event *> events;
   std::deque<uint64_t> queue;
   uint64_t next_id = 1;
+  double l2_band_bytes = 0;  // extrinsic operand kept in L2 per sweep of the bank
   // completion callbacks -> admission worker
   std::mutex cb_mu;
   std::condition_variable cv;
@@ -330,8 +331,11 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
       return fail(DOTPE_E_UNSUPPORTED, "operand too large for 32-bit TMA coordinates");
     CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     void *abase = bf ? (void *)b.bf : (void *)b.hf;
-    if (encode_tmap_2d(&g.mapA, dt, abase, b.Kpad, a_rows, (uint64_t)b.Kpad * 2, 64, TC_TI) ||
-        encode_tmap_2d(&g.mapB, dt, pa.gpack, b.Kpad, b_rows, (uint64_t)b.Kpad * 2, 64, 2 * TC_TE))
+    g.n_modes = b.M;
+    g.l2_band_bytes = ctx->l2_band_bytes;
+    const int kbx = tc_kblocks_per_stage();
+    if (encode_tmap_kblocks(&g.mapA, dt, abase, a_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, TC_TI, kbx) ||
+        encode_tmap_kblocks(&g.mapB, dt, pa.gpack, b_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, 2 * TC_TE, kbx))
       return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed");
     g.a_plane_rows = b.M * (int)b.I;
     g.a_mode_rows = (int)b.I;
@@ -519,6 +523,11 @@ int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   ctx->budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
+  // a third of L2 for the resident extrinsic band: the rest serves the streaming
+  // bank tiles and the two L2 partitions' duplicates
+  ctx->l2_band_bytes = prop.l2CacheSize / 3.0;
+  if (const char *v = getenv("DOTPE_L2_BAND_MB")) ctx->l2_band_bytes = atof(v) * 1048576.0;
+
   int ns = c.n_slots > 0 ? c.n_slots : 4;
   ctx->streams.resize(ns);
   ctx->slot_busy.assign(ns, 0);

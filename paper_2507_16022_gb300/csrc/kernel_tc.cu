@@ -1,8 +1,11 @@
 // K3: fused <d|h> GEMM on the 5th-generation tensor cores + marginalisation epilogue.
 //
 // Persistent kernel, one CTA per SM, warp-specialised:
-//   warp 0      TMA producer: bank tile A (128 rows x 64 k) and extrinsic tile B
-//               (64 rows = 32 samples x (re, im), 64 k) into a STAGES-deep ring
+//   warp 0      TMA producer: bank tile A (128 rows x 2 k-blocks of 64) and
+//               extrinsic tile B (64 rows = 32 samples x (re, im), 2 k-blocks)
+//               into a ring of stages; each load is one 3-D box spanning two
+//               k-blocks (one TMA transaction per operand and stage: the per-CTA
+//               TMA rate grows with the transaction size)
 //   warp 1      TMEM allocator and tcgen05.mma issuer (one elected lane)
 //   warps 2..9  epilogue (two warps per TMEM lane quadrant, each taking half
 //               of the tile's extrinsic samples): tcgen05.ld of the accumulators,
@@ -25,14 +28,16 @@ constexpr int NEPI = 8;              // epilogue warps
 constexpr int NT = (2 + NEPI) * 32;  // 320 threads
 constexpr int EPT = NEPI * 32;       // epilogue threads
 constexpr int EHALF = TE / 2;        // extrinsic samples per epilogue thread and tile
-constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2;
-// Pipeline depth: single pass = 7 stages of {A, B} (24 KB); split precision =
-// 4 stages of {A_hi, A_lo, B_hi, B_lo} (48 KB), whose three MMA groups
-// (hi*hi, hi*lo, lo*hi) share one load of each operand plane.
+constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2;  // one k-block
+constexpr int KBX = 2;  // k-blocks per stage (one 3-D TMA box)
+// Pipeline: single pass = 4 stages of {A, B} x 2 k-blocks (48 KB); split
+// precision = 2 stages of {A_hi, A_lo, B_hi, B_lo} x 2 k-blocks (96 KB), whose
+// three MMA groups (hi*hi, hi*lo, lo*hi) share one load of each plane.
 template <bool SPLIT> struct Pipe {
   static constexpr int NPL = SPLIT ? 2 : 1;
-  static constexpr int ST = SPLIT ? 4 : 7;
-  static constexpr uint32_t STAGE = NPL * (A_BYTES + B_BYTES);
+  static constexpr int ST = SPLIT ? 2 : 4;
+  static constexpr uint32_t A_ST = KBX * A_BYTES, B_ST = KBX * B_BYTES;  // per plane
+  static constexpr uint32_t STAGE = NPL * (A_ST + B_ST);
 };
 constexpr uint32_t TMEM_COLS = 512, BUF_COLS = MAXM * BN;
 constexpr int XS_LD = TE + 1;
@@ -40,6 +45,7 @@ static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
 
 struct TcShape {
   int n_itile, n_etile, kb;
+  int band;  // extrinsic tile groups per L2 band (see super_tile)
   int a_plane_rows, a_mode_rows, a_row0;
   int b_plane_rows, b_mode_rows;
 };
@@ -53,7 +59,7 @@ struct TcTail {
   float wm1[NEPI], ws1[NEPI], wm2[NEPI], ws2[NEPI], wml[NEPI];
   long long warg[NEPI];
   int wnp[NEPI];
-  uint64_t full[7], empty[7], tfull[2], tempty[2], drain;
+  uint64_t full[4], empty[4], tfull[2], tempty[2], drain;
   uint32_t tmem_slot;
   int abort_flag;
 };
@@ -72,22 +78,37 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
   b = __uint_as_float(r1);
 }
 
+// Tile order: the extrinsic tiles are swept in bands of S.band cluster-groups;
+// within a band every bank tile meets every extrinsic tile of the band before
+// the next band starts.  The band's extrinsic operand stays resident in L2 while
+// the bank streams through, so the bank is read once per band instead of the
+// extrinsic operand once per bank tile.
+__device__ __forceinline__ void super_tile(int st, int n_itile, int n_etile, int band, int &it, int &et) {
+  const int per = n_itile * band;
+  const int b = st / per;
+  const int w = min(band, n_etile - b * band);
+  const int rem = st - b * per;
+  it = rem / w;
+  et = b * band + rem % w;
+}
+
 template <bool BF16, bool CONSEC, bool SPLIT>
 __global__ void __launch_bounds__(NT, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const TcShape S, const EpiParams P) {
   constexpr int ST = Pipe<SPLIT>::ST, NPL = Pipe<SPLIT>::NPL;
-  constexpr uint32_t STAGE_BYTES = Pipe<SPLIT>::STAGE;
+  constexpr uint32_t STAGE_BYTES = Pipe<SPLIT>::STAGE, A_ST = Pipe<SPLIT>::A_ST, B_ST = Pipe<SPLIT>::B_ST;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // stage s, plane p: A at sA + (s NPL + p) A_BYTES, B at sB + (s NPL + p) B_BYTES
+  // stage s, plane p: A at sA + (s NPL + p) A_ST as [KBX][128 rows][64],
+  //                   B at sB + (s NPL + p) B_ST as [KBX][64 rows][64]
   uint8_t *sA = base;
-  uint8_t *sB = base + ST * NPL * A_BYTES;
+  uint8_t *sB = base + ST * NPL * A_ST;
   TcTail &T = *reinterpret_cast<TcTail *>(base + (size_t)ST * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tiles = S.n_itile * S.n_etile;
   const int M = P.n_modes;
-
+  const int n_super = S.n_itile * S.n_etile;
+  const int nst = (S.kb + KBX - 1) / KBX;  // stages per mode (an odd last k-block is zero-filled)
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(&T.full[s], 1);
@@ -118,20 +139,21 @@ __global__ void __launch_bounds__(NT, 1)
       // ---------------- TMA producer ----------------
       uint32_t q = 0;
       bool ok = !P.test_stall;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int it = t / S.n_etile, et = t % S.n_etile;
+      for (int st = blockIdx.x; st < n_super && ok; st += gridDim.x) {
+        int it, et;
+        super_tile(st, S.n_itile, S.n_etile, S.band, it, et);
         for (int m = 0; m < M && ok; ++m) {
           const int arow = m * S.a_mode_rows + S.a_row0 + it * TI;
           const int brow = m * S.b_mode_rows + et * BN;
-          for (int kb = 0; kb < S.kb; ++kb, ++q) {
+          for (int ks = 0; ks < nst; ++ks, ++q) {
             const int s = q % ST;
             const uint32_t n = q / ST;
             if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, P.status, abortp, P.wait_ns))) break;
             mbar_expect_tx(&T.full[s], STAGE_BYTES);
 #pragma unroll
             for (int pl = 0; pl < NPL; ++pl) {
-              tma_load_2d(sA + (s * NPL + pl) * A_BYTES, &mapA, &T.full[s], kb * BK, pl * S.a_plane_rows + arow);
-              tma_load_2d(sB + (s * NPL + pl) * B_BYTES, &mapB, &T.full[s], kb * BK, pl * S.b_plane_rows + brow);
+              tma_load_3d(sA + (s * NPL + pl) * A_ST, &mapA, &T.full[s], 0, pl * S.a_plane_rows + arow, ks * KBX);
+              tma_load_3d(sB + (s * NPL + pl) * B_ST, &mapB, &T.full[s], 0, pl * S.b_plane_rows + brow, ks * KBX);
             }
           }
         }
@@ -151,27 +173,31 @@ __global__ void __launch_bounds__(NT, 1)
       constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
       uint32_t q = 0, u = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++u) {
+      for (int st = blockIdx.x; st < n_super && ok; st += gridDim.x, ++u) {
         const int b = u & 1;
         const uint32_t use = u >> 1;
         if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, P.status, abortp, P.wait_ns))) break;
         tc_fence_after();
         for (int m = 0; m < M && ok; ++m) {
           const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
-          for (int kb = 0; kb < S.kb; ++kb, ++q) {
+          for (int ks = 0; ks < nst; ++ks, ++q) {
             const int s = q % ST;
             const uint32_t n = q / ST;
             if (!(ok = mbar_wait(&T.full[s], n & 1, P.status, abortp, P.wait_ns))) break;
             tc_fence_after();
-            const uint64_t ah = sdesc_k128(sA + (s * NPL) * A_BYTES), bh = sdesc_k128(sB + (s * NPL) * B_BYTES);
-            const uint64_t al = sdesc_k128(sA + (s * NPL + NPL - 1) * A_BYTES);
-            const uint64_t bl = sdesc_k128(sB + (s * NPL + NPL - 1) * B_BYTES);
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (kb | k) ? 1u : 0u);
-              if (SPLIT) {
-                tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
-                tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+            for (int kx = 0; kx < KBX; ++kx) {
+              const uint64_t ah = sdesc_k128(sA + (s * NPL) * A_ST + kx * A_BYTES);
+              const uint64_t bh = sdesc_k128(sB + (s * NPL) * B_ST + kx * B_BYTES);
+              const uint64_t al = sdesc_k128(sA + (s * NPL + NPL - 1) * A_ST + kx * A_BYTES);
+              const uint64_t bl = sdesc_k128(sB + (s * NPL + NPL - 1) * B_ST + kx * B_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
+                if (SPLIT) {
+                  tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
+                  tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+                }
               }
             }
             tc_commit(&T.empty[s]);
@@ -197,10 +223,13 @@ __global__ void __launch_bounds__(NT, 1)
     double lwi = 0.0;
     int cur_it = -1;
     uint32_t u = 0;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++u) {
+    for (int st = blockIdx.x; st < n_super; st += gridDim.x, ++u) {
       const int b = u & 1;
       const uint32_t use = u >> 1;
-      const int it = t / S.n_etile, et = t % S.n_etile;
+      int it, et;
+      super_tile(st, S.n_itile, S.n_etile, S.band, it, et);
+      const bool etv = true;
+      const int t = it * S.n_etile + et;
       const int64_t i = (int64_t)it * TI + row;
       const bool vi = i < P.n_int;
       const int64_t e0 = (int64_t)et * TE;
@@ -301,7 +330,7 @@ __global__ void __launch_bounds__(NT, 1)
         }
       }
       named_bar_sync(1, EPT);
-      if (half == 0 && vi) {
+      if (half == 0 && vi && etv) {
         ra.merge(T.rowh[row].x, T.rowh[row].y);
         P.row_part[(int64_t)et * P.n_int + i] = make_float2(ra.m, ra.s);
       }
@@ -317,9 +346,10 @@ __global__ void __launch_bounds__(NT, 1)
           float os = __shfl_xor_sync(0xffffffffu, a.s, o);
           a.merge(om, os);
         }
-        if (qq == 0 && e0 + cc < P.n_ext) P.col_part[(int64_t)it * P.n_ext + e0 + cc] = make_float2(a.m, a.s);
+        if (qq == 0 && etv && e0 + cc < P.n_ext)
+          P.col_part[(int64_t)it * P.n_ext + e0 + cc] = make_float2(a.m, a.s);
       }
-      if (etid == 0) {
+      if (etid == 0 && etv) {
         Lse a, bb;
         a.init();
         bb.init();
@@ -368,6 +398,30 @@ int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_
   return r == CUDA_SUCCESS ? 0 : -2;
 }
 
+// 3-D view of a row-major [rows][n_kb * 64] matrix: dims {64, rows, n_kb}, box
+// {64, box_rows, box_kb} -> shared memory [box_kb][box_rows][64], 128-byte swizzle.
+int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,
+                        uint64_t row_bytes, uint32_t box_rows, uint32_t box_kb) {
+  if (!g_encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  cuuint64_t dims[3] = {64, rows, n_kb};
+  cuuint64_t strides[2] = {row_bytes, 128};
+  cuuint32_t box[3] = {64, box_rows, box_kb};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = g_encode(map, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -2;
+}
+
+int tc_kblocks_per_stage() { return KBX; }
+
 int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   TcShape S;
   S.n_itile = (int)((P.n_int + TI - 1) / TI);
@@ -378,26 +432,33 @@ int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   S.a_row0 = g.a_row0;
   S.b_plane_rows = g.b_plane_rows;
   S.b_mode_rows = g.b_mode_rows;
-  const int n_tiles = S.n_itile * S.n_etile;
-  int grid = g.n_sms < n_tiles ? g.n_sms : n_tiles;
+  const int n_super = S.n_itile * S.n_etile;
+  {
+    // extrinsic operand bytes of one tile column (all modes, planes)
+    const double tile_bytes = 2.0 * TE * g.kb_per_mode * BK * 2.0 * g.n_modes * (g.n_pass == 3 ? 2 : 1);
+    int band = (int)(g.l2_band_bytes / tile_bytes);
+    S.band = band < 1 ? 1 : (band > S.n_etile ? S.n_etile : band);
+  }
+  int grid = g.n_sms < n_super ? g.n_sms : n_super;
   if (grid < 1) grid = 1;
-  cudaError_t err;
-  auto go = [&](auto kern, size_t smem) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto go = [&](auto kern, size_t smem) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     kern<<<grid, NT, smem, st>>>(g.mapA, g.mapB, S, P);
+    return cudaGetLastError();
   };
   const bool split = g.n_pass == 3;
+  cudaError_t err;
   if (split) {
-    if (P.consec) go(tc_fused_kernel<true, true, true>, smem_bytes<true>());
-    else go(tc_fused_kernel<true, false, true>, smem_bytes<true>());
+    err = P.consec ? go(tc_fused_kernel<true, true, true>, smem_bytes<true>())
+                   : go(tc_fused_kernel<true, false, true>, smem_bytes<true>());
   } else if (g.bf16) {
-    if (P.consec) go(tc_fused_kernel<true, true, false>, smem_bytes<false>());
-    else go(tc_fused_kernel<true, false, false>, smem_bytes<false>());
+    err = P.consec ? go(tc_fused_kernel<true, true, false>, smem_bytes<false>())
+                   : go(tc_fused_kernel<true, false, false>, smem_bytes<false>());
   } else {
-    if (P.consec) go(tc_fused_kernel<false, true, false>, smem_bytes<false>());
-    else go(tc_fused_kernel<false, false, false>, smem_bytes<false>());
+    err = P.consec ? go(tc_fused_kernel<false, true, false>, smem_bytes<false>())
+                   : go(tc_fused_kernel<false, false, false>, smem_bytes<false>());
   }
-  err = cudaGetLastError();
   return (int)err;
 }
 

@@ -69,6 +69,8 @@ struct TcArgs {
   int b_plane_rows, b_mode_rows;
   bool bf16;
   int n_sms;
+  int n_modes;
+  double l2_band_bytes;  // extrinsic operand bytes kept resident per band
 };
 int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st);  // returns cudaError_t as int
 
@@ -104,5 +106,8 @@ size_t reduce_scratch_bytes();
 // Tensor-map encoding through the driver entry point.
 int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t inner, uint64_t rows,
                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows);
+int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,
+                        uint64_t row_bytes, uint32_t box_rows, uint32_t box_kb);
+int tc_kblocks_per_stage();
 
 }  // namespace dotpe
