@@ -38,6 +38,11 @@ import numpy as np
 WORKLOAD = dict(n_int=65536, n_ext=4096, n_det=3, n_modes=4, n_bins=512, snr=15.0, seed=2)
 N_PHI = 32
 CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
+# DRAM bytes (read + write) per (i,e) pair of the fused split-precision kernel,
+# from one ncu capture of a 16,384 x 2,048 launch (917.3 MB); its traffic grows
+# with I*E (the bank is re-read once per L2 band).  Valid for the kernel version
+# with two-k-block TMA boxes; None for other precisions.
+FUSED_BF16X3_DRAM_BYTES_PER_PAIR = 917.3e6 / (16384 * 2048)
 
 
 def algorithmic_flops_per_pair(B, M, D):
@@ -174,10 +179,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_name():
+def workload_name(n_int=None, n_ext=None):
     w = WORKLOAD
-    return (f"single event, I={w['n_int']} x E={w['n_ext']}, D={w['n_det']}, M={w['n_modes']}, "
-            f"B={w['n_bins']}, N_phi={N_PHI}, SNR={w['snr']:g}")
+    return (f"single event, I={n_int or w['n_int']} x E={n_ext or w['n_ext']}, D={w['n_det']}, "
+            f"M={w['n_modes']}, B={w['n_bins']}, N_phi={N_PHI}, SNR={w['snr']:g}")
 
 
 def main():
@@ -190,6 +195,8 @@ def main():
     ap.add_argument("--cut", type=float, default=CUT_DELTA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=4, help="distinct event realisations cycled")
+    ap.add_argument("--n-int", type=int, default=WORKLOAD["n_int"], help="bank rows (profiling runs)")
+    ap.add_argument("--n-ext", type=int, default=WORKLOAD["n_ext"], help="extrinsic samples (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -212,6 +219,7 @@ def main():
     import synth
 
     kw = dict(WORKLOAD)
+    kw["n_int"], kw["n_ext"] = args.n_int, args.n_ext
     kw["seed"] = WORKLOAD["seed"] + 1000 * rank
     wl = synth.make_workload(**kw, n_phi=N_PHI)
     I, E, D, M, B = (kw["n_int"], kw["n_ext"], kw["n_det"], kw["n_modes"], kw["n_bins"])
@@ -356,7 +364,7 @@ def main():
         "dtype": "bf16" if args.precision.startswith("bf16") else args.precision,
         "data": "synthetic",
         "config": {
-            "workload": workload_name(),
+            "workload": workload_name(I, E),
             "precision": args.precision,
             "passes": passes,
             "ml_cut_delta": args.cut,
@@ -377,7 +385,8 @@ def main():
             "peak": sustained,
             "unit": "TFLOP/s",
             "frac": achieved / sustained,
-            "traffic": None,
+            "traffic": (FUSED_BF16X3_DRAM_BYTES_PER_PAIR * pairs if args.precision == "bf16x3" else None),
+            "traffic_note": "bytes per launch, scaled by pairs from an ncu capture at 16,384 x 2,048",
             "kernel": "tc_fused_kernel (fused <d|h> GEMM + marginalisation)",
             "flops_per_pair": algorithmic_flops_per_pair(B, M, D),
             "peak_source": f"{peak_src} bf16_tflops_sustained",
