@@ -3,9 +3,11 @@
 
 Metric: (int x ext) ln L pairs per second for one event of the production-size
 synthetic workload (65,536 bank waveforms x 4,096 extrinsic samples, 3
-detectors, 4 modes, 512 bins, 32 phases, distance marginalisation, evidence),
-served in split precision (bf16 hi/lo, three tcgen05 passes), with |d ln Z|
-against the plain FP32 path on the same GPU reported beside it.
+detectors, 4 modes, 512 bins, 32 phases, the paper's coherent-ML cut,
+distance marginalisation, evidence), served in mixed precision (one fp16
+tcgen05 pass screens every pair; the tiles that can pass the cut are
+recomputed in split fp16 hi/lo precision), with |d ln Z| against the plain FP32
+path on the same GPU reported beside it.
 
 One step = one event through every stage of the path: FP64 data weights,
 extrinsic operand build, bank cross terms, the fused GEMM + marginalisation
@@ -38,11 +40,11 @@ import numpy as np
 WORKLOAD = dict(n_int=65536, n_ext=4096, n_det=3, n_modes=4, n_bins=512, snr=15.0, seed=2)
 N_PHI = 32
 CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
-# DRAM bytes (read + write) per (i,e) pair of the fused split-precision kernel,
-# from one ncu capture of a 16,384 x 2,048 launch (917.3 MB); its traffic grows
-# with I*E (the bank is re-read once per L2 band).  Valid for the kernel version
-# with two-k-block TMA boxes; None for other precisions.
-FUSED_BF16X3_DRAM_BYTES_PER_PAIR = 917.3e6 / (16384 * 2048)
+# DRAM bytes (read + write) per (i,e) pair of the dominant launch, from one ncu
+# capture of a 16,384 x 2,048 event (the traffic grows with I*E: the bank is
+# re-read once per L2 band), keyed by precision; absent = not measured for the
+# current kernel version.
+DRAM_BYTES_PER_PAIR = {}
 
 
 def algorithmic_flops_per_pair(B, M, D):
@@ -191,7 +193,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--precision", default="mixed")
     ap.add_argument("--cut", type=float, default=CUT_DELTA)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=4, help="distinct event realisations cycled")
@@ -335,11 +337,21 @@ def main():
     e2e_value = world * pairs * args.steps / (e2e_ms * 1e-3)
     fused_ms = statistics.mean(s["fused_ms"] for s in stats)
     prep_ms = statistics.mean(s["prep_ms"] for s in stats)
+    mixed = args.precision == "mixed"
+    n_tiles = -(-I // 128) * -(-E // 32)
+    refine_ms = statistics.mean(s["refine_ms"] for s in stats) if mixed else 0.0
+    refined = statistics.mean(ev["n_refined_tiles"] for ev in evs) if mixed else 0.0
+    # the dominant launch: the screening pass (mixed) or the one fused kernel
+    dom_ms = fused_ms - refine_ms
     flops_alg = algorithmic_flops_per_pair(B, M, D) * pairs
-    passes = 3 if args.precision == "bf16x3" else 1
-    flops_issued = (8 * B * M * passes + D * (2 * M + 4 * M * (M - 1))) * pairs
+    passes = 3 if args.precision in ("bf16x3", "fp16x3") else 1
+    hh_flops = D * (2 * M + 4 * M * (M - 1))
+    flops_issued = (8 * B * M * passes + hh_flops) * pairs
+    if mixed:
+        flops_issued += (8 * B * M * 3 + hh_flops) * pairs * refined / n_tiles
     burst, sustained, hbm, peak_src = load_peaks()
-    achieved = flops_alg / (fused_ms * 1e-3) / 1e12
+    achieved = flops_alg / (dom_ms * 1e-3) / 1e12
+    launches_per_event = 5 + 1 + (4 if mixed else 1) + 5  # prep, cross terms, fused, reduction
     dlnz = max(abs(evs[k]["ln_z"] - ref_fp32[k % len(events)][0]["ln_z"]) for k in range(len(evs)))
     if rank != 0:
         if dist is not None:
@@ -361,7 +373,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16" if args.precision.startswith("bf16") else args.precision,
+        "dtype": "bf16" if args.precision.startswith("bf16") else ("fp16" if args.precision != "fp32" else "fp32"),
         "data": "synthetic",
         "config": {
             "workload": workload_name(I, E),
@@ -377,6 +389,8 @@ def main():
             "latency_ms_p99": lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "prep_ms": prep_ms,
             "fused_ms": fused_ms,
+            "refine_ms": refine_ms if mixed else None,
+            "refined_tile_fraction": refined / n_tiles if mixed else None,
             "issued_tflops": flops_issued / (fused_ms * 1e-3) / 1e12,
         },
         "roofline": {
@@ -385,15 +399,18 @@ def main():
             "peak": sustained,
             "unit": "TFLOP/s",
             "frac": achieved / sustained,
-            "traffic": (FUSED_BF16X3_DRAM_BYTES_PER_PAIR * pairs if args.precision == "bf16x3" else None),
+            "traffic": (DRAM_BYTES_PER_PAIR[args.precision] * pairs if args.precision in DRAM_BYTES_PER_PAIR
+                        else None),
             "traffic_note": "bytes per launch, scaled by pairs from an ncu capture at 16,384 x 2,048",
-            "kernel": "tc_fused_kernel (fused <d|h> GEMM + marginalisation)",
+            "kernel": ("tc_fused_kernel screening pass (fp16 <d|h> GEMM + <h|h> + ML over the phase grid)"
+                       if mixed else "tc_fused_kernel (fused <d|h> GEMM + marginalisation)"),
+            "kernel_ms": dom_ms,
             "flops_per_pair": algorithmic_flops_per_pair(B, M, D),
             "peak_source": f"{peak_src} bf16_tflops_sustained",
         },
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": d2h_bytes, "wall_s": e2e_wall},
-        "gpu_launches": 9 * args.steps,
+        "gpu_launches": launches_per_event * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -48,8 +48,26 @@ extern "C" {
  *   FP32   : SIMT FFMA path (the plain baseline)
  *   BF16   : one tcgen05 pass, bf16 operands
  *   FP16   : one tcgen05 pass, fp16 operands
- *   BF16X3 : split precision x = hi + lo (both bf16); hi*hi + hi*lo + lo*hi */
-enum { DOTPE_PREC_FP32 = 0, DOTPE_PREC_BF16 = 1, DOTPE_PREC_FP16 = 2, DOTPE_PREC_BF16X3 = 3 };
+ *   BF16X3 : split precision x = hi + lo (both bf16); hi*hi + hi*lo + lo*hi
+ *   FP16X3 : the same split with fp16 hi and lo (operands scaled by powers of
+ *            two to |x| <= 1; lo keeps ~2^-24 absolute accuracy)
+ *   MIXED  : every pair screened with one fp16 pass (best ln L^ML only), then
+ *            the tiles of 128 x 32 pairs that can reach the coherent-ML cut
+ *            (Eq. coherent_ML_selection) recomputed in FP16X3 with the full
+ *            marginalisation.  The screening margin is 2u (ml + sqrt(2 ml)
+ *            sqrt<d|d>), u = 2^-11, around both the tile's and the global best
+ *            ln L^ML; the cut is applied at (screened max - margin) - cut_delta.
+ *            With the cut off, tiles more than 30 + 2 margins below the maximum
+ *            keep their single-pass fp16 values (each of their pairs weighs
+ *            < e^-30 of the best one). */
+enum {
+  DOTPE_PREC_FP32 = 0,
+  DOTPE_PREC_BF16 = 1,
+  DOTPE_PREC_FP16 = 2,
+  DOTPE_PREC_BF16X3 = 3,
+  DOTPE_PREC_FP16X3 = 4,
+  DOTPE_PREC_MIXED = 5
+};
 
 /* bank waveform element type */
 enum { DOTPE_C128 = 0, DOTPE_C64 = 1 };
@@ -136,7 +154,8 @@ typedef struct dotpe_event_stats {
   int64_t footprint_bytes;                    /* device bytes held while running */
   float device_ms;                            /* GPU time from first to last kernel */
   float prep_ms;                              /* data weights, extrinsic operand, cross terms */
-  float fused_ms;                             /* fused GEMM + marginalisation kernel */
+  float fused_ms;                             /* fused GEMM + marginalisation kernel(s) */
+  float refine_ms;                            /* MIXED: selection + refinement part of fused_ms; else -1 */
   int precision;
   int state;
 } dotpe_event_stats;
@@ -151,7 +170,7 @@ typedef struct dotpe_evidence_out {
   int64_t n_pairs;
   double lnl_ml_threshold;  /* the cut applied (running maximum - cut_delta), -inf when off */
   int32_t device_status;    /* 0, or a DOTPE_E_* raised inside a kernel */
-  int32_t reserved;
+  int32_t n_refined_tiles;  /* MIXED: tiles recomputed in split precision; else -1 */
 } dotpe_evidence_out;
 
 /* ---- context ----------------------------------------------------------- */

@@ -28,7 +28,8 @@ DOTPE_E_NOT_FOUND = -7
 DOTPE_E_UNSUPPORTED = -8
 
 DOTPE_PREC_FP32, DOTPE_PREC_BF16, DOTPE_PREC_FP16, DOTPE_PREC_BF16X3 = 0, 1, 2, 3
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
+DOTPE_PREC_FP16X3, DOTPE_PREC_MIXED = 4, 5
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4, "mixed": 5}
 DOTPE_C128, DOTPE_C64 = 0, 1
 DOTPE_FLAG_STORE_LNL = 0x1
 DOTPE_FLAG_GEMM_ONLY = 0x2
@@ -78,7 +79,7 @@ class dotpe_event_stats(ctypes.Structure):
     _fields_ = [("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
                 ("t_done_ns", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("footprint_bytes", ctypes.c_int64), ("device_ms", ctypes.c_float),
-                ("prep_ms", ctypes.c_float), ("fused_ms", ctypes.c_float),
+                ("prep_ms", ctypes.c_float), ("fused_ms", ctypes.c_float), ("refine_ms", ctypes.c_float),
                 ("precision", ctypes.c_int), ("state", ctypes.c_int)]
 
 
@@ -89,7 +90,7 @@ class dotpe_evidence_out(ctypes.Structure):
                 ("arg_e", ctypes.c_int64), ("arg_o", ctypes.c_int64),
                 ("n_marginalised", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("lnl_ml_threshold", ctypes.c_double), ("device_status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("n_refined_tiles", ctypes.c_int32)]
 
 
 _lib = None

@@ -44,6 +44,10 @@ struct EpiParams {
   const double *lw_ext;     // [n_ext], may be null
   const float4 *dm_table;   // distance-marginal Hermite table
   float *ml_running;        // running max of ln L^ML (>= 0)
+  int track_max;            // raise *ml_running with each tile's best ln L^ML
+  int screen_ml;            // screening pass: max_o ln L^ML only (no distance marginal)
+  float margin_k;           // screening error scale kappa*u (0: exact threshold)
+  const float *sqrt_dd;     // sqrt<d|d> of the event (screening margin)
   // outputs
   float4 *tile_part;        // [n_itile * n_etile] (m1, s1, m2, s2) of x = ln(w_i w_e sum_o Lbar)
   float2 *row_part;         // [n_etile][n_int]
@@ -58,6 +62,28 @@ struct EpiParams {
   int test_stall;           // producer withholds its first stage (failure-path test)
   unsigned long long wait_ns;  // bound of every mbarrier wait
 };
+
+// Error allowance of a single-pass (one rounding of each operand, unit roundoff u)
+// ln L^ML of size ml: the <d|h> components carry a relative error ~u of
+// sum_b |h||G| <~ sqrt<h|h> sqrt<d|d>, so ln L^ML = x^2/2 (x = dh / sqrt hh)
+// moves by about u (ml + sqrt(2 ml) sqrt<d|d>); margin_k = kappa*u scales it.
+__host__ __device__ __forceinline__ float screen_margin(float ml, float margin_k, float sqrt_dd) {
+  ml = ml > 0.f ? ml : 0.f;
+  return margin_k * (ml + sqrtf(2.f * ml) * sqrt_dd);
+}
+
+// Tile order: the extrinsic tiles are swept in bands of `band` tiles; within a
+// band every bank tile meets every extrinsic tile of the band before the next
+// band starts, so the band's extrinsic operand stays resident in L2 while the
+// bank streams through once per band.
+__host__ __device__ __forceinline__ void super_tile(int st, int n_itile, int n_etile, int band, int &it, int &et) {
+  const int per = n_itile * band;
+  const int b = st / per;
+  const int w = min(band, n_etile - b * band);
+  const int rem = st - b * per;
+  it = rem / w;
+  et = b * band + rem % w;
+}
 
 // ---------------------------------------------------------------------------
 // PTX helpers (mbarrier, TMA, tcgen05)

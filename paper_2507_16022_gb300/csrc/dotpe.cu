@@ -74,7 +74,7 @@ struct Bank {
   double *f = nullptr, *w = nullptr, *lw = nullptr;  // device
   float *master = nullptr;                           // [M][I][Kpad]
   __nv_bfloat16 *bf = nullptr;                       // [2][M][I][Kpad] hi, lo
-  __half *hf = nullptr;                              // [M][I][Kpad]
+  __half *hf = nullptr;                              // [2][M][I][Kpad] hi, lo
   float a_scale = 1.f;
   void *block = nullptr;
   size_t bytes = 0;
@@ -96,7 +96,8 @@ struct Event {
   double2 *data = nullptr, *R = nullptr;
   void *in_stage = nullptr;  // pinned host staging of host inputs
   size_t stage_bytes = 0;
-  cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+  cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr, ev_k0 = nullptr, ev_k1 = nullptr,
+              ev_ks = nullptr;
   // results kept until release
   void *keep_block = nullptr;
   size_t keep_bytes = 0;
@@ -108,7 +109,8 @@ struct Event {
   int slot = -1;
   int64_t t_submit = 0, t_admit = 0;
   volatile int64_t t_done = 0;
-  float device_ms = -1.f, prep_ms = -1.f, fused_ms = -1.f;
+  float device_ms = -1.f, prep_ms = -1.f, fused_ms = -1.f, refine_ms = -1.f;
+  int refined = -1;  // tiles refined (mixed precision)
 };
 
 }  // namespace dotpe
@@ -160,10 +162,19 @@ static void CUDART_CB mark_done(void *p) {
 // footprint of one event's device scratch (freed when the event completes)
 // ---------------------------------------------------------------------------
 struct ScratchLayout {
-  size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, gpack, mx, tile_part, tile_ml, tile_arg,
-      tile_npass, row_part, col_part, ml_running, status, red, total;
+  size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, sqrt_dd, gpack, mx, tile_part, tile_ml, tile_arg,
+      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, sel_counts, status, red, total;
   int n_itile, n_etile, pack_kind, pack_planes, TI, TE;
 };
+
+static bool prec_split(int p) { return p == DOTPE_PREC_BF16X3 || p == DOTPE_PREC_FP16X3 || p == DOTPE_PREC_MIXED; }
+static bool prec_bf16(int p) { return p == DOTPE_PREC_BF16 || p == DOTPE_PREC_BF16X3; }
+
+// Screening error scale kappa*u of a single fp16 pass (u = 2^-11, kappa = 2).
+static const float MIXED_MARGIN_K = 2.0f * 0.00048828125f;
+// With the cut off, tiles whose screened best ln L^ML lies this far below the
+// maximum keep their screened values (their share of Z is below e^-30 each).
+static const float MIXED_FAR_WINDOW = 30.0f;
 
 static ScratchLayout scratch_layout(const Event &e) {
   ScratchLayout L{};
@@ -174,8 +185,8 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.TE = simt ? SIMT_TE : TC_TE;
   L.n_itile = (int)((NI + L.TI - 1) / L.TI);
   L.n_etile = (int)((E + L.TE - 1) / L.TE);
-  L.pack_kind = simt ? 0 : (e.prec == DOTPE_PREC_FP16 ? 2 : 1);
-  L.pack_planes = (e.prec == DOTPE_PREC_BF16X3) ? 2 : 1;
+  L.pack_kind = simt ? 0 : (prec_bf16(e.prec) ? 1 : 2);
+  L.pack_planes = prec_split(e.prec) ? 2 : 1;
   size_t elem = (L.pack_kind == 0) ? 4 : 2;
   const int64_t T = (int64_t)L.n_itile * L.n_etile;
   Carver c;
@@ -190,6 +201,7 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.G32 = c.take<float2>(M * E * B);
   L.gmax = c.take<float>(1);
   L.gscale = c.take<float>(1);
+  L.sqrt_dd = c.take<float>(1);
   L.gpack = c.take<uint8_t>((size_t)L.pack_planes * M * 2 * E * Kp * elem);
   L.mx = c.take<float>(NI * D * REC);
   L.tile_part = c.take<float4>(T);
@@ -199,6 +211,11 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.row_part = c.take<float2>((size_t)L.n_etile * NI);
   L.col_part = c.take<float2>((size_t)L.n_itile * E);
   L.ml_running = c.take<float>(1);
+  const bool mixed = (e.prec == DOTPE_PREC_MIXED);
+  L.ml_refine = c.take<float>(1);
+  L.list = c.take<int>(mixed ? T : 0);
+  L.n_list = c.take<int>(1);
+  L.sel_counts = c.take<int>(mixed ? select_count_blocks((int)T) : 0);
   L.status = c.take<int>(1);
   L.red = c.take<uint8_t>(reduce_scratch_bytes());
   L.total = c.off;
@@ -260,6 +277,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   pa.pack_kind = L.pack_kind;
   pa.pack_planes = L.pack_planes;
   pa.gscale = (float *)(scr + L.gscale);
+  pa.sqrt_dd = (float *)(scr + L.sqrt_dd);
   pa.status = status;
   launch_prep(pa, st);
   float *mx = (float *)(scr + L.mx);
@@ -292,6 +310,8 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   P.lw_ext = e.has_lwe ? e.lwe : nullptr;
   P.dm_table = ctx->dm_table;
   P.ml_running = (float *)(scr + L.ml_running);
+  P.track_max = P.cut_delta > 0.f ? 1 : 0;
+  P.sqrt_dd = pa.sqrt_dd;
   P.tile_part = (float4 *)(scr + L.tile_part);
   P.row_part = (float2 *)(scr + L.row_part);
   P.col_part = (float2 *)(scr + L.col_part);
@@ -321,11 +341,11 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
     P.g_scale = pa.gscale;
     TcArgs g;
     memset(&g, 0, sizeof(g));
-    const bool bf = (e.prec != DOTPE_PREC_FP16);
+    const bool bf = prec_bf16(e.prec);
     g.bf16 = bf;
     g.kb_per_mode = b.Kpad / 64;
     g.n_sms = ctx->n_sms;
-    const int64_t a_rows = (bf ? 2 : 1) * (int64_t)b.M * b.I;
+    const int64_t a_rows = 2 * (int64_t)b.M * b.I;
     const int64_t b_rows = (int64_t)L.pack_planes * b.M * 2 * e.NE;
     if (a_rows >= (1ll << 31) || b_rows >= (1ll << 31))
       return fail(DOTPE_E_UNSUPPORTED, "operand too large for 32-bit TMA coordinates");
@@ -342,13 +362,41 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
     g.a_row0 = (int)e.i0;
     g.b_plane_rows = b.M * 2 * (int)e.NE;
     g.b_mode_rows = 2 * (int)e.NE;
-    if (e.prec == DOTPE_PREC_BF16X3) {
-      g.n_pass = 3;
-      g.pa[0] = 0; g.pb[0] = 0;  // hi * hi
-      g.pa[1] = 0; g.pb[1] = 1;  // hi * lo
-      g.pa[2] = 1; g.pb[2] = 0;  // lo * hi
-    } else {
+    g.n_pass = prec_split(e.prec) ? 3 : 1;  // hi*hi (+ hi*lo + lo*hi)
+    if (e.prec == DOTPE_PREC_MIXED) {
+      // screening pass: one fp16 product for every pair, best ln L^ML per tile
+      // (with the cut off, the full single-pass epilogue)
+      EpiParams Ps = P;
+      Ps.track_max = 1;
+      Ps.screen_ml = (P.cut_delta > 0.f) ? 1 : 0;
+      Ps.margin_k = MIXED_MARGIN_K;
       g.n_pass = 1;
+      int r = launch_tc(g, Ps, st);
+      if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+      CUDA_OR_FAIL(cudaEventRecord(e.ev_ks, st));
+      // the tiles that can reach the cut (or, with the cut off, within the far window)
+      SelectArgs sa;
+      sa.tile_ml = P.tile_ml;
+      sa.n_itile = L.n_itile;
+      sa.n_etile = L.n_etile;
+      g.n_pass = 3;
+      sa.band = tc_band(g, L.n_etile);
+      sa.ml_screen = P.ml_running;
+      sa.sqrt_dd = pa.sqrt_dd;
+      sa.window = (P.cut_delta > 0.f) ? P.cut_delta : MIXED_FAR_WINDOW;
+      sa.margin_k = MIXED_MARGIN_K;
+      sa.ml_refine = (float *)(scr + L.ml_refine);
+      sa.list = (int *)(scr + L.list);
+      sa.n_list = (int *)(scr + L.n_list);
+      sa.counts = (int *)(scr + L.sel_counts);
+      launch_select(sa, st);
+      CUDA_OR_FAIL(cudaGetLastError());
+      // refinement: split precision on the selected tiles, threshold frozen at
+      // (screened maximum - margin) - cut_delta, a lower bound of the exact cut
+      P.ml_running = sa.ml_refine;
+      P.track_max = 0;
+      g.list = sa.list;
+      g.n_list = sa.n_list;
     }
     int r = launch_tc(g, P, st);
     if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
@@ -375,6 +423,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   ra.status = status;
   ra.scratch = scr + L.red;
   ra.out = e.d_out;
+  ra.n_refined = (e.prec == DOTPE_PREC_MIXED) ? (const int *)(scr + L.n_list) : nullptr;
   launch_reduce(ra, st);
   CUDA_OR_FAIL(cudaGetLastError());
   CUDA_OR_FAIL(cudaMemcpyAsync(e.h_out, e.d_out, sizeof(ReduceOut), cudaMemcpyDeviceToHost, st));
@@ -407,6 +456,7 @@ static void progress(dotpe_ctx *ctx) {
         if (cudaEventElapsedTime(&ms, e.ev_start, e.ev_end) == cudaSuccess) e.device_ms = ms;
         if (cudaEventElapsedTime(&ms, e.ev_start, e.ev_k0) == cudaSuccess) e.prep_ms = ms;
         if (cudaEventElapsedTime(&ms, e.ev_k0, e.ev_k1) == cudaSuccess) e.fused_ms = ms;
+        if (e.prec == DOTPE_PREC_MIXED && cudaEventElapsedTime(&ms, e.ev_ks, e.ev_k1) == cudaSuccess) e.refine_ms = ms;
         if (e.t_done == 0) e.t_done = now_ns();
         ctx->slot_busy[e.slot] = 0;
         ctx->used -= e.scratch_bytes + e.in_bytes;
@@ -464,6 +514,7 @@ static void free_event(dotpe_ctx *ctx, Event *e) {
   if (e->ev_end) cudaEventDestroy(e->ev_end);
   if (e->ev_k0) cudaEventDestroy(e->ev_k0);
   if (e->ev_k1) cudaEventDestroy(e->ev_k1);
+  if (e->ev_ks) cudaEventDestroy(e->ev_ks);
   size_t give = e->keep_bytes + e->scratch_bytes + e->in_bytes;
   if (e->state == DOTPE_STATE_QUEUED) give = e->in_bytes;
   ctx->used = (ctx->used >= give) ? ctx->used - give : 0;
@@ -634,7 +685,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   const size_t nel = (size_t)b->M * b->I * b->Kpad;
   Carver c;
   size_t o_f = c.take<double>(b->B), o_w = c.take<double>(b->B), o_lw = c.take<double>(b->I);
-  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(nel);
+  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(2 * nel);
   size_t o_scal = c.take<float>(4);
   b->bytes = c.off;
   if (ctx->used + b->bytes > ctx->budget) {
@@ -739,7 +790,7 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   if (d->n_phi < 1 || d->n_phi > MAXPHI) return fail(DOTPE_E_INVALID, "n_phi=%d not in 1..%d", d->n_phi, MAXPHI);
   if (!(d->u_min > 0.0) || !std::isfinite(d->u_min)) return fail(DOTPE_E_INVALID, "u_min must be > 0");
   if (!d->psd || !d->data || !d->t || !d->R) return fail(DOTPE_E_INVALID, "null input array");
-  if (d->precision < DOTPE_PREC_FP32 || d->precision > DOTPE_PREC_BF16X3)
+  if (d->precision < DOTPE_PREC_FP32 || d->precision > DOTPE_PREC_MIXED)
     return fail(DOTPE_E_INVALID, "precision %d", d->precision);
   const int64_t NI = d->i1 - d->i0, NE = d->n_ext;
   if (d->precision != DOTPE_PREC_FP32 && (2 * (int64_t)b->M * 2 * NE >= (1ll << 31)))
@@ -827,6 +878,7 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   cudaEventCreate(&e->ev_end);
   cudaEventCreate(&e->ev_k0);
   cudaEventCreate(&e->ev_k1);
+  cudaEventCreate(&e->ev_ks);
   cudaEventRecord(e->ev_inputs, ist);
   if (cudaHostAlloc((void **)&e->h_out, sizeof(ReduceOut), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
@@ -855,6 +907,7 @@ static void fill_stats(const Event &e, dotpe_event_stats *s) {
   s->device_ms = e.device_ms;
   s->prep_ms = e.prep_ms;
   s->fused_ms = e.fused_ms;
+  s->refine_ms = e.refine_ms;
   s->precision = e.prec;
   s->state = e.state;
 }
@@ -940,6 +993,7 @@ int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out) {
   out->n_pairs = e.NI * e.NE;
   out->lnl_ml_threshold = r.threshold;
   out->device_status = r.status;
+  out->n_refined_tiles = r.n_refined;
   if (r.status == DEV_E_NONFINITE) return fail(DOTPE_E_INVALID, "non-finite or non-positive event input");
   if (r.status == DEV_E_TIMEOUT) return fail(DOTPE_E_TIMEOUT, "device wait timed out");
   if (r.status != 0) return fail(DOTPE_E_DEVICE, "device status %d", r.status);

@@ -147,6 +147,56 @@ __device__ __forceinline__ PairRes pair_eval(const float Zr[MAXM], const float Z
   return R;
 }
 
+// Screening evaluation (no distance marginal): max_o ln L^ML_o and its phase.
+// A pair whose upper bound (as in pair_eval) is below thr returns ml = -1: it
+// cannot reach the cut.
+__device__ __forceinline__ float pair_ml(const float Zr[MAXM], const float Zi[MAXM], float C0, const float Cr[3],
+                                         const float Ci[3], float thr, bool allow_skip, const EpiParams &P,
+                                         const float2 *__restrict__ ph, int &argo) {
+  argo = 0;
+  if (allow_skip && thr > 0.f) {
+    float a = 0.f, hmin = C0;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) a += sqrtf(Zr[m] * Zr[m] + Zi[m] * Zi[m]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) hmin -= 2.f * sqrtf(Cr[k] * Cr[k] + Ci[k] * Ci[k]);
+    if (hmin > 0.f && a * a < 2.f * hmin * thr) return -1.f;
+  }
+  const float2 *phm = ph;
+  const float2 *phd = ph + MAXM * MAXPHI;
+  float best = -1.f;
+#pragma unroll 4
+  for (int o = 0; o < P.n_phi; ++o) {
+    float dh = 0.f;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      float2 cs = phm[m * MAXPHI + o];
+      dh = fmaf(Zr[m], cs.x, fmaf(-Zi[m], cs.y, dh));
+    }
+    float hs = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float2 cs = phd[k * MAXPHI + o];
+      hs = fmaf(Cr[k], cs.x, fmaf(-Ci[k], cs.y, hs));
+    }
+    float hh = fmaf(2.f, hs, C0);
+    float ml = (dh > 0.f && hh > 0.f) ? __fdividef(0.5f * dh * dh, hh) : 0.f;
+    if (ml > best) { best = ml; argo = o; }
+  }
+  return best;
+}
+
+// Cut threshold of a tile (Eq. coherent_ML_selection): running maximum - cut_delta,
+// lowered by twice the screening margin in a screening pass (so that no pair the
+// exact product would keep is skipped); -inf when the cut is off.
+__device__ __forceinline__ float tile_threshold(const EpiParams &P) {
+  if (!(P.cut_delta > 0.f)) return -INFINITY;
+  const float run = *(volatile float *)P.ml_running;
+  float thr = run - P.cut_delta;
+  if (P.margin_k > 0.f) thr -= 2.f * screen_margin(run, P.margin_k, *P.sqrt_dd);
+  return thr;
+}
+
 // Online log-sum-exp accumulator.
 struct Lse {
   float m, s;

@@ -185,8 +185,90 @@ __global__ void reduce_finish_kernel(ReduceArgs a, int nb, const float *__restri
   o.n_marg = np;
   o.threshold = (a.cut_delta > 0.f) ? (double)(*a.ml_running) - (double)a.cut_delta : -INFINITY;
   o.status = *a.status;
-  o.pad = 0;
+  o.n_refined = a.n_refined ? *a.n_refined : -1;
   *a.out = o;
+}
+
+// ---------------------------------------------------------------------------
+// Refinement selection (after a screening pass).  Tile t is refined when its
+// screened best ln L^ML reaches max - window - 2 margin(max): the exact value of
+// any pair differs from its screened one by at most one margin, and so does the
+// exact maximum.  Two kernels keep the list in banded tile order: per-block
+// counts, then each block writes its tiles at the prefix of the earlier counts.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int SB = 1024;  // tiles per selection block
+}
+
+__device__ __forceinline__ bool select_tile(const SelectArgs &a, int w, float thr, int &t) {
+  const int n = a.n_itile * a.n_etile;
+  if (w >= n) return false;
+  int it, et;
+  super_tile(w, a.n_itile, a.n_etile, a.band, it, et);
+  t = it * a.n_etile + et;
+  return a.tile_ml[t] >= thr;
+}
+
+__device__ __forceinline__ float select_threshold(const SelectArgs &a) {
+  const float mx = *a.ml_screen;
+  return mx - a.window - 2.f * screen_margin(mx, a.margin_k, *a.sqrt_dd);
+}
+
+__global__ void __launch_bounds__(SB) select_count_kernel(SelectArgs a) {
+  int t;
+  const bool f = select_tile(a, blockIdx.x * SB + threadIdx.x, select_threshold(a), t);
+  const int c = __syncthreads_count(f);
+  if (threadIdx.x == 0) a.counts[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(SB) select_write_kernel(SelectArgs a) {
+  __shared__ int wsum[SB / 32];
+  __shared__ int base_s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // prefix of the earlier blocks' counts (and, in block 0, the total)
+  {
+    const int upto = (blockIdx.x == 0) ? (int)gridDim.x : (int)blockIdx.x;
+    int v = 0;
+    for (int k = tid; k < upto; k += SB) v += a.counts[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[wid] = v;
+    __syncthreads();
+    if (tid == 0) {
+      int s = 0;
+      for (int k = 0; k < SB / 32; ++k) s += wsum[k];
+      base_s = (blockIdx.x == 0) ? 0 : s;
+      if (blockIdx.x == 0) {
+        *a.n_list = s;
+        const float mx = *a.ml_screen;
+        *a.ml_refine = fmaxf(mx - screen_margin(mx, a.margin_k, *a.sqrt_dd), 0.f);
+      }
+    }
+    __syncthreads();
+  }
+  int t = 0;
+  const bool f = select_tile(a, blockIdx.x * SB + tid, select_threshold(a), t);
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) wsum[wid] = __popc(bal);
+  __syncthreads();
+  if (tid == 0) {
+    int s = 0;
+    for (int k = 0; k < SB / 32; ++k) {
+      const int c = wsum[k];
+      wsum[k] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+  if (f) a.list[base_s + wsum[wid] + __popc(bal & ((1u << lane) - 1u))] = t;
+}
+
+int select_count_blocks(int n_tiles) { return (n_tiles + SB - 1) / SB; }
+
+void launch_select(const SelectArgs &a, cudaStream_t st) {
+  const int nb = select_count_blocks(a.n_itile * a.n_etile);
+  if (nb < 1) return;
+  select_count_kernel<<<nb, SB, 0, st>>>(a);
+  select_write_kernel<<<nb, SB, 0, st>>>(a);
 }
 
 size_t reduce_scratch_bytes() {

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT) simt_fused_kernel(SimtArgs g, EpiParams P)
   }
   __syncthreads();
 
-  const float thr = (P.cut_delta > 0.f) ? (*(volatile float *)P.ml_running - P.cut_delta) : -INFINITY;
+  const float thr = tile_threshold(P);
   const bool store = (P.lnl_tile != nullptr);
   const float zs = P.z_scale / (P.g_scale ? *P.g_scale : 1.f);
   // epilogue: 4 rows x 2 extrinsic samples per thread
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(NT) simt_fused_kernel(SimtArgs g, EpiParams P)
       P.tile_ml[tile] = best;
       P.tile_arg[tile] = barg;
       P.tile_npass[tile] = np;
-      if (best > 0.f && P.cut_delta > 0.f) atomic_max_nonneg(P.ml_running, best);
+      if (best > 0.f && P.track_max) atomic_max_nonneg(P.ml_running, best);
     }
   }
 }

@@ -45,9 +45,11 @@ static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
 
 struct TcShape {
   int n_itile, n_etile, kb;
-  int band;  // extrinsic tile groups per L2 band (see super_tile)
+  int band;  // extrinsic tiles per L2 band (see super_tile)
   int a_plane_rows, a_mode_rows, a_row0;
   int b_plane_rows, b_mode_rows;
+  const int *list;    // optional tile list (device), else all tiles in banded order
+  const int *n_list;  // its length (device)
 };
 
 struct TcTail {
@@ -78,18 +80,16 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
   b = __uint_as_float(r1);
 }
 
-// Tile order: the extrinsic tiles are swept in bands of S.band cluster-groups;
-// within a band every bank tile meets every extrinsic tile of the band before
-// the next band starts.  The band's extrinsic operand stays resident in L2 while
-// the bank streams through, so the bank is read once per band instead of the
-// extrinsic operand once per bank tile.
-__device__ __forceinline__ void super_tile(int st, int n_itile, int n_etile, int band, int &it, int &et) {
-  const int per = n_itile * band;
-  const int b = st / per;
-  const int w = min(band, n_etile - b * band);
-  const int rem = st - b * per;
-  it = rem / w;
-  et = b * band + rem % w;
+// Work item w -> tile (it, et): the banded order of super_tile, or entry w of a
+// tile list (linear tile indices it * n_etile + et) written by an earlier kernel.
+__device__ __forceinline__ void work_tile(const TcShape &S, int w, int &it, int &et) {
+  if (S.list) {
+    const int t = S.list[w];
+    it = t / S.n_etile;
+    et = t - it * S.n_etile;
+  } else {
+    super_tile(w, S.n_itile, S.n_etile, S.band, it, et);
+  }
 }
 
 template <bool BF16, bool CONSEC, bool SPLIT>
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NT, 1)
   TcTail &T = *reinterpret_cast<TcTail *>(base + (size_t)ST * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = P.n_modes;
-  const int n_super = S.n_itile * S.n_etile;
+  const int n_work = S.list ? *S.n_list : S.n_itile * S.n_etile;
   const int nst = (S.kb + KBX - 1) / KBX;  // stages per mode (an odd last k-block is zero-filled)
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(NT, 1)
       // ---------------- TMA producer ----------------
       uint32_t q = 0;
       bool ok = !P.test_stall;
-      for (int st = blockIdx.x; st < n_super && ok; st += gridDim.x) {
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
         int it, et;
-        super_tile(st, S.n_itile, S.n_etile, S.band, it, et);
+        work_tile(S, w, it, et);
         for (int m = 0; m < M && ok; ++m) {
           const int arow = m * S.a_mode_rows + S.a_row0 + it * TI;
           const int brow = m * S.b_mode_rows + et * BN;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(NT, 1)
       constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
       uint32_t q = 0, u = 0;
       bool ok = true;
-      for (int st = blockIdx.x; st < n_super && ok; st += gridDim.x, ++u) {
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++u) {
         const int b = u & 1;
         const uint32_t use = u >> 1;
         if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, P.status, abortp, P.wait_ns))) break;
@@ -223,11 +223,11 @@ __global__ void __launch_bounds__(NT, 1)
     double lwi = 0.0;
     int cur_it = -1;
     uint32_t u = 0;
-    for (int st = blockIdx.x; st < n_super; st += gridDim.x, ++u) {
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++u) {
       const int b = u & 1;
       const uint32_t use = u >> 1;
       int it, et;
-      super_tile(st, S.n_itile, S.n_etile, S.band, it, et);
+      work_tile(S, w, it, et);
       const bool etv = true;
       const int t = it * S.n_etile + et;
       const int64_t i = (int64_t)it * TI + row;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       for (int k = etid; k < TE; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
       named_bar_sync(1, EPT);
-      const float thr = (P.cut_delta > 0.f) ? (*(volatile float *)P.ml_running - P.cut_delta) : -INFINITY;
+      const float thr = tile_threshold(P);
       if (!mbar_wait(&T.tfull[b], use & 1, P.status, abortp, P.wait_ns)) break;
       tc_fence_after();
 
@@ -294,6 +294,19 @@ __global__ void __launch_bounds__(NT, 1)
             for (int m = 0; m < MAXM; ++m) sx += Zr[m] + Zi[m];
             x = sx;
             x2 = sx;
+          } else if (P.screen_ml) {
+            float C0, Cr[3], Ci[3];
+            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            int argo;
+            const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph, argo);
+            if (ml > best) {
+              best = ml;
+              barg = (i * P.n_ext + e) * (long long)P.n_phi + argo;
+            }
+            if (store) {
+              P.lnl_tile[i * P.n_ext + e] = -INFINITY;
+              P.ml_tile[i * P.n_ext + e] = ml;
+            }
           } else {
             float C0, Cr[3], Ci[3];
             hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
@@ -366,7 +379,7 @@ __global__ void __launch_bounds__(NT, 1)
         P.tile_ml[t] = bv;
         P.tile_arg[t] = bi;
         P.tile_npass[t] = n;
-        if (bv > 0.f && P.cut_delta > 0.f) atomic_max_nonneg(P.ml_running, bv);
+        if (bv > 0.f && P.track_max) atomic_max_nonneg(P.ml_running, bv);
       }
       named_bar_sync(1, EPT);
     }
@@ -422,6 +435,13 @@ int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, ui
 
 int tc_kblocks_per_stage() { return KBX; }
 
+int tc_band(const TcArgs &g, int n_etile) {
+  // extrinsic operand bytes of one tile column (all modes, planes)
+  const double tile_bytes = 2.0 * TE * g.kb_per_mode * BK * 2.0 * g.n_modes * (g.n_pass == 3 ? 2 : 1);
+  int band = (int)(g.l2_band_bytes / tile_bytes);
+  return band < 1 ? 1 : (band > n_etile ? n_etile : band);
+}
+
 int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   TcShape S;
   S.n_itile = (int)((P.n_int + TI - 1) / TI);
@@ -433,13 +453,11 @@ int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   S.b_plane_rows = g.b_plane_rows;
   S.b_mode_rows = g.b_mode_rows;
   const int n_super = S.n_itile * S.n_etile;
-  {
-    // extrinsic operand bytes of one tile column (all modes, planes)
-    const double tile_bytes = 2.0 * TE * g.kb_per_mode * BK * 2.0 * g.n_modes * (g.n_pass == 3 ? 2 : 1);
-    int band = (int)(g.l2_band_bytes / tile_bytes);
-    S.band = band < 1 ? 1 : (band > S.n_etile ? S.n_etile : band);
-  }
-  int grid = g.n_sms < n_super ? g.n_sms : n_super;
+  S.band = tc_band(g, S.n_etile);
+  S.list = g.list;
+  S.n_list = g.n_list;
+  // a tile list's length is known on the device only: one CTA per SM
+  int grid = (g.list || g.n_sms < n_super) ? g.n_sms : n_super;
   if (grid < 1) grid = 1;
   auto go = [&](auto kern, size_t smem) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -449,9 +467,12 @@ int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st) {
   };
   const bool split = g.n_pass == 3;
   cudaError_t err;
-  if (split) {
+  if (split && g.bf16) {
     err = P.consec ? go(tc_fused_kernel<true, true, true>, smem_bytes<true>())
                    : go(tc_fused_kernel<true, false, true>, smem_bytes<true>());
+  } else if (split) {
+    err = P.consec ? go(tc_fused_kernel<false, true, true>, smem_bytes<true>())
+                   : go(tc_fused_kernel<false, false, true>, smem_bytes<true>());
   } else if (g.bf16) {
     err = P.consec ? go(tc_fused_kernel<true, true, false>, smem_bytes<false>())
                    : go(tc_fused_kernel<true, false, false>, smem_bytes<false>());

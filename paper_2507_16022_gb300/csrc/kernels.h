@@ -28,8 +28,9 @@ struct PrepArgs {
   float *gmax;     // 1 float, zeroed
   void *gpack;     // packed operand planes
   int pack_kind;   // 0 fp32, 1 bf16, 2 fp16
-  int pack_planes; // 1 or 2 (bf16 hi/lo)
+  int pack_planes; // 1 or 2 (hi, lo)
   float *gscale;   // 1 float out
+  float *sqrt_dd;  // 1 float out: sqrt<d|d> (Eq. inner_product, FP64 sum)
   int *status;
 };
 
@@ -38,8 +39,8 @@ void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int
                         const float *master, const float *omega, float *mx, int n_sms, cudaStream_t st);
 void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, const void *src,
                            int dtype, float *master, float *amax, int *status, cudaStream_t st);
-void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf, __half *hf,
-                             float *scale_out, cudaStream_t st);
+void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf /*[2][n]*/,
+                             __half *hf /*[2][n]*/, float *scale_out, cudaStream_t st);
 void launch_build_dm_table(float4 *tab, cudaStream_t st);
 void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
                            cudaStream_t st);
@@ -71,8 +72,28 @@ struct TcArgs {
   int n_sms;
   int n_modes;
   double l2_band_bytes;  // extrinsic operand bytes kept resident per band
+  const int *list;       // optional device tile list (linear tile indices) and its device length
+  const int *n_list;
 };
 int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st);  // returns cudaError_t as int
+int tc_band(const TcArgs &g, int n_etile);                           // extrinsic tiles per L2 band
+
+// Refinement selection after a screening pass: the tiles whose screened best
+// ln L^ML can reach the cut, in banded tile order.
+struct SelectArgs {
+  const float *tile_ml;   // [n_itile * n_etile] screened best ln L^ML per tile (-1: none evaluated)
+  int n_itile, n_etile, band;
+  const float *ml_screen; // screened running maximum
+  const float *sqrt_dd;   // sqrt<d|d>
+  float window;           // tiles within window + 2 margins of the maximum are refined
+  float margin_k;         // kappa*u of the screening precision
+  float *ml_refine;       // out: screened maximum - margin (a lower bound of the exact maximum)
+  int *list;              // out: [n_itile * n_etile] tile indices
+  int *n_list;            // out: count
+  int *counts;            // scratch: select_count_blocks() ints
+};
+int select_count_blocks(int n_tiles);
+void launch_select(const SelectArgs &a, cudaStream_t st);
 
 // Cross-tile FP64 reduction -> evidence.
 struct ReduceOut {
@@ -82,7 +103,7 @@ struct ReduceOut {
   long long n_marg;
   double threshold;
   int status;
-  int pad;
+  int n_refined;  // tiles refined in split precision (mixed), else -1
 };
 struct ReduceArgs {
   int64_t n_int, n_ext;
@@ -98,6 +119,7 @@ struct ReduceArgs {
   double *ln_p_ext;  // [n_ext] out
   void *scratch;     // reduce_scratch_bytes() of device memory
   const int *status;
+  const int *n_refined;  // optional
   ReduceOut *out;
 };
 void launch_reduce(const ReduceArgs &a, cudaStream_t st);

@@ -48,6 +48,25 @@ __global__ void prep_bins_kernel(int D, int B, const double *__restrict__ f, con
   c[k] = cv;
 }
 
+// sqrt<d|d> = sqrt(sum_{d,b} omega_{d,b} |d_d(f_b)|^2) in FP64, one block, fixed order.
+__global__ void data_norm_kernel(int D, int B, const double *__restrict__ w, const double *__restrict__ psd,
+                                 const double2 *__restrict__ data, float *__restrict__ sqrt_dd) {
+  __shared__ double part[256];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < D * B; k += blockDim.x) {
+    const double S = psd[k];
+    const double2 dk = data[k];
+    if (S > 0.0 && isfinite(S) && isfinite(dk.x) && isfinite(dk.y)) v += 4.0 * w[k % B] / S * (dk.x * dk.x + dk.y * dk.y);
+  }
+  part[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *sqrt_dd = (float)sqrt(part[0]);
+}
+
 __global__ void prep_ext_kernel(int64_t E, int D, int M, const double *__restrict__ t,
                                 const double2 *__restrict__ R, float *__restrict__ th, float *__restrict__ tl,
                                 float2 *__restrict__ Rf, float *__restrict__ qx, int *status) {
@@ -140,7 +159,8 @@ __device__ __forceinline__ float pow2_scale(float maxabs) {
 }
 
 // Real-ified operand rows: (e, re) = [Gr | -Gi], (e, im) = [Gi | Gr], K padded with zeros.
-// kind: 0 = fp32 plane, 1 = bf16 hi (+ lo if nplanes == 2), 2 = fp16 hi.
+// kind: 0 = fp32 plane, 1 = bf16 hi, 2 = fp16 hi; nplanes == 2 adds the lo plane
+// RN(v - hi) of the same type.
 __global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *__restrict__ G,
                               const float *__restrict__ gmax, int kind, int nplanes, void *__restrict__ out,
                               float *__restrict__ scale_out) {
@@ -168,7 +188,9 @@ __global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *_
     ((__nv_bfloat16 *)out)[k] = hi;
     if (nplanes == 2) ((__nv_bfloat16 *)out)[total + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
   } else {
-    ((__half *)out)[k] = __float2half_rn(v);
+    __half hi = __float2half_rn(v);
+    ((__half *)out)[k] = hi;
+    if (nplanes == 2) ((__half *)out)[total + k] = __float2half_rn(v - __half2float(hi));
   }
 }
 
@@ -261,7 +283,7 @@ template __global__ void bank_to_master_kernel<float2>(int64_t, int64_t, int64_t
                                                        float *, float *, int *);
 
 __global__ void master_to_planes_kernel(int64_t n, const float *__restrict__ master, const float *__restrict__ amax,
-                                        __nv_bfloat16 *__restrict__ bf /*[2][n]*/, __half *__restrict__ hf,
+                                        __nv_bfloat16 *__restrict__ bf /*[2][n]*/, __half *__restrict__ hf /*[2][n]*/,
                                         float *__restrict__ scale_out) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float sc = pow2_scale(*amax);
@@ -271,7 +293,9 @@ __global__ void master_to_planes_kernel(int64_t n, const float *__restrict__ mas
   __nv_bfloat16 hi = __float2bfloat16_rn(v);
   bf[k] = hi;
   bf[n + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-  hf[k] = __float2half_rn(v);
+  __half h = __float2half_rn(v);
+  hf[k] = h;
+  hf[n + k] = __float2half_rn(v - __half2float(h));
 }
 
 // ---------------------------------------------------------------------------
@@ -350,6 +374,7 @@ static inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) 
 void launch_prep(const PrepArgs &a, cudaStream_t st) {
   prep_bins_kernel<<<nblk((int64_t)a.D * a.B, 256), 256, 0, st>>>(a.D, a.B, a.f, a.w, a.psd, a.data, a.c, a.omega,
                                                                 a.fh, a.fl, a.status);
+  if (a.sqrt_dd) data_norm_kernel<<<1, 256, 0, st>>>(a.D, a.B, a.w, a.psd, a.data, a.sqrt_dd);
   prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, a.th, a.tl, a.Rf, a.qx, a.status);
   build_G_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.Rf, a.G32,
                                                        a.gmax);
