@@ -129,7 +129,14 @@ typedef struct dotpe_bank_desc {
  * u_min = d_L^0 / d_max of the distance prior pi(d_L) ~ d_L^2 on (0, d_max].
  * cut_delta > 0 enables the coherent-ML selection of Eq. coherent_ML_selection
  *   (phases with ln L^ML < max - cut_delta are not marginalised); <= 0 disables it.
- * stream: cudaStream_t the event's work is ordered after (NULL: none). */
+ * stream: cudaStream_t the event's work is ordered after (NULL: none).
+ * block_rows: 0 processes the slice in one pass; otherwise a positive multiple
+ *   of 128: the slice streams through the kernels in blocks of that many bank
+ *   rows (the event's device scratch then scales with block_rows, not with the
+ *   slice), and each block's log-sum-exp partials, marginals and best ln L^ML
+ *   are merged into FP64 accumulators in block order.  The result does not
+ *   depend on block_rows beyond FP64 rounding, except with the ML cut on, where
+ *   the running maximum (and so the kept superset) evolves block by block. */
 typedef struct dotpe_event_desc {
   uint64_t bank_id;
   int64_t i0, i1;
@@ -146,6 +153,7 @@ typedef struct dotpe_event_desc {
   int precision;
   int flags;
   void *stream;
+  int64_t block_rows;
 } dotpe_event_desc;
 
 typedef struct dotpe_event_stats {

@@ -72,7 +72,8 @@ class dotpe_event_desc(ctypes.Structure):
                 ("n_det", ctypes.c_int), ("psd", _dp), ("data", _dp), ("n_ext", ctypes.c_int64),
                 ("t", _dp), ("R", _dp), ("ln_w_ext", _dp), ("n_phi", ctypes.c_int),
                 ("u_min", ctypes.c_double), ("cut_delta", ctypes.c_double),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("block_rows", ctypes.c_int64)]
 
 
 class dotpe_event_stats(ctypes.Structure):
@@ -218,9 +219,10 @@ def dotpe_bank_release(ctx, bank_id):
 
 
 def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
-                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None):
+                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0):
     """psd [D,B], data [D,B] complex, t [E,D], R [E,D,M] complex, ln_w_ext [E]: numpy (host)
-    or torch tensors (host or device; complex tensors as float64 views are accepted)."""
+    or torch tensors (host or device; complex tensors as float64 views are accepted).
+    block_rows: 0, or a multiple of 128 to stream the slice through in bank blocks."""
     L = load()
     keep = []
 
@@ -241,7 +243,7 @@ def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_p
     if stream is not None:
         st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     desc = dotpe_event_desc(bank_id, i0, i1, D, arr(psd), arr(data, True), E, arr(t), arr(R, True),
-                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st)
+                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st, block_rows)
     eid = ctypes.c_uint64()
     _check(L.dotpe_event_submit(ctx, ctypes.byref(desc), ctypes.byref(eid)))
     return eid.value

@@ -86,6 +86,7 @@ struct Event {
   Bank *bank = nullptr;
   int state = DOTPE_STATE_QUEUED;
   int64_t i0 = 0, NI = 0, NE = 0;
+  int64_t block_rows = 0;  // rows per streamed bank block (0: the whole slice)
   int D = 0, nphi = 0, prec = 0, flags = 0;
   double u_min = 0, cut = 0;
   bool has_lwe = false;
@@ -163,8 +164,10 @@ static void CUDART_CB mark_done(void *p) {
 // ---------------------------------------------------------------------------
 struct ScratchLayout {
   size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, sqrt_dd, gpack, mx, tile_part, tile_ml, tile_arg,
-      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, sel_counts, status, red, total;
-  int n_itile, n_etile, pack_kind, pack_planes, TI, TE;
+      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, sel_counts, acc, acc_col, status, red,
+      total;
+  int64_t block_rows;  // bank rows per streamed block (the whole slice when not streamed)
+  int n_itile, n_etile, pack_kind, pack_planes, TI, TE;  // n_itile: tiles of one block
 };
 
 static bool prec_split(int p) { return p == DOTPE_PREC_BF16X3 || p == DOTPE_PREC_FP16X3 || p == DOTPE_PREC_MIXED; }
@@ -179,8 +182,10 @@ static const float MIXED_FAR_WINDOW = 30.0f;
 static ScratchLayout scratch_layout(const Event &e) {
   ScratchLayout L{};
   const Bank &b = *e.bank;
-  const int64_t D = e.D, B = b.B, M = b.M, E = e.NE, NI = e.NI, Kp = b.Kpad;
+  const int64_t D = e.D, B = b.B, M = b.M, E = e.NE, Kp = b.Kpad;
   const bool simt = (e.prec == DOTPE_PREC_FP32);
+  L.block_rows = (e.block_rows > 0 && e.block_rows < e.NI) ? e.block_rows : e.NI;
+  const int64_t NI = L.block_rows;  // per-block arrays
   L.TI = simt ? SIMT_TI : TC_TI;
   L.TE = simt ? SIMT_TE : TC_TE;
   L.n_itile = (int)((NI + L.TI - 1) / L.TI);
@@ -216,6 +221,8 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.list = c.take<int>(mixed ? T : 0);
   L.n_list = c.take<int>(1);
   L.sel_counts = c.take<int>(mixed ? select_count_blocks((int)T) : 0);
+  L.acc = c.take<EvAcc>(1);
+  L.acc_col = c.take<double2>(E);
   L.status = c.take<int>(1);
   L.red = c.take<uint8_t>(reduce_scratch_bytes());
   L.total = c.off;
@@ -281,7 +288,6 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   pa.status = status;
   launch_prep(pa, st);
   float *mx = (float *)(scr + L.mx);
-  launch_cross_terms(e.NI, e.i0, b.I, b.M, e.D, b.B, b.Kpad, b.master, pa.omega, mx, ctx->n_sms, st);
 
   EpiParams P;
   memset(&P, 0, sizeof(P));
@@ -301,12 +307,9 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   P.u_min = (float)e.u_min;
   P.cut_delta = (float)(e.cut > 0 ? e.cut : 0.0);
   P.ln_nphi = (float)std::log((double)e.nphi);
-  P.n_int = e.NI;
   P.n_ext = e.NE;
-  P.i_base = e.i0;
   P.mx = mx;
   P.qx = pa.qx;
-  P.lw_int = b.lw ? b.lw + e.i0 : nullptr;
   P.lw_ext = e.has_lwe ? e.lwe : nullptr;
   P.dm_table = ctx->dm_table;
   P.ml_running = (float *)(scr + L.ml_running);
@@ -318,29 +321,16 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   P.tile_ml = (float *)(scr + L.tile_ml);
   P.tile_arg = (long long *)(scr + L.tile_arg);
   P.tile_npass = (int *)(scr + L.tile_npass);
-  P.lnl_tile = e.lnl_tile;
-  P.ml_tile = e.ml_tile;
   P.status = status;
   P.gemm_only = (e.flags & DOTPE_FLAG_GEMM_ONLY) ? 1 : 0;
   P.test_stall = (e.flags & DOTPE_FLAG_TEST_STALL) ? 1 : 0;
   P.wait_ns = P.test_stall ? 250000000ull : 4000000000ull;
+  const bool mixed = (e.prec == DOTPE_PREC_MIXED);
 
-  CUDA_OR_FAIL(cudaEventRecord(e.ev_k0, st));
-  if (e.prec == DOTPE_PREC_FP32) {
-    P.z_scale = 1.f;
-    P.g_scale = nullptr;
-    SimtArgs g;
-    g.A = b.master;
-    g.Bm = (const float *)pa.gpack;
-    g.I_bank = b.I;
-    g.Kpad = b.Kpad;
-    g.K = 2 * b.B;
-    launch_simt(g, P, st);
-  } else {
-    P.z_scale = 1.f / b.a_scale;
-    P.g_scale = pa.gscale;
-    TcArgs g;
-    memset(&g, 0, sizeof(g));
+  // tensor-core operand maps (the whole bank and the event's packed G)
+  TcArgs g;
+  memset(&g, 0, sizeof(g));
+  if (e.prec != DOTPE_PREC_FP32) {
     const bool bf = prec_bf16(e.prec);
     g.bf16 = bf;
     g.kb_per_mode = b.Kpad / 64;
@@ -359,55 +349,19 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
       return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed");
     g.a_plane_rows = b.M * (int)b.I;
     g.a_mode_rows = (int)b.I;
-    g.a_row0 = (int)e.i0;
     g.b_plane_rows = b.M * 2 * (int)e.NE;
     g.b_mode_rows = 2 * (int)e.NE;
-    g.n_pass = prec_split(e.prec) ? 3 : 1;  // hi*hi (+ hi*lo + lo*hi)
-    if (e.prec == DOTPE_PREC_MIXED) {
-      // screening pass: one fp16 product for every pair, best ln L^ML per tile
-      // (with the cut off, the full single-pass epilogue)
-      EpiParams Ps = P;
-      Ps.track_max = 1;
-      Ps.screen_ml = (P.cut_delta > 0.f) ? 1 : 0;
-      Ps.margin_k = MIXED_MARGIN_K;
-      g.n_pass = 1;
-      int r = launch_tc(g, Ps, st);
-      if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
-      CUDA_OR_FAIL(cudaEventRecord(e.ev_ks, st));
-      // the tiles that can reach the cut (or, with the cut off, within the far window)
-      SelectArgs sa;
-      sa.tile_ml = P.tile_ml;
-      sa.n_itile = L.n_itile;
-      sa.n_etile = L.n_etile;
-      g.n_pass = 3;
-      sa.band = tc_band(g, L.n_etile);
-      sa.ml_screen = P.ml_running;
-      sa.sqrt_dd = pa.sqrt_dd;
-      sa.window = (P.cut_delta > 0.f) ? P.cut_delta : MIXED_FAR_WINDOW;
-      sa.margin_k = MIXED_MARGIN_K;
-      sa.ml_refine = (float *)(scr + L.ml_refine);
-      sa.list = (int *)(scr + L.list);
-      sa.n_list = (int *)(scr + L.n_list);
-      sa.counts = (int *)(scr + L.sel_counts);
-      launch_select(sa, st);
-      CUDA_OR_FAIL(cudaGetLastError());
-      // refinement: split precision on the selected tiles, threshold frozen at
-      // (screened maximum - margin) - cut_delta, a lower bound of the exact cut
-      P.ml_running = sa.ml_refine;
-      P.track_max = 0;
-      g.list = sa.list;
-      g.n_list = sa.n_list;
-    }
-    int r = launch_tc(g, P, st);
-    if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+    P.z_scale = 1.f / b.a_scale;
+    P.g_scale = pa.gscale;
+  } else {
+    P.z_scale = 1.f;
+    P.g_scale = nullptr;
   }
-  CUDA_OR_FAIL(cudaEventRecord(e.ev_k1, st));
 
   ReduceArgs ra;
   memset(&ra, 0, sizeof(ra));
-  ra.n_int = e.NI;
   ra.n_ext = e.NE;
-  ra.n_itile = L.n_itile;
+  ra.n_int_total = e.NI;
   ra.n_etile = L.n_etile;
   ra.n_phi = e.nphi;
   ra.tile_part = P.tile_part;
@@ -416,15 +370,90 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   ra.tile_ml = P.tile_ml;
   ra.tile_arg = P.tile_arg;
   ra.tile_npass = P.tile_npass;
-  ra.ml_running = P.ml_running;
+  ra.ml_running = mixed ? (const float *)(scr + L.ml_refine) : P.ml_running;
   ra.cut_delta = P.cut_delta;
   ra.ln_p_int = e.ln_p_int;
   ra.ln_p_ext = e.ln_p_ext;
+  ra.acc = (EvAcc *)(scr + L.acc);
+  ra.acc_col = (double2 *)(scr + L.acc_col);
   ra.status = status;
   ra.scratch = scr + L.red;
   ra.out = e.d_out;
-  ra.n_refined = (e.prec == DOTPE_PREC_MIXED) ? (const int *)(scr + L.n_list) : nullptr;
-  launch_reduce(ra, st);
+  ra.n_refined = mixed ? (const int *)(scr + L.n_list) : nullptr;
+
+  // the slice in bank blocks of L.block_rows rows: cross terms, fused kernel(s),
+  // then the block's partials merged into the FP64 accumulators
+  const int n_blocks = (int)((e.NI + L.block_rows - 1) / L.block_rows);
+  for (int k = 0; k < n_blocks; ++k) {
+    const int64_t r0 = (int64_t)k * L.block_rows;
+    const int64_t nr = std::min<int64_t>(L.block_rows, e.NI - r0);
+    launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, pa.omega, mx, ctx->n_sms, st);
+    P.n_int = nr;
+    P.i_base = e.i0 + r0;
+    P.lw_int = b.lw ? b.lw + e.i0 + r0 : nullptr;
+    P.lnl_tile = e.lnl_tile ? e.lnl_tile + r0 * e.NE : nullptr;
+    P.ml_tile = e.ml_tile ? e.ml_tile + r0 * e.NE : nullptr;
+    if (k == 0) CUDA_OR_FAIL(cudaEventRecord(e.ev_k0, st));
+    if (e.prec == DOTPE_PREC_FP32) {
+      SimtArgs sg;
+      sg.A = b.master;
+      sg.Bm = (const float *)pa.gpack;
+      sg.I_bank = b.I;
+      sg.Kpad = b.Kpad;
+      sg.K = 2 * b.B;
+      launch_simt(sg, P, st);
+    } else {
+      g.a_row0 = (int)(e.i0 + r0);
+      g.list = nullptr;
+      g.n_list = nullptr;
+      g.n_pass = prec_split(e.prec) ? 3 : 1;  // hi*hi (+ hi*lo + lo*hi)
+      EpiParams Pf = P;
+      if (mixed) {
+        // screening pass: one fp16 product for every pair, best ln L^ML per tile
+        // (with the cut off, the full single-pass epilogue)
+        EpiParams Ps = P;
+        Ps.track_max = 1;
+        Ps.screen_ml = (P.cut_delta > 0.f) ? 1 : 0;
+        Ps.margin_k = MIXED_MARGIN_K;
+        g.n_pass = 1;
+        int r = launch_tc(g, Ps, st);
+        if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+        if (k == n_blocks - 1) CUDA_OR_FAIL(cudaEventRecord(e.ev_ks, st));
+        // the tiles that can reach the cut (or, with the cut off, within the far window)
+        SelectArgs sa;
+        sa.tile_ml = P.tile_ml;
+        sa.n_itile = (int)((nr + TC_TI - 1) / TC_TI);
+        sa.n_etile = L.n_etile;
+        g.n_pass = 3;
+        sa.band = tc_band(g, L.n_etile);
+        sa.ml_screen = P.ml_running;
+        sa.sqrt_dd = pa.sqrt_dd;
+        sa.window = (P.cut_delta > 0.f) ? P.cut_delta : MIXED_FAR_WINDOW;
+        sa.margin_k = MIXED_MARGIN_K;
+        sa.ml_refine = (float *)(scr + L.ml_refine);
+        sa.list = (int *)(scr + L.list);
+        sa.n_list = (int *)(scr + L.n_list);
+        sa.counts = (int *)(scr + L.sel_counts);
+        launch_select(sa, st);
+        CUDA_OR_FAIL(cudaGetLastError());
+        // refinement: split precision on the selected tiles, threshold frozen at
+        // (screened maximum - margin) - cut_delta, a lower bound of the exact cut
+        Pf.ml_running = sa.ml_refine;
+        Pf.track_max = 0;
+        g.list = sa.list;
+        g.n_list = sa.n_list;
+      }
+      int r = launch_tc(g, Pf, st);
+      if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+    }
+    if (k == n_blocks - 1) CUDA_OR_FAIL(cudaEventRecord(e.ev_k1, st));
+    ra.n_int = nr;
+    ra.row_offset = r0;
+    ra.n_itile = (int)((nr + L.TI - 1) / L.TI);
+    ra.first = (k == 0);
+    launch_reduce_block(ra, st);
+  }
+  launch_reduce_final(ra, st);
   CUDA_OR_FAIL(cudaGetLastError());
   CUDA_OR_FAIL(cudaMemcpyAsync(e.h_out, e.d_out, sizeof(ReduceOut), cudaMemcpyDeviceToHost, st));
   CUDA_OR_FAIL(cudaEventRecord(e.ev_end, st));
@@ -792,6 +821,8 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   if (!d->psd || !d->data || !d->t || !d->R) return fail(DOTPE_E_INVALID, "null input array");
   if (d->precision < DOTPE_PREC_FP32 || d->precision > DOTPE_PREC_MIXED)
     return fail(DOTPE_E_INVALID, "precision %d", d->precision);
+  if (d->block_rows < 0 || d->block_rows % TC_TI != 0)
+    return fail(DOTPE_E_INVALID, "block_rows=%lld is not a non-negative multiple of %d", (long long)d->block_rows, TC_TI);
   const int64_t NI = d->i1 - d->i0, NE = d->n_ext;
   if (d->precision != DOTPE_PREC_FP32 && (2 * (int64_t)b->M * 2 * NE >= (1ll << 31)))
     return fail(DOTPE_E_UNSUPPORTED, "n_ext too large");
@@ -803,6 +834,7 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   e->D = d->n_det;
   e->nphi = d->n_phi;
   e->prec = d->precision;
+  e->block_rows = d->block_rows;
   e->flags = d->flags;
   e->u_min = d->u_min;
   e->cut = d->cut_delta;

@@ -7,6 +7,9 @@
 // Two passes per log-sum-exp: the maximum (FP32, exact), then the sum of
 // s * exp(m - max) accumulated in FP64 (the exponentials of FP32 partials are
 // evaluated in FP32: their relative error is that of the partials themselves).
+// A slice processed as several bank blocks merges each block's (max, sum) pairs,
+// its column marginals and its best ln L^ML into FP64 accumulators in block
+// order; the final kernel turns them into the evidence.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -15,11 +18,14 @@ namespace dotpe {
 namespace {
 constexpr int RB = 256;  // threads per block
 constexpr int NB = 128;  // blocks of the parallel passes
-constexpr int NSUM = 4;  // quantities reduced in the final pass
+constexpr int NQ = 3;    // log-sum-exp inputs of a bank block: tile m1, tile m2, 2 ln P_i
 }
 
 // ln P over partials [nparts][n] (row or column marginal), one thread per entry.
-__global__ void reduce_lines_kernel(int64_t n, int nparts, const float2 *__restrict__ part, double *__restrict__ out) {
+// With acc != nullptr the value is merged into the FP64 accumulator acc[k] = (m, s)
+// (s = 0: empty) instead of written to out.
+__global__ void reduce_lines_kernel(int64_t n, int nparts, const float2 *__restrict__ part, double *__restrict__ out,
+                                    double2 *__restrict__ acc, int first) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   float m = -INFINITY;
@@ -27,16 +33,24 @@ __global__ void reduce_lines_kernel(int64_t n, int nparts, const float2 *__restr
     float2 v = part[(int64_t)p * n + k];
     if (v.y > 0.f) m = fmaxf(m, v.x);
   }
-  if (m == -INFINITY) {
-    out[k] = -INFINITY;
+  double s = 0.0;
+  if (m != -INFINITY)
+    for (int p = 0; p < nparts; ++p) {
+      float2 v = part[(int64_t)p * n + k];
+      if (v.y > 0.f) s += (double)v.y * (double)__expf(v.x - m);
+    }
+  if (!acc) {
+    out[k] = (m == -INFINITY) ? -INFINITY : (double)m + log(s);
     return;
   }
-  double s = 0.0;
-  for (int p = 0; p < nparts; ++p) {
-    float2 v = part[(int64_t)p * n + k];
-    if (v.y > 0.f) s += (double)v.y * (double)__expf(v.x - m);
+  double2 a = first ? make_double2(0.0, 0.0) : acc[k];
+  if (s > 0.0) {
+    const double bm = (double)m;
+    if (!(a.y > 0.0)) a = make_double2(bm, s);
+    else if (bm > a.x) a = make_double2(bm, a.y * exp(a.x - bm) + s);
+    else a.y += s * exp(bm - a.x);
   }
-  out[k] = (double)m + log(s);
+  acc[k] = a;
 }
 
 __device__ __forceinline__ float block_max(float v, float *sh) {
@@ -69,8 +83,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return v;
 }
 
-// Pass 1: per-block maxima of the four log-sum-exp inputs (tile m1, tile m2,
-// 2 ln P_i, 2 ln P_e), the argmax and the marginalised count.
+// Pass 1 over one bank block: per-block maxima of the log-sum-exp inputs, the
+// argmax and the marginalised count.
 __global__ void __launch_bounds__(RB) reduce_pass1_kernel(ReduceArgs a, float *__restrict__ bmax,
                                                            float *__restrict__ bml, long long *__restrict__ barg,
                                                            long long *__restrict__ bnp) {
@@ -81,7 +95,7 @@ __global__ void __launch_bounds__(RB) reduce_pass1_kernel(ReduceArgs a, float *_
   const int64_t n_tiles = (int64_t)a.n_itile * a.n_etile;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float m1 = -INFINITY, m2 = -INFINITY, mr = -INFINITY, mc = -INFINITY, best = -1.f;
+  float m1 = -INFINITY, m2 = -INFINITY, mr = -INFINITY, best = -1.f;
   long long arg = 0x7fffffffffffffffLL, np = 0;
   for (int64_t k = k0; k < n_tiles; k += stride) {
     float4 v = a.tile_part[k];
@@ -92,10 +106,10 @@ __global__ void __launch_bounds__(RB) reduce_pass1_kernel(ReduceArgs a, float *_
     if (ml > best || (ml == best && g < arg)) { best = ml; arg = g; }
     np += a.tile_npass[k];
   }
-  for (int64_t k = k0; k < a.n_int; k += stride) mr = fmaxf(mr, (float)(2.0 * a.ln_p_int[k]));
-  for (int64_t k = k0; k < a.n_ext; k += stride) mc = fmaxf(mc, (float)(2.0 * a.ln_p_ext[k]));
-  float r[NSUM] = {m1, m2, mr, mc};
-  for (int q = 0; q < NSUM; ++q) {
+  const double *lpi = a.ln_p_int + a.row_offset;
+  for (int64_t k = k0; k < a.n_int; k += stride) mr = fmaxf(mr, (float)(2.0 * lpi[k]));
+  float r[NQ] = {m1, m2, mr};
+  for (int q = 0; q < NQ; ++q) {
     float v = block_max(r[q], shf);
     if (threadIdx.x == 0) bmax[q * gridDim.x + blockIdx.x] = v;
   }
@@ -120,12 +134,12 @@ __global__ void __launch_bounds__(RB) reduce_pass1_kernel(ReduceArgs a, float *_
   }
 }
 
-// Pass 2: per-block FP64 sums of s * exp(m - M) against the global maxima.
+// Pass 2: per-block FP64 sums of s * exp(m - M) against the bank block's maxima.
 __global__ void __launch_bounds__(RB) reduce_pass2_kernel(ReduceArgs a, const float *__restrict__ bmax,
                                                            double *__restrict__ bsum) {
   __shared__ double shd[32];
-  __shared__ float M[NSUM];
-  if (threadIdx.x < NSUM) {
+  __shared__ float M[NQ];
+  if (threadIdx.x < NQ) {
     float m = -INFINITY;
     for (int b = 0; b < (int)gridDim.x; ++b) m = fmaxf(m, bmax[threadIdx.x * gridDim.x + b]);
     M[threadIdx.x] = m;
@@ -134,60 +148,115 @@ __global__ void __launch_bounds__(RB) reduce_pass2_kernel(ReduceArgs a, const fl
   const int64_t n_tiles = (int64_t)a.n_itile * a.n_etile;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double s[NSUM] = {0.0, 0.0, 0.0, 0.0};
+  double s[NQ] = {0.0, 0.0, 0.0};
   for (int64_t k = k0; k < n_tiles; k += stride) {
     float4 v = a.tile_part[k];
     if (v.y > 0.f) s[0] += (double)v.y * (double)__expf(v.x - M[0]);
     if (v.w > 0.f) s[1] += (double)v.w * (double)__expf(v.z - M[1]);
   }
+  const double *lpi = a.ln_p_int + a.row_offset;
   for (int64_t k = k0; k < a.n_int; k += stride) {
-    double v = a.ln_p_int[k];
+    double v = lpi[k];
     if (v != -INFINITY) s[2] += exp(2.0 * v - (double)M[2]);
   }
-  for (int64_t k = k0; k < a.n_ext; k += stride) {
-    double v = a.ln_p_ext[k];
-    if (v != -INFINITY) s[3] += exp(2.0 * v - (double)M[3]);
-  }
-  for (int q = 0; q < NSUM; ++q) {
+  for (int q = 0; q < NQ; ++q) {
     double v = block_sum(s[q], shd);
     if (threadIdx.x == 0) bsum[q * gridDim.x + blockIdx.x] = v;
   }
 }
 
-__global__ void reduce_finish_kernel(ReduceArgs a, int nb, const float *__restrict__ bmax, const double *__restrict__ bsum,
-                                     const float *__restrict__ bml, const long long *__restrict__ barg,
-                                     const long long *__restrict__ bnp) {
+__device__ __forceinline__ void acc_merge(double &am, double &as, double bm, double bs) {
+  if (!(bs > 0.0)) return;
+  if (!(as > 0.0)) { am = bm; as = bs; return; }
+  if (bm > am) { as = as * exp(am - bm) + bs; am = bm; }
+  else as += bs * exp(bm - am);
+}
+
+// Merges one bank block into the event's FP64 accumulators (fixed order: deterministic).
+__global__ void reduce_block_merge_kernel(ReduceArgs a, int nb, const float *__restrict__ bmax,
+                                          const double *__restrict__ bsum, const float *__restrict__ bml,
+                                          const long long *__restrict__ barg, const long long *__restrict__ bnp) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double lv[NSUM];
-  for (int q = 0; q < NSUM; ++q) {
+  EvAcc c = a.first ? EvAcc{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, -1.f, 0x7fffffffffffffffLL, 0} : *a.acc;
+  double *dst[NQ][2] = {{&c.s1_m, &c.s1_s}, {&c.s2_m, &c.s2_s}, {&c.pi_m, &c.pi_s}};
+  for (int q = 0; q < NQ; ++q) {
     float m = -INFINITY;
     double s = 0.0;
     for (int b = 0; b < nb; ++b) m = fmaxf(m, bmax[q * nb + b]);
-    for (int b = 0; b < nb; ++b) s += bsum[q * nb + b];  // fixed order: deterministic
-    lv[q] = (m == -INFINITY || !(s > 0.0)) ? -INFINITY : (double)m + log(s);
+    for (int b = 0; b < nb; ++b) s += bsum[q * nb + b];
+    if (m != -INFINITY) acc_merge(*dst[q][0], *dst[q][1], (double)m, s);
   }
-  float best = -1.f;
-  long long arg = 0x7fffffffffffffffLL, np = 0;
+  // arguments are packed ((i * n_ext + e) * n_phi + o) with i relative to the block
+  const long long shift = (long long)a.row_offset * a.n_ext * a.n_phi;
   for (int b = 0; b < nb; ++b) {
-    if (bml[b] > best || (bml[b] == best && barg[b] < arg)) { best = bml[b]; arg = barg[b]; }
-    np += bnp[b];
+    const long long g = barg[b] + shift;
+    if (bml[b] > c.best || (bml[b] == c.best && g < c.arg)) { c.best = bml[b]; c.arg = g; }
+    c.n_marg += bnp[b];
   }
+  *a.acc = c;
+}
+
+// After the last block: column marginals, Sum_e P_e^2 (two passes) and the evidence.
+__global__ void __launch_bounds__(1024) reduce_final_kernel(ReduceArgs a) {
+  __shared__ float shf[32];
+  __shared__ double shd[32];
+  const EvAcc c = *a.acc;
+  float mc = -INFINITY;
+  for (int64_t k = threadIdx.x; k < a.n_ext; k += blockDim.x) {
+    const double2 v = a.acc_col[k];
+    const double l = (v.y > 0.0) ? v.x + log(v.y) : -INFINITY;
+    a.ln_p_ext[k] = l;
+    mc = fmaxf(mc, (float)(2.0 * l));
+  }
+  mc = block_max(mc, shf);
+  double sc = 0.0;
+  if (mc != -INFINITY)
+    for (int64_t k = threadIdx.x; k < a.n_ext; k += blockDim.x) {
+      const double l = a.ln_p_ext[k];
+      if (l != -INFINITY) sc += exp(2.0 * l - (double)mc);
+    }
+  sc = block_sum(sc, shd);
+  if (threadIdx.x != 0) return;
+  auto lnv = [](double m, double s) { return (s > 0.0) ? m + log(s) : -INFINITY; };
+  const double l1 = lnv(c.s1_m, c.s1_s), l2 = lnv(c.s2_m, c.s2_s), lpi = lnv(c.pi_m, c.pi_s);
+  const double lpe = (mc == -INFINITY || !(sc > 0.0)) ? -INFINITY : (double)mc + log(sc);
   ReduceOut o;
-  const double l1 = lv[0], l2 = lv[1];
   o.ln_s1 = l1;
   o.ln_s2 = l2;
-  o.ln_z = l1 - log((double)a.n_int) - log((double)a.n_ext) - log((double)a.n_phi);
+  o.ln_z = l1 - log((double)a.n_int_total) - log((double)a.n_ext) - log((double)a.n_phi);
   o.n_eff = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - l2);
-  o.n_eff_int = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - lv[2]);
-  o.n_eff_ext = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - lv[3]);
-  o.max_ml = best;
-  o.arg = arg;
-  o.n_marg = np;
+  o.n_eff_int = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - lpi);
+  o.n_eff_ext = (l1 == -INFINITY) ? 0.0 : exp(2.0 * l1 - lpe);
+  o.max_ml = c.best;
+  o.arg = c.arg;
+  o.n_marg = c.n_marg;
   o.threshold = (a.cut_delta > 0.f) ? (double)(*a.ml_running) - (double)a.cut_delta : -INFINITY;
   o.status = *a.status;
   o.n_refined = a.n_refined ? *a.n_refined : -1;
   *a.out = o;
 }
+
+size_t reduce_scratch_bytes() {
+  return (size_t)NB * (NQ * sizeof(float) + NQ * sizeof(double) + sizeof(float) + 2 * sizeof(long long)) + 256;
+}
+
+void launch_reduce_block(const ReduceArgs &a, cudaStream_t st) {
+  reduce_lines_kernel<<<(unsigned)((a.n_int + 255) / 256), 256, 0, st>>>(a.n_int, a.n_etile, a.row_part,
+                                                                        a.ln_p_int + a.row_offset, nullptr, 0);
+  reduce_lines_kernel<<<(unsigned)((a.n_ext + 255) / 256), 256, 0, st>>>(a.n_ext, a.n_itile, a.col_part, nullptr,
+                                                                        a.acc_col, a.first);
+  uint8_t *w = (uint8_t *)a.scratch;
+  float *bmax = (float *)w;
+  double *bsum = (double *)(w + NB * NQ * sizeof(float));
+  float *bml = (float *)(bsum + NB * NQ);
+  long long *barg = (long long *)(((uintptr_t)(bml + NB) + 7) & ~(uintptr_t)7);
+  long long *bnp = barg + NB;
+  reduce_pass1_kernel<<<NB, RB, 0, st>>>(a, bmax, bml, barg, bnp);
+  reduce_pass2_kernel<<<NB, RB, 0, st>>>(a, bmax, bsum);
+  reduce_block_merge_kernel<<<1, 32, 0, st>>>(a, NB, bmax, bsum, bml, barg, bnp);
+}
+
+void launch_reduce_final(const ReduceArgs &a, cudaStream_t st) { reduce_final_kernel<<<1, 1024, 0, st>>>(a); }
 
 // ---------------------------------------------------------------------------
 // Refinement selection (after a screening pass).  Tile t is refined when its
@@ -269,24 +338,6 @@ void launch_select(const SelectArgs &a, cudaStream_t st) {
   if (nb < 1) return;
   select_count_kernel<<<nb, SB, 0, st>>>(a);
   select_write_kernel<<<nb, SB, 0, st>>>(a);
-}
-
-size_t reduce_scratch_bytes() {
-  return (size_t)NB * (NSUM * sizeof(float) + NSUM * sizeof(double) + sizeof(float) + 2 * sizeof(long long)) + 256;
-}
-
-void launch_reduce(const ReduceArgs &a, cudaStream_t st) {
-  reduce_lines_kernel<<<(unsigned)((a.n_int + 255) / 256), 256, 0, st>>>(a.n_int, a.n_etile, a.row_part, a.ln_p_int);
-  reduce_lines_kernel<<<(unsigned)((a.n_ext + 255) / 256), 256, 0, st>>>(a.n_ext, a.n_itile, a.col_part, a.ln_p_ext);
-  uint8_t *w = (uint8_t *)a.scratch;
-  float *bmax = (float *)w;
-  double *bsum = (double *)(w + NB * NSUM * sizeof(float));
-  float *bml = (float *)(bsum + NB * NSUM);
-  long long *barg = (long long *)(((uintptr_t)(bml + NB) + 7) & ~(uintptr_t)7);
-  long long *bnp = barg + NB;
-  reduce_pass1_kernel<<<NB, RB, 0, st>>>(a, bmax, bml, barg, bnp);
-  reduce_pass2_kernel<<<NB, RB, 0, st>>>(a, bmax, bsum);
-  reduce_finish_kernel<<<1, 32, 0, st>>>(a, NB, bmax, bsum, bml, barg, bnp);
 }
 
 }  // namespace dotpe

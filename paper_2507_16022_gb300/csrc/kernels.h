@@ -95,7 +95,7 @@ struct SelectArgs {
 int select_count_blocks(int n_tiles);
 void launch_select(const SelectArgs &a, cudaStream_t st);
 
-// Cross-tile FP64 reduction -> evidence.
+// Cross-tile FP64 reduction -> evidence, one bank block at a time.
 struct ReduceOut {
   double ln_z, ln_s1, ln_s2, n_eff, n_eff_int, n_eff_ext;
   double max_ml;
@@ -105,9 +105,19 @@ struct ReduceOut {
   int status;
   int n_refined;  // tiles refined in split precision (mixed), else -1
 };
+// FP64 accumulators across bank blocks: (m, s) pairs with s = 0 meaning empty.
+struct EvAcc {
+  double s1_m, s1_s, s2_m, s2_s, pi_m, pi_s;  // ln S1, ln S2, ln sum_i P_i^2
+  float best;                                 // best ln L^ML so far
+  long long arg;                              // its packed (i, e, o), i relative to the slice
+  long long n_marg;
+};
 struct ReduceArgs {
-  int64_t n_int, n_ext;
+  int64_t n_int, n_ext;  // rows of this block, extrinsic samples
+  int64_t row_offset;    // first row of the block within the slice
+  int64_t n_int_total;   // rows of the slice
   int n_itile, n_etile, n_phi;
+  int first;             // first block: accumulators start empty
   const float4 *tile_part;
   const float2 *row_part, *col_part;
   const float *tile_ml;
@@ -115,14 +125,17 @@ struct ReduceArgs {
   const int *tile_npass;
   const float *ml_running;
   float cut_delta;
-  double *ln_p_int;  // [n_int] out
-  double *ln_p_ext;  // [n_ext] out
+  double *ln_p_int;  // [n_int_total] out (slice)
+  double *ln_p_ext;  // [n_ext] out (final kernel)
+  EvAcc *acc;        // device
+  double2 *acc_col;  // [n_ext] device
   void *scratch;     // reduce_scratch_bytes() of device memory
   const int *status;
   const int *n_refined;  // optional
   ReduceOut *out;
 };
-void launch_reduce(const ReduceArgs &a, cudaStream_t st);
+void launch_reduce_block(const ReduceArgs &a, cudaStream_t st);
+void launch_reduce_final(const ReduceArgs &a, cudaStream_t st);
 size_t reduce_scratch_bytes();
 
 // Tensor-map encoding through the driver entry point.

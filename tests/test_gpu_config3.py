@@ -1,0 +1,137 @@
+"""Large-bank stress (1,048,576 bank rows x 2,048 extrinsic samples, D=3, M=4,
+B=384, injection SNR 30): the slice streams through the kernels in blocks of
+65,536 bank rows with FP64 accumulation across blocks.
+
+Checks, against the FP64 oracle on sampled pairs and against the plain FP32
+path on the same GPU:
+  * split fp16 (hi + lo) meets |d ln L| <= 1e-3 per pair at SNR 30, where
+    ln L^ML ~ 450 and the cancellation in Re<d|h> - <h|h>/2 is largest;
+  * the served mixed path meets |d ln Z| <= 1e-2 against FP32, with the same
+    maximum and argmax;
+  * streaming in blocks reproduces the one-pass result (FP64 rounding only);
+  * single-pass fp16 is reported against its own bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+BLOCK = 65536
+
+
+@pytest.fixture(scope="module")
+def big():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2507_16022_gb300 as dp
+    wl = synth.named_workload("cfg3")
+    ctx = dp.dotpe_create(0)
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    yield dp, ctx, bid, wl
+    dp.dotpe_bank_release(ctx, bid)
+    dp.dotpe_destroy(ctx)
+
+
+def submit(dp, ctx, bid, wl, precision, cut=20.0, flags=0, block_rows=BLOCK):
+    I = wl.bank.h.shape[0]
+    eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R, wl.ext.ln_w,
+                                n_phi=wl.event.n_phi, u_min=wl.event.u_min, cut_delta=cut,
+                                precision=precision, flags=flags, block_rows=block_rows)
+    dp.dotpe_event_wait(ctx, eid, 600.0)
+    return eid
+
+
+def evidence(dp, ctx, bid, wl, precision, **kw):
+    eid = submit(dp, ctx, bid, wl, precision, **kw)
+    ev = dp.dotpe_evidence(ctx, eid)
+    dp.dotpe_event_release(ctx, eid)
+    return ev
+
+
+def test_config3_served_path_against_fp32(big):
+    dp, ctx, bid, wl = big
+    ref = evidence(dp, ctx, bid, wl, "fp32")
+    got = evidence(dp, ctx, bid, wl, "mixed")
+    assert abs(got["ln_z"] - ref["ln_z"]) <= 1e-2
+    assert got["max_lnl_ml"] == pytest.approx(ref["max_lnl_ml"], abs=1e-3)
+    assert (got["arg_i"], got["arg_e"], got["arg_o"]) == (ref["arg_i"], ref["arg_e"], ref["arg_o"])
+    assert got["n_eff"] == pytest.approx(ref["n_eff"], rel=2e-2)
+    n_tiles = (wl.bank.h.shape[0] // 128) * (wl.ext.t.shape[0] // 32)
+    assert 0 < got["n_refined_tiles"] < n_tiles
+    # the peak of an SNR-30 injection: ln L^ML ~ SNR^2 / 2
+    assert 300.0 < ref["max_lnl_ml"] < 650.0
+
+
+def test_config3_block_streaming_matches_one_pass(big):
+    dp, ctx, bid, wl = big
+    for precision in ("fp32", "mixed"):
+        a = evidence(dp, ctx, bid, wl, precision, cut=0.0, block_rows=BLOCK)
+        b = evidence(dp, ctx, bid, wl, precision, cut=0.0, block_rows=0)
+        assert a["ln_z"] == pytest.approx(b["ln_z"], abs=1e-9), precision
+        for k in ("n_eff", "n_eff_int", "n_eff_ext"):
+            assert a[k] == pytest.approx(b[k], rel=1e-9), (precision, k)
+        assert (a["arg_i"], a["arg_e"], a["arg_o"]) == (b["arg_i"], b["arg_e"], b["arg_o"])
+        assert a["max_lnl_ml"] == b["max_lnl_ml"]
+
+
+def test_config3_sampled_pairs_against_oracle(big):
+    import oracle
+    dp, ctx, bid, wl = big
+    I, E = wl.bank.h.shape[0], wl.ext.t.shape[0]
+    rng = np.random.default_rng(33)
+    # row windows of 256 rows, two of them straddling block boundaries, plus the peak row
+    peak = evidence(dp, ctx, bid, wl, "fp32")
+    starts = [BLOCK - 128, 5 * BLOCK - 128, int(rng.integers(0, I - 256)), int(peak["arg_i"]) // 256 * 256]
+    res = {}
+    for precision in ("fp16x3", "mixed", "fp16"):
+        eid = submit(dp, ctx, bid, wl, precision, cut=0.0, flags=dp.DOTPE_FLAG_STORE_LNL)
+        rows = []
+        for s0 in starts:
+            lnl = dp.dotpe_lnl_blocks(ctx, eid, s0, s0 + 256, 0, E)
+            ml = dp.dotpe_lnl_blocks(ctx, eid, s0, s0 + 256, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+            rows.append((lnl, ml))
+        dp.dotpe_event_release(ctx, eid)
+        res[precision] = rows
+    # 600 pairs per window, plus the peak pair
+    pi, pe, win, loc = [], [], [], []
+    for w, s0 in enumerate(starts):
+        flat = rng.choice(256 * E, size=600, replace=False)
+        for f in flat:
+            pi.append(s0 + f // E)
+            pe.append(f % E)
+            win.append(w)
+            loc.append(f // E)
+    pi.append(int(peak["arg_i"]))
+    pe.append(int(peak["arg_e"]))
+    win.append(3)
+    loc.append(int(peak["arg_i"]) - starts[3])
+    pi, pe, win, loc = (np.array(x, dtype=np.int64) for x in (pi, pe, win, loc))
+    # the oracle on the sampled rows only (a sub-bank keeps the host memory small)
+    urows, inv = np.unique(pi, return_inverse=True)
+    sub = synth.Bank(**{**wl.bank.__dict__, "h": wl.bank.h[urows], "ln_w": wl.bank.ln_w[urows]})
+    P = oracle.OracleProblem(sub, wl.ext, wl.event)
+    ref = P.eval_pairs(inv, pe)
+    ml_ref = np.maximum(ref["lnl_ml_max"], 0.0)
+    dd = float(np.sum(4.0 * wl.bank.w[None, :] * np.abs(wl.event.data) ** 2 / wl.event.psd))
+    u = 2.0 ** -11
+    fp16_tol = 2e-2 + 4 * u * ml_ref + 2 * u * np.sqrt(2 * ml_ref + 1) * math.sqrt(dd)
+    for precision, rows in res.items():
+        lnl = np.array([rows[w][0][l, e] for w, l, e in zip(win, loc, pe)], dtype=np.float64)
+        ml = np.array([rows[w][1][l, e] for w, l, e in zip(win, loc, pe)], dtype=np.float64)
+        if precision == "fp16x3":
+            tol = np.full_like(ml_ref, 1e-3)
+        elif precision == "mixed":
+            tol = np.where(ml_ref >= ml_ref.max() - 30.0, 1e-3, fp16_tol)
+        else:
+            tol = fp16_tol
+        d1 = np.abs(lnl - ref["lnl_marg"])
+        d2 = np.abs(ml - ref["lnl_ml_max"])
+        assert np.all(np.isfinite(lnl))
+        assert np.all(d1 <= tol), (precision, float(d1.max()), float(ml_ref[np.argmax(d1 - tol)]))
+        assert np.all(d2 <= tol), (precision, float(d2.max()))
+    # the peak pair itself: ln L^ML ~ 450 to 1e-3 in split precision
+    assert abs(res["fp16x3"][3][1][loc[-1], pe[-1]] - ref["lnl_ml_max"][-1]) <= 1e-3
