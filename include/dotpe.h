@@ -94,11 +94,17 @@ enum {
 /* ---- structures -------------------------------------------------------- */
 typedef struct dotpe_ctx dotpe_ctx;
 
+/* context flags */
+#define DOTPE_CONFIG_AUTOTUNE 0x1  /* time candidate L2 tile bands on the first event of each shape */
+#define DOTPE_CONFIG_NO_GRAPHS 0x2 /* launch batches directly instead of as captured CUDA graphs */
+
 typedef struct dotpe_config {
   int device;                /* CUDA ordinal */
   uint64_t hbm_budget_bytes; /* device bytes the context may hold for banks + events; 0 = 90% of free */
-  int n_slots;               /* events that may run concurrently on the device (0 = 4) */
-  int flags;                 /* reserved, 0 */
+  int n_slots;               /* launches (events or batches) that may run concurrently (0 = 4) */
+  int flags;                 /* DOTPE_CONFIG_* */
+  int max_batch;             /* continuous batching: up to this many queued events of one bank and
+                                precision are admitted together as one batch (0 or 1: one at a time) */
 } dotpe_config;
 
 /* Intrinsic waveform bank on fixed bins (Sec. IV.C; h_{impb} stored on f_b only).
@@ -215,6 +221,22 @@ int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id);
  * device.  Errors: E_INVALID, E_NOT_FOUND (bank), E_ADMISSION (footprint larger
  * than the whole budget), E_NOMEM. */
 int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *desc, uint64_t *event_id);
+
+/* Queues n events that share one bank and one precision as one batch: they are
+ * admitted together (the sum of their footprints) and run as one launch
+ * sequence on one slot: every event's preparation, then one persistent fused
+ * tcgen05 launch per 64 events whose work items are the events' tiles one
+ * event after the other (mixed precision: one screening launch, one selection
+ * over the batch, one refinement launch), then every event's reduction.  The
+ * sequence is captured as a CUDA graph (unless DOTPE_CONFIG_NO_GRAPHS) whose
+ * executable is kept per slot and updated in place for the next batch.  Each
+ * event's results are those it gets when submitted alone (same tiles, same
+ * per-event reductions).  descs[k].block_rows must be 0.  event_ids: [n] out.
+ * The paper has no counterpart (it evaluates one event at a time, Sec. IV).
+ * Errors: as dotpe_event_submit for any event (then none is queued);
+ * E_INVALID (banks or precisions differ, block_rows != 0); E_ADMISSION (the
+ * batch can never fit the budget). */
+int dotpe_batch_submit(dotpe_ctx *ctx, int n, const dotpe_event_desc *descs, uint64_t *event_ids);
 
 /* Non-blocking state query; also admits queued events whose memory now fits.
  * stats may be NULL.  Errors: E_NOT_FOUND. */

@@ -29,6 +29,7 @@ DOTPE_E_UNSUPPORTED = -8
 
 DOTPE_PREC_FP32, DOTPE_PREC_BF16, DOTPE_PREC_FP16, DOTPE_PREC_BF16X3 = 0, 1, 2, 3
 DOTPE_PREC_FP16X3, DOTPE_PREC_MIXED = 4, 5
+DOTPE_CONFIG_AUTOTUNE, DOTPE_CONFIG_NO_GRAPHS = 0x1, 0x2
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4, "mixed": 5}
 DOTPE_C128, DOTPE_C64 = 0, 1
 DOTPE_FLAG_STORE_LNL = 0x1
@@ -42,7 +43,7 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_version", "dotpe_device_info", "dotpe_bank_load", "dotpe_bank_release",
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
-           "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc")
+           "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit")
 
 
 class DotpeError(RuntimeError):
@@ -57,7 +58,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class dotpe_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64),
-                ("n_slots", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("n_slots", ctypes.c_int), ("flags", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 class dotpe_bank_desc(ctypes.Structure):
@@ -117,6 +118,7 @@ def load(path: str = LIB_PATH):
         "dotpe_bank_load": ([vp, ctypes.POINTER(dotpe_bank_desc), u64p], ctypes.c_int),
         "dotpe_bank_release": ([vp, ctypes.c_uint64], ctypes.c_int),
         "dotpe_event_submit": ([vp, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
+        "dotpe_batch_submit": ([vp, ctypes.c_int, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
         "dotpe_event_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(dotpe_event_stats)], ctypes.c_int),
         "dotpe_event_wait": ([vp, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
@@ -160,9 +162,9 @@ def _host_c128(a):
 
 
 # ---- thin wrappers with the ABI's names ---------------------------------------
-def dotpe_create(device=0, hbm_budget_bytes=0, n_slots=0):
+def dotpe_create(device=0, hbm_budget_bytes=0, n_slots=0, flags=0, max_batch=0):
     L = load()
-    cfg = dotpe_config(device, hbm_budget_bytes, n_slots, 0)
+    cfg = dotpe_config(device, hbm_budget_bytes, n_slots, flags, max_batch)
     h = ctypes.c_void_p()
     _check(L.dotpe_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -218,13 +220,8 @@ def dotpe_bank_release(ctx, bank_id):
     return _check(load().dotpe_bank_release(ctx, bank_id))
 
 
-def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
-                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0):
-    """psd [D,B], data [D,B] complex, t [E,D], R [E,D,M] complex, ln_w_ext [E]: numpy (host)
-    or torch tensors (host or device; complex tensors as float64 views are accepted).
-    block_rows: 0, or a multiple of 128 to stream the slice through in bank blocks."""
-    L = load()
-    keep = []
+def _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
+                cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0):
 
     def arr(a, cplx=False):
         if a is None:
@@ -242,11 +239,32 @@ def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_p
     st = None
     if stream is not None:
         st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
-    desc = dotpe_event_desc(bank_id, i0, i1, D, arr(psd), arr(data, True), E, arr(t), arr(R, True),
+    return dotpe_event_desc(bank_id, i0, i1, D, arr(psd), arr(data, True), E, arr(t), arr(R, True),
                             arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st, block_rows)
+
+
+def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
+                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0):
+    """psd [D,B], data [D,B] complex, t [E,D], R [E,D,M] complex, ln_w_ext [E]: numpy (host)
+    or torch tensors (host or device; complex tensors as float64 views are accepted).
+    block_rows: 0, or a multiple of 128 to stream the slice through in bank blocks."""
+    keep = []
+    desc = _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext, n_phi, u_min, cut_delta,
+                       precision, flags, stream, block_rows)
     eid = ctypes.c_uint64()
-    _check(L.dotpe_event_submit(ctx, ctypes.byref(desc), ctypes.byref(eid)))
+    _check(load().dotpe_event_submit(ctx, ctypes.byref(desc), ctypes.byref(eid)))
     return eid.value
+
+
+def dotpe_batch_submit(ctx, specs):
+    """specs: list of dicts of dotpe_event_submit's keyword arguments (bank_id, i0, i1, psd,
+    data, t, R, ...), one per event; all share the bank and the precision.  Returns the ids."""
+    keep = []
+    n = len(specs)
+    descs = (dotpe_event_desc * n)(*[_event_desc(keep, **sp) for sp in specs])
+    ids = (ctypes.c_uint64 * n)()
+    _check(load().dotpe_batch_submit(ctx, n, descs, ids))
+    return list(ids)
 
 
 def dotpe_event_poll(ctx, event_id):

@@ -87,6 +87,7 @@ struct Event {
   int state = DOTPE_STATE_QUEUED;
   int64_t i0 = 0, NI = 0, NE = 0;
   int64_t block_rows = 0;  // rows per streamed bank block (0: the whole slice)
+  uint64_t group = 0;      // batch of dotpe_batch_submit (0: none)
   int D = 0, nphi = 0, prec = 0, flags = 0;
   double u_min = 0, cut = 0;
   bool has_lwe = false;
@@ -122,14 +123,19 @@ struct dotpe_ctx {
   char name[256] = {0};
   uint64_t budget = 0, used = 0;
   std::vector<cudaStream_t> streams;
-  std::vector<int> slot_busy;
+  std::vector<int> slot_busy;  // events in flight on each slot's stream
   cudaStream_t main_stream = nullptr, input_stream = nullptr;
   float4 *dm_table = nullptr;
   std::mutex mu;
   std::unordered_map<uint64_t, dotpe::Bank *> banks;
   std::unordered_map<uint64_t, dotpe::Event *> events;
   std::deque<uint64_t> queue;
-  uint64_t next_id = 1;
+  uint64_t next_id = 1, next_group = 1;
+  int max_batch = 1;     // queued events one fused launch may take (continuous batching)
+  bool use_graphs = true;  // batches run as captured CUDA graphs
+  bool autotune = false;   // time L2 band widths on first use of a shape
+  std::unordered_map<std::string, int> band_cache;                        // shape key -> band
+  std::vector<std::unordered_map<std::string, cudaGraphExec_t>> graphs;  // per slot
   double l2_band_bytes = 0;  // extrinsic operand kept in L2 per sweep of the bank
   // completion callbacks -> admission worker
   std::mutex cb_mu;
@@ -164,8 +170,8 @@ static void CUDART_CB mark_done(void *p) {
 // ---------------------------------------------------------------------------
 struct ScratchLayout {
   size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, sqrt_dd, gpack, mx, tile_part, tile_ml, tile_arg,
-      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, sel_counts, acc, acc_col, status, red,
-      total;
+      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, n_list_total, sel_counts, acc, acc_col,
+      status, red, total;
   int64_t block_rows;  // bank rows per streamed block (the whole slice when not streamed)
   int n_itile, n_etile, pack_kind, pack_planes, TI, TE;  // n_itile: tiles of one block
 };
@@ -218,8 +224,9 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.ml_running = c.take<float>(1);
   const bool mixed = (e.prec == DOTPE_PREC_MIXED);
   L.ml_refine = c.take<float>(1);
-  L.list = c.take<int>(mixed ? T : 0);
+  L.list = c.take<int2>(mixed ? T : 0);
   L.n_list = c.take<int>(1);
+  L.n_list_total = c.take<int>(1);
   L.sel_counts = c.take<int>(mixed ? select_count_blocks((int)T) : 0);
   L.acc = c.take<EvAcc>(1);
   L.acc_col = c.take<double2>(E);
@@ -236,17 +243,55 @@ static size_t keep_bytes_of(const Event &e) {
 }
 
 // ---------------------------------------------------------------------------
-// launch one admitted event on its slot stream
+// launching admitted events
 // ---------------------------------------------------------------------------
-static int run_event(dotpe_ctx *ctx, Event &e) {
-  cudaStream_t st = ctx->streams[e.slot];
-  Bank &b = *e.bank;
-  ScratchLayout L = scratch_layout(e);
-  e.scratch_bytes = L.total;
+// Device-side plan of one admitted event: its scratch, the prep arguments, the
+// epilogue parameters, its tensor-core work record and the reduction arguments.
+struct EventRun {
+  ScratchLayout L;
   uint8_t *scr = nullptr;
+  PrepArgs pa;
+  EpiParams P;
+  TcWork W;
+  ReduceArgs ra;
+  bool mixed = false;
+};
+
+// The bank operand map and the shape common to every event of a launch.
+static int tc_launch_of(dotpe_ctx *ctx, const Bank &b, int prec, TcLaunch &T) {
+  memset(&T, 0, sizeof(T));
+  const bool bf = prec_bf16(prec);
+  const int64_t a_rows = 2 * (int64_t)b.M * b.I;
+  if (a_rows >= (1ll << 31)) return fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
+  CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  void *abase = bf ? (void *)b.bf : (void *)b.hf;
+  if (encode_tmap_kblocks(&T.mapA, dt, abase, a_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, TC_TI,
+                          tc_kblocks_per_stage()))
+    return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (bank)");
+  T.C.kb = b.Kpad / 64;
+  T.C.a_plane_rows = b.M * (int)b.I;
+  T.C.a_mode_rows = (int)b.I;
+  T.C.n_modes = b.M;
+  T.bf16 = bf;
+  T.split = prec_split(prec) && prec != DOTPE_PREC_MIXED;
+  T.consec = true;
+  for (int m = 1; m < b.M; ++m)
+    if (b.mode_m[m] != b.mode_m[m - 1] + 1) T.consec = false;
+  T.n_sms = ctx->n_sms;
+  return DOTPE_OK;
+}
+
+// L2 band width of an event: tuned value if the autotuner has one, else the default.
+static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bool split);
+
+// Device allocations of an event and every pointer of its plan (no launches).
+static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
+  Bank &b = *e.bank;
+  R.L = scratch_layout(e);
+  const ScratchLayout &L = R.L;
+  e.scratch_bytes = L.total;
   CUDA_OR_FAIL(cudaStreamWaitEvent(st, e.ev_inputs, 0));
-  CUDA_OR_FAIL(cudaMallocAsync((void **)&scr, L.total, st));
-  // keep block
+  CUDA_OR_FAIL(cudaMallocAsync((void **)&R.scr, L.total, st));
   e.keep_bytes = keep_bytes_of(e);
   uint8_t *keep = nullptr;
   CUDA_OR_FAIL(cudaMallocAsync((void **)&keep, e.keep_bytes, st));
@@ -261,13 +306,9 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
       e.ml_tile = (float *)(keep + c.take<float>((size_t)e.NI * e.NE));
     }
   }
-  CUDA_OR_FAIL(cudaMemsetAsync(scr + L.gmax, 0, 4, st));
-  CUDA_OR_FAIL(cudaMemsetAsync(scr + L.ml_running, 0, 4, st));
-  CUDA_OR_FAIL(cudaMemsetAsync(scr + L.status, 0, 4, st));
-  CUDA_OR_FAIL(cudaEventRecord(e.ev_start, st));
-
+  uint8_t *scr = R.scr;
   int *status = (int *)(scr + L.status);
-  PrepArgs pa;
+  PrepArgs &pa = R.pa;
   pa.D = e.D; pa.B = b.B; pa.M = b.M; pa.Kpad = b.Kpad; pa.E = e.NE;
   pa.f = b.f; pa.w = b.w; pa.psd = e.psd; pa.data = e.data; pa.t = e.t; pa.R = e.R;
   pa.c = (float2 *)(scr + L.c);
@@ -286,10 +327,8 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   pa.gscale = (float *)(scr + L.gscale);
   pa.sqrt_dd = (float *)(scr + L.sqrt_dd);
   pa.status = status;
-  launch_prep(pa, st);
-  float *mx = (float *)(scr + L.mx);
 
-  EpiParams P;
+  EpiParams &P = R.P;
   memset(&P, 0, sizeof(P));
   P.n_modes = b.M;
   P.n_det = e.D;
@@ -308,7 +347,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   P.cut_delta = (float)(e.cut > 0 ? e.cut : 0.0);
   P.ln_nphi = (float)std::log((double)e.nphi);
   P.n_ext = e.NE;
-  P.mx = mx;
+  P.mx = (float *)(scr + L.mx);
   P.qx = pa.qx;
   P.lw_ext = e.has_lwe ? e.lwe : nullptr;
   P.dm_table = ctx->dm_table;
@@ -325,40 +364,29 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   P.gemm_only = (e.flags & DOTPE_FLAG_GEMM_ONLY) ? 1 : 0;
   P.test_stall = (e.flags & DOTPE_FLAG_TEST_STALL) ? 1 : 0;
   P.wait_ns = P.test_stall ? 250000000ull : 4000000000ull;
-  const bool mixed = (e.prec == DOTPE_PREC_MIXED);
-
-  // tensor-core operand maps (the whole bank and the event's packed G)
-  TcArgs g;
-  memset(&g, 0, sizeof(g));
+  R.mixed = (e.prec == DOTPE_PREC_MIXED);
   if (e.prec != DOTPE_PREC_FP32) {
-    const bool bf = prec_bf16(e.prec);
-    g.bf16 = bf;
-    g.kb_per_mode = b.Kpad / 64;
-    g.n_sms = ctx->n_sms;
-    const int64_t a_rows = 2 * (int64_t)b.M * b.I;
-    const int64_t b_rows = (int64_t)L.pack_planes * b.M * 2 * e.NE;
-    if (a_rows >= (1ll << 31) || b_rows >= (1ll << 31))
-      return fail(DOTPE_E_UNSUPPORTED, "operand too large for 32-bit TMA coordinates");
-    CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    void *abase = bf ? (void *)b.bf : (void *)b.hf;
-    g.n_modes = b.M;
-    g.l2_band_bytes = ctx->l2_band_bytes;
-    const int kbx = tc_kblocks_per_stage();
-    if (encode_tmap_kblocks(&g.mapA, dt, abase, a_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, TC_TI, kbx) ||
-        encode_tmap_kblocks(&g.mapB, dt, pa.gpack, b_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, 2 * TC_TE, kbx))
-      return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed");
-    g.a_plane_rows = b.M * (int)b.I;
-    g.a_mode_rows = (int)b.I;
-    g.b_plane_rows = b.M * 2 * (int)e.NE;
-    g.b_mode_rows = 2 * (int)e.NE;
-    P.z_scale = 1.f / b.a_scale;
+    P.z_scale = 1.f / (b.a_scale * (prec_bf16(e.prec) ? 1.f : FP16_OPERAND_SCALE));
     P.g_scale = pa.gscale;
+    TcWork &W = R.W;
+    memset(&W, 0, sizeof(W));
+    const bool bf = prec_bf16(e.prec);
+    const int64_t b_rows = (int64_t)L.pack_planes * b.M * 2 * e.NE;
+    if (b_rows >= (1ll << 31)) return fail(DOTPE_E_UNSUPPORTED, "n_ext too large for 32-bit TMA coordinates");
+    CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    if (encode_tmap_kblocks(&W.mapB, dt, pa.gpack, b_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, 2 * TC_TE,
+                            tc_kblocks_per_stage()))
+      return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (extrinsic operand)");
+    W.n_etile = L.n_etile;
+    W.band = event_band(ctx, e, L, prec_split(e.prec));
+    W.b_plane_rows = b.M * 2 * (int)e.NE;
+    W.b_mode_rows = 2 * (int)e.NE;
   } else {
     P.z_scale = 1.f;
     P.g_scale = nullptr;
   }
 
-  ReduceArgs ra;
+  ReduceArgs &ra = R.ra;
   memset(&ra, 0, sizeof(ra));
   ra.n_ext = e.NE;
   ra.n_int_total = e.NI;
@@ -370,7 +398,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   ra.tile_ml = P.tile_ml;
   ra.tile_arg = P.tile_arg;
   ra.tile_npass = P.tile_npass;
-  ra.ml_running = mixed ? (const float *)(scr + L.ml_refine) : P.ml_running;
+  ra.ml_running = R.mixed ? (const float *)(scr + L.ml_refine) : P.ml_running;
   ra.cut_delta = P.cut_delta;
   ra.ln_p_int = e.ln_p_int;
   ra.ln_p_ext = e.ln_p_ext;
@@ -379,88 +407,368 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   ra.status = status;
   ra.scratch = scr + L.red;
   ra.out = e.d_out;
-  ra.n_refined = mixed ? (const int *)(scr + L.n_list) : nullptr;
+  ra.n_refined = R.mixed ? (const int *)(scr + L.n_list) : nullptr;
+  return DOTPE_OK;
+}
 
-  // the slice in bank blocks of L.block_rows rows: cross terms, fused kernel(s),
-  // then the block's partials merged into the FP64 accumulators
-  const int n_blocks = (int)((e.NI + L.block_rows - 1) / L.block_rows);
-  for (int k = 0; k < n_blocks; ++k) {
-    const int64_t r0 = (int64_t)k * L.block_rows;
-    const int64_t nr = std::min<int64_t>(L.block_rows, e.NI - r0);
-    launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, pa.omega, mx, ctx->n_sms, st);
-    P.n_int = nr;
-    P.i_base = e.i0 + r0;
-    P.lw_int = b.lw ? b.lw + e.i0 + r0 : nullptr;
-    P.lnl_tile = e.lnl_tile ? e.lnl_tile + r0 * e.NE : nullptr;
-    P.ml_tile = e.ml_tile ? e.ml_tile + r0 * e.NE : nullptr;
-    if (k == 0) CUDA_OR_FAIL(cudaEventRecord(e.ev_k0, st));
-    if (e.prec == DOTPE_PREC_FP32) {
-      SimtArgs sg;
-      sg.A = b.master;
-      sg.Bm = (const float *)pa.gpack;
-      sg.I_bank = b.I;
-      sg.Kpad = b.Kpad;
-      sg.K = 2 * b.B;
-      launch_simt(sg, P, st);
-    } else {
-      g.a_row0 = (int)(e.i0 + r0);
-      g.list = nullptr;
-      g.n_list = nullptr;
-      g.n_pass = prec_split(e.prec) ? 3 : 1;  // hi*hi (+ hi*lo + lo*hi)
-      EpiParams Pf = P;
-      if (mixed) {
-        // screening pass: one fp16 product for every pair, best ln L^ML per tile
-        // (with the cut off, the full single-pass epilogue)
-        EpiParams Ps = P;
-        Ps.track_max = 1;
-        Ps.screen_ml = (P.cut_delta > 0.f) ? 1 : 0;
-        Ps.margin_k = MIXED_MARGIN_K;
-        g.n_pass = 1;
-        int r = launch_tc(g, Ps, st);
-        if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
-        if (k == n_blocks - 1) CUDA_OR_FAIL(cudaEventRecord(e.ev_ks, st));
-        // the tiles that can reach the cut (or, with the cut off, within the far window)
-        SelectArgs sa;
-        sa.tile_ml = P.tile_ml;
-        sa.n_itile = (int)((nr + TC_TI - 1) / TC_TI);
-        sa.n_etile = L.n_etile;
-        g.n_pass = 3;
-        sa.band = tc_band(g, L.n_etile);
-        sa.ml_screen = P.ml_running;
-        sa.sqrt_dd = pa.sqrt_dd;
-        sa.window = (P.cut_delta > 0.f) ? P.cut_delta : MIXED_FAR_WINDOW;
-        sa.margin_k = MIXED_MARGIN_K;
-        sa.ml_refine = (float *)(scr + L.ml_refine);
-        sa.list = (int *)(scr + L.list);
-        sa.n_list = (int *)(scr + L.n_list);
-        sa.counts = (int *)(scr + L.sel_counts);
-        launch_select(sa, st);
-        CUDA_OR_FAIL(cudaGetLastError());
-        // refinement: split precision on the selected tiles, threshold frozen at
-        // (screened maximum - margin) - cut_delta, a lower bound of the exact cut
-        Pf.ml_running = sa.ml_refine;
-        Pf.track_max = 0;
-        g.list = sa.list;
-        g.n_list = sa.n_list;
-      }
-      int r = launch_tc(g, Pf, st);
-      if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
-    }
-    if (k == n_blocks - 1) CUDA_OR_FAIL(cudaEventRecord(e.ev_k1, st));
-    ra.n_int = nr;
-    ra.row_offset = r0;
-    ra.n_itile = (int)((nr + L.TI - 1) / L.TI);
-    ra.first = (k == 0);
-    launch_reduce_block(ra, st);
+// Stream work before the fused kernel: zeroed scalars, data weights, extrinsic operand.
+static int event_begin(Event &e, EventRun &R, cudaStream_t st) {
+  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.gmax, 0, 4, st));
+  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
+  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.status, 0, 4, st));
+  CUDA_OR_FAIL(cudaEventRecord(e.ev_start, st));
+  launch_prep(R.pa, st);
+  return DOTPE_OK;
+}
+
+// Rows [r0, r0 + nr) of the slice as the current bank block of the plan.
+static void event_block(dotpe_ctx *ctx, Event &e, EventRun &R, int64_t r0, int64_t nr, cudaStream_t st) {
+  Bank &b = *e.bank;
+  launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, (float *)(R.scr + R.L.mx),
+                     ctx->n_sms, st);
+  R.P.n_int = nr;
+  R.P.i_base = e.i0 + r0;
+  R.P.lw_int = b.lw ? b.lw + e.i0 + r0 : nullptr;
+  R.P.lnl_tile = e.lnl_tile ? e.lnl_tile + r0 * e.NE : nullptr;
+  R.P.ml_tile = e.ml_tile ? e.ml_tile + r0 * e.NE : nullptr;
+  R.W.n_itile = (int)((nr + TC_TI - 1) / TC_TI);
+  R.W.a_row0 = (int)(e.i0 + r0);
+  R.ra.n_int = nr;
+  R.ra.row_offset = r0;
+  R.ra.n_itile = (int)((nr + R.L.TI - 1) / R.L.TI);
+}
+
+// Screening variant of an event's parameters (mixed precision).
+static EpiParams screen_params(const EventRun &R) {
+  EpiParams Ps = R.P;
+  Ps.track_max = 1;
+  Ps.screen_ml = (R.P.cut_delta > 0.f) ? 1 : 0;
+  Ps.margin_k = MIXED_MARGIN_K;
+  return Ps;
+}
+
+static SelectEvent select_event_of(const EventRun &R) {
+  SelectEvent v;
+  v.tile_ml = R.P.tile_ml;
+  v.n_itile = R.W.n_itile;
+  v.n_etile = R.W.n_etile;
+  v.band = R.W.band;
+  v.ml_screen = R.P.ml_running;
+  v.sqrt_dd = R.pa.sqrt_dd;
+  v.window = (R.P.cut_delta > 0.f) ? R.P.cut_delta : MIXED_FAR_WINDOW;
+  v.margin_k = MIXED_MARGIN_K;
+  v.ml_refine = (float *)(R.scr + R.L.ml_refine);
+  v.n_refined = (int *)(R.scr + R.L.n_list);
+  return v;
+}
+
+// Refinement variant: threshold frozen at (screened maximum - margin) - cut_delta.
+static EpiParams refine_params(const EventRun &R) {
+  EpiParams Pf = R.P;
+  Pf.ml_running = (float *)(R.scr + R.L.ml_refine);
+  Pf.track_max = 0;
+  return Pf;
+}
+
+// The fused kernel(s) of the current block of one event (mixed: screen,
+// selection, refinement over the event's own list).
+static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, cudaStream_t st) {
+  Bank &b = *e.bank;
+  if (e.prec == DOTPE_PREC_FP32) {
+    SimtArgs sg;
+    sg.A = b.master;
+    sg.Bm = (const float *)R.pa.gpack;
+    sg.I_bank = b.I;
+    sg.Kpad = b.Kpad;
+    sg.K = 2 * b.B;
+    launch_simt(sg, R.P, st);
+    return DOTPE_OK;
   }
-  launch_reduce_final(ra, st);
+  TcLaunch T;
+  int rc = tc_launch_of(ctx, b, e.prec, T);
+  if (rc != DOTPE_OK) return rc;
+  TcWork W = R.W;
+  if (!R.mixed) {
+    W.P = R.P;
+    int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
+    if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+    return DOTPE_OK;
+  }
+  W.P = screen_params(R);
+  int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
+  if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+  if (last_block) CUDA_OR_FAIL(cudaEventRecord(e.ev_ks, st));
+  SelectBatch sb;
+  memset(&sb, 0, sizeof(sb));
+  sb.ev[0] = select_event_of(R);
+  sb.begin[0] = 0;
+  sb.begin[1] = R.W.n_itile * R.W.n_etile;
+  sb.n = 1;
+  sb.list = (int2 *)(R.scr + R.L.list);
+  sb.n_list = (int *)(R.scr + R.L.n_list_total);
+  sb.counts = (int *)(R.scr + R.L.sel_counts);
+  launch_select(sb, st);
+  CUDA_OR_FAIL(cudaGetLastError());
+  W.P = refine_params(R);
+  T.split = true;
+  r = launch_tc(T, &W, 1, sb.list, sb.n_list, st);
+  if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+  return DOTPE_OK;
+}
+
+// After the last block: evidence, copy to the host, completion callback.
+static int event_end(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
+  launch_reduce_final(R.ra, st);
   CUDA_OR_FAIL(cudaGetLastError());
   CUDA_OR_FAIL(cudaMemcpyAsync(e.h_out, e.d_out, sizeof(ReduceOut), cudaMemcpyDeviceToHost, st));
   CUDA_OR_FAIL(cudaEventRecord(e.ev_end, st));
   CUDA_OR_FAIL(cudaLaunchHostFunc(st, mark_done, new DoneArg{ctx, e.id}));
-  CUDA_OR_FAIL(cudaFreeAsync(scr, st));
+  return DOTPE_OK;
+}
+
+static int event_free(Event &e, EventRun &R, cudaStream_t st) {
+  CUDA_OR_FAIL(cudaFreeAsync(R.scr, st));
   CUDA_OR_FAIL(cudaFreeAsync(e.in_block, st));
   e.in_block = nullptr;
+  R.scr = nullptr;
+  return DOTPE_OK;
+}
+
+static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st);
+
+// One event on its slot stream, its slice in bank blocks.
+static int run_event(dotpe_ctx *ctx, Event &e) {
+  cudaStream_t st = ctx->streams[e.slot];
+  EventRun R;
+  int rc = event_alloc(ctx, e, st, R);
+  if (rc != DOTPE_OK) return rc;
+  if ((rc = event_begin(e, R, st)) != DOTPE_OK) return rc;
+  const int64_t BR = R.L.block_rows;
+  const int n_blocks = (int)((e.NI + BR - 1) / BR);
+  for (int k = 0; k < n_blocks; ++k) {
+    const int64_t r0 = (int64_t)k * BR;
+    event_block(ctx, e, R, r0, std::min<int64_t>(BR, e.NI - r0), st);
+    if (k == 0 && ctx->autotune && (rc = autotune_band(ctx, e, R, st)) != DOTPE_OK) return rc;
+    if (k == 0) CUDA_OR_FAIL(cudaEventRecord(e.ev_k0, st));
+    if ((rc = event_fused(ctx, e, R, k == n_blocks - 1, st)) != DOTPE_OK) return rc;
+    if (k == n_blocks - 1) CUDA_OR_FAIL(cudaEventRecord(e.ev_k1, st));
+    R.ra.first = (k == 0);
+    launch_reduce_block(R.ra, st);
+  }
+  if ((rc = event_end(ctx, e, R, st)) != DOTPE_OK) return rc;
+  return event_free(e, R, st);
+}
+
+// ---------------------------------------------------------------------------
+// L2 band autotuner.  The fused kernel walks the extrinsic tiles in bands: every
+// bank tile meets the band's extrinsic tiles before the next band starts, so the
+// band's operand stays in L2 while the bank streams once per band.  The best
+// band width depends on the operand sizes and on how the two L2 partitions
+// share lines; it is chosen per shape (precision class, modes, k-blocks,
+// extrinsic tiles) by timing candidate widths on the first event of that shape.
+// ---------------------------------------------------------------------------
+static std::string band_key(const Event &e, const ScratchLayout &L, bool split) {
+  char buf[96];
+  snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d", prec_bf16(e.prec) ? 1 : 0, split ? 1 : 0, e.bank->M, e.bank->Kpad,
+           L.n_etile);
+  return buf;
+}
+
+static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bool split) {
+  auto it = ctx->band_cache.find(band_key(e, L, split));
+  if (it != ctx->band_cache.end()) return std::min(it->second, L.n_etile);
+  return tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, split, L.n_etile);
+}
+
+// Times the event's first fused launch at candidate band widths (the event's
+// own inputs, prepared on `st`); the results of these runs are overwritten by
+// the real launch that follows.  Blocks the calling thread once per shape.
+static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
+  const bool split_main = prec_split(e.prec) && e.prec != DOTPE_PREC_MIXED;
+  const std::string key = band_key(e, R.L, prec_split(e.prec));
+  if (e.prec == DOTPE_PREC_FP32 || ctx->band_cache.count(key)) return DOTPE_OK;
+  TcLaunch T;
+  int rc = tc_launch_of(ctx, *e.bank, e.prec, T);
+  if (rc != DOTPE_OK) return rc;
+  T.split = split_main;
+  std::vector<int> cand;
+  for (int c = 1; c < R.W.n_etile; c *= 2) cand.push_back(c);
+  cand.push_back(R.W.n_etile);
+  const int dflt = tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, prec_split(e.prec), R.L.n_etile);
+  if (std::find(cand.begin(), cand.end(), dflt) == cand.end()) cand.push_back(dflt);
+  std::vector<cudaEvent_t> ev(cand.size() + 1);
+  for (auto &x : ev) CUDA_OR_FAIL(cudaEventCreate(&x));
+  TcWork W = R.W;
+  W.P = R.mixed ? screen_params(R) : R.P;
+  // warm-up at the default width, then one timed launch per candidate
+  W.band = dflt;
+  int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
+  CUDA_OR_FAIL(cudaEventRecord(ev[0], st));
+  for (size_t c = 0; c < cand.size() && r == 0; ++c) {
+    W.band = cand[c];
+    r = launch_tc(T, &W, 1, nullptr, nullptr, st);
+    CUDA_OR_FAIL(cudaEventRecord(ev[c + 1], st));
+  }
+  if (r != 0) return fail(DOTPE_E_DEVICE, "autotune launch failed: %s", cudaGetErrorString((cudaError_t)r));
+  CUDA_OR_FAIL(cudaEventSynchronize(ev.back()));
+  int best = dflt;
+  float best_ms = 1e30f;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    float ms = 0.f;
+    CUDA_OR_FAIL(cudaEventElapsedTime(&ms, ev[c], ev[c + 1]));
+    if (ms < best_ms) { best_ms = ms; best = cand[c]; }
+  }
+  for (auto &x : ev) cudaEventDestroy(x);
+  ctx->band_cache[key] = best;
+  R.W.band = best;
+  // the tuning runs raised the running maximum: start the real launch afresh
+  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
+  return DOTPE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A batch of events over one bank in one launch sequence: every event's prep,
+// then one persistent fused launch per TC_MAXB events (mixed: screen, one
+// selection over the batch, refinement), then every event's reduction.  With
+// graphs on, the sequence is captured once per launch and replayed through a
+// per-slot executable graph updated in place when the topology repeats.
+// ---------------------------------------------------------------------------
+static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) {
+  cudaStream_t st = ctx->streams[slot];
+  const int n = (int)evs.size();
+  std::vector<EventRun> R(n);
+  for (int k = 0; k < n; ++k) {
+    int rc = event_alloc(ctx, *evs[k], st, R[k]);
+    if (rc != DOTPE_OK) return rc;
+  }
+  const int prec = evs[0]->prec;
+  const bool mixed = (prec == DOTPE_PREC_MIXED);
+  int total_tiles = 0;
+  for (int k = 0; k < n; ++k) total_tiles += (int)((evs[k]->NI + TC_TI - 1) / TC_TI) * R[k].L.n_etile;
+  // batch-wide (event, tile) list of the refinement
+  uint8_t *blist = nullptr;
+  size_t o_list = 0, o_n = 0, o_counts = 0;
+  if (mixed) {
+    Carver c;
+    o_list = c.take<int2>(total_tiles);
+    o_n = c.take<int>(1);
+    o_counts = c.take<int>(select_count_blocks(total_tiles));
+    CUDA_OR_FAIL(cudaMallocAsync((void **)&blist, c.off, st));
+  }
+  TcLaunch T;
+  if (prec != DOTPE_PREC_FP32) {
+    int rc = tc_launch_of(ctx, *evs[0]->bank, prec, T);
+    if (rc != DOTPE_OK) return rc;
+  }
+  const bool capture = ctx->use_graphs;
+  if (capture) CUDA_OR_FAIL(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = DOTPE_OK;
+  auto body = [&]() -> int {
+    for (int k = 0; k < n; ++k) {
+      int r = event_begin(*evs[k], R[k], st);
+      if (r != DOTPE_OK) return r;
+      event_block(ctx, *evs[k], R[k], 0, evs[k]->NI, st);
+      CUDA_OR_FAIL(cudaEventRecord(evs[k]->ev_k0, st));
+    }
+    if (prec == DOTPE_PREC_FP32) {
+      for (int k = 0; k < n; ++k) {
+        int r = event_fused(ctx, *evs[k], R[k], true, st);
+        if (r != DOTPE_OK) return r;
+      }
+    } else {
+      std::vector<TcWork> W(n);
+      for (int k0 = 0; k0 < n; k0 += TC_MAXB) {
+        const int m = std::min(TC_MAXB, n - k0);
+        for (int k = k0; k < k0 + m; ++k) {
+          W[k] = R[k].W;
+          W[k].P = mixed ? screen_params(R[k]) : R[k].P;
+        }
+        TcLaunch T1 = T;
+        T1.split = prec_split(prec) && !mixed;
+        int r = launch_tc(T1, &W[k0], m, nullptr, nullptr, st);
+        if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
+      }
+      if (mixed) {
+        for (int k = 0; k < n; ++k) CUDA_OR_FAIL(cudaEventRecord(evs[k]->ev_ks, st));
+        int2 *glist = (int2 *)(blist + o_list);
+        int *gn = (int *)(blist + o_n);
+        for (int k0 = 0; k0 < n; k0 += TC_MAXB) {
+          const int m = std::min(TC_MAXB, n - k0);
+          SelectBatch sb;
+          memset(&sb, 0, sizeof(sb));
+          int b0 = 0;
+          for (int k = 0; k < m; ++k) {
+            sb.ev[k] = select_event_of(R[k0 + k]);
+            sb.begin[k] = b0;
+            b0 += R[k0 + k].W.n_itile * R[k0 + k].W.n_etile;
+          }
+          sb.begin[m] = b0;
+          sb.n = m;
+          sb.list = glist;
+          sb.n_list = gn;
+          sb.counts = (int *)(blist + o_counts);
+          launch_select(sb, st);
+          CUDA_OR_FAIL(cudaGetLastError());
+          for (int k = k0; k < k0 + m; ++k) W[k].P = refine_params(R[k]);
+          TcLaunch T2 = T;
+          T2.split = true;
+          int r = launch_tc(T2, &W[k0], m, glist, gn, st);
+          if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
+        }
+      }
+    }
+    for (int k = 0; k < n; ++k) {
+      CUDA_OR_FAIL(cudaEventRecord(evs[k]->ev_k1, st));
+      R[k].ra.first = 1;
+      launch_reduce_block(R[k].ra, st);
+      int r = event_end(ctx, *evs[k], R[k], st);
+      if (r != DOTPE_OK) return r;
+    }
+    return DOTPE_OK;
+  };
+  rc = body();
+  if (capture) {
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (rc != DOTPE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return fail(DOTPE_E_DEVICE, "graph capture: %s", cudaGetErrorString(ce));
+    char key[64];
+    snprintf(key, sizeof(key), "%d/%d", n, prec);
+    auto &cache = ctx->graphs[slot];
+    auto it = cache.find(key);
+    bool ok = false;
+    if (it != cache.end()) {
+      cudaGraphExecUpdateResultInfo info;
+      ok = cudaGraphExecUpdate(it->second, g, &info) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(it->second);
+        cache.erase(it);
+      }
+    }
+    if (!ok) {
+      cudaGraphExec_t x = nullptr;
+      cudaError_t ie = cudaGraphInstantiate(&x, g, 0);
+      if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(DOTPE_E_DEVICE, "graph instantiate: %s", cudaGetErrorString(ie));
+      }
+      cache[key] = x;
+    }
+    cudaError_t le = cudaGraphLaunch(cache[key], st);
+    cudaGraphDestroy(g);
+    if (le != cudaSuccess) return fail(DOTPE_E_DEVICE, "graph launch: %s", cudaGetErrorString(le));
+  } else if (rc != DOTPE_OK) {
+    return rc;
+  }
+  for (int k = 0; k < n; ++k) {
+    int r = event_free(*evs[k], R[k], st);
+    if (r != DOTPE_OK) return r;
+  }
+  if (blist) CUDA_OR_FAIL(cudaFreeAsync(blist, st));
   return DOTPE_OK;
 }
 
@@ -487,7 +795,7 @@ static void progress(dotpe_ctx *ctx) {
         if (cudaEventElapsedTime(&ms, e.ev_k0, e.ev_k1) == cudaSuccess) e.fused_ms = ms;
         if (e.prec == DOTPE_PREC_MIXED && cudaEventElapsedTime(&ms, e.ev_ks, e.ev_k1) == cudaSuccess) e.refine_ms = ms;
         if (e.t_done == 0) e.t_done = now_ns();
-        ctx->slot_busy[e.slot] = 0;
+        ctx->slot_busy[e.slot]--;
         ctx->used -= e.scratch_bytes + e.in_bytes;
         e.scratch_bytes = 0;
         e.in_bytes = 0;
@@ -498,7 +806,7 @@ static void progress(dotpe_ctx *ctx) {
       } else if (q != cudaErrorNotReady) {
         cudaGetLastError();
         e.state = DOTPE_STATE_FAILED;
-        ctx->slot_busy[e.slot] = 0;
+        ctx->slot_busy[e.slot]--;
       }
     }
   }
@@ -517,16 +825,44 @@ static void progress(dotpe_ctx *ctx) {
         break;
       }
     if (slot < 0) break;
+    // the launch unit: a submitted batch, or (continuous batching) the queued
+    // events of the same bank and precision behind the head, as far as they fit
+    std::vector<Event *> grp{&e};
     size_t need = scratch_layout(e).total + keep_bytes_of(e);
+    auto batchable = [&](const Event &x) {
+      return x.group == 0 && x.bank == e.bank && x.prec == e.prec && x.block_rows == 0 &&
+             !(x.flags & DOTPE_FLAG_TEST_STALL);
+    };
+    if (e.group != 0) {
+      for (size_t q = 1; q < ctx->queue.size(); ++q) {
+        auto jt = ctx->events.find(ctx->queue[q]);
+        if (jt == ctx->events.end() || jt->second->group != e.group) break;
+        grp.push_back(jt->second);
+        need += scratch_layout(*jt->second).total + keep_bytes_of(*jt->second);
+      }
+    } else if (ctx->max_batch > 1 && batchable(e)) {
+      for (size_t q = 1; q < ctx->queue.size() && (int)grp.size() < ctx->max_batch; ++q) {
+        auto jt = ctx->events.find(ctx->queue[q]);
+        if (jt == ctx->events.end() || !batchable(*jt->second)) break;
+        const size_t more = scratch_layout(*jt->second).total + keep_bytes_of(*jt->second);
+        if (ctx->used + need + more > ctx->budget) break;
+        grp.push_back(jt->second);
+        need += more;
+      }
+    }
     if (ctx->used + need > ctx->budget) break;
-    ctx->queue.pop_front();
-    e.slot = slot;
-    ctx->slot_busy[slot] = 1;
+    for (size_t q = 0; q < grp.size(); ++q) ctx->queue.pop_front();
     ctx->used += need;
-    e.t_admit = now_ns();
-    e.state = DOTPE_STATE_RUNNING;
-    if (run_event(ctx, e) != DOTPE_OK) {
-      e.state = DOTPE_STATE_FAILED;
+    const int64_t t_admit = now_ns();
+    for (Event *x : grp) {
+      x->slot = slot;
+      x->t_admit = t_admit;
+      x->state = DOTPE_STATE_RUNNING;
+    }
+    ctx->slot_busy[slot] = (int)grp.size();
+    const int rc = (grp.size() == 1 && e.group == 0) ? run_event(ctx, e) : run_batch(ctx, grp, slot);
+    if (rc != DOTPE_OK) {
+      for (Event *x : grp) x->state = DOTPE_STATE_FAILED;
       ctx->slot_busy[slot] = 0;
     }
   }
@@ -547,7 +883,7 @@ static void free_event(dotpe_ctx *ctx, Event *e) {
   size_t give = e->keep_bytes + e->scratch_bytes + e->in_bytes;
   if (e->state == DOTPE_STATE_QUEUED) give = e->in_bytes;
   ctx->used = (ctx->used >= give) ? ctx->used - give : 0;
-  if (e->slot >= 0 && e->state == DOTPE_STATE_RUNNING) ctx->slot_busy[e->slot] = 0;
+  if (e->slot >= 0 && e->state == DOTPE_STATE_RUNNING) ctx->slot_busy[e->slot]--;
   if (e->bank) e->bank->refs--;
   delete e;
 }
@@ -609,6 +945,10 @@ int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
   if (const char *v = getenv("DOTPE_L2_BAND_MB")) ctx->l2_band_bytes = atof(v) * 1048576.0;
 
   int ns = c.n_slots > 0 ? c.n_slots : 4;
+  ctx->max_batch = c.max_batch > 1 ? c.max_batch : 1;
+  ctx->autotune = (c.flags & DOTPE_CONFIG_AUTOTUNE) != 0;
+  ctx->use_graphs = (c.flags & DOTPE_CONFIG_NO_GRAPHS) == 0;
+  ctx->graphs.resize(ns);
   ctx->streams.resize(ns);
   ctx->slot_busy.assign(ns, 0);
   for (int s = 0; s < ns; ++s) cudaStreamCreateWithFlags(&ctx->streams[s], cudaStreamNonBlocking);
@@ -671,6 +1011,8 @@ int dotpe_destroy(dotpe_ctx *ctx) {
   }
   cudaDeviceSynchronize();
   cudaFree(ctx->dm_table);
+  for (auto &m : ctx->graphs)
+    for (auto &kv : m) cudaGraphExecDestroy(kv.second);
   for (auto s : ctx->streams) cudaStreamDestroy(s);
   cudaStreamDestroy(ctx->main_stream);
   cudaStreamDestroy(ctx->input_stream);
@@ -805,10 +1147,12 @@ int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id) {
   return DOTPE_OK;
 }
 
-int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *event_id) {
-  if (!ctx || !d || !event_id) return fail(DOTPE_E_INVALID, "null argument");
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+}  // extern "C"
+
+// Validates one descriptor, copies its inputs into device memory and queues the
+// event (caller holds ctx->mu).  group != 0 marks the events of one batch.
+static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t group, uint64_t *event_id) {
+  if (!d) return fail(DOTPE_E_INVALID, "null descriptor");
   auto bit = ctx->banks.find(d->bank_id);
   if (bit == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)d->bank_id);
   Bank *b = bit->second;
@@ -839,6 +1183,7 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   e->u_min = d->u_min;
   e->cut = d->cut_delta;
   e->has_lwe = d->ln_w_ext != nullptr;
+  e->group = group;
   // footprint check against the whole budget
   size_t need = scratch_layout(*e).total + keep_bytes_of(*e);
   Carver c;
@@ -924,8 +1269,62 @@ int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *even
   ctx->events[e->id] = e;
   ctx->queue.push_back(e->id);
   *event_id = e->id;
+  return DOTPE_OK;
+}
+
+extern "C" {
+
+int dotpe_event_submit(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t *event_id) {
+  if (!ctx || !d || !event_id) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  int rc = submit_locked(ctx, d, 0, event_id);
+  if (rc != DOTPE_OK) return rc;
   progress(ctx);
+  Event *e = ctx->events[*event_id];
   if (e->state == DOTPE_STATE_FAILED) return fail(DOTPE_E_DEVICE, "launch failed: %s", g_last_error.c_str());
+  return DOTPE_OK;
+}
+
+int dotpe_batch_submit(dotpe_ctx *ctx, int n, const dotpe_event_desc *descs, uint64_t *event_ids) {
+  if (!ctx || !descs || !event_ids || n < 1) return fail(DOTPE_E_INVALID, "null argument or n < 1");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  for (int k = 1; k < n; ++k)
+    if (descs[k].bank_id != descs[0].bank_id || descs[k].precision != descs[0].precision)
+      return fail(DOTPE_E_INVALID, "batch events must share the bank and the precision");
+  size_t need = 0;
+  const uint64_t group = ctx->next_group++;
+  for (int k = 0; k < n; ++k) {
+    if (descs[k].block_rows != 0) return fail(DOTPE_E_INVALID, "batch events are not streamed in bank blocks");
+    int rc = submit_locked(ctx, &descs[k], group, &event_ids[k]);
+    if (rc != DOTPE_OK) {
+      std::string msg = g_last_error;
+      for (int j = 0; j < k; ++j) {
+        auto it = ctx->events.find(event_ids[j]);
+        ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), event_ids[j]), ctx->queue.end());
+        free_event(ctx, it->second);
+        ctx->events.erase(it);
+      }
+      return fail(rc, "batch event %d: %s", k, msg.c_str());
+    }
+    Event *e = ctx->events[event_ids[k]];
+    need += scratch_layout(*e).total + keep_bytes_of(*e) + e->in_bytes;
+  }
+  if (need + ctx->events[event_ids[0]]->bank->bytes > ctx->budget) {
+    for (int j = 0; j < n; ++j) {
+      auto it = ctx->events.find(event_ids[j]);
+      ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), event_ids[j]), ctx->queue.end());
+      free_event(ctx, it->second);
+      ctx->events.erase(it);
+    }
+    return fail(DOTPE_E_ADMISSION, "batch needs %zu device bytes, budget %llu", need,
+                (unsigned long long)ctx->budget);
+  }
+  progress(ctx);
+  for (int k = 0; k < n; ++k)
+    if (ctx->events[event_ids[k]]->state == DOTPE_STATE_FAILED)
+      return fail(DOTPE_E_DEVICE, "launch failed: %s", g_last_error.c_str());
   return DOTPE_OK;
 }
 

@@ -259,38 +259,47 @@ void launch_reduce_block(const ReduceArgs &a, cudaStream_t st) {
 void launch_reduce_final(const ReduceArgs &a, cudaStream_t st) { reduce_final_kernel<<<1, 1024, 0, st>>>(a); }
 
 // ---------------------------------------------------------------------------
-// Refinement selection (after a screening pass).  Tile t is refined when its
-// screened best ln L^ML reaches max - window - 2 margin(max): the exact value of
-// any pair differs from its screened one by at most one margin, and so does the
-// exact maximum.  Two kernels keep the list in banded tile order: per-block
-// counts, then each block writes its tiles at the prefix of the earlier counts.
+// Refinement selection (after a screening pass).  Tile t of event k is refined
+// when its screened best ln L^ML reaches max_k - window - 2 margin(max_k): the
+// exact value of any pair differs from its screened one by at most one margin,
+// and so does the exact maximum.  Two kernels keep the list in event order and
+// banded tile order within an event: per-block counts, then each block writes
+// its items at the prefix of the earlier counts.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int SB = 1024;  // tiles per selection block
 }
 
-__device__ __forceinline__ bool select_tile(const SelectArgs &a, int w, float thr, int &t) {
-  const int n = a.n_itile * a.n_etile;
-  if (w >= n) return false;
+__device__ __forceinline__ bool select_tile(const SelectBatch &a, int w, int &k, int &t) {
+  if (w >= a.begin[a.n]) return false;
+  int lo = 0, hi = a.n - 1;  // largest k with begin[k] <= w
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.begin[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  k = lo;
+  const SelectEvent &v = a.ev[k];
   int it, et;
-  super_tile(w, a.n_itile, a.n_etile, a.band, it, et);
-  t = it * a.n_etile + et;
-  return a.tile_ml[t] >= thr;
+  super_tile(w - a.begin[k], v.n_itile, v.n_etile, v.band, it, et);
+  t = it * v.n_etile + et;
+  const float mx = *v.ml_screen;
+  const float thr = mx - v.window - 2.f * screen_margin(mx, v.margin_k, *v.sqrt_dd);
+  return v.tile_ml[t] >= thr;
 }
 
-__device__ __forceinline__ float select_threshold(const SelectArgs &a) {
-  const float mx = *a.ml_screen;
-  return mx - a.window - 2.f * screen_margin(mx, a.margin_k, *a.sqrt_dd);
-}
-
-__global__ void __launch_bounds__(SB) select_count_kernel(SelectArgs a) {
-  int t;
-  const bool f = select_tile(a, blockIdx.x * SB + threadIdx.x, select_threshold(a), t);
+__global__ void __launch_bounds__(SB) select_count_kernel(SelectBatch a) {
+  int k = -1, t;
+  const bool f = select_tile(a, blockIdx.x * SB + threadIdx.x, k, t);
   const int c = __syncthreads_count(f);
   if (threadIdx.x == 0) a.counts[blockIdx.x] = c;
+  // per-event counts: one atomic per (warp, event)
+  const unsigned grp = __match_any_sync(0xffffffffu, f ? k : -1);
+  const int lane = threadIdx.x & 31;
+  if (f && lane == __ffs(grp) - 1) atomicAdd(a.ev[k].n_refined, __popc(grp));
 }
 
-__global__ void __launch_bounds__(SB) select_write_kernel(SelectArgs a) {
+__global__ void __launch_bounds__(SB) select_write_kernel(SelectBatch a) {
   __shared__ int wsum[SB / 32];
   __shared__ int base_s;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -298,44 +307,51 @@ __global__ void __launch_bounds__(SB) select_write_kernel(SelectArgs a) {
   {
     const int upto = (blockIdx.x == 0) ? (int)gridDim.x : (int)blockIdx.x;
     int v = 0;
-    for (int k = tid; k < upto; k += SB) v += a.counts[k];
+    for (int q = tid; q < upto; q += SB) v += a.counts[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) wsum[wid] = v;
     __syncthreads();
     if (tid == 0) {
       int s = 0;
-      for (int k = 0; k < SB / 32; ++k) s += wsum[k];
+      for (int q = 0; q < SB / 32; ++q) s += wsum[q];
       base_s = (blockIdx.x == 0) ? 0 : s;
-      if (blockIdx.x == 0) {
-        *a.n_list = s;
-        const float mx = *a.ml_screen;
-        *a.ml_refine = fmaxf(mx - screen_margin(mx, a.margin_k, *a.sqrt_dd), 0.f);
-      }
+      if (blockIdx.x == 0) *a.n_list = s;
     }
     __syncthreads();
   }
-  int t = 0;
-  const bool f = select_tile(a, blockIdx.x * SB + tid, select_threshold(a), t);
+  int k = 0, t = 0;
+  const bool f = select_tile(a, blockIdx.x * SB + tid, k, t);
   const unsigned bal = __ballot_sync(0xffffffffu, f);
   if (lane == 0) wsum[wid] = __popc(bal);
   __syncthreads();
   if (tid == 0) {
     int s = 0;
-    for (int k = 0; k < SB / 32; ++k) {
-      const int c = wsum[k];
-      wsum[k] = s;
+    for (int q = 0; q < SB / 32; ++q) {
+      const int c = wsum[q];
+      wsum[q] = s;
       s += c;
     }
   }
   __syncthreads();
-  if (f) a.list[base_s + wsum[wid] + __popc(bal & ((1u << lane) - 1u))] = t;
+  if (f) a.list[base_s + wsum[wid] + __popc(bal & ((1u << lane) - 1u))] = make_int2(k, t);
+}
+
+// Per event: the frozen refinement maximum; the refined-tile count starts at 0.
+__global__ void select_events_kernel(SelectBatch a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const SelectEvent &v = a.ev[k];
+  const float mx = *v.ml_screen;
+  *v.ml_refine = fmaxf(mx - screen_margin(mx, v.margin_k, *v.sqrt_dd), 0.f);
+  *v.n_refined = 0;
 }
 
 int select_count_blocks(int n_tiles) { return (n_tiles + SB - 1) / SB; }
 
-void launch_select(const SelectArgs &a, cudaStream_t st) {
-  const int nb = select_count_blocks(a.n_itile * a.n_etile);
+void launch_select(const SelectBatch &a, cudaStream_t st) {
+  const int nb = select_count_blocks(a.begin[a.n]);
   if (nb < 1) return;
+  select_events_kernel<<<(a.n + 63) / 64, 64, 0, st>>>(a);
   select_count_kernel<<<nb, SB, 0, st>>>(a);
   select_write_kernel<<<nb, SB, 0, st>>>(a);
 }

@@ -1,0 +1,425 @@
+// K3: fused <d|h> GEMM on the 5th-generation tensor cores + marginalisation epilogue.
+//
+// Persistent kernel, one CTA per SM, warp-specialised:
+//   warp 0      TMA producer: bank tile A (128 rows x 2 k-blocks of 64) and
+//               extrinsic tile B (64 rows = 32 samples x (re, im), 2 k-blocks)
+//               into a ring of stages; each load is one 3-D box spanning two
+//               k-blocks (one TMA transaction per operand and stage: the per-CTA
+//               TMA rate grows with the transaction size)
+//   warp 1      TMEM allocator and tcgen05.mma issuer (one elected lane)
+//   warps 2..9  epilogue (two warps per TMEM lane quadrant, each taking half
+//               of the tile's extrinsic samples): tcgen05.ld of the accumulators,
+//               <h|h> coefficients, phase grid, ML cut, distance marginal,
+//               log-sum-exp partials
+// Tile = 128 bank rows x 32 extrinsic samples, all modes: accumulators for mode
+// m live in TMEM columns [buf*256 + 64 m, +64) (two buffers, so the epilogue of
+// tile t overlaps the MMAs of tile t+1).  Per mode the GEMM is the real-ified
+// complex product of Eq. dh_ieo (K = 2B, padded to a multiple of 64); split
+// precision adds passes over hi/lo operand planes into the same accumulator.
+//
+// One launch serves a batch of events over one bank (a single event is a batch
+// of one): the work items are the events' tiles one event after the other
+// (banded order within each), or an (event, tile) list written on the device.
+// The epilogue copies an event's parameters into shared memory when its work
+// crosses into the next event.
+#pragma once
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "kernels.h"
+
+namespace dotpe {
+
+namespace {
+constexpr int TI = TC_TI, TE = TC_TE, BN = 2 * TE, BK = 64;
+constexpr int NEPI = 8;              // epilogue warps
+constexpr int NT = (2 + NEPI) * 32;  // 320 threads
+constexpr int EPT = NEPI * 32;       // epilogue threads
+constexpr int EHALF = TE / 2;        // extrinsic samples per epilogue thread and tile
+constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2;  // one k-block
+constexpr int KBX = 2;  // k-blocks per stage (one 3-D TMA box)
+// Pipeline: single pass = 4 stages of {A, B} x 2 k-blocks (48 KB); split
+// precision = 2 stages of {A_hi, A_lo, B_hi, B_lo} x 2 k-blocks (96 KB), whose
+// three MMA groups (hi*hi, hi*lo, lo*hi) share one load of each plane.
+template <bool SPLIT> struct Pipe {
+  static constexpr int NPL = SPLIT ? 2 : 1;
+  static constexpr int ST = SPLIT ? 2 : 4;
+  static constexpr uint32_t A_ST = KBX * A_BYTES, B_ST = KBX * B_BYTES;  // per plane
+  static constexpr uint32_t STAGE = NPL * (A_ST + B_ST);
+};
+constexpr uint32_t TMEM_COLS = 512, BUF_COLS = MAXM * BN;
+constexpr int XS_LD = TE + 1;
+static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
+
+struct TcTail {
+  EpiParams ep;  // parameters of the event whose tile the epilogue is on
+  float xs[TI * XS_LD];
+  float qs[TE * MAXD * REC];
+  double lwe[TE];
+  float2 ph[7 * MAXPHI];
+  float2 rowh[TI];  // second-half row partial of each row
+  float wm1[NEPI], ws1[NEPI], wm2[NEPI], ws2[NEPI], wml[NEPI];
+  long long warg[NEPI];
+  int wnp[NEPI];
+  uint64_t full[4], empty[4], tfull[2], tempty[2], drain;
+  uint32_t tmem_slot;
+  int abort_flag;
+};
+template <bool SPLIT>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)Pipe<SPLIT>::ST * Pipe<SPLIT>::STAGE + sizeof(TcTail);
+}
+static_assert(smem_bytes<true>() <= 232448 && smem_bytes<false>() <= 232448, "shared memory budget");
+}  // namespace
+
+// 32 lanes x 32-bit, 2 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
+  a = __uint_as_float(r0);
+  b = __uint_as_float(r1);
+}
+
+// Work item w -> (event k, tile it, et): entry w of the device list, or the
+// event whose range [begin[k], begin[k+1]) holds w and, within it, the banded
+// order of super_tile.
+template <int NB>
+__device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, int &it, int &et) {
+  if (Bt.glist) {
+    const int2 q = Bt.glist[w];
+    k = q.x;
+    it = q.y / Bt.w[k].n_etile;
+    et = q.y - it * Bt.w[k].n_etile;
+    return;
+  }
+  k = 0;
+  if (NB > 1) {
+    int lo = 0, hi = Bt.n - 1;  // largest k with begin[k] <= w
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (Bt.begin[mid] <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    k = lo;
+  }
+  const TcEvent &W = Bt.w[k];
+  super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
+}
+
+template <bool BF16, bool CONSEC, bool SPLIT, int NB>
+__global__ void __launch_bounds__(NT, 1)
+    tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcBatch<NB> Bt,
+                    const TcCommon C) {
+  constexpr int ST = Pipe<SPLIT>::ST, NPL = Pipe<SPLIT>::NPL;
+  constexpr uint32_t STAGE_BYTES = Pipe<SPLIT>::STAGE, A_ST = Pipe<SPLIT>::A_ST, B_ST = Pipe<SPLIT>::B_ST;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // stage s, plane p: A at sA + (s NPL + p) A_ST as [KBX][128 rows][64],
+  //                   B at sB + (s NPL + p) B_ST as [KBX][64 rows][64]
+  uint8_t *sA = base;
+  uint8_t *sB = base + ST * NPL * A_ST;
+  TcTail &T = *reinterpret_cast<TcTail *>(base + (size_t)ST * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int M = C.n_modes;
+  const int n_work = Bt.glist ? *Bt.glist_n : Bt.begin[Bt.n];
+  const int nst = (C.kb + KBX - 1) / KBX;  // stages per mode (an odd last k-block is zero-filled)
+  const unsigned long long wait_ns = Bt.w[0].P.wait_ns;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&T.full[s], 1);
+      mbar_init(&T.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&T.tfull[b], 1);
+      mbar_init(&T.tempty[b], NEPI);
+    }
+    mbar_init(&T.drain, 1);
+    T.abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&mapA);
+    tma_prefetch_desc(&Bt.mapB[0]);
+  }
+  if (warp == 1) tmem_alloc(&T.tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = T.tmem_slot;
+  volatile int *abortp = &T.abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      uint32_t q = 0;
+      bool ok = !Bt.w[0].P.test_stall;
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+        int k, it, et;
+        work_tile(Bt, w, k, it, et);
+        const TcEvent &W = Bt.w[k];
+        for (int m = 0; m < M && ok; ++m) {
+          const int arow = m * C.a_mode_rows + W.a_row0 + it * TI;
+          const int brow = m * W.b_mode_rows + et * BN;
+          for (int ks = 0; ks < nst; ++ks, ++q) {
+            const int s = q % ST;
+            const uint32_t n = q / ST;
+            if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, nullptr, abortp, wait_ns))) break;
+            mbar_expect_tx(&T.full[s], STAGE_BYTES);
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+              tma_load_3d(sA + (s * NPL + pl) * A_ST, &mapA, &T.full[s], 0, pl * C.a_plane_rows + arow, ks * KBX);
+              tma_load_3d(sB + (s * NPL + pl) * B_ST, &Bt.mapB[k], &T.full[s], 0, pl * W.b_plane_rows + brow, ks * KBX);
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let copies already in flight land before the CTA exits
+        uint32_t first = q > (uint32_t)ST ? q - ST : 0;
+        for (uint32_t j = first; j < q; ++j) {
+          volatile int no_abort = 0;
+          mbar_wait(&T.full[j % ST], (j / ST) & 1, nullptr, &no_abort, 200000000ull);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
+      uint32_t q = 0, u = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++u) {
+        const int b = u & 1;
+        const uint32_t use = u >> 1;
+        if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, wait_ns))) break;
+        tc_fence_after();
+        for (int m = 0; m < M && ok; ++m) {
+          const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
+          for (int ks = 0; ks < nst; ++ks, ++q) {
+            const int s = q % ST;
+            const uint32_t n = q / ST;
+            if (!(ok = mbar_wait(&T.full[s], n & 1, nullptr, abortp, wait_ns))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int kx = 0; kx < KBX; ++kx) {
+              const uint64_t ah = sdesc_k128(sA + (s * NPL) * A_ST + kx * A_BYTES);
+              const uint64_t bh = sdesc_k128(sB + (s * NPL) * B_ST + kx * B_BYTES);
+              const uint64_t al = sdesc_k128(sA + (s * NPL + NPL - 1) * A_ST + kx * A_BYTES);
+              const uint64_t bl = sdesc_k128(sB + (s * NPL + NPL - 1) * B_ST + kx * B_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
+                if (SPLIT) {
+                  tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
+                  tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+                }
+              }
+            }
+            tc_commit(&T.empty[s]);
+          }
+        }
+        if (ok) tc_commit(&T.tfull[b]);
+      }
+      // all MMAs of this CTA complete before TMEM is released
+      tc_commit(&T.drain);
+      volatile int no_abort = 0;
+      mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
+    }
+  } else {
+    // ---------------- epilogue (256 threads: one tile row, half the samples each) ----------------
+    const int ew = warp - 2;      // 0..7
+    const int quad = warp & 3;    // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;     // which 16 of the tile's 32 extrinsic samples
+    const int row = quad * 32 + lane;
+    const int etid = threadIdx.x - 64;
+    const EpiParams &P = T.ep;
+    bool store = false;
+    float zs = 1.f;
+    float mrec[MAXD * REC];
+    double lwi = 0.0;
+    int cur_it = -1, cur_k = -1;
+    uint32_t u = 0;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++u) {
+      const int b = u & 1;
+      const uint32_t use = u >> 1;
+      int k, it, et;
+      work_tile(Bt, w, k, it, et);
+      if (k != cur_k) {
+        // the next event: its parameters and phase tables into shared memory
+        named_bar_sync(1, EPT);
+        {
+          const int *src = reinterpret_cast<const int *>(&Bt.w[k].P);
+          int *dst = reinterpret_cast<int *>(&T.ep);
+          for (int q = etid; q < (int)(sizeof(EpiParams) / 4); q += EPT) dst[q] = src[q];
+        }
+        named_bar_sync(1, EPT);
+        fill_phase_tables(T.ph, P, etid, EPT);
+        store = (P.lnl_tile != nullptr);
+        zs = P.z_scale / (P.g_scale ? *P.g_scale : 1.f);
+        cur_k = k;
+        cur_it = -1;
+      }
+      const bool etv = true;
+      const int t = it * Bt.w[k].n_etile + et;
+      const int64_t i = (int64_t)it * TI + row;
+      const bool vi = i < P.n_int;
+      const int64_t e0 = (int64_t)et * TE;
+      if (it != cur_it) {
+#pragma unroll
+        for (int k = 0; k < MAXD * REC; ++k) mrec[k] = 0.f;
+        const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
+#pragma unroll
+        for (int k = 0; k < MAXD * REC / 4; ++k) {
+          if (vi && k < P.n_det * REC / 4) {
+            float4 v = __ldg(src + k);
+            mrec[4 * k] = v.x; mrec[4 * k + 1] = v.y; mrec[4 * k + 2] = v.z; mrec[4 * k + 3] = v.w;
+          }
+        }
+        lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
+        cur_it = it;
+      }
+      for (int k = etid; k < TE * P.n_det * REC; k += EPT) {
+        const int e = k / (P.n_det * REC), qq = k % (P.n_det * REC);
+        T.qs[e * MAXD * REC + qq] = (e0 + e < P.n_ext) ? __ldg(P.qx + (e0 + e) * P.n_det * REC + qq) : 0.f;
+      }
+      for (int k = etid; k < TE; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
+      named_bar_sync(1, EPT);
+      const float thr = tile_threshold(P);
+      if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
+      tc_fence_after();
+
+      Lse ra, rb;
+      ra.init();
+      rb.init();
+      float best = -1.f;
+      long long barg = 0x7fffffffffffffffLL;
+      int np = 0;
+      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS;
+#pragma unroll 1
+      for (int j = 0; j < EHALF; ++j) {
+        const int el = half * EHALF + j;
+        const int64_t e = e0 + el;
+        float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) {
+          if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
+          else { Zr[m] = 0.f; Zi[m] = 0.f; }
+        }
+        tmem_ld_wait();
+        if (j == EHALF - 1) {
+          // this warp's accumulators are in registers: release the buffer to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&T.tempty[b]);
+        }
+        float x = -INFINITY, x2 = -INFINITY;
+        if (vi && e < P.n_ext) {
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) {
+            Zr[m] *= zs;
+            Zi[m] *= zs;
+          }
+          if (P.gemm_only) {
+            float sx = 0.f;
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) sx += Zr[m] + Zi[m];
+            x = sx;
+            x2 = sx;
+          } else if (P.screen_ml) {
+            float C0, Cr[3], Ci[3];
+            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            int argo;
+            const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph, argo);
+            if (ml > best) {
+              best = ml;
+              barg = (i * P.n_ext + e) * (long long)P.n_phi + argo;
+            }
+            if (store) {
+              P.lnl_tile[i * P.n_ext + e] = -INFINITY;
+              P.ml_tile[i * P.n_ext + e] = ml;
+            }
+          } else {
+            float C0, Cr[3], Ci[3];
+            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph);
+            const float lw = (float)(lwi + T.lwe[el]);
+            x = pr.lsum + lw;
+            x2 = pr.lsum2 + 2.f * lw;
+            np += pr.npass;
+            if (pr.ml > best) {
+              best = pr.ml;
+              barg = (i * P.n_ext + e) * (long long)P.n_phi + pr.argo;
+            }
+            if (store) {
+              P.lnl_tile[i * P.n_ext + e] = pr.lsum - P.ln_nphi;
+              P.ml_tile[i * P.n_ext + e] = pr.ml;
+            }
+          }
+        }
+        T.xs[row * XS_LD + el] = x;
+        ra.add(x);
+        rb.add(x2);
+      }
+      if (half == 1) T.rowh[row] = make_float2(ra.m, ra.s);
+      warp_merge_lse(rb);
+      warp_argmax(best, barg);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+      {
+        Lse w = ra;
+        warp_merge_lse(w);
+        if (lane == 0) {
+          T.wm1[ew] = w.m; T.ws1[ew] = w.s; T.wm2[ew] = rb.m; T.ws2[ew] = rb.s;
+          T.wml[ew] = best; T.warg[ew] = barg; T.wnp[ew] = np;
+        }
+      }
+      named_bar_sync(1, EPT);
+      if (half == 0 && vi && etv) {
+        ra.merge(T.rowh[row].x, T.rowh[row].y);
+        P.row_part[(int64_t)et * P.n_int + i] = make_float2(ra.m, ra.s);
+      }
+      {
+        // column partials: 8 threads per extrinsic sample, 16 rows each
+        const int cc = etid >> 3, qq = etid & 7;
+        Lse a;
+        a.init();
+        for (int r = qq * 16; r < qq * 16 + 16; ++r) a.add(T.xs[r * XS_LD + cc]);
+#pragma unroll
+        for (int o = 1; o <= 4; o <<= 1) {
+          float om = __shfl_xor_sync(0xffffffffu, a.m, o);
+          float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+          a.merge(om, os);
+        }
+        if (qq == 0 && etv && e0 + cc < P.n_ext)
+          P.col_part[(int64_t)it * P.n_ext + e0 + cc] = make_float2(a.m, a.s);
+      }
+      if (etid == 0 && etv) {
+        Lse a, bb;
+        a.init();
+        bb.init();
+        float bv = -1.f;
+        long long bi = 0x7fffffffffffffffLL;
+        int n = 0;
+        for (int w = 0; w < NEPI; ++w) {
+          a.merge(T.wm1[w], T.ws1[w]);
+          bb.merge(T.wm2[w], T.ws2[w]);
+          n += T.wnp[w];
+          if (T.wml[w] > bv || (T.wml[w] == bv && T.warg[w] < bi)) { bv = T.wml[w]; bi = T.warg[w]; }
+        }
+        P.tile_part[t] = make_float4(a.m, a.s, bb.m, bb.s);
+        P.tile_ml[t] = bv;
+        P.tile_arg[t] = bi;
+        P.tile_npass[t] = n;
+        if (bv > 0.f && P.track_max) atomic_max_nonneg(P.ml_running, bv);
+      }
+      named_bar_sync(1, EPT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+  // a wait that ran out leaves this CTA's tiles of every event unfinished
+  if (threadIdx.x == 0 && T.abort_flag)
+    for (int k = 0; k < Bt.n; ++k) atomicCAS(Bt.w[k].P.status, 0, DEV_E_TIMEOUT);
+}
+
+}  // namespace dotpe

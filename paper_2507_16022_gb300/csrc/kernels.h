@@ -11,6 +11,12 @@
 
 namespace dotpe {
 
+// fp16 operands are scaled to magnitudes up to 2^14 instead of 1: the five
+// exponent bits then keep hi normal down to ~4e-9 of the largest element and lo
+// (~2^-11 hi) normal down to ~8e-6 of it, so the split keeps ~2^-22 relative
+// accuracy over the data's dynamic range (products and K-sums stay far inside FP32).
+constexpr float FP16_OPERAND_SCALE = 16384.0f;
+
 struct PrepArgs {
   int D, B, M, Kpad;
   int64_t E;
@@ -59,41 +65,66 @@ struct SimtArgs {
 constexpr int SIMT_TI = 64, SIMT_TE = 32;
 void launch_simt(const SimtArgs &g, const EpiParams &P, cudaStream_t st);
 
-// Fused tcgen05 kernel.
+// Fused tcgen05 kernel over a batch of events sharing one bank.
 constexpr int TC_TI = 128, TC_TE = 32;
-struct TcArgs {
-  CUtensorMap mapA, mapB;
-  int kb_per_mode;   // Kpad / 64
-  int n_pass;
-  int pa[3], pb[3];  // plane index of A and B per pass
-  int a_plane_rows, a_mode_rows, a_row0;
-  int b_plane_rows, b_mode_rows;
-  bool bf16;
-  int n_sms;
-  int n_modes;
-  double l2_band_bytes;  // extrinsic operand bytes kept resident per band
-  const int *list;       // optional device tile list (linear tile indices) and its device length
-  const int *n_list;
+constexpr int TC_MAXB = 64;  // events per batched launch (kernel-parameter space)
+struct TcEvent {             // one event of a launch (without its tensor map)
+  EpiParams P;
+  int n_itile, n_etile, band;      // tiles of the event (block) and its L2 band width
+  int a_row0;                      // first bank row of the event's slice (block)
+  int b_plane_rows, b_mode_rows;   // rows of one operand plane / one mode in mapB
 };
-int launch_tc(const TcArgs &g, const EpiParams &P, cudaStream_t st);  // returns cudaError_t as int
-int tc_band(const TcArgs &g, int n_etile);                           // extrinsic tiles per L2 band
+struct TcWork : TcEvent {    // host-side record: the event and its map
+  CUtensorMap mapB;          // packed extrinsic operand planes [planes][M][2E][Kpad]
+};
+template <int NB>
+struct TcBatch {
+  CUtensorMap mapB[NB];
+  TcEvent w[NB];
+  int begin[NB + 1];     // grid mode: event k owns work items [begin[k], begin[k+1])
+  int n;                 // events
+  const int2 *glist;     // list mode (device): work item -> (event, linear tile it * n_etile + et)
+  const int *glist_n;    // its length (device)
+};
+struct TcCommon {
+  int kb;                          // k-blocks of 64 per mode (Kpad / 64)
+  int a_plane_rows, a_mode_rows;   // bank rows of one plane / one mode in mapA
+  int n_modes;
+};
+struct TcLaunch {
+  CUtensorMap mapA;  // bank operand planes [planes][M][I][Kpad]
+  TcCommon C;
+  bool bf16, split, consec;
+  int n_sms;
+};
+// n <= TC_MAXB works; glist/glist_n non-null for list mode.  Returns a cudaError_t.
+int launch_tc(const TcLaunch &L, const TcWork *works, int n, const int2 *glist, const int *glist_n, cudaStream_t st);
+// extrinsic tiles per L2 band: the band's operand planes fill about l2_band_bytes
+int tc_band(double l2_band_bytes, int kb, int n_modes, bool split, int n_etile);
 
-// Refinement selection after a screening pass: the tiles whose screened best
-// ln L^ML can reach the cut, in banded tile order.
-struct SelectArgs {
-  const float *tile_ml;   // [n_itile * n_etile] screened best ln L^ML per tile (-1: none evaluated)
+// Refinement selection after a screening pass, over a batch of events: the
+// tiles whose screened best ln L^ML can reach the cut, in banded tile order,
+// written as (event, tile) work items.
+struct SelectEvent {
+  const float *tile_ml;    // [n_itile * n_etile] screened best ln L^ML per tile (-1: none evaluated)
   int n_itile, n_etile, band;
-  const float *ml_screen; // screened running maximum
-  const float *sqrt_dd;   // sqrt<d|d>
-  float window;           // tiles within window + 2 margins of the maximum are refined
-  float margin_k;         // kappa*u of the screening precision
-  float *ml_refine;       // out: screened maximum - margin (a lower bound of the exact maximum)
-  int *list;              // out: [n_itile * n_etile] tile indices
-  int *n_list;            // out: count
-  int *counts;            // scratch: select_count_blocks() ints
+  const float *ml_screen;  // screened running maximum
+  const float *sqrt_dd;    // sqrt<d|d>
+  float window;            // tiles within window + 2 margins of the maximum are refined
+  float margin_k;          // kappa*u of the screening precision
+  float *ml_refine;        // out: screened maximum - margin (a lower bound of the exact maximum)
+  int *n_refined;          // out: the event's refined tiles
+};
+struct SelectBatch {
+  SelectEvent ev[TC_MAXB];
+  int begin[TC_MAXB + 1];  // event k's tiles are [begin[k], begin[k+1]) of the batch
+  int n;
+  int2 *list;              // out: (event, tile) items, event by event
+  int *n_list;             // out: total
+  int *counts;             // scratch: select_count_blocks(begin[n]) ints
 };
 int select_count_blocks(int n_tiles);
-void launch_select(const SelectArgs &a, cudaStream_t st);
+void launch_select(const SelectBatch &a, cudaStream_t st);
 
 // Cross-tile FP64 reduction -> evidence, one bank block at a time.
 struct ReduceOut {
