@@ -45,6 +45,17 @@ static int64_t now_ns() {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Records `ev` on `st`; inside a stream capture as an event-record node of the
+// graph (a plain record there only orders the captured work and is never
+// executed, so the host could not query or time the event afterwards).
+static cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecordWithFlags(ev, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                               : cudaEventRecordDefault);
+}
+
 // Carves one allocation into 256-byte aligned pieces.
 struct Carver {
   size_t off = 0;
@@ -88,6 +99,7 @@ struct Event {
   int64_t i0 = 0, NI = 0, NE = 0;
   int64_t block_rows = 0;  // rows per streamed bank block (0: the whole slice)
   uint64_t group = 0;      // batch of dotpe_batch_submit (0: none)
+  std::string launch_error;  // why the launch failed on the host (state FAILED, device status 0)
   int D = 0, nphi = 0, prec = 0, flags = 0;
   double u_min = 0, cut = 0;
   bool has_lwe = false;
@@ -416,7 +428,7 @@ static int event_begin(Event &e, EventRun &R, cudaStream_t st) {
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.gmax, 0, 4, st));
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.status, 0, 4, st));
-  CUDA_OR_FAIL(cudaEventRecord(e.ev_start, st));
+  CUDA_OR_FAIL(record(e.ev_start, st));
   launch_prep(R.pa, st);
   return DOTPE_OK;
 }
@@ -497,7 +509,7 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
   W.P = screen_params(R);
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
-  if (last_block) CUDA_OR_FAIL(cudaEventRecord(e.ev_ks, st));
+  if (last_block) CUDA_OR_FAIL(record(e.ev_ks, st));
   SelectBatch sb;
   memset(&sb, 0, sizeof(sb));
   sb.ev[0] = select_event_of(R);
@@ -521,7 +533,7 @@ static int event_end(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
   launch_reduce_final(R.ra, st);
   CUDA_OR_FAIL(cudaGetLastError());
   CUDA_OR_FAIL(cudaMemcpyAsync(e.h_out, e.d_out, sizeof(ReduceOut), cudaMemcpyDeviceToHost, st));
-  CUDA_OR_FAIL(cudaEventRecord(e.ev_end, st));
+  CUDA_OR_FAIL(record(e.ev_end, st));
   CUDA_OR_FAIL(cudaLaunchHostFunc(st, mark_done, new DoneArg{ctx, e.id}));
   return DOTPE_OK;
 }
@@ -549,9 +561,9 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
     const int64_t r0 = (int64_t)k * BR;
     event_block(ctx, e, R, r0, std::min<int64_t>(BR, e.NI - r0), st);
     if (k == 0 && ctx->autotune && (rc = autotune_band(ctx, e, R, st)) != DOTPE_OK) return rc;
-    if (k == 0) CUDA_OR_FAIL(cudaEventRecord(e.ev_k0, st));
+    if (k == 0) CUDA_OR_FAIL(record(e.ev_k0, st));
     if ((rc = event_fused(ctx, e, R, k == n_blocks - 1, st)) != DOTPE_OK) return rc;
-    if (k == n_blocks - 1) CUDA_OR_FAIL(cudaEventRecord(e.ev_k1, st));
+    if (k == n_blocks - 1) CUDA_OR_FAIL(record(e.ev_k1, st));
     R.ra.first = (k == 0);
     launch_reduce_block(R.ra, st);
   }
@@ -668,7 +680,7 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
       int r = event_begin(*evs[k], R[k], st);
       if (r != DOTPE_OK) return r;
       event_block(ctx, *evs[k], R[k], 0, evs[k]->NI, st);
-      CUDA_OR_FAIL(cudaEventRecord(evs[k]->ev_k0, st));
+      CUDA_OR_FAIL(record(evs[k]->ev_k0, st));
     }
     if (prec == DOTPE_PREC_FP32) {
       for (int k = 0; k < n; ++k) {
@@ -689,7 +701,7 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
         if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
       }
       if (mixed) {
-        for (int k = 0; k < n; ++k) CUDA_OR_FAIL(cudaEventRecord(evs[k]->ev_ks, st));
+        for (int k = 0; k < n; ++k) CUDA_OR_FAIL(record(evs[k]->ev_ks, st));
         int2 *glist = (int2 *)(blist + o_list);
         int *gn = (int *)(blist + o_n);
         for (int k0 = 0; k0 < n; k0 += TC_MAXB) {
@@ -718,7 +730,7 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
       }
     }
     for (int k = 0; k < n; ++k) {
-      CUDA_OR_FAIL(cudaEventRecord(evs[k]->ev_k1, st));
+      CUDA_OR_FAIL(record(evs[k]->ev_k1, st));
       R[k].ra.first = 1;
       launch_reduce_block(R[k].ra, st);
       int r = event_end(ctx, *evs[k], R[k], st);
@@ -862,7 +874,10 @@ static void progress(dotpe_ctx *ctx) {
     ctx->slot_busy[slot] = (int)grp.size();
     const int rc = (grp.size() == 1 && e.group == 0) ? run_event(ctx, e) : run_batch(ctx, grp, slot);
     if (rc != DOTPE_OK) {
-      for (Event *x : grp) x->state = DOTPE_STATE_FAILED;
+      for (Event *x : grp) {
+        x->state = DOTPE_STATE_FAILED;
+        x->launch_error = g_last_error;
+      }
       ctx->slot_busy[slot] = 0;
     }
   }
@@ -1370,7 +1385,8 @@ int dotpe_event_wait(dotpe_ctx *ctx, uint64_t event_id, double timeout_s) {
       if (s == DOTPE_STATE_FAILED) {
         int ds = it->second->h_out->status;
         int code = ds == DEV_E_NONFINITE ? DOTPE_E_INVALID : ds == DEV_E_TIMEOUT ? DOTPE_E_TIMEOUT : DOTPE_E_DEVICE;
-        return fail(code, "event failed (device status %d)", ds);
+        return fail(code, "event failed (device status %d%s%s)", ds, it->second->launch_error.empty() ? "" : "; ",
+                    it->second->launch_error.c_str());
       }
     }
     if (timeout_s > 0 && (now_ns() - t0) > (int64_t)(timeout_s * 1e9)) return fail(DOTPE_E_TIMEOUT, "event wait");

@@ -360,6 +360,72 @@ def make_workload(n_int, n_ext, n_det, n_modes, n_bins, snr=15.0, seed=0, n_phi=
     return Workload(bank=bank, ext=ext, event=ev)
 
 
+@dataclasses.dataclass
+class BatchWorkload:
+    bank: Bank
+    events: list  # [(Extrinsic, Event)]
+
+
+def make_batch_workload(n_events=64, n_int=262144, n_modes=4, n_bins=512, seed=4,
+                        e_choices=(512, 1024, 2048, 4096), d_choices=(2, 3), snr_range=(8.0, 40.0),
+                        bank_dtype=np.complex128):
+    """Many events over one shared bank: per event an extrinsic count drawn from
+    e_choices, a detector count from d_choices and an injection SNR uniform in
+    snr_range (prior-drawn extrinsic samples, a random bank member injected)."""
+    rng = np.random.default_rng(seed)
+    bank = make_bank(rng, n_int, n_modes, n_bins, dtype=bank_dtype)
+    events = []
+    for _ in range(n_events):
+        E = int(rng.choice(e_choices))
+        D = int(rng.choice(d_choices))
+        snr = float(rng.uniform(*snr_range))
+        ext = make_extrinsic(rng, E, D, bank)
+        events.append((ext, make_event(rng, bank, ext, D, snr=snr)))
+    return BatchWorkload(bank=bank, events=events)
+
+
+@dataclasses.dataclass
+class Arrival:
+    t: float            # arrival time (s) from the start of the stream
+    n_bins: int         # which bank (one per bin grid)
+    i0: int
+    i1: int             # bank slice [i0, i1)
+    ext: Extrinsic
+    event: Event
+
+
+def make_serving_stream(n_events=2000, rate=20.0, seed=5, n_int=524288, n_modes=4, bins=(256, 512),
+                        slice_range=(16384, 524288), e_range=(1024, 8192), d_choices=(2, 3),
+                        snr_range=(8.0, 50.0), pool=8, bank_dtype=np.complex64):
+    """A Poisson stream of events (exponential inter-arrival times of mean
+    1/rate) against resident banks, one per bin grid in `bins`.  Per event: a
+    bin grid, a bank slice of uniform length in slice_range at a uniform
+    offset, an extrinsic count uniform in e_range (the first E samples of one
+    of `pool` prior-drawn sets per detector count), a detector count and an
+    injection SNR uniform in snr_range, the injected member inside the slice."""
+    rng = np.random.default_rng(seed)
+    banks = {B: make_bank(rng, n_int, n_modes, B, dtype=bank_dtype) for B in bins}
+    emax = e_range[1]
+    pools = {(B, D): [make_extrinsic(rng, emax, D, banks[B]) for _ in range(pool)]
+             for B in bins for D in d_choices}
+    t = 0.0
+    stream = []
+    for _ in range(n_events):
+        t += float(rng.exponential(1.0 / rate))
+        B = int(rng.choice(bins))
+        D = int(rng.choice(d_choices))
+        L = int(rng.integers(slice_range[0], slice_range[1] + 1))
+        i0 = int(rng.integers(0, n_int - L + 1))
+        E = int(rng.integers(e_range[0], e_range[1] + 1))
+        src = pools[(B, D)][int(rng.integers(0, pool))]
+        ext = Extrinsic(t=src.t[:E], R=src.R[:E], ln_w=src.ln_w[:E], lat=src.lat[:E], lon=src.lon[:E],
+                        psi=src.psi[:E], cos_iota=src.cos_iota[:E], t_geo=src.t_geo[:E])
+        ev = make_event(rng, banks[B], ext, D, snr=float(rng.uniform(*snr_range)),
+                        inj_i=int(rng.integers(i0, i0 + L)))
+        stream.append(Arrival(t=t, n_bins=B, i0=i0, i1=i0 + L, ext=ext, event=ev))
+    return banks, stream
+
+
 def named_workload(name: str, **overrides):
     kw = dict(WORKLOADS[name])
     kw.update(overrides)
