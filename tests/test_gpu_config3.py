@@ -5,9 +5,9 @@ B=384, injection SNR 30): the slice streams through the kernels in blocks of
 Checks, against the FP64 oracle on sampled pairs and against the plain FP32
 path on the same GPU:
   * split fp16 (hi + lo) meets |d ln L| <= 1e-3 per pair at SNR 30, where
-    ln L^ML ~ 450 and the cancellation in Re<d|h> - <h|h>/2 is largest;
-  * the served mixed path meets |d ln Z| <= 1e-2 against FP32, with the same
-    maximum and argmax;
+    ln L^ML ~ 350 and the cancellation in Re<d|h> - <h|h>/2 is largest;
+  * the served mixed path meets |d ln Z| <= 1e-2 against FP32, and its peak
+    meets 1e-3 against the oracle;
   * streaming in blocks reproduces the one-pass result (FP64 rounding only);
   * single-pass fp16 is reported against its own bound.
 """
@@ -52,14 +52,29 @@ def evidence(dp, ctx, bid, wl, precision, **kw):
     return ev
 
 
+def oracle_pairs(wl, pi, pe):
+    """The oracle on a few pairs, through a sub-bank of their rows."""
+    import oracle
+    urows, inv = np.unique(np.asarray(pi, dtype=np.int64), return_inverse=True)
+    sub = synth.Bank(**{**wl.bank.__dict__, "h": wl.bank.h[urows], "ln_w": wl.bank.ln_w[urows]})
+    return oracle.OracleProblem(sub, wl.ext, wl.event).eval_pairs(inv, np.asarray(pe, dtype=np.int64))
+
+
 def test_config3_served_path_against_fp32(big):
+    """At SNR 30 (ln L^ML ~ 350) an FP32 accumulation over K = 768 terms carries
+    ~1e-3 in ln L^ML on its own, so the peak is checked against the FP64
+    oracle, and the plain FP32 path against the served one at the evidence
+    tolerance."""
     dp, ctx, bid, wl = big
     ref = evidence(dp, ctx, bid, wl, "fp32")
     got = evidence(dp, ctx, bid, wl, "mixed")
     assert abs(got["ln_z"] - ref["ln_z"]) <= 1e-2
-    assert got["max_lnl_ml"] == pytest.approx(ref["max_lnl_ml"], abs=1e-3)
-    assert (got["arg_i"], got["arg_e"], got["arg_o"]) == (ref["arg_i"], ref["arg_e"], ref["arg_o"])
     assert got["n_eff"] == pytest.approx(ref["n_eff"], rel=2e-2)
+    o = oracle_pairs(wl, [got["arg_i"], ref["arg_i"]], [got["arg_e"], ref["arg_e"]])
+    assert abs(got["max_lnl_ml"] - o["lnl_ml_max"][0]) <= 1e-3
+    assert abs(ref["max_lnl_ml"] - o["lnl_ml_max"][1]) <= 1e-2
+    # the same peak pair, or one whose exact value ties it within the tolerance
+    assert abs(o["lnl_ml_max"][0] - o["lnl_ml_max"][1]) <= 2e-3
     n_tiles = (wl.bank.h.shape[0] // 128) * (wl.ext.t.shape[0] // 32)
     assert 0 < got["n_refined_tiles"] < n_tiles
     # the peak of an SNR-30 injection: ln L^ML ~ SNR^2 / 2
@@ -79,7 +94,6 @@ def test_config3_block_streaming_matches_one_pass(big):
 
 
 def test_config3_sampled_pairs_against_oracle(big):
-    import oracle
     dp, ctx, bid, wl = big
     I, E = wl.bank.h.shape[0], wl.ext.t.shape[0]
     rng = np.random.default_rng(33)
@@ -111,10 +125,7 @@ def test_config3_sampled_pairs_against_oracle(big):
     loc.append(int(peak["arg_i"]) - starts[3])
     pi, pe, win, loc = (np.array(x, dtype=np.int64) for x in (pi, pe, win, loc))
     # the oracle on the sampled rows only (a sub-bank keeps the host memory small)
-    urows, inv = np.unique(pi, return_inverse=True)
-    sub = synth.Bank(**{**wl.bank.__dict__, "h": wl.bank.h[urows], "ln_w": wl.bank.ln_w[urows]})
-    P = oracle.OracleProblem(sub, wl.ext, wl.event)
-    ref = P.eval_pairs(inv, pe)
+    ref = oracle_pairs(wl, pi, pe)
     ml_ref = np.maximum(ref["lnl_ml_max"], 0.0)
     dd = float(np.sum(4.0 * wl.bank.w[None, :] * np.abs(wl.event.data) ** 2 / wl.event.psd))
     u = 2.0 ** -11
@@ -133,5 +144,5 @@ def test_config3_sampled_pairs_against_oracle(big):
         assert np.all(np.isfinite(lnl))
         assert np.all(d1 <= tol), (precision, float(d1.max()), float(ml_ref[np.argmax(d1 - tol)]))
         assert np.all(d2 <= tol), (precision, float(d2.max()))
-    # the peak pair itself: ln L^ML ~ 450 to 1e-3 in split precision
+    # the peak pair itself: ln L^ML ~ 350 to 1e-3 in split precision
     assert abs(res["fp16x3"][3][1][loc[-1], pe[-1]] - ref["lnl_ml_max"][-1]) <= 1e-3
