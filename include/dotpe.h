@@ -141,8 +141,9 @@ typedef struct dotpe_bank_desc {
  *   rows (the event's device scratch then scales with block_rows, not with the
  *   slice), and each block's log-sum-exp partials, marginals and best ln L^ML
  *   are merged into FP64 accumulators in block order.  The result does not
- *   depend on block_rows beyond FP64 rounding, except with the ML cut on, where
- *   the running maximum (and so the kept superset) evolves block by block. */
+ *   depend on block_rows beyond FP64 rounding, except where a maximum known
+ *   block by block decides what is kept: the ML cut's superset, and in MIXED
+ *   precision which tiles far below the maximum are refined. */
 typedef struct dotpe_event_desc {
   uint64_t bank_id;
   int64_t i0, i1;

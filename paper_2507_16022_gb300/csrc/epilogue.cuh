@@ -39,19 +39,32 @@ __device__ __forceinline__ void fill_phase_tables(float2 *ph, const EpiParams &P
 // <h|h> coefficients for one pair from the row record (mrec) and column record (qrec):
 // C_0 = sum_d sum_m M_d[m,m] Q_d[m,m];  C_delta = sum_d sum_{a>b, m_a-m_b=delta} M_d[a,b] Q_d[a,b].
 // CONSEC: the modes' azimuthal numbers are consecutive, so pair (a, b) has delta = a - b.
+// Each detector accumulates into its own partial sums (independent FMA chains),
+// added at the end; records of detectors d >= n_det are zero.
 template <bool CONSEC>
 __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const float *__restrict__ qrec,
                                           const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
-  C0 = 0.f;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) { Cr[k] = 0.f; Ci[k] = 0.f; }
+  float c0[MAXD], cr[MAXD][3], ci[MAXD][3];
 #pragma unroll
   for (int d = 0; d < MAXD; ++d) {
-    if (d >= P.n_det) break;
-    const float *mr = mrec + d * REC;
-    const float *qr = qrec + d * REC;
+    c0[d] = 0.f;
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m) C0 = fmaf(mr[m], qr[m], C0);
+    for (int k = 0; k < 3; ++k) { cr[d][k] = 0.f; ci[d][k] = 0.f; }
+  }
+  const int nd = P.n_det;
+#pragma unroll
+  for (int d = 0; d < MAXD; ++d) {
+    if (d >= nd) break;
+    const float *mr = mrec + d * REC;
+    const float4 *q4 = reinterpret_cast<const float4 *>(qrec + d * REC);
+    float qr[REC];
+#pragma unroll
+    for (int v = 0; v < REC / 4; ++v) {
+      const float4 x = q4[v];
+      qr[4 * v] = x.x; qr[4 * v + 1] = x.y; qr[4 * v + 2] = x.z; qr[4 * v + 3] = x.w;
+    }
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) c0[d] = fmaf(mr[m], qr[m], c0[d]);
     int p = 0;
 #pragma unroll
     for (int a = 1; a < MAXM; ++a)
@@ -61,20 +74,38 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
         const float br = qr[4 + 2 * p], bi = qr[5 + 2 * p];
         if (CONSEC) {
           const int k = a - b - 1;
-          Cr[k] = fmaf(ar, br, fmaf(-ai, bi, Cr[k]));
-          Ci[k] = fmaf(ar, bi, fmaf(ai, br, Ci[k]));
+          cr[d][k] = fmaf(ar, br, fmaf(-ai, bi, cr[d][k]));
+          ci[d][k] = fmaf(ar, bi, fmaf(ai, br, ci[d][k]));
         } else {
           const float hr = ar * br - ai * bi, hi = ar * bi + ai * br;
           const int dl = P.pdelta[p];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             const bool sel = (dl == k + 1);
-            Cr[k] += sel ? hr : 0.f;
-            Ci[k] += sel ? hi : 0.f;
+            cr[d][k] += sel ? hr : 0.f;
+            ci[d][k] += sel ? hi : 0.f;
           }
         }
       }
   }
+  C0 = (c0[0] + c0[1]) + c0[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Cr[k] = (cr[0][k] + cr[1][k]) + cr[2][k];
+    Ci[k] = (ci[0][k] + ci[1][k]) + ci[2][k];
+  }
+}
+
+// Upper bound of max_o ln L^ML_o of a pair: |dh| <= sum_m |Z_m| and
+// hh >= C_0 - 2 sum |C_delta| at every phase; +inf when that lower bound is not positive.
+__device__ __forceinline__ float pair_bound(const float Zr[MAXM], const float Zi[MAXM], float C0, const float Cr[3],
+                                            const float Ci[3]) {
+  float a = 0.f, hmin = C0;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) a += sqrtf(Zr[m] * Zr[m] + Zi[m] * Zi[m]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) hmin -= 2.f * sqrtf(Cr[k] * Cr[k] + Ci[k] * Ci[k]);
+  return hmin > 0.f ? __fdividef(0.5f * a * a, hmin) * 1.000001f : INFINITY;
 }
 
 // Out-of-line distance marginal: it runs for the few phases that pass the ML

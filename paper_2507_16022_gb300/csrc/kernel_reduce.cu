@@ -5,8 +5,8 @@
 //   ln Z  = ln S1 - ln(N_i N_e N_phi)
 //   N_eff = S1^2 / S2, N_eff,int = S1^2 / sum_i P_i^2, N_eff,ext = S1^2 / sum_e P_e^2
 // Two passes per log-sum-exp: the maximum (FP32, exact), then the sum of
-// s * exp(m - max) accumulated in FP64 (the exponentials of FP32 partials are
-// evaluated in FP32: their relative error is that of the partials themselves).
+// s * exp(m - max) with the exponential and the accumulation in FP64, so that
+// the combination adds only FP64 rounding to the FP32 partials.
 // A slice processed as several bank blocks merges each block's (max, sum) pairs,
 // its column marginals and its best ln L^ML into FP64 accumulators in block
 // order; the final kernel turns them into the evidence.
@@ -37,7 +37,7 @@ __global__ void reduce_lines_kernel(int64_t n, int nparts, const float2 *__restr
   if (m != -INFINITY)
     for (int p = 0; p < nparts; ++p) {
       float2 v = part[(int64_t)p * n + k];
-      if (v.y > 0.f) s += (double)v.y * (double)__expf(v.x - m);
+      if (v.y > 0.f) s += (double)v.y * exp((double)v.x - (double)m);
     }
   if (!acc) {
     out[k] = (m == -INFINITY) ? -INFINITY : (double)m + log(s);
@@ -151,8 +151,8 @@ __global__ void __launch_bounds__(RB) reduce_pass2_kernel(ReduceArgs a, const fl
   double s[NQ] = {0.0, 0.0, 0.0};
   for (int64_t k = k0; k < n_tiles; k += stride) {
     float4 v = a.tile_part[k];
-    if (v.y > 0.f) s[0] += (double)v.y * (double)__expf(v.x - M[0]);
-    if (v.w > 0.f) s[1] += (double)v.w * (double)__expf(v.z - M[1]);
+    if (v.y > 0.f) s[0] += (double)v.y * exp((double)v.x - (double)M[0]);
+    if (v.w > 0.f) s[1] += (double)v.w * exp((double)v.z - (double)M[1]);
   }
   const double *lpi = a.ln_p_int + a.row_offset;
   for (int64_t k = k0; k < a.n_int; k += stride) {

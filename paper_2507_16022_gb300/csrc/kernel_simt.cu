@@ -25,7 +25,7 @@ struct SimtSmem {
   } u;
   float mls[TI][TE + 1];
   int pks[TI][TE + 1];  // argo | npass << 16
-  float qs[TE * MAXD * REC];
+  alignas(16) float qs[TE * MAXD * REC];  // read as float4 records
   double lwe[TE];
   float2 ph[7 * MAXPHI];
   float r_m1[TI], r_s1[TI], r_m2[TI], r_s2[TI], r_ml[TI];

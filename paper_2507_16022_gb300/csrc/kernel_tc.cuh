@@ -53,7 +53,7 @@ static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
 struct TcTail {
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
   float xs[TI * XS_LD];
-  float qs[TE * MAXD * REC];
+  alignas(16) float qs[TE * MAXD * REC];  // read as float4 records
   double lwe[TE];
   float2 ph[7 * MAXPHI];
   float2 rowh[TI];  // second-half row partial of each row
@@ -294,6 +294,95 @@ __global__ void __launch_bounds__(NT, 1)
       long long barg = 0x7fffffffffffffffLL;
       int np = 0;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS;
+      if (P.screen_ml && !store && !P.gemm_only) {
+        // Screening without stored values needs only the tile's best ln L^ML.
+        // Pass 1 bounds every pair of this thread (bounds kept in the thread's
+        // own xs entries); pass 2 evaluates pairs in decreasing bound order
+        // until the next bound lies below both the threshold and the best so far.
+        float *xb = &T.xs[row * XS_LD + half * EHALF];
+#pragma unroll 1
+        for (int j = 0; j < EHALF; ++j) {
+          const int64_t e = e0 + half * EHALF + j;
+          float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) {
+            if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), Zr[m], Zi[m]);
+            else { Zr[m] = 0.f; Zi[m] = 0.f; }
+          }
+          tmem_ld_wait();
+          float bound = -INFINITY;
+          if (vi && e < P.n_ext) {
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              Zr[m] *= zs;
+              Zi[m] *= zs;
+            }
+            float C0, Cr[3], Ci[3];
+            hh_coeffs<CONSEC>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
+            bound = pair_bound(Zr, Zi, C0, Cr, Ci);
+          }
+          xb[j] = bound;
+        }
+        // Rounds: each lane picks its highest remaining bound; the warp reads the
+        // accumulator columns its lanes picked (tcgen05.ld takes one column for the
+        // whole warp), then each lane evaluates its own pick.
+#pragma unroll 1
+        while (true) {
+          int jm = 0;
+          float bm = xb[0];
+#pragma unroll
+          for (int j = 1; j < EHALF; ++j) {
+            const float v = xb[j];
+            if (v > bm) { bm = v; jm = j; }
+          }
+          // ties with the best are evaluated, so the lowest index wins them
+          const bool want = (bm >= thr) && !(bm < best);
+          if (!__any_sync(0xffffffffu, want)) break;
+          if (want) xb[jm] = -INFINITY;
+          float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) { Zr[m] = 0.f; Zi[m] = 0.f; }
+#pragma unroll 1
+          for (int j = 0; j < EHALF; ++j) {
+            if (!__any_sync(0xffffffffu, want && jm == j)) continue;
+            float zr[MAXM], zi[MAXM];
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
+              else { zr[m] = 0.f; zi[m] = 0.f; }
+            }
+            tmem_ld_wait();
+            if (want && jm == j) {
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) { Zr[m] = zr[m]; Zi[m] = zi[m]; }
+            }
+          }
+          if (want) {
+            const int el = half * EHALF + jm;
+            const int64_t e = e0 + el;
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              Zr[m] *= zs;
+              Zi[m] *= zs;
+            }
+            float C0, Cr[3], Ci[3];
+            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            int argo;
+            const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
+            const long long g = (i * P.n_ext + e) * (long long)P.n_phi + argo;
+            if (ml > best || (ml == best && g < barg)) {
+              best = ml;
+              barg = g;
+            }
+          }
+        }
+        // the accumulators are no longer needed: release the buffer to the MMA warp
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&T.tempty[b]);
+#pragma unroll 1
+        for (int j = 0; j < EHALF; ++j) xb[j] = -INFINITY;
+      } else {
 #pragma unroll 1
       for (int j = 0; j < EHALF; ++j) {
         const int el = half * EHALF + j;
@@ -358,6 +447,7 @@ __global__ void __launch_bounds__(NT, 1)
         T.xs[row * XS_LD + el] = x;
         ra.add(x);
         rb.add(x2);
+      }
       }
       if (half == 1) T.rowh[row] = make_float2(ra.m, ra.s);
       warp_merge_lse(rb);
