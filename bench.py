@@ -10,8 +10,10 @@ recomputed in split fp16 hi/lo precision), with |d ln Z| against the plain FP32
 path on the same GPU reported beside it.
 
 One step = one event through every stage of the path: FP64 data weights,
-extrinsic operand build, bank cross terms, the fused GEMM + marginalisation
-kernel and the FP64 evidence reduction.
+extrinsic operand build, bank cross terms (computed once per bank and PSD and
+kept), the fused GEMM + marginalisation kernels and the FP64 evidence
+reduction.  The K timed events are submitted together; the runtime runs up to
+four at once.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload event|batch64|serve]
@@ -530,10 +532,12 @@ def main():
     ids = []
     with torch.cuda.stream(S):
         t_start.record(S)
+        # all K events in flight at once: the runtime's slots overlap one event's
+        # preparation and reduction with another's fused kernel
         for k in range(args.steps):
-            eid = submit(k, args.precision, stream=S)
+            ids.append(submit(k, args.precision, stream=S))
+        for eid in ids:
             dp.dotpe_event_stream_wait(ctx, eid, S)
-            ids.append(eid)
         t_end.record(S)
     barrier()
     clocks = sampler.stop()

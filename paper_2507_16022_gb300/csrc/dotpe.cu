@@ -77,6 +77,20 @@ static bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Row records <h_m|h_m'>_d of every bank row for one noise PSD (Eq. hh_ieo):
+// they depend on the bank and on omega = 4w/S only, so events that share a PSD
+// share them.  Kept per bank, keyed by a hash of (n_det, PSD values).
+struct XEntry {
+  uint64_t key = 0;
+  int D = 0;
+  float *mx = nullptr;  // [I][D][16]
+  size_t bytes = 0;
+  cudaEvent_t ready = nullptr;  // recorded after the records are written
+  int refs = 0;                 // events that may still read them
+  int64_t last = 0;             // last use (LRU)
+};
+constexpr int XCACHE_MAX = 4;  // entries per bank
+
 struct Bank {
   uint64_t id = 0;
   int64_t I = 0;
@@ -90,6 +104,7 @@ struct Bank {
   void *block = nullptr;
   size_t bytes = 0;
   int refs = 0;
+  std::vector<XEntry *> xcache;
 };
 
 struct Event {
@@ -99,6 +114,8 @@ struct Event {
   int64_t i0 = 0, NI = 0, NE = 0;
   int64_t block_rows = 0;  // rows per streamed bank block (0: the whole slice)
   uint64_t group = 0;      // batch of dotpe_batch_submit (0: none)
+  uint64_t psd_key = 0;    // hash of (n_det, PSD values): the cross-term cache key
+  XEntry *xent = nullptr;  // cross terms in use
   std::string launch_error;  // why the launch failed on the host (state FAILED, device status 0)
   int D = 0, nphi = 0, prec = 0, flags = 0;
   double u_min = 0, cut = 0;
@@ -436,8 +453,12 @@ static int event_begin(Event &e, EventRun &R, cudaStream_t st) {
 // Rows [r0, r0 + nr) of the slice as the current bank block of the plan.
 static void event_block(dotpe_ctx *ctx, Event &e, EventRun &R, int64_t r0, int64_t nr, cudaStream_t st) {
   Bank &b = *e.bank;
-  launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, (float *)(R.scr + R.L.mx),
-                     ctx->n_sms, st);
+  if (e.xent) {
+    R.P.mx = e.xent->mx + (e.i0 + r0) * e.D * REC;
+  } else {
+    launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, (float *)(R.scr + R.L.mx),
+                       ctx->n_sms, st);
+  }
   R.P.n_int = nr;
   R.P.i_base = e.i0 + r0;
   R.P.lw_int = b.lw ? b.lw + e.i0 + r0 : nullptr;
@@ -548,12 +569,66 @@ static int event_free(Event &e, EventRun &R, cudaStream_t st) {
 
 static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st);
 
+// The event's cross terms: a cached entry of its bank for its PSD, or a new
+// entry computed now for every bank row on `st` (outside any capture) when the
+// slice covers at least a quarter of the bank (a smaller slice computes its own
+// rows into its scratch instead).  The stream waits for the entry's records.
+// Entries past XCACHE_MAX per bank are dropped least recently used first, when
+// no event holds them.
+static int xterms_acquire(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
+  Bank &b = *e.bank;
+  XEntry *x = nullptr;
+  for (XEntry *c : b.xcache)
+    if (c->key == e.psd_key && c->D == e.D) x = c;
+  if (x) {
+    CUDA_OR_FAIL(cudaStreamWaitEvent(st, x->ready, 0));
+  } else if (4 * e.NI < b.I) {
+    return DOTPE_OK;
+  } else {
+    if ((int)b.xcache.size() >= XCACHE_MAX) {
+      auto victim = b.xcache.end();
+      for (auto it = b.xcache.begin(); it != b.xcache.end(); ++it)
+        if ((*it)->refs == 0 && (victim == b.xcache.end() || (*it)->last < (*victim)->last)) victim = it;
+      if (victim != b.xcache.end()) {
+        XEntry *v = *victim;
+        CUDA_OR_FAIL(cudaEventSynchronize(v->ready));
+        CUDA_OR_FAIL(cudaFree(v->mx));
+        cudaEventDestroy(v->ready);
+        ctx->used -= v->bytes;
+        delete v;
+        b.xcache.erase(victim);
+      }
+    }
+    x = new XEntry();
+    x->key = e.psd_key;
+    x->D = e.D;
+    x->bytes = (size_t)b.I * e.D * REC * sizeof(float);
+    if (cudaMallocAsync((void **)&x->mx, x->bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      delete x;
+      return fail(DOTPE_E_NOMEM, "cross-term records (%zu bytes)", (size_t)b.I * e.D * REC * sizeof(float));
+    }
+    CUDA_OR_FAIL(cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming));
+    // omega of this event (its prep on `st` writes it) -> records of every bank row
+    launch_prep(R.pa, st);
+    launch_cross_terms(b.I, 0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, x->mx, ctx->n_sms, st);
+    CUDA_OR_FAIL(cudaEventRecord(x->ready, st));
+    ctx->used += x->bytes;
+    b.xcache.push_back(x);
+  }
+  x->refs++;
+  x->last = now_ns();
+  e.xent = x;
+  return DOTPE_OK;
+}
+
 // One event on its slot stream, its slice in bank blocks.
 static int run_event(dotpe_ctx *ctx, Event &e) {
   cudaStream_t st = ctx->streams[e.slot];
   EventRun R;
   int rc = event_alloc(ctx, e, st, R);
   if (rc != DOTPE_OK) return rc;
+  if ((rc = xterms_acquire(ctx, e, R, st)) != DOTPE_OK) return rc;
   if ((rc = event_begin(e, R, st)) != DOTPE_OK) return rc;
   const int64_t BR = R.L.block_rows;
   const int n_blocks = (int)((e.NI + BR - 1) / BR);
@@ -652,6 +727,7 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
   for (int k = 0; k < n; ++k) {
     int rc = event_alloc(ctx, *evs[k], st, R[k]);
     if (rc != DOTPE_OK) return rc;
+    if ((rc = xterms_acquire(ctx, *evs[k], R[k], st)) != DOTPE_OK) return rc;
   }
   const int prec = evs[0]->prec;
   const bool mixed = (prec == DOTPE_PREC_MIXED);
@@ -808,6 +884,10 @@ static void progress(dotpe_ctx *ctx) {
         if (e.prec == DOTPE_PREC_MIXED && cudaEventElapsedTime(&ms, e.ev_ks, e.ev_k1) == cudaSuccess) e.refine_ms = ms;
         if (e.t_done == 0) e.t_done = now_ns();
         ctx->slot_busy[e.slot]--;
+        if (e.xent) {
+          e.xent->refs--;
+          e.xent = nullptr;
+        }
         ctx->used -= e.scratch_bytes + e.in_bytes;
         e.scratch_bytes = 0;
         e.in_bytes = 0;
@@ -885,6 +965,7 @@ static void progress(dotpe_ctx *ctx) {
 
 static void free_event(dotpe_ctx *ctx, Event *e) {
   if (e->state == DOTPE_STATE_RUNNING) cudaEventSynchronize(e->ev_end);
+  if (e->xent) e->xent->refs--;
   if (e->keep_block) cudaFree(e->keep_block);
   if (e->in_block) cudaFree(e->in_block);
   if (e->in_stage) cudaFreeHost(e->in_stage);
@@ -1155,6 +1236,12 @@ int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id) {
   if (it->second->refs > 0) return fail(DOTPE_E_INVALID, "bank still used by %d events", it->second->refs);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (XEntry *x : it->second->xcache) {
+    cudaFree(x->mx);
+    cudaEventDestroy(x->ready);
+    ctx->used -= x->bytes;
+    delete x;
+  }
   cudaFree(it->second->block);
   ctx->used -= it->second->bytes;
   delete it->second;
@@ -1264,6 +1351,24 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
       so += p.n;
       if (copy_in(p.dst, hs, p.n, ist) != DOTPE_OK) return cleanup(DOTPE_E_DEVICE);
     }
+  }
+  {
+    // cross-term cache key: FNV-1a over n_det and the PSD bytes
+    std::vector<double> ps((size_t)(D * B));
+    if (is_device_ptr(d->psd)) {
+      if (cudaMemcpy(ps.data(), d->psd, ps.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cleanup(fail(DOTPE_E_DEVICE, "reading the PSD"));
+    } else {
+      memcpy(ps.data(), d->psd, ps.size() * 8);
+    }
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+      const uint8_t *c = (const uint8_t *)p;
+      for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
+    };
+    mix(&e->D, sizeof(e->D));
+    mix(ps.data(), ps.size() * 8);
+    e->psd_key = h;
   }
   cudaEventCreateWithFlags(&e->ev_inputs, cudaEventDisableTiming);
   cudaEventCreate(&e->ev_start);

@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(NT, 1)
     const int half = ew >> 2;     // which 16 of the tile's 32 extrinsic samples
     const int row = quad * 32 + lane;
     const int etid = threadIdx.x - 64;
-    const EpiParams &P = T.ep;
+    // one event: its parameters straight from kernel-parameter space (constant
+    // bank); a batch: the current event's copy in shared memory
+    const EpiParams &P = (NB == 1) ? Bt.w[0].P : T.ep;
     bool store = false;
     float zs = 1.f;
     float mrec[MAXD * REC];
