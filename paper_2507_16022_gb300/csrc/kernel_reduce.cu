@@ -21,35 +21,42 @@ constexpr int NB = 128;  // blocks of the parallel passes
 constexpr int NQ = 3;    // log-sum-exp inputs of a bank block: tile m1, tile m2, 2 ln P_i
 }
 
-// ln P over partials [nparts][n] (row or column marginal), one thread per entry.
-// With acc != nullptr the value is merged into the FP64 accumulator acc[k] = (m, s)
-// (s = 0: empty) instead of written to out.
-__global__ void reduce_lines_kernel(int64_t n, int nparts, const float2 *__restrict__ part, double *__restrict__ out,
-                                    double2 *__restrict__ acc, int first) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  float m = -INFINITY;
-  for (int p = 0; p < nparts; ++p) {
-    float2 v = part[(int64_t)p * n + k];
-    if (v.y > 0.f) m = fmaxf(m, v.x);
-  }
-  double s = 0.0;
-  if (m != -INFINITY)
-    for (int p = 0; p < nparts; ++p) {
-      float2 v = part[(int64_t)p * n + k];
-      if (v.y > 0.f) s += (double)v.y * exp((double)v.x - (double)m);
+// ln P over partials [nparts][n] (row or column marginal).  A block takes 32
+// consecutive entries (coalesced) and splits the parts over its 8 thread rows;
+// each thread keeps an online (max, sum) in FP64 and the rows merge in shared
+// memory.  With acc != nullptr the value is merged into the FP64 accumulator
+// acc[k] = (m, s) (s = 0: empty) instead of written to out.
+constexpr int LX = 32, LY = 8;
+
+__device__ __forceinline__ void lse_add(double &m, double &s, double x, double w) {
+  if (!(w > 0.0)) return;
+  if (!(s > 0.0)) { m = x; s = w; return; }
+  if (x > m) { s = s * exp(m - x) + w; m = x; }
+  else s += w * exp(x - m);
+}
+
+__global__ void __launch_bounds__(LX * LY) reduce_lines_kernel(int64_t n, int nparts, const float2 *__restrict__ part,
+                                                               double *__restrict__ out, double2 *__restrict__ acc,
+                                                               int first) {
+  __shared__ double sm[LY][LX], ss[LY][LX];
+  const int64_t k = blockIdx.x * (int64_t)LX + threadIdx.x;
+  double m = 0.0, s = 0.0;
+  if (k < n)
+    for (int p = threadIdx.y; p < nparts; p += LY) {
+      const float2 v = part[(int64_t)p * n + k];
+      if (v.y > 0.f) lse_add(m, s, (double)v.x, (double)v.y);
     }
+  sm[threadIdx.y][threadIdx.x] = m;
+  ss[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y != 0 || k >= n) return;
+  for (int y = 1; y < LY; ++y) lse_add(m, s, sm[y][threadIdx.x], ss[y][threadIdx.x]);
   if (!acc) {
-    out[k] = (m == -INFINITY) ? -INFINITY : (double)m + log(s);
+    out[k] = (s > 0.0) ? m + log(s) : -INFINITY;
     return;
   }
   double2 a = first ? make_double2(0.0, 0.0) : acc[k];
-  if (s > 0.0) {
-    const double bm = (double)m;
-    if (!(a.y > 0.0)) a = make_double2(bm, s);
-    else if (bm > a.x) a = make_double2(bm, a.y * exp(a.x - bm) + s);
-    else a.y += s * exp(bm - a.x);
-  }
+  lse_add(a.x, a.y, m, s);
   acc[k] = a;
 }
 
@@ -241,10 +248,11 @@ size_t reduce_scratch_bytes() {
 }
 
 void launch_reduce_block(const ReduceArgs &a, cudaStream_t st) {
-  reduce_lines_kernel<<<(unsigned)((a.n_int + 255) / 256), 256, 0, st>>>(a.n_int, a.n_etile, a.row_part,
-                                                                        a.ln_p_int + a.row_offset, nullptr, 0);
-  reduce_lines_kernel<<<(unsigned)((a.n_ext + 255) / 256), 256, 0, st>>>(a.n_ext, a.n_itile, a.col_part, nullptr,
-                                                                        a.acc_col, a.first);
+  const dim3 lb(LX, LY);
+  reduce_lines_kernel<<<(unsigned)((a.n_int + LX - 1) / LX), lb, 0, st>>>(a.n_int, a.n_etile, a.row_part,
+                                                                         a.ln_p_int + a.row_offset, nullptr, 0);
+  reduce_lines_kernel<<<(unsigned)((a.n_ext + LX - 1) / LX), lb, 0, st>>>(a.n_ext, a.n_itile, a.col_part, nullptr,
+                                                                         a.acc_col, a.first);
   uint8_t *w = (uint8_t *)a.scratch;
   float *bmax = (float *)w;
   double *bsum = (double *)(w + NB * NQ * sizeof(float));
