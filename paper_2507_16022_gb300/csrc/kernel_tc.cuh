@@ -182,23 +182,29 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
-      uint32_t q = 0, u = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++u) {
-        const int b = u & 1;
-        const uint32_t use = u >> 1;
-        if (use > 0 && !(ok = mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, wait_ns))) break;
-        tc_fence_after();
-        for (int m = 0; m < M && ok; ++m) {
-          const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
-          for (int ks = 0; ks < nst; ++ks, ++q) {
-            const int s = q % ST;
-            const uint32_t n = q / ST;
-            if (!(ok = mbar_wait(&T.full[s], n & 1, nullptr, abortp, wait_ns))) break;
-            tc_fence_after();
+    // ---------------- MMA issuer ----------------
+    // The whole warp walks the schedule (so descriptors and addresses stay
+    // warp-uniform); lane 0 issues every MMA and commit (a commit tracks the
+    // MMAs of the thread that issues it).
+    constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
+    const bool issuer = (lane == 0);
+    uint32_t q = 0, u = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++u) {
+      const int b = u & 1;
+      const uint32_t use = u >> 1;
+      if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, wait_ns));
+      if (!ok) break;
+      tc_fence_after();
+      for (int m = 0; m < M && ok; ++m) {
+        const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
+        for (int ks = 0; ks < nst; ++ks, ++q) {
+          const int s = q % ST;
+          const uint32_t n = q / ST;
+          ok = __all_sync(0xffffffffu, mbar_wait(&T.full[s], n & 1, nullptr, abortp, wait_ns));
+          if (!ok) break;
+          tc_fence_after();
+          if (issuer) {
 #pragma unroll
             for (int kx = 0; kx < KBX; ++kx) {
               const uint64_t ah = sdesc_k128(sA + (s * NPL) * A_ST + kx * A_BYTES);
@@ -216,14 +222,17 @@ __global__ void __launch_bounds__(NT, 1)
             }
             tc_commit(&T.empty[s]);
           }
+          __syncwarp();
         }
-        if (ok) tc_commit(&T.tfull[b]);
       }
-      // all MMAs of this CTA complete before TMEM is released
-      tc_commit(&T.drain);
-      volatile int no_abort = 0;
-      mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
+      if (ok && issuer) tc_commit(&T.tfull[b]);
+      __syncwarp();
     }
+    // all MMAs of this CTA complete before TMEM is released
+    if (issuer) tc_commit(&T.drain);
+    __syncwarp();
+    volatile int no_abort = 0;
+    mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
   } else {
     // ---------------- epilogue (256 threads: one tile row, half the samples each) ----------------
     const int ew = warp - 2;      // 0..7
