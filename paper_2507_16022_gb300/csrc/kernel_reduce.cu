@@ -183,23 +183,45 @@ __device__ __forceinline__ void acc_merge(double &am, double &as, double bm, dou
 __global__ void reduce_block_merge_kernel(ReduceArgs a, int nb, const float *__restrict__ bmax,
                                           const double *__restrict__ bsum, const float *__restrict__ bml,
                                           const long long *__restrict__ barg, const long long *__restrict__ bnp) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  EvAcc c = a.first ? EvAcc{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, -1.f, 0x7fffffffffffffffLL, 0} : *a.acc;
-  double *dst[NQ][2] = {{&c.s1_m, &c.s1_s}, {&c.s2_m, &c.s2_s}, {&c.pi_m, &c.pi_s}};
+  // one warp; lane l takes the per-block entries l, l + 32, ...; fixed shuffle order
+  const int lane = threadIdx.x;
+  double m[NQ], sm[NQ];
   for (int q = 0; q < NQ; ++q) {
-    float m = -INFINITY;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) m = fmaxf(m, bmax[q * nb + b]);
-    for (int b = 0; b < nb; ++b) s += bsum[q * nb + b];
-    if (m != -INFINITY) acc_merge(*dst[q][0], *dst[q][1], (double)m, s);
+    float mq = -INFINITY;
+    double sq = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+      mq = fmaxf(mq, bmax[q * nb + b]);
+      sq += bsum[q * nb + b];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+      sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
+    m[q] = mq;
+    sm[q] = sq;
   }
   // arguments are packed ((i * n_ext + e) * n_phi + o) with i relative to the block
   const long long shift = (long long)a.row_offset * a.n_ext * a.n_phi;
-  for (int b = 0; b < nb; ++b) {
+  float best = -1.f;
+  long long arg = 0x7fffffffffffffffLL, np = 0;
+  for (int b = lane; b < nb; b += 32) {
     const long long g = barg[b] + shift;
-    if (bml[b] > c.best || (bml[b] == c.best && g < c.arg)) { c.best = bml[b]; c.arg = g; }
-    c.n_marg += bnp[b];
+    if (bml[b] > best || (bml[b] == best && g < arg)) { best = bml[b]; arg = g; }
+    np += bnp[b];
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const long long oa = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    np += __shfl_xor_sync(0xffffffffu, np, o);
+  }
+  if (lane != 0) return;
+  EvAcc c = a.first ? EvAcc{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, -1.f, 0x7fffffffffffffffLL, 0} : *a.acc;
+  double *dst[NQ][2] = {{&c.s1_m, &c.s1_s}, {&c.s2_m, &c.s2_s}, {&c.pi_m, &c.pi_s}};
+  for (int q = 0; q < NQ; ++q)
+    if (m[q] != -INFINITY) acc_merge(*dst[q][0], *dst[q][1], m[q], sm[q]);
+  if (best > c.best || (best == c.best && arg < c.arg)) { c.best = best; c.arg = arg; }
+  c.n_marg += np;
   *a.acc = c;
 }
 

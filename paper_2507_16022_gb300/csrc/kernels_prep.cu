@@ -12,6 +12,7 @@
 //  K9  build_dm_table         FP64 Gauss-Legendre table of the distance-marginal remainder
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "dist_marg.cuh"
@@ -162,39 +163,54 @@ __device__ __forceinline__ float pow2_scale(float maxabs) {
   return ldexpf(1.0f, -ex);
 }
 
-// Real-ified operand rows: (e, re) = [Gr | -Gi], (e, im) = [Gi | Gr], K padded with zeros.
+// Real-ified operand rows: (e, re) = [Gr | -Gi], (e, im) = [Gi | Gr], K padded with zeros
+// (the bank rows use the same column order: [Re h | Im h | 0]).
 // kind: 0 = fp32 plane, 1 = bf16 hi, 2 = fp16 hi; nplanes == 2 adds the lo plane
-// RN(v - hi) of the same type.
+// RN(v - hi) of the same type.  One thread per (m, e, c): for c < B it reads
+// G[m][e][c] once and writes the four entries that hold it (columns c and B + c
+// of both rows); for c < Kpad - 2B it zeroes column 2B + c of both rows.
+template <typename T>
+__device__ __forceinline__ void put(void *out, int64_t total, int64_t k, float v, int nplanes) {
+  if constexpr (sizeof(T) == 4) {
+    ((float *)out)[k] = v;
+  } else {
+    T hi;
+    float hf;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) { hi = __float2bfloat16_rn(v); hf = __bfloat162float(hi); }
+    else { hi = __float2half_rn(v); hf = __half2float(hi); }
+    ((T *)out)[k] = hi;
+    if (nplanes == 2) {
+      if constexpr (std::is_same<T, __nv_bfloat16>::value) ((T *)out)[total + k] = __float2bfloat16_rn(v - hf);
+      else ((T *)out)[total + k] = __float2half_rn(v - hf);
+    }
+  }
+}
+
+template <typename T>
 __global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *__restrict__ G,
                               const float *__restrict__ gmax, int kind, int nplanes, void *__restrict__ out,
                               float *__restrict__ scale_out) {
-  int64_t total = (int64_t)M * 2 * E * Kpad;
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float sc = (kind == 0) ? 1.0f : pow2_scale(*gmax) * (kind == 2 ? FP16_OPERAND_SCALE : 1.0f);
+  const int pad = Kpad - 2 * B;
+  const int P = B > pad ? B : pad;  // threads per (m, e)
+  const int64_t total = (int64_t)M * 2 * E * Kpad;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const float sc = (kind == 0) ? 1.0f : pow2_scale(*gmax) * (kind == 2 ? FP16_OPERAND_SCALE : 1.0f);
   if (k == 0 && scale_out) *scale_out = sc;
-  if (k >= total) return;
-  int col = (int)(k % Kpad);
-  int64_t row = k / Kpad;  // m * 2E + 2e + ri
-  int ri = (int)(row & 1);
-  int64_t me = row >> 1;   // m * E + e
-  float v = 0.f;
-  if (col < 2 * B) {
-    int b = col < B ? col : col - B;
-    float2 g = G[me * B + b];
-    if (ri == 0) v = (col < B) ? g.x : -g.y;
-    else v = (col < B) ? g.y : g.x;
+  if (k >= (int64_t)M * E * P) return;
+  const int c = (int)(k % P);
+  const int64_t me = k / P;  // m * E + e
+  const int64_t re = (2 * me) * Kpad, im = (2 * me + 1) * Kpad;
+  if (c < B) {
+    const float2 g = G[me * B + c];
+    const float gr = g.x * sc, gi = g.y * sc;
+    put<T>(out, total, re + c, gr, nplanes);
+    put<T>(out, total, re + B + c, -gi, nplanes);
+    put<T>(out, total, im + c, gi, nplanes);
+    put<T>(out, total, im + B + c, gr, nplanes);
   }
-  v *= sc;
-  if (kind == 0) {
-    ((float *)out)[k] = v;
-  } else if (kind == 1) {
-    __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    ((__nv_bfloat16 *)out)[k] = hi;
-    if (nplanes == 2) ((__nv_bfloat16 *)out)[total + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
-  } else {
-    __half hi = __float2half_rn(v);
-    ((__half *)out)[k] = hi;
-    if (nplanes == 2) ((__half *)out)[total + k] = __float2half_rn(v - __half2float(hi));
+  if (c < pad) {
+    put<T>(out, total, re + 2 * B + c, 0.f, nplanes);
+    put<T>(out, total, im + 2 * B + c, 0.f, nplanes);
   }
 }
 
@@ -383,9 +399,16 @@ void launch_prep(const PrepArgs &a, cudaStream_t st) {
   prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, a.th, a.tl, a.Rf, a.qx, a.status);
   build_G_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.Rf, a.G32,
                                                        a.gmax);
-  int64_t total = (int64_t)a.M * 2 * a.E * a.Kpad;
-  pack_G_kernel<<<nblk(total, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, a.pack_kind, a.pack_planes,
-                                                  a.gpack, a.gscale);
+  const int pad = a.Kpad - 2 * a.B;
+  const int64_t n = (int64_t)a.M * a.E * (a.B > pad ? a.B : pad);
+  if (a.pack_kind == 0)
+    pack_G_kernel<float><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, 0, 1, a.gpack, a.gscale);
+  else if (a.pack_kind == 1)
+    pack_G_kernel<__nv_bfloat16><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, 1, a.pack_planes,
+                                                               a.gpack, a.gscale);
+  else
+    pack_G_kernel<__half><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, 2, a.pack_planes,
+                                                        a.gpack, a.gscale);
 }
 
 void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
