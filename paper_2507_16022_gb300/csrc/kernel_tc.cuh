@@ -12,10 +12,14 @@
 //               <h|h> coefficients, phase grid, ML cut, distance marginal,
 //               log-sum-exp partials
 // Tile = 128 bank rows x 32 extrinsic samples, all modes: accumulators for mode
-// m live in TMEM columns [buf*256 + 64 m, +64) (two buffers, so the epilogue of
-// tile t overlaps the MMAs of tile t+1).  Per mode the GEMM is the real-ified
-// complex product of Eq. dh_ieo (K = 2B, padded to a multiple of 64); split
-// precision adds passes over hi/lo operand planes into the same accumulator.
+// m live in TMEM columns [buf*256 + 64 m, +64).  Per mode the GEMM is the
+// real-ified complex product of Eq. dh_ieo (K = 2B, padded to a multiple of 64).
+// Single pass: two buffers, so the epilogue of tile t overlaps the MMAs of tile
+// t+1.  Split precision: hi*hi accumulates in the first buffer and the small
+// hi*lo + lo*hi terms in the second, added in the epilogue.  The tensor cores'
+// FP32 accumulation truncates at every step, so keeping the small terms out of
+// the large accumulator shortens its chain of truncating additions threefold
+// (the cost: no overlap of a split tile's epilogue with the next tile's MMAs).
 //
 // One launch serves a batch of events over one bank (a single event is a batch
 // of one): the work items are the events' tiles one event after the other
@@ -191,13 +195,14 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t q = 0, u = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++u) {
-      const int b = u & 1;
-      const uint32_t use = u >> 1;
+      const int b = SPLIT ? 0 : (u & 1);
+      const uint32_t use = SPLIT ? u : (u >> 1);
       if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, wait_ns));
       if (!ok) break;
       tc_fence_after();
       for (int m = 0; m < M && ok; ++m) {
         const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
+        const uint32_t dlo = tmem + BUF_COLS + m * BN;  // split: the hi*lo + lo*hi accumulator
         for (int ks = 0; ks < nst; ++ks, ++q) {
           const int s = q % ST;
           const uint32_t n = q / ST;
@@ -215,8 +220,8 @@ __global__ void __launch_bounds__(NT, 1)
               for (int k = 0; k < BK / 16; ++k) {
                 tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
                 if (SPLIT) {
-                  tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
-                  tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+                  tc_mma(dlo, ah + 2 * k, bl + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);  // hi * lo
+                  tc_mma(dlo, al + 2 * k, bh + 2 * k, idesc, 1u);                      // lo * hi
                 }
               }
             }
@@ -250,8 +255,8 @@ __global__ void __launch_bounds__(NT, 1)
     int cur_it = -1, cur_k = -1;
     uint32_t u = 0;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++u) {
-      const int b = u & 1;
-      const uint32_t use = u >> 1;
+      const int b = SPLIT ? 0 : (u & 1);
+      const uint32_t use = SPLIT ? u : (u >> 1);
       int k, it, et;
       work_tile(Bt, w, k, it, et);
       if (k != cur_k) {
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(NT, 1)
       long long barg = 0x7fffffffffffffffLL;
       int np = 0;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * BUF_COLS;
-      if (P.screen_ml && !store && !P.gemm_only) {
+      if (!SPLIT && P.screen_ml && !store && !P.gemm_only) {
         // Screening without stored values needs only the tile's best ln L^ML.
         // Pass 1 bounds every pair of this thread (bounds kept in the thread's
         // own xs entries); pass 2 evaluates pairs in decreasing bound order
@@ -403,6 +408,20 @@ __global__ void __launch_bounds__(NT, 1)
         for (int m = 0; m < MAXM; ++m) {
           if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
           else { Zr[m] = 0.f; Zi[m] = 0.f; }
+        }
+        if (SPLIT) {
+          float Lr[MAXM], Li[MAXM];
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) {
+            if (m < M) tmem_ld2(tbase + BUF_COLS + m * BN + 2 * el, Lr[m], Li[m]);
+            else { Lr[m] = 0.f; Li[m] = 0.f; }
+          }
+          tmem_ld_wait();
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) {
+            Zr[m] += Lr[m];
+            Zi[m] += Li[m];
+          }
         }
         tmem_ld_wait();
         if (j == EHALF - 1) {
