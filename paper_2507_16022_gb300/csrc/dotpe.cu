@@ -199,8 +199,8 @@ static void CUDART_CB mark_done(void *p) {
 // ---------------------------------------------------------------------------
 struct ScratchLayout {
   size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, sqrt_dd, gpack, mx, tile_part, tile_ml, tile_arg,
-      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, n_list_total, sel_counts, acc, acc_col,
-      status, red, total;
+      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, n_list_total, sel_counts, sep, acc,
+      acc_col, status, red, total;
   int64_t block_rows;  // bank rows per streamed block (the whole slice when not streamed)
   int n_itile, n_etile, pack_kind, pack_planes, TI, TE;  // n_itile: tiles of one block
 };
@@ -256,6 +256,7 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.list = c.take<int2>(mixed ? T : 0);
   L.n_list = c.take<int>(1);
   L.n_list_total = c.take<int>(1);
+  L.sep = c.take<int>(1);
   L.sel_counts = c.take<int>(mixed ? select_count_blocks((int)T) : 0);
   L.acc = c.take<EvAcc>(1);
   L.acc_col = c.take<double2>(E);
@@ -303,6 +304,7 @@ static int tc_launch_of(dotpe_ctx *ctx, const Bank &b, int prec, TcLaunch &T) {
   T.C.n_modes = b.M;
   T.bf16 = bf;
   T.split = prec_split(prec) && prec != DOTPE_PREC_MIXED;
+  T.sep = T.split;  // full split runs keep the low-order terms apart (precision first)
   T.consec = true;
   for (int m = 1; m < b.M; ++m)
     if (b.mode_m[m] != b.mode_m[m - 1] + 1) T.consec = false;
@@ -540,12 +542,20 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
   sb.list = (int2 *)(R.scr + R.L.list);
   sb.n_list = (int *)(R.scr + R.L.n_list_total);
   sb.counts = (int *)(R.scr + R.L.sel_counts);
+  sb.sep = (int *)(R.scr + R.L.sep);
   launch_select(sb, st);
   CUDA_OR_FAIL(cudaGetLastError());
   W.P = refine_params(R);
+  // two variants, gated per event by its screened maximum: the shared
+  // accumulator, or the separate low-order accumulator above SEP_ML
   T.split = true;
-  r = launch_tc(T, &W, 1, sb.list, sb.n_list, st);
-  if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+  T.gate = sb.sep;
+  for (int want = 0; want < 2; ++want) {
+    T.sep = want == 1;
+    T.gate_want = want;
+    r = launch_tc(T, &W, 1, sb.list, sb.n_list, st);
+    if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
+  }
   return DOTPE_OK;
 }
 
@@ -678,6 +688,7 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
   int rc = tc_launch_of(ctx, *e.bank, e.prec, T);
   if (rc != DOTPE_OK) return rc;
   T.split = split_main;
+  T.sep = split_main;
   std::vector<int> cand;
   for (int c = 1; c < R.W.n_etile; c *= 2) cand.push_back(c);
   cand.push_back(R.W.n_etile);
@@ -735,12 +746,13 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
   for (int k = 0; k < n; ++k) total_tiles += (int)((evs[k]->NI + TC_TI - 1) / TC_TI) * R[k].L.n_etile;
   // batch-wide (event, tile) list of the refinement
   uint8_t *blist = nullptr;
-  size_t o_list = 0, o_n = 0, o_counts = 0;
+  size_t o_list = 0, o_n = 0, o_counts = 0, o_sep = 0;
   if (mixed) {
     Carver c;
     o_list = c.take<int2>(total_tiles);
     o_n = c.take<int>(1);
     o_counts = c.take<int>(select_count_blocks(total_tiles));
+    o_sep = c.take<int>(TC_MAXB);
     CUDA_OR_FAIL(cudaMallocAsync((void **)&blist, c.off, st));
   }
   TcLaunch T;
@@ -773,6 +785,7 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
         }
         TcLaunch T1 = T;
         T1.split = prec_split(prec) && !mixed;
+        T1.sep = T1.split;
         int r = launch_tc(T1, &W[k0], m, nullptr, nullptr, st);
         if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
       }
@@ -795,13 +808,20 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
           sb.list = glist;
           sb.n_list = gn;
           sb.counts = (int *)(blist + o_counts);
+          sb.sep = (int *)(blist + o_sep);
           launch_select(sb, st);
           CUDA_OR_FAIL(cudaGetLastError());
           for (int k = k0; k < k0 + m; ++k) W[k].P = refine_params(R[k]);
           TcLaunch T2 = T;
           T2.split = true;
-          int r = launch_tc(T2, &W[k0], m, glist, gn, st);
-          if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
+          T2.gate = sb.sep;
+          for (int want = 0; want < 2; ++want) {
+            T2.sep = want == 1;
+            T2.gate_want = want;
+            int r = launch_tc(T2, &W[k0], m, glist, gn, st);
+            if (r != 0)
+              return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
+          }
         }
       }
     }

@@ -75,29 +75,12 @@ int launch_tc_nb(const TcLaunch &L, const TcWork *works, int n, const int2 *glis
   bt->n = n;
   bt->glist = glist;
   bt->glist_n = glist_n;
+  bt->gate = L.gate;
+  bt->gate_want = L.gate_want;
   // a list's length is known on the device only: one CTA per SM
   int grid = (glist || L.n_sms < total) ? L.n_sms : total;
   if (grid < 1) grid = 1;
-  auto go = [&](auto kern, size_t smem) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, NT, smem, st>>>(L.mapA, *bt, L.C);
-    return cudaGetLastError();
-  };
-  cudaError_t err;
-  if (L.split && L.bf16) {
-    err = L.consec ? go(tc_fused_kernel<true, true, true, NB>, smem_bytes<true>())
-                   : go(tc_fused_kernel<true, false, true, NB>, smem_bytes<true>());
-  } else if (L.split) {
-    err = L.consec ? go(tc_fused_kernel<false, true, true, NB>, smem_bytes<true>())
-                   : go(tc_fused_kernel<false, false, true, NB>, smem_bytes<true>());
-  } else if (L.bf16) {
-    err = L.consec ? go(tc_fused_kernel<true, true, false, NB>, smem_bytes<false>())
-                   : go(tc_fused_kernel<true, false, false, NB>, smem_bytes<false>());
-  } else {
-    err = L.consec ? go(tc_fused_kernel<false, true, false, NB>, smem_bytes<false>())
-                   : go(tc_fused_kernel<false, false, false, NB>, smem_bytes<false>());
-  }
+  const cudaError_t err = launch_tc_any<NB>(L, *bt, grid, st);
   delete bt;
   return (int)err;
 }

@@ -14,12 +14,17 @@
 // Tile = 128 bank rows x 32 extrinsic samples, all modes: accumulators for mode
 // m live in TMEM columns [buf*256 + 64 m, +64).  Per mode the GEMM is the
 // real-ified complex product of Eq. dh_ieo (K = 2B, padded to a multiple of 64).
-// Single pass: two buffers, so the epilogue of tile t overlaps the MMAs of tile
-// t+1.  Split precision: hi*hi accumulates in the first buffer and the small
-// hi*lo + lo*hi terms in the second, added in the epilogue.  The tensor cores'
-// FP32 accumulation truncates at every step, so keeping the small terms out of
-// the large accumulator shortens its chain of truncating additions threefold
-// (the cost: no overlap of a split tile's epilogue with the next tile's MMAs).
+// Two buffers, so the epilogue of tile t overlaps the MMAs of tile t+1; split
+// precision adds the hi*lo and lo*hi passes into the same accumulator.  With
+// SEP (split only) hi*hi accumulates in the first buffer and the small
+// hi*lo + lo*hi terms in the second, added in the epilogue: the tensor cores'
+// FP32 accumulation truncates at every step, and keeping the small terms out of
+// the large accumulator shortens its chain of truncating additions threefold,
+// at the cost of the overlap of a tile's epilogue with the next tile's MMAs.
+// A launch may carry a gate: a device word per event; work items of events
+// whose word differs from the launch's expected value are skipped by every
+// role alike (two variants are launched, each event's word picks the one that
+// processes its tiles).
 //
 // One launch serves a batch of events over one bank (a single event is a batch
 // of one): the work items are the events' tiles one event after the other
@@ -109,10 +114,11 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
   super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
 }
 
-template <bool BF16, bool CONSEC, bool SPLIT, int NB>
+template <bool BF16, bool CONSEC, bool SPLIT, int NB, bool SEP>
 __global__ void __launch_bounds__(NT, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcBatch<NB> Bt,
                     const TcCommon C) {
+  static_assert(SPLIT || !SEP, "a separate low-order accumulator needs split operands");
   constexpr int ST = Pipe<SPLIT>::ST, NPL = Pipe<SPLIT>::NPL;
   constexpr uint32_t STAGE_BYTES = Pipe<SPLIT>::STAGE, A_ST = Pipe<SPLIT>::A_ST, B_ST = Pipe<SPLIT>::B_ST;
   extern __shared__ uint8_t smem_raw[];
@@ -159,6 +165,7 @@ __global__ void __launch_bounds__(NT, 1)
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
         int k, it, et;
         work_tile(Bt, w, k, it, et);
+        if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
         const TcEvent &W = Bt.w[k];
         for (int m = 0; m < M && ok; ++m) {
           const int arow = m * C.a_mode_rows + W.a_row0 + it * TI;
@@ -194,9 +201,15 @@ __global__ void __launch_bounds__(NT, 1)
     const bool issuer = (lane == 0);
     uint32_t q = 0, u = 0;
     bool ok = true;
-    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x, ++u) {
-      const int b = SPLIT ? 0 : (u & 1);
-      const uint32_t use = SPLIT ? u : (u >> 1);
+    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+      if (Bt.gate) {
+        int k, it, et;
+        work_tile(Bt, w, k, it, et);
+        if (Bt.gate[k] != Bt.gate_want) continue;
+      }
+      const int b = SEP ? 0 : (u & 1);
+      const uint32_t use = SEP ? u : (u >> 1);
+      ++u;
       if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, wait_ns));
       if (!ok) break;
       tc_fence_after();
@@ -219,9 +232,12 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k) {
                 tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
-                if (SPLIT) {
+                if (SEP) {
                   tc_mma(dlo, ah + 2 * k, bl + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);  // hi * lo
                   tc_mma(dlo, al + 2 * k, bh + 2 * k, idesc, 1u);                      // lo * hi
+                } else if (SPLIT) {
+                  tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
+                  tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
                 }
               }
             }
@@ -254,11 +270,13 @@ __global__ void __launch_bounds__(NT, 1)
     double lwi = 0.0;
     int cur_it = -1, cur_k = -1;
     uint32_t u = 0;
-    for (int w = blockIdx.x; w < n_work; w += gridDim.x, ++u) {
-      const int b = SPLIT ? 0 : (u & 1);
-      const uint32_t use = SPLIT ? u : (u >> 1);
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
       int k, it, et;
       work_tile(Bt, w, k, it, et);
+      if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
+      const int b = SEP ? 0 : (u & 1);
+      const uint32_t use = SEP ? u : (u >> 1);
+      ++u;
       if (k != cur_k) {
         // the next event: its parameters and phase tables into shared memory
         named_bar_sync(1, EPT);
@@ -409,7 +427,7 @@ __global__ void __launch_bounds__(NT, 1)
           if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
           else { Zr[m] = 0.f; Zi[m] = 0.f; }
         }
-        if (SPLIT) {
+        if (SEP) {
           float Lr[MAXM], Li[MAXM];
 #pragma unroll
           for (int m = 0; m < MAXM; ++m) {
@@ -540,6 +558,28 @@ __global__ void __launch_bounds__(NT, 1)
   // a wait that ran out leaves this CTA's tiles of every event unfinished
   if (threadIdx.x == 0 && T.abort_flag)
     for (int k = 0; k < Bt.n; ++k) atomicCAS(Bt.w[k].P.status, 0, DEV_E_TIMEOUT);
+}
+
+// Launches one instantiation chosen by the run-time flags (the kernel's
+// parameter block is copied from *bt at launch).
+template <int NB, bool SPLIT, bool SEP>
+cudaError_t launch_tc_variant(const TcLaunch &L, const TcBatch<NB> &bt, int grid, cudaStream_t st) {
+  auto go = [&](auto kern) -> cudaError_t {
+    const size_t smem = smem_bytes<SPLIT>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, smem, st>>>(L.mapA, bt, L.C);
+    return cudaGetLastError();
+  };
+  if (L.bf16) return L.consec ? go(tc_fused_kernel<true, true, SPLIT, NB, SEP>)
+                              : go(tc_fused_kernel<true, false, SPLIT, NB, SEP>);
+  return L.consec ? go(tc_fused_kernel<false, true, SPLIT, NB, SEP>) : go(tc_fused_kernel<false, false, SPLIT, NB, SEP>);
+}
+
+template <int NB>
+cudaError_t launch_tc_any(const TcLaunch &L, const TcBatch<NB> &bt, int grid, cudaStream_t st) {
+  if (!L.split) return launch_tc_variant<NB, false, false>(L, bt, grid, st);
+  return L.sep ? launch_tc_variant<NB, true, true>(L, bt, grid, st) : launch_tc_variant<NB, true, false>(L, bt, grid, st);
 }
 
 }  // namespace dotpe

@@ -13,29 +13,12 @@ int launch_tc_single(const TcLaunch &L, const TcWork *works, const int2 *glist, 
   bt.n = 1;
   bt.glist = glist;
   bt.glist_n = glist_n;
+  bt.gate = L.gate;
+  bt.gate_want = L.gate_want;
   const int total = bt.begin[1];
   int grid = (glist || L.n_sms < total) ? L.n_sms : total;
   if (grid < 1) grid = 1;
-  auto go = [&](auto kern, size_t smem) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, NT, smem, st>>>(L.mapA, bt, L.C);
-    return cudaGetLastError();
-  };
-  cudaError_t err;
-  if (L.split && L.bf16) {
-    err = L.consec ? go(tc_fused_kernel<true, true, true, 1>, smem_bytes<true>())
-                   : go(tc_fused_kernel<true, false, true, 1>, smem_bytes<true>());
-  } else if (L.split) {
-    err = L.consec ? go(tc_fused_kernel<false, true, true, 1>, smem_bytes<true>())
-                   : go(tc_fused_kernel<false, false, true, 1>, smem_bytes<true>());
-  } else if (L.bf16) {
-    err = L.consec ? go(tc_fused_kernel<true, true, false, 1>, smem_bytes<false>())
-                   : go(tc_fused_kernel<true, false, false, 1>, smem_bytes<false>());
-  } else {
-    err = L.consec ? go(tc_fused_kernel<false, true, false, 1>, smem_bytes<false>())
-                   : go(tc_fused_kernel<false, false, false, 1>, smem_bytes<false>());
-  }
+  const cudaError_t err = launch_tc_any<1>(L, bt, grid, st);
   return (int)err;
 }
 

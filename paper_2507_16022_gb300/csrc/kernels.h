@@ -85,6 +85,8 @@ struct TcBatch {
   int n;                 // events
   const int2 *glist;     // list mode (device): work item -> (event, linear tile it * n_etile + et)
   const int *glist_n;    // its length (device)
+  const int *gate;       // optional [n] per event: items of event k run only if gate[k] == gate_want
+  int gate_want;
 };
 struct TcCommon {
   int kb;                          // k-blocks of 64 per mode (Kpad / 64)
@@ -95,8 +97,15 @@ struct TcLaunch {
   CUtensorMap mapA;  // bank operand planes [planes][M][I][Kpad]
   TcCommon C;
   bool bf16, split, consec;
+  bool sep;          // split: hi*lo + lo*hi in their own accumulator (see kernel_tc.cuh)
+  const int *gate;   // optional device words per event: event k's items run only if gate[k] == gate_want
+  int gate_want;
   int n_sms;
 };
+// A refinement whose screened maximum ln L^ML exceeds this uses the separate
+// low-order accumulator: below it, one shared FP32 accumulator keeps the
+// tensor-core truncation floor (~7e-6 ln L^ML) under 1e-3.
+constexpr float SEP_ML = 140.0f;
 // n <= TC_MAXB works; glist/glist_n non-null for list mode.  Returns a cudaError_t.
 int launch_tc(const TcLaunch &L, const TcWork *works, int n, const int2 *glist, const int *glist_n, cudaStream_t st);
 // extrinsic tiles per L2 band: the band's operand planes fill about l2_band_bytes
@@ -122,6 +131,7 @@ struct SelectBatch {
   int2 *list;              // out: (event, tile) items, event by event
   int *n_list;             // out: total
   int *counts;             // scratch: select_count_blocks(begin[n]) ints
+  int *sep;                // out [n]: 1 where the event's screened maximum exceeds SEP_ML
 };
 int select_count_blocks(int n_tiles);
 void launch_select(const SelectBatch &a, cudaStream_t st);
