@@ -593,7 +593,10 @@ def main():
         flops_issued += (8 * B * M * 3 + hh_flops) * pairs * refined / n_tiles
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops_alg / (dom_ms * 1e-3) / 1e12
-    launches_per_event = 5 + 1 + (4 if mixed else 1) + 5  # prep, cross terms, fused, reduction
+    # prep (data norm, bins, extrinsic, G build, G pack), fused (mixed: screen, 3 selection
+    # kernels, 2 gated refinement variants), reduction (2 line, 2 pass, merge, final);
+    # cross terms are computed once per (bank, PSD) and reused
+    launches_per_event = 5 + (6 if mixed else 1) + 6
     dlnz = max(abs(evs[k]["ln_z"] - ref_fp32[k % len(events)][0]["ln_z"]) for k in range(len(evs)))
     if rank != 0:
         if dist is not None:
