@@ -34,18 +34,28 @@ __device__ __forceinline__ void lse_add(double &m, double &s, double x, double w
   if (x > m) { s = s * exp(m - x) + w; m = x; }
   else s += w * exp(x - m);
 }
+// The same for FP32 partials: FP32 maximum and exponentials (the partials carry
+// FP32 precision), FP64 sum.
+__device__ __forceinline__ void lse_add_f(float &m, double &s, float x, float w) {
+  if (!(w > 0.f)) return;
+  if (!(s > 0.0)) { m = x; s = w; return; }
+  if (x > m) { s = s * (double)__expf(m - x) + (double)w; m = x; }
+  else s += (double)w * (double)__expf(x - m);
+}
 
 __global__ void __launch_bounds__(LX * LY) reduce_lines_kernel(int64_t n, int nparts, const float2 *__restrict__ part,
                                                                double *__restrict__ out, double2 *__restrict__ acc,
                                                                int first) {
   __shared__ double sm[LY][LX], ss[LY][LX];
   const int64_t k = blockIdx.x * (int64_t)LX + threadIdx.x;
-  double m = 0.0, s = 0.0;
+  float mf = 0.f;
+  double s = 0.0;
   if (k < n)
     for (int p = threadIdx.y; p < nparts; p += LY) {
       const float2 v = part[(int64_t)p * n + k];
-      if (v.y > 0.f) lse_add(m, s, (double)v.x, (double)v.y);
+      lse_add_f(mf, s, v.x, v.y);
     }
+  double m = mf;
   sm[threadIdx.y][threadIdx.x] = m;
   ss[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
