@@ -258,10 +258,15 @@ int dotpe_event_stream_wait(dotpe_ctx *ctx, uint64_t event_id, void *stream);
 int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out);
 
 /* Copies a block of per-pair or marginal results into out (host or device),
- * row-major with leading dimension ld (floats).  LNL_MARG / LNL_ML_MAX need
- * DOTPE_FLAG_STORE_LNL; i and e are relative to the event's slice.
+ * row-major with leading dimension ld (floats); i and e are relative to the
+ * event's slice.  LNL_MARG / LNL_ML_MAX come from the stored values when the
+ * event ran with DOTPE_FLAG_STORE_LNL; otherwise the block is recomputed
+ * synchronously from the event's inputs (kept until dotpe_event_release), in
+ * the event's arithmetic (split fp16 for MIXED), with the ML cut fixed at the
+ * event's final threshold (lnl_ml_threshold), on memory outside the budget
+ * for the duration of the call.
  * ROW_MARGINAL writes out[k] for i = i0+k; COL_MARGINAL out[k] for e = e0+k.
- * Errors: E_NOT_READY, E_NOT_FOUND, E_INVALID (range), E_UNSUPPORTED. */
+ * Errors: E_NOT_READY, E_NOT_FOUND, E_INVALID (range), E_NOMEM, E_DEVICE. */
 int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, int64_t e0,
                      int64_t e1, int what, float *out, int64_t ld);
 

@@ -117,6 +117,8 @@ struct Event {
   uint64_t psd_key = 0;    // hash of (n_det, PSD values): the cross-term cache key
   XEntry *xent = nullptr;  // cross terms in use
   std::string launch_error;  // why the launch failed on the host (state FAILED, device status 0)
+  float frozen_max = -1.f;   // >= 0: the cut's maximum is fixed at this value (block recomputation)
+  bool owns_inputs = true;   // false: the inputs belong to another event
   int D = 0, nphi = 0, prec = 0, flags = 0;
   double u_min = 0, cut = 0;
   bool has_lwe = false;
@@ -383,7 +385,7 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
   P.lw_ext = e.has_lwe ? e.lwe : nullptr;
   P.dm_table = ctx->dm_table;
   P.ml_running = (float *)(scr + L.ml_running);
-  P.track_max = P.cut_delta > 0.f ? 1 : 0;
+  P.track_max = (P.cut_delta > 0.f && e.frozen_max < 0.f) ? 1 : 0;
   P.sqrt_dd = pa.sqrt_dd;
   P.tile_part = (float4 *)(scr + L.tile_part);
   P.row_part = (float2 *)(scr + L.row_part);
@@ -445,7 +447,10 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
 // Stream work before the fused kernel: zeroed scalars, data weights, extrinsic operand.
 static int event_begin(Event &e, EventRun &R, cudaStream_t st) {
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.gmax, 0, 4, st));
-  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
+  if (e.frozen_max >= 0.f)
+    CUDA_OR_FAIL(cudaMemcpyAsync(R.scr + R.L.ml_running, &e.frozen_max, 4, cudaMemcpyHostToDevice, st));
+  else
+    CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.status, 0, 4, st));
   CUDA_OR_FAIL(record(e.ev_start, st));
   launch_prep(R.pa, st);
@@ -569,10 +574,11 @@ static int event_end(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
   return DOTPE_OK;
 }
 
+// The scratch goes back at once; the inputs stay with the event until it is
+// released (dotpe_lnl_blocks recomputes blocks from them).
 static int event_free(Event &e, EventRun &R, cudaStream_t st) {
+  (void)e;
   CUDA_OR_FAIL(cudaFreeAsync(R.scr, st));
-  CUDA_OR_FAIL(cudaFreeAsync(e.in_block, st));
-  e.in_block = nullptr;
   R.scr = nullptr;
   return DOTPE_OK;
 }
@@ -908,9 +914,8 @@ static void progress(dotpe_ctx *ctx) {
           e.xent->refs--;
           e.xent = nullptr;
         }
-        ctx->used -= e.scratch_bytes + e.in_bytes;
+        ctx->used -= e.scratch_bytes;
         e.scratch_bytes = 0;
-        e.in_bytes = 0;
         if (e.in_stage) {
           cudaFreeHost(e.in_stage);
           e.in_stage = nullptr;
@@ -987,7 +992,7 @@ static void free_event(dotpe_ctx *ctx, Event *e) {
   if (e->state == DOTPE_STATE_RUNNING) cudaEventSynchronize(e->ev_end);
   if (e->xent) e->xent->refs--;
   if (e->keep_block) cudaFree(e->keep_block);
-  if (e->in_block) cudaFree(e->in_block);
+  if (e->in_block && e->owns_inputs) cudaFree(e->in_block);
   if (e->in_stage) cudaFreeHost(e->in_stage);
   if (e->h_out) cudaFreeHost(e->h_out);
   if (e->ev_inputs) cudaEventDestroy(e->ev_inputs);
@@ -1572,6 +1577,86 @@ int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out) {
   return DOTPE_OK;
 }
 
+}  // extern "C"
+
+// Recomputes ln Lbar_ie or max_o ln L^ML_ie of rows [a, b) x samples [e0, e1)
+// of a finished event that did not store them: a sub-event over that block with
+// the event's inputs, in the event's arithmetic (split fp16 for the mixed
+// path), with the ML cut fixed at the event's final threshold, run to
+// completion on the context's main stream (caller holds ctx->mu).
+static int recompute_block(dotpe_ctx *ctx, Event &e, int64_t a, int64_t b, int64_t e0, int64_t e1, int what,
+                           float *out, int64_t ld) {
+  Event sub;
+  sub.id = 0;
+  sub.bank = e.bank;
+  sub.i0 = e.i0 + a;
+  sub.NI = b - a;
+  sub.NE = e1 - e0;
+  sub.D = e.D;
+  sub.nphi = e.nphi;
+  sub.prec = (e.prec == DOTPE_PREC_MIXED) ? DOTPE_PREC_FP16X3 : e.prec;
+  sub.flags = DOTPE_FLAG_STORE_LNL;
+  sub.u_min = e.u_min;
+  sub.cut = e.cut;
+  sub.has_lwe = e.has_lwe;
+  sub.psd = e.psd;
+  sub.data = e.data;
+  sub.t = e.t + e0 * e.D;
+  sub.R = e.R + e0 * e.D * e.bank->M;
+  sub.lwe = e.lwe + e0;
+  sub.in_block = e.in_block;
+  sub.owns_inputs = false;
+  sub.psd_key = e.psd_key;
+  if (e.cut > 0) sub.frozen_max = (float)(e.h_out->threshold + e.cut);
+  sub.slot = 0;
+  CUDA_OR_FAIL(cudaEventCreateWithFlags(&sub.ev_inputs, cudaEventDisableTiming));
+  CUDA_OR_FAIL(cudaEventCreate(&sub.ev_start));
+  CUDA_OR_FAIL(cudaEventCreate(&sub.ev_end));
+  CUDA_OR_FAIL(cudaEventCreate(&sub.ev_k0));
+  CUDA_OR_FAIL(cudaEventCreate(&sub.ev_k1));
+  CUDA_OR_FAIL(cudaEventCreate(&sub.ev_ks));
+  CUDA_OR_FAIL(cudaHostAlloc((void **)&sub.h_out, sizeof(ReduceOut), cudaHostAllocDefault));
+  cudaStream_t st = ctx->main_stream;
+  CUDA_OR_FAIL(cudaEventRecord(sub.ev_inputs, st));
+  int rc = DOTPE_OK;
+  {
+    EventRun R;
+    rc = event_alloc(ctx, sub, st, R);
+    if (rc == DOTPE_OK) {
+      // cross terms of these rows: the cached entry of the bank for this PSD if there is one
+      for (XEntry *c : sub.bank->xcache)
+        if (c->key == sub.psd_key && c->D == sub.D) {
+          CUDA_OR_FAIL(cudaStreamWaitEvent(st, c->ready, 0));
+          sub.xent = c;
+        }
+      if ((rc = event_begin(sub, R, st)) == DOTPE_OK) {
+        event_block(ctx, sub, R, 0, sub.NI, st);
+        rc = event_fused(ctx, sub, R, true, st);
+      }
+      cudaFreeAsync(R.scr, st);
+    }
+  }
+  if (rc == DOTPE_OK) {
+    CUDA_OR_FAIL(cudaStreamSynchronize(st));
+    const float *src = (what == DOTPE_LNL_MARG) ? sub.lnl_tile : sub.ml_tile;
+    cudaError_t ce = cudaMemcpy2D(out, ld * 4, src, sub.NE * 4, sub.NE * 4, sub.NI, cudaMemcpyDefault);
+    if (ce != cudaSuccess) rc = fail(DOTPE_E_DEVICE, "copying the recomputed block: %s", cudaGetErrorString(ce));
+  } else {
+    cudaStreamSynchronize(st);
+  }
+  if (sub.keep_block) cudaFree(sub.keep_block);
+  cudaFreeHost(sub.h_out);
+  cudaEventDestroy(sub.ev_inputs);
+  cudaEventDestroy(sub.ev_start);
+  cudaEventDestroy(sub.ev_end);
+  cudaEventDestroy(sub.ev_k0);
+  cudaEventDestroy(sub.ev_k1);
+  cudaEventDestroy(sub.ev_ks);
+  return rc;
+}
+
+extern "C" {
+
 int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, int64_t e0, int64_t e1, int what,
                      float *out, int64_t ld) {
   if (!ctx || !out) return fail(DOTPE_E_INVALID, "null argument");
@@ -1583,9 +1668,9 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
   Event &e = *it->second;
   if (e.state != DOTPE_STATE_DONE) return fail(DOTPE_E_NOT_READY, "event not done");
   if (what == DOTPE_LNL_MARG || what == DOTPE_LNL_ML_MAX) {
-    if (!(e.flags & DOTPE_FLAG_STORE_LNL)) return fail(DOTPE_E_UNSUPPORTED, "event ran without DOTPE_FLAG_STORE_LNL");
     if (i0 < 0 || i1 > e.NI || i1 <= i0 || e0 < 0 || e1 > e.NE || e1 <= e0 || ld < e1 - e0)
       return fail(DOTPE_E_INVALID, "block range");
+    if (!(e.flags & DOTPE_FLAG_STORE_LNL)) return recompute_block(ctx, e, i0, i1, e0, e1, what, out, ld);
     const float *src = (what == DOTPE_LNL_MARG ? e.lnl_tile : e.ml_tile) + i0 * e.NE + e0;
     CUDA_OR_FAIL(cudaMemcpy2D(out, ld * 4, src, e.NE * 4, (e1 - e0) * 4, i1 - i0, cudaMemcpyDefault));
     return DOTPE_OK;

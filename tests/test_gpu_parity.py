@@ -453,6 +453,53 @@ def test_device_resident_inputs_on_caller_stream(dpx):
     dp.dotpe_bank_release(ctx, bid)
 
 
+def test_lnl_blocks_recomputed_without_stored_tiles(dpx):
+    """An event run without DOTPE_FLAG_STORE_LNL: dotpe_lnl_blocks recomputes the
+    asked block from the kept inputs.  Without the cut it equals the stored values
+    of the same event run with the flag (the same per-pair arithmetic); with the
+    cut it applies the event's final threshold; in mixed precision the block is
+    computed in split fp16 and meets the split tolerance against the oracle."""
+    import oracle
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=900, n_ext=200, n_det=3, n_modes=4, n_bins=128, snr=14.0, seed=12,
+                             ln_w="random")
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    a, b, e0, e1 = 130, 517, 33, 170  # a ragged block, not aligned to tiles
+    try:
+        def sub(precision, flags, cut):
+            eid = dp.dotpe_event_submit(ctx, bid, 50, 900, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                        wl.ext.ln_w, n_phi=32, u_min=wl.event.u_min, cut_delta=cut,
+                                        precision=precision, flags=flags)
+            dp.dotpe_event_wait(ctx, eid, 60)
+            return eid
+        for precision in ("fp32", "bf16x3"):
+            full = sub(precision, dp.DOTPE_FLAG_STORE_LNL, 0.0)
+            bare = sub(precision, 0, 0.0)
+            for what in (dp.DOTPE_LNL_MARG, dp.DOTPE_LNL_ML_MAX):
+                x = dp.dotpe_lnl_blocks(ctx, full, a, b, e0, e1, what=what)
+                y = dp.dotpe_lnl_blocks(ctx, bare, a, b, e0, e1, what=what)
+                assert np.array_equal(x, y), (precision, what)
+            dp.dotpe_event_release(ctx, full)
+            dp.dotpe_event_release(ctx, bare)
+        # with the cut: the final threshold, fixed
+        eid = sub("bf16x3", 0, 20.0)
+        ev = dp.dotpe_evidence(ctx, eid)
+        lnl = dp.dotpe_lnl_blocks(ctx, eid, a, b, e0, e1)
+        ml = dp.dotpe_lnl_blocks(ctx, eid, a, b, e0, e1, what=dp.DOTPE_LNL_ML_MAX)
+        assert np.all(np.isneginf(lnl) <= (ml < ev["lnl_ml_threshold"] + 1e-3))
+        dp.dotpe_event_release(ctx, eid)
+        # mixed: split fp16 against the oracle on the block
+        eid = sub("mixed", 0, 0.0)
+        lnl = dp.dotpe_lnl_blocks(ctx, eid, a, b, e0, e1).astype(np.float64)
+        dp.dotpe_event_release(ctx, eid)
+        P = oracle.OracleProblem(wl.bank, wl.ext, wl.event, i_slice=slice(50 + a, 50 + b))
+        ii, ee = np.meshgrid(np.arange(b - a), np.arange(e0, e1), indexing="ij")
+        ref = P.eval_pairs(ii.ravel(), ee.ravel())
+        assert np.max(np.abs(lnl.ravel() - ref["lnl_marg"])) <= 1e-3
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+
+
 def test_gemm_only_diagnostic_runs(dpx):
     dp, ctx = dpx
     wl = synth.make_workload(n_int=1024, n_ext=256, n_det=3, n_modes=4, n_bins=256, seed=2)
