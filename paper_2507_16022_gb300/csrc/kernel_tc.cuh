@@ -414,8 +414,29 @@ __global__ void __launch_bounds__(NT, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&T.tempty[b]);
-#pragma unroll 1
-        for (int j = 0; j < EHALF; ++j) xb[j] = -INFINITY;
+        // tile outputs of a screen: empty marginal partials and the tile's best ln L^ML
+        warp_argmax(best, barg);
+        if (lane == 0) {
+          T.wml[ew] = best;
+          T.warg[ew] = barg;
+        }
+        if (half == 0 && vi) P.row_part[(int64_t)et * P.n_int + i] = make_float2(-INFINITY, 0.f);
+        if (etid < TE && e0 + etid < P.n_ext) P.col_part[(int64_t)it * P.n_ext + e0 + etid] = make_float2(-INFINITY, 0.f);
+        named_bar_sync(1, EPT);
+        if (etid == 0) {
+          float bv = -1.f;
+          long long bi = 0x7fffffffffffffffLL;
+          for (int q = 0; q < NEPI; ++q)
+            if (T.wml[q] > bv || (T.wml[q] == bv && T.warg[q] < bi)) { bv = T.wml[q]; bi = T.warg[q]; }
+          P.tile_part[t] = make_float4(-INFINITY, 0.f, -INFINITY, 0.f);
+          P.tile_ml[t] = bv;
+          P.tile_arg[t] = bi;
+          P.tile_npass[t] = 0;
+          if (bv > 0.f && P.track_max) atomic_max_nonneg(P.ml_running, bv);
+        }
+        // the next tile's barrier (after its column records) orders these reads
+        // of T.wml before any thread writes it again
+        continue;
       } else {
 #pragma unroll 1
       for (int j = 0; j < EHALF; ++j) {

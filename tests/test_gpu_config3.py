@@ -9,8 +9,9 @@ path on the same GPU:
     largest (TC_ACC: the tensor cores' accumulation floor, below);
   * the served mixed path meets |d ln Z| <= 1e-2 against FP32, and its peak
     the same bound against the oracle;
-  * streaming in blocks reproduces the one-pass result (FP64 rounding of the
-    combination for FP32; the per-block far window of mixed precision);
+  * streaming in blocks reproduces the one-pass result (ln Z to FP64 rounding
+    for FP32, the marginals to the FP32 exponentials of their partials; the
+    per-block far window of mixed precision);
   * single-pass fp16 is reported against its own bound.
 """
 import math
@@ -94,11 +95,12 @@ def test_config3_block_streaming_matches_one_pass(big):
     for precision in ("fp32", "mixed"):
         a = evidence(dp, ctx, bid, wl, precision, cut=0.0, block_rows=BLOCK)
         b = evidence(dp, ctx, bid, wl, precision, cut=0.0, block_rows=0)
-        # fp32: same tiles, FP64 combination in another order; mixed: the far
-        # window is placed per block, so a few tiles more than 30 below the
+        # fp32: same tiles, FP64 sums in another order (the line marginals weigh
+        # their FP32 partials with FP32 exponentials, ~1e-7 relative); mixed: the
+        # far window is placed per block, so a few tiles more than 30 below the
         # maximum may be refined in one run and not in the other
-        tol = 1e-9 if precision == "fp32" else 1e-6
-        assert a["ln_z"] == pytest.approx(b["ln_z"], abs=tol), precision
+        tol = 1e-6
+        assert a["ln_z"] == pytest.approx(b["ln_z"], abs=1e-9 if precision == "fp32" else tol), precision
         for k in ("n_eff", "n_eff_int", "n_eff_ext"):
             assert a[k] == pytest.approx(b[k], rel=tol), (precision, k)
         assert (a["arg_i"], a["arg_e"], a["arg_o"]) == (b["arg_i"], b["arg_e"], b["arg_o"])
