@@ -551,26 +551,36 @@ __global__ void __launch_bounds__(NT, 1)
         if (qq == 0 && etv && e0 + cc < P.n_ext)
           P.col_part[(int64_t)it * P.n_ext + e0 + cc] = make_float2(a.m, a.s);
       }
-      if (etid == 0 && etv) {
+      if (etid < 32 && etv) {
+        // tile totals: lanes 0..NEPI-1 of the first epilogue warp hold the warps' values
         Lse a, bb;
         a.init();
         bb.init();
         float bv = -1.f;
         long long bi = 0x7fffffffffffffffLL;
         int n = 0;
-        for (int w = 0; w < NEPI; ++w) {
-          a.merge(T.wm1[w], T.ws1[w]);
-          bb.merge(T.wm2[w], T.ws2[w]);
-          n += T.wnp[w];
-          if (T.wml[w] > bv || (T.wml[w] == bv && T.warg[w] < bi)) { bv = T.wml[w]; bi = T.warg[w]; }
+        if (etid < NEPI) {
+          a.merge(T.wm1[etid], T.ws1[etid]);
+          bb.merge(T.wm2[etid], T.ws2[etid]);
+          n = T.wnp[etid];
+          bv = T.wml[etid];
+          bi = T.warg[etid];
         }
-        P.tile_part[t] = make_float4(a.m, a.s, bb.m, bb.s);
-        P.tile_ml[t] = bv;
-        P.tile_arg[t] = bi;
-        P.tile_npass[t] = n;
-        if (bv > 0.f && P.track_max) atomic_max_nonneg(P.ml_running, bv);
+        warp_merge_lse(a);
+        warp_merge_lse(bb);
+        warp_argmax(bv, bi);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if (etid == 0) {
+          P.tile_part[t] = make_float4(a.m, a.s, bb.m, bb.s);
+          P.tile_ml[t] = bv;
+          P.tile_arg[t] = bi;
+          P.tile_npass[t] = n;
+          if (bv > 0.f && P.track_max) atomic_max_nonneg(P.ml_running, bv);
+        }
       }
-      named_bar_sync(1, EPT);
+      // no trailing barrier: the next tile's barrier (after its column records)
+      // orders these reads of the per-warp values before they are written again
     }
   }
   tc_fence_before();
