@@ -6,26 +6,6 @@ namespace dotpe {
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t inner, uint64_t rows,
-                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows) {
-  if (!g_encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return -1;
-    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
-  cuuint64_t dims[2] = {inner, rows};
-  cuuint64_t strides[1] = {row_bytes};
-  cuuint32_t box[2] = {box_inner, box_rows};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = g_encode(map, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : -2;
-}
-
 // 3-D view of a row-major [rows][n_kb * 64] matrix: dims {64, rows, n_kb}, box
 // {64, box_rows, box_kb} -> shared memory [box_kb][box_rows][64], 128-byte swizzle.
 int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,

@@ -180,8 +180,6 @@ void launch_reduce_final(const ReduceArgs &a, cudaStream_t st);
 size_t reduce_scratch_bytes();
 
 // Tensor-map encoding through the driver entry point.
-int encode_tmap_2d(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t inner, uint64_t rows,
-                   uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows);
 int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,
                         uint64_t row_bytes, uint32_t box_rows, uint32_t box_kb);
 int tc_kblocks_per_stage();
