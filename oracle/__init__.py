@@ -69,9 +69,11 @@ def lib():
             L.or_lnl_ml.restype = ctypes.c_double
             L.or_lnl_ml.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_default_threads.restype = ctypes.c_int
+            L.or_quad_ml.restype = ctypes.c_double
+            L.or_quad_ml.argtypes = [ctypes.c_double] * 5
             for name in ("or_data_weights", "or_direct_phases", "or_mode_components",
                          "or_rotate_phases", "or_eval_pairs", "or_eval_grid",
-                         "or_direct_grid_ml", "or_evidence"):
+                         "or_direct_grid_ml", "or_evidence", "or_presel_grid", "or_presel"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
         return _lib
@@ -192,6 +194,71 @@ class OracleProblem:
                     n_eff_ext=ev.n_eff_ext, max_lnl_ml=ev.max_lnl_ml,
                     arg=(ev.arg_i, ev.arg_e, ev.arg_o), n_marginalised=ev.n_marginalised,
                     ln_p_int=lpi, ln_p_ext=lpe)
+
+
+class PreselStruct(ctypes.Structure):
+    _fields_ = [("n_int", ctypes.c_int), ("n_det", ctypes.c_int), ("n_modes", ctypes.c_int),
+                ("n_bins", ctypes.c_int), ("n_t", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("mode_m", ctypes.POINTER(ctypes.c_int)),
+                ("f", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
+                ("psd", ctypes.POINTER(ctypes.c_double)), ("data", ctypes.POINTER(ctypes.c_double)),
+                ("h", ctypes.POINTER(ctypes.c_double)), ("pol", ctypes.POINTER(ctypes.c_double)),
+                ("t_grid", ctypes.POINTER(ctypes.c_double))]
+
+
+class PreselProblem:
+    """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of one event
+    over bank rows: h [I, M, B], pol [I, M, 2] (K_{imp}, p = +, x), t_grid [D, n_t]."""
+
+    def __init__(self, f, w, mode_m, h, pol, psd, data, t_grid, n_phi=32):
+        self.mode_m = np.ascontiguousarray(mode_m, dtype=np.int32)
+        self.f = np.ascontiguousarray(f, dtype=np.float64)
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+        self.h = _c128(h)
+        self.pol = _c128(pol)
+        self.psd = np.ascontiguousarray(psd, dtype=np.float64)
+        self.data = _c128(data)
+        self.t_grid = np.ascontiguousarray(t_grid, dtype=np.float64)
+        I, M, B = self.h.shape
+        D, NT = self.t_grid.shape
+        assert self.pol.shape == (I, M, 2) and self.psd.shape == (D, B) and self.data.shape == (D, B)
+        self.shape = (I, D, M, B, NT)
+        self.n_phi = int(n_phi)
+        self.s = PreselStruct(I, D, M, B, NT, self.n_phi,
+                              self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                              _dp(self.f), _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),
+                              _dp(self.h.view(np.float64)), _dp(self.pol.view(np.float64)),
+                              _dp(self.t_grid))
+
+    def grid(self, i, k):
+        """ln L^ML_{i k o t} [n_phi, n_t] (Eq. single_det_ML)."""
+        NT = self.shape[4]
+        out = np.zeros((self.n_phi, NT))
+        if lib().or_presel_grid(ctypes.byref(self.s), ctypes.c_int64(i), int(k), _dp(out)):
+            raise MemoryError("or_presel_grid")
+        return out
+
+    def run(self, delta=20.0, n_threads=0):
+        """Every row: ml [I, D], arg_ot [I, D, 2], lnl_inco [I], keep [I], threshold, arg_i."""
+        I, D = self.shape[:2]
+        ml = np.zeros((I, D))
+        arg = np.zeros((I, D, 2), dtype=np.int32)
+        inco = np.zeros(I)
+        keep = np.zeros(I, dtype=np.uint8)
+        thr = ctypes.c_double(0.0)
+        ai = ctypes.c_int64(0)
+        if lib().or_presel(ctypes.byref(self.s), ctypes.c_double(delta), int(n_threads), _dp(ml),
+                           arg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(inco),
+                           keep.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(thr),
+                           ctypes.byref(ai)):
+            raise MemoryError("or_presel")
+        return dict(ml=ml, arg_ot=arg, lnl_inco=inco, keep=keep.astype(bool), threshold=thr.value,
+                    arg_i=int(ai.value))
+
+
+def quad_ml(dh_p, dh_x, a, b, c):
+    """Eqs. x_ML, single_det_ML for one (i, k, o, t)."""
+    return lib().or_quad_ml(float(dh_p), float(dh_x), float(a), float(b), float(c))
 
 
 def dist_marg(dh, hh, u_min):

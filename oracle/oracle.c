@@ -571,3 +571,198 @@ int or_evidence(const or_problem *p, const or_pair_out *g, or_evidence_out *ev,
   free(lp); free(lp2); free(row); free(col); free(row2); free(col2);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Incoherent single-detector pre-selection (Sec. IV.D, App. B)             */
+/* ------------------------------------------------------------------------ */
+/* Eqs. x_ML, single_det_ML: x^ML = hh^+ dh, ln L^ML = dh^T hh^+ dh / 2. */
+double or_quad_ml(double dp, double dx, double a, double b, double c) {
+  if (!(a > 0.0) && !(c > 0.0)) return 0.0; /* no template power: nothing to fit */
+  double det = a * c - b * b;
+  if (det > OR_PRESEL_RANK_TOL * a * c) return 0.5 * (c * dp * dp - 2.0 * b * dp * dx + a * dx * dx) / det;
+  /* rank one: hh = lambda v v^T with lambda = a + c, hh^+ = hh / lambda^2 */
+  double s = a + c;
+  return 0.5 * (a * dp * dp + 2.0 * b * dp * dx + c * dx * dx) / (s * s);
+}
+
+/* W_{t b} = c_{k b} T_{t k b} = 4 w_b d_k^*(f_b) / S_k(f_b) e^{-2 pi i f_b t_{k t}} of one
+ * detector: [n_t][B] (Eq. dh_itop without the waveform). */
+static cplx *presel_weights(const or_presel_problem *p, int k) {
+  const int B = p->n_bins, NT = p->n_t;
+  const int64_t kb = (int64_t)k * B;
+  cplx *W = malloc(sizeof(cplx) * (size_t)NT * B);
+  if (!W) return NULL;
+  for (int t = 0; t < NT; ++t) {
+    double tt = p->t_grid[(int64_t)k * NT + t];
+    for (int b = 0; b < B; ++b) {
+      double om = 4.0 * p->w[b] / p->psd[kb + b];
+      W[(int64_t)t * B + b] = om * conj(ld_c(p->data, kb + b)) * cexp(-I * TWO_PI * p->f[b] * tt);
+    }
+  }
+  return W;
+}
+
+static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, int k, double *ml_out) {
+  const int M = p->n_modes, B = p->n_bins, NT = p->n_t, NP = p->n_phi;
+  const int64_t kb = (int64_t)k * B;
+  cplx *hp = malloc(sizeof(cplx) * (size_t)2 * M * B); /* h_{i m p}(f_b): [p][m][b] */
+  cplx *z = malloc(sizeof(cplx) * (size_t)2 * M);      /* [p][m]: sum_b W_{t b} h_{i m p}(f_b) */
+  cplx *ov = malloc(sizeof(cplx) * (size_t)3 * M * M); /* [pp'][m][m']: sum_b omega h_{m p} h^*_{m' p'} */
+  double *hh = malloc(sizeof(double) * (size_t)3 * NP); /* (++, +x, xx) per o */
+  if (!hp || !z || !ov || !hh) {
+    free(hp); free(z); free(ov); free(hh);
+    return -1;
+  }
+  for (int q = 0; q < 2; ++q)
+    for (int m = 0; m < M; ++m) {
+      cplx K = ld_c(p->pol, (i * M + m) * 2 + q);
+      for (int b = 0; b < B; ++b) hp[((int64_t)q * M + m) * B + b] = K * ld_c(p->h, (i * M + m) * B + b);
+    }
+  /* <h|h>_{i k o p p'}: frequency sums per mode pair, then the phase factors */
+  const int pq[3][2] = {{0, 0}, {0, 1}, {1, 1}};
+  for (int r = 0; r < 3; ++r)
+    for (int m = 0; m < M; ++m)
+      for (int mp = 0; mp < M; ++mp) {
+        cplx s = 0.0;
+        for (int b = 0; b < B; ++b) {
+          double om = 4.0 * p->w[b] / p->psd[kb + b];
+          s += om * hp[((int64_t)pq[r][0] * M + m) * B + b] * conj(hp[((int64_t)pq[r][1] * M + mp) * B + b]);
+        }
+        ov[(r * M + m) * M + mp] = s;
+      }
+  for (int o = 0; o < NP; ++o)
+    for (int r = 0; r < 3; ++r) {
+      cplx acc = 0.0;
+      for (int m = 0; m < M; ++m)
+        for (int mp = 0; mp < M; ++mp)
+          acc += ov[(r * M + m) * M + mp] * grid_phase(p->mode_m[m] - p->mode_m[mp], o, NP);
+      hh[3 * o + r] = creal(acc);
+    }
+  /* <d|h>_{i k o t p} (Eq. dh_itop) and ln L^ML (Eq. single_det_ML) */
+  for (int t = 0; t < NT; ++t) {
+    for (int q = 0; q < 2; ++q)
+      for (int m = 0; m < M; ++m) {
+        cplx acc = 0.0;
+        for (int b = 0; b < B; ++b) acc += W[(int64_t)t * B + b] * hp[((int64_t)q * M + m) * B + b];
+        z[q * M + m] = acc;
+      }
+    for (int o = 0; o < NP; ++o) {
+      double dh[2];
+      for (int q = 0; q < 2; ++q) {
+        cplx s = 0.0;
+        for (int m = 0; m < M; ++m) s += z[q * M + m] * grid_phase(p->mode_m[m], o, NP);
+        dh[q] = creal(s);
+      }
+      ml_out[(int64_t)o * NT + t] = or_quad_ml(dh[0], dh[1], hh[3 * o], hh[3 * o + 1], hh[3 * o + 2]);
+    }
+  }
+  free(hp); free(z); free(ov); free(hh);
+  return 0;
+}
+
+int or_presel_grid(const or_presel_problem *p, int64_t i, int k, double *ml_out) {
+  cplx *W = presel_weights(p, k);
+  if (!W) return -1;
+  int rc = presel_grid_w(p, W, i, k, ml_out);
+  free(W);
+  return rc;
+}
+
+typedef struct {
+  const or_presel_problem *p;
+  int64_t r0, r1;
+  double *ml_ik;
+  int32_t *arg_ot;
+  double *inco;
+  cplx **W; /* per detector */
+  int err;
+} ps_job;
+
+static void *ps_run(void *arg) {
+  ps_job *j = (ps_job *)arg;
+  const or_presel_problem *p = j->p;
+  const int D = p->n_det, NT = p->n_t, NP = p->n_phi;
+  double *g = malloc(sizeof(double) * (size_t)NP * NT);
+  if (!g) {
+    j->err = -1;
+    return NULL;
+  }
+  for (int64_t i = j->r0; i < j->r1; ++i) {
+    double sum = 0.0;
+    for (int k = 0; k < D; ++k) {
+      if (presel_grid_w(p, j->W[k], i, k, g)) {
+        j->err = -1;
+        free(g);
+        return NULL;
+      }
+      double best = -INFINITY;
+      int bo = 0, bt = 0;
+      for (int t = 0; t < NT; ++t) /* lowest t, then lowest o, on ties */
+        for (int o = 0; o < NP; ++o)
+          if (g[(int64_t)o * NT + t] > best) {
+            best = g[(int64_t)o * NT + t];
+            bo = o;
+            bt = t;
+          }
+      if (j->ml_ik) j->ml_ik[i * D + k] = best;
+      if (j->arg_ot) {
+        j->arg_ot[(i * D + k) * 2] = bo;
+        j->arg_ot[(i * D + k) * 2 + 1] = bt;
+      }
+      sum += best;
+    }
+    j->inco[i] = sum;
+  }
+  free(g);
+  return NULL;
+}
+
+int or_presel(const or_presel_problem *p, double delta, int n_threads, double *ml_ik, int32_t *arg_ot,
+              double *lnl_inco, uint8_t *keep, double *thr_out, int64_t *arg_out) {
+  const int64_t n = p->n_int;
+  if (!lnl_inco) return -1;
+  if (n_threads <= 0) n_threads = or_default_threads();
+  if (n_threads > 256) n_threads = 256;
+  if ((int64_t)n_threads > n) n_threads = n > 0 ? (int)n : 1;
+  cplx *W[64];
+  if (p->n_det < 1 || p->n_det > 64) return -1;
+  for (int k = 0; k < p->n_det; ++k) W[k] = presel_weights(p, k);
+  for (int k = 0; k < p->n_det; ++k)
+    if (!W[k]) {
+      for (int q = 0; q < p->n_det; ++q) free(W[q]);
+      return -1;
+    }
+  ps_job jobs[256];
+  pthread_t th[256];
+  for (int t = 0; t < n_threads; ++t) {
+    ps_job *j = &jobs[t];
+    memset(j, 0, sizeof(*j));
+    j->p = p;
+    j->W = W;
+    j->ml_ik = ml_ik;
+    j->arg_ot = arg_ot;
+    j->inco = lnl_inco;
+    j->r0 = n * t / n_threads;
+    j->r1 = n * (t + 1) / n_threads;
+  }
+  for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, ps_run, &jobs[t]);
+  ps_run(&jobs[0]);
+  for (int t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+  for (int k = 0; k < p->n_det; ++k) free(W[k]);
+  for (int t = 0; t < n_threads; ++t)
+    if (jobs[t].err) return -1;
+  /* Sec. IV.D selection: keep ln L^inco.ML_i >= max_j ln L^inco.ML_j - delta */
+  double best = -INFINITY;
+  int64_t bi = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (lnl_inco[i] > best) {
+      best = lnl_inco[i];
+      bi = i;
+    }
+  double thr = best - delta;
+  if (keep)
+    for (int64_t i = 0; i < n; ++i) keep[i] = lnl_inco[i] >= thr;
+  if (thr_out) *thr_out = thr;
+  if (arg_out) *arg_out = bi;
+  return 0;
+}

@@ -104,6 +104,47 @@ int or_direct_grid_ml(const or_problem *p, int n_threads, double *lnl_ml_max_out
 int or_evidence(const or_problem *p, const or_pair_out *grid, or_evidence_out *ev,
                 double *ln_p_int, double *ln_p_ext);
 
+/* ---- Incoherent single-detector pre-selection (Sec. IV.D, App. B) ----------
+ * Each detector k alone: the polarisation amplitudes x_{k+}, x_{kx} are free
+ * (App. B: sky position, distance and polarisation angle are degenerate for
+ * one detector), time and orbital phase run over regular grids.
+ *   h_{i m p}(f_b) = K_{i m p} h_{i m}(f_b)        polarisation p = (+, x)
+ *   <d|h>_{i k o t p}  = Re sum_{m,b} c_{k b} e^{-2 pi i f_b t_{k t}} h_{i m p}(f_b) e^{i m phi_o}
+ *   <h|h>_{i k o p p'} = Re sum_{m,m',b} omega_{k b} h_{i m p} h^*_{i m' p'} e^{i (m - m') phi_o}
+ *   ln L^ML_{i k o t}  = 1/2 dh^T [hh]^+ dh          (Eqs. dh_itop, x_ML, single_det_ML)
+ *   ln L^inco.ML_i     = sum_k max_{o,t} ln L^ML_{i k o t}
+ * and a row is kept when ln L^inco.ML_i >= max_j ln L^inco.ML_j - delta.
+ * The sign of the phase factor differs from App. B's e^{-i m phi}: the grid
+ * phi_o = 2 pi o / n_phi is closed under phi -> -phi, so the maximum over o is
+ * the same.  [hh]^+ is the inverse when det > PRESEL_RANK_TOL hh_{++} hh_{xx},
+ * else the pseudo-inverse of the rank-one limit, hh / (hh_{++} + hh_{xx})^2. */
+#define OR_PRESEL_RANK_TOL 1e-3
+
+typedef struct or_presel {
+  int n_int, n_det, n_modes, n_bins, n_t, n_phi;
+  const int *mode_m;
+  const double *f, *w, *psd, *data;  /* data: complex [D][B] */
+  const double *h;                   /* complex [I][M][B] */
+  const double *pol;                 /* complex [I][M][2]: K_{i m +}, K_{i m x} */
+  const double *t_grid;              /* [D][n_t] arrival times at detector k (s) */
+} or_presel_problem;
+
+/* Eqs. x_ML, single_det_ML: max over real (x_+, x_x) of
+ * dh_+ x_+ + dh_x x_x - (a x_+^2 + 2 b x_+ x_x + c x_x^2)/2, with
+ * hh = [[a, b], [b, c]] positive semi-definite (pseudo-inverse reading above). */
+double or_quad_ml(double dh_p, double dh_x, double a, double b, double c);
+
+/* ln L^ML_{i k o t} of one row i and detector k over the whole grid:
+ * ml_out [n_phi][n_t]. */
+int or_presel_grid(const or_presel_problem *p, int64_t i, int k, double *ml_out);
+
+/* Every row: ml_ik [I][D] = max_{o,t} ln L^ML_{i k o t}, arg_ot [I][D][2] its
+ * (o, t) (lowest t, then lowest o, on ties), lnl_inco [I], keep [I] (0/1) for
+ * the window delta; *thr_out = max - delta, *arg_out = the row of the maximum
+ * (lowest on ties).  Any output pointer may be NULL except lnl_inco. */
+int or_presel(const or_presel_problem *p, double delta, int n_threads, double *ml_ik, int32_t *arg_ot,
+              double *lnl_inco, uint8_t *keep, double *thr_out, int64_t *arg_out);
+
 /* Number of hardware threads the oracle will use by default. */
 int or_default_threads(void);
 

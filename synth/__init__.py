@@ -294,9 +294,9 @@ def make_event(rng, bank: Bank, ext: Extrinsic, n_det, snr=15.0, n_phi=32,
         inj_i = int(rng.integers(0, I))
     if inj_e is None:
         e1 = make_extrinsic(rng, 1, D, bank)
-        R_dm, t_d = e1.R[0], e1.t[0]
+        R_dm, t_d, cos_iota = e1.R[0], e1.t[0], float(e1.cos_iota[0])
     else:
-        R_dm, t_d = ext.R[inj_e], ext.t[inj_e]
+        R_dm, t_d, cos_iota = ext.R[inj_e], ext.t[inj_e], float(ext.cos_iota[inj_e])
     if phi_inj is None:
         phi_inj = float(rng.uniform(0.0, 2.0 * np.pi))
     h_modes = np.asarray(bank.h[inj_i], dtype=np.complex128)
@@ -310,7 +310,8 @@ def make_event(rng, bank: Bank, ext: Extrinsic, n_det, snr=15.0, n_phi=32,
     if u_min is None:
         u_min = default_u_min(bank, D)
     return Event(psd=psd, data=data, u_min=float(u_min), n_phi=int(n_phi),
-                 injection=dict(i=inj_i, e=inj_e, phi=phi_inj, u=u_inj, snr=snr))
+                 injection=dict(i=inj_i, e=inj_e, phi=phi_inj, u=u_inj, snr=snr,
+                                cos_iota=cos_iota, t_det=np.array(t_d, dtype=np.float64)))
 
 
 def default_u_min(bank: Bank, n_det: int, snr_at_dmax: float = 4.0):
@@ -424,6 +425,44 @@ def make_serving_stream(n_events=2000, rate=20.0, seed=5, n_int=524288, n_modes=
                         inj_i=int(rng.integers(i0, i0 + L)))
         stream.append(Arrival(t=t, n_bins=B, i0=i0, i1=i0 + L, ext=ext, event=ev))
     return banks, stream
+
+
+@dataclasses.dataclass
+class PreselInputs:
+    """Inputs of the incoherent single-detector pre-selection (Sec. IV.D, App. B)."""
+    pol: np.ndarray        # [I, M, 2] complex128: K_{i m +}, K_{i m x}
+    cos_iota: np.ndarray   # [I] inclination of each bank row (an intrinsic parameter there)
+    t_grid: np.ndarray     # [D, n_t] arrival-time grid at each detector (s)
+
+
+def row_polarisation_factors(bank: Bank, cos_iota):
+    """K_{i m p} of every row: h_{i m p} = K_{i m p} h_{i m} (App. B's h_impb)."""
+    iota = np.arccos(np.asarray(cos_iota, dtype=np.float64))
+    M = bank.mode_m.shape[0]
+    pol = np.empty((iota.shape[0], M, 2), dtype=np.complex128)
+    for k in range(M):
+        a, b = polarisation_factors(int(bank.mode_l[k]), int(bank.mode_m[k]), iota)
+        pol[:, k, 0] = a
+        pol[:, k, 1] = b
+    return pol
+
+
+def make_presel_inputs(wl: "Workload", n_t=128, dt=5.0e-4, seed=7):
+    """Rows draw cos(iota) ~ U[-1, 1] (the bank's inclination prior); the
+    injected row takes the injection's.  The time grid is shared by the
+    detectors: n_t points spaced dt, centred on the geocentric trigger time 0,
+    so it spans the prior's t_geo window plus the light travel time across
+    the Earth (n_t dt = 64 ms at the defaults)."""
+    rng = np.random.default_rng(seed)
+    I = wl.bank.h.shape[0]
+    cos_iota = rng.uniform(-1.0, 1.0, I)
+    inj = wl.event.injection
+    if inj.get("cos_iota") is not None and 0 <= inj["i"] < I:
+        cos_iota[inj["i"]] = inj["cos_iota"]
+    D = wl.event.psd.shape[0]
+    t = (np.arange(n_t) - n_t // 2) * dt
+    return PreselInputs(pol=row_polarisation_factors(wl.bank, cos_iota), cos_iota=cos_iota,
+                        t_grid=np.tile(t, (D, 1)))
 
 
 def named_workload(name: str, **overrides):
