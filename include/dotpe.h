@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define DOTPE_ABI_VERSION 1
+#define DOTPE_ABI_VERSION 2
 
 /* ---- status codes ------------------------------------------------------ */
 #define DOTPE_OK 0
@@ -112,7 +112,12 @@ typedef struct dotpe_config {
  * f, w_quad: [n_bins] host or device doubles: bin frequencies (Hz) and quadrature
  * weights such that <a|b> = sum_d sum_b 4 w_quad[b] a b^* / S_d(f_b) (Eq. inner_product).
  * mode_m: host int [n_modes], azimuthal numbers, each in 1..4, distinct.
- * ln_w_int: [n_int] host or device, ln(pi/pi') of each sample (Eq. int_weights); NULL = 0. */
+ * ln_w_int: [n_int] host or device, ln(pi/pi') of each sample (Eq. int_weights); NULL = 0.
+ * pol: [n_int][n_modes][2] complex, host or device, or NULL: the polarisation
+ *   factors K_{i m p} (p = +, x) of each row, h_{i m p} = K_{i m p} h_{i m}
+ *   (App. B's h_impb, with the inclination an intrinsic parameter as in
+ *   Sec. IV.A).  Only dotpe_preselect reads them; a bank without them cannot be
+ *   pre-selected.  Kept on the device as FP32. */
 typedef struct dotpe_bank_desc {
   int64_t n_int;
   int n_modes;
@@ -123,6 +128,7 @@ typedef struct dotpe_bank_desc {
   const void *h;
   int h_dtype;
   const double *ln_w_int;
+  const double *pol;
 } dotpe_bank_desc;
 
 /* One event: data, PSD, extrinsic samples (Sec. IV.B-E).
@@ -187,6 +193,53 @@ typedef struct dotpe_evidence_out {
   int32_t device_status;    /* 0, or a DOTPE_E_* raised inside a kernel */
   int32_t n_refined_tiles;  /* MIXED: tiles recomputed in split precision; else -1 */
 } dotpe_evidence_out;
+
+/* Incoherent single-detector pre-selection of bank rows (Sec. IV.D, App. B).
+ * Each detector k on its own, over a grid of arrival times t_{kt} and the
+ * orbital-phase grid phi_o = 2 pi o / n_phi, with the two polarisation
+ * amplitudes free (App. B: for one detector, sky position, distance and
+ * polarisation angle reduce to them):
+ *   <d|h>_{i k o t p} = Re sum_{m,b} 4 w_b d_k^*(f_b) / S_k(f_b) K_{imp} h_{im}(f_b)
+ *                        e^{-2 pi i f_b t_{kt}} e^{i m phi_o}               (Eq. dh_itop)
+ *   <h|h>_{i k o p p'} = Re sum_{m,m',b} 4 w_b / S_k(f_b) K_{imp} h_{im} K^*_{im'p'} h^*_{im'}
+ *                        e^{i (m - m') phi_o}
+ *   ln L^ML_{i k o t} = dh^T [hh]^+ dh / 2                                   (Eqs. x_ML, single_det_ML)
+ *   ln L^inco.ML_i = sum_k max_{o,t} ln L^ML_{i k o t}, and row i is kept when
+ *   ln L^inco.ML_i >= max_j ln L^inco.ML_j - delta                          (Sec. IV.D, delta = 20 there)
+ * [hh]^+ is the inverse when det > 1e-3 hh_{++} hh_{xx}, else the rank-one
+ * pseudo-inverse hh / (hh_{++} + hh_{xx})^2 (a row seen edge-on has hx = 0).
+ * The phase factor's sign differs from App. B's e^{-i m phi}; the grid is
+ * closed under phi -> -phi, so the maxima are the same.
+ * The <d|h> components are one tensor-core GEMM per mode against the bank's
+ * operand planes (precision FP16, FP16X3, BF16 or BF16X3); the rest is FP32,
+ * the detector sum and the selection FP64.  Rows [i0, i1) of the bank.
+ * psd [n_det][n_bins] (double) and data [n_det][n_bins] (complex): host or
+ * device, as for events.  t_grid [n_det][n_t] (double, s; host or device):
+ * the arrival times at each detector.  1 <= n_t <= 4096, 1 <= n_phi <= 64,
+ * delta >= 0.  Synchronous: returns when every output is written. */
+typedef struct dotpe_presel_desc {
+  uint64_t bank_id;
+  int64_t i0, i1;
+  int n_det;
+  const double *psd;
+  const double *data;
+  int n_t;
+  const double *t_grid;
+  int n_phi;
+  double delta;
+  int precision;
+  int flags; /* 0 */
+} dotpe_presel_desc;
+
+typedef struct dotpe_presel_out {
+  double max_lnl_inco; /* max_i ln L^inco.ML_i */
+  double threshold;    /* max_lnl_inco - delta */
+  int64_t arg_i;       /* lowest row (slice-relative) attaining the maximum */
+  int64_t n_selected;  /* N_int' of Sec. IV.D */
+  float kernel_ms;     /* device time of the GEMM + single-detector ML kernel */
+  float device_ms;     /* device time of the whole call (preparation to selection) */
+  int32_t device_status; /* 0, or a DOTPE_E_* raised inside a kernel */
+} dotpe_presel_out;
 
 /* ---- context ----------------------------------------------------------- */
 /* Creates a context on cfg->device (cfg may be NULL: defaults).  Allocates the
@@ -272,6 +325,25 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
 
 /* Frees an event's device state (waits for it if still running). */
 int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id);
+
+/* ---- pre-selection ----------------------------------------------------- */
+/* Runs the pre-selection of dotpe_presel_desc on the bank's rows [i0, i1)
+ * (N = i1 - i0) and writes, into host or device buffers the caller owns
+ * (each may be NULL):
+ *   lnl_ml   [N][n_det] float   max_{o,t} ln L^ML_{i k o t}
+ *   arg_ot   [N][n_det][2] int  its (o, t); lowest t, then lowest o, on ties
+ *   lnl_inco [N] double         ln L^inco.ML_i
+ *   selected [N] int64          the kept rows (slice-relative) in increasing
+ *                               order; the first out->n_selected are valid
+ * The <h|h>_k mode overlaps come from the bank's cross-term cache for this
+ * PSD when an event has filled it, else are computed for the slice.
+ * Temporary device memory (about N (4 n_det + 2) x 8 bytes plus the packed
+ * time-grid operand) is taken outside the HBM budget for the call.
+ * Errors: E_INVALID (shape, range, precision, a bank without pol, non-finite
+ * input), E_NOT_FOUND (bank), E_NOMEM, E_TIMEOUT (a device wait ran out),
+ * E_DEVICE. */
+int dotpe_preselect(dotpe_ctx *ctx, const dotpe_presel_desc *desc, float *lnl_ml, int32_t *arg_ot,
+                    double *lnl_inco, int64_t *selected, dotpe_presel_out *out);
 
 /* ---- diagnostics ------------------------------------------------------- */
 /* Evaluates the device distance marginal ln Lbar(dh, hh) (Eq.

@@ -43,7 +43,8 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_version", "dotpe_device_info", "dotpe_bank_load", "dotpe_bank_release",
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
-           "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit")
+           "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit",
+           "dotpe_preselect")
 
 
 class DotpeError(RuntimeError):
@@ -65,7 +66,7 @@ class dotpe_bank_desc(ctypes.Structure):
     _fields_ = [("n_int", ctypes.c_int64), ("n_modes", ctypes.c_int),
                 ("mode_m", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int),
                 ("f", _dp), ("w_quad", _dp), ("h", ctypes.c_void_p), ("h_dtype", ctypes.c_int),
-                ("ln_w_int", _dp)]
+                ("ln_w_int", _dp), ("pol", _dp)]
 
 
 class dotpe_event_desc(ctypes.Structure):
@@ -75,6 +76,20 @@ class dotpe_event_desc(ctypes.Structure):
                 ("u_min", ctypes.c_double), ("cut_delta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("block_rows", ctypes.c_int64)]
+
+
+class dotpe_presel_desc(ctypes.Structure):
+    _fields_ = [("bank_id", ctypes.c_uint64), ("i0", ctypes.c_int64), ("i1", ctypes.c_int64),
+                ("n_det", ctypes.c_int), ("psd", _dp), ("data", _dp), ("n_t", ctypes.c_int),
+                ("t_grid", _dp), ("n_phi", ctypes.c_int), ("delta", ctypes.c_double),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class dotpe_presel_out(ctypes.Structure):
+    _fields_ = [("max_lnl_inco", ctypes.c_double), ("threshold", ctypes.c_double),
+                ("arg_i", ctypes.c_int64), ("n_selected", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_float), ("device_ms", ctypes.c_float),
+                ("device_status", ctypes.c_int32)]
 
 
 class dotpe_event_stats(ctypes.Structure):
@@ -129,6 +144,8 @@ def load(path: str = LIB_PATH):
         "dotpe_dist_marg_eval": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "dotpe_event_stream_wait": ([vp, ctypes.c_uint64, vp], ctypes.c_int),
         "dotpe_dist_marg_eval_noalloc": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "dotpe_preselect": ([vp, ctypes.POINTER(dotpe_presel_desc), vp, vp, vp, vp,
+                             ctypes.POINTER(dotpe_presel_out)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -185,9 +202,10 @@ def dotpe_device_info(ctx):
     return n.value, buf.value.decode()
 
 
-def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None):
+def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None, pol=None):
     """h: [I, M, B] complex128/complex64 numpy array, or a torch tensor on the device
-    (complex128/complex64, contiguous)."""
+    (complex128/complex64, contiguous).  pol: optional [I, M, 2] complex
+    polarisation factors K_{imp} (needed by dotpe_preselect)."""
     L = load()
     keep = []
     if hasattr(h, "data_ptr"):
@@ -209,8 +227,11 @@ def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None):
     f = np.ascontiguousarray(f, dtype=np.float64)
     w = np.ascontiguousarray(w_quad, dtype=np.float64)
     lw = None if ln_w_int is None else np.ascontiguousarray(ln_w_int, dtype=np.float64)
+    pl = None if pol is None else _host_c128(pol)
+    if pl is not None and pl.shape != (I, M, 2):
+        raise ValueError(f"pol has shape {pl.shape}, expected {(I, M, 2)}")
     desc = dotpe_bank_desc(I, M, mm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), B, _ptr(f), _ptr(w),
-                           hp, dtype, _ptr(lw))
+                           hp, dtype, _ptr(lw), None if pl is None else _ptr(pl.view(np.float64)))
     bid = ctypes.c_uint64()
     _check(L.dotpe_bank_load(ctx, ctypes.byref(desc), ctypes.byref(bid)))
     return bid.value
@@ -307,6 +328,43 @@ def dotpe_lnl_blocks(ctx, event_id, i0, i1, e0, e1, what=DOTPE_LNL_MARG, out=Non
 
 def dotpe_event_release(ctx, event_id):
     return _check(load().dotpe_event_release(ctx, event_id))
+
+
+def dotpe_preselect(ctx, bank_id, i0, i1, psd, data, t_grid, n_phi=32, delta=20.0, precision="fp16x3",
+                    outputs=("lnl_ml", "arg_ot", "lnl_inco", "selected")):
+    """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of bank rows [i0, i1).
+
+    psd [D, B], data [D, B] complex, t_grid [D, n_t] (numpy, host).  Returns a dict
+    with the dotpe_presel_out fields and the requested host arrays: lnl_ml [N, D]
+    float32, arg_ot [N, D, 2] int32 ((o, t)), lnl_inco [N] float64, selected
+    [n_selected] int64 (slice-relative rows)."""
+    L = load()
+    psd = np.ascontiguousarray(psd, dtype=np.float64)
+    data = _host_c128(data)
+    tg = np.ascontiguousarray(t_grid, dtype=np.float64)
+    D, n_t = tg.shape
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    desc = dotpe_presel_desc(bank_id, i0, i1, D, _ptr(psd), _ptr(data.view(np.float64)), n_t, _ptr(tg),
+                             n_phi, float(delta), prec, 0)
+    N = i1 - i0
+    arrs = {}
+    if "lnl_ml" in outputs:
+        arrs["lnl_ml"] = np.empty((N, D), dtype=np.float32)
+    if "arg_ot" in outputs:
+        arrs["arg_ot"] = np.empty((N, D, 2), dtype=np.int32)
+    if "lnl_inco" in outputs:
+        arrs["lnl_inco"] = np.empty(N, dtype=np.float64)
+    if "selected" in outputs:
+        arrs["selected"] = np.empty(N, dtype=np.int64)
+    vp = lambda k: ctypes.c_void_p(arrs[k].ctypes.data) if k in arrs else None
+    o = dotpe_presel_out()
+    _check(L.dotpe_preselect(ctx, ctypes.byref(desc), vp("lnl_ml"), vp("arg_ot"), vp("lnl_inco"),
+                             vp("selected"), ctypes.byref(o)))
+    res = {k: getattr(o, k) for k, _ in o._fields_}
+    if "selected" in arrs:
+        arrs["selected"] = arrs["selected"][:o.n_selected]
+    res.update(arrs)
+    return res
 
 
 def dotpe_dist_marg_eval(ctx, dh, hh, u_min):

@@ -101,6 +101,7 @@ struct Bank {
   __nv_bfloat16 *bf = nullptr;                       // [2][M][I][Kpad] hi, lo
   __half *hf = nullptr;                              // [2][M][I][Kpad] hi, lo
   float a_scale = 1.f;
+  float2 *pol = nullptr;  // [I][M][2] polarisation factors K_{imp} (pre-selection), or null
   void *block = nullptr;
   size_t bytes = 0;
   int refs = 0;
@@ -591,50 +592,85 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
 // rows into its scratch instead).  The stream waits for the entry's records.
 // Entries past XCACHE_MAX per bank are dropped least recently used first, when
 // no event holds them.
+static XEntry *xcache_find(Bank &b, uint64_t key, int D) {
+  for (XEntry *c : b.xcache)
+    if (c->key == key && c->D == D) return c;
+  return nullptr;
+}
+
+// A new cache entry of the bank's row records for one PSD, computed on `st`
+// from omega (which `st` has already been ordered after); evicts the least
+// recently used unreferenced entry when the bank's cache is full.
+static int xcache_build(dotpe_ctx *ctx, Bank &b, uint64_t key, int D, const float *omega, cudaStream_t st,
+                        XEntry **out) {
+  if ((int)b.xcache.size() >= XCACHE_MAX) {
+    auto victim = b.xcache.end();
+    for (auto it = b.xcache.begin(); it != b.xcache.end(); ++it)
+      if ((*it)->refs == 0 && (victim == b.xcache.end() || (*it)->last < (*victim)->last)) victim = it;
+    if (victim != b.xcache.end()) {
+      XEntry *v = *victim;
+      CUDA_OR_FAIL(cudaEventSynchronize(v->ready));
+      CUDA_OR_FAIL(cudaFree(v->mx));
+      cudaEventDestroy(v->ready);
+      ctx->used -= v->bytes;
+      delete v;
+      b.xcache.erase(victim);
+    }
+  }
+  XEntry *x = new XEntry();
+  x->key = key;
+  x->D = D;
+  x->bytes = (size_t)b.I * D * REC * sizeof(float);
+  if (cudaMallocAsync((void **)&x->mx, x->bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    delete x;
+    return fail(DOTPE_E_NOMEM, "cross-term records (%zu bytes)", (size_t)b.I * D * REC * sizeof(float));
+  }
+  CUDA_OR_FAIL(cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming));
+  launch_cross_terms(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.master, omega, x->mx, ctx->n_sms, st);
+  CUDA_OR_FAIL(cudaEventRecord(x->ready, st));
+  ctx->used += x->bytes;
+  b.xcache.push_back(x);
+  *out = x;
+  return DOTPE_OK;
+}
+
 static int xterms_acquire(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
   Bank &b = *e.bank;
-  XEntry *x = nullptr;
-  for (XEntry *c : b.xcache)
-    if (c->key == e.psd_key && c->D == e.D) x = c;
+  XEntry *x = xcache_find(b, e.psd_key, e.D);
   if (x) {
     CUDA_OR_FAIL(cudaStreamWaitEvent(st, x->ready, 0));
   } else if (4 * e.NI < b.I) {
     return DOTPE_OK;
   } else {
-    if ((int)b.xcache.size() >= XCACHE_MAX) {
-      auto victim = b.xcache.end();
-      for (auto it = b.xcache.begin(); it != b.xcache.end(); ++it)
-        if ((*it)->refs == 0 && (victim == b.xcache.end() || (*it)->last < (*victim)->last)) victim = it;
-      if (victim != b.xcache.end()) {
-        XEntry *v = *victim;
-        CUDA_OR_FAIL(cudaEventSynchronize(v->ready));
-        CUDA_OR_FAIL(cudaFree(v->mx));
-        cudaEventDestroy(v->ready);
-        ctx->used -= v->bytes;
-        delete v;
-        b.xcache.erase(victim);
-      }
-    }
-    x = new XEntry();
-    x->key = e.psd_key;
-    x->D = e.D;
-    x->bytes = (size_t)b.I * e.D * REC * sizeof(float);
-    if (cudaMallocAsync((void **)&x->mx, x->bytes, st) != cudaSuccess) {
-      cudaGetLastError();
-      delete x;
-      return fail(DOTPE_E_NOMEM, "cross-term records (%zu bytes)", (size_t)b.I * e.D * REC * sizeof(float));
-    }
-    CUDA_OR_FAIL(cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming));
     // omega of this event (its prep on `st` writes it) -> records of every bank row
     launch_prep(R.pa, st);
-    launch_cross_terms(b.I, 0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, x->mx, ctx->n_sms, st);
-    CUDA_OR_FAIL(cudaEventRecord(x->ready, st));
-    ctx->used += x->bytes;
-    b.xcache.push_back(x);
+    int rc = xcache_build(ctx, b, e.psd_key, e.D, R.pa.omega, st, &x);
+    if (rc != DOTPE_OK) return rc;
   }
   x->refs++;
   x->last = now_ns();
   e.xent = x;
+  return DOTPE_OK;
+}
+
+// Cross-term cache key: FNV-1a over n_det and the PSD bytes (host or device).
+static int psd_hash(int D, int B, const double *psd, uint64_t *out) {
+  std::vector<double> ps((size_t)D * B);
+  if (is_device_ptr(psd)) {
+    if (cudaMemcpy(ps.data(), psd, ps.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(DOTPE_E_DEVICE, "reading the PSD");
+  } else {
+    memcpy(ps.data(), psd, ps.size() * 8);
+  }
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void *p, size_t n) {
+    const uint8_t *c = (const uint8_t *)p;
+    for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
+  };
+  mix(&D, sizeof(D));
+  mix(ps.data(), ps.size() * 8);
+  *out = h;
   return DOTPE_OK;
 }
 
@@ -1009,6 +1045,193 @@ static void free_event(dotpe_ctx *ctx, Event *e) {
   delete e;
 }
 
+// ---------------------------------------------------------------------------
+// Incoherent single-detector pre-selection (Sec. IV.D, App. B)
+// ---------------------------------------------------------------------------
+static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *lnl_ml, int32_t *arg_ot,
+                            double *lnl_inco, int64_t *selected, dotpe_presel_out *out) {
+  auto bit = ctx->banks.find(d->bank_id);
+  if (bit == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)d->bank_id);
+  Bank &b = *bit->second;
+  if (!b.pol) return fail(DOTPE_E_INVALID, "bank %llu was loaded without polarisation factors (pol)",
+                          (unsigned long long)d->bank_id);
+  if (d->i0 < 0 || d->i1 <= d->i0 || d->i1 > b.I)
+    return fail(DOTPE_E_INVALID, "slice [%lld,%lld) of %lld rows", (long long)d->i0, (long long)d->i1, (long long)b.I);
+  if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
+  if (d->n_t < 1 || d->n_t > 4096) return fail(DOTPE_E_INVALID, "n_t=%d not in 1..4096", d->n_t);
+  if (d->n_phi < 1 || d->n_phi > PS_MAXPHI) return fail(DOTPE_E_INVALID, "n_phi=%d not in 1..%d", d->n_phi, PS_MAXPHI);
+  if (!(d->delta >= 0.0) || !std::isfinite(d->delta)) return fail(DOTPE_E_INVALID, "delta must be finite and >= 0");
+  if (!d->psd || !d->data || !d->t_grid) return fail(DOTPE_E_INVALID, "null input array");
+  const int prec = d->precision;
+  if (prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 && prec != DOTPE_PREC_BF16X3)
+    return fail(DOTPE_E_INVALID, "pre-selection precision %d (FP16, FP16X3, BF16 or BF16X3)", prec);
+  if (d->flags != 0) return fail(DOTPE_E_INVALID, "flags must be 0");
+  const int64_t NI = d->i1 - d->i0;
+  if (NI >= (1ll << 31) / 2) return fail(DOTPE_E_UNSUPPORTED, "slice too large");
+  const int D = d->n_det, B = b.B, M = b.M, NT = d->n_t;
+  const int NTP = (NT + PS_TC - 1) / PS_TC * PS_TC;
+  const bool bf = prec_bf16(prec), split = prec_split(prec);
+  const int planes = split ? 2 : 1;
+  cudaStream_t st = ctx->main_stream;
+
+  // cross-term records: the bank's cache entry for this PSD, a new one when the
+  // slice is a large part of the bank, else the slice's own
+  uint64_t key = 0;
+  int rc = psd_hash(D, B, d->psd, &key);
+  if (rc != DOTPE_OK) return rc;
+  XEntry *x = xcache_find(b, key, D);
+  const bool build_cache = !x && 4 * NI >= b.I;
+  const bool own_mx = !x && !build_cache;
+
+  Carver c;
+  const size_t o_psd = c.take<double>((size_t)D * B), o_data = c.take<double2>((size_t)D * B);
+  const size_t o_tg = c.take<double>((size_t)D * NT);
+  const size_t o_c = c.take<float2>((size_t)D * B), o_om = c.take<float>((size_t)D * B);
+  const size_t o_fh = c.take<float>(B), o_fl = c.take<float>(B);
+  const size_t o_G = c.take<float2>((size_t)D * NTP * B);
+  const size_t o_gmax = c.take<float>(1), o_gs = c.take<float>(1);
+  const size_t o_pack = c.take<uint16_t>((size_t)planes * 2 * D * NTP * b.Kpad);
+  const size_t o_mx = own_mx ? c.take<float>((size_t)NI * D * REC) : 0;
+  const size_t o_keys = c.take<unsigned long long>((size_t)NI * D);
+  const size_t o_ml = c.take<float>((size_t)NI * D), o_arg = c.take<int>((size_t)NI * D * 2);
+  const size_t o_inco = c.take<double>(NI), o_sel = c.take<int64_t>(NI);
+  const size_t o_maxb = c.take<unsigned long long>(1), o_out = c.take<PreselOut>(1), o_st = c.take<int>(1);
+  uint8_t *scr = nullptr;
+  if (cudaMallocAsync((void **)&scr, c.off, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DOTPE_E_NOMEM, "pre-selection scratch (%zu bytes)", c.off);
+  }
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  auto finish = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaFreeAsync(scr, st);
+    cudaStreamSynchronize(st);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    return code;
+  };
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return finish(fail(DOTPE_E_DEVICE, "event creation"));
+  auto ck = [&](cudaError_t e, const char *what) {
+    if (e != cudaSuccess && rc == DOTPE_OK) rc = fail(DOTPE_E_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+  };
+  int *status = (int *)(scr + o_st);
+  ck(cudaEventRecord(ev[0], st), "event record");
+  ck(cudaMemsetAsync(status, 0, sizeof(int), st), "memset");
+  ck(cudaMemsetAsync(scr + o_gmax, 0, 4, st), "memset");
+  ck(cudaMemsetAsync(scr + o_keys, 0, (size_t)NI * D * 8, st), "memset");
+  ck(cudaMemsetAsync(scr + o_maxb, 0, 8, st), "memset");
+  ck(cudaMemcpyAsync(scr + o_psd, d->psd, (size_t)D * B * 8, cudaMemcpyDefault, st), "copying psd");
+  ck(cudaMemcpyAsync(scr + o_data, d->data, (size_t)D * B * 16, cudaMemcpyDefault, st), "copying data");
+  ck(cudaMemcpyAsync(scr + o_tg, d->t_grid, (size_t)D * NT * 8, cudaMemcpyDefault, st), "copying t_grid");
+  if (rc != DOTPE_OK) return finish(rc);
+
+  PreselPrepArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.D = D; pa.B = B; pa.Kpad = b.Kpad; pa.n_t = NT; pa.n_tpad = NTP;
+  pa.f = b.f; pa.w = b.w; pa.psd = (const double *)(scr + o_psd); pa.data = (const double2 *)(scr + o_data);
+  pa.t_grid = (const double *)(scr + o_tg);
+  pa.c = (float2 *)(scr + o_c); pa.omega = (float *)(scr + o_om);
+  pa.fh = (float *)(scr + o_fh); pa.fl = (float *)(scr + o_fl);
+  pa.G32 = (float2 *)(scr + o_G); pa.gmax = (float *)(scr + o_gmax);
+  pa.gpack = scr + o_pack; pa.pack_kind = bf ? 1 : 2; pa.pack_planes = planes;
+  pa.gscale = (float *)(scr + o_gs); pa.status = status;
+  launch_presel_prep(pa, st);
+
+  const float *mx = nullptr;
+  if (x) {
+    ck(cudaStreamWaitEvent(st, x->ready, 0), "cross-term wait");
+    mx = x->mx + (size_t)d->i0 * D * REC;
+  } else if (build_cache) {
+    if ((rc = xcache_build(ctx, b, key, D, pa.omega, st, &x)) != DOTPE_OK) return finish(rc);
+    mx = x->mx + (size_t)d->i0 * D * REC;
+  } else {
+    launch_cross_terms(NI, d->i0, b.I, M, D, B, b.Kpad, b.master, pa.omega, (float *)(scr + o_mx), ctx->n_sms, st);
+    mx = (const float *)(scr + o_mx);
+  }
+  if (x) {
+    x->refs++;
+    x->last = now_ns();
+  }
+
+  CUtensorMap mapA, mapB;
+  const int64_t a_rows = 2 * (int64_t)M * b.I;
+  CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  if (a_rows >= (1ll << 31)) rc = fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
+  else if (encode_tmap_kblocks(&mapA, dt, bf ? (void *)b.bf : (void *)b.hf, a_rows, b.Kpad / 64,
+                               (uint64_t)b.Kpad * 2, 128, PS_KBX) ||
+           encode_tmap_kblocks(&mapB, dt, scr + o_pack, (uint64_t)planes * 2 * D * NTP, b.Kpad / 64,
+                               (uint64_t)b.Kpad * 2, 2 * PS_TC, PS_KBX))
+    rc = fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (pre-selection)");
+  PreselParams P;
+  memset(&P, 0, sizeof(P));
+  P.n_rows = (int)NI;
+  P.a_row0 = (int)d->i0;
+  P.n_det = D; P.n_t = NT; P.n_tpad = NTP; P.n_phi = d->n_phi; P.n_modes = M;
+  for (int m = 0; m < MAXM; ++m) P.mode_m[m] = m < M ? b.mode_m[m] : 0;
+  {
+    int p = 0;
+    for (int a = 1; a < MAXM; ++a)
+      for (int q = 0; q < a; ++q, ++p) P.pdelta[p] = (a < M) ? (b.mode_m[a] - b.mode_m[q]) : 0;
+  }
+  P.n_itile = (int)((NI + 127) / 128);
+  P.n_ctile = D * NTP / PS_TC;
+  P.kb = b.Kpad / 64;
+  P.a_plane_rows = M * (int)b.I;
+  P.a_mode_rows = (int)b.I;
+  P.b_plane_rows = 2 * D * NTP;
+  P.pol = b.pol + (size_t)d->i0 * M * 2;
+  P.mx = mx;
+  P.z_scale = 1.f / (b.a_scale * (bf ? 1.f : FP16_OPERAND_SCALE));
+  P.g_scale = pa.gscale;
+  P.rank_tol = PS_RANK_TOL;
+  P.keys = (unsigned long long *)(scr + o_keys);
+  P.status = status;
+  P.wait_ns = 4000000000ull;
+  if (rc == DOTPE_OK) {
+    ck(cudaEventRecord(ev[1], st), "event record");
+    ck((cudaError_t)launch_presel(mapA, mapB, P, bf, split, ctx->n_sms, st), "pre-selection kernel");
+    ck(cudaEventRecord(ev[2], st), "event record");
+    launch_presel_finish(NI, D, d->n_phi, d->delta, P.keys, (float *)(scr + o_ml), (int *)(scr + o_arg),
+                         (double *)(scr + o_inco), (unsigned long long *)(scr + o_maxb), (int64_t *)(scr + o_sel),
+                         (PreselOut *)(scr + o_out), st);
+    ck(cudaGetLastError(), "pre-selection finish");
+    ck(cudaEventRecord(ev[3], st), "event record");
+  }
+  PreselOut po;
+  int dev_status = 0;
+  memset(&po, 0, sizeof(po));
+  if (rc == DOTPE_OK) {
+    ck(cudaMemcpyAsync(&po, scr + o_out, sizeof(po), cudaMemcpyDeviceToHost, st), "result copy");
+    ck(cudaMemcpyAsync(&dev_status, status, sizeof(int), cudaMemcpyDeviceToHost, st), "result copy");
+    ck(cudaStreamSynchronize(st), "pre-selection");
+  }
+  if (x) x->refs--;
+  if (rc != DOTPE_OK) return finish(rc);
+  if (dev_status != 0) {
+    rc = dev_status == DEV_E_TIMEOUT ? fail(DOTPE_E_TIMEOUT, "a device wait ran out in the pre-selection kernel")
+                                     : fail(DOTPE_E_INVALID, "non-finite values in the pre-selection inputs");
+    return finish(rc);
+  }
+  if (lnl_ml) ck(cudaMemcpyAsync(lnl_ml, scr + o_ml, (size_t)NI * D * 4, cudaMemcpyDefault, st), "copying lnl_ml");
+  if (arg_ot) ck(cudaMemcpyAsync(arg_ot, scr + o_arg, (size_t)NI * D * 8, cudaMemcpyDefault, st), "copying arg_ot");
+  if (lnl_inco) ck(cudaMemcpyAsync(lnl_inco, scr + o_inco, (size_t)NI * 8, cudaMemcpyDefault, st), "copying lnl_inco");
+  if (selected && po.n_selected > 0)
+    ck(cudaMemcpyAsync(selected, scr + o_sel, (size_t)po.n_selected * 8, cudaMemcpyDefault, st), "copying selected");
+  ck(cudaStreamSynchronize(st), "pre-selection outputs");
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->max_lnl_inco = po.max_inco;
+    out->threshold = po.threshold;
+    out->arg_i = po.arg_i;
+    out->n_selected = po.n_selected;
+    cudaEventElapsedTime(&out->kernel_ms, ev[1], ev[2]);
+    cudaEventElapsedTime(&out->device_ms, ev[0], ev[3]);
+    out->device_status = dev_status;
+  }
+  return finish(rc);
+}
+
 }  // namespace dotpe
 
 using namespace dotpe;
@@ -1179,6 +1402,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   size_t o_f = c.take<double>(b->B), o_w = c.take<double>(b->B), o_lw = c.take<double>(b->I);
   size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(2 * nel);
   size_t o_scal = c.take<float>(4);
+  size_t o_pol = d->pol ? c.take<float2>((size_t)b->I * b->M * 2) : 0;
   b->bytes = c.off;
   if (ctx->used + b->bytes > ctx->budget) {
     delete b;
@@ -1197,6 +1421,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   b->bf = (__nv_bfloat16 *)(base + o_bf);
   b->hf = (__half *)(base + o_hf);
   float *scal = (float *)(base + o_scal);  // [0] amax, [1] a_scale, [2] status
+  b->pol = d->pol ? (float2 *)(base + o_pol) : nullptr;
   cudaStream_t st = ctx->main_stream;
   int rc = DOTPE_OK;
   auto check = [&](cudaError_t x) {
@@ -1207,6 +1432,25 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   check(cudaMemcpyAsync(b->f, d->f, b->B * 8, cudaMemcpyDefault, st));
   check(cudaMemcpyAsync(b->w, d->w_quad, b->B * 8, cudaMemcpyDefault, st));
   if (d->ln_w_int) check(cudaMemcpyAsync(b->lw, d->ln_w_int, b->I * 8, cudaMemcpyDefault, st));
+  if (d->pol && rc == DOTPE_OK) {
+    // polarisation factors: FP64 complex -> FP32 on the host, then one copy
+    const size_t n = (size_t)b->I * b->M * 2;
+    std::vector<double> src;
+    const double *pd = d->pol;
+    if (is_device_ptr(d->pol)) {
+      src.resize(2 * n);
+      check(cudaMemcpy(src.data(), d->pol, 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
+      pd = src.data();
+    }
+    std::vector<float2> pf(n);
+    bool finite = true;
+    for (size_t k = 0; k < n && rc == DOTPE_OK; ++k) {
+      if (!std::isfinite(pd[2 * k]) || !std::isfinite(pd[2 * k + 1])) finite = false;
+      pf[k] = make_float2((float)pd[2 * k], (float)pd[2 * k + 1]);
+    }
+    if (!finite && rc == DOTPE_OK) rc = fail(DOTPE_E_INVALID, "pol contains non-finite values");
+    if (rc == DOTPE_OK) check(cudaMemcpy(b->pol, pf.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   // stream the waveforms through a device staging buffer in row chunks
   const size_t row_bytes = (size_t)b->M * b->B * (d->h_dtype == DOTPE_C128 ? 16 : 8);
   const bool hdev = is_device_ptr(d->h);
@@ -1378,22 +1622,8 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
     }
   }
   {
-    // cross-term cache key: FNV-1a over n_det and the PSD bytes
-    std::vector<double> ps((size_t)(D * B));
-    if (is_device_ptr(d->psd)) {
-      if (cudaMemcpy(ps.data(), d->psd, ps.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return cleanup(fail(DOTPE_E_DEVICE, "reading the PSD"));
-    } else {
-      memcpy(ps.data(), d->psd, ps.size() * 8);
-    }
-    uint64_t h = 1469598103934665603ull;
-    auto mix = [&](const void *p, size_t n) {
-      const uint8_t *c = (const uint8_t *)p;
-      for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
-    };
-    mix(&e->D, sizeof(e->D));
-    mix(ps.data(), ps.size() * 8);
-    e->psd_key = h;
+    int rc = psd_hash(e->D, (int)B, d->psd, &e->psd_key);
+    if (rc != DOTPE_OK) return cleanup(rc);
   }
   cudaEventCreateWithFlags(&e->ev_inputs, cudaEventDisableTiming);
   cudaEventCreate(&e->ev_start);
@@ -1687,6 +1917,14 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
     return DOTPE_OK;
   }
   return fail(DOTPE_E_INVALID, "what=%d", what);
+}
+
+int dotpe_preselect(dotpe_ctx *ctx, const dotpe_presel_desc *desc, float *lnl_ml, int32_t *arg_ot,
+                    double *lnl_inco, int64_t *selected, dotpe_presel_out *out) {
+  if (!ctx || !desc) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  return preselect_locked(ctx, desc, lnl_ml, arg_ot, lnl_inco, selected, out);
 }
 
 int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id) {

@@ -179,6 +179,56 @@ void launch_reduce_block(const ReduceArgs &a, cudaStream_t st);
 void launch_reduce_final(const ReduceArgs &a, cudaStream_t st);
 size_t reduce_scratch_bytes();
 
+// Incoherent single-detector pre-selection (Sec. IV.D, App. B): kernel_presel.cu.
+constexpr int PS_TC = 32;       // (detector, time) columns per tile; time grids are padded to a multiple
+constexpr int PS_MAXPHI = 64;   // phases per grid
+constexpr float PS_RANK_TOL = 1e-3f;
+constexpr int PS_KBX = 2;       // k-blocks of 64 per TMA box (both operand maps)  // [hh]^+ is the rank-one limit when det <= PS_RANK_TOL hh_++ hh_xx
+struct PreselPrepArgs {
+  int D, B, Kpad, n_t, n_tpad;
+  const double *f, *w, *psd;
+  const double2 *data;
+  const double *t_grid;  // [D][n_t]
+  float2 *c;             // [D][B] 4 w conj(d) / S
+  float *omega, *fh, *fl;
+  float2 *G32;           // [D n_tpad][B] c_{kb} e^{-2 pi i f_b t_{kt}} (0 on padding columns)
+  float *gmax;           // 1 float, zeroed
+  void *gpack;           // packed operand planes [planes][2 D n_tpad][Kpad]
+  int pack_kind;         // 1 bf16, 2 fp16
+  int pack_planes;       // 1 or 2 (hi, lo)
+  float *gscale;         // 1 float out
+  int *status;
+};
+void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st);
+struct PreselParams {
+  int n_rows;            // rows of the slice
+  int a_row0;            // first bank row of the slice
+  int n_det, n_t, n_tpad, n_phi, n_modes;
+  int mode_m[MAXM];
+  int pdelta[NPAIR];     // m_a - m_b of mode pair p (a > b), 1..3
+  int n_itile, n_ctile;  // 128-row tiles, 32-column tiles
+  int kb;                // k-blocks of 64 per mode
+  int a_plane_rows, a_mode_rows, b_plane_rows;
+  const float2 *pol;     // [n_rows][M][2] K_{imp} (slice-relative)
+  const float *mx;       // [n_rows][n_det][REC] <h_m|h_m'>_k (slice-relative)
+  float z_scale;         // accumulator -> Z scale (times 1 / *g_scale)
+  const float *g_scale;
+  float rank_tol;
+  unsigned long long *keys;  // [n_rows][n_det] out: (ln L^ML bits << 32) | ~(t n_phi + o), zeroed
+  int *status;
+  unsigned long long wait_ns;
+};
+struct PreselOut {
+  double max_inco, threshold;
+  long long arg_i, n_selected;
+};
+// returns a cudaError_t
+int launch_presel(const CUtensorMap &mapA, const CUtensorMap &mapB, const PreselParams &p, bool bf16, bool split,
+                  int n_sms, cudaStream_t st);
+void launch_presel_finish(int64_t n, int D, int n_phi, double delta, const unsigned long long *keys, float *ml,
+                          int *arg_ot, double *inco, unsigned long long *max_bits /*zeroed*/, int64_t *sel,
+                          PreselOut *out, cudaStream_t st);
+
 // Tensor-map encoding through the driver entry point.
 int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,
                         uint64_t row_bytes, uint32_t box_rows, uint32_t box_kb);

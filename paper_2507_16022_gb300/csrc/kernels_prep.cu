@@ -411,6 +411,54 @@ void launch_prep(const PrepArgs &a, cudaStream_t st) {
                                                         a.gpack, a.gscale);
 }
 
+// ---------------------------------------------------------------------------
+// Pre-selection operand (Sec. IV.D, App. B): G_k[b, t] = c_{kb} e^{-2 pi i f_b t_{kt}}
+// ---------------------------------------------------------------------------
+__global__ void presel_G_kernel(int D, int B, int n_t, int n_tpad, const float *__restrict__ fh,
+                                const float *__restrict__ fl, const double *__restrict__ t_grid,
+                                const float2 *__restrict__ c, float2 *__restrict__ G, float *__restrict__ gmax,
+                                int *status) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float a = 0.f;
+  if (k < (int64_t)D * n_tpad * B) {
+    const int b = (int)(k % B);
+    const int col = (int)(k / B);
+    const int d = col / n_tpad, t = col - d * n_tpad;
+    float2 g = make_float2(0.f, 0.f);
+    if (t < n_t) {
+      double tv = t_grid[(int64_t)d * n_t + t];
+      if (!isfinite(tv)) { atomicCAS(status, 0, DEV_E_NONFINITE); tv = 0.0; }
+      const float th = (float)tv, tl = (float)(tv - (double)th);
+      const float2 T = shift_factor(fh[b], fl[b], th, tl);
+      const float2 cc = c[d * B + b];
+      g = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
+    }
+    G[k] = g;
+    a = fmaxf(fabsf(g.x), fabsf(g.y));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(gmax, a);
+}
+
+void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st) {
+  const int DB = a.D * a.B;
+  prep_bins_kernel<<<nblk(DB > a.B ? DB : a.B, 256), 256, 0, st>>>(a.D, a.B, a.f, a.w, a.psd, a.data, a.c, a.omega,
+                                                                   a.fh, a.fl, a.status);
+  const int64_t n = (int64_t)a.D * a.n_tpad * a.B;
+  presel_G_kernel<<<nblk(n, 256), 256, 0, st>>>(a.D, a.B, a.n_t, a.n_tpad, a.fh, a.fl, a.t_grid, a.c, a.G32,
+                                                a.gmax, a.status);
+  const int64_t E = (int64_t)a.D * a.n_tpad;
+  const int pad = a.Kpad - 2 * a.B;
+  const int64_t np = E * (a.B > pad ? a.B : pad);
+  if (a.pack_kind == 1)
+    pack_G_kernel<__nv_bfloat16><<<nblk(np, 256), 256, 0, st>>>(E, 1, a.B, a.Kpad, a.G32, a.gmax, 1, a.pack_planes,
+                                                                a.gpack, a.gscale);
+  else
+    pack_G_kernel<__half><<<nblk(np, 256), 256, 0, st>>>(E, 1, a.B, a.Kpad, a.G32, a.gmax, 2, a.pack_planes, a.gpack,
+                                                         a.gscale);
+}
+
 void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
                         const float *master, const float *omega, float *mx, int n_sms, cudaStream_t st) {
   int bs = 256;
