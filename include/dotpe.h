@@ -215,7 +215,7 @@ typedef struct dotpe_evidence_out {
  * the detector sum and the selection FP64.  Rows [i0, i1) of the bank.
  * psd [n_det][n_bins] (double) and data [n_det][n_bins] (complex): host or
  * device, as for events.  t_grid [n_det][n_t] (double, s; host or device):
- * the arrival times at each detector.  1 <= n_t <= 4096, 1 <= n_phi <= 64,
+ * the arrival times at each detector.  1 <= n_t <= 4096, 1 <= n_phi <= 32,
  * delta >= 0.  Synchronous: returns when every output is written. */
 typedef struct dotpe_presel_desc {
   uint64_t bank_id;

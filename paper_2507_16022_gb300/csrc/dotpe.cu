@@ -1154,14 +1154,14 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     x->last = now_ns();
   }
 
-  CUtensorMap mapA, mapB;
+  CUtensorMap mapG, mapBank;
   const int64_t a_rows = 2 * (int64_t)M * b.I;
   CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   if (a_rows >= (1ll << 31)) rc = fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
-  else if (encode_tmap_kblocks(&mapA, dt, bf ? (void *)b.bf : (void *)b.hf, a_rows, b.Kpad / 64,
-                               (uint64_t)b.Kpad * 2, 128, PS_KBX) ||
-           encode_tmap_kblocks(&mapB, dt, scr + o_pack, (uint64_t)planes * 2 * D * NTP, b.Kpad / 64,
-                               (uint64_t)b.Kpad * 2, 2 * PS_TC, PS_KBX))
+  else if (encode_tmap_kblocks(&mapBank, dt, bf ? (void *)b.bf : (void *)b.hf, a_rows, b.Kpad / 64,
+                               (uint64_t)b.Kpad * 2, PS_TR, 1) ||
+           encode_tmap_kblocks(&mapG, dt, scr + o_pack, (uint64_t)planes * 2 * D * NTP, b.Kpad / 64,
+                               (uint64_t)b.Kpad * 2, 2 * PS_TC, 1))
     rc = fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (pre-selection)");
   PreselParams P;
   memset(&P, 0, sizeof(P));
@@ -1173,8 +1173,16 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     int p = 0;
     for (int a = 1; a < MAXM; ++a)
       for (int q = 0; q < a; ++q, ++p) P.pdelta[p] = (a < M) ? (b.mode_m[a] - b.mode_m[q]) : 0;
+    // epilogue slots: modes with even m first (the phase pairing phi, phi + pi)
+    int ns = 0;
+    for (int m = 0; m < M; ++m)
+      if (b.mode_m[m] % 2 == 0) P.slot[ns++] = m;
+    P.n_even = ns;
+    for (int m = 0; m < M; ++m)
+      if (b.mode_m[m] % 2 != 0) P.slot[ns++] = m;
+    for (; ns < MAXM; ++ns) P.slot[ns] = 0;
   }
-  P.n_itile = (int)((NI + 127) / 128);
+  P.n_itile = (int)((NI + PS_TR - 1) / PS_TR);
   P.n_ctile = D * NTP / PS_TC;
   P.kb = b.Kpad / 64;
   P.a_plane_rows = M * (int)b.I;
@@ -1190,7 +1198,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   P.wait_ns = 4000000000ull;
   if (rc == DOTPE_OK) {
     ck(cudaEventRecord(ev[1], st), "event record");
-    ck((cudaError_t)launch_presel(mapA, mapB, P, bf, split, ctx->n_sms, st), "pre-selection kernel");
+    ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, ctx->n_sms, st), "pre-selection kernel");
     ck(cudaEventRecord(ev[2], st), "event record");
     launch_presel_finish(NI, D, d->n_phi, d->delta, P.keys, (float *)(scr + o_ml), (int *)(scr + o_arg),
                          (double *)(scr + o_inco), (unsigned long long *)(scr + o_maxb), (int64_t *)(scr + o_sel),

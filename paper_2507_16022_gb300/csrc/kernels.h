@@ -180,10 +180,10 @@ void launch_reduce_final(const ReduceArgs &a, cudaStream_t st);
 size_t reduce_scratch_bytes();
 
 // Incoherent single-detector pre-selection (Sec. IV.D, App. B): kernel_presel.cu.
-constexpr int PS_TC = 32;       // (detector, time) columns per tile; time grids are padded to a multiple
-constexpr int PS_MAXPHI = 64;   // phases per grid
-constexpr float PS_RANK_TOL = 1e-3f;
-constexpr int PS_KBX = 2;       // k-blocks of 64 per TMA box (both operand maps)  // [hh]^+ is the rank-one limit when det <= PS_RANK_TOL hh_++ hh_xx
+constexpr int PS_TC = 64;       // (detector, time) columns per tile; time grids are padded to a multiple
+constexpr int PS_TR = 64;       // bank rows per tile
+constexpr int PS_MAXPHI = 32;   // phases per grid
+constexpr float PS_RANK_TOL = 1e-3f;  // [hh]^+ is the rank-one limit when det <= PS_RANK_TOL hh_++ hh_xx
 struct PreselPrepArgs {
   int D, B, Kpad, n_t, n_tpad;
   const double *f, *w, *psd;
@@ -206,7 +206,9 @@ struct PreselParams {
   int n_det, n_t, n_tpad, n_phi, n_modes;
   int mode_m[MAXM];
   int pdelta[NPAIR];     // m_a - m_b of mode pair p (a > b), 1..3
-  int n_itile, n_ctile;  // 128-row tiles, 32-column tiles
+  int slot[MAXM];        // epilogue mode slots: bank mode index, even m first
+  int n_even;            // modes with even m
+  int n_itile, n_ctile;  // 64-row tiles, 64-column tiles
   int kb;                // k-blocks of 64 per mode
   int a_plane_rows, a_mode_rows, b_plane_rows;
   const float2 *pol;     // [n_rows][M][2] K_{imp} (slice-relative)
@@ -223,7 +225,7 @@ struct PreselOut {
   long long arg_i, n_selected;
 };
 // returns a cudaError_t
-int launch_presel(const CUtensorMap &mapA, const CUtensorMap &mapB, const PreselParams &p, bool bf16, bool split,
+int launch_presel(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p, bool bf16, bool split,
                   int n_sms, cudaStream_t st);
 void launch_presel_finish(int64_t n, int D, int n_phi, double delta, const unsigned long long *keys, float *ml,
                           int *arg_ot, double *inco, unsigned long long *max_bits /*zeroed*/, int64_t *sel,

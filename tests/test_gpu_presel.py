@@ -206,7 +206,7 @@ def test_invalid_requests_are_rejected(dpx):
         with pytest.raises(dp.DotpeError) as ei:
             dp.dotpe_preselect(ctx, nopol, 0, 256, wl.event.psd, wl.event.data, ps.t_grid)
         assert ei.value.status == dp.DOTPE_E_INVALID and "pol" in str(ei.value)
-        for kw in (dict(n_phi=65), dict(precision="fp32"), dict(precision="mixed"), dict(delta=-1.0)):
+        for kw in (dict(n_phi=33), dict(precision="fp32"), dict(precision="mixed"), dict(delta=-1.0)):
             with pytest.raises(dp.DotpeError) as ei:
                 dp.dotpe_preselect(ctx, bid, 0, 256, wl.event.psd, wl.event.data, ps.t_grid, **kw)
             assert ei.value.status == dp.DOTPE_E_INVALID
