@@ -16,7 +16,7 @@ reduction.  The K timed events are submitted together; the runtime runs up to
 four at once.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload event|batch64|serve]
+                  [--workload event|batch64|serve|presel]
 
 --workload batch64: 64 events (extrinsic counts from {512, ..., 4096}, 2-3
 detectors, SNR 8-40) over one shared 262,144-row bank, submitted as one batch:
@@ -25,7 +25,10 @@ is one batch.  --workload serve: a Poisson stream of events (default 2,000 at
 20 per second) with bank slices of 16K-512K rows of a resident 512K bank per
 bin grid (B = 256 or 512), 1K-8K extrinsic samples, 2-3 detectors, SNR 8-50,
 admitted by HBM footprint with continuous batching; reports throughput and
-p50/p99 event latency.
+p50/p99 event latency.  --workload presel: the incoherent single-detector
+pre-selection (Sec. IV.D, App. B) of the same 65,536-row bank at the scale of
+the paper's Table flops (3 detectors, 4 modes, 512 bins, N_t = 128 arrival
+times, N_phi = 32), split fp16 by default; a step is one dotpe_preselect call.
 
 Under torchrun (N > 1) every rank runs its own independent events on its own
 GPU (events do not share data: weak scaling, no collective on the data path);
@@ -339,6 +342,96 @@ def bench_batch64(args, dp, ctx_factory, torch, dev, load_peaks_fn):
     return line
 
 
+def presel_cpu_baseline(wl, ps, target_s=12.0):
+    """The FP64 oracle's pre-selection on a bounded random sample of the bank's
+    rows (every detector, time and phase of each sampled row), all host cores."""
+    import oracle
+    cores = oracle.default_threads()
+    rng = np.random.default_rng(2468)
+    I = wl.bank.h.shape[0]
+
+    def run(n):
+        rows = np.sort(rng.choice(I, size=n, replace=False))
+        P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h[rows], ps.pol[rows],
+                                 wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI)
+        t0 = time.perf_counter()
+        P.run(n_threads=cores)
+        return time.perf_counter() - t0
+
+    n0 = max(16, 2 * cores)
+    rate = n0 / run(n0)
+    n = int(min(I, max(n0, rate * target_s)))
+    dt = run(n)
+    return {"value": n / dt, "unit": "bank rows/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} uniform random bank rows (seed 2468), all 3 detectors x 128 times x "
+                      f"{N_PHI} phases each, Eqs. dh_itop / single_det_ML in FP64, {dt:.1f} s"}
+
+
+def bench_presel(args, dp, ctx_factory, torch, dev):
+    """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of one event
+    over the whole 65,536-row bank; a step is one dotpe_preselect call."""
+    import synth
+    wl = synth.make_workload(**dict(WORKLOAD, n_int=args.n_int), n_phi=N_PHI)
+    ps = synth.make_presel_inputs(wl)
+    I, D, M, B = args.n_int, WORKLOAD["n_det"], WORKLOAD["n_modes"], WORKLOAD["n_bins"]
+    NT = ps.t_grid.shape[1]
+    prec = args.precision if args.precision != "mixed" else "fp16x3"
+    ctx = ctx_factory()
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w, pol=ps.pol)
+
+    def call():
+        return dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI,
+                                  delta=CUT_DELTA, precision=prec, outputs=("lnl_inco", "selected"))
+
+    for _ in range(args.warmup):
+        call()
+    sampler = ClockSampler(dev.index or 0)
+    torch.cuda.synchronize()
+    sampler.start()
+    dev_ms, ker_ms = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = call()
+        dev_ms.append(r["device_ms"])
+        ker_ms.append(r["kernel_ms"])
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    # useful work: the per-mode complex GEMM of Eq. dh_itop, one pass (8 B flops per
+    # (i, k, m, t)); the split precision issues three passes
+    flops = 8.0 * I * M * D * NT * B
+    kern = statistics.median(ker_ms)
+    burst, sustained, hbm, peak_src = load_peaks()
+    achieved = flops / (kern * 1e-3) / 1e12
+    evals = I * D * NT * N_PHI
+    dms = sum(dev_ms)
+    cpu = None if args.no_cpu_baseline else presel_cpu_baseline(wl, ps)
+    line = {
+        "metric": "pre-selected bank rows/s", "value": I * args.steps / (dms * 1e-3), "unit": "rows/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if prec.startswith("bf16") else "fp16", "data": "synthetic",
+        "config": {"workload": f"incoherent pre-selection of one event: I={I} bank rows, D={D}, M={M}, B={B}, "
+                               f"N_t={NT} (0.5 ms grid), N_phi={N_PHI}, window {CUT_DELTA:g}",
+                   "precision": prec,
+                   "l2": f"inputs larger than L2 (bank operand planes {I * M * 2 * B * 2 * 2 / 1e9:.2f} GB per call)",
+                   "evaluations_per_s": evals * args.steps / (dms * 1e-3), "kept_rows": r["n_selected"],
+                   "kernel_ms": kern, "device_ms_per_call": dms / args.steps},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
+                     "frac": achieved / sustained, "traffic": None,
+                     "kernel": "presel_kernel (per-mode <d|h> GEMM against the time grid + 2x2 ML epilogue)",
+                     "kernel_ms": kern, "flops_per_call": flops,
+                     "issued_tflops": achieved * (3 if prec.endswith("x3") else 1),
+                     "peak_source": f"{peak_src} bf16_tflops_sustained"},
+        "e2e": {"value": I * args.steps / wall, "unit": "rows/s",
+                "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + ps.t_grid.nbytes),
+                "d2h_bytes_per_step": int(8 * I + 8 * r["n_selected"] + 64)},
+        "gpu_launches": 6 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
+    }
+    dp.dotpe_bank_release(ctx, bid)
+    dp.dotpe_destroy(ctx)
+    return line
+
+
 def bench_serve(args, dp, ctx_factory, torch, dev):
     """Poisson arrivals against resident banks; continuous batching at admission."""
     import synth
@@ -423,7 +516,7 @@ def main():
     ap.add_argument("--events", type=int, default=4, help="distinct event realisations cycled")
     ap.add_argument("--n-int", type=int, default=WORKLOAD["n_int"], help="bank rows (profiling runs)")
     ap.add_argument("--n-ext", type=int, default=WORKLOAD["n_ext"], help="extrinsic samples (profiling runs)")
-    ap.add_argument("--workload", default="event", choices=["event", "batch64", "serve"])
+    ap.add_argument("--workload", default="event", choices=["event", "batch64", "serve", "presel"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
     args = ap.parse_args()
@@ -455,6 +548,8 @@ def main():
         dev = torch.device("cuda", local)
         if args.workload == "batch64":
             line = bench_batch64(args, dp, lambda: dp.dotpe_create(local), torch, dev, load_peaks)
+        elif args.workload == "presel":
+            line = bench_presel(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         else:
             line = bench_serve(args, dp, lambda: dp.dotpe_create(local, max_batch=args.max_batch), torch, dev)
         print(json.dumps(line), flush=True)

@@ -155,11 +155,12 @@ __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const floa
 
 // The warp's 16 rows of one tile for the thread's column t (Re or Im part):
 // mode components from TMEM (the buffer is released after the last read),
-// parts swapped with the partner lane, Y = K Z, the best tagged ln L^ML over
-// the thread's phases, the warp maximum over its 16 times, one atomic per row.
+// parts swapped with the partner lane, Y = K Z (the accumulator scale is in
+// the [hh]^+ table), the best tagged ln L^ML over the thread's phases, the
+// warp maximum over its 16 times, one atomic per row.
 template <int NE, bool PAIR>
 __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T, uint32_t tbase, int rb, int j_first,
-                                          int k, int t, int part, int lane, float zs, uint64_t *tempty) {
+                                          int k, int t, int part, int lane, uint64_t *tempty) {
   const int M = P.n_modes;
   const bool tv = t < P.n_t;
 #pragma unroll 1
@@ -190,8 +191,8 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
       for (int s = 0; s < MAXM; ++s) {
         const float own = z[s][jj];
         const float other = __shfl_xor_sync(0xffffffffu, own, 1);
-        zr[s] = (part ? other : own) * zs;
-        zi[s] = (part ? own : other) * zs;
+        zr[s] = part ? other : own;
+        zi[s] = part ? own : other;
       }
       if (i >= P.n_rows) continue;  // warp-uniform
       float yr[MAXM][2], yi[MAXM][2];
@@ -205,20 +206,19 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
         yi[s][1] = kv.z * zi[s] + kv.w * zr[s];
       }
       const float best = row_best<NE, PAIR>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi, part);
-      // (tagged ln L^ML, time) -> key; the warp's maximum over its 16 times
-      unsigned long long key = 0;
-      if (tv && best >= -0.5f) {
-        const float v = fmaxf(best, 0.f);
-        const uint32_t o = 63u - (uint32_t)(__float_as_int(best) & 63);
-        key = ((unsigned long long)__float_as_uint(v) << 32) |
-              (unsigned long long)(0xffffffffu - (uint32_t)(t * P.n_phi + (int)o));
-      }
+      // the warp's maximum over its 16 times: tagged values are distinct between
+      // partner lanes, so the lowest lane holding the maximum has the lowest time
+      float m = tv ? best : -1.f;
 #pragma unroll
-      for (int sh = 16; sh > 0; sh >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, sh);
-        key = y > key ? y : key;
+      for (int sh = 16; sh > 0; sh >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, sh));
+      const unsigned hit = __ballot_sync(0xffffffffu, tv && best == m);
+      if (lane == 0 && m >= -0.5f && hit) {
+        const int t_hit = t + ((__ffs(hit) - 1) >> 1);  // lane 0's time + half the lane offset
+        const uint32_t o = 63u - (uint32_t)(__float_as_int(m) & 63);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(fmaxf(m, 0.f)) << 32) |
+                                       (unsigned long long)(0xffffffffu - (uint32_t)(t_hit * P.n_phi + (int)o));
+        atomicMax(P.keys + i * P.n_det + k, key);
       }
-      if (lane == 0 && key != 0) atomicMax(P.keys + i * P.n_det + k, key);
     }
   }
 }
@@ -358,6 +358,7 @@ __global__ void __launch_bounds__(QNT, 1)
     const int L = quad * 32 + lane;        // TMEM lane = A row
     const int part = L & 1;                // 0: Re row, 1: Im row
     const float zs = P.z_scale / (P.g_scale ? *P.g_scale : 1.f);
+    const float zs2 = zs * zs;
     const bool pair = (P.n_phi & 3) == 0;
     uint32_t u = 0;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
@@ -437,7 +438,8 @@ __global__ void __launch_bounds__(QNT, 1)
               const float inv = 0.5f / (sm * sm);
               a = A * inv; bb = B * inv; c = C * inv;
             }
-            T.hs[j * PS_MAXPHI + o] = make_float4(a, 2.f * bb, c, 0.f);
+            // the accumulators' scale enters ln L^ML squared: fold it into the table
+            T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, 0.f);
           }
         }
       }
@@ -449,12 +451,12 @@ __global__ void __launch_bounds__(QNT, 1)
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * Q_BUF_COLS;
       const int j0 = sub * QJW;
       switch ((pair ? 8 : 0) + (pair ? P.n_even : 2)) {
-        case 8: tile_rows<0, true>(P, T, tbase, rb, j0, k, t, part, lane, zs, &T.tempty[b]); break;
-        case 9: tile_rows<1, true>(P, T, tbase, rb, j0, k, t, part, lane, zs, &T.tempty[b]); break;
-        case 10: tile_rows<2, true>(P, T, tbase, rb, j0, k, t, part, lane, zs, &T.tempty[b]); break;
-        case 11: tile_rows<3, true>(P, T, tbase, rb, j0, k, t, part, lane, zs, &T.tempty[b]); break;
-        case 12: tile_rows<4, true>(P, T, tbase, rb, j0, k, t, part, lane, zs, &T.tempty[b]); break;
-        default: tile_rows<2, false>(P, T, tbase, rb, j0, k, t, part, lane, zs, &T.tempty[b]); break;
+        case 8: tile_rows<0, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 9: tile_rows<1, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 10: tile_rows<2, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 11: tile_rows<3, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 12: tile_rows<4, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        default: tile_rows<2, false>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
       }
     }
   }
