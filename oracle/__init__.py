@@ -42,7 +42,8 @@ class Problem(ctypes.Structure):
                 ("t", ctypes.POINTER(ctypes.c_double)),
                 ("ln_w_int", ctypes.POINTER(ctypes.c_double)),
                 ("ln_w_ext", ctypes.POINTER(ctypes.c_double)),
-                ("u_min", ctypes.c_double)]
+                ("u_min", ctypes.c_double),
+                ("rb_dh", ctypes.POINTER(ctypes.c_double)), ("rb_hh", ctypes.POINTER(ctypes.c_double))]
 
 
 PAIR_DTYPE = np.dtype([("lnl_marg", "f8"), ("lnl_sq", "f8"), ("lnl_ml_max", "f8"),
@@ -73,7 +74,8 @@ def lib():
             L.or_quad_ml.argtypes = [ctypes.c_double] * 5
             for name in ("or_data_weights", "or_direct_phases", "or_mode_components",
                          "or_rotate_phases", "or_eval_pairs", "or_eval_grid",
-                         "or_direct_grid_ml", "or_evidence", "or_presel_grid", "or_presel"):
+                         "or_direct_grid_ml", "or_evidence", "or_presel_grid", "or_presel",
+                         "or_rb_weights"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
         return _lib
@@ -91,7 +93,8 @@ def _c128(a):
 class OracleProblem:
     """Holds contiguous FP64 copies of one workload and the ctypes struct."""
 
-    def __init__(self, bank, ext, event, i_slice=None):
+    def __init__(self, bank, ext, event, i_slice=None, rb=None):
+        """rb: optional (w_dh [D, M, B], w_hh [D, M, M, B]) relative-binning weights (App. A)."""
         h = bank.h if i_slice is None else bank.h[i_slice]
         lw_i = bank.ln_w if i_slice is None else bank.ln_w[i_slice]
         self.mode_m = np.ascontiguousarray(bank.mode_m, dtype=np.int32)
@@ -109,11 +112,16 @@ class OracleProblem:
         self.shape = (I, E, D, M, B)
         self.n_phi = int(event.n_phi)
         self.u_min = float(event.u_min)
+        self.rb = None if rb is None else (_c128(rb[0]), _c128(rb[1]))
+        if self.rb is not None:
+            assert self.rb[0].shape == (D, M, B) and self.rb[1].shape == (D, M, M, B)
         self.s = Problem(I, E, D, M, B, self.n_phi,
                          self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          _dp(self.f), _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),
                          _dp(self.h.view(np.float64)), _dp(self.R.view(np.float64)), _dp(self.t),
-                         _dp(self.ln_w_int), _dp(self.ln_w_ext), self.u_min)
+                         _dp(self.ln_w_int), _dp(self.ln_w_ext), self.u_min,
+                         None if rb is None else _dp(self.rb[0].view(np.float64)),
+                         None if rb is None else _dp(self.rb[1].view(np.float64)))
 
     # -- components -------------------------------------------------------
     def data_weights(self):
@@ -203,14 +211,15 @@ class PreselStruct(ctypes.Structure):
                 ("f", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
                 ("psd", ctypes.POINTER(ctypes.c_double)), ("data", ctypes.POINTER(ctypes.c_double)),
                 ("h", ctypes.POINTER(ctypes.c_double)), ("pol", ctypes.POINTER(ctypes.c_double)),
-                ("t_grid", ctypes.POINTER(ctypes.c_double))]
+                ("t_grid", ctypes.POINTER(ctypes.c_double)),
+                ("rb_dh", ctypes.POINTER(ctypes.c_double)), ("rb_hh", ctypes.POINTER(ctypes.c_double))]
 
 
 class PreselProblem:
     """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of one event
     over bank rows: h [I, M, B], pol [I, M, 2] (K_{imp}, p = +, x), t_grid [D, n_t]."""
 
-    def __init__(self, f, w, mode_m, h, pol, psd, data, t_grid, n_phi=32):
+    def __init__(self, f, w, mode_m, h, pol, psd, data, t_grid, n_phi=32, rb=None):
         self.mode_m = np.ascontiguousarray(mode_m, dtype=np.int32)
         self.f = np.ascontiguousarray(f, dtype=np.float64)
         self.w = np.ascontiguousarray(w, dtype=np.float64)
@@ -224,11 +233,14 @@ class PreselProblem:
         assert self.pol.shape == (I, M, 2) and self.psd.shape == (D, B) and self.data.shape == (D, B)
         self.shape = (I, D, M, B, NT)
         self.n_phi = int(n_phi)
+        self.rb = None if rb is None else (_c128(rb[0]), _c128(rb[1]))
         self.s = PreselStruct(I, D, M, B, NT, self.n_phi,
                               self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                               _dp(self.f), _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),
                               _dp(self.h.view(np.float64)), _dp(self.pol.view(np.float64)),
-                              _dp(self.t_grid))
+                              _dp(self.t_grid),
+                              None if rb is None else _dp(self.rb[0].view(np.float64)),
+                              None if rb is None else _dp(self.rb[1].view(np.float64)))
 
     def grid(self, i, k):
         """ln L^ML_{i k o t} [n_phi, n_t] (Eq. single_det_ML)."""
@@ -254,6 +266,30 @@ class PreselProblem:
             raise MemoryError("or_presel")
         return dict(ml=ml, arg_ot=arg, lnl_inco=inco, keep=keep.astype(bool), threshold=thr.value,
                     arg_i=int(ai.value))
+
+
+def rb_weights(f_fine, dff, psd, data, h0, nodes, t0=None):
+    """Relative-binning weights (App. A, Eqs. dh_weights, hh_weights) with hat
+    functions on the nodes f_fine[nodes], for the reference modes h0 [M, N]
+    arriving at detector d at t0[d]: returns (w_dh [D, M, B], w_hh [D, M, M, B])."""
+    f_fine = np.ascontiguousarray(f_fine, dtype=np.float64)
+    dff = np.ascontiguousarray(dff, dtype=np.float64)
+    psd = np.ascontiguousarray(psd, dtype=np.float64)
+    data = _c128(data)
+    h0 = _c128(h0)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    D, N = psd.shape
+    M = h0.shape[0]
+    B = nodes.shape[0]
+    w_dh = np.zeros((D, M, B), np.complex128)
+    w_hh = np.zeros((D, M, M, B), np.complex128)
+    t0 = None if t0 is None else np.ascontiguousarray(t0, dtype=np.float64)
+    if lib().or_rb_weights(D, M, ctypes.c_int64(N), _dp(f_fine), _dp(dff), _dp(psd), _dp(data.view(np.float64)),
+                           _dp(h0.view(np.float64)), None if t0 is None else _dp(t0), B,
+                           nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           _dp(w_dh.view(np.float64)), _dp(w_hh.view(np.float64))):
+        raise ValueError("reference waveform vanishes at a node")
+    return w_dh, w_hh
 
 
 def quad_ml(dh_p, dh_x, a, b, c):

@@ -62,6 +62,60 @@ static cplx grid_phase(int k, int o, int n_phi) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Relative-binning weights (App. A, Eqs. dh_weights, hh_weights)            */
+/* ------------------------------------------------------------------------ */
+/* hat function of node b at fine frequency f (nodes fn[0..B-1]) */
+static double hat(const double *fn, int B, int b, double f) {
+  if (b > 0 && f >= fn[b - 1] && f <= fn[b]) return (f - fn[b - 1]) / (fn[b] - fn[b - 1]);
+  if (b < B - 1 && f >= fn[b] && f <= fn[b + 1]) return (fn[b + 1] - f) / (fn[b + 1] - fn[b]);
+  return f == fn[b] ? 1.0 : 0.0;
+}
+
+int or_rb_weights(int D, int M, int64_t n_fine, const double *ff, const double *dff, const double *psd,
+                  const double *data, const double *h0, const double *t0, int B, const int64_t *node,
+                  double *w_dh, double *w_hh) {
+  double *fn = malloc(sizeof(double) * (size_t)B);
+  if (!fn) return -1;
+  for (int b = 0; b < B; ++b) fn[b] = ff[node[b]];
+  for (int m = 0; m < M; ++m)
+    for (int b = 0; b < B; ++b)
+      if (cabs(ld_c(h0, (int64_t)m * n_fine + node[b])) == 0.0) {
+        free(fn);
+        return -1;
+      }
+  for (int d = 0; d < D; ++d) {
+    const double td = t0 ? t0[d] : 0.0;
+    for (int b = 0; b < B; ++b) {
+      /* the support of s_b: fine points from node b-1 to node b+1 */
+      const int64_t n0 = node[b > 0 ? b - 1 : 0], n1 = node[b < B - 1 ? b + 1 : B - 1];
+      const cplx Tb = cexp(-I * TWO_PI * fn[b] * td);
+      for (int m = 0; m < M; ++m) {
+        const cplx h0b = ld_c(h0, (int64_t)m * n_fine + node[b]) * Tb; /* h0_dm(f_b) */
+        cplx acc = 0.0;
+        for (int64_t n = n0; n <= n1; ++n) {
+          const cplx h0n = ld_c(h0, (int64_t)m * n_fine + n) * cexp(-I * TWO_PI * ff[n] * td);
+          acc += 4.0 * dff[n] * ld_c(data, (int64_t)d * n_fine + n) * conj(h0n) * hat(fn, B, b, ff[n]) /
+                 psd[(int64_t)d * n_fine + n];
+        }
+        st_c(w_dh, ((int64_t)d * M + m) * B + b, acc / conj(h0b));
+        for (int mp = 0; mp < M; ++mp) {
+          const cplx h0pb = ld_c(h0, (int64_t)mp * n_fine + node[b]) * Tb;
+          cplx a2 = 0.0;
+          for (int64_t n = n0; n <= n1; ++n) {
+            const cplx T = cexp(-I * TWO_PI * ff[n] * td);
+            a2 += 4.0 * dff[n] * ld_c(h0, (int64_t)m * n_fine + n) * T * conj(ld_c(h0, (int64_t)mp * n_fine + n) * T) *
+                  hat(fn, B, b, ff[n]) / psd[(int64_t)d * n_fine + n];
+          }
+          st_c(w_hh, (((int64_t)d * M + m) * M + mp) * B + b, a2 / (h0b * conj(h0pb)));
+        }
+      }
+    }
+  }
+  free(fn);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Route O1: plain definition per (i, e, o)                                  */
 /* ------------------------------------------------------------------------ */
 int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, double *hh_out) {
@@ -95,18 +149,28 @@ int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, 
 /* ------------------------------------------------------------------------ */
 /* Route O2: per-mode components, then phase rotation                        */
 /* ------------------------------------------------------------------------ */
-/* <h_{i m}|h_{i m'}>_d = sum_b omega_{d b} h_m h_{m'}^*  -> hm[d][M][M] */
+/* <h_{i m}|h_{i m'}>_d = sum_b omega_{d b} h_m h_{m'}^*  -> hm[d][M][M]
+ * (relative binning: the weight of each mode pair, Eq. h_h) */
 static void mode_overlaps(const or_problem *p, const double *omega, int64_t i, cplx *hm) {
   const int M = p->n_modes, D = p->n_det, B = p->n_bins;
   for (int d = 0; d < D; ++d)
     for (int m = 0; m < M; ++m)
       for (int mp = 0; mp < M; ++mp) {
         cplx acc = 0.0;
-        for (int b = 0; b < B; ++b)
-          acc += omega[(int64_t)d * B + b] * ld_c(p->h, (i * M + m) * B + b) *
-                 conj(ld_c(p->h, (i * M + mp) * B + b));
+        for (int b = 0; b < B; ++b) {
+          cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)d * M + m) * M + mp) * B + b)
+                              : (cplx)omega[(int64_t)d * B + b];
+          acc += wgt * ld_c(p->h, (i * M + m) * B + b) * conj(ld_c(p->h, (i * M + mp) * B + b));
+        }
         hm[(d * M + m) * M + mp] = acc;
       }
+}
+
+/* Data weight of mode m at bin b: c_{d b} = 4 w_b conj(d) / S (plain quadrature), or
+ * (W^{<d|h>}_{d m b})^* with relative binning (Eq. d_h: Re<d|h> = Re sum_b c h). */
+static cplx data_weight(const or_problem *p, const double *c, int d, int m, int b) {
+  if (p->rb_dh) return conj(ld_c(p->rb_dh, ((int64_t)d * p->n_modes + m) * p->n_bins + b));
+  return ld_c(c, (int64_t)d * p->n_bins + b);
 }
 
 static void mode_components_cached(const or_problem *p, const double *c, const cplx *hm,
@@ -120,8 +184,7 @@ static void mode_components_cached(const or_problem *p, const double *c, const c
     for (int m = 0; m < M; ++m) {
       cplx acc = 0.0;
       for (int b = 0; b < B; ++b)
-        acc += ld_c(c, (int64_t)d * B + b) * cexp(-I * TWO_PI * p->f[b] * t) *
-               ld_c(p->h, (i * M + m) * B + b);
+        acc += data_weight(p, c, d, m, b) * cexp(-I * TWO_PI * p->f[b] * t) * ld_c(p->h, (i * M + m) * B + b);
       z[m] += ld_c(p->R, (e * D + d) * M + m) * acc;
     }
     for (int m = 0; m < M; ++m)
@@ -585,20 +648,24 @@ double or_quad_ml(double dp, double dx, double a, double b, double c) {
   return 0.5 * (a * dp * dp + 2.0 * b * dp * dx + c * dx * dx) / (s * s);
 }
 
-/* W_{t b} = c_{k b} T_{t k b} = 4 w_b d_k^*(f_b) / S_k(f_b) e^{-2 pi i f_b t_{k t}} of one
- * detector: [n_t][B] (Eq. dh_itop without the waveform). */
+/* W_{m t b} = c_{k m b} T_{t k b} of one detector: [M][n_t][B] (Eq. dh_itop without the
+ * waveform), c_{k m b} = 4 w_b d_k^*(f_b) / S_k(f_b), or (W^{<d|h>}_{k m b})^* with
+ * relative binning (App. A; the polarisation factors cancel in Eq. dh_weights for a
+ * reference waveform h0_{mp} = K_{mp} h0_m). */
 static cplx *presel_weights(const or_presel_problem *p, int k) {
-  const int B = p->n_bins, NT = p->n_t;
+  const int B = p->n_bins, NT = p->n_t, M = p->n_modes;
   const int64_t kb = (int64_t)k * B;
-  cplx *W = malloc(sizeof(cplx) * (size_t)NT * B);
+  cplx *W = malloc(sizeof(cplx) * (size_t)M * NT * B);
   if (!W) return NULL;
-  for (int t = 0; t < NT; ++t) {
-    double tt = p->t_grid[(int64_t)k * NT + t];
-    for (int b = 0; b < B; ++b) {
-      double om = 4.0 * p->w[b] / p->psd[kb + b];
-      W[(int64_t)t * B + b] = om * conj(ld_c(p->data, kb + b)) * cexp(-I * TWO_PI * p->f[b] * tt);
+  for (int m = 0; m < M; ++m)
+    for (int t = 0; t < NT; ++t) {
+      double tt = p->t_grid[(int64_t)k * NT + t];
+      for (int b = 0; b < B; ++b) {
+        cplx c = p->rb_dh ? conj(ld_c(p->rb_dh, ((int64_t)k * M + m) * B + b))
+                          : (4.0 * p->w[b] / p->psd[kb + b]) * conj(ld_c(p->data, kb + b));
+        W[((int64_t)m * NT + t) * B + b] = c * cexp(-I * TWO_PI * p->f[b] * tt);
+      }
     }
-  }
   return W;
 }
 
@@ -625,8 +692,9 @@ static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, i
       for (int mp = 0; mp < M; ++mp) {
         cplx s = 0.0;
         for (int b = 0; b < B; ++b) {
-          double om = 4.0 * p->w[b] / p->psd[kb + b];
-          s += om * hp[((int64_t)pq[r][0] * M + m) * B + b] * conj(hp[((int64_t)pq[r][1] * M + mp) * B + b]);
+          cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)k * M + m) * M + mp) * B + b)
+                              : (cplx)(4.0 * p->w[b] / p->psd[kb + b]);
+          s += wgt * hp[((int64_t)pq[r][0] * M + m) * B + b] * conj(hp[((int64_t)pq[r][1] * M + mp) * B + b]);
         }
         ov[(r * M + m) * M + mp] = s;
       }
@@ -643,7 +711,7 @@ static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, i
     for (int q = 0; q < 2; ++q)
       for (int m = 0; m < M; ++m) {
         cplx acc = 0.0;
-        for (int b = 0; b < B; ++b) acc += W[(int64_t)t * B + b] * hp[((int64_t)q * M + m) * B + b];
+        for (int b = 0; b < B; ++b) acc += W[((int64_t)m * NT + t) * B + b] * hp[((int64_t)q * M + m) * B + b];
         z[q * M + m] = acc;
       }
     for (int o = 0; o < NP; ++o) {

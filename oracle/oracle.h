@@ -34,6 +34,12 @@ typedef struct or_problem {
   const double *t;                   /* [E][D] */
   const double *ln_w_int, *ln_w_ext; /* [I], [E] (may be NULL: zeros) */
   double u_min;                      /* d_L^0 / d_max of pi(d_L) ~ d_L^2 */
+  /* relative binning (App. A), both or neither (NULL: plain quadrature with w):
+   * rb_dh complex [D][M][B] = W^{<d|h>}_{d m b}, rb_hh complex [D][M][M][B] =
+   * W^{<h|h>}_{d m m' b}; then <d|h_m>_d = sum_b W^{<d|h>}_{d m b} h_m^*(f_b) and
+   * <h_m|h_m'>_d = sum_b W^{<h|h>}_{d m m' b} h_m(f_b) h_m'^*(f_b) (Eqs. d_h, h_h).
+   * Route O2 only (the weights are per mode). */
+  const double *rb_dh, *rb_hh;
 } or_problem;
 
 /* Per-(i,e) outputs. */
@@ -57,6 +63,23 @@ typedef struct or_evidence_out {
  *   c_{d,b} = 4 w_b conj(d_d(f_b)) / S_d(f_b),  omega_{d,b} = 4 w_b / S_d(f_b). */
 int or_data_weights(int D, int B, const double *w, const double *psd, const double *data,
                     double *c_out, double *omega_out);
+
+/* Relative-binning weights (App. A, Eqs. dh_weights, hh_weights) on a fine
+ * frequency grid ff[n] (increasing) with quadrature weights dff[n]:
+ *   <a|b>_d = sum_n 4 dff_n a(f_n) b^*(f_n) / S_d(f_n),
+ *   W^{<d|h>}_{d m b}    = <d_d | h0_dm s_b>_d / h0_dm^*(f_b)
+ *   W^{<h|h>}_{d m m' b} = <h0_dm | h0_dm' s_b>_d / (h0_dm(f_b) h0_dm'^*(f_b))
+ * with h0_dm(f) = h0_m(f) e^{-2 pi i f t0_d}, the reference waveform's modes
+ * arriving at detector d at t0_d (constant factors such as the response
+ * cancel in the ratios; the time shift does not), and s_b the piecewise-linear
+ * hat functions on the nodes f_b = ff[node[b]] (s_b(f_b') = delta_bb',
+ * supported on [f_{b-1}, f_{b+1}]; fine points outside [f_0, f_{B-1}] do not
+ * enter).  psd, data: [D][n]; h0: complex [M][n]; t0: [D] (NULL: 0);
+ * node: [B] increasing fine-grid indices.  w_dh: complex [D][M][B];
+ * w_hh: complex [D][M][M][B].  Returns -1 if some |h0_m(f_b)| is 0. */
+int or_rb_weights(int D, int M, int64_t n_fine, const double *ff, const double *dff, const double *psd,
+                  const double *data, const double *h0, const double *t0, int B, const int64_t *node,
+                  double *w_dh, double *w_hh);
 
 /* Route O1 (plain definition): for one (i, e) build the detector strain of
  * Eq. h_k at d_L = d_L^0 and phase phi_o = 2 pi o / n_phi, then evaluate
@@ -127,6 +150,7 @@ typedef struct or_presel {
   const double *h;                   /* complex [I][M][B] */
   const double *pol;                 /* complex [I][M][2]: K_{i m +}, K_{i m x} */
   const double *t_grid;              /* [D][n_t] arrival times at detector k (s) */
+  const double *rb_dh, *rb_hh;       /* relative binning as in or_problem, or NULL */
 } or_presel_problem;
 
 /* Eqs. x_ML, single_det_ML: max over real (x_+, x_x) of

@@ -465,6 +465,113 @@ def make_presel_inputs(wl: "Workload", n_t=128, dt=5.0e-4, seed=7):
                         t_grid=np.tile(t, (D, 1)))
 
 
+# ----------------------------------------------------------------------------
+# relative binning (App. A): full-resolution data, a reference waveform, a bank
+# stored on coarse nodes of the fine grid
+# ----------------------------------------------------------------------------
+def waveform_modes(f, mc, ratios, mode_m, amp22):
+    """The bank's waveform model (module doc) for rows (mc [n], ratios [n, M],
+    amp22 [n]) on any frequencies f: complex [n, M, len(f)]."""
+    mc = np.atleast_1d(np.asarray(mc, dtype=np.float64))
+    x = np.pi * GM_SUN_S * mc[:, None] * f[None, :]
+    psi22 = -0.25 * np.pi + (3.0 / 128.0) * x ** (-5.0 / 3.0)
+    base = f ** (-7.0 / 6.0)
+    out = np.empty((mc.shape[0], len(mode_m), f.shape[0]), dtype=np.complex128)
+    for k, m in enumerate(mode_m):
+        out[:, k, :] = (amp22 * ratios[:, k])[:, None] * base[None, :] * np.exp(1j * (0.5 * m) * psi22)
+    return out
+
+
+@dataclasses.dataclass
+class RBWorkload:
+    bank: Bank             # rows on the coarse nodes f_fine[nodes]; row 0 is the reference
+    ext: Extrinsic
+    event: Event           # psd and data sampled at the nodes (plain quadrature on the same bins)
+    f_fine: np.ndarray     # [N] uniform grid (Hz)
+    dff: np.ndarray        # [N] trapezoid weights (Hz)
+    psd_fine: np.ndarray   # [D, N]
+    data_fine: np.ndarray  # [D, N] complex
+    h0_fine: np.ndarray    # [M, N] complex: the reference waveform's modes
+    t0: np.ndarray         # [D] the reference's arrival time at each detector (s)
+    nodes: np.ndarray      # [B] increasing indices into f_fine
+    ratios: np.ndarray     # [I, M] mode amplitude ratios of the rows
+    amp22: np.ndarray      # [I] 22-mode amplitude scale of the rows
+
+    def rows_fine(self, rows):
+        """The bank rows' modes on the fine grid: complex [len(rows), M, N]."""
+        rows = np.atleast_1d(rows)
+        return waveform_modes(self.f_fine, self.bank.mchirp[rows], self.ratios[rows], self.bank.mode_m,
+                              self.amp22[rows])
+
+
+def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.0, seed=0, mc0=12.0,
+                     spread=0.02, n_phi=32, noise=True, sky_sigma=0.05, t_sigma=5e-4, fmin=20.0, fmax=1024.0):
+    """Full-resolution event and a bank stored on coarse nodes (App. A).
+
+    The fine grid is uniform over [fmin, fmax] with n_fine points; the nodes are
+    the fine points nearest to n_bins log-spaced frequencies.  The reference
+    waveform (row 0 of the bank, chirp mass mc0, mode ratios in [0.05, 0.3]) is
+    also the injection; the other rows have chirp masses within +-spread of
+    mc0 (a bank around the signal, as the pre-selection leaves it) and mode
+    ratios U[0, 0.3].  Extrinsic samples concentrate near the injection (sky
+    offsets N(0, sky_sigma) rad, arrival offsets N(0, t_sigma) s, psi and
+    cos(iota) from the prior), like the output of an adaptive extrinsic
+    sampler, so that the time shifts relative to the reference stay small.
+    The reference's arrival times t0 are the injection's.
+    """
+    rng = np.random.default_rng(seed)
+    f_fine = np.linspace(fmin, fmax, n_fine)
+    dff = np.full(n_fine, f_fine[1] - f_fine[0])
+    dff[0] *= 0.5
+    dff[-1] *= 0.5
+    target = fmin * (fmax / fmin) ** (np.arange(n_bins) / (n_bins - 1))
+    nodes = np.unique(np.clip(np.rint((target - fmin) / (f_fine[1] - f_fine[0])).astype(np.int64), 0, n_fine - 1))
+    if nodes.shape[0] != n_bins:
+        raise ValueError("fine grid too coarse for the requested nodes")
+    fb = f_fine[nodes]
+    lm = MODE_SETS[n_modes]
+    mode_l = np.array([l for l, _ in lm], dtype=np.int32)
+    mode_m = np.array([m for _, m in lm], dtype=np.int32)
+    i22 = int(np.nonzero((mode_l == 2) & (mode_m == 2))[0][0])
+    mc = mc0 * (1.0 + rng.uniform(-spread, spread, n_int))
+    mc[0] = mc0
+    ratios = rng.uniform(0.0, 0.3, (n_int, n_modes))
+    ratios[0] = rng.uniform(0.05, 0.3, n_modes)
+    ratios[:, i22] = 1.0
+    psd_fine = np.stack([analytic_psd(f_fine, PSD_SCALES[d]) for d in range(n_det)])
+    norm = math.sqrt(np.sum(4.0 * dff * f_fine ** (-7.0 / 3.0) / psd_fine[0]))
+    amp22 = (mc / mc0) ** (5.0 / 6.0) / norm
+    h = waveform_modes(fb, mc, ratios, mode_m, amp22)
+    # coarse-grid quadrature weights for the plain comparison on the same bins
+    w = np.empty(n_bins)
+    w[0] = 0.5 * (fb[1] - fb[0])
+    w[-1] = 0.5 * (fb[-1] - fb[-2])
+    w[1:-1] = 0.5 * (fb[2:] - fb[:-2])
+    bank = Bank(f=fb, w=w, mode_m=mode_m, mode_l=mode_l, h=h, ln_w=np.zeros(n_int), mchirp=mc)
+    # injection: the reference through a prior draw at a random phase
+    e1 = make_extrinsic(rng, 1, n_det, bank)
+    phi_inj = float(rng.uniform(0.0, 2.0 * np.pi))
+    h0 = waveform_modes(f_fine, mc[:1], ratios[:1], mode_m, amp22[:1])[0]
+    unit = signal_at_detectors(h0, e1.R[0], e1.t[0], f_fine, mode_m, phi_inj, 1.0)
+    u_inj = snr / math.sqrt(float(np.sum(4.0 * dff[None, :] * np.abs(unit) ** 2 / psd_fine)))
+    data_fine = u_inj * unit
+    if noise:
+        sigma = np.sqrt(psd_fine / (4.0 * dff[None, :]))
+        data_fine = data_fine + sigma * (rng.standard_normal(sigma.shape) + 1j * rng.standard_normal(sigma.shape))
+    # extrinsic samples near the injection
+    lat = np.clip(e1.lat[0] + rng.normal(0.0, sky_sigma, n_ext), -0.5 * np.pi, 0.5 * np.pi)
+    lon = e1.lon[0] + rng.normal(0.0, sky_sigma, n_ext)
+    psi = rng.uniform(0.0, np.pi, n_ext)
+    cos_iota = rng.uniform(-1.0, 1.0, n_ext)
+    t_geo = e1.t_geo[0] + rng.normal(0.0, t_sigma, n_ext)
+    ext = extrinsic_from_params(lat, lon, psi, cos_iota, t_geo, n_det, bank, ln_w=np.zeros(n_ext))
+    ev = Event(psd=psd_fine[:, nodes].copy(), data=data_fine[:, nodes].copy(), u_min=default_u_min(bank, n_det),
+               n_phi=int(n_phi), injection=dict(i=0, e=None, phi=phi_inj, u=u_inj, snr=snr,
+                                                cos_iota=float(e1.cos_iota[0]), t_det=e1.t[0].copy()))
+    return RBWorkload(bank=bank, ext=ext, event=ev, f_fine=f_fine, dff=dff, psd_fine=psd_fine, data_fine=data_fine,
+                      h0_fine=h0, t0=e1.t[0].copy(), nodes=nodes, ratios=ratios, amp22=amp22)
+
+
 def named_workload(name: str, **overrides):
     kw = dict(WORKLOADS[name])
     kw.update(overrides)
