@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define DOTPE_ABI_VERSION 2
+#define DOTPE_ABI_VERSION 3
 
 /* ---- status codes ------------------------------------------------------ */
 #define DOTPE_OK 0
@@ -149,7 +149,15 @@ typedef struct dotpe_bank_desc {
  *   are merged into FP64 accumulators in block order.  The result does not
  *   depend on block_rows beyond FP64 rounding, except where a maximum known
  *   block by block decides what is kept: the ML cut's superset, and in MIXED
- *   precision which tiles far below the maximum are refined. */
+ *   precision which tiles far below the maximum are refined.
+ * rb_dh [n_det][n_modes][n_bins], rb_hh [n_det][n_modes][n_modes][n_bins]
+ *   (complex, host or device; both or neither): relative-binning weights
+ *   (App. A, from dotpe_rb_weights) replacing the plain quadrature: the data
+ *   weight of mode m becomes conj(W^{<d|h>}_{d m b}) and <h_m|h_m'>_d uses
+ *   W^{<h|h>}_{d m m' b}.  psd and data are then not read (may be NULL); the
+ *   cross-term cache is keyed by the <h|h> weights; the mixed-precision
+ *   screening margin takes max_m sum_{d,b} |W^{<d|h>}|^2 / W^{<h|h>}_{mm} in
+ *   place of <d|d>. */
 typedef struct dotpe_event_desc {
   uint64_t bank_id;
   int64_t i0, i1;
@@ -167,6 +175,8 @@ typedef struct dotpe_event_desc {
   int flags;
   void *stream;
   int64_t block_rows;
+  const double *rb_dh;
+  const double *rb_hh;
 } dotpe_event_desc;
 
 typedef struct dotpe_event_stats {
@@ -216,7 +226,11 @@ typedef struct dotpe_evidence_out {
  * psd [n_det][n_bins] (double) and data [n_det][n_bins] (complex): host or
  * device, as for events.  t_grid [n_det][n_t] (double, s; host or device):
  * the arrival times at each detector.  1 <= n_t <= 4096, 1 <= n_phi <= 32,
- * delta >= 0.  Synchronous: returns when every output is written. */
+ * delta >= 0.  rb_dh / rb_hh as in dotpe_event_desc (relative binning, App. A;
+ * the weights do not depend on the polarisation for a reference h0_{mp} =
+ * K_{mp} h0_m, so the per-mode weights serve both polarisations); the time
+ * grid operand is then one per mode.  Synchronous: returns when every output
+ * is written. */
 typedef struct dotpe_presel_desc {
   uint64_t bank_id;
   int64_t i0, i1;
@@ -229,6 +243,8 @@ typedef struct dotpe_presel_desc {
   double delta;
   int precision;
   int flags; /* 0 */
+  const double *rb_dh;
+  const double *rb_hh;
 } dotpe_presel_desc;
 
 typedef struct dotpe_presel_out {
@@ -240,6 +256,36 @@ typedef struct dotpe_presel_out {
   float device_ms;     /* device time of the whole call (preparation to selection) */
   int32_t device_status; /* 0, or a DOTPE_E_* raised inside a kernel */
 } dotpe_presel_out;
+
+/* Relative-binning weights (App. A, Eqs. dh_weights, hh_weights) of one
+ * event for a bank stored on coarse nodes of a fine frequency grid:
+ *   W^{<d|h>}_{d m b}    = <d_d | h0_dm s_b> / h0_dm^*(f_b)
+ *   W^{<h|h>}_{d m m' b} = <h0_dm | h0_dm' s_b> / (h0_dm(f_b) h0_dm'^*(f_b))
+ * with <a|b> = sum_n 4 df_fine[n] a(f_n) b^*(f_n) / S_d(f_n) on the fine grid,
+ * h0_dm(f) = h0_m(f) e^{-2 pi i f t0_d} (the reference waveform's modes
+ * arriving at detector d at t0_d), s_b the piecewise-linear hat function of
+ * node b (1 at f_b = f_fine[nodes[b]], 0 at the neighbouring nodes; the fine
+ * points outside [f_0, f_{B-1}] do not enter).  Then <d|h_m>_d is
+ * approximated by sum_b W^{<d|h>}_{d m b} h_m^*(f_b) and <h_m|h_m'>_d by
+ * sum_b W^{<h|h>}_{d m m' b} h_m(f_b) h_m'^*(f_b) (Eqs. d_h, h_h), which
+ * dotpe_event_desc.rb_dh / rb_hh and dotpe_presel_desc.rb_dh / rb_hh take.
+ * The bank's bins must be the node frequencies.  f_fine [n_fine] (increasing),
+ * df_fine [n_fine] (quadrature weights), psd [n_det][n_fine],
+ * data [n_det][n_fine] complex, h0 [n_modes][n_fine] complex, t0 [n_det]
+ * (may be NULL: 0), nodes [n_bins] (strictly increasing indices into
+ * f_fine): host or device.  Computed on the device in FP64. */
+typedef struct dotpe_rb_desc {
+  int n_det, n_modes;
+  int64_t n_fine;
+  const double *f_fine;
+  const double *df_fine;
+  const double *psd;
+  const double *data;
+  const double *h0;
+  const double *t0;
+  int n_bins;
+  const int64_t *nodes;
+} dotpe_rb_desc;
 
 /* ---- context ----------------------------------------------------------- */
 /* Creates a context on cfg->device (cfg may be NULL: defaults).  Allocates the
@@ -325,6 +371,15 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
 
 /* Frees an event's device state (waits for it if still running). */
 int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id);
+
+/* ---- relative binning -------------------------------------------------- */
+/* Computes the weights of dotpe_rb_desc into w_dh [n_det][n_modes][n_bins]
+ * and w_hh [n_det][n_modes][n_modes][n_bins] (complex, host or device, owned
+ * by the caller).  Synchronous; temporary device memory outside the HBM
+ * budget for the call.  Errors: E_INVALID (shapes, nodes not strictly
+ * increasing or out of range, non-finite or non-positive PSD, a reference
+ * mode that vanishes at a node), E_NOMEM, E_DEVICE. */
+int dotpe_rb_weights(dotpe_ctx *ctx, const dotpe_rb_desc *desc, double *w_dh, double *w_hh);
 
 /* ---- pre-selection ----------------------------------------------------- */
 /* Runs the pre-selection of dotpe_presel_desc on the bank's rows [i0, i1)

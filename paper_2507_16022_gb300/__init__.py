@@ -44,7 +44,7 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
            "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit",
-           "dotpe_preselect")
+           "dotpe_preselect", "dotpe_rb_weights")
 
 
 class DotpeError(RuntimeError):
@@ -75,14 +75,20 @@ class dotpe_event_desc(ctypes.Structure):
                 ("t", _dp), ("R", _dp), ("ln_w_ext", _dp), ("n_phi", ctypes.c_int),
                 ("u_min", ctypes.c_double), ("cut_delta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("block_rows", ctypes.c_int64)]
+                ("block_rows", ctypes.c_int64), ("rb_dh", _dp), ("rb_hh", _dp)]
 
 
 class dotpe_presel_desc(ctypes.Structure):
     _fields_ = [("bank_id", ctypes.c_uint64), ("i0", ctypes.c_int64), ("i1", ctypes.c_int64),
                 ("n_det", ctypes.c_int), ("psd", _dp), ("data", _dp), ("n_t", ctypes.c_int),
                 ("t_grid", _dp), ("n_phi", ctypes.c_int), ("delta", ctypes.c_double),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("rb_dh", _dp), ("rb_hh", _dp)]
+
+
+class dotpe_rb_desc(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int), ("n_modes", ctypes.c_int), ("n_fine", ctypes.c_int64),
+                ("f_fine", _dp), ("df_fine", _dp), ("psd", _dp), ("data", _dp), ("h0", _dp), ("t0", _dp),
+                ("n_bins", ctypes.c_int), ("nodes", ctypes.POINTER(ctypes.c_int64))]
 
 
 class dotpe_presel_out(ctypes.Structure):
@@ -146,6 +152,7 @@ def load(path: str = LIB_PATH):
         "dotpe_dist_marg_eval_noalloc": ([vp, ctypes.c_int64, vp, vp, ctypes.c_float, vp], ctypes.c_int),
         "dotpe_preselect": ([vp, ctypes.POINTER(dotpe_presel_desc), vp, vp, vp, vp,
                              ctypes.POINTER(dotpe_presel_out)], ctypes.c_int),
+        "dotpe_rb_weights": ([vp, ctypes.POINTER(dotpe_rb_desc), vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -242,7 +249,7 @@ def dotpe_bank_release(ctx, bank_id):
 
 
 def _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
-                cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0):
+                cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0, rb=None):
 
     def arr(a, cplx=False):
         if a is None:
@@ -254,24 +261,26 @@ def _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32,
         keep.append(a)
         return _ptr(a.view(np.float64) if cplx else a)
 
-    D, B = (psd.shape[0], psd.shape[1])
+    D = t.shape[1]
     E = t.shape[0]
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     st = None
     if stream is not None:
         st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    rbd, rbh = (None, None) if rb is None else (arr(rb[0], True), arr(rb[1], True))
     return dotpe_event_desc(bank_id, i0, i1, D, arr(psd), arr(data, True), E, arr(t), arr(R, True),
-                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st, block_rows)
+                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st, block_rows, rbd, rbh)
 
 
 def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
-                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0):
+                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0, rb=None):
     """psd [D,B], data [D,B] complex, t [E,D], R [E,D,M] complex, ln_w_ext [E]: numpy (host)
     or torch tensors (host or device; complex tensors as float64 views are accepted).
-    block_rows: 0, or a multiple of 128 to stream the slice through in bank blocks."""
+    block_rows: 0, or a multiple of 128 to stream the slice through in bank blocks.
+    rb: optional (w_dh [D,M,B], w_hh [D,M,M,B]) relative-binning weights (psd, data may be None)."""
     keep = []
     desc = _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext, n_phi, u_min, cut_delta,
-                       precision, flags, stream, block_rows)
+                       precision, flags, stream, block_rows, rb)
     eid = ctypes.c_uint64()
     _check(load().dotpe_event_submit(ctx, ctypes.byref(desc), ctypes.byref(eid)))
     return eid.value
@@ -330,8 +339,30 @@ def dotpe_event_release(ctx, event_id):
     return _check(load().dotpe_event_release(ctx, event_id))
 
 
+def dotpe_rb_weights(ctx, f_fine, df_fine, psd, data, h0, nodes, t0=None):
+    """Relative-binning weights (App. A) on the device: f_fine, df_fine [N], psd [D,N],
+    data [D,N] complex, h0 [M,N] complex, nodes [B] int64, t0 [D] (numpy, host).
+    Returns (w_dh [D,M,B], w_hh [D,M,M,B]) complex128."""
+    f_fine = np.ascontiguousarray(f_fine, dtype=np.float64)
+    df_fine = np.ascontiguousarray(df_fine, dtype=np.float64)
+    psd = np.ascontiguousarray(psd, dtype=np.float64)
+    data = _host_c128(data)
+    h0 = _host_c128(h0)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    t0 = None if t0 is None else np.ascontiguousarray(t0, dtype=np.float64)
+    D, N = psd.shape
+    M, B = h0.shape[0], nodes.shape[0]
+    w_dh = np.zeros((D, M, B), np.complex128)
+    w_hh = np.zeros((D, M, M, B), np.complex128)
+    desc = dotpe_rb_desc(D, M, N, _ptr(f_fine), _ptr(df_fine), _ptr(psd), _ptr(data.view(np.float64)),
+                         _ptr(h0.view(np.float64)), _ptr(t0), B, nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    _check(load().dotpe_rb_weights(ctx, ctypes.byref(desc), ctypes.c_void_p(w_dh.ctypes.data),
+                                   ctypes.c_void_p(w_hh.ctypes.data)))
+    return w_dh, w_hh
+
+
 def dotpe_preselect(ctx, bank_id, i0, i1, psd, data, t_grid, n_phi=32, delta=20.0, precision="fp16x3",
-                    outputs=("lnl_ml", "arg_ot", "lnl_inco", "selected")):
+                    outputs=("lnl_ml", "arg_ot", "lnl_inco", "selected"), rb=None):
     """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of bank rows [i0, i1).
 
     psd [D, B], data [D, B] complex, t_grid [D, n_t] (numpy, host).  Returns a dict
@@ -339,13 +370,18 @@ def dotpe_preselect(ctx, bank_id, i0, i1, psd, data, t_grid, n_phi=32, delta=20.
     float32, arg_ot [N, D, 2] int32 ((o, t)), lnl_inco [N] float64, selected
     [n_selected] int64 (slice-relative rows)."""
     L = load()
-    psd = np.ascontiguousarray(psd, dtype=np.float64)
-    data = _host_c128(data)
+    psd = None if psd is None else np.ascontiguousarray(psd, dtype=np.float64)
+    data = None if data is None else _host_c128(data)
     tg = np.ascontiguousarray(t_grid, dtype=np.float64)
     D, n_t = tg.shape
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    desc = dotpe_presel_desc(bank_id, i0, i1, D, _ptr(psd), _ptr(data.view(np.float64)), n_t, _ptr(tg),
-                             n_phi, float(delta), prec, 0)
+    rbd = rbh = None
+    if rb is not None:
+        rbd, rbh = _host_c128(rb[0]), _host_c128(rb[1])
+    desc = dotpe_presel_desc(bank_id, i0, i1, D, _ptr(psd), None if data is None else _ptr(data.view(np.float64)),
+                             n_t, _ptr(tg), n_phi, float(delta), prec, 0,
+                             None if rbd is None else _ptr(rbd.view(np.float64)),
+                             None if rbh is None else _ptr(rbh.view(np.float64)))
     N = i1 - i0
     arrs = {}
     if "lnl_ml" in outputs:

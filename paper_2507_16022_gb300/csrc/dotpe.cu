@@ -128,6 +128,7 @@ struct Event {
   size_t in_bytes = 0;
   double *psd = nullptr, *t = nullptr, *lwe = nullptr;
   double2 *data = nullptr, *R = nullptr;
+  double2 *rb_dh = nullptr, *rb_hh = nullptr;  // relative-binning weights (App. A), or null
   void *in_stage = nullptr;  // pinned host staging of host inputs
   size_t stage_bytes = 0;
   cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr, ev_k0 = nullptr, ev_k1 = nullptr,
@@ -233,7 +234,7 @@ static ScratchLayout scratch_layout(const Event &e) {
   size_t elem = (L.pack_kind == 0) ? 4 : 2;
   const int64_t T = (int64_t)L.n_itile * L.n_etile;
   Carver c;
-  L.c = c.take<float2>(D * B);
+  L.c = c.take<float2>(D * M * B);
   L.omega = c.take<float>(D * B);
   L.fh = c.take<float>(B);
   L.fl = c.take<float>(B);
@@ -345,6 +346,7 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
   PrepArgs &pa = R.pa;
   pa.D = e.D; pa.B = b.B; pa.M = b.M; pa.Kpad = b.Kpad; pa.E = e.NE;
   pa.f = b.f; pa.w = b.w; pa.psd = e.psd; pa.data = e.data; pa.t = e.t; pa.R = e.R;
+  pa.rb_dh = e.rb_dh; pa.rb_hh = e.rb_hh;
   pa.c = (float2 *)(scr + L.c);
   pa.omega = (float *)(scr + L.omega);
   pa.fh = (float *)(scr + L.fh);
@@ -464,8 +466,8 @@ static void event_block(dotpe_ctx *ctx, Event &e, EventRun &R, int64_t r0, int64
   if (e.xent) {
     R.P.mx = e.xent->mx + (e.i0 + r0) * e.D * REC;
   } else {
-    launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, (float *)(R.scr + R.L.mx),
-                       ctx->n_sms, st);
+    launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, e.rb_hh,
+                       (float *)(R.scr + R.L.mx), ctx->n_sms, st);
   }
   R.P.n_int = nr;
   R.P.i_base = e.i0 + r0;
@@ -601,8 +603,8 @@ static XEntry *xcache_find(Bank &b, uint64_t key, int D) {
 // A new cache entry of the bank's row records for one PSD, computed on `st`
 // from omega (which `st` has already been ordered after); evicts the least
 // recently used unreferenced entry when the bank's cache is full.
-static int xcache_build(dotpe_ctx *ctx, Bank &b, uint64_t key, int D, const float *omega, cudaStream_t st,
-                        XEntry **out) {
+static int xcache_build(dotpe_ctx *ctx, Bank &b, uint64_t key, int D, const float *omega, const double2 *rb_hh,
+                        cudaStream_t st, XEntry **out) {
   if ((int)b.xcache.size() >= XCACHE_MAX) {
     auto victim = b.xcache.end();
     for (auto it = b.xcache.begin(); it != b.xcache.end(); ++it)
@@ -627,7 +629,7 @@ static int xcache_build(dotpe_ctx *ctx, Bank &b, uint64_t key, int D, const floa
     return fail(DOTPE_E_NOMEM, "cross-term records (%zu bytes)", (size_t)b.I * D * REC * sizeof(float));
   }
   CUDA_OR_FAIL(cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming));
-  launch_cross_terms(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.master, omega, x->mx, ctx->n_sms, st);
+  launch_cross_terms(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.master, omega, rb_hh, x->mx, ctx->n_sms, st);
   CUDA_OR_FAIL(cudaEventRecord(x->ready, st));
   ctx->used += x->bytes;
   b.xcache.push_back(x);
@@ -645,7 +647,7 @@ static int xterms_acquire(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st
   } else {
     // omega of this event (its prep on `st` writes it) -> records of every bank row
     launch_prep(R.pa, st);
-    int rc = xcache_build(ctx, b, e.psd_key, e.D, R.pa.omega, st, &x);
+    int rc = xcache_build(ctx, b, e.psd_key, e.D, R.pa.omega, e.rb_hh, st, &x);
     if (rc != DOTPE_OK) return rc;
   }
   x->refs++;
@@ -654,20 +656,25 @@ static int xterms_acquire(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st
   return DOTPE_OK;
 }
 
-// Cross-term cache key: FNV-1a over n_det and the PSD bytes (host or device).
-static int psd_hash(int D, int B, const double *psd, uint64_t *out) {
-  std::vector<double> ps((size_t)D * B);
-  if (is_device_ptr(psd)) {
-    if (cudaMemcpy(ps.data(), psd, ps.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return fail(DOTPE_E_DEVICE, "reading the PSD");
+// Cross-term cache key: FNV-1a over n_det and the PSD bytes (host or device),
+// or, with relative binning, over a tag, n_det and the <h|h> weights (complex
+// [D][M][M][B]: n = 2 D M M B doubles), which then replace the PSD.
+static int psd_hash(int D, int B, const double *psd, uint64_t *out, const double *rb_hh = nullptr, size_t n_rb = 0) {
+  const bool rb = rb_hh != nullptr;
+  const double *src = rb ? rb_hh : psd;
+  std::vector<double> ps(rb ? n_rb : (size_t)D * B);
+  if (is_device_ptr(src)) {
+    if (cudaMemcpy(ps.data(), src, ps.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(DOTPE_E_DEVICE, "reading the PSD or weights");
   } else {
-    memcpy(ps.data(), psd, ps.size() * 8);
+    memcpy(ps.data(), src, ps.size() * 8);
   }
   uint64_t h = 1469598103934665603ull;
   auto mix = [&](const void *p, size_t n) {
     const uint8_t *c = (const uint8_t *)p;
     for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
   };
+  if (rb) mix("relative binning", 16);
   mix(&D, sizeof(D));
   mix(ps.data(), ps.size() * 8);
   *out = h;
@@ -1061,7 +1068,9 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   if (d->n_t < 1 || d->n_t > 4096) return fail(DOTPE_E_INVALID, "n_t=%d not in 1..4096", d->n_t);
   if (d->n_phi < 1 || d->n_phi > PS_MAXPHI) return fail(DOTPE_E_INVALID, "n_phi=%d not in 1..%d", d->n_phi, PS_MAXPHI);
   if (!(d->delta >= 0.0) || !std::isfinite(d->delta)) return fail(DOTPE_E_INVALID, "delta must be finite and >= 0");
-  if (!d->psd || !d->data || !d->t_grid) return fail(DOTPE_E_INVALID, "null input array");
+  const bool rb = d->rb_dh || d->rb_hh;
+  if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
+  if ((!rb && (!d->psd || !d->data)) || !d->t_grid) return fail(DOTPE_E_INVALID, "null input array");
   const int prec = d->precision;
   if (prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 && prec != DOTPE_PREC_BF16X3)
     return fail(DOTPE_E_INVALID, "pre-selection precision %d (FP16, FP16X3, BF16 or BF16X3)", prec);
@@ -1072,12 +1081,13 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   const int NTP = (NT + PS_TC - 1) / PS_TC * PS_TC;
   const bool bf = prec_bf16(prec), split = prec_split(prec);
   const int planes = split ? 2 : 1;
+  const int MG = rb ? M : 1;  // time-grid operands: one per mode with relative binning
   cudaStream_t st = ctx->main_stream;
 
   // cross-term records: the bank's cache entry for this PSD, a new one when the
   // slice is a large part of the bank, else the slice's own
   uint64_t key = 0;
-  int rc = psd_hash(D, B, d->psd, &key);
+  int rc = rb ? psd_hash(D, B, nullptr, &key, d->rb_hh, (size_t)2 * D * M * M * B) : psd_hash(D, B, d->psd, &key);
   if (rc != DOTPE_OK) return rc;
   XEntry *x = xcache_find(b, key, D);
   const bool build_cache = !x && 4 * NI >= b.I;
@@ -1086,11 +1096,12 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   Carver c;
   const size_t o_psd = c.take<double>((size_t)D * B), o_data = c.take<double2>((size_t)D * B);
   const size_t o_tg = c.take<double>((size_t)D * NT);
-  const size_t o_c = c.take<float2>((size_t)D * B), o_om = c.take<float>((size_t)D * B);
+  const size_t o_rbd = c.take<double2>(rb ? (size_t)D * M * B : 0), o_rbh = c.take<double2>(rb ? (size_t)D * M * M * B : 0);
+  const size_t o_c = c.take<float2>((size_t)D * M * B), o_om = c.take<float>((size_t)D * B);
   const size_t o_fh = c.take<float>(B), o_fl = c.take<float>(B);
-  const size_t o_G = c.take<float2>((size_t)D * NTP * B);
+  const size_t o_G = c.take<float2>((size_t)MG * D * NTP * B);
   const size_t o_gmax = c.take<float>(1), o_gs = c.take<float>(1);
-  const size_t o_pack = c.take<uint16_t>((size_t)planes * 2 * D * NTP * b.Kpad);
+  const size_t o_pack = c.take<uint16_t>((size_t)planes * MG * 2 * D * NTP * b.Kpad);
   const size_t o_mx = own_mx ? c.take<float>((size_t)NI * D * REC) : 0;
   const size_t o_keys = c.take<unsigned long long>((size_t)NI * D);
   const size_t o_ml = c.take<float>((size_t)NI * D), o_arg = c.take<int>((size_t)NI * D * 2);
@@ -1121,14 +1132,20 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   ck(cudaMemsetAsync(scr + o_gmax, 0, 4, st), "memset");
   ck(cudaMemsetAsync(scr + o_keys, 0, (size_t)NI * D * 8, st), "memset");
   ck(cudaMemsetAsync(scr + o_maxb, 0, 8, st), "memset");
-  ck(cudaMemcpyAsync(scr + o_psd, d->psd, (size_t)D * B * 8, cudaMemcpyDefault, st), "copying psd");
-  ck(cudaMemcpyAsync(scr + o_data, d->data, (size_t)D * B * 16, cudaMemcpyDefault, st), "copying data");
+  if (d->psd) ck(cudaMemcpyAsync(scr + o_psd, d->psd, (size_t)D * B * 8, cudaMemcpyDefault, st), "copying psd");
+  if (d->data) ck(cudaMemcpyAsync(scr + o_data, d->data, (size_t)D * B * 16, cudaMemcpyDefault, st), "copying data");
+  if (rb) {
+    ck(cudaMemcpyAsync(scr + o_rbd, d->rb_dh, (size_t)D * M * B * 16, cudaMemcpyDefault, st), "copying rb_dh");
+    ck(cudaMemcpyAsync(scr + o_rbh, d->rb_hh, (size_t)D * M * M * B * 16, cudaMemcpyDefault, st), "copying rb_hh");
+  }
   ck(cudaMemcpyAsync(scr + o_tg, d->t_grid, (size_t)D * NT * 8, cudaMemcpyDefault, st), "copying t_grid");
   if (rc != DOTPE_OK) return finish(rc);
 
   PreselPrepArgs pa;
   memset(&pa, 0, sizeof(pa));
-  pa.D = D; pa.B = B; pa.Kpad = b.Kpad; pa.n_t = NT; pa.n_tpad = NTP;
+  pa.D = D; pa.B = B; pa.M = M; pa.Kpad = b.Kpad; pa.n_t = NT; pa.n_tpad = NTP;
+  pa.rb_dh = rb ? (const double2 *)(scr + o_rbd) : nullptr;
+  const double2 *rb_hh = rb ? (const double2 *)(scr + o_rbh) : nullptr;
   pa.f = b.f; pa.w = b.w; pa.psd = (const double *)(scr + o_psd); pa.data = (const double2 *)(scr + o_data);
   pa.t_grid = (const double *)(scr + o_tg);
   pa.c = (float2 *)(scr + o_c); pa.omega = (float *)(scr + o_om);
@@ -1143,10 +1160,11 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     ck(cudaStreamWaitEvent(st, x->ready, 0), "cross-term wait");
     mx = x->mx + (size_t)d->i0 * D * REC;
   } else if (build_cache) {
-    if ((rc = xcache_build(ctx, b, key, D, pa.omega, st, &x)) != DOTPE_OK) return finish(rc);
+    if ((rc = xcache_build(ctx, b, key, D, pa.omega, rb_hh, st, &x)) != DOTPE_OK) return finish(rc);
     mx = x->mx + (size_t)d->i0 * D * REC;
   } else {
-    launch_cross_terms(NI, d->i0, b.I, M, D, B, b.Kpad, b.master, pa.omega, (float *)(scr + o_mx), ctx->n_sms, st);
+    launch_cross_terms(NI, d->i0, b.I, M, D, B, b.Kpad, b.master, pa.omega, rb_hh, (float *)(scr + o_mx), ctx->n_sms,
+                       st);
     mx = (const float *)(scr + o_mx);
   }
   if (x) {
@@ -1160,7 +1178,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   if (a_rows >= (1ll << 31)) rc = fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
   else if (encode_tmap_kblocks(&mapBank, dt, bf ? (void *)b.bf : (void *)b.hf, a_rows, b.Kpad / 64,
                                (uint64_t)b.Kpad * 2, PS_TR, 1) ||
-           encode_tmap_kblocks(&mapG, dt, scr + o_pack, (uint64_t)planes * 2 * D * NTP, b.Kpad / 64,
+           encode_tmap_kblocks(&mapG, dt, scr + o_pack, (uint64_t)planes * MG * 2 * D * NTP, b.Kpad / 64,
                                (uint64_t)b.Kpad * 2, 2 * PS_TC, 1))
     rc = fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (pre-selection)");
   PreselParams P;
@@ -1187,7 +1205,8 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   P.kb = b.Kpad / 64;
   P.a_plane_rows = M * (int)b.I;
   P.a_mode_rows = (int)b.I;
-  P.b_plane_rows = 2 * D * NTP;
+  P.b_plane_rows = MG * 2 * D * NTP;
+  P.b_mode_rows = rb ? 2 * D * NTP : 0;
   P.pol = b.pol + (size_t)d->i0 * M * 2;
   P.mx = mx;
   P.z_scale = 1.f / (b.a_scale * (bf ? 1.f : FP16_OPERAND_SCALE));
@@ -1198,7 +1217,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   P.wait_ns = 4000000000ull;
   if (rc == DOTPE_OK) {
     ck(cudaEventRecord(ev[1], st), "event record");
-    ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, ctx->n_sms, st), "pre-selection kernel");
+    ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, rb, ctx->n_sms, st), "pre-selection kernel");
     ck(cudaEventRecord(ev[2], st), "event record");
     launch_presel_finish(NI, D, d->n_phi, d->delta, P.keys, (float *)(scr + o_ml), (int *)(scr + o_arg),
                          (double *)(scr + o_inco), (unsigned long long *)(scr + o_maxb), (int64_t *)(scr + o_sel),
@@ -1238,6 +1257,76 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     out->device_status = dev_status;
   }
   return finish(rc);
+}
+
+// ---------------------------------------------------------------------------
+// Relative-binning weights (App. A)
+// ---------------------------------------------------------------------------
+static int rb_weights_locked(dotpe_ctx *ctx, const dotpe_rb_desc *d, double *w_dh, double *w_hh) {
+  if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
+  if (d->n_modes < 1 || d->n_modes > MAXM) return fail(DOTPE_E_INVALID, "n_modes=%d not in 1..%d", d->n_modes, MAXM);
+  if (d->n_bins < 2 || d->n_fine < d->n_bins) return fail(DOTPE_E_INVALID, "n_bins=%d, n_fine=%lld", d->n_bins,
+                                                           (long long)d->n_fine);
+  if (!d->f_fine || !d->df_fine || !d->psd || !d->data || !d->h0 || !d->nodes || !w_dh || !w_hh)
+    return fail(DOTPE_E_INVALID, "null array");
+  const int D = d->n_det, M = d->n_modes, B = d->n_bins;
+  const int64_t N = d->n_fine;
+  std::vector<int64_t> nodes(B);
+  if (is_device_ptr(d->nodes)) CUDA_OR_FAIL(cudaMemcpy(nodes.data(), d->nodes, B * 8, cudaMemcpyDeviceToHost));
+  else memcpy(nodes.data(), d->nodes, B * 8);
+  for (int b = 0; b < B; ++b)
+    if (nodes[b] < 0 || nodes[b] >= N || (b > 0 && nodes[b] <= nodes[b - 1]))
+      return fail(DOTPE_E_INVALID, "nodes must be strictly increasing indices into f_fine (node %d = %lld)", b,
+                  (long long)nodes[b]);
+  cudaStream_t st = ctx->main_stream;
+  Carver c;
+  const size_t o_f = c.take<double>(N), o_df = c.take<double>(N), o_psd = c.take<double>((size_t)D * N);
+  const size_t o_data = c.take<double2>((size_t)D * N), o_h0 = c.take<double2>((size_t)M * N);
+  const size_t o_t0 = c.take<double>(D), o_nodes = c.take<int64_t>(B);
+  const size_t o_wdh = c.take<double2>((size_t)D * M * B), o_whh = c.take<double2>((size_t)D * M * M * B);
+  const size_t o_st = c.take<int>(1);
+  uint8_t *scr = nullptr;
+  if (cudaMallocAsync((void **)&scr, c.off, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DOTPE_E_NOMEM, "relative-binning scratch (%zu bytes)", c.off);
+  }
+  int rc = DOTPE_OK;
+  auto ck = [&](cudaError_t e, const char *what) {
+    if (e != cudaSuccess && rc == DOTPE_OK) rc = fail(DOTPE_E_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+  };
+  ck(cudaMemsetAsync(scr + o_st, 0, sizeof(int), st), "memset");
+  ck(cudaMemsetAsync(scr + o_t0, 0, D * 8, st), "memset");
+  ck(cudaMemcpyAsync(scr + o_f, d->f_fine, N * 8, cudaMemcpyDefault, st), "copying f_fine");
+  ck(cudaMemcpyAsync(scr + o_df, d->df_fine, N * 8, cudaMemcpyDefault, st), "copying df_fine");
+  ck(cudaMemcpyAsync(scr + o_psd, d->psd, (size_t)D * N * 8, cudaMemcpyDefault, st), "copying psd");
+  ck(cudaMemcpyAsync(scr + o_data, d->data, (size_t)D * N * 16, cudaMemcpyDefault, st), "copying data");
+  ck(cudaMemcpyAsync(scr + o_h0, d->h0, (size_t)M * N * 16, cudaMemcpyDefault, st), "copying h0");
+  if (d->t0) ck(cudaMemcpyAsync(scr + o_t0, d->t0, D * 8, cudaMemcpyDefault, st), "copying t0");
+  ck(cudaMemcpyAsync(scr + o_nodes, nodes.data(), B * 8, cudaMemcpyHostToDevice, st), "copying nodes");
+  if (rc == DOTPE_OK) {
+    launch_rb_weights(D, M, N, (const double *)(scr + o_f), (const double *)(scr + o_df),
+                      (const double *)(scr + o_psd), (const double2 *)(scr + o_data), (const double2 *)(scr + o_h0),
+                      (const double *)(scr + o_t0), B, (const int64_t *)(scr + o_nodes), (double2 *)(scr + o_wdh),
+                      (double2 *)(scr + o_whh), (int *)(scr + o_st), st);
+    ck(cudaGetLastError(), "relative-binning weights kernel");
+  }
+  int dev_status = 0;
+  if (rc == DOTPE_OK) {
+    ck(cudaMemcpyAsync(&dev_status, scr + o_st, sizeof(int), cudaMemcpyDeviceToHost, st), "status copy");
+    ck(cudaStreamSynchronize(st), "relative-binning weights");
+  }
+  if (rc == DOTPE_OK && dev_status != 0)
+    rc = fail(DOTPE_E_INVALID, dev_status == DEV_E_SHAPE ? "a reference mode vanishes at a node"
+                                                          : "non-finite or non-positive PSD, or non-finite inputs");
+  if (rc == DOTPE_OK) {
+    ck(cudaMemcpyAsync(w_dh, scr + o_wdh, (size_t)D * M * B * 16, cudaMemcpyDefault, st), "copying w_dh");
+    ck(cudaMemcpyAsync(w_hh, scr + o_whh, (size_t)D * M * M * B * 16, cudaMemcpyDefault, st), "copying w_hh");
+    ck(cudaStreamSynchronize(st), "relative-binning outputs");
+  }
+  cudaStreamSynchronize(st);
+  cudaFreeAsync(scr, st);
+  cudaStreamSynchronize(st);
+  return rc;
 }
 
 }  // namespace dotpe
@@ -1541,7 +1630,9 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   if (d->n_ext < 1) return fail(DOTPE_E_INVALID, "n_ext=%lld", (long long)d->n_ext);
   if (d->n_phi < 1 || d->n_phi > MAXPHI) return fail(DOTPE_E_INVALID, "n_phi=%d not in 1..%d", d->n_phi, MAXPHI);
   if (!(d->u_min > 0.0) || !std::isfinite(d->u_min)) return fail(DOTPE_E_INVALID, "u_min must be > 0");
-  if (!d->psd || !d->data || !d->t || !d->R) return fail(DOTPE_E_INVALID, "null input array");
+  const bool rb = d->rb_dh || d->rb_hh;
+  if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
+  if ((!rb && (!d->psd || !d->data)) || !d->t || !d->R) return fail(DOTPE_E_INVALID, "null input array");
   if (d->precision < DOTPE_PREC_FP32 || d->precision > DOTPE_PREC_MIXED)
     return fail(DOTPE_E_INVALID, "precision %d", d->precision);
   if (d->block_rows < 0 || d->block_rows % TC_TI != 0)
@@ -1569,6 +1660,7 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   const int64_t D = e->D, B = b->B, M = b->M;
   size_t o_psd = c.take<double>(D * B), o_data = c.take<double2>(D * B), o_t = c.take<double>(NE * D);
   size_t o_R = c.take<double2>(NE * D * M), o_lw = c.take<double>(NE);
+  size_t o_rbd = c.take<double2>(rb ? D * M * B : 0), o_rbh = c.take<double2>(rb ? D * M * M * B : 0);
   e->in_bytes = c.off;
   if (need + e->in_bytes + b->bytes > ctx->budget) {
     delete e;
@@ -1594,12 +1686,18 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   e->t = (double *)(ib + o_t);
   e->R = (double2 *)(ib + o_R);
   e->lwe = (double *)(ib + o_lw);
+  if (rb) {
+    e->rb_dh = (double2 *)(ib + o_rbd);
+    e->rb_hh = (double2 *)(ib + o_rbh);
+  }
   struct Piece { const void *src; void *dst; size_t n; };
-  Piece pieces[5] = {{d->psd, e->psd, (size_t)(D * B * 8)},
-                     {d->data, e->data, (size_t)(D * B * 16)},
+  Piece pieces[7] = {{d->psd, e->psd, d->psd ? (size_t)(D * B * 8) : 0},
+                     {d->data, e->data, d->data ? (size_t)(D * B * 16) : 0},
                      {d->t, e->t, (size_t)(NE * D * 8)},
                      {d->R, e->R, (size_t)(NE * D * M * 16)},
-                     {d->ln_w_ext, e->lwe, d->ln_w_ext ? (size_t)(NE * 8) : 0}};
+                     {d->ln_w_ext, e->lwe, d->ln_w_ext ? (size_t)(NE * 8) : 0},
+                     {d->rb_dh, e->rb_dh, rb ? (size_t)(D * M * B * 16) : 0},
+                     {d->rb_hh, e->rb_hh, rb ? (size_t)(D * M * M * B * 16) : 0}};
   size_t host_total = 0;
   for (auto &p : pieces)
     if (p.n && !is_device_ptr(p.src)) host_total += p.n;
@@ -1630,7 +1728,8 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
     }
   }
   {
-    int rc = psd_hash(e->D, (int)B, d->psd, &e->psd_key);
+    int rc = rb ? psd_hash(e->D, (int)B, nullptr, &e->psd_key, d->rb_hh, (size_t)(2 * D * M * M * B))
+                : psd_hash(e->D, (int)B, d->psd, &e->psd_key);
     if (rc != DOTPE_OK) return cleanup(rc);
   }
   cudaEventCreateWithFlags(&e->ev_inputs, cudaEventDisableTiming);
@@ -1839,6 +1938,8 @@ static int recompute_block(dotpe_ctx *ctx, Event &e, int64_t a, int64_t b, int64
   sub.has_lwe = e.has_lwe;
   sub.psd = e.psd;
   sub.data = e.data;
+  sub.rb_dh = e.rb_dh;
+  sub.rb_hh = e.rb_hh;
   sub.t = e.t + e0 * e.D;
   sub.R = e.R + e0 * e.D * e.bank->M;
   sub.lwe = e.lwe + e0;
@@ -1925,6 +2026,13 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
     return DOTPE_OK;
   }
   return fail(DOTPE_E_INVALID, "what=%d", what);
+}
+
+int dotpe_rb_weights(dotpe_ctx *ctx, const dotpe_rb_desc *desc, double *w_dh, double *w_hh) {
+  if (!ctx || !desc) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  return rb_weights_locked(ctx, desc, w_dh, w_hh);
 }
 
 int dotpe_preselect(dotpe_ctx *ctx, const dotpe_presel_desc *desc, float *lnl_ml, int32_t *arg_ot,

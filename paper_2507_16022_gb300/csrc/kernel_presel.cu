@@ -17,6 +17,9 @@
 //       rows [(k, t) re-row; (k, t) im-row] x [re | im]: 64 (k, t) columns per tile;
 //   B (N = 64 M) = 64 bank rows of each mode, the bank's own operand planes
 //       (one TMA box per mode, stacked in shared memory mode after mode).
+// With relative binning (App. A) the data weights, hence G, differ per mode
+// (PERMODE): a stage then holds one mode's A and B and each MMA is N = 64
+// into that mode's TMEM columns.
 // TMEM lane 2c + part holds Re (part 0) or Im (part 1) of column c's Z; TMEM
 // column 64 m + j holds bank row j of mode m.  The small G operand stays in
 // L2; the bank streams from HBM, each row block once for all its column tiles
@@ -59,10 +62,14 @@ static_assert(QEPT == QTR * 8 && PS_MAXPHI == 32, "table pass: one thread per (r
 constexpr uint32_t QA_BYTES = QBM * QBK * 2;             // 16 KB per plane
 constexpr uint32_t QB_MODE = QTR * QBK * 2;              // 8 KB per mode and plane
 constexpr uint32_t QB_BYTES = MAXM * QB_MODE;            // 32 KB per plane
-template <bool SPLIT> struct QPipe {
+// Stage = one k-block of A and of all modes' B (shared time-grid operand), or,
+// PERMODE (a time-grid operand per mode: relative binning), one k-block of one
+// mode's A and B.  Both fill 192 KB.
+template <bool SPLIT, bool PERMODE> struct QPipe {
   static constexpr int NPL = SPLIT ? 2 : 1;
-  static constexpr int ST = SPLIT ? 2 : 4;
-  static constexpr uint32_t STAGE = NPL * (QA_BYTES + QB_BYTES);
+  static constexpr uint32_t BSZ = PERMODE ? QB_MODE : QB_BYTES;  // B bytes per plane and stage
+  static constexpr int ST = PERMODE ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4);
+  static constexpr uint32_t STAGE = NPL * (QA_BYTES + BSZ);
 };
 constexpr uint32_t Q_TMEM_COLS = 512, Q_BUF_COLS = MAXM * QTR;
 static_assert(2 * Q_BUF_COLS <= Q_TMEM_COLS, "TMEM budget");
@@ -71,15 +78,18 @@ struct QTail {
   float4 hs[QTR * PS_MAXPHI];       // [row][o]: (a, 2b, c, -), ln L^ML = a dp^2 + 2b dp dx + c dx^2
   float4 phm[PS_MAXPHI * 2];        // (cos, sin)(m_s phi_o) of the four mode slots: [o][(c0, s0, c1, s1), (c2, s2, c3, s3)]
   float2 phd[PS_MAXPHI * 3];        // (cos, sin)(delta phi_o), delta = 1..3
-  uint64_t full[4], empty[4], tfull[2], tempty[2], drain;
+  uint64_t full[8], empty[8], tfull[2], tempty[2], drain;
   uint32_t tmem_slot;
   int abort_flag;
 };
-template <bool SPLIT>
+template <bool SPLIT, bool PERMODE>
 constexpr size_t q_smem_bytes() {
-  return 1024 + (size_t)QPipe<SPLIT>::ST * QPipe<SPLIT>::STAGE + sizeof(QTail);
+  return 1024 + (size_t)QPipe<SPLIT, PERMODE>::ST * QPipe<SPLIT, PERMODE>::STAGE + sizeof(QTail);
 }
-static_assert(q_smem_bytes<true>() <= 232448 && q_smem_bytes<false>() <= 232448, "shared memory budget");
+static_assert(q_smem_bytes<true, false>() <= 232448 && q_smem_bytes<false, false>() <= 232448 &&
+                  q_smem_bytes<true, true>() <= 232448 && q_smem_bytes<false, true>() <= 232448,
+              "shared memory budget");
+static_assert(QPipe<false, true>::ST <= 8, "stage barriers");
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
   uint32_t r[8];
@@ -223,21 +233,23 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
   }
 }
 
-template <bool BF16, bool SPLIT>
+template <bool BF16, bool SPLIT, bool PERMODE>
 __global__ void __launch_bounds__(QNT, 1)
     presel_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapBank,
                   const __grid_constant__ PreselParams P) {
-  constexpr int ST = QPipe<SPLIT>::ST, NPL = QPipe<SPLIT>::NPL;
+  using Pipe = QPipe<SPLIT, PERMODE>;
+  constexpr int ST = Pipe::ST, NPL = Pipe::NPL;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // stage s, plane p: A (G, 16 KB) then B (bank, 4 x 8 KB)
-  QTail &T = *reinterpret_cast<QTail *>(base + (size_t)ST * QPipe<SPLIT>::STAGE);
-  auto sA = [&](int s, int p) { return base + (size_t)(s * NPL + p) * (QA_BYTES + QB_BYTES); };
+  // stage s, plane p: A (G, 16 KB) then B (bank: all modes, 4 x 8 KB, or PERMODE one mode, 8 KB)
+  QTail &T = *reinterpret_cast<QTail *>(base + (size_t)ST * Pipe::STAGE);
+  auto sA = [&](int s, int p) { return base + (size_t)(s * NPL + p) * (QA_BYTES + Pipe::BSZ); };
   auto sB = [&](int s, int p) { return sA(s, p) + QA_BYTES; };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = P.n_modes;
   const int n_work = P.n_itile * P.n_ctile;
   const int nkb = P.kb;
+  const int nsub = PERMODE ? M : 1;  // stages per k-block
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(&T.full[s], 1);
@@ -279,24 +291,26 @@ __global__ void __launch_bounds__(QNT, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      const uint32_t stage_bytes = NPL * (QA_BYTES + M * QB_MODE);
+      const uint32_t stage_bytes = PERMODE ? NPL * (QA_BYTES + QB_MODE) : NPL * (QA_BYTES + M * QB_MODE);
       uint32_t q = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
         const int rb = w / P.n_ctile, ct = w - rb * P.n_ctile;
-        for (int kb = 0; kb < nkb; ++kb, ++q) {
-          const int s = q % ST;
-          const uint32_t n = q / ST;
-          if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, nullptr, abortp, P.wait_ns))) break;
-          mbar_expect_tx(&T.full[s], stage_bytes);
+        for (int kb = 0; kb < nkb && ok; ++kb)
+          for (int sub = 0; sub < nsub; ++sub, ++q) {
+            const int s = q % ST;
+            const uint32_t n = q / ST;
+            if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, nullptr, abortp, P.wait_ns))) break;
+            mbar_expect_tx(&T.full[s], stage_bytes);
 #pragma unroll
-          for (int pl = 0; pl < NPL; ++pl) {
-            tma_load_3d(sA(s, pl), &mapG, &T.full[s], 0, pl * P.b_plane_rows + ct * QBM, kb);
-            for (int m = 0; m < M; ++m)
-              tma_load_3d(sB(s, pl) + m * QB_MODE, &mapBank, &T.full[s], 0,
-                          pl * P.a_plane_rows + m * P.a_mode_rows + P.a_row0 + rb * QTR, kb);
+            for (int pl = 0; pl < NPL; ++pl) {
+              tma_load_3d(sA(s, pl), &mapG, &T.full[s], 0, pl * P.b_plane_rows + sub * P.b_mode_rows + ct * QBM, kb);
+              const int m0 = PERMODE ? sub : 0, m1 = PERMODE ? sub + 1 : M;
+              for (int m = m0; m < m1; ++m)
+                tma_load_3d(sB(s, pl) + (m - m0) * QB_MODE, &mapBank, &T.full[s], 0,
+                            pl * P.a_plane_rows + m * P.a_mode_rows + P.a_row0 + rb * QTR, kb);
+            }
           }
-        }
       }
       if (!ok) {
         // let copies already in flight land before the CTA exits
@@ -309,7 +323,7 @@ __global__ void __launch_bounds__(QNT, 1)
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    const uint32_t idesc = idesc_f16(128, QTR * M, BF16);
+    const uint32_t idesc = idesc_f16(128, PERMODE ? QTR : QTR * M, BF16);
     const bool issuer = (lane == 0);
     uint32_t q = 0, u = 0;
     bool ok = true;
@@ -320,28 +334,29 @@ __global__ void __launch_bounds__(QNT, 1)
       if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, P.wait_ns));
       if (!ok) break;
       tc_fence_after();
-      const uint32_t dcol = tmem + b * Q_BUF_COLS;
-      for (int kb = 0; kb < nkb; ++kb, ++q) {
-        const int s = q % ST;
-        const uint32_t n = q / ST;
-        ok = __all_sync(0xffffffffu, mbar_wait(&T.full[s], n & 1, nullptr, abortp, P.wait_ns));
-        if (!ok) break;
-        tc_fence_after();
-        if (issuer) {
-          const uint64_t ah = sdesc_k128(sA(s, 0)), bh = sdesc_k128(sB(s, 0));
-          const uint64_t al = sdesc_k128(sA(s, NPL - 1)), bl = sdesc_k128(sB(s, NPL - 1));
+      for (int kb = 0; kb < nkb && ok; ++kb)
+        for (int sub = 0; sub < nsub; ++sub, ++q) {
+          const int s = q % ST;
+          const uint32_t n = q / ST;
+          ok = __all_sync(0xffffffffu, mbar_wait(&T.full[s], n & 1, nullptr, abortp, P.wait_ns));
+          if (!ok) break;
+          tc_fence_after();
+          if (issuer) {
+            const uint32_t dcol = tmem + b * Q_BUF_COLS + (PERMODE ? sub * QTR : 0);
+            const uint64_t ah = sdesc_k128(sA(s, 0)), bh = sdesc_k128(sB(s, 0));
+            const uint64_t al = sdesc_k128(sA(s, NPL - 1)), bl = sdesc_k128(sB(s, NPL - 1));
 #pragma unroll
-          for (int k = 0; k < QBK / 16; ++k) {
-            tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (kb | k) ? 1u : 0u);
-            if (SPLIT) {
-              tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
-              tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+            for (int k = 0; k < QBK / 16; ++k) {
+              tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (kb | k) ? 1u : 0u);
+              if (SPLIT) {
+                tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
+                tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+              }
             }
+            tc_commit(&T.empty[s]);
           }
-          tc_commit(&T.empty[s]);
+          __syncwarp();
         }
-        __syncwarp();
-      }
       if (ok && issuer) tc_commit(&T.tfull[b]);
       __syncwarp();
     }
@@ -567,26 +582,32 @@ __global__ void presel_select_kernel(int64_t n, double delta, const double *__re
   }
 }
 
-template <bool BF16, bool SPLIT>
+template <bool BF16, bool SPLIT, bool PERMODE>
 static cudaError_t launch_presel_variant(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p,
                                          int grid, cudaStream_t st) {
-  auto kern = presel_kernel<BF16, SPLIT>;
-  const size_t smem = q_smem_bytes<SPLIT>();
+  auto kern = presel_kernel<BF16, SPLIT, PERMODE>;
+  const size_t smem = q_smem_bytes<SPLIT, PERMODE>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, QNT, smem, st>>>(mapG, mapBank, p);
   return cudaGetLastError();
 }
 
+template <bool PERMODE>
+static cudaError_t launch_presel_pm(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p,
+                                    bool bf16, bool split, int grid, cudaStream_t st) {
+  if (bf16) return split ? launch_presel_variant<true, true, PERMODE>(mapG, mapBank, p, grid, st)
+                         : launch_presel_variant<true, false, PERMODE>(mapG, mapBank, p, grid, st);
+  return split ? launch_presel_variant<false, true, PERMODE>(mapG, mapBank, p, grid, st)
+               : launch_presel_variant<false, false, PERMODE>(mapG, mapBank, p, grid, st);
+}
+
 int launch_presel(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p, bool bf16, bool split,
-                  int n_sms, cudaStream_t st) {
+                  bool per_mode, int n_sms, cudaStream_t st) {
   const int total = p.n_itile * p.n_ctile;
   const int grid = total < n_sms ? (total > 0 ? total : 1) : n_sms;
-  cudaError_t e;
-  if (bf16) e = split ? launch_presel_variant<true, true>(mapG, mapBank, p, grid, st)
-                      : launch_presel_variant<true, false>(mapG, mapBank, p, grid, st);
-  else e = split ? launch_presel_variant<false, true>(mapG, mapBank, p, grid, st)
-                 : launch_presel_variant<false, false>(mapG, mapBank, p, grid, st);
+  const cudaError_t e = per_mode ? launch_presel_pm<true>(mapG, mapBank, p, bf16, split, grid, st)
+                                 : launch_presel_pm<false>(mapG, mapBank, p, bf16, split, grid, st);
   return (int)e;
 }
 

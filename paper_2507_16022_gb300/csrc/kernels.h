@@ -38,11 +38,15 @@ struct PrepArgs {
   float *gscale;   // 1 float out
   float *sqrt_dd;  // 1 float out: sqrt<d|d> (Eq. inner_product, FP64 sum)
   int *status;
+  // relative binning (App. A), both or neither: W^{<d|h>} [D][M][B], W^{<h|h>} [D][M][M][B]
+  const double2 *rb_dh, *rb_hh;
 };
 
 void launch_prep(const PrepArgs &a, cudaStream_t st);
+// rb_hh non-null: relative-binning mode-pair weights instead of omega
 void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
-                        const float *master, const float *omega, float *mx, int n_sms, cudaStream_t st);
+                        const float *master, const float *omega, const double2 *rb_hh, float *mx, int n_sms,
+                        cudaStream_t st);
 void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, const void *src,
                            int dtype, float *master, float *amax, int *status, cudaStream_t st);
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf /*[2][n]*/,
@@ -185,13 +189,14 @@ constexpr int PS_TR = 64;       // bank rows per tile
 constexpr int PS_MAXPHI = 32;   // phases per grid
 constexpr float PS_RANK_TOL = 1e-3f;  // [hh]^+ is the rank-one limit when det <= PS_RANK_TOL hh_++ hh_xx
 struct PreselPrepArgs {
-  int D, B, Kpad, n_t, n_tpad;
+  int D, B, M, Kpad, n_t, n_tpad;
   const double *f, *w, *psd;
   const double2 *data;
   const double *t_grid;  // [D][n_t]
-  float2 *c;             // [D][B] 4 w conj(d) / S
+  const double2 *rb_dh;  // relative binning (App. A) or null: then G is per mode
+  float2 *c;             // [D][M][B] data weights of each mode
   float *omega, *fh, *fl;
-  float2 *G32;           // [D n_tpad][B] c_{kb} e^{-2 pi i f_b t_{kt}} (0 on padding columns)
+  float2 *G32;           // [1 or M][D n_tpad][B] c_{kmb} e^{-2 pi i f_b t_{kt}} (0 on padding columns)
   float *gmax;           // 1 float, zeroed
   void *gpack;           // packed operand planes [planes][2 D n_tpad][Kpad]
   int pack_kind;         // 1 bf16, 2 fp16
@@ -211,6 +216,7 @@ struct PreselParams {
   int n_itile, n_ctile;  // 64-row tiles, 64-column tiles
   int kb;                // k-blocks of 64 per mode
   int a_plane_rows, a_mode_rows, b_plane_rows;
+  int b_mode_rows;       // per-mode time-grid operand (relative binning): rows of one mode, else 0
   const float2 *pol;     // [n_rows][M][2] K_{imp} (slice-relative)
   const float *mx;       // [n_rows][n_det][REC] <h_m|h_m'>_k (slice-relative)
   float z_scale;         // accumulator -> Z scale (times 1 / *g_scale)
@@ -226,10 +232,15 @@ struct PreselOut {
 };
 // returns a cudaError_t
 int launch_presel(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p, bool bf16, bool split,
-                  int n_sms, cudaStream_t st);
+                  bool per_mode, int n_sms, cudaStream_t st);
 void launch_presel_finish(int64_t n, int D, int n_phi, double delta, const unsigned long long *keys, float *ml,
                           int *arg_ot, double *inco, unsigned long long *max_bits /*zeroed*/, int64_t *sel,
                           PreselOut *out, cudaStream_t st);
+
+// Relative-binning weights (App. A): kernel_rb.cu.  w_dh [D][M][B], w_hh [D][M][M][B].
+void launch_rb_weights(int D, int M, int64_t N, const double *ff, const double *dff, const double *psd,
+                       const double2 *data, const double2 *h0, const double *t0, int B, const int64_t *node,
+                       double2 *w_dh, double2 *w_hh, int *status, cudaStream_t st);
 
 // Tensor-map encoding through the driver entry point.
 int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,

@@ -23,10 +23,14 @@ namespace dotpe {
 // ---------------------------------------------------------------------------
 // K0
 // ---------------------------------------------------------------------------
-__global__ void prep_bins_kernel(int D, int B, const double *__restrict__ f, const double *__restrict__ w,
+// Data weights of every mode, c[d][m][b]: the plain quadrature's
+// 4 w_b conj(d_d(f_b)) / S_d(f_b) (the same for every mode), or, with relative
+// binning (App. A, Eq. d_h), conj(W^{<d|h>}_{d m b}).
+__global__ void prep_bins_kernel(int D, int B, int M, const double *__restrict__ f, const double *__restrict__ w,
                                  const double *__restrict__ psd, const double2 *__restrict__ data,
-                                 float2 *__restrict__ c, float *__restrict__ omega, float *__restrict__ fh,
-                                 float *__restrict__ fl, int *status) {
+                                 const double2 *__restrict__ rb_dh, float2 *__restrict__ c,
+                                 float *__restrict__ omega, float *__restrict__ fh, float *__restrict__ fl,
+                                 int *status) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < B) {
     double fb = f[k];
@@ -36,7 +40,16 @@ __global__ void prep_bins_kernel(int D, int B, const double *__restrict__ f, con
     if (!isfinite(fb) || !isfinite(w[k])) atomicCAS(status, 0, DEV_E_NONFINITE);
   }
   if (k >= D * B) return;
-  int b = k % B;
+  const int b = k % B, d = k / B;
+  if (rb_dh) {
+    omega[k] = 0.f;
+    for (int m = 0; m < M; ++m) {
+      double2 v = rb_dh[((int64_t)d * M + m) * B + b];
+      if (!isfinite(v.x) || !isfinite(v.y)) { atomicCAS(status, 0, DEV_E_NONFINITE); v = make_double2(0.0, 0.0); }
+      c[((int64_t)d * M + m) * B + b] = make_float2((float)v.x, (float)(-v.y));
+    }
+    return;
+  }
   double S = psd[k];
   double2 dk = data[k];
   if (!(S > 0.0) || !isfinite(S) || !isfinite(dk.x) || !isfinite(dk.y)) {
@@ -45,8 +58,35 @@ __global__ void prep_bins_kernel(int D, int B, const double *__restrict__ f, con
   }
   double om = 4.0 * w[b] / S;
   omega[k] = (float)om;
-  float2 cv = make_float2((float)(om * dk.x), (float)(-om * dk.y));
-  c[k] = cv;
+  const float2 cv = make_float2((float)(om * dk.x), (float)(-om * dk.y));
+  for (int m = 0; m < M; ++m) c[((int64_t)d * M + m) * B + b] = cv;
+}
+
+// Relative binning: the Cauchy-Schwarz scale of the screening margin,
+// sqrt(max_m sum_{d,b} |W^{<d|h>}_{d m b}|^2 / W^{<h|h>}_{d m m b}) (with plain
+// weights the same sum is <d|d>), in FP64, one block, fixed order.
+__global__ void rb_norm_kernel(int D, int M, int B, const double2 *__restrict__ rb_dh,
+                               const double2 *__restrict__ rb_hh, float *__restrict__ sqrt_dd) {
+  __shared__ double part[256];
+  double best = 0.0;
+  for (int m = 0; m < M; ++m) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < D * B; k += blockDim.x) {
+      const int d = k / B, b = k % B;
+      const double2 a = rb_dh[((int64_t)d * M + m) * B + b];
+      const double h = rb_hh[(((int64_t)d * M + m) * M + m) * B + b].x;
+      if (h > 0.0 && isfinite(h)) v += (a.x * a.x + a.y * a.y) / h;
+    }
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+      __syncthreads();
+    }
+    best = fmax(best, part[0]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *sqrt_dd = (float)sqrt(best);
 }
 
 // sqrt<d|d> = sqrt(sum_{d,b} omega_{d,b} |d_d(f_b)|^2) in FP64, one block, fixed order.
@@ -131,11 +171,11 @@ __global__ void build_G_kernel(int64_t E, int D, int M, int B, const float *__re
   float f_h = fh[b], f_l = fl[b];
   for (int d = 0; d < D; ++d) {
     float2 T = shift_factor(f_h, f_l, th[e * D + d], tl[e * D + d]);
-    float2 cc = c[d * B + b];
-    float2 W = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) {
       if (m >= M) break;
+      const float2 cc = c[((int64_t)d * M + m) * B + b];
+      const float2 W = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
       float2 r = Rf[(e * D + d) * M + m];
       g[m].x += r.x * W.x - r.y * W.y;
       g[m].y += r.x * W.y + r.y * W.x;
@@ -217,11 +257,16 @@ __global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *_
 // ---------------------------------------------------------------------------
 // K2: row records <h_{im}|h_{im'}>_d  (one warp per bank row)
 // ---------------------------------------------------------------------------
+// RB: the weight of each mode pair is W^{<h|h>}_{d a c b} of relative binning
+// (App. A, Eq. h_h; complex, rb_hh [D][M][M][B]) instead of omega_{d b}.
+template <bool RB>
 __global__ void cross_terms_kernel(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
                                    const float *__restrict__ master /*[M][I_bank][Kpad]*/,
-                                   const float *__restrict__ omega /*[D][B]*/, float *__restrict__ mx) {
+                                   const float *__restrict__ omega /*[D][B]*/,
+                                   const double2 *__restrict__ rb_hh, float *__restrict__ mx) {
   extern __shared__ float om_s[];
-  for (int k = threadIdx.x; k < D * B; k += blockDim.x) om_s[k] = omega[k];
+  if (!RB)
+    for (int k = threadIdx.x; k < D * B; k += blockDim.x) om_s[k] = omega[k];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -247,18 +292,39 @@ __global__ void cross_terms_kernel(int64_t n_rows, int64_t row0, int64_t I_bank,
 #pragma unroll
       for (int d = 0; d < MAXD; ++d) {
         if (d >= D) break;
-        float w = om_s[d * B + b];
+        if (!RB) {
+          float w = om_s[d * B + b];
 #pragma unroll
-        for (int m = 0; m < MAXM; ++m) acc[d][m] += w * (hr[m] * hr[m] + hi[m] * hi[m]);
-        int p = 0;
+          for (int m = 0; m < MAXM; ++m) acc[d][m] += w * (hr[m] * hr[m] + hi[m] * hi[m]);
+          int p = 0;
 #pragma unroll
-        for (int a = 1; a < MAXM; ++a)
+          for (int a = 1; a < MAXM; ++a)
 #pragma unroll
-          for (int c = 0; c < a; ++c, ++p) {
-            // h_a h_c^*
-            acc[d][4 + 2 * p] += w * (hr[a] * hr[c] + hi[a] * hi[c]);
-            acc[d][5 + 2 * p] += w * (hi[a] * hr[c] - hr[a] * hi[c]);
+            for (int c = 0; c < a; ++c, ++p) {
+              // h_a h_c^*
+              acc[d][4 + 2 * p] += w * (hr[a] * hr[c] + hi[a] * hi[c]);
+              acc[d][5 + 2 * p] += w * (hi[a] * hr[c] - hr[a] * hi[c]);
+            }
+        } else {
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) {
+            if (m >= M) break;
+            const float w = (float)__ldg(&rb_hh[(((int64_t)d * M + m) * M + m) * B + b].x);
+            acc[d][m] += w * (hr[m] * hr[m] + hi[m] * hi[m]);
           }
+          int p = 0;
+#pragma unroll
+          for (int a = 1; a < MAXM; ++a)
+#pragma unroll
+            for (int c = 0; c < a; ++c, ++p) {
+              if (a >= M) continue;
+              const double2 wv = __ldg(&rb_hh[(((int64_t)d * M + a) * M + c) * B + b]);
+              const float wr = (float)wv.x, wi = (float)wv.y;
+              const float pr = hr[a] * hr[c] + hi[a] * hi[c], pi = hi[a] * hr[c] - hr[a] * hi[c];
+              acc[d][4 + 2 * p] += wr * pr - wi * pi;
+              acc[d][5 + 2 * p] += wr * pi + wi * pr;
+            }
+        }
       }
     }
 #pragma unroll
@@ -393,9 +459,12 @@ __global__ void dist_marg_eval_kernel(int64_t n, const float *__restrict__ dh, c
 static inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 void launch_prep(const PrepArgs &a, cudaStream_t st) {
-  prep_bins_kernel<<<nblk((int64_t)a.D * a.B, 256), 256, 0, st>>>(a.D, a.B, a.f, a.w, a.psd, a.data, a.c, a.omega,
-                                                                a.fh, a.fl, a.status);
-  if (a.sqrt_dd) data_norm_kernel<<<1, 256, 0, st>>>(a.D, a.B, a.w, a.psd, a.data, a.sqrt_dd);
+  prep_bins_kernel<<<nblk((int64_t)a.D * a.B, 256), 256, 0, st>>>(a.D, a.B, a.M, a.f, a.w, a.psd, a.data, a.rb_dh,
+                                                                a.c, a.omega, a.fh, a.fl, a.status);
+  if (a.sqrt_dd) {
+    if (a.rb_dh) rb_norm_kernel<<<1, 256, 0, st>>>(a.D, a.M, a.B, a.rb_dh, a.rb_hh, a.sqrt_dd);
+    else data_norm_kernel<<<1, 256, 0, st>>>(a.D, a.B, a.w, a.psd, a.data, a.sqrt_dd);
+  }
   prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, a.th, a.tl, a.Rf, a.qx, a.status);
   build_G_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.Rf, a.G32,
                                                        a.gmax);
@@ -414,15 +483,19 @@ void launch_prep(const PrepArgs &a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Pre-selection operand (Sec. IV.D, App. B): G_k[b, t] = c_{kb} e^{-2 pi i f_b t_{kt}}
 // ---------------------------------------------------------------------------
-__global__ void presel_G_kernel(int D, int B, int n_t, int n_tpad, const float *__restrict__ fh,
+// One matrix for every mode (plain quadrature), or one per mode when the data
+// weights are per mode (relative binning): G[mg][(d, t)][b], mg < n_gmodes.
+__global__ void presel_G_kernel(int D, int B, int M, int n_gmodes, int n_t, int n_tpad, const float *__restrict__ fh,
                                 const float *__restrict__ fl, const double *__restrict__ t_grid,
                                 const float2 *__restrict__ c, float2 *__restrict__ G, float *__restrict__ gmax,
                                 int *status) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float a = 0.f;
-  if (k < (int64_t)D * n_tpad * B) {
+  if (k < (int64_t)n_gmodes * D * n_tpad * B) {
     const int b = (int)(k % B);
-    const int col = (int)(k / B);
+    const int64_t mcol = k / B;
+    const int col = (int)(mcol % ((int64_t)D * n_tpad));
+    const int mg = (int)(mcol / ((int64_t)D * n_tpad));
     const int d = col / n_tpad, t = col - d * n_tpad;
     float2 g = make_float2(0.f, 0.f);
     if (t < n_t) {
@@ -430,7 +503,7 @@ __global__ void presel_G_kernel(int D, int B, int n_t, int n_tpad, const float *
       if (!isfinite(tv)) { atomicCAS(status, 0, DEV_E_NONFINITE); tv = 0.0; }
       const float th = (float)tv, tl = (float)(tv - (double)th);
       const float2 T = shift_factor(fh[b], fl[b], th, tl);
-      const float2 cc = c[d * B + b];
+      const float2 cc = c[((int64_t)d * M + mg) * B + b];
       g = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
     }
     G[k] = g;
@@ -443,32 +516,40 @@ __global__ void presel_G_kernel(int D, int B, int n_t, int n_tpad, const float *
 
 void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st) {
   const int DB = a.D * a.B;
-  prep_bins_kernel<<<nblk(DB > a.B ? DB : a.B, 256), 256, 0, st>>>(a.D, a.B, a.f, a.w, a.psd, a.data, a.c, a.omega,
-                                                                   a.fh, a.fl, a.status);
-  const int64_t n = (int64_t)a.D * a.n_tpad * a.B;
-  presel_G_kernel<<<nblk(n, 256), 256, 0, st>>>(a.D, a.B, a.n_t, a.n_tpad, a.fh, a.fl, a.t_grid, a.c, a.G32,
-                                                a.gmax, a.status);
+  prep_bins_kernel<<<nblk(DB > a.B ? DB : a.B, 256), 256, 0, st>>>(a.D, a.B, a.M, a.f, a.w, a.psd, a.data,
+                                                                   a.rb_dh, a.c, a.omega, a.fh, a.fl, a.status);
+  const int mg = a.rb_dh ? a.M : 1;
+  const int64_t n = (int64_t)mg * a.D * a.n_tpad * a.B;
+  presel_G_kernel<<<nblk(n, 256), 256, 0, st>>>(a.D, a.B, a.M, mg, a.n_t, a.n_tpad, a.fh, a.fl, a.t_grid, a.c,
+                                                a.G32, a.gmax, a.status);
   const int64_t E = (int64_t)a.D * a.n_tpad;
   const int pad = a.Kpad - 2 * a.B;
-  const int64_t np = E * (a.B > pad ? a.B : pad);
+  const int64_t np = mg * E * (a.B > pad ? a.B : pad);
   if (a.pack_kind == 1)
-    pack_G_kernel<__nv_bfloat16><<<nblk(np, 256), 256, 0, st>>>(E, 1, a.B, a.Kpad, a.G32, a.gmax, 1, a.pack_planes,
+    pack_G_kernel<__nv_bfloat16><<<nblk(np, 256), 256, 0, st>>>(E, mg, a.B, a.Kpad, a.G32, a.gmax, 1, a.pack_planes,
                                                                 a.gpack, a.gscale);
   else
-    pack_G_kernel<__half><<<nblk(np, 256), 256, 0, st>>>(E, 1, a.B, a.Kpad, a.G32, a.gmax, 2, a.pack_planes, a.gpack,
-                                                         a.gscale);
+    pack_G_kernel<__half><<<nblk(np, 256), 256, 0, st>>>(E, mg, a.B, a.Kpad, a.G32, a.gmax, 2, a.pack_planes,
+                                                         a.gpack, a.gscale);
 }
 
 void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
-                        const float *master, const float *omega, float *mx, int n_sms, cudaStream_t st) {
+                        const float *master, const float *omega, const double2 *rb_hh, float *mx, int n_sms,
+                        cudaStream_t st) {
   int bs = 256;
   int64_t warps = (n_rows + 0);
   int64_t blocks = (warps * 32 + bs - 1) / bs;
   int64_t cap = (int64_t)n_sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
+  if (rb_hh) {
+    cross_terms_kernel<true><<<(unsigned)blocks, bs, 0, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, master, omega,
+                                                              rb_hh, mx);
+    return;
+  }
   size_t smem = sizeof(float) * (size_t)D * B;
-  cross_terms_kernel<<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, master, omega, mx);
+  cross_terms_kernel<false><<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, master, omega,
+                                                                nullptr, mx);
 }
 
 void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, const void *src,

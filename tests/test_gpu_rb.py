@@ -1,0 +1,145 @@
+"""Relative binning (App. A) on the device, through the C ABI, against the FP64
+oracle with the same weights.
+
+* dotpe_rb_weights (FP64 on the device) equals the oracle's weights to FP64
+  rounding (|dW| <= 1e-11 max|W|).
+* An event evaluated with the weights (per-mode data weights, complex
+  mode-pair <h|h> weights) meets the coherent path's tolerances against the
+  oracle's route O2 with the same weights, all pairs: 1e-3 per pair for FP32,
+  1e-3 + TC_ACC ln L^ML for split fp16 (the tensor cores' truncating FP32
+  accumulation over Kpad/16 = 48 steps; the peak here is ln L^ML ~ 230);
+  |d ln Z| <= 1e-2.
+* The pre-selection with the weights (one time-grid operand per mode) meets
+  its split tolerance 2e-3 + 1e-4 ln L^ML against the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TC_ACC = 2 * (768 // 16) * 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def dpx():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2507_16022_gb300 as dp
+    ctx = dp.dotpe_create(0)
+    yield dp, ctx
+    dp.dotpe_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def rbw():
+    import oracle
+    # 1,000 rows (a ragged row tile), 200 samples, the paper's N_f = 378 nodes on a 65,536-point grid
+    rw = synth.make_rb_workload(n_int=1000, n_ext=200, n_det=3, n_modes=4, n_bins=378, n_fine=65536, seed=51,
+                                snr=20.0)
+    w = oracle.rb_weights(rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, rw.nodes, rw.t0)
+    return rw, w
+
+
+def test_weights_kernel_matches_oracle(dpx, rbw):
+    dp, ctx = dpx
+    rw, (wdh, whh) = rbw
+    gdh, ghh = dp.dotpe_rb_weights(ctx, rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, rw.nodes, rw.t0)
+    assert np.max(np.abs(gdh - wdh)) <= 1e-11 * np.max(np.abs(wdh))
+    assert np.max(np.abs(ghh - whh)) <= 1e-11 * np.max(np.abs(whh))
+
+
+def test_weights_errors(dpx, rbw):
+    dp, ctx = dpx
+    rw, _ = rbw
+    bad = rw.nodes.copy()
+    bad[5] = bad[4]
+    with pytest.raises(dp.DotpeError) as ei:
+        dp.dotpe_rb_weights(ctx, rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, bad, rw.t0)
+    assert ei.value.status == dp.DOTPE_E_INVALID
+    h0 = rw.h0_fine.copy()
+    h0[1, rw.nodes[7]] = 0.0
+    with pytest.raises(dp.DotpeError) as ei:
+        dp.dotpe_rb_weights(ctx, rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, h0, rw.nodes, rw.t0)
+    assert ei.value.status == dp.DOTPE_E_INVALID and "vanishes" in str(ei.value)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
+def test_event_with_weights_against_oracle(dpx, rbw, precision):
+    dp, ctx = dpx
+    rw, (wdh, whh) = rbw
+    import oracle
+    P = oracle.OracleProblem(rw.bank, rw.ext, rw.event, rb=(wdh, whh))
+    grid, _ = P.eval_grid(0.0)
+    ref = P.evidence(grid)
+    bank = rw.bank
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+    try:
+        I, E = bank.h.shape[0], rw.ext.t.shape[0]
+        eid = dp.dotpe_event_submit(ctx, bid, 0, I, None, None, rw.ext.t, rw.ext.R, rw.ext.ln_w,
+                                    n_phi=rw.event.n_phi, u_min=rw.event.u_min, cut_delta=0.0,
+                                    precision=precision, flags=dp.DOTPE_FLAG_STORE_LNL, rb=(wdh, whh))
+        dp.dotpe_event_wait(ctx, eid, 120.0)
+        ev = dp.dotpe_evidence(ctx, eid)
+        lnl = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E)
+        ml = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+        dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    d1 = np.abs(lnl - grid["lnl_marg"])
+    d2 = np.abs(ml - grid["lnl_ml_max"])
+    ml_ref = grid["lnl_ml_max"]
+    if precision == "mixed":
+        # pairs within 30 of the maximum are refined (split bound); the others keep
+        # the single-pass fp16 bound, with the binned data's Cauchy-Schwarz scale
+        # max_m sum |W^{<d|h>}|^2 / W^{<h|h>}_{mm} in place of <d|d>
+        near = ml_ref >= ml_ref.max() - 30.0
+        u = 2.0 ** -11
+        dd = max(float(np.sum(np.abs(wdh[:, m]) ** 2 / whh[:, m, m].real)) for m in range(wdh.shape[1]))
+        mlp = np.maximum(ml_ref, 0)
+        far_tol = 2e-2 + 4 * u * mlp + 2 * u * np.sqrt(2 * mlp + 1) * np.sqrt(dd)
+        tol = np.where(near, 1e-3 + TC_ACC * mlp, far_tol)
+    elif precision == "fp16x3":
+        tol = 1e-3 + TC_ACC * np.maximum(ml_ref, 0)
+    else:
+        tol = np.full_like(ml_ref, 1e-3)
+    print(f"rb event {precision}: max |d ln Lbar| {d1.max():.3e}, max |d ln L^ML| {d2.max():.3e}, "
+          f"d ln Z {ev['ln_z'] - ref['ln_z']:.3e}, peak ln L^ML {ml_ref.max():.1f}")
+    assert np.all(d1 <= tol)
+    assert np.all(d2 <= tol)
+    assert abs(ev["ln_z"] - ref["ln_z"]) <= 1e-2
+    assert (ev["arg_i"], ev["arg_e"]) == ref["arg"][:2]
+
+
+def test_preselection_with_weights_against_oracle(dpx, rbw):
+    dp, ctx = dpx
+    rw, (wdh, whh) = rbw
+    import oracle
+    I = rw.bank.h.shape[0]
+    cos_iota = np.random.default_rng(52).uniform(-1, 1, I)
+    cos_iota[0] = rw.event.injection["cos_iota"]
+    pol = synth.row_polarisation_factors(rw.bank, cos_iota)
+    D = rw.psd_fine.shape[0]
+    t_grid = rw.t0[:, None] + (np.arange(48) - 24)[None, :] * 2.5e-4
+    Pq = oracle.PreselProblem(rw.bank.f, rw.bank.w, rw.bank.mode_m, rw.bank.h, pol, rw.event.psd, rw.event.data,
+                              t_grid, n_phi=32, rb=(wdh, whh))
+    ref = Pq.run(delta=20.0)
+    bank = rw.bank
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w, pol=pol)
+    try:
+        out = {}
+        for precision in ("fp16x3", "bf16x3"):
+            out[precision] = dp.dotpe_preselect(ctx, bid, 0, I, None, None, t_grid, n_phi=32, delta=20.0,
+                                                precision=precision, rb=(wdh, whh))
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    tol = 2e-3 + 1e-4 * np.abs(ref["ml"])
+    for precision, r in out.items():
+        d = np.abs(r["lnl_ml"] - ref["ml"])
+        print(f"rb presel {precision}: max |d ln L^ML_ik| {d.max():.3e} (up to {ref['ml'].max():.1f})")
+        assert np.all(d <= tol), (precision, float(d.max()))
+        # the kernel's maximum row is the oracle's, or ties it within the tolerance
+        assert abs(ref["lnl_inco"][r["arg_i"]] - ref["lnl_inco"].max()) <= tol.sum(1).max()
+        # the injected (reference) row is kept
+        assert 0 in set(r["selected"].tolist())
