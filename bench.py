@@ -16,7 +16,7 @@ reduction.  The K timed events are submitted together; the runtime runs up to
 four at once.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload event|batch64|serve|presel|rb]
+                  [--workload event|batch64|serve|presel|rb|samples]
 
 --workload batch64: 64 events (extrinsic counts from {512, ..., 4096}, 2-3
 detectors, SNR 8-40) over one shared 262,144-row bank, submitted as one batch:
@@ -32,6 +32,9 @@ times, N_phi = 32), split fp16 by default; a step is one dotpe_preselect call.
 --workload rb: relative binning (App. A) at the paper's N_f = 378 nodes of a
 131,072-point grid: 65,536 bank rows around the signal x 4,096 extrinsic
 samples near it; a step is one dotpe_rb_weights call plus one event.
+--workload samples: posterior samples (Eq. posterior_element resampling with
+App. C distance draws) of the main event stored with DOTPE_FLAG_STORE_LNL;
+a step is one dotpe_posterior_samples call of 65,536 samples.
 
 Under torchrun (N > 1) every rank runs its own independent events on its own
 GPU (events do not share data: weak scaling, no collective on the data path);
@@ -565,6 +568,53 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
     return line
 
 
+def bench_samples(args, dp, ctx_factory, torch, dev):
+    """Posterior samples of one stored 65,536 x 4,096 event; a step draws 65,536
+    samples (the paper's N_s = N_eff/2 is reported beside it)."""
+    import synth
+    wl = synth.make_workload(**WORKLOAD, n_phi=N_PHI)
+    I, E = WORKLOAD["n_int"], WORKLOAD["n_ext"]
+    ctx = ctx_factory()
+    bank = wl.bank
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+    eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R, wl.ext.ln_w,
+                                n_phi=N_PHI, u_min=wl.event.u_min, cut_delta=args.cut, precision=args.precision,
+                                flags=dp.DOTPE_FLAG_STORE_LNL)
+    dp.dotpe_event_wait(ctx, eid, 600.0)
+    ev = dp.dotpe_evidence(ctx, eid)
+    n = 65536
+    rng = np.random.default_rng(99)
+    uni = rng.random((n, 4))
+    for _ in range(args.warmup):
+        dp.dotpe_posterior_samples(ctx, eid, uni)
+    ns = max(1, int(ev["n_eff"] / 2))
+    t = time.perf_counter()
+    dp.dotpe_posterior_samples(ctx, eid, uni[:ns])
+    ns_ms = (time.perf_counter() - t) * 1e3
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        dp.dotpe_posterior_samples(ctx, eid, uni)
+    dt = (time.perf_counter() - t) / args.steps
+    clocks = sampler.stop()
+    dp.dotpe_event_release(ctx, eid)
+    dp.dotpe_bank_release(ctx, bid)
+    dp.dotpe_destroy(ctx)
+    return {
+        "metric": "posterior samples/s", "value": n / dt, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"posterior samples of one stored event ({workload_name()}), 65,536 per call",
+                   "precision": args.precision, "n_eff": ev["n_eff"], "n_s_paper": ns,
+                   "ms_for_n_s": ns_ms, "timing": "wall clock of the synchronous call (uniforms and samples "
+                                                 "copied between host and device inside)"},
+        "roofline": None, "e2e": {"value": n / dt, "unit": "samples/s", "h2d_bytes_per_step": 32 * n,
+                                  "d2h_bytes_per_step": 28 * n},
+        "gpu_launches": 2 * args.steps, "clocks": clocks, "cpu_baseline": None,
+    }
+
+
 def bench_serve(args, dp, ctx_factory, torch, dev):
     """Poisson arrivals against resident banks; continuous batching at admission."""
     import synth
@@ -649,7 +699,8 @@ def main():
     ap.add_argument("--events", type=int, default=4, help="distinct event realisations cycled")
     ap.add_argument("--n-int", type=int, default=WORKLOAD["n_int"], help="bank rows (profiling runs)")
     ap.add_argument("--n-ext", type=int, default=WORKLOAD["n_ext"], help="extrinsic samples (profiling runs)")
-    ap.add_argument("--workload", default="event", choices=["event", "batch64", "serve", "presel", "rb"])
+    ap.add_argument("--workload", default="event",
+                    choices=["event", "batch64", "serve", "presel", "rb", "samples"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
     args = ap.parse_args()
@@ -685,6 +736,8 @@ def main():
             line = bench_presel(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         elif args.workload == "rb":
             line = bench_rb(args, dp, lambda: dp.dotpe_create(local), torch, dev)
+        elif args.workload == "samples":
+            line = bench_samples(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         else:
             line = bench_serve(args, dp, lambda: dp.dotpe_create(local, max_batch=args.max_batch), torch, dev)
         print(json.dumps(line), flush=True)

@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define DOTPE_ABI_VERSION 3
+#define DOTPE_ABI_VERSION 4
 
 /* ---- status codes ------------------------------------------------------ */
 #define DOTPE_OK 0
@@ -368,6 +368,26 @@ int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out);
  * Errors: E_NOT_READY, E_NOT_FOUND, E_INVALID (range), E_NOMEM, E_DEVICE. */
 int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, int64_t e0,
                      int64_t e1, int what, float *out, int64_t ld);
+
+/* Posterior samples of a finished event by resampling (Sec. III: the weights
+ * p_ieo = w_i w_e w_o Lbar_ieo of Eq. posterior_element, w_o = 1) with a
+ * distance drawn per sample from the summand of the distance marginal
+ * (App. C).  The caller supplies the random numbers: uniforms [n][4] in
+ * [0, 1) (host or device).  Per sample: u1 picks the bank row i (weights
+ * sum_{e,o} p_ieo, the event's FP64 row marginals), u2 the extrinsic sample e
+ * (weights w_e Lbar_ie of the stored row), u3 the phase o (weights Lbar_ieo
+ * of the phases that pass the event's ML cut, the pair recomputed in FP64 from
+ * the event's inputs), u4 the distance: d_L / d_L^0 = 1/u with u on
+ * [u_min, inf) of density proportional to u^-4 exp(dh_o u - hh_o u^2 / 2).
+ * Each draw takes the smallest index whose cumulative weight exceeds u times
+ * the total.  The paper draws N_s = N_eff / 2 samples (Sec. V.B).  Outputs
+ * (host or device, each may be NULL): i_out [n] (slice-relative), e_out [n],
+ * o_out [n], dist_out [n].  The event must be DONE and must have run with
+ * DOTPE_FLAG_STORE_LNL.  Errors: E_NOT_FOUND, E_NOT_READY, E_INVALID (no
+ * stored values, n not in 1..2^24, no pair of positive weight), E_NOMEM,
+ * E_DEVICE. */
+int dotpe_posterior_samples(dotpe_ctx *ctx, uint64_t event_id, int64_t n, const double *uniforms,
+                            int64_t *i_out, int64_t *e_out, int32_t *o_out, double *dist_out);
 
 /* Frees an event's device state (waits for it if still running). */
 int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id);

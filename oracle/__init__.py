@@ -70,6 +70,8 @@ def lib():
             L.or_lnl_ml.restype = ctypes.c_double
             L.or_lnl_ml.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_default_threads.restype = ctypes.c_int
+            L.or_dist_sample.restype = ctypes.c_double
+            L.or_dist_sample.argtypes = [ctypes.c_double] * 4
             L.or_quad_ml.restype = ctypes.c_double
             L.or_quad_ml.argtypes = [ctypes.c_double] * 5
             for name in ("or_data_weights", "or_direct_phases", "or_mode_components",
@@ -300,6 +302,41 @@ def quad_ml(dh_p, dh_x, a, b, c):
 def dist_marg(dh, hh, u_min):
     """Eq. lnl_dist_marginalized (pi(d_L) ~ d_L^2 up to d_max = d0/u_min)."""
     return lib().or_dist_marg(float(dh), float(hh), float(u_min))
+
+
+def dist_sample(dh, hh, u_min, q):
+    """Distance draw d_L / d_L^0 at cumulative probability q of the conditional
+    density u^-4 exp(dh u - hh u^2/2), u = d_L^0/d_L >= u_min (App. C)."""
+    return lib().or_dist_sample(float(dh), float(hh), float(u_min), float(q))
+
+
+def posterior_samples(P, grid, ev, uniforms, threshold=-np.inf):
+    """Resampling (Eq. posterior_element weights p_ieo = w_i w_e w_o Lbar_ieo):
+    i from the row marginals, e from row i, o from the pair's phases (those that
+    pass the ML cut at `threshold`), then the distance.  uniforms [n, 4]; the
+    smallest index whose cumulative weight exceeds u * total is taken.
+    Returns (i, e, o, d_L/d_L^0) arrays."""
+    I, E = P.shape[:2]
+    lw_e = P.ln_w_ext
+    ln_pi = ev["ln_p_int"]
+
+    def pick(lnw, u):
+        m = np.max(lnw)
+        c = np.cumsum(np.exp(lnw - m))
+        return int(np.searchsorted(c, u * c[-1], side="right"))
+
+    out_i, out_e, out_o, out_d = [], [], [], []
+    for u1, u2, u3, u4 in np.asarray(uniforms, dtype=np.float64):
+        i = pick(ln_pi, u1)
+        e = pick(grid[i]["lnl_marg"] + lw_e, u2)
+        z, H = P.mode_components(i, e)
+        dh, hh = P.rotate_phases(z, H)
+        lo = np.array([dist_marg(dh[o], hh[o], P.u_min) if lnl_ml(dh[o], hh[o]) >= threshold else -np.inf
+                       for o in range(P.n_phi)])
+        o = pick(lo, u3)
+        out_i.append(i); out_e.append(e); out_o.append(o)
+        out_d.append(dist_sample(dh[o], hh[o], P.u_min, u4))
+    return np.array(out_i), np.array(out_e), np.array(out_o), np.array(out_d)
 
 
 def lnl_ml(dh, hh):

@@ -386,6 +386,56 @@ double or_dist_marg(double dh, double hh, double u_min) {
   return 0.5 * x * x + log(3.0) + 3.0 * log(s) + pmax + log(tot);
 }
 
+/* integral of the log-shifted integrand over [a, b] by adaptive GK(7/15) */
+static double dm_integral(const dm_ctx *c, double a, double b) {
+  enum { NP = 512 };
+  double pa[NP], pb[NP], pr[NP], pe[NP];
+  int np = 1;
+  pa[0] = a; pb[0] = b;
+  gk15(c, a, b, &pr[0], &pe[0]);
+  for (;;) {
+    double tot = 0.0, err = 0.0;
+    int w = 0;
+    for (int k = 0; k < np; ++k) {
+      tot += pr[k];
+      err += pe[k];
+      if (pe[k] > pe[w]) w = k;
+    }
+    if (err <= 1e-14 * fabs(tot) || np >= NP - 1) return tot;
+    double mid = 0.5 * (pa[w] + pb[w]);
+    if (!(mid > pa[w] && mid < pb[w])) return tot;
+    pa[np] = mid; pb[np] = pb[w];
+    pb[w] = mid;
+    gk15(c, pa[w], pb[w], &pr[w], &pe[w]);
+    gk15(c, pa[np], pb[np], &pr[np], &pe[np]);
+    ++np;
+  }
+}
+
+double or_dist_sample(double dh, double hh, double u_min, double q) {
+  if (!(hh > 0.0)) return cbrt(1.0 - q) / u_min;
+  const double r = sqrt(hh), x = dh / r, s = r * u_min;
+  /* v = sqrt(hh) u: density ~ v^-4 e^{-(v-x)^2/2} on [s, inf); the shift is the
+   * log-density's maximum (at s or at the local maximum v2 for x > 4) */
+  double vmax = s, pmax = -4.0 * log(s) - 0.5 * (s - x) * (s - x);
+  if (x > 4.0) {
+    double v2 = 0.5 * (x + sqrt(x * x - 16.0));
+    double p2 = -4.0 * log(v2) - 0.5 * (v2 - x) * (v2 - x);
+    if (v2 > s && p2 > pmax) { pmax = p2; vmax = v2; }
+  }
+  dm_ctx c = {x, pmax};
+  /* beyond max(s, x, vmax) + 40 the Gaussian factor is below e^-800 */
+  double hi = fmax(fmax(s, x), vmax) + 40.0;
+  double total = dm_integral(&c, s, hi);
+  double lo = s, up = hi;
+  for (int it = 0; it < 200 && up - lo > 1e-14 * up; ++it) {
+    double mid = 0.5 * (lo + up);
+    if (dm_integral(&c, s, mid) < q * total) lo = mid;
+    else up = mid;
+  }
+  return r / (0.5 * (lo + up)); /* d/d0 = 1/u = sqrt(hh) / v */
+}
+
 /* ------------------------------------------------------------------------ */
 /* Per-pair evaluation                                                       */
 /* ------------------------------------------------------------------------ */

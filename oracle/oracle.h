@@ -105,6 +105,14 @@ double or_lnl_ml(double dh, double hh);
  * u_min = d_L^0 / d_max: returns ln Lbar(dh, hh). */
 double or_dist_marg(double dh, double hh, double u_min);
 
+/* Distance draw of one posterior sample (App. C: distance drawn per pair from
+ * the summand of the distance marginal): the conditional density of
+ * u = d_L^0 / d_L on [u_min, inf) is proportional to u^-4 exp(dh u - hh u^2 / 2)
+ * (pi(d_L) ~ d_L^2); returns d_L / d_L^0 = 1/u at cumulative probability q in
+ * [0, 1), found by bisection on the adaptive Gauss-Kronrod CDF.  hh <= 0: the
+ * prior, d_L / d_L^0 = (1 - q)^(1/3) / u_min. */
+double or_dist_sample(double dh, double hh, double u_min, double q);
+
 /* Full per-pair evaluation (route O2, phase grid, ML cut, distance marginal,
  * phase average) for an explicit list of pairs.  lnl_ml_threshold: phases
  * with ln L^ML below it are dropped (pass -INFINITY for no cut). */

@@ -44,7 +44,7 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
            "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit",
-           "dotpe_preselect", "dotpe_rb_weights")
+           "dotpe_preselect", "dotpe_rb_weights", "dotpe_posterior_samples")
 
 
 class DotpeError(RuntimeError):
@@ -153,6 +153,7 @@ def load(path: str = LIB_PATH):
         "dotpe_preselect": ([vp, ctypes.POINTER(dotpe_presel_desc), vp, vp, vp, vp,
                              ctypes.POINTER(dotpe_presel_out)], ctypes.c_int),
         "dotpe_rb_weights": ([vp, ctypes.POINTER(dotpe_rb_desc), vp, vp], ctypes.c_int),
+        "dotpe_posterior_samples": ([vp, ctypes.c_uint64, ctypes.c_int64, vp, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -337,6 +338,21 @@ def dotpe_lnl_blocks(ctx, event_id, i0, i1, e0, e1, what=DOTPE_LNL_MARG, out=Non
 
 def dotpe_event_release(ctx, event_id):
     return _check(load().dotpe_event_release(ctx, event_id))
+
+
+def dotpe_posterior_samples(ctx, event_id, uniforms):
+    """Posterior samples of a finished event (stored with DOTPE_FLAG_STORE_LNL);
+    uniforms [n, 4] in [0, 1).  Returns (i, e, o, d_L / d_L^0) numpy arrays."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    n = u.shape[0]
+    i = np.empty(n, np.int64)
+    e = np.empty(n, np.int64)
+    o = np.empty(n, np.int32)
+    d = np.empty(n, np.float64)
+    _check(load().dotpe_posterior_samples(ctx, event_id, n, ctypes.c_void_p(u.ctypes.data),
+                                          ctypes.c_void_p(i.ctypes.data), ctypes.c_void_p(e.ctypes.data),
+                                          ctypes.c_void_p(o.ctypes.data), ctypes.c_void_p(d.ctypes.data)))
+    return i, e, o, d
 
 
 def dotpe_rb_weights(ctx, f_fine, df_fine, psd, data, h0, nodes, t0=None):

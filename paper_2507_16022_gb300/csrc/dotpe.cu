@@ -1329,6 +1329,84 @@ static int rb_weights_locked(dotpe_ctx *ctx, const dotpe_rb_desc *d, double *w_d
   return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Posterior samples (Eq. posterior_element resampling, App. C distance draws)
+// ---------------------------------------------------------------------------
+static int samples_locked(dotpe_ctx *ctx, Event &e, int64_t n, const double *uniforms, int64_t *i_out,
+                          int64_t *e_out, int32_t *o_out, double *d_out) {
+  Bank &b = *e.bank;
+  if (!(e.flags & DOTPE_FLAG_STORE_LNL))
+    return fail(DOTPE_E_INVALID, "posterior samples need an event run with DOTPE_FLAG_STORE_LNL");
+  if (n < 1 || n > (1ll << 24)) return fail(DOTPE_E_INVALID, "n=%lld not in 1..2^24", (long long)n);
+  if (!uniforms) return fail(DOTPE_E_INVALID, "null uniforms");
+  cudaStream_t st = ctx->main_stream;
+  Carver c;
+  const size_t o_u = c.take<double>((size_t)4 * n), o_cdf = c.take<double>(e.NI);
+  const size_t o_i = c.take<int64_t>(n), o_e = c.take<int64_t>(n), o_o = c.take<int32_t>(n), o_d = c.take<double>(n);
+  const size_t o_st = c.take<int>(1);
+  uint8_t *scr = nullptr;
+  if (cudaMallocAsync((void **)&scr, c.off, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DOTPE_E_NOMEM, "sampling scratch (%zu bytes)", c.off);
+  }
+  int rc = DOTPE_OK;
+  auto ck = [&](cudaError_t x, const char *what) {
+    if (x != cudaSuccess && rc == DOTPE_OK) rc = fail(DOTPE_E_DEVICE, "%s: %s", what, cudaGetErrorString(x));
+  };
+  ck(cudaMemsetAsync(scr + o_st, 0, sizeof(int), st), "memset");
+  ck(cudaMemcpyAsync(scr + o_u, uniforms, (size_t)32 * n, cudaMemcpyDefault, st), "copying uniforms");
+  SampleArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_int = e.NI;
+  a.n_ext = e.NE;
+  a.n_det = e.D;
+  a.n_modes = b.M;
+  a.n_bins = b.B;
+  a.n_phi = e.nphi;
+  for (int m = 0; m < MAXM; ++m) a.mode_m[m] = m < b.M ? b.mode_m[m] : 0;
+  a.i_base = e.i0;
+  a.bank_rows = b.I;
+  a.kpad = b.Kpad;
+  a.master = b.master;
+  a.f = b.f;
+  a.w = b.w;
+  a.psd = e.psd;
+  a.data = e.data;
+  a.rb_dh = e.rb_dh;
+  a.rb_hh = e.rb_hh;
+  a.t = e.t;
+  a.R = e.R;
+  a.lw_ext = e.has_lwe ? e.lwe : nullptr;
+  a.ln_p_int = e.ln_p_int;
+  a.lnl = e.lnl_tile;
+  a.threshold = e.h_out->threshold;
+  a.u_min = (float)e.u_min;
+  a.dm_table = ctx->dm_table;
+  a.status = (int *)(scr + o_st);
+  if (rc == DOTPE_OK) {
+    launch_sample(a, n, (const double *)(scr + o_u), (double *)(scr + o_cdf), (int64_t *)(scr + o_i),
+                  (int64_t *)(scr + o_e), (int32_t *)(scr + o_o), (double *)(scr + o_d), st);
+    ck(cudaGetLastError(), "sampling kernels");
+  }
+  int dev_status = 0;
+  if (rc == DOTPE_OK) {
+    ck(cudaMemcpyAsync(&dev_status, scr + o_st, sizeof(int), cudaMemcpyDeviceToHost, st), "status copy");
+    ck(cudaStreamSynchronize(st), "sampling");
+  }
+  if (rc == DOTPE_OK && dev_status != 0) rc = fail(DOTPE_E_INVALID, "no pair or phase of positive weight");
+  if (rc == DOTPE_OK) {
+    if (i_out) ck(cudaMemcpyAsync(i_out, scr + o_i, 8 * n, cudaMemcpyDefault, st), "copying i");
+    if (e_out) ck(cudaMemcpyAsync(e_out, scr + o_e, 8 * n, cudaMemcpyDefault, st), "copying e");
+    if (o_out) ck(cudaMemcpyAsync(o_out, scr + o_o, 4 * n, cudaMemcpyDefault, st), "copying o");
+    if (d_out) ck(cudaMemcpyAsync(d_out, scr + o_d, 8 * n, cudaMemcpyDefault, st), "copying distances");
+    ck(cudaStreamSynchronize(st), "sampling outputs");
+  }
+  cudaStreamSynchronize(st);
+  cudaFreeAsync(scr, st);
+  cudaStreamSynchronize(st);
+  return rc;
+}
+
 }  // namespace dotpe
 
 using namespace dotpe;
@@ -2026,6 +2104,19 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
     return DOTPE_OK;
   }
   return fail(DOTPE_E_INVALID, "what=%d", what);
+}
+
+int dotpe_posterior_samples(dotpe_ctx *ctx, uint64_t event_id, int64_t n, const double *uniforms, int64_t *i_out,
+                            int64_t *e_out, int32_t *o_out, double *dist_out) {
+  if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  progress(ctx);
+  auto it = ctx->events.find(event_id);
+  if (it == ctx->events.end()) return fail(DOTPE_E_NOT_FOUND, "event %llu", (unsigned long long)event_id);
+  Event &e = *it->second;
+  if (e.state != DOTPE_STATE_DONE) return fail(DOTPE_E_NOT_READY, "event not done");
+  return samples_locked(ctx, e, n, uniforms, i_out, e_out, o_out, dist_out);
 }
 
 int dotpe_rb_weights(dotpe_ctx *ctx, const dotpe_rb_desc *desc, double *w_dh, double *w_hh) {

@@ -242,6 +242,32 @@ void launch_rb_weights(int D, int M, int64_t N, const double *ff, const double *
                        const double2 *data, const double2 *h0, const double *t0, int B, const int64_t *node,
                        double2 *w_dh, double2 *w_hh, int *status, cudaStream_t st);
 
+// Posterior samples of a finished event: kernel_sample.cu.
+struct SampleArgs {
+  int64_t n_int, n_ext;         // slice rows, extrinsic samples
+  int n_det, n_modes, n_bins, n_phi;
+  int mode_m[MAXM];
+  int64_t i_base, bank_rows;    // first bank row of the slice, rows of the bank
+  int kpad;
+  const float *master;          // bank FP32 master [M][bank_rows][kpad] ([re | im | pad])
+  const double *f, *w;          // [B]
+  const double *psd;            // [D][B] (plain quadrature)
+  const double2 *data;          // [D][B]
+  const double2 *rb_dh, *rb_hh; // relative-binning weights, or null
+  const double *t;              // [E][D]
+  const double2 *R;             // [E][D][M]
+  const double *lw_ext;         // [E] or null
+  const double *ln_p_int;       // [n_int] ln sum_{e,o} p_ieo
+  const float *lnl;             // [n_int][n_ext] stored ln Lbar_ie
+  double threshold;             // the event's ML cut (-inf: none)
+  float u_min;
+  const float4 *dm_table;
+  int *status;
+};
+// cdf: n_int doubles of scratch; outputs may be null
+void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cdf, int64_t *i_out, int64_t *e_out,
+                   int32_t *o_out, double *d_out, cudaStream_t st);
+
 // Tensor-map encoding through the driver entry point.
 int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,
                         uint64_t row_bytes, uint32_t box_rows, uint32_t box_kb);
