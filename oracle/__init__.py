@@ -43,7 +43,8 @@ class Problem(ctypes.Structure):
                 ("ln_w_int", ctypes.POINTER(ctypes.c_double)),
                 ("ln_w_ext", ctypes.POINTER(ctypes.c_double)),
                 ("u_min", ctypes.c_double),
-                ("rb_dh", ctypes.POINTER(ctypes.c_double)), ("rb_hh", ctypes.POINTER(ctypes.c_double))]
+                ("rb_dh", ctypes.POINTER(ctypes.c_double)), ("rb_hh", ctypes.POINTER(ctypes.c_double)),
+                ("n_pol", ctypes.c_int), ("F", ctypes.POINTER(ctypes.c_double))]
 
 
 PAIR_DTYPE = np.dtype([("lnl_marg", "f8"), ("lnl_sq", "f8"), ("lnl_ml_max", "f8"),
@@ -105,13 +106,17 @@ class OracleProblem:
         self.psd = np.ascontiguousarray(event.psd, dtype=np.float64)
         self.data = _c128(event.data)
         self.h = _c128(h)
-        self.R = _c128(ext.R)
+        # polarisation-resolved bank: h [I, M, 2, B] with real antenna patterns ext.F [E, D, 2]
+        self.n_pol = 2 if self.h.ndim == 4 else 1
+        self.R = _c128(ext.R) if self.n_pol == 1 else np.zeros(1, np.complex128)
+        self.F = (np.ascontiguousarray(ext.F, dtype=np.float64) if self.n_pol == 2 else None)
         self.t = np.ascontiguousarray(ext.t, dtype=np.float64)
         self.ln_w_int = np.ascontiguousarray(lw_i, dtype=np.float64)
         self.ln_w_ext = np.ascontiguousarray(ext.ln_w, dtype=np.float64)
-        I, M, B = self.h.shape
+        I, M, B = self.h.shape[0], self.h.shape[1], self.h.shape[-1]
         E, D = self.t.shape
         self.shape = (I, E, D, M, B)
+        assert rb is None or self.n_pol == 1, "relative binning with a polarisation-resolved bank"
         self.n_phi = int(event.n_phi)
         self.u_min = float(event.u_min)
         self.rb = None if rb is None else (_c128(rb[0]), _c128(rb[1]))
@@ -123,7 +128,8 @@ class OracleProblem:
                          _dp(self.h.view(np.float64)), _dp(self.R.view(np.float64)), _dp(self.t),
                          _dp(self.ln_w_int), _dp(self.ln_w_ext), self.u_min,
                          None if rb is None else _dp(self.rb[0].view(np.float64)),
-                         None if rb is None else _dp(self.rb[1].view(np.float64)))
+                         None if rb is None else _dp(self.rb[1].view(np.float64)),
+                         self.n_pol, None if self.F is None else _dp(self.F))
 
     # -- components -------------------------------------------------------
     def data_weights(self):

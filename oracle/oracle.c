@@ -61,6 +61,19 @@ static cplx grid_phase(int k, int o, int n_phi) {
   return cexp(I * TWO_PI * (double)r / (double)n_phi);
 }
 
+/* Polarisations per mode (2 for a polarisation-resolved bank), the waveform
+ * component h_{i m q}(f_b) and its response at detector d for sample e:
+ * R_{e d m} (q = 0) or the real antenna pattern F_{e d q}. */
+static inline int n_pol_of(const or_problem *p) { return p->n_pol == 2 ? 2 : 1; }
+static inline cplx hval(const or_problem *p, int64_t i, int m, int q, int b) {
+  const int NP = n_pol_of(p);
+  return ld_c(p->h, ((i * p->n_modes + m) * NP + q) * (int64_t)p->n_bins + b);
+}
+static inline cplx resp(const or_problem *p, int64_t e, int d, int m, int q) {
+  if (n_pol_of(p) == 2) return p->F[(e * p->n_det + d) * 2 + q];
+  return ld_c(p->R, (e * p->n_det + d) * p->n_modes + m);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Relative-binning weights (App. A, Eqs. dh_weights, hh_weights)            */
 /* ------------------------------------------------------------------------ */
@@ -128,10 +141,8 @@ int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, 
         /* strain of Eq. h_k at d_L = d_L^0 */
         cplx hk = 0.0;
         for (int m = 0; m < M; ++m) {
-          cplx hm = ld_c(p->h, (i * M + m) * B + b);
-          cplx R = ld_c(p->R, (e * D + d) * M + m);
           cplx Phi = grid_phase(p->mode_m[m], o, p->n_phi);
-          hk += hm * R * Phi;
+          for (int q = 0; q < n_pol_of(p); ++q) hk += hval(p, i, m, q, b) * resp(p, e, d, m, q) * Phi;
         }
         hk *= cexp(-I * TWO_PI * p->f[b] * t);
         double wgt = 4.0 * p->w[b] / p->psd[(int64_t)d * B + b];
@@ -149,20 +160,21 @@ int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, 
 /* ------------------------------------------------------------------------ */
 /* Route O2: per-mode components, then phase rotation                        */
 /* ------------------------------------------------------------------------ */
-/* <h_{i m}|h_{i m'}>_d = sum_b omega_{d b} h_m h_{m'}^*  -> hm[d][M][M]
- * (relative binning: the weight of each mode pair, Eq. h_h) */
+/* <h_{i m q}|h_{i m' q'}>_d = sum_b omega_{d b} h_{m q} h_{m' q'}^*  -> hm[d][M NP][M NP]
+ * (index m NP + q; relative binning: the weight of each mode pair, Eq. h_h) */
 static void mode_overlaps(const or_problem *p, const double *omega, int64_t i, cplx *hm) {
-  const int M = p->n_modes, D = p->n_det, B = p->n_bins;
+  const int M = p->n_modes, D = p->n_det, B = p->n_bins, NP = n_pol_of(p), J = M * NP;
   for (int d = 0; d < D; ++d)
-    for (int m = 0; m < M; ++m)
-      for (int mp = 0; mp < M; ++mp) {
+    for (int j = 0; j < J; ++j)
+      for (int jp = 0; jp < J; ++jp) {
+        const int m = j / NP, q = j % NP, mp = jp / NP, qp = jp % NP;
         cplx acc = 0.0;
         for (int b = 0; b < B; ++b) {
           cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)d * M + m) * M + mp) * B + b)
                               : (cplx)omega[(int64_t)d * B + b];
-          acc += wgt * ld_c(p->h, (i * M + m) * B + b) * conj(ld_c(p->h, (i * M + mp) * B + b));
+          acc += wgt * hval(p, i, m, q, b) * conj(hval(p, i, mp, qp, b));
         }
-        hm[(d * M + m) * M + mp] = acc;
+        hm[((int64_t)d * J + j) * J + jp] = acc;
       }
 }
 
@@ -175,31 +187,33 @@ static cplx data_weight(const or_problem *p, const double *c, int d, int m, int 
 
 static void mode_components_cached(const or_problem *p, const double *c, const cplx *hm,
                                    int64_t i, int64_t e, cplx *z, cplx *H) {
-  const int M = p->n_modes, D = p->n_det, B = p->n_bins;
+  const int M = p->n_modes, D = p->n_det, B = p->n_bins, NP = n_pol_of(p), J = M * NP;
   for (int m = 0; m < M; ++m) z[m] = 0.0;
   for (int m = 0; m < M * M; ++m) H[m] = 0.0;
   for (int d = 0; d < D; ++d) {
     double t = p->t[e * D + d];
-    /* <d_k | h_m T_k> summed over b, i.e. sum_b c_{d b} T h_m (real part taken later) */
-    for (int m = 0; m < M; ++m) {
-      cplx acc = 0.0;
-      for (int b = 0; b < B; ++b)
-        acc += data_weight(p, c, d, m, b) * cexp(-I * TWO_PI * p->f[b] * t) * ld_c(p->h, (i * M + m) * B + b);
-      z[m] += ld_c(p->R, (e * D + d) * M + m) * acc;
-    }
+    /* <d_k | h_{m q} T_k> summed over b, i.e. sum_b c_{d b} T h_{m q} (real part taken later) */
     for (int m = 0; m < M; ++m)
-      for (int mp = 0; mp < M; ++mp) {
-        cplx Rm = ld_c(p->R, (e * D + d) * M + m);
-        cplx Rmp = ld_c(p->R, (e * D + d) * M + mp);
-        H[m * M + mp] += Rm * conj(Rmp) * hm[(d * M + m) * M + mp];
+      for (int q = 0; q < NP; ++q) {
+        cplx acc = 0.0;
+        for (int b = 0; b < B; ++b)
+          acc += data_weight(p, c, d, m, b) * cexp(-I * TWO_PI * p->f[b] * t) * hval(p, i, m, q, b);
+        z[m] += resp(p, e, d, m, q) * acc;
       }
+    for (int m = 0; m < M; ++m)
+      for (int mp = 0; mp < M; ++mp)
+        for (int q = 0; q < NP; ++q)
+          for (int qp = 0; qp < NP; ++qp)
+            H[m * M + mp] += resp(p, e, d, m, q) * conj(resp(p, e, d, mp, qp)) *
+                             hm[((int64_t)d * J + m * NP + q) * J + mp * NP + qp];
   }
 }
 
 int or_mode_components(const or_problem *p, const double *c, const double *omega, int64_t i,
                        int64_t e, double *z_out, double *H_out) {
   const int M = p->n_modes, D = p->n_det;
-  cplx *hm = malloc(sizeof(cplx) * (size_t)D * M * M);
+  const int J = M * n_pol_of(p);
+  cplx *hm = malloc(sizeof(cplx) * (size_t)D * J * J);
   cplx *z = malloc(sizeof(cplx) * (size_t)M);
   cplx *H = malloc(sizeof(cplx) * (size_t)M * M);
   if (!hm || !z || !H) {
@@ -494,7 +508,8 @@ static void *job_run(void *arg) {
   or_job *j = (or_job *)arg;
   const or_problem *p = j->p;
   const int M = p->n_modes, D = p->n_det, np = p->n_phi;
-  cplx *hm = malloc(sizeof(cplx) * (size_t)D * M * M);
+  const int J = M * n_pol_of(p);
+  cplx *hm = malloc(sizeof(cplx) * (size_t)D * J * J);
   cplx *z = malloc(sizeof(cplx) * (size_t)M);
   cplx *H = malloc(sizeof(cplx) * (size_t)M * M);
   double *dh = malloc(sizeof(double) * (size_t)np);

@@ -40,6 +40,13 @@ typedef struct or_problem {
    * <h_m|h_m'>_d = sum_b W^{<h|h>}_{d m m' b} h_m(f_b) h_m'^*(f_b) (Eqs. d_h, h_h).
    * Route O2 only (the weights are per mode). */
   const double *rb_dh, *rb_hh;
+  /* polarisation-resolved (precessing) bank (Sec. IV.A general case,
+   * Eqs. dh_ieo, hh_ieo with the index p): n_pol = 2, h complex [I][M][2][B]
+   * (h_{i m p}, p = +, x), F [E][D][2] real antenna patterns F_{e d p} replacing R:
+   * the strain is sum_{m,p} F_{edp} h_{imp} e^{i m phi} T.  n_pol = 0 or 1: h [I][M][B]
+   * and R as above.  Relative binning applies to n_pol <= 1 only. */
+  int n_pol;
+  const double *F;
 } or_problem;
 
 /* Per-(i,e) outputs. */

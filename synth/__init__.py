@@ -182,6 +182,7 @@ class Extrinsic:
     psi: np.ndarray
     cos_iota: np.ndarray
     t_geo: np.ndarray
+    F: np.ndarray = None   # [E, D, 2] real antenna patterns (F+, Fx), for polarisation-resolved banks
 
 
 @dataclasses.dataclass
@@ -263,8 +264,12 @@ def extrinsic_from_params(lat, lon, psi, cos_iota, t_geo, n_det, bank: Bank, ln_
         t[:, d] = t_geo - (n_src @ r) / C_LIGHT
         fp, fc = antenna_patterns(tensor, lat, lon, psi)
         R[:, d, :] = fp[:, None] * kp + fc[:, None] * kx
+    F = np.empty((n_ext, n_det, 2))
+    for d in range(n_det):
+        _, tensor = detector_geometry(DET_ORDER[d])
+        F[:, d, 0], F[:, d, 1] = antenna_patterns(tensor, lat, lon, psi)
     return Extrinsic(t=t, R=R, ln_w=np.asarray(ln_w, dtype=np.float64), lat=lat, lon=lon,
-                     psi=psi, cos_iota=cos_iota, t_geo=t_geo)
+                     psi=psi, cos_iota=cos_iota, t_geo=t_geo, F=F)
 
 
 def signal_at_detectors(h_modes, R_dm, t_d, f, mode_m, phi, u):
@@ -570,6 +575,63 @@ def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.
                                                 cos_iota=float(e1.cos_iota[0]), t_det=e1.t[0].copy()))
     return RBWorkload(bank=bank, ext=ext, event=ev, f_fine=f_fine, dff=dff, psd_fine=psd_fine, data_fine=data_fine,
                       h0_fine=h0, t0=e1.t[0].copy(), nodes=nodes, ratios=ratios, amp22=amp22)
+
+
+# ----------------------------------------------------------------------------
+# polarisation-resolved (precessing) banks: h_{i m p}(f), p = +, x
+# ----------------------------------------------------------------------------
+def precessing_bank(base: Bank, rng, wobble_max=0.5):
+    """A polarisation-resolved bank from a non-precessing one: each row's
+    inclination wobbles with frequency, iota_i(f) = iota0_i + a_i sin(2 pi
+    ln(f/f_0) / L_i) (a_i ~ U[0, wobble_max] rad, L_i ~ U[0.5, 2], cos iota0 ~
+    U[-1, 1]), standing in for the spin-precession of the paper's general case
+    (Sec. IV.A): h_{i m p}(f) = K_{m p}(iota_i(f)) h_{i m}(f), whose + / x ratio
+    is not fixed per mode.  Returns h [I, M, 2, B] and iota0 [I]."""
+    I, M, B = base.h.shape
+    iota0 = np.arccos(rng.uniform(-1.0, 1.0, I))
+    amp = rng.uniform(0.0, wobble_max, I)
+    per = rng.uniform(0.5, 2.0, I)
+    x = np.log(base.f / base.f[0])
+    iota = iota0[:, None] + amp[:, None] * np.sin(2.0 * np.pi * x[None, :] / per[:, None])
+    h = np.empty((I, M, 2, B), dtype=np.complex128)
+    for k in range(M):
+        kp, kx = polarisation_factors(int(base.mode_l[k]), int(base.mode_m[k]), iota)
+        h[:, k, 0, :] = kp * base.h[:, k, :]
+        h[:, k, 1, :] = kx * base.h[:, k, :]
+    return h, iota0
+
+
+def make_precessing_workload(n_int, n_ext, n_det, n_modes, n_bins, snr=15.0, seed=0, n_phi=32, noise=True,
+                             insert_injection=False, ln_w="zero"):
+    """Bank (polarisation-resolved), extrinsic samples (with F) and one event
+    whose signal is sum_{m,p} F_{dp} h_{i* m p} e^{i m phi} T_d (Eq. h_k with the
+    polarisation index), scaled to network SNR `snr`, plus noise.
+    insert_injection: the injected sample is extrinsic sample 0 at phase 0."""
+    rng = np.random.default_rng(seed)
+    base = make_bank(rng, n_int, n_modes, n_bins, ln_w=ln_w)
+    hp, _ = precessing_bank(base, rng)
+    bank = Bank(f=base.f, w=base.w, mode_m=base.mode_m, mode_l=base.mode_l, h=hp, ln_w=base.ln_w,
+                mchirp=base.mchirp)
+    ext = make_extrinsic(rng, n_ext, n_det, base, ln_w=ln_w)
+    psd = np.stack([analytic_psd(bank.f, PSD_SCALES[d]) for d in range(n_det)])
+    inj_i = int(rng.integers(0, n_int))
+    if insert_injection:
+        Fd, td, phi = ext.F[0], ext.t[0], 0.0
+    else:
+        e1 = make_extrinsic(rng, 1, n_det, base)
+        Fd, td, phi = e1.F[0], e1.t[0], float(rng.uniform(0.0, 2.0 * np.pi))
+    ph = np.exp(1j * bank.mode_m * phi)
+    shift = np.exp(-2j * np.pi * bank.f[None, :] * td[:, None])
+    unit = np.einsum("mpb,dp,m->db", hp[inj_i], Fd, ph) * shift
+    u_inj = snr / math.sqrt(network_norm(unit, psd, bank.w))
+    data = u_inj * unit
+    if noise:
+        sigma = np.sqrt(psd / (4.0 * bank.w[None, :]))
+        data = data + sigma * (rng.standard_normal(sigma.shape) + 1j * rng.standard_normal(sigma.shape))
+    ev = Event(psd=psd, data=data, u_min=default_u_min(base, n_det), n_phi=int(n_phi),
+               injection=dict(i=inj_i, e=0 if insert_injection else None, phi=phi, u=u_inj, snr=snr,
+                              cos_iota=None, t_det=np.array(td)))
+    return Workload(bank=bank, ext=ext, event=ev)
 
 
 def named_workload(name: str, **overrides):
