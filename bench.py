@@ -16,7 +16,7 @@ reduction.  The K timed events are submitted together; the runtime runs up to
 four at once.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload event|batch64|serve|presel|rb|samples]
+                  [--workload event|batch64|serve|presel|rb|samples|precessing]
 
 --workload batch64: 64 events (extrinsic counts from {512, ..., 4096}, 2-3
 detectors, SNR 8-40) over one shared 262,144-row bank, submitted as one batch:
@@ -35,6 +35,9 @@ samples near it; a step is one dotpe_rb_weights call plus one event.
 --workload samples: posterior samples (Eq. posterior_element resampling with
 App. C distance draws) of the main event stored with DOTPE_FLAG_STORE_LNL;
 a step is one dotpe_posterior_samples call of 65,536 samples.
+--workload precessing: a polarisation-resolved bank (Sec. IV.A general case,
+h_{imp} with both polarisations, antenna patterns per sample) of 16,384 rows x
+4,096 samples, 3 detectors, 4 modes, 512 bins, in FP32; a step is one event.
 
 Under torchrun (N > 1) every rank runs its own independent events on its own
 GPU (events do not share data: weak scaling, no collective on the data path);
@@ -568,6 +571,121 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
     return line
 
 
+# FP32 pipe of one GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) at the 2,070 MHz maximum SM clock
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def bench_precessing(args, dp, ctx_factory, torch, dev):
+    """Polarisation-resolved (precessing) bank, Sec. IV.A general case: one FP32
+    event per step over a 16,384-row bank h_{imp} (both polarisations) x 4,096
+    extrinsic samples with antenna patterns F_{edp}."""
+    import oracle
+    import synth
+    D, M, B = 3, 4, 512
+    I = args.n_int if "--n-int" in sys.argv else 16384
+    E = args.n_ext
+    wl = synth.make_precessing_workload(I, E, D, M, B, snr=15.0, seed=8, n_phi=N_PHI)
+    ctx = ctx_factory()
+    bank = wl.bank
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+
+    def to_dev(a):
+        a = np.ascontiguousarray(a)
+        if np.iscomplexobj(a):
+            a = a.view(np.float64)
+        return torch.from_numpy(a.copy()).to(dev)
+
+    d_psd, d_data, d_t, d_F, d_lw = (to_dev(wl.event.psd), to_dev(wl.event.data), to_dev(wl.ext.t),
+                                     to_dev(wl.ext.F), to_dev(wl.ext.ln_w))
+
+    def submit(stream=None, psd=d_psd, data=d_data, t=d_t, F=d_F, lw=d_lw):
+        return dp.dotpe_event_submit(ctx, bid, 0, I, psd, data, t, None, lw, n_phi=N_PHI, u_min=wl.event.u_min,
+                                     cut_delta=args.cut, precision="fp32", stream=stream, F=F)
+
+    def one(**kw):
+        eid = submit(**kw)
+        dp.dotpe_event_wait(ctx, eid, 600.0)
+        ev = dp.dotpe_evidence(ctx, eid)
+        _, st = dp.dotpe_event_poll(ctx, eid)
+        dp.dotpe_event_release(ctx, eid)
+        return ev, st
+
+    for _ in range(args.warmup):
+        one()
+    S = torch.cuda.Stream(device=dev)
+    sampler = ClockSampler(dev.index or 0)
+    torch.cuda.synchronize()
+    sampler.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ids = []
+    with torch.cuda.stream(S):
+        t0.record(S)
+        for _ in range(args.steps):
+            ids.append(submit(stream=S))
+        for eid in ids:
+            dp.dotpe_event_stream_wait(ctx, eid, S)
+        t1.record(S)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ev_ms = t0.elapsed_time(t1) / args.steps
+    evs, sts = [], []
+    for eid in ids:
+        evs.append(dp.dotpe_evidence(ctx, eid))
+        sts.append(dp.dotpe_event_poll(ctx, eid)[1])
+        dp.dotpe_event_release(ctx, eid)
+    # end to end: host inputs copied in, evidence read back, every step
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        one(psd=wl.event.psd, data=wl.event.data, t=wl.ext.t, F=wl.ext.F, lw=wl.ext.ln_w)
+    e2e_s = (time.perf_counter() - te) / args.steps
+    pairs = I * E
+    fused_ms = statistics.mean(st["fused_ms"] for st in sts)
+    # <d|h>: 8 flops per complex multiply-add over M modes x 2 polarisations x B bins;
+    # <h|h>: per detector 21 real multiply-adds of the row and column records
+    flops_per_pair = 8 * 2 * B * M + D * 2 * 21
+    achieved = flops_per_pair * pairs / (fused_ms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        P = oracle.OracleProblem(bank, wl.ext, wl.event)
+        cores = oracle.default_threads()
+        rng = np.random.default_rng(4322)
+        n = 600000
+        flat = np.sort(rng.choice(pairs, size=n, replace=False))
+        tc = time.perf_counter()
+        P.eval_pairs(flat // E, flat % E, n_threads=cores, threshold=evs[-1]["lnl_ml_threshold"])
+        dtc = time.perf_counter() - tc
+        cpu = {"value": n / dtc, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} uniform random (i,e) pairs (seed 4322), route O2 with polarisation-resolved "
+                         f"components, {N_PHI}-phase grid, distance marginal, {dtc:.1f} s"}
+    line = {
+        "metric": "(int x ext) lnL pairs/s", "value": pairs / (ev_ms * 1e-3), "unit": "pairs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ev_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": f"polarisation-resolved (precessing) bank: I={I} rows h_(i m p) x E={E} samples "
+                               f"with antenna patterns, D={D}, M={M}, B={B}, N_phi={N_PHI}, SNR 15",
+                   "precision": "fp32", "ml_cut_delta": args.cut, "fused_ms": fused_ms,
+                   "prep_ms": statistics.mean(st["prep_ms"] for st in sts),
+                   "marginalised_fraction": evs[-1]["n_marginalised"] / (pairs * N_PHI),
+                   "l2": f"inputs larger than L2 (FP32 bank {I * M * 2 * 2 * B * 4 / 1e9:.2f} GB, re-read every "
+                         "step)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "simt_fused_kernel (FP32 <d|h> GEMM over both polarisations + marginalisation)",
+                     "kernel_ms": fused_ms, "flops_per_pair": flops_per_pair,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz"},
+        "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
+                "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + wl.ext.t.nbytes
+                                          + wl.ext.F.nbytes + wl.ext.ln_w.nbytes),
+                "d2h_bytes_per_step": 96},
+        # prep (data weights, norm, extrinsic, G build, G pack), the fused kernel, the
+        # reduction (6); the bank's cross terms are cached from the warm-up
+        "gpu_launches": 12 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
+    }
+    dp.dotpe_bank_release(ctx, bid)
+    dp.dotpe_destroy(ctx)
+    return line
+
+
 def bench_samples(args, dp, ctx_factory, torch, dev):
     """Posterior samples of one stored 65,536 x 4,096 event; a step draws 65,536
     samples (the paper's N_s = N_eff/2 is reported beside it)."""
@@ -700,7 +818,7 @@ def main():
     ap.add_argument("--n-int", type=int, default=WORKLOAD["n_int"], help="bank rows (profiling runs)")
     ap.add_argument("--n-ext", type=int, default=WORKLOAD["n_ext"], help="extrinsic samples (profiling runs)")
     ap.add_argument("--workload", default="event",
-                    choices=["event", "batch64", "serve", "presel", "rb", "samples"])
+                    choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
     args = ap.parse_args()
@@ -738,6 +856,8 @@ def main():
             line = bench_rb(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         elif args.workload == "samples":
             line = bench_samples(args, dp, lambda: dp.dotpe_create(local), torch, dev)
+        elif args.workload == "precessing":
+            line = bench_precessing(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         else:
             line = bench_serve(args, dp, lambda: dp.dotpe_create(local, max_batch=args.max_batch), torch, dev)
         print(json.dumps(line), flush=True)

@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define DOTPE_ABI_VERSION 4
+#define DOTPE_ABI_VERSION 5
 
 /* ---- status codes ------------------------------------------------------ */
 #define DOTPE_OK 0
@@ -117,7 +117,14 @@ typedef struct dotpe_config {
  *   factors K_{i m p} (p = +, x) of each row, h_{i m p} = K_{i m p} h_{i m}
  *   (App. B's h_impb, with the inclination an intrinsic parameter as in
  *   Sec. IV.A).  Only dotpe_preselect reads them; a bank without them cannot be
- *   pre-selected.  Kept on the device as FP32. */
+ *   pre-selected.  Kept on the device as FP32.
+ * n_pol: 0 or 1 for the mode bank above; 2 for a polarisation-resolved bank
+ *   (the general, precessing case of Sec. IV.A, Eqs. dh_ieo and hh_ieo with
+ *   the polarisation index p): h is then [n_int][n_modes][2][n_bins] complex,
+ *   h_{i m p b} with p = +, x, and each extrinsic sample carries real antenna
+ *   patterns F_{e d p} (dotpe_event_desc.F) in place of R.  Such a bank is
+ *   evaluated in DOTPE_PREC_FP32 only; dotpe_preselect, relative binning and
+ *   dotpe_posterior_samples return DOTPE_E_UNSUPPORTED for it. */
 typedef struct dotpe_bank_desc {
   int64_t n_int;
   int n_modes;
@@ -129,6 +136,7 @@ typedef struct dotpe_bank_desc {
   int h_dtype;
   const double *ln_w_int;
   const double *pol;
+  int n_pol;
 } dotpe_bank_desc;
 
 /* One event: data, PSD, extrinsic samples (Sec. IV.B-E).
@@ -157,7 +165,13 @@ typedef struct dotpe_bank_desc {
  *   W^{<h|h>}_{d m m' b}.  psd and data are then not read (may be NULL); the
  *   cross-term cache is keyed by the <h|h> weights; the mixed-precision
  *   screening margin takes max_m sum_{d,b} |W^{<d|h>}|^2 / W^{<h|h>}_{mm} in
- *   place of <d|d>. */
+ *   place of <d|d>.
+ * F [n_ext][n_det][2] (double, host or device): antenna patterns F_{e d p}
+ *   (p = +, x) of each sample, read for a polarisation-resolved bank (n_pol = 2),
+ *   which then ignores R (may be NULL).  A mode bank ignores F (may be NULL).
+ * Without relative binning n_det * n_bins <= 58,112 (the <h|h> quadrature
+ *   weights of all detectors are staged in 227 KB of shared memory); larger
+ *   events return DOTPE_E_UNSUPPORTED. */
 typedef struct dotpe_event_desc {
   uint64_t bank_id;
   int64_t i0, i1;
@@ -177,6 +191,7 @@ typedef struct dotpe_event_desc {
   int64_t block_rows;
   const double *rb_dh;
   const double *rb_hh;
+  const double *F;
 } dotpe_event_desc;
 
 typedef struct dotpe_event_stats {

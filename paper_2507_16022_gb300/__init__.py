@@ -66,7 +66,7 @@ class dotpe_bank_desc(ctypes.Structure):
     _fields_ = [("n_int", ctypes.c_int64), ("n_modes", ctypes.c_int),
                 ("mode_m", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int),
                 ("f", _dp), ("w_quad", _dp), ("h", ctypes.c_void_p), ("h_dtype", ctypes.c_int),
-                ("ln_w_int", _dp), ("pol", _dp)]
+                ("ln_w_int", _dp), ("pol", _dp), ("n_pol", ctypes.c_int)]
 
 
 class dotpe_event_desc(ctypes.Structure):
@@ -75,7 +75,7 @@ class dotpe_event_desc(ctypes.Structure):
                 ("t", _dp), ("R", _dp), ("ln_w_ext", _dp), ("n_phi", ctypes.c_int),
                 ("u_min", ctypes.c_double), ("cut_delta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("block_rows", ctypes.c_int64), ("rb_dh", _dp), ("rb_hh", _dp)]
+                ("block_rows", ctypes.c_int64), ("rb_dh", _dp), ("rb_hh", _dp), ("F", _dp)]
 
 
 class dotpe_presel_desc(ctypes.Structure):
@@ -212,14 +212,16 @@ def dotpe_device_info(ctx):
 
 def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None, pol=None):
     """h: [I, M, B] complex128/complex64 numpy array, or a torch tensor on the device
-    (complex128/complex64, contiguous).  pol: optional [I, M, 2] complex
-    polarisation factors K_{imp} (needed by dotpe_preselect)."""
+    (complex128/complex64, contiguous); [I, M, 2, B] is a polarisation-resolved
+    (precessing) bank h_{impb}, whose events take antenna patterns F.  pol:
+    optional [I, M, 2] complex polarisation factors K_{imp} (needed by
+    dotpe_preselect)."""
     L = load()
     keep = []
     if hasattr(h, "data_ptr"):
         import torch
         dtype = DOTPE_C128 if h.dtype == torch.complex128 else DOTPE_C64
-        I, M, B = h.shape
+        I, M, B = h.shape[0], h.shape[1], h.shape[-1]
         hp = ctypes.c_void_p(h.data_ptr())
     else:
         if h.dtype == np.complex64:
@@ -228,9 +230,12 @@ def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None, pol=None):
         else:
             h = _host_c128(h)
             dtype = DOTPE_C128
-        I, M, B = h.shape
+        I, M, B = h.shape[0], h.shape[1], h.shape[-1]
         hp = ctypes.c_void_p(h.ctypes.data)
         keep.append(h)
+    if len(h.shape) == 4 and h.shape[2] != 2:
+        raise ValueError(f"a polarisation-resolved bank is [I, M, 2, B], got {tuple(h.shape)}")
+    n_pol = 2 if len(h.shape) == 4 else 1
     mm = np.ascontiguousarray(mode_m, dtype=np.int32)
     f = np.ascontiguousarray(f, dtype=np.float64)
     w = np.ascontiguousarray(w_quad, dtype=np.float64)
@@ -239,7 +244,7 @@ def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None, pol=None):
     if pl is not None and pl.shape != (I, M, 2):
         raise ValueError(f"pol has shape {pl.shape}, expected {(I, M, 2)}")
     desc = dotpe_bank_desc(I, M, mm.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), B, _ptr(f), _ptr(w),
-                           hp, dtype, _ptr(lw), None if pl is None else _ptr(pl.view(np.float64)))
+                           hp, dtype, _ptr(lw), None if pl is None else _ptr(pl.view(np.float64)), n_pol)
     bid = ctypes.c_uint64()
     _check(L.dotpe_bank_load(ctx, ctypes.byref(desc), ctypes.byref(bid)))
     return bid.value
@@ -250,7 +255,7 @@ def dotpe_bank_release(ctx, bank_id):
 
 
 def _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
-                cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0, rb=None):
+                cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0, rb=None, F=None):
 
     def arr(a, cplx=False):
         if a is None:
@@ -270,18 +275,20 @@ def _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32,
         st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     rbd, rbh = (None, None) if rb is None else (arr(rb[0], True), arr(rb[1], True))
     return dotpe_event_desc(bank_id, i0, i1, D, arr(psd), arr(data, True), E, arr(t), arr(R, True),
-                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st, block_rows, rbd, rbh)
+                            arr(ln_w_ext), n_phi, u_min, cut_delta, prec, flags, st, block_rows, rbd, rbh,
+                            arr(F))
 
 
 def dotpe_event_submit(ctx, bank_id, i0, i1, psd, data, t, R, ln_w_ext=None, n_phi=32, u_min=1.0,
-                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0, rb=None):
+                       cut_delta=0.0, precision="bf16x3", flags=0, stream=None, block_rows=0, rb=None, F=None):
     """psd [D,B], data [D,B] complex, t [E,D], R [E,D,M] complex, ln_w_ext [E]: numpy (host)
     or torch tensors (host or device; complex tensors as float64 views are accepted).
     block_rows: 0, or a multiple of 128 to stream the slice through in bank blocks.
-    rb: optional (w_dh [D,M,B], w_hh [D,M,M,B]) relative-binning weights (psd, data may be None)."""
+    rb: optional (w_dh [D,M,B], w_hh [D,M,M,B]) relative-binning weights (psd, data may be None).
+    F: [E,D,2] real antenna patterns, for a polarisation-resolved bank (R may then be None)."""
     keep = []
     desc = _event_desc(keep, bank_id, i0, i1, psd, data, t, R, ln_w_ext, n_phi, u_min, cut_delta,
-                       precision, flags, stream, block_rows, rb)
+                       precision, flags, stream, block_rows, rb, F)
     eid = ctypes.c_uint64()
     _check(load().dotpe_event_submit(ctx, ctypes.byref(desc), ctypes.byref(eid)))
     return eid.value

@@ -13,6 +13,7 @@ namespace dotpe {
 constexpr int MAXM = 4;    // modes per waveform
 constexpr int MAXD = 3;    // detectors (H, L, V)
 constexpr int REC = 16;    // floats per (row or column, detector) cross-term record
+constexpr int REC_P = 24;  // row record of a polarisation-resolved bank (21 used, see cross_terms_pol_kernel)
 constexpr int MAXPHI = 128;
 constexpr int NPAIR = 6;   // mode pairs (a > b) for MAXM = 4
 
@@ -59,6 +60,7 @@ struct EpiParams {
   float *ml_tile;           // optional [n_int][n_ext]
   int *status;
   int gemm_only;
+  int n_pol;                // 2: polarisation-resolved bank (row records REC_P, column records F_p F_p')
   int test_stall;           // producer withholds its first stage (failure-path test)
   unsigned long long wait_ns;  // bound of every mbarrier wait
 };

@@ -96,6 +96,7 @@ struct Bank {
   int64_t I = 0;
   int M = 0, B = 0, Kpad = 0;
   int mode_m[MAXM] = {0, 0, 0, 0};
+  int n_pol = 1;  // 2: polarisation-resolved bank, rows [Re h+ | Im h+ | Re hx | Im hx | pad]
   double *f = nullptr, *w = nullptr, *lw = nullptr;  // device
   float *master = nullptr;                           // [M][I][Kpad]
   __nv_bfloat16 *bf = nullptr;                       // [2][M][I][Kpad] hi, lo
@@ -129,6 +130,7 @@ struct Event {
   double *psd = nullptr, *t = nullptr, *lwe = nullptr;
   double2 *data = nullptr, *R = nullptr;
   double2 *rb_dh = nullptr, *rb_hh = nullptr;  // relative-binning weights (App. A), or null
+  double *F = nullptr;  // [E][D][2] antenna patterns (polarisation-resolved bank), or null
   void *in_stage = nullptr;  // pinned host staging of host inputs
   size_t stage_bytes = 0;
   cudaEvent_t ev_inputs = nullptr, ev_start = nullptr, ev_end = nullptr, ev_k0 = nullptr, ev_k1 = nullptr,
@@ -242,12 +244,12 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.tl = c.take<float>(E * D);
   L.Rf = c.take<float2>(E * D * M);
   L.qx = c.take<float>(E * D * REC);
-  L.G32 = c.take<float2>(M * E * B);
+  L.G32 = c.take<float2>(M * E * B * (b.n_pol == 2 ? 2 : 1));
   L.gmax = c.take<float>(1);
   L.gscale = c.take<float>(1);
   L.sqrt_dd = c.take<float>(1);
   L.gpack = c.take<uint8_t>((size_t)L.pack_planes * M * 2 * E * Kp * elem);
-  L.mx = c.take<float>(NI * D * REC);
+  L.mx = c.take<float>(NI * D * (b.n_pol == 2 ? REC_P : REC));
   L.tile_part = c.take<float4>(T);
   L.tile_ml = c.take<float>(T);
   L.tile_arg = c.take<long long>(T);
@@ -347,6 +349,7 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
   pa.D = e.D; pa.B = b.B; pa.M = b.M; pa.Kpad = b.Kpad; pa.E = e.NE;
   pa.f = b.f; pa.w = b.w; pa.psd = e.psd; pa.data = e.data; pa.t = e.t; pa.R = e.R;
   pa.rb_dh = e.rb_dh; pa.rb_hh = e.rb_hh;
+  pa.n_pol = b.n_pol; pa.F = e.F;
   pa.c = (float2 *)(scr + L.c);
   pa.omega = (float *)(scr + L.omega);
   pa.fh = (float *)(scr + L.fh);
@@ -369,6 +372,7 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
   P.n_modes = b.M;
   P.n_det = e.D;
   P.n_phi = e.nphi;
+  P.n_pol = b.n_pol;
   for (int m = 0; m < MAXM; ++m) P.mode_m[m] = m < b.M ? b.mode_m[m] : 0;
   P.npair = b.M * (b.M - 1) / 2;
   {
@@ -464,7 +468,10 @@ static int event_begin(Event &e, EventRun &R, cudaStream_t st) {
 static void event_block(dotpe_ctx *ctx, Event &e, EventRun &R, int64_t r0, int64_t nr, cudaStream_t st) {
   Bank &b = *e.bank;
   if (e.xent) {
-    R.P.mx = e.xent->mx + (e.i0 + r0) * e.D * REC;
+    R.P.mx = e.xent->mx + (e.i0 + r0) * e.D * (b.n_pol == 2 ? REC_P : REC);
+  } else if (b.n_pol == 2) {
+    launch_cross_terms_pol(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.mode_m, b.master, R.pa.omega,
+                           (float *)(R.scr + R.L.mx), ctx->n_sms, st);
   } else {
     launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, e.rb_hh,
                        (float *)(R.scr + R.L.mx), ctx->n_sms, st);
@@ -523,7 +530,7 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
     sg.Bm = (const float *)R.pa.gpack;
     sg.I_bank = b.I;
     sg.Kpad = b.Kpad;
-    sg.K = 2 * b.B;
+    sg.K = 2 * b.n_pol * b.B;
     launch_simt(sg, R.P, st);
     return DOTPE_OK;
   }
@@ -622,14 +629,18 @@ static int xcache_build(dotpe_ctx *ctx, Bank &b, uint64_t key, int D, const floa
   XEntry *x = new XEntry();
   x->key = key;
   x->D = D;
-  x->bytes = (size_t)b.I * D * REC * sizeof(float);
+  const int rec = (b.n_pol == 2) ? REC_P : REC;
+  x->bytes = (size_t)b.I * D * rec * sizeof(float);
   if (cudaMallocAsync((void **)&x->mx, x->bytes, st) != cudaSuccess) {
     cudaGetLastError();
     delete x;
-    return fail(DOTPE_E_NOMEM, "cross-term records (%zu bytes)", (size_t)b.I * D * REC * sizeof(float));
+    return fail(DOTPE_E_NOMEM, "cross-term records (%zu bytes)", (size_t)b.I * D * rec * sizeof(float));
   }
   CUDA_OR_FAIL(cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming));
-  launch_cross_terms(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.master, omega, rb_hh, x->mx, ctx->n_sms, st);
+  if (b.n_pol == 2)
+    launch_cross_terms_pol(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.mode_m, b.master, omega, x->mx, ctx->n_sms, st);
+  else
+    launch_cross_terms(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.master, omega, rb_hh, x->mx, ctx->n_sms, st);
   CUDA_OR_FAIL(cudaEventRecord(x->ready, st));
   ctx->used += x->bytes;
   b.xcache.push_back(x);
@@ -1062,6 +1073,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   Bank &b = *bit->second;
   if (!b.pol) return fail(DOTPE_E_INVALID, "bank %llu was loaded without polarisation factors (pol)",
                           (unsigned long long)d->bank_id);
+  if (b.n_pol == 2) return fail(DOTPE_E_UNSUPPORTED, "pre-selection of a polarisation-resolved bank");
   if (d->i0 < 0 || d->i1 <= d->i0 || d->i1 > b.I)
     return fail(DOTPE_E_INVALID, "slice [%lld,%lld) of %lld rows", (long long)d->i0, (long long)d->i1, (long long)b.I);
   if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
@@ -1337,6 +1349,7 @@ static int samples_locked(dotpe_ctx *ctx, Event &e, int64_t n, const double *uni
   Bank &b = *e.bank;
   if (!(e.flags & DOTPE_FLAG_STORE_LNL))
     return fail(DOTPE_E_INVALID, "posterior samples need an event run with DOTPE_FLAG_STORE_LNL");
+  if (b.n_pol == 2) return fail(DOTPE_E_UNSUPPORTED, "posterior samples of a polarisation-resolved bank");
   if (n < 1 || n > (1ll << 24)) return fail(DOTPE_E_INVALID, "n=%lld not in 1..2^24", (long long)n);
   if (!uniforms) return fail(DOTPE_E_INVALID, "null uniforms");
   cudaStream_t st = ctx->main_stream;
@@ -1560,6 +1573,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
     return fail(DOTPE_E_INVALID, "bank shape: n_int=%lld n_modes=%d n_bins=%d", (long long)d->n_int, d->n_modes,
                 d->n_bins);
   if (d->h_dtype != DOTPE_C128 && d->h_dtype != DOTPE_C64) return fail(DOTPE_E_INVALID, "h_dtype");
+  if (d->n_pol < 0 || d->n_pol > 2) return fail(DOTPE_E_INVALID, "n_pol=%d not in 0..2", d->n_pol);
   for (int m = 0; m < d->n_modes; ++m) {
     if (d->mode_m[m] < 1 || d->mode_m[m] > 4) return fail(DOTPE_E_INVALID, "mode_m[%d]=%d not in 1..4", m, d->mode_m[m]);
     if (m > 0 && d->mode_m[m] <= d->mode_m[m - 1]) return fail(DOTPE_E_INVALID, "mode_m must increase");
@@ -1570,12 +1584,15 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   b->I = d->n_int;
   b->M = d->n_modes;
   b->B = d->n_bins;
-  b->Kpad = (int)(((2 * (int64_t)d->n_bins + 63) / 64) * 64);
+  b->n_pol = (d->n_pol == 2) ? 2 : 1;
+  b->Kpad = (int)(((2 * b->n_pol * (int64_t)d->n_bins + 63) / 64) * 64);
   for (int m = 0; m < d->n_modes; ++m) b->mode_m[m] = d->mode_m[m];
   const size_t nel = (size_t)b->M * b->I * b->Kpad;
   Carver c;
   size_t o_f = c.take<double>(b->B), o_w = c.take<double>(b->B), o_lw = c.take<double>(b->I);
-  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(2 * nel);
+  // a polarisation-resolved bank runs in FP32 only: no bf16/fp16 operand planes
+  const size_t nplane = (b->n_pol == 2) ? 0 : 2 * nel;
+  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(nplane), o_hf = c.take<__half>(nplane);
   size_t o_scal = c.take<float>(4);
   size_t o_pol = d->pol ? c.take<float2>((size_t)b->I * b->M * 2) : 0;
   b->bytes = c.off;
@@ -1593,8 +1610,8 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   b->w = (double *)(base + o_w);
   b->lw = d->ln_w_int ? (double *)(base + o_lw) : nullptr;
   b->master = (float *)(base + o_master);
-  b->bf = (__nv_bfloat16 *)(base + o_bf);
-  b->hf = (__half *)(base + o_hf);
+  b->bf = nplane ? (__nv_bfloat16 *)(base + o_bf) : nullptr;
+  b->hf = nplane ? (__half *)(base + o_hf) : nullptr;
   float *scal = (float *)(base + o_scal);  // [0] amax, [1] a_scale, [2] status
   b->pol = d->pol ? (float2 *)(base + o_pol) : nullptr;
   cudaStream_t st = ctx->main_stream;
@@ -1627,7 +1644,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
     if (rc == DOTPE_OK) check(cudaMemcpy(b->pol, pf.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
   }
   // stream the waveforms through a device staging buffer in row chunks
-  const size_t row_bytes = (size_t)b->M * b->B * (d->h_dtype == DOTPE_C128 ? 16 : 8);
+  const size_t row_bytes = (size_t)b->M * b->n_pol * b->B * (d->h_dtype == DOTPE_C128 ? 16 : 8);
   const bool hdev = is_device_ptr(d->h);
   int64_t chunk = (int64_t)((256u << 20) / row_bytes);
   if (chunk < 1) chunk = 1;
@@ -1647,10 +1664,10 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
       check(cudaMemcpyAsync(stage, pin, (size_t)rows * row_bytes, cudaMemcpyHostToDevice, st));
       dsrc = stage;
     }
-    launch_bank_to_master(rows, r0, b->I, b->M, b->B, b->Kpad, dsrc, d->h_dtype, b->master, &scal[0],
+    launch_bank_to_master(rows, r0, b->I, b->M, b->B, b->Kpad, b->n_pol, dsrc, d->h_dtype, b->master, &scal[0],
                           (int *)&scal[2], st);
   }
-  launch_master_to_planes((int64_t)nel, b->master, &scal[0], b->bf, b->hf, &scal[1], st);
+  if (nplane) launch_master_to_planes((int64_t)nel, b->master, &scal[0], b->bf, b->hf, &scal[1], st);
   check(cudaGetLastError());
   check(cudaStreamSynchronize(st));
   if (stage) cudaFree(stage);
@@ -1709,8 +1726,16 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   if (d->n_phi < 1 || d->n_phi > MAXPHI) return fail(DOTPE_E_INVALID, "n_phi=%d not in 1..%d", d->n_phi, MAXPHI);
   if (!(d->u_min > 0.0) || !std::isfinite(d->u_min)) return fail(DOTPE_E_INVALID, "u_min must be > 0");
   const bool rb = d->rb_dh || d->rb_hh;
+  const bool pol = (b->n_pol == 2);
   if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
-  if ((!rb && (!d->psd || !d->data)) || !d->t || !d->R) return fail(DOTPE_E_INVALID, "null input array");
+  if ((!rb && (!d->psd || !d->data)) || !d->t || (pol ? !d->F : !d->R))
+    return fail(DOTPE_E_INVALID, pol ? "null input array (a polarisation-resolved bank needs F)" : "null input array");
+  if (pol && d->precision != DOTPE_PREC_FP32)
+    return fail(DOTPE_E_UNSUPPORTED, "polarisation-resolved banks run in FP32 only (the tensor-core variant is not built)");
+  if (pol && rb) return fail(DOTPE_E_UNSUPPORTED, "relative binning with a polarisation-resolved bank");
+  if (!rb && (size_t)d->n_det * b->B * sizeof(float) > 227 * 1024)
+    return fail(DOTPE_E_UNSUPPORTED, "n_det * n_bins = %lld: the <h|h> weights exceed shared memory",
+                (long long)d->n_det * b->B);
   if (d->precision < DOTPE_PREC_FP32 || d->precision > DOTPE_PREC_MIXED)
     return fail(DOTPE_E_INVALID, "precision %d", d->precision);
   if (d->block_rows < 0 || d->block_rows % TC_TI != 0)
@@ -1739,6 +1764,7 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   size_t o_psd = c.take<double>(D * B), o_data = c.take<double2>(D * B), o_t = c.take<double>(NE * D);
   size_t o_R = c.take<double2>(NE * D * M), o_lw = c.take<double>(NE);
   size_t o_rbd = c.take<double2>(rb ? D * M * B : 0), o_rbh = c.take<double2>(rb ? D * M * M * B : 0);
+  size_t o_F = c.take<double>(pol ? NE * D * 2 : 0);
   e->in_bytes = c.off;
   if (need + e->in_bytes + b->bytes > ctx->budget) {
     delete e;
@@ -1768,11 +1794,13 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
     e->rb_dh = (double2 *)(ib + o_rbd);
     e->rb_hh = (double2 *)(ib + o_rbh);
   }
+  if (pol) e->F = (double *)(ib + o_F);
   struct Piece { const void *src; void *dst; size_t n; };
-  Piece pieces[7] = {{d->psd, e->psd, d->psd ? (size_t)(D * B * 8) : 0},
+  Piece pieces[8] = {{d->psd, e->psd, d->psd ? (size_t)(D * B * 8) : 0},
                      {d->data, e->data, d->data ? (size_t)(D * B * 16) : 0},
                      {d->t, e->t, (size_t)(NE * D * 8)},
-                     {d->R, e->R, (size_t)(NE * D * M * 16)},
+                     {d->R, e->R, (!pol && d->R) ? (size_t)(NE * D * M * 16) : 0},
+                     {d->F, e->F, pol ? (size_t)(NE * D * 2 * 8) : 0},
                      {d->ln_w_ext, e->lwe, d->ln_w_ext ? (size_t)(NE * 8) : 0},
                      {d->rb_dh, e->rb_dh, rb ? (size_t)(D * M * B * 16) : 0},
                      {d->rb_hh, e->rb_hh, rb ? (size_t)(D * M * M * B * 16) : 0}};
@@ -2018,6 +2046,7 @@ static int recompute_block(dotpe_ctx *ctx, Event &e, int64_t a, int64_t b, int64
   sub.data = e.data;
   sub.rb_dh = e.rb_dh;
   sub.rb_hh = e.rb_hh;
+  sub.F = e.F;
   sub.t = e.t + e0 * e.D;
   sub.R = e.R + e0 * e.D * e.bank->M;
   sub.lwe = e.lwe + e0;

@@ -41,6 +41,31 @@ __device__ __forceinline__ void fill_phase_tables(float2 *ph, const EpiParams &P
 // CONSEC: the modes' azimuthal numbers are consecutive, so pair (a, b) has delta = a - b.
 // Each detector accumulates into its own partial sums (independent FMA chains),
 // added at the end; records of detectors d >= n_det are zero.
+// <h|h> coefficients for a polarisation-resolved bank (Eqs. hh_ieo with the
+// polarisation index): H_{mm'} = sum_d sum_{pp'} F_p F_p' <h_{mp}|h_{m'p'}>_d.
+// The row record of detector d (mrow + d REC_P, read through the cache) holds
+// the overlaps grouped by delta = m - m': [X0, Y0, W0] for delta = 0 (real), then
+// for delta = 1..3 (X, Y, W) complex, with X = sum <h_a+|h_c+>, Y = sum (<h_a+|h_cx>
+// + <h_ax|h_c+>), W = sum <h_ax|h_cx>; the column record holds (F+^2, F+ Fx, Fx^2).
+__device__ __forceinline__ void hh_coeffs_pol(const float *__restrict__ mrow, const float *__restrict__ qrec,
+                                              const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
+  C0 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { Cr[k] = 0.f; Ci[k] = 0.f; }
+  for (int d = 0; d < P.n_det; ++d) {
+    const float *r = mrow + d * REC_P;
+    const float *q = qrec + d * REC;
+    const float q0 = q[0], q1 = q[1], q2 = q[2];
+    C0 += q0 * __ldg(r) + q1 * __ldg(r + 1) + q2 * __ldg(r + 2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float *g = r + 3 + 6 * k;
+      Cr[k] += q0 * __ldg(g) + q1 * __ldg(g + 2) + q2 * __ldg(g + 4);
+      Ci[k] += q0 * __ldg(g + 1) + q1 * __ldg(g + 3) + q2 * __ldg(g + 5);
+    }
+  }
+}
+
 template <bool CONSEC>
 __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const float *__restrict__ qrec,
                                           const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {

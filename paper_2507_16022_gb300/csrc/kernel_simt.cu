@@ -118,11 +118,12 @@ __global__ void __launch_bounds__(NT) simt_fused_kernel(SimtArgs g, EpiParams P)
     const int64_t i = i0 + rl;
     const bool vi = i < P.n_int;
     float mrec[MAXD * REC];
+    const bool pol = (P.n_pol == 2);
 #pragma unroll
     for (int q = 0; q < MAXD * REC; ++q) mrec[q] = 0.f;
 #pragma unroll
     for (int q = 0; q < MAXD * REC; ++q)
-      if (vi && q < P.n_det * REC) mrec[q] = __ldg(P.mx + i * P.n_det * REC + q);
+      if (vi && !pol && q < P.n_det * REC) mrec[q] = __ldg(P.mx + i * P.n_det * REC + q);
     const double lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -145,7 +146,8 @@ __global__ void __launch_bounds__(NT) simt_fused_kernel(SimtArgs g, EpiParams P)
           x = sx; x2 = sx; ml = 0.f;
         } else {
           float C0, Cr[3], Ci[3];
-          hh_coeffs<false>(mrec, &qs[el * MAXD * REC], P, C0, Cr, Ci);
+          if (pol) hh_coeffs_pol(P.mx + i * P.n_det * REC_P, &qs[el * MAXD * REC], P, C0, Cr, Ci);
+          else hh_coeffs<false>(mrec, &qs[el * MAXD * REC], P, C0, Cr, Ci);
           PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, ph);
           float lw = (float)(lwi + lwe[el]);
           x = pr.lsum + lw;

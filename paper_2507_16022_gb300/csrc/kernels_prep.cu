@@ -108,8 +108,11 @@ __global__ void data_norm_kernel(int D, int B, const double *__restrict__ w, con
   if (threadIdx.x == 0) *sqrt_dd = (float)sqrt(part[0]);
 }
 
+// F non-null (polarisation-resolved bank): the column record is (F+^2, F+ Fx, Fx^2)
+// of the real antenna patterns F [E][D][2] and R is not read.
 __global__ void prep_ext_kernel(int64_t E, int D, int M, const double *__restrict__ t,
-                                const double2 *__restrict__ R, float *__restrict__ th, float *__restrict__ tl,
+                                const double2 *__restrict__ R, const double *__restrict__ F,
+                                float *__restrict__ th, float *__restrict__ tl,
                                 float2 *__restrict__ Rf, float *__restrict__ qx, int *status) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= E * D) return;
@@ -118,6 +121,16 @@ __global__ void prep_ext_kernel(int64_t E, int D, int M, const double *__restric
   float h = (float)tv;
   th[k] = h;
   tl[k] = (float)(tv - (double)h);
+  if (F) {
+    double fp = F[2 * k], fx = F[2 * k + 1];
+    if (!isfinite(fp) || !isfinite(fx)) { atomicCAS(status, 0, DEV_E_NONFINITE); fp = 0.0; fx = 0.0; }
+    float *q = qx + k * REC;
+    q[0] = (float)(fp * fp);
+    q[1] = (float)(fp * fx);
+    q[2] = (float)(fx * fx);
+    for (int j = 3; j < REC; ++j) q[j] = 0.f;
+    return;
+  }
   float2 r[MAXM];
 #pragma unroll
   for (int m = 0; m < MAXM; ++m) {
@@ -191,6 +204,46 @@ __global__ void build_G_kernel(int64_t E, int D, int M, int B, const float *__re
   atomic_max_nonneg(gmax, a);
 }
 
+// Polarisation-resolved bank: G_{m p}[b, e] = sum_d F_{e d p} e^{-2 pi i f_b t_{e d}} c_{d m b},
+// G [M][2][E][B] (Eq. dh_ieo with the polarisation index; real antenna patterns).
+__global__ void build_G_pol_kernel(int64_t E, int D, int M, int B, const float *__restrict__ fh,
+                                   const float *__restrict__ fl, const float *__restrict__ th,
+                                   const float *__restrict__ tl, const float2 *__restrict__ c,
+                                   const double *__restrict__ F, float2 *__restrict__ G,
+                                   float *__restrict__ gmax) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= E * B) return;
+  int64_t e = k / B;
+  int b = (int)(k % B);
+  float2 g[MAXM][2];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) { g[m][0] = make_float2(0.f, 0.f); g[m][1] = make_float2(0.f, 0.f); }
+  float f_h = fh[b], f_l = fl[b];
+  for (int d = 0; d < D; ++d) {
+    const float2 T = shift_factor(f_h, f_l, th[e * D + d], tl[e * D + d]);
+    const float fp = (float)F[(e * D + d) * 2], fx = (float)F[(e * D + d) * 2 + 1];
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      if (m >= M) break;
+      const float2 cc = c[((int64_t)d * M + m) * B + b];
+      const float2 W = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
+      g[m][0].x += fp * W.x; g[m][0].y += fp * W.y;
+      g[m][1].x += fx * W.x; g[m][1].y += fx * W.y;
+    }
+  }
+  float a = 0.f;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    if (m >= M) break;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      G[(((int64_t)m * 2 + q) * E + e) * B + b] = g[m][q];
+      a = fmaxf(a, fmaxf(fabsf(g[m][q].x), fabsf(g[m][q].y)));
+    }
+  }
+  atomic_max_nonneg(gmax, a);
+}
+
 // fp16 operands are scaled to magnitudes up to 2^14 instead of 1: the five
 // exponent bits then keep hi normal down to ~4e-9 of the largest element and lo
 // (~2^-11 hi) normal down to ~8e-6 of it, so the split keeps ~2^-22 relative
@@ -227,10 +280,12 @@ __device__ __forceinline__ void put(void *out, int64_t total, int64_t k, float v
 }
 
 template <typename T>
-__global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *__restrict__ G,
+__global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, int NP, const float2 *__restrict__ G,
                               const float *__restrict__ gmax, int kind, int nplanes, void *__restrict__ out,
                               float *__restrict__ scale_out) {
-  const int pad = Kpad - 2 * B;
+  // NP polarisation blocks along K (1, or 2 for a polarisation-resolved bank):
+  // row (m, e, re) = [Gr_0 | -Gi_0 | Gr_1 | -Gi_1 | 0], (m, e, im) = [Gi_0 | Gr_0 | Gi_1 | Gr_1 | 0]
+  const int pad = Kpad - 2 * NP * B;
   const int P = B > pad ? B : pad;  // threads per (m, e)
   const int64_t total = (int64_t)M * 2 * E * Kpad;
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -239,18 +294,22 @@ __global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, const float2 *_
   if (k >= (int64_t)M * E * P) return;
   const int c = (int)(k % P);
   const int64_t me = k / P;  // m * E + e
+  const int64_t m = me / E, e = me - m * E;
   const int64_t re = (2 * me) * Kpad, im = (2 * me + 1) * Kpad;
   if (c < B) {
-    const float2 g = G[me * B + c];
-    const float gr = g.x * sc, gi = g.y * sc;
-    put<T>(out, total, re + c, gr, nplanes);
-    put<T>(out, total, re + B + c, -gi, nplanes);
-    put<T>(out, total, im + c, gi, nplanes);
-    put<T>(out, total, im + B + c, gr, nplanes);
+    for (int q = 0; q < NP; ++q) {
+      const float2 g = G[((m * NP + q) * E + e) * B + c];
+      const float gr = g.x * sc, gi = g.y * sc;
+      const int o = 2 * q * B;
+      put<T>(out, total, re + o + c, gr, nplanes);
+      put<T>(out, total, re + o + B + c, -gi, nplanes);
+      put<T>(out, total, im + o + c, gi, nplanes);
+      put<T>(out, total, im + o + B + c, gr, nplanes);
+    }
   }
   if (c < pad) {
-    put<T>(out, total, re + 2 * B + c, 0.f, nplanes);
-    put<T>(out, total, im + 2 * B + c, 0.f, nplanes);
+    put<T>(out, total, re + 2 * NP * B + c, 0.f, nplanes);
+    put<T>(out, total, im + 2 * NP * B + c, 0.f, nplanes);
   }
 }
 
@@ -341,32 +400,120 @@ __global__ void cross_terms_kernel(int64_t n_rows, int64_t row0, int64_t I_bank,
   }
 }
 
+// Polarisation-resolved bank: row records of Eq. hh_ieo grouped by
+// delta = m_a - m_c (one warp per bank row), REC_P floats per detector:
+//   [0..2]  delta = 0:  X0 = sum_a <h_a+|h_a+>, Y0 = sum_a 2 Re <h_a+|h_ax>, W0 = sum_a <h_ax|h_ax>
+//   [3 + 6 (delta - 1) ...]  delta = 1..3, complex (re, im):
+//           X = sum <h_a+|h_c+>, Y = sum (<h_a+|h_cx> + <h_ax|h_c+>), W = sum <h_ax|h_cx>  (a > c)
+// with <a|b>_d = sum_b omega_{d b} a b^*; master rows [Re h+ | Im h+ | Re hx | Im hx | 0].
+__global__ void cross_terms_pol_kernel(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
+                                       int4 mode_m, const float *__restrict__ master,
+                                       const float *__restrict__ omega, float *__restrict__ mx) {
+  extern __shared__ float om_s[];
+  for (int k = threadIdx.x; k < D * B; k += blockDim.x) om_s[k] = omega[k];
+  __syncthreads();
+  const int mm[MAXM] = {mode_m.x, mode_m.y, mode_m.z, mode_m.w};
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp_global; i < n_rows; i += nwarps) {
+    float acc[MAXD][21];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d)
+#pragma unroll
+      for (int q = 0; q < 21; ++q) acc[d][q] = 0.f;
+    for (int b = lane; b < B; b += 32) {
+      float hr[MAXM][2], hi[MAXM][2];
+#pragma unroll
+      for (int m = 0; m < MAXM; ++m)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (m < M) {
+            const float *row = master + ((int64_t)m * I_bank + row0 + i) * Kpad + 2 * q * B;
+            hr[m][q] = __ldg(row + b);
+            hi[m][q] = __ldg(row + B + b);
+          } else {
+            hr[m][q] = 0.f; hi[m][q] = 0.f;
+          }
+        }
+#pragma unroll
+      for (int d = 0; d < MAXD; ++d) {
+        if (d >= D) break;
+        const float w = om_s[d * B + b];
+#pragma unroll
+        for (int a = 0; a < MAXM; ++a) {
+          acc[d][0] += w * (hr[a][0] * hr[a][0] + hi[a][0] * hi[a][0]);
+          acc[d][1] += 2.f * w * (hr[a][0] * hr[a][1] + hi[a][0] * hi[a][1]);
+          acc[d][2] += w * (hr[a][1] * hr[a][1] + hi[a][1] * hi[a][1]);
+        }
+#pragma unroll
+        for (int a = 1; a < MAXM; ++a)
+#pragma unroll
+          for (int c = 0; c < a; ++c) {
+            if (a >= M) continue;
+            const int g = 3 + 6 * (mm[a] - mm[c] - 1);
+            // h_a+ h_c+^*, h_a+ h_cx^* + h_ax h_c+^*, h_ax h_cx^*
+            const float xr = hr[a][0] * hr[c][0] + hi[a][0] * hi[c][0], xi = hi[a][0] * hr[c][0] - hr[a][0] * hi[c][0];
+            const float y1r = hr[a][0] * hr[c][1] + hi[a][0] * hi[c][1], y1i = hi[a][0] * hr[c][1] - hr[a][0] * hi[c][1];
+            const float y2r = hr[a][1] * hr[c][0] + hi[a][1] * hi[c][0], y2i = hi[a][1] * hr[c][0] - hr[a][1] * hi[c][0];
+            const float wr = hr[a][1] * hr[c][1] + hi[a][1] * hi[c][1], wi = hi[a][1] * hr[c][1] - hr[a][1] * hi[c][1];
+#pragma unroll
+            for (int z = 0; z < 3; ++z)
+              if (g == 3 + 6 * z) {
+                acc[d][3 + 6 * z] += w * xr;
+                acc[d][4 + 6 * z] += w * xi;
+                acc[d][5 + 6 * z] += w * (y1r + y2r);
+                acc[d][6 + 6 * z] += w * (y1i + y2i);
+                acc[d][7 + 6 * z] += w * wr;
+                acc[d][8 + 6 * z] += w * wi;
+              }
+          }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) {
+      if (d >= D) break;
+#pragma unroll
+      for (int q = 0; q < 21; ++q) {
+        float v = acc[d][q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == q) mx[(i * D + d) * REC_P + q] = v;
+      }
+      if (lane >= 21 && lane < REC_P) mx[(i * D + d) * REC_P + lane] = 0.f;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Bank conversion (load time)
 // ---------------------------------------------------------------------------
 // complex [rows][M][B] (double2 or float2) -> FP32 master [M][I_bank][Kpad] rows [re | im]
 template <typename CT>
-__global__ void bank_to_master_kernel(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad,
+__global__ void bank_to_master_kernel(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, int NP,
                                       const CT *__restrict__ src, float *__restrict__ master,
                                       float *__restrict__ amax, int *status) {
+  // src [rows][M][NP][B] -> master row (m, i): [Re h_0 | Im h_0 | Re h_1 | Im h_1 | pad]
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= rows * M * B) return;
+  if (k >= rows * M * NP * B) return;
   int b = (int)(k % B);
-  int64_t rm = k / B;
+  int64_t rq = k / B;
+  int q = (int)(rq % NP);
+  int64_t rm = rq / NP;
   int m = (int)(rm % M);
   int64_t r = rm / M;
   CT v = src[k];
   float re = (float)v.x, im = (float)v.y;
   if (!isfinite(re) || !isfinite(im)) { atomicCAS(status, 0, DEV_E_NONFINITE); re = 0.f; im = 0.f; }
-  float *row = master + ((int64_t)m * I_bank + row0 + r) * Kpad;
+  float *row = master + ((int64_t)m * I_bank + row0 + r) * Kpad + 2 * q * B;
   row[b] = re;
   row[B + b] = im;
   atomic_max_nonneg(amax, fmaxf(fabsf(re), fabsf(im)));
 }
-template __global__ void bank_to_master_kernel<double2>(int64_t, int64_t, int64_t, int, int, int, const double2 *,
-                                                        float *, float *, int *);
-template __global__ void bank_to_master_kernel<float2>(int64_t, int64_t, int64_t, int, int, int, const float2 *,
-                                                       float *, float *, int *);
+template __global__ void bank_to_master_kernel<double2>(int64_t, int64_t, int64_t, int, int, int, int,
+                                                        const double2 *, float *, float *, int *);
+template __global__ void bank_to_master_kernel<float2>(int64_t, int64_t, int64_t, int, int, int, int,
+                                                       const float2 *, float *, float *, int *);
 
 __global__ void master_to_planes_kernel(int64_t n, const float *__restrict__ master, const float *__restrict__ amax,
                                         __nv_bfloat16 *__restrict__ bf /*[2][n]*/, __half *__restrict__ hf /*[2][n]*/,
@@ -465,18 +612,26 @@ void launch_prep(const PrepArgs &a, cudaStream_t st) {
     if (a.rb_dh) rb_norm_kernel<<<1, 256, 0, st>>>(a.D, a.M, a.B, a.rb_dh, a.rb_hh, a.sqrt_dd);
     else data_norm_kernel<<<1, 256, 0, st>>>(a.D, a.B, a.w, a.psd, a.data, a.sqrt_dd);
   }
-  prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, a.th, a.tl, a.Rf, a.qx, a.status);
-  build_G_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.Rf, a.G32,
-                                                       a.gmax);
-  const int pad = a.Kpad - 2 * a.B;
+  const bool pol = (a.n_pol == 2);
+  const int NP = pol ? 2 : 1;
+  prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, pol ? a.F : nullptr, a.th, a.tl,
+                                                        a.Rf, a.qx, a.status);
+  if (pol)
+    build_G_pol_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.F,
+                                                             a.G32, a.gmax);
+  else
+    build_G_kernel<<<nblk(a.E * a.B, 256), 256, 0, st>>>(a.E, a.D, a.M, a.B, a.fh, a.fl, a.th, a.tl, a.c, a.Rf,
+                                                         a.G32, a.gmax);
+  const int pad = a.Kpad - 2 * NP * a.B;
   const int64_t n = (int64_t)a.M * a.E * (a.B > pad ? a.B : pad);
   if (a.pack_kind == 0)
-    pack_G_kernel<float><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, 0, 1, a.gpack, a.gscale);
+    pack_G_kernel<float><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, NP, a.G32, a.gmax, 0, 1, a.gpack,
+                                                       a.gscale);
   else if (a.pack_kind == 1)
-    pack_G_kernel<__nv_bfloat16><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, 1, a.pack_planes,
-                                                               a.gpack, a.gscale);
+    pack_G_kernel<__nv_bfloat16><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, NP, a.G32, a.gmax, 1,
+                                                               a.pack_planes, a.gpack, a.gscale);
   else
-    pack_G_kernel<__half><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, a.G32, a.gmax, 2, a.pack_planes,
+    pack_G_kernel<__half><<<nblk(n, 256), 256, 0, st>>>(a.E, a.M, a.B, a.Kpad, NP, a.G32, a.gmax, 2, a.pack_planes,
                                                         a.gpack, a.gscale);
 }
 
@@ -526,10 +681,10 @@ void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st) {
   const int pad = a.Kpad - 2 * a.B;
   const int64_t np = mg * E * (a.B > pad ? a.B : pad);
   if (a.pack_kind == 1)
-    pack_G_kernel<__nv_bfloat16><<<nblk(np, 256), 256, 0, st>>>(E, mg, a.B, a.Kpad, a.G32, a.gmax, 1, a.pack_planes,
+    pack_G_kernel<__nv_bfloat16><<<nblk(np, 256), 256, 0, st>>>(E, mg, a.B, a.Kpad, 1, a.G32, a.gmax, 1, a.pack_planes,
                                                                 a.gpack, a.gscale);
   else
-    pack_G_kernel<__half><<<nblk(np, 256), 256, 0, st>>>(E, mg, a.B, a.Kpad, a.G32, a.gmax, 2, a.pack_planes,
+    pack_G_kernel<__half><<<nblk(np, 256), 256, 0, st>>>(E, mg, a.B, a.Kpad, 1, a.G32, a.gmax, 2, a.pack_planes,
                                                          a.gpack, a.gscale);
 }
 
@@ -547,20 +702,39 @@ void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int
                                                               rb_hh, mx);
     return;
   }
+  // omega [D][B] staged in shared memory (the caller keeps D B floats within 227 KB)
   size_t smem = sizeof(float) * (size_t)D * B;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(cross_terms_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cross_terms_kernel<false><<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, master, omega,
                                                                 nullptr, mx);
 }
 
-void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, const void *src,
-                           int dtype, float *master, float *amax, int *status, cudaStream_t st) {
-  int64_t n = rows * M * B;
+void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, int NP,
+                           const void *src, int dtype, float *master, float *amax, int *status, cudaStream_t st) {
+  int64_t n = rows * M * NP * B;
   if (dtype == DOTPE_C128)
-    bank_to_master_kernel<double2><<<nblk(n, 256), 256, 0, st>>>(rows, row0, I_bank, M, B, Kpad,
+    bank_to_master_kernel<double2><<<nblk(n, 256), 256, 0, st>>>(rows, row0, I_bank, M, B, Kpad, NP,
                                                                  (const double2 *)src, master, amax, status);
   else
-    bank_to_master_kernel<float2><<<nblk(n, 256), 256, 0, st>>>(rows, row0, I_bank, M, B, Kpad,
+    bank_to_master_kernel<float2><<<nblk(n, 256), 256, 0, st>>>(rows, row0, I_bank, M, B, Kpad, NP,
                                                                 (const float2 *)src, master, amax, status);
+}
+
+void launch_cross_terms_pol(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
+                            const int *mode_m, const float *master, const float *omega, float *mx, int n_sms,
+                            cudaStream_t st) {
+  int bs = 256;
+  int64_t blocks = (n_rows * 32 + bs - 1) / bs;
+  int64_t cap = (int64_t)n_sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  const int4 mm = make_int4(mode_m[0], M > 1 ? mode_m[1] : 0, M > 2 ? mode_m[2] : 0, M > 3 ? mode_m[3] : 0);
+  const size_t smem = sizeof(float) * (size_t)D * B;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(cross_terms_pol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cross_terms_pol_kernel<<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B,
+                                                                                      Kpad, mm, master, omega, mx);
 }
 
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf, __half *hf,

@@ -1,0 +1,121 @@
+"""Polarisation-resolved (precessing) banks on the device, through the C ABI,
+against the FP64 oracle (Sec. IV.A general case: Eqs. dh_ieo and hh_ieo with
+the polarisation index p and real antenna patterns F_{edp}).
+
+* An FP32 event over the whole bank (cross terms from the per-bank cache), a
+  slice of it (cross terms per slice), and the same slice streamed in blocks of
+  128 rows each meet the coherent path's FP32 tolerances against the oracle's
+  route O2, all pairs: 1e-3 per pair in ln Lbar and max_o ln L^ML, 1e-2 in ln Z.
+* Recomputed blocks (dotpe_lnl_blocks without stored values) read the same
+  antenna patterns.
+* The tensor-core precisions, pre-selection, relative binning and posterior
+  samples are refused with DOTPE_E_UNSUPPORTED; a missing F with DOTPE_E_INVALID.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dpx():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2507_16022_gb300 as dp
+    ctx = dp.dotpe_create(0)
+    yield dp, ctx
+    dp.dotpe_destroy(ctx)
+
+
+@pytest.fixture(scope="module")
+def pwl():
+    import oracle
+    # 640 rows (5 row tiles), 200 samples (a ragged column tile), 3 detectors, 4 modes
+    wl = synth.make_precessing_workload(640, 200, 3, 4, 256, snr=18.0, seed=61, n_phi=32, ln_w="random")
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event)
+    grid, _ = P.eval_grid(0.0)
+    return wl, P, grid
+
+
+def run_event(dp, ctx, bid, wl, i0, i1, flags, block_rows=0):
+    eid = dp.dotpe_event_submit(ctx, bid, i0, i1, wl.event.psd, wl.event.data, wl.ext.t, None, wl.ext.ln_w,
+                                n_phi=wl.event.n_phi, u_min=wl.event.u_min, cut_delta=0.0, precision="fp32",
+                                flags=flags, block_rows=block_rows, F=wl.ext.F)
+    dp.dotpe_event_wait(ctx, eid, 120.0)
+    E = wl.ext.t.shape[0]
+    ev = dp.dotpe_evidence(ctx, eid)
+    lnl = dp.dotpe_lnl_blocks(ctx, eid, 0, i1 - i0, 0, E)
+    ml = dp.dotpe_lnl_blocks(ctx, eid, 0, i1 - i0, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+    dp.dotpe_event_release(ctx, eid)
+    return ev, lnl, ml
+
+
+@pytest.mark.parametrize("case", ["whole", "slice", "slice_blocks", "recompute"])
+def test_event_against_oracle(dpx, pwl, case):
+    dp, ctx = dpx
+    import oracle
+    wl, P, grid = pwl
+    bank = wl.bank
+    I = bank.h.shape[0]
+    i0, i1 = (0, I) if case in ("whole", "recompute") else (128, 256)
+    flags = 0 if case == "recompute" else dp.DOTPE_FLAG_STORE_LNL
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+    try:
+        ev, lnl, ml = run_event(dp, ctx, bid, wl, i0, i1, flags, 128 if case == "slice_blocks" else 0)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    sub = grid[i0:i1]
+    if i0 or i1 != I:
+        sbank = synth.Bank(**{**bank.__dict__, "h": bank.h[i0:i1], "ln_w": bank.ln_w[i0:i1]})
+        P = oracle.OracleProblem(sbank, wl.ext, wl.event)
+    ref = P.evidence(sub)
+    d1 = np.abs(lnl - sub["lnl_marg"])
+    d2 = np.abs(ml - sub["lnl_ml_max"])
+    print(f"precessing {case}: max |d ln Lbar| {d1.max():.3e}, max |d ln L^ML| {d2.max():.3e}, "
+          f"d ln Z {ev['ln_z'] - ref['ln_z']:.3e}, peak ln L^ML {sub['lnl_ml_max'].max():.1f}")
+    assert np.all(d1 <= 1e-3)
+    assert np.all(d2 <= 1e-3)
+    assert abs(ev["ln_z"] - ref["ln_z"]) <= 1e-2
+    assert (ev["arg_i"], ev["arg_e"]) == (i0 + ref["arg"][0], ref["arg"][1])  # arg_i is a bank row
+
+
+def test_refusals(dpx, pwl):
+    dp, ctx = dpx
+    wl, _, _ = pwl
+    bank = wl.bank
+    I, M = bank.h.shape[0], bank.h.shape[1]
+    pol = np.ones((I, M, 2), np.complex128)
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w, pol=pol)
+    try:
+        for precision in ("fp16x3", "bf16x3", "mixed"):
+            with pytest.raises(dp.DotpeError) as ei:
+                dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None,
+                                      n_phi=32, precision=precision, F=wl.ext.F)
+            assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None,
+                                  n_phi=32, precision="fp32")
+        assert ei.value.status == dp.DOTPE_E_INVALID
+        D, B = wl.event.psd.shape
+        rb = (np.ones((D, M, B), np.complex128), np.ones((D, M, M, B), np.complex128))
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_event_submit(ctx, bid, 0, I, None, None, wl.ext.t, None, n_phi=32, precision="fp32",
+                                  rb=rb, F=wl.ext.F)
+        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+        t_grid = np.zeros((D, 16))
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,
+                               precision="fp16x3")
+        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+        eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None,
+                                    n_phi=32, u_min=wl.event.u_min, precision="fp32",
+                                    flags=dp.DOTPE_FLAG_STORE_LNL, F=wl.ext.F)
+        dp.dotpe_event_wait(ctx, eid, 120.0)
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_posterior_samples(ctx, eid, np.full((4, 4), 0.5))
+        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+        dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
