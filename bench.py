@@ -37,7 +37,7 @@ App. C distance draws) of the main event stored with DOTPE_FLAG_STORE_LNL;
 a step is one dotpe_posterior_samples call of 65,536 samples.
 --workload precessing: a polarisation-resolved bank (Sec. IV.A general case,
 h_{imp} with both polarisations, antenna patterns per sample) of 16,384 rows x
-4,096 samples, 3 detectors, 4 modes, 512 bins, in FP32; a step is one event.
+4,096 samples, 3 detectors, 4 modes, 512 bins; a step is one event.
 
 Under torchrun (N > 1) every rank runs its own independent events on its own
 GPU (events do not share data: weak scaling, no collective on the data path);
@@ -576,9 +576,10 @@ FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def bench_precessing(args, dp, ctx_factory, torch, dev):
-    """Polarisation-resolved (precessing) bank, Sec. IV.A general case: one FP32
-    event per step over a 16,384-row bank h_{imp} (both polarisations) x 4,096
-    extrinsic samples with antenna patterns F_{edp}."""
+    """Polarisation-resolved (precessing) bank, Sec. IV.A general case: one
+    event per step (mixed precision by default) over a 16,384-row bank h_{imp}
+    (both polarisations) x 4,096 extrinsic samples with antenna patterns F_{edp};
+    the plain FP32 path is timed beside it."""
     import oracle
     import synth
     D, M, B = 3, 4, 512
@@ -598,9 +599,9 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     d_psd, d_data, d_t, d_F, d_lw = (to_dev(wl.event.psd), to_dev(wl.event.data), to_dev(wl.ext.t),
                                      to_dev(wl.ext.F), to_dev(wl.ext.ln_w))
 
-    def submit(stream=None, psd=d_psd, data=d_data, t=d_t, F=d_F, lw=d_lw):
+    def submit(stream=None, psd=d_psd, data=d_data, t=d_t, F=d_F, lw=d_lw, precision=args.precision):
         return dp.dotpe_event_submit(ctx, bid, 0, I, psd, data, t, None, lw, n_phi=N_PHI, u_min=wl.event.u_min,
-                                     cut_delta=args.cut, precision="fp32", stream=stream, F=F)
+                                     cut_delta=args.cut, precision=precision, stream=stream, F=F)
 
     def one(**kw):
         eid = submit(**kw)
@@ -610,6 +611,7 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
         dp.dotpe_event_release(ctx, eid)
         return ev, st
 
+    ref, ref_st = one(precision="fp32")
     for _ in range(args.warmup):
         one()
     S = torch.cuda.Stream(device=dev)
@@ -628,11 +630,12 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ev_ms = t0.elapsed_time(t1) / args.steps
-    evs, sts = [], []
+    evs = []
     for eid in ids:
         evs.append(dp.dotpe_evidence(ctx, eid))
-        sts.append(dp.dotpe_event_poll(ctx, eid)[1])
         dp.dotpe_event_release(ctx, eid)
+    # kernel durations from events run one at a time (the timed events overlap)
+    sts = [one()[1] for _ in range(3)]
     # end to end: host inputs copied in, evidence read back, every step
     te = time.perf_counter()
     for _ in range(args.steps):
@@ -640,10 +643,17 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     e2e_s = (time.perf_counter() - te) / args.steps
     pairs = I * E
     fused_ms = statistics.mean(st["fused_ms"] for st in sts)
+    mixed = args.precision == "mixed"
+    refine_ms = statistics.mean(st["refine_ms"] for st in sts) if mixed else 0.0
+    dom_ms = fused_ms - refine_ms  # the screening pass (mixed) or the one fused kernel
     # <d|h>: 8 flops per complex multiply-add over M modes x 2 polarisations x B bins;
     # <h|h>: per detector 21 real multiply-adds of the row and column records
     flops_per_pair = 8 * 2 * B * M + D * 2 * 21
-    achieved = flops_per_pair * pairs / (fused_ms * 1e-3) / 1e12
+    achieved = flops_per_pair * pairs / (dom_ms * 1e-3) / 1e12
+    fp32 = args.precision == "fp32"
+    burst, sustained, hbm, peak_src = load_peaks()
+    peak = FP32_SIMT_PEAK_TFLOPS if fp32 else sustained
+    n_tiles = -(-I // 128) * -(-E // 32)
     cpu = None
     if not args.no_cpu_baseline:
         P = oracle.OracleProblem(bank, wl.ext, wl.event)
@@ -660,26 +670,37 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     line = {
         "metric": "(int x ext) lnL pairs/s", "value": pairs / (ev_ms * 1e-3), "unit": "pairs/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ev_ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32" if fp32 else ("bf16" if args.precision.startswith("bf16") else "fp16"), "data": "synthetic",
         "config": {"workload": f"polarisation-resolved (precessing) bank: I={I} rows h_(i m p) x E={E} samples "
                                f"with antenna patterns, D={D}, M={M}, B={B}, N_phi={N_PHI}, SNR 15",
-                   "precision": "fp32", "ml_cut_delta": args.cut, "fused_ms": fused_ms,
+                   "precision": args.precision, "ml_cut_delta": args.cut, "fused_ms": fused_ms,
+                   "refine_ms": refine_ms if mixed else None,
+                   "refined_tile_fraction": (evs[-1]["n_refined_tiles"] / n_tiles
+                                             if mixed and evs[-1]["n_refined_tiles"] >= 0 else None),
                    "prep_ms": statistics.mean(st["prep_ms"] for st in sts),
+                   "dlnz_vs_fp32": abs(evs[-1]["ln_z"] - ref["ln_z"]),
+                   "fp32_path_ms": ref_st["device_ms"], "fp32_path_pairs_per_s": pairs / (ref_st["device_ms"] * 1e-3),
                    "marginalised_fraction": evs[-1]["n_marginalised"] / (pairs * N_PHI),
-                   "l2": f"inputs larger than L2 (FP32 bank {I * M * 2 * 2 * B * 4 / 1e9:.2f} GB, re-read every "
-                         "step)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "simt_fused_kernel (FP32 <d|h> GEMM over both polarisations + marginalisation)",
-                     "kernel_ms": fused_ms, "flops_per_pair": flops_per_pair,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz"},
+                   "l2": f"inputs larger than L2 (bank operand planes {I * M * 4 * B * 2 * 2 / 1e9:.2f} GB, "
+                         "re-read every step)"},
+        "roofline": {"bound": "alu" if fp32 else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": ("simt_fused_kernel (FP32 <d|h> GEMM over both polarisations + marginalisation)"
+                                if fp32 else
+                                "tc_fused_kernel<HH=2> " + ("screening pass" if mixed else "fused pass")
+                                + " (<d|h> GEMM over both polarisations, K = 4B)"),
+                     "kernel_ms": dom_ms, "flops_per_pair": flops_per_pair,
+                     "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if fp32
+                                     else f"{peak_src} bf16_tflops_sustained")},
         "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + wl.ext.t.nbytes
                                           + wl.ext.F.nbytes + wl.ext.ln_w.nbytes),
                 "d2h_bytes_per_step": 96},
-        # prep (data weights, norm, extrinsic, G build, G pack), the fused kernel, the
-        # reduction (6); the bank's cross terms are cached from the warm-up
-        "gpu_launches": 12 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
+        # prep (data weights, norm, extrinsic, G build, G pack), the fused kernel (mixed:
+        # screen, 3 selection kernels, 2 gated refinement variants), the reduction (6);
+        # the bank's cross terms are cached from the warm-up
+        "gpu_launches": (5 + (6 if mixed else 1) + 6) * args.steps, "clocks": clocks, "cpu_baseline": cpu,
     }
     dp.dotpe_bank_release(ctx, bid)
     dp.dotpe_destroy(ctx)

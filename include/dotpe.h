@@ -122,9 +122,11 @@ typedef struct dotpe_config {
  *   (the general, precessing case of Sec. IV.A, Eqs. dh_ieo and hh_ieo with
  *   the polarisation index p): h is then [n_int][n_modes][2][n_bins] complex,
  *   h_{i m p b} with p = +, x, and each extrinsic sample carries real antenna
- *   patterns F_{e d p} (dotpe_event_desc.F) in place of R.  Such a bank is
- *   evaluated in DOTPE_PREC_FP32 only; dotpe_preselect, relative binning and
- *   dotpe_posterior_samples return DOTPE_E_UNSUPPORTED for it. */
+ *   patterns F_{e d p} (dotpe_event_desc.F) in place of R.  Every precision
+ *   applies (the tensor-core kernels contract K = 4 n_bins, padded); its events
+ *   are not batched with one another (dotpe_batch_submit in a precision other
+ *   than DOTPE_PREC_FP32 returns DOTPE_E_UNSUPPORTED); dotpe_preselect,
+ *   relative binning and dotpe_posterior_samples return DOTPE_E_UNSUPPORTED. */
 typedef struct dotpe_bank_desc {
   int64_t n_int;
   int n_modes;

@@ -14,6 +14,8 @@ constexpr int MAXM = 4;    // modes per waveform
 constexpr int MAXD = 3;    // detectors (H, L, V)
 constexpr int REC = 16;    // floats per (row or column, detector) cross-term record
 constexpr int REC_P = 24;  // row record of a polarisation-resolved bank (21 used, see cross_terms_pol_kernel)
+constexpr int REC_POL = 21;     // used floats of that record
+constexpr int POL_TC_MAXD = 3;  // detectors of a polarisation-resolved bank on the tensor cores (registers)
 constexpr int MAXPHI = 128;
 constexpr int NPAIR = 6;   // mode pairs (a > b) for MAXM = 4
 

@@ -314,6 +314,7 @@ static int tc_launch_of(dotpe_ctx *ctx, const Bank &b, int prec, TcLaunch &T) {
   T.consec = true;
   for (int m = 1; m < b.M; ++m)
     if (b.mode_m[m] != b.mode_m[m - 1] + 1) T.consec = false;
+  T.pol = (b.n_pol == 2);
   T.n_sms = ctx->n_sms;
   return DOTPE_OK;
 }
@@ -1002,7 +1003,7 @@ static void progress(dotpe_ctx *ctx) {
     size_t need = scratch_layout(e).total + keep_bytes_of(e);
     auto batchable = [&](const Event &x) {
       return x.group == 0 && x.bank == e.bank && x.prec == e.prec && x.block_rows == 0 &&
-             !(x.flags & DOTPE_FLAG_TEST_STALL);
+             !(x.flags & DOTPE_FLAG_TEST_STALL) && x.bank->n_pol == 1;
     };
     if (e.group != 0) {
       for (size_t q = 1; q < ctx->queue.size(); ++q) {
@@ -1590,9 +1591,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   const size_t nel = (size_t)b->M * b->I * b->Kpad;
   Carver c;
   size_t o_f = c.take<double>(b->B), o_w = c.take<double>(b->B), o_lw = c.take<double>(b->I);
-  // a polarisation-resolved bank runs in FP32 only: no bf16/fp16 operand planes
-  const size_t nplane = (b->n_pol == 2) ? 0 : 2 * nel;
-  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(nplane), o_hf = c.take<__half>(nplane);
+  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(2 * nel);
   size_t o_scal = c.take<float>(4);
   size_t o_pol = d->pol ? c.take<float2>((size_t)b->I * b->M * 2) : 0;
   b->bytes = c.off;
@@ -1610,8 +1609,8 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   b->w = (double *)(base + o_w);
   b->lw = d->ln_w_int ? (double *)(base + o_lw) : nullptr;
   b->master = (float *)(base + o_master);
-  b->bf = nplane ? (__nv_bfloat16 *)(base + o_bf) : nullptr;
-  b->hf = nplane ? (__half *)(base + o_hf) : nullptr;
+  b->bf = (__nv_bfloat16 *)(base + o_bf);
+  b->hf = (__half *)(base + o_hf);
   float *scal = (float *)(base + o_scal);  // [0] amax, [1] a_scale, [2] status
   b->pol = d->pol ? (float2 *)(base + o_pol) : nullptr;
   cudaStream_t st = ctx->main_stream;
@@ -1667,7 +1666,7 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
     launch_bank_to_master(rows, r0, b->I, b->M, b->B, b->Kpad, b->n_pol, dsrc, d->h_dtype, b->master, &scal[0],
                           (int *)&scal[2], st);
   }
-  if (nplane) launch_master_to_planes((int64_t)nel, b->master, &scal[0], b->bf, b->hf, &scal[1], st);
+  launch_master_to_planes((int64_t)nel, b->master, &scal[0], b->bf, b->hf, &scal[1], st);
   check(cudaGetLastError());
   check(cudaStreamSynchronize(st));
   if (stage) cudaFree(stage);
@@ -1730,8 +1729,9 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
   if ((!rb && (!d->psd || !d->data)) || !d->t || (pol ? !d->F : !d->R))
     return fail(DOTPE_E_INVALID, pol ? "null input array (a polarisation-resolved bank needs F)" : "null input array");
-  if (pol && d->precision != DOTPE_PREC_FP32)
-    return fail(DOTPE_E_UNSUPPORTED, "polarisation-resolved banks run in FP32 only (the tensor-core variant is not built)");
+  if (pol && d->precision != DOTPE_PREC_FP32 && d->n_det > POL_TC_MAXD)
+    return fail(DOTPE_E_UNSUPPORTED, "a polarisation-resolved bank with n_det=%d runs in FP32 only (tensor cores: "
+                "n_det <= %d)", d->n_det, POL_TC_MAXD);
   if (pol && rb) return fail(DOTPE_E_UNSUPPORTED, "relative binning with a polarisation-resolved bank");
   if (!rb && (size_t)d->n_det * b->B * sizeof(float) > 227 * 1024)
     return fail(DOTPE_E_UNSUPPORTED, "n_det * n_bins = %lld: the <h|h> weights exceed shared memory",
@@ -1881,6 +1881,11 @@ int dotpe_batch_submit(dotpe_ctx *ctx, int n, const dotpe_event_desc *descs, uin
   for (int k = 1; k < n; ++k)
     if (descs[k].bank_id != descs[0].bank_id || descs[k].precision != descs[0].precision)
       return fail(DOTPE_E_INVALID, "batch events must share the bank and the precision");
+  {
+    auto bit = ctx->banks.find(descs[0].bank_id);
+    if (bit != ctx->banks.end() && bit->second->n_pol == 2 && descs[0].precision != DOTPE_PREC_FP32)
+      return fail(DOTPE_E_UNSUPPORTED, "batches of a polarisation-resolved bank run in FP32 only");
+  }
   size_t need = 0;
   const uint64_t group = ctx->next_group++;
   for (int k = 0; k < n; ++k) {

@@ -121,6 +121,37 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
   }
 }
 
+// Polarisation-resolved bank, row records held in registers (tensor-core
+// epilogue): mrec [POL_TC_MAXD][REC_POL] as hh_coeffs_pol reads them from
+// memory, the column record's (F+^2, F+ Fx, Fx^2) as one float4 per detector.
+__device__ __forceinline__ void hh_coeffs_pol_reg(const float *mrec, const float *__restrict__ qrec,
+                                                  const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
+  C0 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { Cr[k] = 0.f; Ci[k] = 0.f; }
+#pragma unroll
+  for (int d = 0; d < POL_TC_MAXD; ++d) {
+    if (d >= P.n_det) break;
+    const float4 q = *reinterpret_cast<const float4 *>(qrec + d * REC);
+    const float *r = mrec + d * REC_POL;
+    C0 += q.x * r[0] + q.y * r[1] + q.z * r[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      Cr[k] += q.x * r[3 + 6 * k] + q.y * r[5 + 6 * k] + q.z * r[7 + 6 * k];
+      Ci[k] += q.x * r[4 + 6 * k] + q.y * r[6 + 6 * k] + q.z * r[8 + 6 * k];
+    }
+  }
+}
+
+// <h|h> coefficients of the tensor-core epilogue: HH = 0 general modes, 1
+// consecutive modes, 2 polarisation-resolved bank (registers as above).
+template <int HH>
+__device__ __forceinline__ void hh_tile(const float *mrec, const float *__restrict__ qrec, const EpiParams &P,
+                                        float &C0, float Cr[3], float Ci[3]) {
+  if constexpr (HH == 2) hh_coeffs_pol_reg(mrec, qrec, P, C0, Cr, Ci);
+  else hh_coeffs<HH == 1>(mrec, qrec, P, C0, Cr, Ci);
+}
+
 // Upper bound of max_o ln L^ML_o of a pair: |dh| <= sum_m |Z_m| and
 // hh >= C_0 - 2 sum |C_delta| at every phase; +inf when that lower bound is not positive.
 __device__ __forceinline__ float pair_bound(const float Zr[MAXM], const float Zi[MAXM], float C0, const float Cr[3],

@@ -114,7 +114,7 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
   super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
 }
 
-template <bool BF16, bool CONSEC, bool SPLIT, int NB, bool SEP>
+template <bool BF16, int HH, bool SPLIT, int NB, bool SEP>
 __global__ void __launch_bounds__(NT, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcBatch<NB> Bt,
                     const TcCommon C) {
@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(NT, 1)
     const EpiParams &P = (NB == 1) ? Bt.w[0].P : T.ep;
     bool store = false;
     float zs = 1.f;
-    float mrec[MAXD * REC];
+    constexpr int NREC = (HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC;  // row record floats in registers
+    float mrec[NREC];
     double lwi = 0.0;
     int cur_it = -1, cur_k = -1;
     uint32_t u = 0;
@@ -299,13 +300,30 @@ __global__ void __launch_bounds__(NT, 1)
       const int64_t e0 = (int64_t)et * TE;
       if (it != cur_it) {
 #pragma unroll
-        for (int k = 0; k < MAXD * REC; ++k) mrec[k] = 0.f;
-        const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
+        for (int k = 0; k < NREC; ++k) mrec[k] = 0.f;
+        if constexpr (HH == 2) {
+          // row records of REC_P floats per detector, the first REC_POL kept
+          const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC_P);
 #pragma unroll
-        for (int k = 0; k < MAXD * REC / 4; ++k) {
-          if (vi && k < P.n_det * REC / 4) {
-            float4 v = __ldg(src + k);
-            mrec[4 * k] = v.x; mrec[4 * k + 1] = v.y; mrec[4 * k + 2] = v.z; mrec[4 * k + 3] = v.w;
+          for (int d = 0; d < POL_TC_MAXD; ++d)
+#pragma unroll
+            for (int v = 0; v < REC_P / 4; ++v) {
+              if (vi && d < P.n_det) {
+                const float4 x = __ldg(src + d * (REC_P / 4) + v);
+                const float xs4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                  if (4 * v + c < REC_POL) mrec[d * REC_POL + 4 * v + c] = xs4[c];
+              }
+            }
+        } else {
+          const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
+#pragma unroll
+          for (int k = 0; k < MAXD * REC / 4; ++k) {
+            if (vi && k < P.n_det * REC / 4) {
+              float4 v = __ldg(src + k);
+              mrec[4 * k] = v.x; mrec[4 * k + 1] = v.y; mrec[4 * k + 2] = v.z; mrec[4 * k + 3] = v.w;
+            }
           }
         }
         lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
@@ -352,7 +370,7 @@ __global__ void __launch_bounds__(NT, 1)
               Zi[m] *= zs;
             }
             float C0, Cr[3], Ci[3];
-            hh_coeffs<CONSEC>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
+            hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
             bound = pair_bound(Zr, Zi, C0, Cr, Ci);
           }
           xb[j] = bound;
@@ -400,7 +418,7 @@ __global__ void __launch_bounds__(NT, 1)
               Zi[m] *= zs;
             }
             float C0, Cr[3], Ci[3];
-            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
             int argo;
             const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
             const long long g = (i * P.n_ext + e) * (long long)P.n_phi + argo;
@@ -484,7 +502,7 @@ __global__ void __launch_bounds__(NT, 1)
             x2 = sx;
           } else if (P.screen_ml) {
             float C0, Cr[3], Ci[3];
-            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
             int argo;
             const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph, argo);
             if (ml > best) {
@@ -497,7 +515,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
           } else {
             float C0, Cr[3], Ci[3];
-            hh_coeffs<CONSEC>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
             PairRes pr = pair_eval(Zr, Zi, C0, Cr, Ci, thr, !store, P, T.ph);
             const float lw = (float)(lwi + T.lwe[el]);
             x = pr.lsum + lw;
@@ -602,9 +620,16 @@ cudaError_t launch_tc_variant(const TcLaunch &L, const TcBatch<NB> &bt, int grid
     kern<<<grid, NT, smem, st>>>(L.mapA, bt, L.C);
     return cudaGetLastError();
   };
-  if (L.bf16) return L.consec ? go(tc_fused_kernel<true, true, SPLIT, NB, SEP>)
-                              : go(tc_fused_kernel<true, false, SPLIT, NB, SEP>);
-  return L.consec ? go(tc_fused_kernel<false, true, SPLIT, NB, SEP>) : go(tc_fused_kernel<false, false, SPLIT, NB, SEP>);
+  if (L.pol) {
+    // polarisation-resolved banks run one event per launch
+    if constexpr (NB == 1)
+      return L.bf16 ? go(tc_fused_kernel<true, 2, SPLIT, NB, SEP>) : go(tc_fused_kernel<false, 2, SPLIT, NB, SEP>);
+    else
+      return cudaErrorInvalidValue;
+  }
+  if (L.bf16) return L.consec ? go(tc_fused_kernel<true, 1, SPLIT, NB, SEP>)
+                              : go(tc_fused_kernel<true, 0, SPLIT, NB, SEP>);
+  return L.consec ? go(tc_fused_kernel<false, 1, SPLIT, NB, SEP>) : go(tc_fused_kernel<false, 0, SPLIT, NB, SEP>);
 }
 
 template <int NB>

@@ -109,6 +109,7 @@ struct TcLaunch {
   CUtensorMap mapA;  // bank operand planes [planes][M][I][Kpad]
   TcCommon C;
   bool bf16, split, consec;
+  bool pol;          // polarisation-resolved bank (row records in registers, n_det <= POL_TC_MAXD)
   bool sep;          // split: hi*lo + lo*hi in their own accumulator (see kernel_tc.cuh)
   const int *gate;   // optional device words per event: event k's items run only if gate[k] == gate_want
   int gate_want;

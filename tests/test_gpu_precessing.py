@@ -8,8 +8,15 @@ the polarisation index p and real antenna patterns F_{edp}).
   route O2, all pairs: 1e-3 per pair in ln Lbar and max_o ln L^ML, 1e-2 in ln Z.
 * Recomputed blocks (dotpe_lnl_blocks without stored values) read the same
   antenna patterns.
-* The tensor-core precisions, pre-selection, relative binning and posterior
-  samples are refused with DOTPE_E_UNSUPPORTED; a missing F with DOTPE_E_INVALID.
+* The tensor-core precisions (K = 4B: both polarisations' real and imaginary
+  parts) meet the mode bank's bounds: split fp16x3 / bf16x3 1e-3 + TC_ACC
+  ln L^ML per pair (the tensor cores' truncating FP32 accumulation over
+  Kpad/16 steps); single-pass fp16 2e-2 + 4u ln L^ML + 2u sqrt(2 ln L^ML + 1)
+  sqrt(<d|d>); mixed the split bound within 30 of the maximum and the fp16 bound
+  elsewhere; |d ln Z| <= 1e-2 for the split and mixed precisions.
+* Pre-selection, relative binning, posterior samples and batches in a
+  tensor-core precision are refused with DOTPE_E_UNSUPPORTED; a missing F with
+  DOTPE_E_INVALID.
 """
 import numpy as np
 import pytest
@@ -81,6 +88,51 @@ def test_event_against_oracle(dpx, pwl, case):
     assert (ev["arg_i"], ev["arg_e"]) == (i0 + ref["arg"][0], ref["arg"][1])  # arg_i is a bank row
 
 
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3", "mixed", "fp16"])
+def test_tensor_core_precisions(dpx, pwl, precision):
+    dp, ctx = dpx
+    wl, P, grid = pwl
+    bank = wl.bank
+    I, B = bank.h.shape[0], bank.h.shape[-1]
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+    try:
+        eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None, wl.ext.ln_w,
+                                    n_phi=wl.event.n_phi, u_min=wl.event.u_min, cut_delta=0.0,
+                                    precision=precision, flags=dp.DOTPE_FLAG_STORE_LNL, F=wl.ext.F)
+        dp.dotpe_event_wait(ctx, eid, 120.0)
+        E = wl.ext.t.shape[0]
+        ev = dp.dotpe_evidence(ctx, eid)
+        lnl = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E)
+        ml = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+        dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    ref = P.evidence(grid)
+    ml_ref = grid["lnl_ml_max"]
+    mlp = np.maximum(ml_ref, 0.0)
+    kpad = -(-4 * B // 64) * 64
+    tc_acc = 2 * (kpad // 16) * 2.0 ** -24
+    u = 2.0 ** -11
+    dd = float(np.sum(4 * bank.w[None, :] * np.abs(wl.event.data) ** 2 / wl.event.psd))
+    split_tol = 1e-3 + tc_acc * mlp
+    fp16_tol = 2e-2 + 4 * u * mlp + 2 * u * np.sqrt(2 * mlp + 1) * np.sqrt(dd)
+    if precision == "fp16":
+        tol = fp16_tol
+    elif precision == "mixed":
+        tol = np.where(ml_ref >= ml_ref.max() - 30.0, split_tol, fp16_tol)
+    else:
+        tol = split_tol
+    d1 = np.abs(lnl - grid["lnl_marg"])
+    d2 = np.abs(ml - ml_ref)
+    print(f"precessing {precision}: max |d ln Lbar| {d1.max():.3e}, max |d ln L^ML| {d2.max():.3e}, "
+          f"d ln Z {ev['ln_z'] - ref['ln_z']:.3e}")
+    assert np.all(d1 <= tol)
+    assert np.all(d2 <= tol)
+    if precision != "fp16":
+        assert abs(ev["ln_z"] - ref["ln_z"]) <= 1e-2
+        assert (ev["arg_i"], ev["arg_e"]) == ref["arg"][:2]
+
+
 def test_refusals(dpx, pwl):
     dp, ctx = dpx
     wl, _, _ = pwl
@@ -89,11 +141,11 @@ def test_refusals(dpx, pwl):
     pol = np.ones((I, M, 2), np.complex128)
     bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w, pol=pol)
     try:
-        for precision in ("fp16x3", "bf16x3", "mixed"):
-            with pytest.raises(dp.DotpeError) as ei:
-                dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None,
-                                      n_phi=32, precision=precision, F=wl.ext.F)
-            assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+        spec = dict(bank_id=bid, i0=0, i1=I, psd=wl.event.psd, data=wl.event.data, t=wl.ext.t, R=None,
+                    n_phi=32, u_min=wl.event.u_min, precision="mixed", F=wl.ext.F)
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_batch_submit(ctx, [spec, spec])
+        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
         with pytest.raises(dp.DotpeError) as ei:
             dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None,
                                   n_phi=32, precision="fp32")
