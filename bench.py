@@ -571,6 +571,9 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
     return line
 
 
+# DRAM bytes per (i,e) pair of the polarisation-resolved screening launch, from one
+# ncu capture of a 4,096 x 2,048 event (scaled by pairs like the mode bank's)
+DRAM_BYTES_PER_PAIR_POL = {"mixed": (317.53e6 + 9.51e6) / (4096 * 2048)}
 # FP32 pipe of one GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) at the 2,070 MHz maximum SM clock
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -685,7 +688,10 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
                    "l2": f"inputs larger than L2 (bank operand planes {I * M * 4 * B * 2 * 2 / 1e9:.2f} GB, "
                          "re-read every step)"},
         "roofline": {"bound": "alu" if fp32 else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (DRAM_BYTES_PER_PAIR_POL[args.precision] * pairs
+                                 if args.precision in DRAM_BYTES_PER_PAIR_POL else None),
+                     "traffic_note": "bytes per launch, scaled by pairs from an ncu capture at 4,096 x 2,048",
                      "kernel": ("simt_fused_kernel (FP32 <d|h> GEMM over both polarisations + marginalisation)"
                                 if fp32 else
                                 "tc_fused_kernel<HH=2> " + ("screening pass" if mixed else "fused pass")
