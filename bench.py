@@ -930,8 +930,8 @@ def main():
                                      cut_delta=cut, precision=precision, flags=flags,
                                      stream=stream)
 
-    def one(precision, k=0, cut=args.cut):
-        eid = submit(k, precision, cut=cut)
+    def one(precision, k=0, cut=args.cut, flags=0):
+        eid = submit(k, precision, cut=cut, flags=flags)
         dp.dotpe_event_wait(ctx, eid, 600.0)
         ev = dp.dotpe_evidence(ctx, eid)
         _, st = dp.dotpe_event_poll(ctx, eid)
@@ -980,6 +980,10 @@ def main():
     # own durations come from events run one at a time (CUDA events recorded
     # by the runtime on the launch stream)
     stats = [one(args.precision, k)[1] for k in range(min(4, args.steps))]
+    # GEMM-only figure (diagnostic, outside the timed region): one fp16 pass with the
+    # epilogue reduced to a sum of the accumulators (result not valid)
+    gemm_only_ms = statistics.median(one("fp16", k, cut=0.0, flags=dp.DOTPE_FLAG_GEMM_ONLY)[1]["fused_ms"]
+                                     for k in range(3))
 
     # ---- end to end through the public API: pinned host inputs, results read back ----
     barrier()
@@ -1067,6 +1071,8 @@ def main():
             "refine_ms": refine_ms if mixed else None,
             "refined_tile_fraction": refined / n_tiles if mixed else None,
             "issued_tflops": flops_issued / (fused_ms * 1e-3) / 1e12,
+            "gemm_only_ms": gemm_only_ms,
+            "gemm_only_tflops": 8 * B * M * pairs / (gemm_only_ms * 1e-3) / 1e12,
         },
         "roofline": {
             "bound": "tensor",

@@ -133,6 +133,50 @@ def test_tensor_core_precisions(dpx, pwl, precision):
         assert (ev["arg_i"], ev["arg_e"]) == ref["arg"][:2]
 
 
+@pytest.mark.parametrize("shape", [(300, 77, 2, 3, 128), (129, 33, 1, 1, 96), (200, 50, 3, 2, 200)])
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
+def test_ragged_shapes_and_networks(dpx, shape, precision):
+    """Ragged row and sample tiles, one to three detectors, one to three modes,
+    and K = 4B = 800 (13 k-blocks: an odd last k-block) against the oracle."""
+    dp, ctx = dpx
+    import oracle
+    I, E, D, M, B = shape
+    wl = synth.make_precessing_workload(I, E, D, M, B, snr=14.0, seed=71 + I, n_phi=32, ln_w="random")
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event)
+    grid, _ = P.eval_grid(0.0)
+    ref = P.evidence(grid)
+    bank = wl.bank
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+    try:
+        eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, None, wl.ext.ln_w,
+                                    n_phi=32, u_min=wl.event.u_min, cut_delta=0.0, precision=precision,
+                                    flags=dp.DOTPE_FLAG_STORE_LNL, F=wl.ext.F)
+        dp.dotpe_event_wait(ctx, eid, 120.0)
+        ev = dp.dotpe_evidence(ctx, eid)
+        lnl = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E)
+        ml = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+        dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    ml_ref = grid["lnl_ml_max"]
+    mlp = np.maximum(ml_ref, 0.0)
+    kpad = -(-4 * B // 64) * 64
+    split_tol = 1e-3 + 2 * (kpad // 16) * 2.0 ** -24 * mlp
+    if precision == "mixed":
+        u = 2.0 ** -11
+        dd = float(np.sum(4 * bank.w[None, :] * np.abs(wl.event.data) ** 2 / wl.event.psd))
+        tol = np.where(ml_ref >= ml_ref.max() - 30.0, split_tol,
+                       2e-2 + 4 * u * mlp + 2 * u * np.sqrt(2 * mlp + 1) * np.sqrt(dd))
+    elif precision == "fp16x3":
+        tol = split_tol
+    else:
+        tol = np.full_like(ml_ref, 1e-3)
+    assert np.all(np.abs(lnl - grid["lnl_marg"]) <= tol)
+    assert np.all(np.abs(ml - ml_ref) <= tol)
+    assert abs(ev["ln_z"] - ref["ln_z"]) <= 1e-2
+    assert (ev["arg_i"], ev["arg_e"]) == ref["arg"][:2]
+
+
 def test_refusals(dpx, pwl):
     dp, ctx = dpx
     wl, _, _ = pwl
