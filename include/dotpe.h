@@ -125,8 +125,8 @@ typedef struct dotpe_config {
  *   patterns F_{e d p} (dotpe_event_desc.F) in place of R.  Every precision
  *   applies (the tensor-core kernels contract K = 4 n_bins, padded); its events
  *   are not batched with one another (dotpe_batch_submit in a precision other
- *   than DOTPE_PREC_FP32 returns DOTPE_E_UNSUPPORTED); dotpe_preselect,
- *   relative binning and dotpe_posterior_samples return DOTPE_E_UNSUPPORTED. */
+ *   than DOTPE_PREC_FP32 returns DOTPE_E_UNSUPPORTED); dotpe_preselect and
+ *   relative binning return DOTPE_E_UNSUPPORTED. */
 typedef struct dotpe_bank_desc {
   int64_t n_int;
   int n_modes;

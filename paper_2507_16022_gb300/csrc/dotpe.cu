@@ -1350,7 +1350,6 @@ static int samples_locked(dotpe_ctx *ctx, Event &e, int64_t n, const double *uni
   Bank &b = *e.bank;
   if (!(e.flags & DOTPE_FLAG_STORE_LNL))
     return fail(DOTPE_E_INVALID, "posterior samples need an event run with DOTPE_FLAG_STORE_LNL");
-  if (b.n_pol == 2) return fail(DOTPE_E_UNSUPPORTED, "posterior samples of a polarisation-resolved bank");
   if (n < 1 || n > (1ll << 24)) return fail(DOTPE_E_INVALID, "n=%lld not in 1..2^24", (long long)n);
   if (!uniforms) return fail(DOTPE_E_INVALID, "null uniforms");
   cudaStream_t st = ctx->main_stream;
@@ -1390,6 +1389,8 @@ static int samples_locked(dotpe_ctx *ctx, Event &e, int64_t n, const double *uni
   a.rb_hh = e.rb_hh;
   a.t = e.t;
   a.R = e.R;
+  a.F = e.F;
+  a.n_pol = b.n_pol;
   a.lw_ext = e.has_lwe ? e.lwe : nullptr;
   a.ln_p_int = e.ln_p_int;
   a.lnl = e.lnl_tile;

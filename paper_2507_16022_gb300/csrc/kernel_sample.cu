@@ -8,8 +8,10 @@
 //   u2 -> e  from row i of the stored ln Lbar_ie plus ln w_e,
 //   u3 -> o  from the pair's phases that pass the event's ML cut, weights Lbar_ieo
 //            (the pair recomputed in FP64 from the event's inputs: per-mode
-//            components and mode overlaps, Eqs. dh_ieo, hh_ieo; Lbar from the
-//            same device distance marginal as the fused kernels),
+//            components and mode overlaps, Eqs. dh_ieo, hh_ieo, per (mode,
+//            polarisation) component with real antenna patterns F_edp for a
+//            polarisation-resolved bank; Lbar from the same device distance
+//            marginal as the fused kernels),
 //   u4 -> d_L / d_L^0 = 1/u from the density of u on [u_min, inf),
 //            proportional to u^-4 exp(dh u - hh u^2 / 2) (pi(d_L) ~ d_L^2).
 // Each draw takes the smallest index whose cumulative weight exceeds u times
@@ -125,6 +127,9 @@ __global__ void sample_row_cdf_kernel(int64_t n, const double *__restrict__ ln_p
   }
 }
 
+// NP = 2: polarisation-resolved bank, components j = (m, p) with master row
+// [Re h_m+ | Im h_m+ | Re h_mx | Im h_mx] and response F_edp (real).
+template <int NP>
 __global__ void __launch_bounds__(SW * 32)
     sample_kernel(const SampleArgs a, int64_t n, const double *__restrict__ uni, const double *__restrict__ cdf,
                   int64_t *__restrict__ i_out, int64_t *__restrict__ e_out, int32_t *__restrict__ o_out,
@@ -153,27 +158,33 @@ __global__ void __launch_bounds__(SW * 32)
     const float v = row[k];
     return (v == -INFINITY) ? -INFINITY : (double)v + (a.lw_ext ? a.lw_ext[k] : 0.0);
   });
-  // ---- the pair in FP64: z_m = sum_d R_edm sum_b c_dmb T_db h_m(b); H_mm' = sum_d R R'^* sum_b W h_m h_m'^*
-  double zr[MAXM] = {0, 0, 0, 0}, zi[MAXM] = {0, 0, 0, 0};
-  double Hr[MAXM][MAXM] = {}, Hi[MAXM][MAXM] = {};
+  // ---- the pair in FP64, per component j = (m, p): z_j = sum_d R_edj sum_b c_dmb T_db h_j(b),
+  // H_jj' = sum_d R_edj R_edj'^* sum_b W h_j h_j'^* (R_edj = R_edm, or F_edp for NP = 2)
+  constexpr int MJ = MAXM * NP;
+  const int J = M * NP;
+  double zr[MJ] = {}, zi[MJ] = {};
+  double Hr[MJ][MJ] = {}, Hi[MJ][MJ] = {};
   const int64_t ib = a.i_base + i;
   for (int d = 0; d < D; ++d) {
-    double Sr[MAXM] = {0, 0, 0, 0}, Si[MAXM] = {0, 0, 0, 0};
-    double Qr[MAXM][MAXM] = {}, Qi[MAXM][MAXM] = {};
+    double Sr[MJ] = {}, Si[MJ] = {};
+    double Qr[MJ][MJ] = {}, Qi[MJ][MJ] = {};
     const double td = (e >= 0) ? a.t[(int64_t)e * D + d] : 0.0;
     for (int b = lane; b < B; b += 32) {
       double s_, c_;
       sincospi(2.0 * a.f[b] * td, &s_, &c_);
       const double Tr = c_, Ti = -s_;
-      double hr[MAXM], hi[MAXM];
+      double hr[MJ], hi[MJ];
 #pragma unroll
-      for (int m = 0; m < MAXM; ++m) {
-        hr[m] = (m < M) ? (double)a.master[((int64_t)m * a.bank_rows + ib) * a.kpad + b] : 0.0;
-        hi[m] = (m < M) ? (double)a.master[((int64_t)m * a.bank_rows + ib) * a.kpad + B + b] : 0.0;
+      for (int j = 0; j < MJ; ++j) {
+        const int m = j / NP, p = j % NP;
+        const float *row = a.master + ((int64_t)m * a.bank_rows + ib) * a.kpad + 2 * p * B;
+        hr[j] = (j < J) ? (double)row[b] : 0.0;
+        hi[j] = (j < J) ? (double)row[B + b] : 0.0;
       }
 #pragma unroll
-      for (int m = 0; m < MAXM; ++m) {
-        if (m >= M) break;
+      for (int j = 0; j < MJ; ++j) {
+        if (j >= J) break;
+        const int m = j / NP;
         double cr, ci;
         if (a.rb_dh) {
           const double2 w = a.rb_dh[((int64_t)d * M + m) * B + b];
@@ -183,50 +194,54 @@ __global__ void __launch_bounds__(SW * 32)
           const double2 dd = a.data[(int64_t)d * B + b];
           cr = om * dd.x; ci = -om * dd.y;
         }
-        // (c T) h_m
+        // (c T) h_j
         const double ctr = cr * Tr - ci * Ti, cti = cr * Ti + ci * Tr;
-        Sr[m] += ctr * hr[m] - cti * hi[m];
-        Si[m] += ctr * hi[m] + cti * hr[m];
+        Sr[j] += ctr * hr[j] - cti * hi[j];
+        Si[j] += ctr * hi[j] + cti * hr[j];
 #pragma unroll
-        for (int mp = 0; mp < MAXM; ++mp) {
-          if (mp >= M) break;
+        for (int jp = 0; jp < MJ; ++jp) {
+          if (jp >= J) break;
           double wr, wi;
           if (a.rb_hh) {
-            const double2 w = a.rb_hh[(((int64_t)d * M + m) * M + mp) * B + b];
+            const double2 w = a.rb_hh[(((int64_t)d * M + m) * M + jp / NP) * B + b];
             wr = w.x; wi = w.y;
           } else {
             wr = 4.0 * a.w[b] / a.psd[(int64_t)d * B + b]; wi = 0.0;
           }
-          const double pr = hr[m] * hr[mp] + hi[m] * hi[mp], pi = hi[m] * hr[mp] - hr[m] * hi[mp];
-          Qr[m][mp] += wr * pr - wi * pi;
-          Qi[m][mp] += wr * pi + wi * pr;
+          const double pr = hr[j] * hr[jp] + hi[j] * hi[jp], pi = hi[j] * hr[jp] - hr[j] * hi[jp];
+          Qr[j][jp] += wr * pr - wi * pi;
+          Qi[j][jp] += wr * pi + wi * pr;
         }
       }
     }
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m) {
-      Sr[m] = wsum(Sr[m]);
-      Si[m] = wsum(Si[m]);
+    for (int j = 0; j < MJ; ++j) {
+      Sr[j] = wsum(Sr[j]);
+      Si[j] = wsum(Si[j]);
 #pragma unroll
-      for (int mp = 0; mp < MAXM; ++mp) {
-        Qr[m][mp] = wsum(Qr[m][mp]);
-        Qi[m][mp] = wsum(Qi[m][mp]);
+      for (int jp = 0; jp < MJ; ++jp) {
+        Qr[j][jp] = wsum(Qr[j][jp]);
+        Qi[j][jp] = wsum(Qi[j][jp]);
       }
     }
     if (e >= 0) {
+      auto resp = [&](int j) -> double2 {
+        if (NP == 2) return make_double2(a.F[((int64_t)e * D + d) * 2 + (j % 2)], 0.0);
+        return a.R[((int64_t)e * D + d) * M + j];
+      };
 #pragma unroll
-      for (int m = 0; m < MAXM; ++m) {
-        if (m >= M) break;
-        const double2 R = a.R[((int64_t)e * D + d) * M + m];
-        zr[m] += R.x * Sr[m] - R.y * Si[m];
-        zi[m] += R.x * Si[m] + R.y * Sr[m];
+      for (int j = 0; j < MJ; ++j) {
+        if (j >= J) break;
+        const double2 R = resp(j);
+        zr[j] += R.x * Sr[j] - R.y * Si[j];
+        zi[j] += R.x * Si[j] + R.y * Sr[j];
 #pragma unroll
-        for (int mp = 0; mp < MAXM; ++mp) {
-          if (mp >= M) break;
-          const double2 Rp = a.R[((int64_t)e * D + d) * M + mp];
+        for (int jp = 0; jp < MJ; ++jp) {
+          if (jp >= J) break;
+          const double2 Rp = resp(jp);
           const double rr = R.x * Rp.x + R.y * Rp.y, ri = R.y * Rp.x - R.x * Rp.y;  // R R'^*
-          Hr[m][mp] += rr * Qr[m][mp] - ri * Qi[m][mp];
-          Hi[m][mp] += rr * Qi[m][mp] + ri * Qr[m][mp];
+          Hr[j][jp] += rr * Qr[j][jp] - ri * Qi[j][jp];
+          Hi[j][jp] += rr * Qi[j][jp] + ri * Qr[j][jp];
         }
       }
     }
@@ -237,20 +252,21 @@ __global__ void __launch_bounds__(SW * 32)
     dh = 0.0;
     hh = 0.0;
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m) {
-      if (m >= M) break;
-      const int km = (a.mode_m[m] * o) % np;
+    for (int j = 0; j < MJ; ++j) {
+      if (j >= J) break;
+      const int mj = a.mode_m[j / NP];
+      const int km = (mj * o) % np;
       double sn, cs;
       sincospi(2.0 * (double)km / (double)np, &sn, &cs);
-      dh += zr[m] * cs - zi[m] * sn;
+      dh += zr[j] * cs - zi[j] * sn;
 #pragma unroll
-      for (int mp = 0; mp < MAXM; ++mp) {
-        if (mp >= M) break;
-        int kd = ((a.mode_m[m] - a.mode_m[mp]) * o) % np;
+      for (int jp = 0; jp < MJ; ++jp) {
+        if (jp >= J) break;
+        int kd = ((mj - a.mode_m[jp / NP]) * o) % np;
         if (kd < 0) kd += np;
         double s2, c2;
         sincospi(2.0 * (double)kd / (double)np, &s2, &c2);
-        hh += Hr[m][mp] * c2 - Hi[m][mp] * s2;
+        hh += Hr[j][jp] * c2 - Hi[j][jp] * s2;
       }
     }
   };
@@ -327,7 +343,10 @@ void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cd
                    int32_t *o_out, double *d_out, cudaStream_t st) {
   sample_row_cdf_kernel<<<1, 1024, 0, st>>>(a.n_int, a.ln_p_int, cdf);
   const int64_t blocks = (n + SW - 1) / SW;
-  sample_kernel<<<(unsigned)blocks, SW * 32, 0, st>>>(a, n, uni, cdf, i_out, e_out, o_out, d_out);
+  if (a.n_pol == 2)
+    sample_kernel<2><<<(unsigned)blocks, SW * 32, 0, st>>>(a, n, uni, cdf, i_out, e_out, o_out, d_out);
+  else
+    sample_kernel<1><<<(unsigned)blocks, SW * 32, 0, st>>>(a, n, uni, cdf, i_out, e_out, o_out, d_out);
 }
 
 }  // namespace dotpe

@@ -265,6 +265,8 @@ struct SampleArgs {
   const double2 *rb_dh, *rb_hh; // relative-binning weights, or null
   const double *t;              // [E][D]
   const double2 *R;             // [E][D][M]
+  const double *F;              // [E][D][2] antenna patterns (n_pol = 2)
+  int n_pol;                    // 2: polarisation-resolved bank (master rows [h+ | hx])
   const double *lw_ext;         // [E] or null
   const double *ln_p_int;       // [n_int] ln sum_{e,o} p_ieo
   const float *lnl;             // [n_int][n_ext] stored ln Lbar_ie
