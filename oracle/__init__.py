@@ -97,7 +97,9 @@ class OracleProblem:
     """Holds contiguous FP64 copies of one workload and the ctypes struct."""
 
     def __init__(self, bank, ext, event, i_slice=None, rb=None):
-        """rb: optional (w_dh [D, M, B], w_hh [D, M, M, B]) relative-binning weights (App. A)."""
+        """rb: optional (w_dh [D, J, B], w_hh [D, J, J, B]) relative-binning weights (App. A,
+        Eqs. dh_weights, hh_weights), one per (mode, polarisation) component: J = M for a
+        mode bank, J = 2M (index 2m + p) for a polarisation-resolved bank."""
         h = bank.h if i_slice is None else bank.h[i_slice]
         lw_i = bank.ln_w if i_slice is None else bank.ln_w[i_slice]
         self.mode_m = np.ascontiguousarray(bank.mode_m, dtype=np.int32)
@@ -116,12 +118,12 @@ class OracleProblem:
         I, M, B = self.h.shape[0], self.h.shape[1], self.h.shape[-1]
         E, D = self.t.shape
         self.shape = (I, E, D, M, B)
-        assert rb is None or self.n_pol == 1, "relative binning with a polarisation-resolved bank"
         self.n_phi = int(event.n_phi)
         self.u_min = float(event.u_min)
         self.rb = None if rb is None else (_c128(rb[0]), _c128(rb[1]))
         if self.rb is not None:
-            assert self.rb[0].shape == (D, M, B) and self.rb[1].shape == (D, M, M, B)
+            J = M * self.n_pol
+            assert self.rb[0].shape == (D, J, B) and self.rb[1].shape == (D, J, J, B)
         self.s = Problem(I, E, D, M, B, self.n_phi,
                          self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          _dp(self.f), _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),

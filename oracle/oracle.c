@@ -161,7 +161,9 @@ int or_direct_phases(const or_problem *p, int64_t i, int64_t e, double *dh_out, 
 /* Route O2: per-mode components, then phase rotation                        */
 /* ------------------------------------------------------------------------ */
 /* <h_{i m q}|h_{i m' q'}>_d = sum_b omega_{d b} h_{m q} h_{m' q'}^*  -> hm[d][M NP][M NP]
- * (index m NP + q; relative binning: the weight of each mode pair, Eq. h_h) */
+ * (index m NP + q; relative binning: the weight W^{<h|h>}_{d m m' q q' b} of each
+ * pair of (mode, polarisation) components, Eqs. hh_weights and h_h, stored
+ * [D][M NP][M NP][B] with the same component index) */
 static void mode_overlaps(const or_problem *p, const double *omega, int64_t i, cplx *hm) {
   const int M = p->n_modes, D = p->n_det, B = p->n_bins, NP = n_pol_of(p), J = M * NP;
   for (int d = 0; d < D; ++d)
@@ -170,7 +172,7 @@ static void mode_overlaps(const or_problem *p, const double *omega, int64_t i, c
         const int m = j / NP, q = j % NP, mp = jp / NP, qp = jp % NP;
         cplx acc = 0.0;
         for (int b = 0; b < B; ++b) {
-          cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)d * M + m) * M + mp) * B + b)
+          cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)d * J + j) * J + jp) * B + b)
                               : (cplx)omega[(int64_t)d * B + b];
           acc += wgt * hval(p, i, m, q, b) * conj(hval(p, i, mp, qp, b));
         }
@@ -178,10 +180,12 @@ static void mode_overlaps(const or_problem *p, const double *omega, int64_t i, c
       }
 }
 
-/* Data weight of mode m at bin b: c_{d b} = 4 w_b conj(d) / S (plain quadrature), or
- * (W^{<d|h>}_{d m b})^* with relative binning (Eq. d_h: Re<d|h> = Re sum_b c h). */
-static cplx data_weight(const or_problem *p, const double *c, int d, int m, int b) {
-  if (p->rb_dh) return conj(ld_c(p->rb_dh, ((int64_t)d * p->n_modes + m) * p->n_bins + b));
+/* Data weight of component (m, q) at bin b: c_{d b} = 4 w_b conj(d) / S (plain
+ * quadrature), or (W^{<d|h>}_{d m q b})^* with relative binning (Eqs. dh_weights,
+ * d_h: Re<d|h> = Re sum_b c h), stored [D][M NP][B] with index m NP + q. */
+static cplx data_weight(const or_problem *p, const double *c, int d, int m, int q, int b) {
+  const int NP = n_pol_of(p);
+  if (p->rb_dh) return conj(ld_c(p->rb_dh, ((int64_t)d * p->n_modes * NP + m * NP + q) * p->n_bins + b));
   return ld_c(c, (int64_t)d * p->n_bins + b);
 }
 
@@ -197,7 +201,7 @@ static void mode_components_cached(const or_problem *p, const double *c, const c
       for (int q = 0; q < NP; ++q) {
         cplx acc = 0.0;
         for (int b = 0; b < B; ++b)
-          acc += data_weight(p, c, d, m, b) * cexp(-I * TWO_PI * p->f[b] * t) * hval(p, i, m, q, b);
+          acc += data_weight(p, c, d, m, q, b) * cexp(-I * TWO_PI * p->f[b] * t) * hval(p, i, m, q, b);
         z[m] += resp(p, e, d, m, q) * acc;
       }
     for (int m = 0; m < M; ++m)

@@ -496,21 +496,30 @@ class RBWorkload:
     dff: np.ndarray        # [N] trapezoid weights (Hz)
     psd_fine: np.ndarray   # [D, N]
     data_fine: np.ndarray  # [D, N] complex
-    h0_fine: np.ndarray    # [M, N] complex: the reference waveform's modes
+    h0_fine: np.ndarray    # [J, N] complex: the reference waveform's components (modes, or
+                           # (mode, polarisation) pairs j = 2m + p of a polarisation-resolved bank)
     t0: np.ndarray         # [D] the reference's arrival time at each detector (s)
     nodes: np.ndarray      # [B] increasing indices into f_fine
     ratios: np.ndarray     # [I, M] mode amplitude ratios of the rows
     amp22: np.ndarray      # [I] 22-mode amplitude scale of the rows
+    wobble: tuple = None   # (iota0, amp, per) per row of a polarisation-resolved bank, else None
 
     def rows_fine(self, rows):
-        """The bank rows' modes on the fine grid: complex [len(rows), M, N]."""
+        """The bank rows on the fine grid: complex [len(rows), M, N], or
+        [len(rows), M, 2, N] for a polarisation-resolved bank."""
         rows = np.atleast_1d(rows)
-        return waveform_modes(self.f_fine, self.bank.mchirp[rows], self.ratios[rows], self.bank.mode_m,
-                              self.amp22[rows])
+        h = waveform_modes(self.f_fine, self.bank.mchirp[rows], self.ratios[rows], self.bank.mode_m,
+                           self.amp22[rows])
+        if self.wobble is None:
+            return h
+        iota0, amp, per = (x[rows] for x in self.wobble)
+        return wobbled_polarisations(h, self.f_fine, self.bank.mode_l, self.bank.mode_m, iota0, amp, per,
+                                     self.f_fine[0])
 
 
 def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.0, seed=0, mc0=12.0,
-                     spread=0.02, n_phi=32, noise=True, sky_sigma=0.05, t_sigma=5e-4, fmin=20.0, fmax=1024.0):
+                     spread=0.02, n_phi=32, noise=True, sky_sigma=0.05, t_sigma=5e-4, fmin=20.0, fmax=1024.0,
+                     precessing=False):
     """Full-resolution event and a bank stored on coarse nodes (App. A).
 
     The fine grid is uniform over [fmin, fmax] with n_fine points; the nodes are
@@ -523,6 +532,11 @@ def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.
     cos(iota) from the prior), like the output of an adaptive extrinsic
     sampler, so that the time shifts relative to the reference stay small.
     The reference's arrival times t0 are the injection's.
+    precessing: a polarisation-resolved bank h_{imp} (each row's inclination
+    wobbling with frequency as in precessing_bank, the reference's too), data
+    sum_{m,p} F_dp h0_mp e^{i m phi} T_d, and h0_fine the reference's 2M
+    components j = 2m + p, so that the weights carry the polarisation index of
+    App. A (W_{kmpb}, W_{kmm'pp'b}).
     """
     rng = np.random.default_rng(seed)
     f_fine = np.linspace(fmin, fmax, n_fine)
@@ -547,6 +561,10 @@ def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.
     norm = math.sqrt(np.sum(4.0 * dff * f_fine ** (-7.0 / 3.0) / psd_fine[0]))
     amp22 = (mc / mc0) ** (5.0 / 6.0) / norm
     h = waveform_modes(fb, mc, ratios, mode_m, amp22)
+    wob = None
+    if precessing:
+        wob = (np.arccos(rng.uniform(-1.0, 1.0, n_int)), rng.uniform(0.0, 0.5, n_int), rng.uniform(0.5, 2.0, n_int))
+        h = wobbled_polarisations(h, fb, mode_l, mode_m, *wob, fmin)
     # coarse-grid quadrature weights for the plain comparison on the same bins
     w = np.empty(n_bins)
     w[0] = 0.5 * (fb[1] - fb[0])
@@ -557,7 +575,14 @@ def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.
     e1 = make_extrinsic(rng, 1, n_det, bank)
     phi_inj = float(rng.uniform(0.0, 2.0 * np.pi))
     h0 = waveform_modes(f_fine, mc[:1], ratios[:1], mode_m, amp22[:1])[0]
-    unit = signal_at_detectors(h0, e1.R[0], e1.t[0], f_fine, mode_m, phi_inj, 1.0)
+    if precessing:
+        h0p = wobbled_polarisations(h0[None], f_fine, mode_l, mode_m, *(x[:1] for x in wob), fmin)[0]  # [M, 2, N]
+        ph = np.exp(1j * mode_m * phi_inj)
+        shift = np.exp(-2j * np.pi * f_fine[None, :] * e1.t[0][:, None])
+        unit = np.einsum("mpn,dp,m->dn", h0p, e1.F[0], ph) * shift
+        h0 = h0p.reshape(2 * n_modes, n_fine)
+    else:
+        unit = signal_at_detectors(h0, e1.R[0], e1.t[0], f_fine, mode_m, phi_inj, 1.0)
     u_inj = snr / math.sqrt(float(np.sum(4.0 * dff[None, :] * np.abs(unit) ** 2 / psd_fine)))
     data_fine = u_inj * unit
     if noise:
@@ -574,12 +599,26 @@ def make_rb_workload(n_int, n_ext, n_det, n_modes, n_bins, n_fine=65536, snr=15.
                n_phi=int(n_phi), injection=dict(i=0, e=None, phi=phi_inj, u=u_inj, snr=snr,
                                                 cos_iota=float(e1.cos_iota[0]), t_det=e1.t[0].copy()))
     return RBWorkload(bank=bank, ext=ext, event=ev, f_fine=f_fine, dff=dff, psd_fine=psd_fine, data_fine=data_fine,
-                      h0_fine=h0, t0=e1.t[0].copy(), nodes=nodes, ratios=ratios, amp22=amp22)
+                      h0_fine=h0, t0=e1.t[0].copy(), nodes=nodes, ratios=ratios, amp22=amp22, wobble=wob)
 
 
 # ----------------------------------------------------------------------------
 # polarisation-resolved (precessing) banks: h_{i m p}(f), p = +, x
 # ----------------------------------------------------------------------------
+def wobbled_polarisations(h, f, mode_l, mode_m, iota0, amp, per, f0):
+    """h_{i m p}(f) = K_{m p}(iota_i(f)) h_{i m}(f) with iota_i(f) = iota0_i +
+    amp_i sin(2 pi ln(f/f0) / per_i): h [I, M, N] -> [I, M, 2, N]."""
+    I, M, N = h.shape
+    x = np.log(f / f0)
+    iota = iota0[:, None] + amp[:, None] * np.sin(2.0 * np.pi * x[None, :] / per[:, None])
+    out = np.empty((I, M, 2, N), dtype=np.complex128)
+    for k in range(M):
+        kp, kx = polarisation_factors(int(mode_l[k]), int(mode_m[k]), iota)
+        out[:, k, 0, :] = kp * h[:, k, :]
+        out[:, k, 1, :] = kx * h[:, k, :]
+    return out
+
+
 def precessing_bank(base: Bank, rng, wobble_max=0.5):
     """A polarisation-resolved bank from a non-precessing one: each row's
     inclination wobbles with frequency, iota_i(f) = iota0_i + a_i sin(2 pi
@@ -587,18 +626,11 @@ def precessing_bank(base: Bank, rng, wobble_max=0.5):
     U[-1, 1]), standing in for the spin-precession of the paper's general case
     (Sec. IV.A): h_{i m p}(f) = K_{m p}(iota_i(f)) h_{i m}(f), whose + / x ratio
     is not fixed per mode.  Returns h [I, M, 2, B] and iota0 [I]."""
-    I, M, B = base.h.shape
+    I = base.h.shape[0]
     iota0 = np.arccos(rng.uniform(-1.0, 1.0, I))
     amp = rng.uniform(0.0, wobble_max, I)
     per = rng.uniform(0.5, 2.0, I)
-    x = np.log(base.f / base.f[0])
-    iota = iota0[:, None] + amp[:, None] * np.sin(2.0 * np.pi * x[None, :] / per[:, None])
-    h = np.empty((I, M, 2, B), dtype=np.complex128)
-    for k in range(M):
-        kp, kx = polarisation_factors(int(base.mode_l[k]), int(base.mode_m[k]), iota)
-        h[:, k, 0, :] = kp * base.h[:, k, :]
-        h[:, k, 1, :] = kx * base.h[:, k, :]
-    return h, iota0
+    return wobbled_polarisations(base.h, base.f, base.mode_l, base.mode_m, iota0, amp, per, base.f[0]), iota0
 
 
 def make_precessing_workload(n_int, n_ext, n_det, n_modes, n_bins, snr=15.0, seed=0, n_phi=32, noise=True,

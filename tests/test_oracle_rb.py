@@ -128,3 +128,97 @@ def test_preselection_uses_the_weights(rbw):
             x, *_ = np.linalg.lstsq(A, vd, rcond=None)
             res = vd - A @ x
             assert g[o, 0] == pytest.approx(0.5 * (vd @ vd - res @ res), rel=1e-9)
+
+
+# --------------------------------------------------------------------------
+# polarisation-resolved (precessing) bank: weights per (mode, polarisation)
+# component, W_{kmpb} and W_{kmm'pp'b} (Eqs. dh_weights, hh_weights)
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def rbp():
+    import oracle
+    oracle.build()
+    rw = synth.make_rb_workload(n_int=12, n_ext=6, n_det=2, n_modes=3, n_bins=120, n_fine=12000, seed=13,
+                                precessing=True)
+    w = oracle.rb_weights(rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, rw.nodes, rw.t0)
+    return oracle, rw, w
+
+
+def test_polarisation_resolved_reference_is_exact(rbp):
+    """Every component j = (m, p) of a precessing reference: the binned sums
+    equal the fine-grid <d|h0_j> and <h0_j|h0_j'>."""
+    oracle, rw, (wdh, whh) = rbp
+    D, J = rw.psd_fine.shape[0], rw.h0_fine.shape[0]
+    assert wdh.shape == (D, J, len(rw.nodes)) and whh.shape == (D, J, J, len(rw.nodes))
+    for d in range(D):
+        h0d = rw.h0_fine * shift(rw, d)[None, :]
+        at = h0d[:, rw.nodes]
+        for j in range(J):
+            assert np.sum(wdh[d, j] * np.conj(at[j])) == pytest.approx(
+                fine_ip(rw, d, rw.data_fine[d], h0d[j]), rel=1e-11)
+            for jp in range(J):
+                assert np.sum(whh[d, j, jp] * at[j] * np.conj(at[jp])) == pytest.approx(
+                    fine_ip(rw, d, h0d[j], h0d[jp]), rel=1e-11)
+
+
+def test_polarisation_resolved_pipeline(rbp):
+    """Route O2 of a precessing bank with the component weights: per-mode
+    components z_m = sum_{d,p} F_edp conj<d|h_mp T> and overlaps H_mm' =
+    sum_{d,p,p'} F_edp F_edp' <h_mp|h_m'p'> equal the fine-grid sums for the
+    reference row at the reference's arrival times."""
+    oracle, rw, (wdh, whh) = rbp
+    import copy
+    ext0 = copy.deepcopy(rw.ext)
+    ext0.t[:] = rw.t0[None, :]
+    P = oracle.OracleProblem(rw.bank, ext0, rw.event, rb=(wdh, whh))
+    hf = rw.rows_fine(0)[0]  # [M, 2, N]
+    M = hf.shape[0]
+    for e in (0, 3):
+        z, H = P.mode_components(0, e)
+        zt = np.zeros(M, np.complex128)
+        Ht = np.zeros((M, M), np.complex128)
+        for d in range(rw.psd_fine.shape[0]):
+            sh = shift(rw, d)
+            F = ext0.F[e, d]
+            for m in range(M):
+                for p in range(2):
+                    zt[m] += F[p] * np.conj(fine_ip(rw, d, rw.data_fine[d], hf[m, p] * sh))
+                    for mp in range(M):
+                        for pp in range(2):
+                            Ht[m, mp] += F[p] * F[pp] * fine_ip(rw, d, hf[m, p], hf[mp, pp])
+        assert np.max(np.abs(z - zt)) <= 1e-10 * np.max(np.abs(zt))
+        assert np.max(np.abs(H - Ht)) <= 1e-10 * np.max(np.abs(Ht))
+
+
+def test_fixed_inclination_components_reduce_to_mode_weights():
+    """A reference whose polarisations are h0_mp = K_mp h0_m with constant K:
+    the factor cancels in both ratios, so W_{k(m,p)b} = W_{kmb} and
+    W_{k(m,p)(m',p')b} = W_{kmm'b}; with those weights a fixed-inclination
+    polarisation-resolved bank gives the mode bank's likelihood with
+    R_edm = F_ed+ K_m+ + F_edx K_mx, pair by pair."""
+    import copy
+    import oracle
+    oracle.build()
+    rw = synth.make_rb_workload(n_int=10, n_ext=7, n_det=2, n_modes=3, n_bins=100, n_fine=10000, seed=17)
+    iota = np.arccos(0.35)
+    K = np.array([synth.polarisation_factors(int(l), int(m), iota)
+                  for l, m in zip(rw.bank.mode_l, rw.bank.mode_m)])  # [M, 2]
+    M = K.shape[0]
+    h0p = (rw.h0_fine[:, None, :] * K[:, :, None]).reshape(2 * M, -1)
+    wdh, whh = oracle.rb_weights(rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, rw.nodes, rw.t0)
+    pdh, phh = oracle.rb_weights(rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, h0p, rw.nodes, rw.t0)
+    D, B = wdh.shape[0], wdh.shape[-1]
+    np.testing.assert_allclose(pdh.reshape(D, M, 2, B), np.repeat(wdh[:, :, None, :], 2, axis=2), rtol=1e-11,
+                               atol=1e-13 * np.abs(wdh).max())
+    np.testing.assert_allclose(phh.reshape(D, M, 2, M, 2, B),
+                               np.broadcast_to(whh[:, :, None, :, None, :], (D, M, 2, M, 2, B)), rtol=1e-11,
+                               atol=1e-13 * np.abs(whh).max())
+    bank_p = synth.Bank(**{**rw.bank.__dict__, "h": rw.bank.h[:, :, None, :] * K[None, :, :, None]})
+    ext_k = copy.deepcopy(rw.ext)
+    ext_k.R = np.einsum("edp,mp->edm", rw.ext.F, K)
+    Pp = oracle.OracleProblem(bank_p, rw.ext, rw.event, rb=(pdh, phh))
+    Pn = oracle.OracleProblem(rw.bank, ext_k, rw.event, rb=(wdh, whh))
+    pi, pe = np.divmod(np.arange(10 * 7), 7)
+    a, b = Pp.eval_pairs(pi, pe), Pn.eval_pairs(pi, pe)
+    np.testing.assert_allclose(a["lnl_marg"], b["lnl_marg"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(a["lnl_ml_max"], b["lnl_ml_max"], rtol=1e-10, atol=1e-10)
