@@ -453,8 +453,10 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
     import oracle
     import synth
     D, M, B, N_FINE = 3, 4, 378, 131072
+    prec_bank = args.precessing
     rw = synth.make_rb_workload(n_int=args.n_int, n_ext=args.n_ext, n_det=D, n_modes=M, n_bins=B, n_fine=N_FINE,
-                                snr=15.0, seed=6, n_phi=N_PHI)
+                                snr=15.0, seed=6, n_phi=N_PHI, precessing=prec_bank)
+    resp = rw.ext.F if prec_bank else rw.ext.R  # antenna patterns of a polarisation-resolved bank
     I, E = args.n_int, args.n_ext
     ctx = ctx_factory()
     bank = rw.bank
@@ -471,12 +473,13 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
             a = a.view(np.float64)
         return torch.from_numpy(a.copy()).to(dev)
 
-    d_t, d_R, d_lw = to_dev(rw.ext.t), to_dev(rw.ext.R), to_dev(rw.ext.ln_w)
+    d_t, d_R, d_lw = to_dev(rw.ext.t), to_dev(resp), to_dev(rw.ext.ln_w)
     d_rb = (to_dev(wdh), to_dev(whh))
 
     def submit(precision, stream=None, rb=d_rb, t=d_t, R=d_R, lw=d_lw):
-        return dp.dotpe_event_submit(ctx, bid, 0, I, None, None, t, R, lw, n_phi=N_PHI, u_min=rw.event.u_min,
-                                     cut_delta=args.cut, precision=precision, stream=stream, rb=rb)
+        return dp.dotpe_event_submit(ctx, bid, 0, I, None, None, t, None if prec_bank else R, lw, n_phi=N_PHI,
+                                     u_min=rw.event.u_min, cut_delta=args.cut, precision=precision, stream=stream,
+                                     rb=rb, F=R if prec_bank else None)
 
     def one(precision):
         eid = submit(precision)
@@ -520,7 +523,7 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
     te = time.perf_counter()
     for _ in range(args.steps):
         w = weights()
-        eid = submit(args.precision, rb=w, t=rw.ext.t, R=rw.ext.R, lw=rw.ext.ln_w)
+        eid = submit(args.precision, rb=w, t=rw.ext.t, R=resp, lw=rw.ext.ln_w)
         dp.dotpe_event_wait(ctx, eid, 600.0)
         dp.dotpe_evidence(ctx, eid)
         dp.dotpe_event_release(ctx, eid)
@@ -529,7 +532,10 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
     step_ms = ev_ms + w_ms
     mixed = args.precision == "mixed"
     dom_ms = st["fused_ms"] - (st["refine_ms"] if mixed else 0.0)
-    flops = algorithmic_flops_per_pair(B, M, D) * pairs
+    # <d|h> over both polarisations and the 21-float <h|h> records for a polarisation-resolved bank
+    fpp = (8 * 2 * B * M + D * 2 * 21) if prec_bank else algorithmic_flops_per_pair(B, M, D)
+    kpad = -(-(4 if prec_bank else 2) * B // 64) * 64
+    flops = fpp * pairs
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops / (dom_ms * 1e-3) / 1e12
     cpu = None
@@ -550,8 +556,10 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "fp16" if args.precision in ("fp16", "fp16x3", "mixed") else args.precision, "data": "synthetic",
-        "config": {"workload": f"relative binning: N_f={B} nodes of a {N_FINE}-point grid, I={I} rows around the "
-                               f"signal x E={E} samples near it, D={D}, M={M}, N_phi={N_PHI}, SNR 15",
+        "config": {"workload": f"relative binning: N_f={B} nodes of a {N_FINE}-point grid, I={I} "
+                               + ("polarisation-resolved (precessing) " if prec_bank else "")
+                               + f"rows around the signal x E={E} samples near it, D={D}, M={M}, N_phi={N_PHI}, "
+                               "SNR 15",
                    "precision": args.precision, "ml_cut_delta": args.cut, "rb_weights_ms": w_ms,
                    "event_ms": ev_ms, "dlnz_vs_fp32": abs(evs[-1]["ln_z"] - ref["ln_z"]),
                    "marginalised_fraction": evs[-1]["n_marginalised"] / (pairs * N_PHI),
@@ -559,16 +567,16 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
                                              if evs[-1]["n_refined_tiles"] >= 0 else None),
                    "screen_ms": dom_ms, "refine_ms": st["refine_ms"], "prep_ms": st["prep_ms"],
                    "fp32_path_ms": ref_st["device_ms"],
-                   "l2": f"inputs larger than L2 (bank operand planes {I * M * 768 * 2 * 2 / 1e9:.2f} GB, "
+                   "l2": f"inputs larger than L2 (bank operand planes {I * M * kpad * 2 * 2 / 1e9:.2f} GB, "
                          "re-read every step)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                      "frac": achieved / sustained, "traffic": None,
                      "kernel": "tc_fused_kernel screening pass with relative-binning weights", "kernel_ms": dom_ms,
-                     "flops_per_pair": algorithmic_flops_per_pair(B, M, D),
+                     "flops_per_pair": fpp,
                      "peak_source": f"{peak_src} bf16_tflops_sustained"},
         "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(rw.f_fine.nbytes + rw.dff.nbytes + rw.psd_fine.nbytes + rw.data_fine.nbytes
-                                          + rw.h0_fine.nbytes + rw.ext.t.nbytes + rw.ext.R.nbytes + rw.ext.ln_w.nbytes),
+                                          + rw.h0_fine.nbytes + rw.ext.t.nbytes + resp.nbytes + rw.ext.ln_w.nbytes),
                 "d2h_bytes_per_step": int(wdh.nbytes + whh.nbytes + 96)},
         "gpu_launches": None, "clocks": clocks, "cpu_baseline": cpu,
     }
@@ -853,6 +861,8 @@ def main():
     ap.add_argument("--workload", default="event",
                     choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--precessing", action="store_true",
+                    help="rb: a polarisation-resolved bank with weights per (mode, polarisation) component")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
     args = ap.parse_args()
     if args.workload == "serve" and "--events" not in sys.argv:

@@ -125,8 +125,9 @@ typedef struct dotpe_config {
  *   patterns F_{e d p} (dotpe_event_desc.F) in place of R.  Every precision
  *   applies (the tensor-core kernels contract K = 4 n_bins, padded); its events
  *   are not batched with one another (dotpe_batch_submit in a precision other
- *   than DOTPE_PREC_FP32 returns DOTPE_E_UNSUPPORTED); dotpe_preselect and
- *   relative binning return DOTPE_E_UNSUPPORTED. */
+ *   than DOTPE_PREC_FP32 returns DOTPE_E_UNSUPPORTED); relative binning takes
+ *   weights per (mode, polarisation) component; dotpe_preselect returns
+ *   DOTPE_E_UNSUPPORTED. */
 typedef struct dotpe_bank_desc {
   int64_t n_int;
   int n_modes;
@@ -160,14 +161,16 @@ typedef struct dotpe_bank_desc {
  *   depend on block_rows beyond FP64 rounding, except where a maximum known
  *   block by block decides what is kept: the ML cut's superset, and in MIXED
  *   precision which tiles far below the maximum are refined.
- * rb_dh [n_det][n_modes][n_bins], rb_hh [n_det][n_modes][n_modes][n_bins]
- *   (complex, host or device; both or neither): relative-binning weights
+ * rb_dh [n_det][J][n_bins], rb_hh [n_det][J][J][n_bins]
+ *   (complex, host or device; both or neither; J = n_modes, or 2 n_modes
+ *   (mode, polarisation) components j = 2m + p for a polarisation-resolved
+ *   bank): relative-binning weights
  *   (App. A, from dotpe_rb_weights) replacing the plain quadrature: the data
- *   weight of mode m becomes conj(W^{<d|h>}_{d m b}) and <h_m|h_m'>_d uses
- *   W^{<h|h>}_{d m m' b}.  psd and data are then not read (may be NULL); the
+ *   weight of component j becomes conj(W^{<d|h>}_{d j b}) and <h_j|h_j'>_d uses
+ *   W^{<h|h>}_{d j j' b}.  psd and data are then not read (may be NULL); the
  *   cross-term cache is keyed by the <h|h> weights; the mixed-precision
- *   screening margin takes max_m sum_{d,b} |W^{<d|h>}|^2 / W^{<h|h>}_{mm} in
- *   place of <d|d>.
+ *   screening margin takes max_j sum_{d,b} |W^{<d|h>}_{d j b}|^2 / W^{<h|h>}_{d j j b}
+ *   in place of <d|d>.
  * F [n_ext][n_det][2] (double, host or device): antenna patterns F_{e d p}
  *   (p = +, x) of each sample, read for a polarisation-resolved bank (n_pol = 2),
  *   which then ignores R (may be NULL).  A mode bank ignores F (may be NULL).
@@ -290,7 +293,11 @@ typedef struct dotpe_presel_out {
  * df_fine [n_fine] (quadrature weights), psd [n_det][n_fine],
  * data [n_det][n_fine] complex, h0 [n_modes][n_fine] complex, t0 [n_det]
  * (may be NULL: 0), nodes [n_bins] (strictly increasing indices into
- * f_fine): host or device.  Computed on the device in FP64. */
+ * f_fine): host or device.  Computed on the device in FP64.
+ * n_modes counts components, 1..8: the modes of a mode bank, or, for a
+ * polarisation-resolved bank, its (mode, polarisation) pairs j = 2m + p with
+ * h0 [2 M][n_fine] the reference's h0_{mp} (the weights then carry the
+ * polarisation index, W_{d m p b} and W_{d m m' p p' b}, as App. A writes them). */
 typedef struct dotpe_rb_desc {
   int n_det, n_modes;
   int64_t n_fine;

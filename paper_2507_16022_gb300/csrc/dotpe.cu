@@ -236,7 +236,7 @@ static ScratchLayout scratch_layout(const Event &e) {
   size_t elem = (L.pack_kind == 0) ? 4 : 2;
   const int64_t T = (int64_t)L.n_itile * L.n_etile;
   Carver c;
-  L.c = c.take<float2>(D * M * B);
+  L.c = c.take<float2>(D * M * b.n_pol * B);  // data weights per (mode, polarisation) component
   L.omega = c.take<float>(D * B);
   L.fh = c.take<float>(B);
   L.fl = c.take<float>(B);
@@ -471,7 +471,7 @@ static void event_block(dotpe_ctx *ctx, Event &e, EventRun &R, int64_t r0, int64
   if (e.xent) {
     R.P.mx = e.xent->mx + (e.i0 + r0) * e.D * (b.n_pol == 2 ? REC_P : REC);
   } else if (b.n_pol == 2) {
-    launch_cross_terms_pol(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.mode_m, b.master, R.pa.omega,
+    launch_cross_terms_pol(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.mode_m, b.master, R.pa.omega, e.rb_hh,
                            (float *)(R.scr + R.L.mx), ctx->n_sms, st);
   } else {
     launch_cross_terms(nr, e.i0 + r0, b.I, b.M, e.D, b.B, b.Kpad, b.master, R.pa.omega, e.rb_hh,
@@ -639,7 +639,8 @@ static int xcache_build(dotpe_ctx *ctx, Bank &b, uint64_t key, int D, const floa
   }
   CUDA_OR_FAIL(cudaEventCreateWithFlags(&x->ready, cudaEventDisableTiming));
   if (b.n_pol == 2)
-    launch_cross_terms_pol(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.mode_m, b.master, omega, x->mx, ctx->n_sms, st);
+    launch_cross_terms_pol(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.mode_m, b.master, omega, rb_hh, x->mx, ctx->n_sms,
+                           st);
   else
     launch_cross_terms(b.I, 0, b.I, b.M, D, b.B, b.Kpad, b.master, omega, rb_hh, x->mx, ctx->n_sms, st);
   CUDA_OR_FAIL(cudaEventRecord(x->ready, st));
@@ -1277,7 +1278,8 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
 // ---------------------------------------------------------------------------
 static int rb_weights_locked(dotpe_ctx *ctx, const dotpe_rb_desc *d, double *w_dh, double *w_hh) {
   if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
-  if (d->n_modes < 1 || d->n_modes > MAXM) return fail(DOTPE_E_INVALID, "n_modes=%d not in 1..%d", d->n_modes, MAXM);
+  if (d->n_modes < 1 || d->n_modes > 2 * MAXM)
+    return fail(DOTPE_E_INVALID, "n_modes=%d components not in 1..%d", d->n_modes, 2 * MAXM);
   if (d->n_bins < 2 || d->n_fine < d->n_bins) return fail(DOTPE_E_INVALID, "n_bins=%d, n_fine=%lld", d->n_bins,
                                                            (long long)d->n_fine);
   if (!d->f_fine || !d->df_fine || !d->psd || !d->data || !d->h0 || !d->nodes || !w_dh || !w_hh)
@@ -1733,7 +1735,6 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   if (pol && d->precision != DOTPE_PREC_FP32 && d->n_det > POL_TC_MAXD)
     return fail(DOTPE_E_UNSUPPORTED, "a polarisation-resolved bank with n_det=%d runs in FP32 only (tensor cores: "
                 "n_det <= %d)", d->n_det, POL_TC_MAXD);
-  if (pol && rb) return fail(DOTPE_E_UNSUPPORTED, "relative binning with a polarisation-resolved bank");
   if (!rb && (size_t)d->n_det * b->B * sizeof(float) > 227 * 1024)
     return fail(DOTPE_E_UNSUPPORTED, "n_det * n_bins = %lld: the <h|h> weights exceed shared memory",
                 (long long)d->n_det * b->B);
@@ -1762,9 +1763,10 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
   size_t need = scratch_layout(*e).total + keep_bytes_of(*e);
   Carver c;
   const int64_t D = e->D, B = b->B, M = b->M;
+  const int64_t J = M * b->n_pol;  // relative-binning components (mode, polarisation)
   size_t o_psd = c.take<double>(D * B), o_data = c.take<double2>(D * B), o_t = c.take<double>(NE * D);
   size_t o_R = c.take<double2>(NE * D * M), o_lw = c.take<double>(NE);
-  size_t o_rbd = c.take<double2>(rb ? D * M * B : 0), o_rbh = c.take<double2>(rb ? D * M * M * B : 0);
+  size_t o_rbd = c.take<double2>(rb ? D * J * B : 0), o_rbh = c.take<double2>(rb ? D * J * J * B : 0);
   size_t o_F = c.take<double>(pol ? NE * D * 2 : 0);
   e->in_bytes = c.off;
   if (need + e->in_bytes + b->bytes > ctx->budget) {
@@ -1803,8 +1805,8 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
                      {d->R, e->R, (!pol && d->R) ? (size_t)(NE * D * M * 16) : 0},
                      {d->F, e->F, pol ? (size_t)(NE * D * 2 * 8) : 0},
                      {d->ln_w_ext, e->lwe, d->ln_w_ext ? (size_t)(NE * 8) : 0},
-                     {d->rb_dh, e->rb_dh, rb ? (size_t)(D * M * B * 16) : 0},
-                     {d->rb_hh, e->rb_hh, rb ? (size_t)(D * M * M * B * 16) : 0}};
+                     {d->rb_dh, e->rb_dh, rb ? (size_t)(D * J * B * 16) : 0},
+                     {d->rb_hh, e->rb_hh, rb ? (size_t)(D * J * J * B * 16) : 0}};
   size_t host_total = 0;
   for (auto &p : pieces)
     if (p.n && !is_device_ptr(p.src)) host_total += p.n;
@@ -1835,7 +1837,7 @@ static int submit_locked(dotpe_ctx *ctx, const dotpe_event_desc *d, uint64_t gro
     }
   }
   {
-    int rc = rb ? psd_hash(e->D, (int)B, nullptr, &e->psd_key, d->rb_hh, (size_t)(2 * D * M * M * B))
+    int rc = rb ? psd_hash(e->D, (int)B, nullptr, &e->psd_key, d->rb_hh, (size_t)(2 * D * J * J * B))
                 : psd_hash(e->D, (int)B, d->psd, &e->psd_key);
     if (rc != DOTPE_OK) return cleanup(rc);
   }

@@ -1,6 +1,8 @@
 // Relative-binning weights (App. A, Eqs. dh_weights, hh_weights).
 //
-// For detector d, mode m (and m') and coarse node b:
+// The components m are the bank's modes, or its (mode, polarisation) pairs
+// m = 2 m_az + p for a polarisation-resolved bank (W_{kmpb}, W_{kmm'pp'b}); up to
+// 2 MAXM of them.  For detector d, component m (and m') and coarse node b:
 //   W^{<d|h>}_{d m b}    = sum_n 4 dff_n d_d(f_n) h0_dm^*(f_n) s_b(f_n) / S_d(f_n)  /  h0_dm^*(f_b)
 //   W^{<h|h>}_{d m m' b} = sum_n 4 dff_n h0_dm(f_n) h0_dm'^*(f_n) s_b(f_n) / S_d(f_n) / (h0_dm(f_b) h0_dm'^*(f_b))
 // with h0_dm(f) = h0_m(f) e^{-2 pi i f t0_d} (the reference arriving at the
@@ -17,8 +19,11 @@ namespace dotpe {
 
 namespace {
 constexpr int RB_THREADS = 256;
-constexpr int RB_NPAIR = MAXM * (MAXM + 1) / 2;  // upper triangle m <= m'
-constexpr int RB_NACC = 2 * (MAXM + RB_NPAIR);   // re, im of the dh and hh sums
+// NC: components per weight set, MAXM modes or 2 MAXM (mode, polarisation) pairs
+template <int NC> struct RbAcc {
+  static constexpr int NPAIR = NC * (NC + 1) / 2;  // upper triangle m <= m'
+  static constexpr int NACC = 2 * (NC + NPAIR);    // re, im of the dh and hh sums
+};
 
 // e^{-2 pi i f t} in FP64 (the phase reduced with sincospi of the product f t)
 __device__ __forceinline__ double2 shift64(double f, double t) {
@@ -38,12 +43,14 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 }  // namespace
 
+template <int NC>
 __global__ void __launch_bounds__(RB_THREADS)
     rb_weights_kernel(int D, int M, int64_t N, const double *__restrict__ ff, const double *__restrict__ dff,
                       const double *__restrict__ psd, const double2 *__restrict__ data,
                       const double2 *__restrict__ h0, const double *__restrict__ t0, int B,
                       const int64_t *__restrict__ node, double2 *__restrict__ w_dh, double2 *__restrict__ w_hh,
                       int *status) {
+  constexpr int RB_NACC = RbAcc<NC>::NACC;
   __shared__ double red[RB_THREADS / 32][RB_NACC];
   __shared__ double fn3[3];
   const int d = blockIdx.x / B, b = blockIdx.x % B;
@@ -76,23 +83,23 @@ __global__ void __launch_bounds__(RB_THREADS)
     }
     const double2 T = shift64(f, td);
     const double2 dd = data[(int64_t)d * N + n];
-    double2 hv[MAXM];
+    double2 hv[NC];
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m) hv[m] = (m < M) ? cmul(h0[(int64_t)m * N + n], T) : make_double2(0.0, 0.0);
+    for (int m = 0; m < NC; ++m) hv[m] = (m < M) ? cmul(h0[(int64_t)m * N + n], T) : make_double2(0.0, 0.0);
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m) {
+    for (int m = 0; m < NC; ++m) {
       const double2 v = cmulc(dd, hv[m]);  // d h0^*
       acc[2 * m] += wgt * v.x;
       acc[2 * m + 1] += wgt * v.y;
     }
     int p = 0;
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m)
+    for (int m = 0; m < NC; ++m)
 #pragma unroll
-      for (int mp = m; mp < MAXM; ++mp, ++p) {
+      for (int mp = m; mp < NC; ++mp, ++p) {
         const double2 v = cmulc(hv[m], hv[mp]);  // h0_m h0_m'^*
-        acc[2 * MAXM + 2 * p] += wgt * v.x;
-        acc[2 * MAXM + 2 * p + 1] += wgt * v.y;
+        acc[2 * NC + 2 * p] += wgt * v.x;
+        acc[2 * NC + 2 * p + 1] += wgt * v.y;
       }
   }
   // block reduction (fixed order: warp shuffles, then warp 0 over the warps)
@@ -112,8 +119,8 @@ __global__ void __launch_bounds__(RB_THREADS)
       tot[q] = v;
     }
     const double2 T = shift64(fb, td);
-    double2 hb[MAXM];
-    for (int m = 0; m < MAXM; ++m) {
+    double2 hb[NC];
+    for (int m = 0; m < NC; ++m) {
       hb[m] = (m < M) ? cmul(h0[(int64_t)m * N + node[b]], T) : make_double2(1.0, 0.0);
       if (m < M && hb[m].x == 0.0 && hb[m].y == 0.0) atomicCAS(status, 0, DEV_E_SHAPE);
     }
@@ -122,10 +129,10 @@ __global__ void __launch_bounds__(RB_THREADS)
       w_dh[((int64_t)d * M + m) * B + b] = cdiv(num, make_double2(hb[m].x, -hb[m].y));
     }
     int p = 0;
-    for (int m = 0; m < MAXM; ++m)
-      for (int mp = m; mp < MAXM; ++mp, ++p) {
+    for (int m = 0; m < NC; ++m)
+      for (int mp = m; mp < NC; ++mp, ++p) {
         if (m >= M || mp >= M) continue;
-        const double2 num = make_double2(tot[2 * MAXM + 2 * p], tot[2 * MAXM + 2 * p + 1]);
+        const double2 num = make_double2(tot[2 * NC + 2 * p], tot[2 * NC + 2 * p + 1]);
         const double2 w = cdiv(num, cmulc(hb[m], hb[mp]));
         w_hh[(((int64_t)d * M + m) * M + mp) * B + b] = w;
         if (mp != m) w_hh[(((int64_t)d * M + mp) * M + m) * B + b] = make_double2(w.x, -w.y);
@@ -136,8 +143,12 @@ __global__ void __launch_bounds__(RB_THREADS)
 void launch_rb_weights(int D, int M, int64_t N, const double *ff, const double *dff, const double *psd,
                        const double2 *data, const double2 *h0, const double *t0, int B, const int64_t *node,
                        double2 *w_dh, double2 *w_hh, int *status, cudaStream_t st) {
-  rb_weights_kernel<<<(unsigned)(D * B), RB_THREADS, 0, st>>>(D, M, N, ff, dff, psd, data, h0, t0, B, node, w_dh,
-                                                              w_hh, status);
+  if (M <= MAXM)
+    rb_weights_kernel<MAXM><<<(unsigned)(D * B), RB_THREADS, 0, st>>>(D, M, N, ff, dff, psd, data, h0, t0, B, node,
+                                                                      w_dh, w_hh, status);
+  else
+    rb_weights_kernel<2 * MAXM><<<(unsigned)(D * B), RB_THREADS, 0, st>>>(D, M, N, ff, dff, psd, data, h0, t0, B,
+                                                                          node, w_dh, w_hh, status);
 }
 
 }  // namespace dotpe

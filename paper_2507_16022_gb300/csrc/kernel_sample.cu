@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(SW * 32)
         const int m = j / NP;
         double cr, ci;
         if (a.rb_dh) {
-          const double2 w = a.rb_dh[((int64_t)d * M + m) * B + b];
+          const double2 w = a.rb_dh[((int64_t)d * J + j) * B + b];
           cr = w.x; ci = -w.y;
         } else {
           const double om = 4.0 * a.w[b] / a.psd[(int64_t)d * B + b];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(SW * 32)
           if (jp >= J) break;
           double wr, wi;
           if (a.rb_hh) {
-            const double2 w = a.rb_hh[(((int64_t)d * M + m) * M + jp / NP) * B + b];
+            const double2 w = a.rb_hh[(((int64_t)d * J + j) * J + jp) * B + b];
             wr = w.x; wi = w.y;
           } else {
             wr = 4.0 * a.w[b] / a.psd[(int64_t)d * B + b]; wi = 0.0;

@@ -38,7 +38,8 @@ struct PrepArgs {
   float *gscale;   // 1 float out
   float *sqrt_dd;  // 1 float out: sqrt<d|d> (Eq. inner_product, FP64 sum)
   int *status;
-  // relative binning (App. A), both or neither: W^{<d|h>} [D][M][B], W^{<h|h>} [D][M][M][B]
+  // relative binning (App. A), both or neither: W^{<d|h>} [D][J][B], W^{<h|h>} [D][J][J][B]
+  // over the J = M n_pol (mode, polarisation) components
   const double2 *rb_dh, *rb_hh;
   // polarisation-resolved bank (n_pol = 2): real antenna patterns F [E][D][2] replace R;
   // G32 is then [M][2][E][B] and the packed rows carry two polarisation blocks along K
@@ -53,10 +54,11 @@ void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int
                         cudaStream_t st);
 void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, int B, int Kpad, int NP,
                            const void *src, int dtype, float *master, float *amax, int *status, cudaStream_t st);
-// polarisation-resolved bank: row records of REC_P floats per detector (kernels_prep.cu)
+// polarisation-resolved bank: row records of REC_P floats per detector (kernels_prep.cu);
+// rb_hh non-null: relative-binning weights per component pair [D][2M][2M][B] instead of omega
 void launch_cross_terms_pol(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
-                            const int *mode_m, const float *master, const float *omega, float *mx, int n_sms,
-                            cudaStream_t st);
+                            const int *mode_m, const float *master, const float *omega, const double2 *rb_hh,
+                            float *mx, int n_sms, cudaStream_t st);
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf /*[2][n]*/,
                              __half *hf /*[2][n]*/, float *scale_out, cudaStream_t st);
 void launch_build_dm_table(float4 *tab, cudaStream_t st);

@@ -23,9 +23,11 @@ namespace dotpe {
 // ---------------------------------------------------------------------------
 // K0
 // ---------------------------------------------------------------------------
-// Data weights of every mode, c[d][m][b]: the plain quadrature's
-// 4 w_b conj(d_d(f_b)) / S_d(f_b) (the same for every mode), or, with relative
-// binning (App. A, Eq. d_h), conj(W^{<d|h>}_{d m b}).
+// Data weights of every component j (a mode, or a (mode, polarisation) pair
+// j = 2m + p of a polarisation-resolved bank; M counts components here),
+// c[d][j][b]: the plain quadrature's 4 w_b conj(d_d(f_b)) / S_d(f_b) (the same
+// for every component), or, with relative binning (App. A, Eqs. dh_weights,
+// d_h), conj(W^{<d|h>}_{d j b}).
 __global__ void prep_bins_kernel(int D, int B, int M, const double *__restrict__ f, const double *__restrict__ w,
                                  const double *__restrict__ psd, const double2 *__restrict__ data,
                                  const double2 *__restrict__ rb_dh, float2 *__restrict__ c,
@@ -204,8 +206,9 @@ __global__ void build_G_kernel(int64_t E, int D, int M, int B, const float *__re
   atomic_max_nonneg(gmax, a);
 }
 
-// Polarisation-resolved bank: G_{m p}[b, e] = sum_d F_{e d p} e^{-2 pi i f_b t_{e d}} c_{d m b},
-// G [M][2][E][B] (Eq. dh_ieo with the polarisation index; real antenna patterns).
+// Polarisation-resolved bank: G_{m p}[b, e] = sum_d F_{e d p} e^{-2 pi i f_b t_{e d}} c_{d m p b},
+// G [M][2][E][B] (Eq. dh_ieo with the polarisation index; real antenna patterns); the data
+// weights c [D][M][2][B] are per component (the same for both with plain quadrature).
 __global__ void build_G_pol_kernel(int64_t E, int D, int M, int B, const float *__restrict__ fh,
                                    const float *__restrict__ fl, const float *__restrict__ th,
                                    const float *__restrict__ tl, const float2 *__restrict__ c,
@@ -225,10 +228,11 @@ __global__ void build_G_pol_kernel(int64_t E, int D, int M, int B, const float *
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) {
       if (m >= M) break;
-      const float2 cc = c[((int64_t)d * M + m) * B + b];
-      const float2 W = make_float2(T.x * cc.x - T.y * cc.y, T.x * cc.y + T.y * cc.x);
-      g[m][0].x += fp * W.x; g[m][0].y += fp * W.y;
-      g[m][1].x += fx * W.x; g[m][1].y += fx * W.y;
+      const float2 c0 = c[((int64_t)(d * M + m) * 2) * B + b], c1 = c[((int64_t)(d * M + m) * 2 + 1) * B + b];
+      const float2 W0 = make_float2(T.x * c0.x - T.y * c0.y, T.x * c0.y + T.y * c0.x);
+      const float2 W1 = make_float2(T.x * c1.x - T.y * c1.y, T.x * c1.y + T.y * c1.x);
+      g[m][0].x += fp * W0.x; g[m][0].y += fp * W0.y;
+      g[m][1].x += fx * W1.x; g[m][1].y += fx * W1.y;
     }
   }
   float a = 0.f;
@@ -405,14 +409,22 @@ __global__ void cross_terms_kernel(int64_t n_rows, int64_t row0, int64_t I_bank,
 //   [0..2]  delta = 0:  X0 = sum_a <h_a+|h_a+>, Y0 = sum_a 2 Re <h_a+|h_ax>, W0 = sum_a <h_ax|h_ax>
 //   [3 + 6 (delta - 1) ...]  delta = 1..3, complex (re, im):
 //           X = sum <h_a+|h_c+>, Y = sum (<h_a+|h_cx> + <h_ax|h_c+>), W = sum <h_ax|h_cx>  (a > c)
-// with <a|b>_d = sum_b omega_{d b} a b^*; master rows [Re h+ | Im h+ | Re hx | Im hx | 0].
+// with <h_j|h_j'>_d = sum_b omega_{d b} h_j h_j'^*, or, with relative binning
+// (App. A, Eqs. hh_weights, h_h), sum_b W^{<h|h>}_{d j j' b} h_j h_j'^* over the
+// (mode, polarisation) components j = 2m + p (RB: rb_hh [D][2M][2M][B]);
+// master rows [Re h+ | Im h+ | Re hx | Im hx | 0].
+template <bool RB>
 __global__ void cross_terms_pol_kernel(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
                                        int4 mode_m, const float *__restrict__ master,
-                                       const float *__restrict__ omega, float *__restrict__ mx) {
+                                       const float *__restrict__ omega, const double2 *__restrict__ rb_hh,
+                                       float *__restrict__ mx) {
   extern __shared__ float om_s[];
-  for (int k = threadIdx.x; k < D * B; k += blockDim.x) om_s[k] = omega[k];
-  __syncthreads();
+  if (!RB) {
+    for (int k = threadIdx.x; k < D * B; k += blockDim.x) om_s[k] = omega[k];
+    __syncthreads();
+  }
   const int mm[MAXM] = {mode_m.x, mode_m.y, mode_m.z, mode_m.w};
+  const int J = 2 * M;
   const int lane = threadIdx.x & 31;
   const int64_t warp_global = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -439,12 +451,25 @@ __global__ void cross_terms_pol_kernel(int64_t n_rows, int64_t row0, int64_t I_b
 #pragma unroll
       for (int d = 0; d < MAXD; ++d) {
         if (d >= D) break;
-        const float w = om_s[d * B + b];
+        const float om = RB ? 0.f : om_s[d * B + b];
+        // weight of the component pair (j, j') at this bin, and w h_j h_j'^*
+        auto wgt = [&](int j, int jp) -> float2 {
+          if (!RB) return make_float2(om, 0.f);
+          const double2 v = __ldg(&rb_hh[(((int64_t)d * J + j) * J + jp) * B + b]);
+          return make_float2((float)v.x, (float)v.y);
+        };
+        auto term = [&](int a, int p, int c, int pc) -> float2 {
+          const float pr = hr[a][p] * hr[c][pc] + hi[a][p] * hi[c][pc];
+          const float pi = hi[a][p] * hr[c][pc] - hr[a][p] * hi[c][pc];
+          const float2 w = wgt(2 * a + p, 2 * c + pc);
+          return make_float2(w.x * pr - w.y * pi, w.x * pi + w.y * pr);
+        };
 #pragma unroll
         for (int a = 0; a < MAXM; ++a) {
-          acc[d][0] += w * (hr[a][0] * hr[a][0] + hi[a][0] * hi[a][0]);
-          acc[d][1] += 2.f * w * (hr[a][0] * hr[a][1] + hi[a][0] * hi[a][1]);
-          acc[d][2] += w * (hr[a][1] * hr[a][1] + hi[a][1] * hi[a][1]);
+          if (a >= M) break;
+          acc[d][0] += term(a, 0, a, 0).x;
+          acc[d][1] += 2.f * term(a, 0, a, 1).x;
+          acc[d][2] += term(a, 1, a, 1).x;
         }
 #pragma unroll
         for (int a = 1; a < MAXM; ++a)
@@ -452,20 +477,17 @@ __global__ void cross_terms_pol_kernel(int64_t n_rows, int64_t row0, int64_t I_b
           for (int c = 0; c < a; ++c) {
             if (a >= M) continue;
             const int g = 3 + 6 * (mm[a] - mm[c] - 1);
-            // h_a+ h_c+^*, h_a+ h_cx^* + h_ax h_c+^*, h_ax h_cx^*
-            const float xr = hr[a][0] * hr[c][0] + hi[a][0] * hi[c][0], xi = hi[a][0] * hr[c][0] - hr[a][0] * hi[c][0];
-            const float y1r = hr[a][0] * hr[c][1] + hi[a][0] * hi[c][1], y1i = hi[a][0] * hr[c][1] - hr[a][0] * hi[c][1];
-            const float y2r = hr[a][1] * hr[c][0] + hi[a][1] * hi[c][0], y2i = hi[a][1] * hr[c][0] - hr[a][1] * hi[c][0];
-            const float wr = hr[a][1] * hr[c][1] + hi[a][1] * hi[c][1], wi = hi[a][1] * hr[c][1] - hr[a][1] * hi[c][1];
+            // h_a+ h_c+^*, h_a+ h_cx^* + h_ax h_c+^*, h_ax h_cx^* (each with its weight)
+            const float2 x = term(a, 0, c, 0), y1 = term(a, 0, c, 1), y2 = term(a, 1, c, 0), w = term(a, 1, c, 1);
 #pragma unroll
             for (int z = 0; z < 3; ++z)
               if (g == 3 + 6 * z) {
-                acc[d][3 + 6 * z] += w * xr;
-                acc[d][4 + 6 * z] += w * xi;
-                acc[d][5 + 6 * z] += w * (y1r + y2r);
-                acc[d][6 + 6 * z] += w * (y1i + y2i);
-                acc[d][7 + 6 * z] += w * wr;
-                acc[d][8 + 6 * z] += w * wi;
+                acc[d][3 + 6 * z] += x.x;
+                acc[d][4 + 6 * z] += x.y;
+                acc[d][5 + 6 * z] += y1.x + y2.x;
+                acc[d][6 + 6 * z] += y1.y + y2.y;
+                acc[d][7 + 6 * z] += w.x;
+                acc[d][8 + 6 * z] += w.y;
               }
           }
       }
@@ -606,14 +628,15 @@ __global__ void dist_marg_eval_kernel(int64_t n, const float *__restrict__ dh, c
 static inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 void launch_prep(const PrepArgs &a, cudaStream_t st) {
-  prep_bins_kernel<<<nblk((int64_t)a.D * a.B, 256), 256, 0, st>>>(a.D, a.B, a.M, a.f, a.w, a.psd, a.data, a.rb_dh,
-                                                                a.c, a.omega, a.fh, a.fl, a.status);
-  if (a.sqrt_dd) {
-    if (a.rb_dh) rb_norm_kernel<<<1, 256, 0, st>>>(a.D, a.M, a.B, a.rb_dh, a.rb_hh, a.sqrt_dd);
-    else data_norm_kernel<<<1, 256, 0, st>>>(a.D, a.B, a.w, a.psd, a.data, a.sqrt_dd);
-  }
   const bool pol = (a.n_pol == 2);
   const int NP = pol ? 2 : 1;
+  // data weights per (mode, polarisation) component: c [D][M NP][B]
+  prep_bins_kernel<<<nblk((int64_t)a.D * a.B, 256), 256, 0, st>>>(a.D, a.B, a.M * NP, a.f, a.w, a.psd, a.data,
+                                                                a.rb_dh, a.c, a.omega, a.fh, a.fl, a.status);
+  if (a.sqrt_dd) {
+    if (a.rb_dh) rb_norm_kernel<<<1, 256, 0, st>>>(a.D, a.M * NP, a.B, a.rb_dh, a.rb_hh, a.sqrt_dd);
+    else data_norm_kernel<<<1, 256, 0, st>>>(a.D, a.B, a.w, a.psd, a.data, a.sqrt_dd);
+  }
   prep_ext_kernel<<<nblk(a.E * a.D, 256), 256, 0, st>>>(a.E, a.D, a.M, a.t, a.R, pol ? a.F : nullptr, a.th, a.tl,
                                                         a.Rf, a.qx, a.status);
   if (pol)
@@ -722,19 +745,24 @@ void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, in
 }
 
 void launch_cross_terms_pol(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
-                            const int *mode_m, const float *master, const float *omega, float *mx, int n_sms,
-                            cudaStream_t st) {
+                            const int *mode_m, const float *master, const float *omega, const double2 *rb_hh,
+                            float *mx, int n_sms, cudaStream_t st) {
   int bs = 256;
   int64_t blocks = (n_rows * 32 + bs - 1) / bs;
   int64_t cap = (int64_t)n_sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   const int4 mm = make_int4(mode_m[0], M > 1 ? mode_m[1] : 0, M > 2 ? mode_m[2] : 0, M > 3 ? mode_m[3] : 0);
+  if (rb_hh) {
+    cross_terms_pol_kernel<true><<<(unsigned)blocks, bs, 0, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, mm, master,
+                                                                  omega, rb_hh, mx);
+    return;
+  }
   const size_t smem = sizeof(float) * (size_t)D * B;
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(cross_terms_pol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cross_terms_pol_kernel<<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B,
-                                                                                      Kpad, mm, master, omega, mx);
+    cudaFuncSetAttribute(cross_terms_pol_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cross_terms_pol_kernel<false><<<(unsigned)blocks, bs, smem, st>>>(n_rows, row0, I_bank, M, D, B, Kpad, mm, master,
+                                                                    omega, nullptr, mx);
 }
 
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf, __half *hf,

@@ -18,8 +18,9 @@ the polarisation index p and real antenna patterns F_{edp}).
   polarisation) component) match the oracle's resampling with the same
   uniforms: identical (i, e, o) except within the weights' tolerance of a
   cumulative boundary, distances to 2e-3.
-* Pre-selection, relative binning and batches in a tensor-core precision are
-  refused with DOTPE_E_UNSUPPORTED; a missing F with DOTPE_E_INVALID.
+* Pre-selection and batches in a tensor-core precision are refused with
+  DOTPE_E_UNSUPPORTED; a missing F with DOTPE_E_INVALID.  (Relative binning
+  with component weights is tested with the other relative-binning cases.)
 """
 import numpy as np
 import pytest
@@ -249,11 +250,6 @@ def test_refusals(dpx, pwl):
                                   n_phi=32, precision="fp32")
         assert ei.value.status == dp.DOTPE_E_INVALID
         D, B = wl.event.psd.shape
-        rb = (np.ones((D, M, B), np.complex128), np.ones((D, M, M, B), np.complex128))
-        with pytest.raises(dp.DotpeError) as ei:
-            dp.dotpe_event_submit(ctx, bid, 0, I, None, None, wl.ext.t, None, n_phi=32, precision="fp32",
-                                  rb=rb, F=wl.ext.F)
-        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
         t_grid = np.zeros((D, 16))
         with pytest.raises(dp.DotpeError) as ei:
             dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,

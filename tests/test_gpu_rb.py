@@ -143,3 +143,78 @@ def test_preselection_with_weights_against_oracle(dpx, rbw):
         assert abs(ref["lnl_inco"][r["arg_i"]] - ref["lnl_inco"].max()) <= tol.sum(1).max()
         # the injected (reference) row is kept
         assert 0 in set(r["selected"].tolist())
+
+
+# --------------------------------------------------------------------------
+# polarisation-resolved (precessing) bank: weights per (mode, polarisation)
+# component, W_{kmpb} and W_{kmm'pp'b} (App. A as written)
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def rbp():
+    import oracle
+    # 8 components (4 modes x 2 polarisations), 378 nodes, a ragged row tile
+    rw = synth.make_rb_workload(n_int=520, n_ext=150, n_det=3, n_modes=4, n_bins=378, n_fine=65536, seed=57,
+                                snr=20.0, precessing=True)
+    w = oracle.rb_weights(rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, rw.nodes, rw.t0)
+    return rw, w
+
+
+def test_component_weights_kernel_matches_oracle(dpx, rbp):
+    dp, ctx = dpx
+    rw, (wdh, whh) = rbp
+    gdh, ghh = dp.dotpe_rb_weights(ctx, rw.f_fine, rw.dff, rw.psd_fine, rw.data_fine, rw.h0_fine, rw.nodes, rw.t0)
+    assert gdh.shape == (3, 8, 378) and ghh.shape == (3, 8, 8, 378)
+    assert np.max(np.abs(gdh - wdh)) <= 1e-11 * np.max(np.abs(wdh))
+    assert np.max(np.abs(ghh - whh)) <= 1e-11 * np.max(np.abs(whh))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
+def test_precessing_event_with_component_weights(dpx, rbp, precision):
+    """A polarisation-resolved event with relative binning against the
+    oracle's route O2 with the same component weights, all pairs: the
+    coherent path's bounds (K = 4B here: TC_ACC over Kpad = 1536), FP32 with
+    an ln L^ML-proportional term (the peak here is ln L^ML ~ 200)."""
+    dp, ctx = dpx
+    rw, (wdh, whh) = rbp
+    import oracle
+    P = oracle.OracleProblem(rw.bank, rw.ext, rw.event, rb=(wdh, whh))
+    grid, _ = P.eval_grid(0.0)
+    ref = P.evidence(grid)
+    bank = rw.bank
+    I, E = bank.h.shape[0], rw.ext.t.shape[0]
+    bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
+    try:
+        eid = dp.dotpe_event_submit(ctx, bid, 0, I, None, None, rw.ext.t, None, rw.ext.ln_w,
+                                    n_phi=rw.event.n_phi, u_min=rw.event.u_min, cut_delta=0.0,
+                                    precision=precision, flags=dp.DOTPE_FLAG_STORE_LNL, rb=(wdh, whh), F=rw.ext.F)
+        dp.dotpe_event_wait(ctx, eid, 120.0)
+        ev = dp.dotpe_evidence(ctx, eid)
+        lnl = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E)
+        ml = dp.dotpe_lnl_blocks(ctx, eid, 0, I, 0, E, what=dp.DOTPE_LNL_ML_MAX)
+        dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    ml_ref = grid["lnl_ml_max"]
+    mlp = np.maximum(ml_ref, 0)
+    tc_acc = 2 * (1536 // 16) * 2.0 ** -24
+    if precision == "mixed":
+        near = ml_ref >= ml_ref.max() - 30.0
+        u = 2.0 ** -11
+        J = wdh.shape[1]
+        dd = max(float(np.sum(np.abs(wdh[:, j]) ** 2 / whh[:, j, j].real)) for j in range(J))
+        far_tol = 2e-2 + 4 * u * mlp + 2 * u * np.sqrt(2 * mlp + 1) * np.sqrt(dd)
+        tol = np.where(near, 1e-3 + tc_acc * mlp, far_tol)
+    elif precision == "fp16x3":
+        tol = 1e-3 + tc_acc * mlp
+    else:
+        # FP32 operands (weights, phases, records) carry ~2^-17 relative error,
+        # which moves ln L^ML = z^2 / 2 hh by about twice that, relative
+        tol = 1e-3 + 2.0 ** -16 * mlp
+    d1 = np.abs(lnl - grid["lnl_marg"])
+    d2 = np.abs(ml - ml_ref)
+    print(f"precessing rb event {precision}: max |d ln Lbar| {d1.max():.3e}, max |d ln L^ML| {d2.max():.3e}, "
+          f"d ln Z {ev['ln_z'] - ref['ln_z']:.3e}, peak ln L^ML {ml_ref.max():.1f}")
+    assert np.all(d1 <= tol)
+    assert np.all(d2 <= tol)
+    assert abs(ev["ln_z"] - ref["ln_z"]) <= 1e-2
+    assert (ev["arg_i"], ev["arg_e"]) == ref["arg"][:2]
