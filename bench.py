@@ -68,7 +68,7 @@ CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
 # capture of a 16,384 x 2,048 event (the traffic grows with I*E: the bank is
 # re-read once per L2 band), keyed by precision; absent = not measured for the
 # current kernel version.
-DRAM_BYTES_PER_PAIR = {"mixed": (308.87e6 + 14.79e6) / (16384 * 2048)}  # screening launch
+DRAM_BYTES_PER_PAIR = {"mixed": (308.76e6 + 14.37e6) / (16384 * 2048)}  # screening launch
 
 
 def rank_seed(base, rank):
