@@ -214,6 +214,33 @@ def test_ragged_shapes(dpx, shape, precision):
         assert (got["ev"]["arg_e"], got["ev"]["arg_o"]) == tuple(ref_ev["arg"][1:])
 
 
+@pytest.mark.parametrize("case", ["one_pair_one_phase", "odd_phase_grid", "zero_data"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
+def test_degenerate_cases(dpx, case, precision):
+    """Degenerate inputs against the oracle: a single (i, e) pair with one
+    detector, one mode and N_phi = 1; an odd phase grid (N_phi = 7: no (phi,
+    phi + pi) pairing); data identically zero (every <d|h> = 0, so ln L^ML = 0,
+    ln Lbar is the distance marginal at dh = 0 and ln Z <= 0)."""
+    import oracle
+    dp, ctx = dpx
+    if case == "one_pair_one_phase":
+        wl = synth.make_workload(n_int=1, n_ext=1, n_det=1, n_modes=1, n_bins=16, snr=10.0, seed=81, n_phi=1)
+    elif case == "odd_phase_grid":
+        wl = synth.make_workload(n_int=130, n_ext=33, n_det=2, n_modes=3, n_bins=64, snr=12.0, seed=82, n_phi=7)
+    else:
+        wl = synth.make_workload(n_int=140, n_ext=40, n_det=2, n_modes=4, n_bins=64, snr=12.0, seed=83, n_phi=8)
+        wl.event.data[:] = 0.0
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event)
+    grid, _ = P.eval_grid(0.0)
+    ref_ev = P.evidence(grid)
+    got = run(dp, ctx, wl, precision)
+    check_pairs(got, grid, precision, data_norm(wl))
+    assert abs(got["ev"]["ln_z"] - ref_ev["ln_z"]) <= 1e-2
+    if case == "zero_data":
+        assert got["ev"]["ln_z"] <= 1e-6
+        assert np.all(got["ml"] == 0.0)
+
+
 def test_noiseless_peak(dpx):
     dp, ctx = dpx
     wl = synth.make_workload(n_int=500, n_ext=96, n_det=3, n_modes=4, n_bins=128, snr=15.0, seed=5,
