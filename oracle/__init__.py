@@ -222,25 +222,30 @@ class PreselStruct(ctypes.Structure):
                 ("psd", ctypes.POINTER(ctypes.c_double)), ("data", ctypes.POINTER(ctypes.c_double)),
                 ("h", ctypes.POINTER(ctypes.c_double)), ("pol", ctypes.POINTER(ctypes.c_double)),
                 ("t_grid", ctypes.POINTER(ctypes.c_double)),
-                ("rb_dh", ctypes.POINTER(ctypes.c_double)), ("rb_hh", ctypes.POINTER(ctypes.c_double))]
+                ("rb_dh", ctypes.POINTER(ctypes.c_double)), ("rb_hh", ctypes.POINTER(ctypes.c_double)),
+                ("n_pol", ctypes.c_int)]
 
 
 class PreselProblem:
     """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of one event
-    over bank rows: h [I, M, B], pol [I, M, 2] (K_{imp}, p = +, x), t_grid [D, n_t]."""
+    over bank rows: h [I, M, B] with pol [I, M, 2] (K_{imp}, p = +, x), or a
+    polarisation-resolved bank h [I, M, 2, B] (pol None); t_grid [D, n_t]."""
 
     def __init__(self, f, w, mode_m, h, pol, psd, data, t_grid, n_phi=32, rb=None):
         self.mode_m = np.ascontiguousarray(mode_m, dtype=np.int32)
         self.f = np.ascontiguousarray(f, dtype=np.float64)
         self.w = np.ascontiguousarray(w, dtype=np.float64)
         self.h = _c128(h)
-        self.pol = _c128(pol)
+        self.n_pol = 2 if self.h.ndim == 4 else 1
+        self.pol = _c128(pol) if self.n_pol == 1 else np.zeros(1, np.complex128)
         self.psd = np.ascontiguousarray(psd, dtype=np.float64)
         self.data = _c128(data)
         self.t_grid = np.ascontiguousarray(t_grid, dtype=np.float64)
-        I, M, B = self.h.shape
+        I, M, B = self.h.shape[0], self.h.shape[1], self.h.shape[-1]
         D, NT = self.t_grid.shape
-        assert self.pol.shape == (I, M, 2) and self.psd.shape == (D, B) and self.data.shape == (D, B)
+        assert self.n_pol == 1 or (rb is None and self.h.shape[2] == 2)
+        assert (self.n_pol == 2 or self.pol.shape == (I, M, 2)) and self.psd.shape == (D, B) \
+            and self.data.shape == (D, B)
         self.shape = (I, D, M, B, NT)
         self.n_phi = int(n_phi)
         self.rb = None if rb is None else (_c128(rb[0]), _c128(rb[1]))
@@ -250,7 +255,7 @@ class PreselProblem:
                               _dp(self.h.view(np.float64)), _dp(self.pol.view(np.float64)),
                               _dp(self.t_grid),
                               None if rb is None else _dp(self.rb[0].view(np.float64)),
-                              None if rb is None else _dp(self.rb[1].view(np.float64)))
+                              None if rb is None else _dp(self.rb[1].view(np.float64)), self.n_pol)
 
     def grid(self, i, k):
         """ln L^ML_{i k o t} [n_phi, n_t] (Eq. single_det_ML)."""

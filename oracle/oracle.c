@@ -749,10 +749,16 @@ static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, i
     free(hp); free(z); free(ov); free(hh);
     return -1;
   }
+  /* h_{i m p}: K_{i m p} h_{i m} for a mode bank, the bank's own polarisations
+   * for a polarisation-resolved one (App. B's general form) */
   for (int q = 0; q < 2; ++q)
     for (int m = 0; m < M; ++m) {
-      cplx K = ld_c(p->pol, (i * M + m) * 2 + q);
-      for (int b = 0; b < B; ++b) hp[((int64_t)q * M + m) * B + b] = K * ld_c(p->h, (i * M + m) * B + b);
+      if (p->n_pol == 2) {
+        for (int b = 0; b < B; ++b) hp[((int64_t)q * M + m) * B + b] = ld_c(p->h, ((i * M + m) * 2 + q) * B + b);
+      } else {
+        cplx K = ld_c(p->pol, (i * M + m) * 2 + q);
+        for (int b = 0; b < B; ++b) hp[((int64_t)q * M + m) * B + b] = K * ld_c(p->h, (i * M + m) * B + b);
+      }
     }
   /* <h|h>_{i k o p p'}: frequency sums per mode pair, then the phase factors */
   const int pq[3][2] = {{0, 0}, {0, 1}, {1, 1}};

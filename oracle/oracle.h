@@ -162,10 +162,11 @@ typedef struct or_presel {
   int n_int, n_det, n_modes, n_bins, n_t, n_phi;
   const int *mode_m;
   const double *f, *w, *psd, *data;  /* data: complex [D][B] */
-  const double *h;                   /* complex [I][M][B] */
-  const double *pol;                 /* complex [I][M][2]: K_{i m +}, K_{i m x} */
+  const double *h;                   /* complex [I][M][B], or [I][M][2][B] when n_pol = 2 */
+  const double *pol;                 /* complex [I][M][2]: K_{i m +}, K_{i m x} (n_pol = 1) */
   const double *t_grid;              /* [D][n_t] arrival times at detector k (s) */
-  const double *rb_dh, *rb_hh;       /* relative binning as in or_problem, or NULL */
+  const double *rb_dh, *rb_hh;       /* relative binning as in or_problem, or NULL (n_pol = 1) */
+  int n_pol;                         /* 2: polarisation-resolved bank, h_{i m p} read directly */
 } or_presel_problem;
 
 /* Eqs. x_ML, single_det_ML: max over real (x_+, x_x) of

@@ -225,3 +225,52 @@ def test_noise_only_projection_is_chi_squared_with_two_dof(orc):
     # mean 2 +- 5 sigma (sigma = 2/sqrt(1500)); exponential tail P(chi2_2 > 6) = e^-3
     assert abs(vals.mean() - 2.0) < 5 * 2.0 / math.sqrt(len(vals))
     assert abs(np.mean(vals > 6.0) - math.exp(-3.0)) < 5 * math.sqrt(math.exp(-3) / len(vals))
+
+
+# ---------------------------------------------------------------------------
+# polarisation-resolved (precessing) bank: h_{i m p} read directly
+# ---------------------------------------------------------------------------
+def pol_templates(p, hpol, i, k, o, t, n_phi):
+    """h_{i k o t p}(f_b) = sum_m h_{imp} e^{i m phi_o} e^{-2 pi i f t}, built directly."""
+    phi = 2.0 * np.pi * o / n_phi
+    shift = np.exp(-2j * np.pi * p["f"] * p["t_grid"][k, t])
+    return [sum(hpol[i, m, q] * np.exp(1j * p["mode_m"][m] * phi) for m in range(hpol.shape[1])) * shift
+            for q in range(2)]
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_polarisation_resolved_grid_equals_projection(orc, seed):
+    """Random independent + and x components per mode (no common factor):
+    the grid equals the projection onto the two built templates."""
+    p = tiny_problem(seed)
+    rng = np.random.default_rng(seed + 100)
+    I, M, B = p["h"].shape
+    hpol = rng.standard_normal((I, M, 2, B)) + 1j * rng.standard_normal((I, M, 2, B))
+    n_phi = 5
+    q = dict(p, h=hpol, pol=None)
+    P = orc.PreselProblem(n_phi=n_phi, **q)
+    D, NT = p["t_grid"].shape
+    for i in range(I):
+        for k in range(D):
+            g = P.grid(i, k)
+            omega = 4.0 * p["w"] / p["psd"][k]
+            vd = whiten(p["data"][k], omega)
+            for o in range(n_phi):
+                for t in range(NT):
+                    hp, hx = pol_templates(p, hpol, i, k, o, t, n_phi)
+                    want = projection_ml(vd, [whiten(hp, omega), whiten(hx, omega)])
+                    assert g[o, t] == pytest.approx(want, rel=1e-10), (i, k, o, t)
+
+
+def test_polarisation_resolved_with_factors_is_the_mode_bank(orc):
+    """h_{imp} = K_{imp} h_{im}: the pre-selection of the polarisation-resolved
+    bank equals that of the mode bank with the factors (rows, maxima, kept set)."""
+    wl = synth.make_workload(n_int=40, n_ext=4, n_det=3, n_modes=4, n_bins=64, seed=21)
+    ps = synth.make_presel_inputs(wl, n_t=16, dt=5e-4, seed=22)
+    hpol = wl.bank.h[:, :, None, :] * ps.pol[:, :, :, None]
+    a = orc.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h, ps.pol, wl.event.psd,
+                          wl.event.data, ps.t_grid, n_phi=8).run(delta=20.0)
+    b = orc.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, hpol, None, wl.event.psd,
+                          wl.event.data, ps.t_grid, n_phi=8).run(delta=20.0)
+    np.testing.assert_allclose(b["ml"], a["ml"], rtol=1e-11, atol=1e-11)
+    np.testing.assert_array_equal(b["keep"], a["keep"])
