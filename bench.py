@@ -367,7 +367,8 @@ def presel_cpu_baseline(wl, ps, target_s=12.0):
 
     def run(n):
         rows = np.sort(rng.choice(I, size=n, replace=False))
-        P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h[rows], ps.pol[rows],
+        P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h[rows],
+                                 None if ps.pol is None else ps.pol[rows],
                                  wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI)
         t0 = time.perf_counter()
         P.run(n_threads=cores)
@@ -386,11 +387,17 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
     """Incoherent single-detector pre-selection (Sec. IV.D, App. B) of one event
     over the whole 65,536-row bank; a step is one dotpe_preselect call."""
     import synth
-    wl = synth.make_workload(**dict(WORKLOAD, n_int=args.n_int), n_phi=N_PHI)
-    ps = synth.make_presel_inputs(wl)
     I, D, M, B = args.n_int, WORKLOAD["n_det"], WORKLOAD["n_modes"], WORKLOAD["n_bins"]
+    pres = args.precessing  # a polarisation-resolved bank: its own h_imp, the FP32 kernel
+    if pres:
+        wl = synth.make_precessing_workload(I, 4, D, M, B, snr=WORKLOAD["snr"], seed=9, n_phi=N_PHI)
+        t = (np.arange(128) - 64) * 5.0e-4
+        ps = synth.PreselInputs(pol=None, cos_iota=None, t_grid=np.tile(t, (D, 1)))
+    else:
+        wl = synth.make_workload(**dict(WORKLOAD, n_int=args.n_int), n_phi=N_PHI)
+        ps = synth.make_presel_inputs(wl)
     NT = ps.t_grid.shape[1]
-    prec = args.precision if args.precision != "mixed" else "fp16x3"
+    prec = "fp32" if pres else (args.precision if args.precision != "mixed" else "fp16x3")
     ctx = ctx_factory()
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w, pol=ps.pol)
 
@@ -412,11 +419,13 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
     # useful work: the per-mode complex GEMM of Eq. dh_itop, one pass (8 B flops per
-    # (i, k, m, t)); the split precision issues three passes
-    flops = 8.0 * I * M * D * NT * B
+    # (i, k, m, t), per polarisation for a polarisation-resolved bank); the split
+    # precision issues three passes
+    flops = 8.0 * I * M * D * NT * B * (2 if pres else 1)
     kern = statistics.median(ker_ms)
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops / (kern * 1e-3) / 1e12
+    peak = FP32_SIMT_PEAK_TFLOPS if pres else sustained
     evals = I * D * NT * N_PHI
     dms = sum(dev_ms)
     cpu = None if args.no_cpu_baseline else presel_cpu_baseline(wl, ps)
@@ -424,19 +433,25 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
         "metric": "pre-selected bank rows/s", "value": I * args.steps / (dms * 1e-3), "unit": "rows/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if prec.startswith("bf16") else "fp16", "data": "synthetic",
-        "config": {"workload": f"incoherent pre-selection of one event: I={I} bank rows, D={D}, M={M}, B={B}, "
+        "dtype": "fp32" if pres else ("bf16" if prec.startswith("bf16") else "fp16"), "data": "synthetic",
+        "config": {"workload": f"incoherent pre-selection of one event: I={I} "
+                               + ("polarisation-resolved (precessing) " if pres else "")
+                               + f"bank rows, D={D}, M={M}, B={B}, "
                                f"N_t={NT} (0.5 ms grid), N_phi={N_PHI}, window {CUT_DELTA:g}",
                    "precision": prec,
-                   "l2": f"inputs larger than L2 (bank operand planes {I * M * 2 * B * 2 * 2 / 1e9:.2f} GB per call)",
+                   "l2": (f"inputs larger than L2 (FP32 bank {I * M * 4 * B * 4 / 1e9:.2f} GB per call)" if pres else
+                          f"inputs larger than L2 (bank operand planes {I * M * 2 * B * 2 * 2 / 1e9:.2f} GB per call)"),
                    "evaluations_per_s": evals * args.steps / (dms * 1e-3), "kept_rows": r["n_selected"],
                    "kernel_ms": kern, "device_ms_per_call": dms / args.steps},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
-                     "frac": achieved / sustained, "traffic": None,
-                     "kernel": "presel_kernel (per-mode <d|h> GEMM against the time grid + 2x2 ML epilogue)",
+        "roofline": {"bound": "alu" if pres else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": ("presel_pol_kernel (FP32 per-component <d|h> against the time grid + 2x2 ML)"
+                                if pres else
+                                "presel_kernel (per-mode <d|h> GEMM against the time grid + 2x2 ML epilogue)"),
                      "kernel_ms": kern, "flops_per_call": flops,
                      "issued_tflops": achieved * (3 if prec.endswith("x3") else 1),
-                     "peak_source": f"{peak_src} bf16_tflops_sustained"},
+                     "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if pres
+                                     else f"{peak_src} bf16_tflops_sustained")},
         "e2e": {"value": I * args.steps / wall, "unit": "rows/s",
                 "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + ps.t_grid.nbytes),
                 "d2h_bytes_per_step": int(8 * I + 8 * r["n_selected"] + 64)},
@@ -862,7 +877,8 @@ def main():
                     choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--precessing", action="store_true",
-                    help="rb: a polarisation-resolved bank with weights per (mode, polarisation) component")
+                    help="rb, presel: a polarisation-resolved bank (rb: weights per (mode, polarisation) "
+                         "component; presel: the FP32 kernel)")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
     args = ap.parse_args()
     if args.workload == "serve" and "--events" not in sys.argv:

@@ -1073,9 +1073,9 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   auto bit = ctx->banks.find(d->bank_id);
   if (bit == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)d->bank_id);
   Bank &b = *bit->second;
-  if (!b.pol) return fail(DOTPE_E_INVALID, "bank %llu was loaded without polarisation factors (pol)",
-                          (unsigned long long)d->bank_id);
-  if (b.n_pol == 2) return fail(DOTPE_E_UNSUPPORTED, "pre-selection of a polarisation-resolved bank");
+  const bool polb = (b.n_pol == 2);  // polarisation-resolved bank: its own h_imp, FP32 kernel
+  if (!polb && !b.pol) return fail(DOTPE_E_INVALID, "bank %llu was loaded without polarisation factors (pol)",
+                                   (unsigned long long)d->bank_id);
   if (d->i0 < 0 || d->i1 <= d->i0 || d->i1 > b.I)
     return fail(DOTPE_E_INVALID, "slice [%lld,%lld) of %lld rows", (long long)d->i0, (long long)d->i1, (long long)b.I);
   if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
@@ -1086,7 +1086,11 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
   if ((!rb && (!d->psd || !d->data)) || !d->t_grid) return fail(DOTPE_E_INVALID, "null input array");
   const int prec = d->precision;
-  if (prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 && prec != DOTPE_PREC_BF16X3)
+  if (polb && prec != DOTPE_PREC_FP32)
+    return fail(DOTPE_E_UNSUPPORTED, "a polarisation-resolved bank is pre-selected in FP32 only");
+  if (polb && rb) return fail(DOTPE_E_UNSUPPORTED, "pre-selection of a polarisation-resolved bank with relative binning");
+  if (!polb && prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 &&
+      prec != DOTPE_PREC_BF16X3)
     return fail(DOTPE_E_INVALID, "pre-selection precision %d (FP16, FP16X3, BF16 or BF16X3)", prec);
   if (d->flags != 0) return fail(DOTPE_E_INVALID, "flags must be 0");
   const int64_t NI = d->i1 - d->i0;
@@ -1115,8 +1119,9 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   const size_t o_fh = c.take<float>(B), o_fl = c.take<float>(B);
   const size_t o_G = c.take<float2>((size_t)MG * D * NTP * B);
   const size_t o_gmax = c.take<float>(1), o_gs = c.take<float>(1);
-  const size_t o_pack = c.take<uint16_t>((size_t)planes * MG * 2 * D * NTP * b.Kpad);
-  const size_t o_mx = own_mx ? c.take<float>((size_t)NI * D * REC) : 0;
+  const int rec = polb ? REC_P : REC;
+  const size_t o_pack = c.take<uint16_t>(polb ? 0 : (size_t)planes * MG * 2 * D * NTP * b.Kpad);
+  const size_t o_mx = own_mx ? c.take<float>((size_t)NI * D * rec) : 0;
   const size_t o_keys = c.take<unsigned long long>((size_t)NI * D);
   const size_t o_ml = c.take<float>((size_t)NI * D), o_arg = c.take<int>((size_t)NI * D * 2);
   const size_t o_inco = c.take<double>(NI), o_sel = c.take<int64_t>(NI);
@@ -1165,17 +1170,21 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   pa.c = (float2 *)(scr + o_c); pa.omega = (float *)(scr + o_om);
   pa.fh = (float *)(scr + o_fh); pa.fl = (float *)(scr + o_fl);
   pa.G32 = (float2 *)(scr + o_G); pa.gmax = (float *)(scr + o_gmax);
-  pa.gpack = scr + o_pack; pa.pack_kind = bf ? 1 : 2; pa.pack_planes = planes;
+  pa.gpack = scr + o_pack; pa.pack_kind = polb ? 0 : (bf ? 1 : 2); pa.pack_planes = planes;
   pa.gscale = (float *)(scr + o_gs); pa.status = status;
   launch_presel_prep(pa, st);
 
   const float *mx = nullptr;
   if (x) {
     ck(cudaStreamWaitEvent(st, x->ready, 0), "cross-term wait");
-    mx = x->mx + (size_t)d->i0 * D * REC;
+    mx = x->mx + (size_t)d->i0 * D * rec;
   } else if (build_cache) {
     if ((rc = xcache_build(ctx, b, key, D, pa.omega, rb_hh, st, &x)) != DOTPE_OK) return finish(rc);
-    mx = x->mx + (size_t)d->i0 * D * REC;
+    mx = x->mx + (size_t)d->i0 * D * rec;
+  } else if (polb) {
+    launch_cross_terms_pol(NI, d->i0, b.I, M, D, B, b.Kpad, b.mode_m, b.master, pa.omega, nullptr,
+                           (float *)(scr + o_mx), ctx->n_sms, st);
+    mx = (const float *)(scr + o_mx);
   } else {
     launch_cross_terms(NI, d->i0, b.I, M, D, B, b.Kpad, b.master, pa.omega, rb_hh, (float *)(scr + o_mx), ctx->n_sms,
                        st);
@@ -1189,7 +1198,9 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   CUtensorMap mapG, mapBank;
   const int64_t a_rows = 2 * (int64_t)M * b.I;
   CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  if (a_rows >= (1ll << 31)) rc = fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
+  if (polb) {
+    // no tensor maps: the FP32 kernel reads the master and the FP32 operand
+  } else if (a_rows >= (1ll << 31)) rc = fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
   else if (encode_tmap_kblocks(&mapBank, dt, bf ? (void *)b.bf : (void *)b.hf, a_rows, b.Kpad / 64,
                                (uint64_t)b.Kpad * 2, PS_TR, 1) ||
            encode_tmap_kblocks(&mapG, dt, scr + o_pack, (uint64_t)planes * MG * 2 * D * NTP, b.Kpad / 64,
@@ -1221,7 +1232,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   P.a_mode_rows = (int)b.I;
   P.b_plane_rows = MG * 2 * D * NTP;
   P.b_mode_rows = rb ? 2 * D * NTP : 0;
-  P.pol = b.pol + (size_t)d->i0 * M * 2;
+  P.pol = b.pol ? b.pol + (size_t)d->i0 * M * 2 : nullptr;
   P.mx = mx;
   P.z_scale = 1.f / (b.a_scale * (bf ? 1.f : FP16_OPERAND_SCALE));
   P.g_scale = pa.gscale;
@@ -1231,7 +1242,23 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   P.wait_ns = 4000000000ull;
   if (rc == DOTPE_OK) {
     ck(cudaEventRecord(ev[1], st), "event record");
-    ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, rb, ctx->n_sms, st), "pre-selection kernel");
+    if (polb) {
+      PreselPolArgs pp;
+      memset(&pp, 0, sizeof(pp));
+      pp.n_rows = NI; pp.row0 = d->i0; pp.bank_rows = b.I;
+      pp.n_det = D; pp.n_t = NT; pp.n_tpad = NTP; pp.n_phi = d->n_phi; pp.n_modes = M; pp.n_bins = B;
+      pp.kpad = b.Kpad;
+      for (int m = 0; m < MAXM; ++m) pp.mode_m[m] = m < M ? b.mode_m[m] : 0;
+      pp.master = b.master;
+      pp.G = pa.G32;
+      pp.mx = mx;
+      pp.rank_tol = PS_RANK_TOL;
+      pp.keys = P.keys;
+      launch_presel_pol(pp, st);
+      ck(cudaGetLastError(), "pre-selection kernel");
+    } else {
+      ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, rb, ctx->n_sms, st), "pre-selection kernel");
+    }
     ck(cudaEventRecord(ev[2], st), "event record");
     launch_presel_finish(NI, D, d->n_phi, d->delta, P.keys, (float *)(scr + o_ml), (int *)(scr + o_arg),
                          (double *)(scr + o_inco), (unsigned long long *)(scr + o_maxb), (int64_t *)(scr + o_sel),

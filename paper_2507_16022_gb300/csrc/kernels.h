@@ -210,7 +210,7 @@ struct PreselPrepArgs {
   float2 *G32;           // [1 or M][D n_tpad][B] c_{kmb} e^{-2 pi i f_b t_{kt}} (0 on padding columns)
   float *gmax;           // 1 float, zeroed
   void *gpack;           // packed operand planes [planes][2 D n_tpad][Kpad]
-  int pack_kind;         // 1 bf16, 2 fp16
+  int pack_kind;         // 0 none (FP32 operand used as it is), 1 bf16, 2 fp16
   int pack_planes;       // 1 or 2 (hi, lo)
   float *gscale;         // 1 float out
   int *status;
@@ -247,6 +247,21 @@ int launch_presel(const CUtensorMap &mapG, const CUtensorMap &mapBank, const Pre
 void launch_presel_finish(int64_t n, int D, int n_phi, double delta, const unsigned long long *keys, float *ml,
                           int *arg_ot, double *inco, unsigned long long *max_bits /*zeroed*/, int64_t *sel,
                           PreselOut *out, cudaStream_t st);
+
+// Pre-selection of a polarisation-resolved bank, FP32 on the CUDA cores
+// (kernel_presel_pol.cu): the same keys as launch_presel, then launch_presel_finish.
+struct PreselPolArgs {
+  int64_t n_rows;            // rows of the slice
+  int64_t row0, bank_rows;   // first bank row of the slice, rows of the bank
+  int n_det, n_t, n_tpad, n_phi, n_modes, n_bins, kpad;
+  int mode_m[MAXM];
+  const float *master;       // FP32 master [M][bank_rows][kpad], rows [Re h+ | Im h+ | Re hx | Im hx | 0]
+  const float2 *G;           // [n_det][n_tpad][n_bins] time-grid operand c_kb e^{-2 pi i f_b t_kt}
+  const float *mx;           // [n_rows][n_det][REC_P] overlap records (slice-relative)
+  float rank_tol;
+  unsigned long long *keys;  // [n_rows][n_det] out, zeroed
+};
+void launch_presel_pol(const PreselPolArgs &a, cudaStream_t st);
 
 // Relative-binning weights (App. A): kernel_rb.cu.  w_dh [D][M][B], w_hh [D][M][M][B].
 void launch_rb_weights(int D, int M, int64_t N, const double *ff, const double *dff, const double *psd,

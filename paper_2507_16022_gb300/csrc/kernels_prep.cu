@@ -700,6 +700,7 @@ void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st) {
   const int64_t n = (int64_t)mg * a.D * a.n_tpad * a.B;
   presel_G_kernel<<<nblk(n, 256), 256, 0, st>>>(a.D, a.B, a.M, mg, a.n_t, a.n_tpad, a.fh, a.fl, a.t_grid, a.c,
                                                 a.G32, a.gmax, a.status);
+  if (a.pack_kind == 0) return;  // the FP32 operand is used as it is
   const int64_t E = (int64_t)a.D * a.n_tpad;
   const int pad = a.Kpad - 2 * a.B;
   const int64_t np = mg * E * (a.B > pad ? a.B : pad);

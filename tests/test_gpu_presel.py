@@ -223,3 +223,56 @@ def test_invalid_requests_are_rejected(dpx):
     finally:
         dp.dotpe_bank_release(ctx, nopol)
         dp.dotpe_bank_release(ctx, bid)
+
+
+# ---------------------------------------------------------------------------
+# polarisation-resolved (precessing) bank: App. B with the bank's own h_imp,
+# the FP32 kernel
+# ---------------------------------------------------------------------------
+def test_polarisation_resolved_bank_fp32(dpx):
+    """All rows of a 700-row precessing bank (a ragged row block), 150 times
+    (two passes of the kernel's 128 time slots), against the oracle: the split
+    bound 2e-3 + 1e-4 ln L^ML (met with room by FP32), the (o, t) within it, the
+    kept set away from the threshold; a slice equals the whole-bank call (the
+    slice's own records against the bank's cached ones); the tensor-core
+    precisions are refused."""
+    dp, ctx = dpx
+    import oracle
+    wl = synth.make_precessing_workload(700, 4, 3, 4, 256, snr=15.0, seed=45, n_phi=32)
+    n_t = 150
+    t_grid = np.tile((np.arange(n_t) - n_t // 2) * 5e-4, (3, 1))
+    P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h, None, wl.event.psd, wl.event.data,
+                             t_grid, n_phi=32)
+    ref = P.run(delta=20.0)
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    try:
+        part = dp.dotpe_preselect(ctx, bid, 150, 250, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,
+                                  precision="fp32")
+        r = dp.dotpe_preselect(ctx, bid, 0, 700, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,
+                               precision="fp32")
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_preselect(ctx, bid, 0, 700, wl.event.psd, wl.event.data, t_grid, n_phi=32,
+                               precision="fp16x3")
+        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    assert r["device_status"] == 0
+    ml_ref = ref["ml"]
+    tol = split_tol(ml_ref)
+    d = np.abs(r["lnl_ml"] - ml_ref)
+    print(f"presel precessing fp32: max |d ln L^ML_ik| {d.max():.3e} (ln L^ML up to {ml_ref.max():.1f})")
+    assert np.all(d <= tol)
+    tol_i = tol.sum(axis=1)
+    assert np.all(np.abs(r["lnl_inco"] - ref["lnl_inco"]) <= tol_i)
+    keep_gpu = np.zeros(700, bool)
+    keep_gpu[r["selected"]] = True
+    clear = np.abs(ref["lnl_inco"] - ref["threshold"]) > 2 * tol_i.max()
+    np.testing.assert_array_equal(keep_gpu[clear], ref["keep"][clear])
+    for i in (0, 350, 699, int(r["arg_i"]), wl.event.injection["i"]):
+        for k in range(3):
+            g = P.grid(i, k)
+            o, t = r["arg_ot"][i, k]
+            assert 0 <= o < 32 and 0 <= t < n_t
+            assert g[o, t] >= g.max() - 2 * tol[i, k]
+    np.testing.assert_array_equal(part["lnl_ml"], r["lnl_ml"][150:250])
+    np.testing.assert_array_equal(part["arg_ot"], r["arg_ot"][150:250])
