@@ -397,7 +397,8 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
         wl = synth.make_workload(**dict(WORKLOAD, n_int=args.n_int), n_phi=N_PHI)
         ps = synth.make_presel_inputs(wl)
     NT = ps.t_grid.shape[1]
-    prec = "fp32" if pres else (args.precision if args.precision != "mixed" else "fp16x3")
+    prec = args.precision if args.precision != "mixed" else "fp16x3"
+    simt = prec == "fp32"  # the FP32 kernel (polarisation-resolved banks only)
     ctx = ctx_factory()
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w, pol=ps.pol)
 
@@ -425,7 +426,7 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
     kern = statistics.median(ker_ms)
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops / (kern * 1e-3) / 1e12
-    peak = FP32_SIMT_PEAK_TFLOPS if pres else sustained
+    peak = FP32_SIMT_PEAK_TFLOPS if simt else sustained
     evals = I * D * NT * N_PHI
     dms = sum(dev_ms)
     cpu = None if args.no_cpu_baseline else presel_cpu_baseline(wl, ps)
@@ -433,24 +434,26 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
         "metric": "pre-selected bank rows/s", "value": I * args.steps / (dms * 1e-3), "unit": "rows/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp32" if pres else ("bf16" if prec.startswith("bf16") else "fp16"), "data": "synthetic",
+        "dtype": "fp32" if simt else ("bf16" if prec.startswith("bf16") else "fp16"), "data": "synthetic",
         "config": {"workload": f"incoherent pre-selection of one event: I={I} "
                                + ("polarisation-resolved (precessing) " if pres else "")
                                + f"bank rows, D={D}, M={M}, B={B}, "
                                f"N_t={NT} (0.5 ms grid), N_phi={N_PHI}, window {CUT_DELTA:g}",
                    "precision": prec,
-                   "l2": (f"inputs larger than L2 (FP32 bank {I * M * 4 * B * 4 / 1e9:.2f} GB per call)" if pres else
-                          f"inputs larger than L2 (bank operand planes {I * M * 2 * B * 2 * 2 / 1e9:.2f} GB per call)"),
+                   "l2": (f"inputs larger than L2 (FP32 bank {I * M * 4 * B * 4 / 1e9:.2f} GB per call)" if simt else
+                          f"inputs larger than L2 (bank operand planes "
+                          f"{I * M * (4 if pres else 2) * B * 2 * 2 / 1e9:.2f} GB per call)"),
                    "evaluations_per_s": evals * args.steps / (dms * 1e-3), "kept_rows": r["n_selected"],
                    "kernel_ms": kern, "device_ms_per_call": dms / args.steps},
-        "roofline": {"bound": "alu" if pres else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "roofline": {"bound": "alu" if simt else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": ("presel_pol_kernel (FP32 per-component <d|h> against the time grid + 2x2 ML)"
-                                if pres else
-                                "presel_kernel (per-mode <d|h> GEMM against the time grid + 2x2 ML epilogue)"),
+                                if simt else
+                                "presel_kernel" + ("<VAR = 2> (per-component" if pres else " (per-mode")
+                                + " <d|h> GEMM against the time grid + 2x2 ML epilogue)"),
                      "kernel_ms": kern, "flops_per_call": flops,
                      "issued_tflops": achieved * (3 if prec.endswith("x3") else 1),
-                     "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if pres
+                     "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if simt
                                      else f"{peak_src} bf16_tflops_sustained")},
         "e2e": {"value": I * args.steps / wall, "unit": "rows/s",
                 "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + ps.t_grid.nbytes),

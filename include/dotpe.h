@@ -126,9 +126,8 @@ typedef struct dotpe_config {
  *   applies (the tensor-core kernels contract K = 4 n_bins, padded); its events
  *   are not batched with one another (dotpe_batch_submit in a precision other
  *   than DOTPE_PREC_FP32 returns DOTPE_E_UNSUPPORTED); relative binning takes
- *   weights per (mode, polarisation) component; dotpe_preselect runs it in
- *   DOTPE_PREC_FP32 (the bank's own h_imp; pol is not needed) without
- *   relative binning. */
+ *   weights per (mode, polarisation) component; dotpe_preselect takes it
+ *   (the bank's own h_imp; pol is not needed) without relative binning. */
 typedef struct dotpe_bank_desc {
   int64_t n_int;
   int n_modes;
@@ -245,8 +244,9 @@ typedef struct dotpe_evidence_out {
  * operand planes (precision FP16, FP16X3, BF16 or BF16X3); the rest is FP32,
  * the detector sum and the selection FP64.  A polarisation-resolved bank
  * (n_pol = 2) uses its own h_{imp} in place of K_{imp} h_{im} (App. B's
- * general form) and runs in DOTPE_PREC_FP32 on the CUDA cores; the other
- * precisions and relative binning return DOTPE_E_UNSUPPORTED for it.
+ * general form; pol is not needed): the tensor-core precisions as above, or
+ * DOTPE_PREC_FP32 on the CUDA cores; relative binning returns
+ * DOTPE_E_UNSUPPORTED for it.
  * Rows [i0, i1) of the bank.
  * psd [n_det][n_bins] (double) and data [n_det][n_bins] (complex): host or
  * device, as for events.  t_grid [n_det][n_t] (double, s; host or device):

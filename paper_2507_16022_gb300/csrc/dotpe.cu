@@ -1073,7 +1073,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   auto bit = ctx->banks.find(d->bank_id);
   if (bit == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)d->bank_id);
   Bank &b = *bit->second;
-  const bool polb = (b.n_pol == 2);  // polarisation-resolved bank: its own h_imp, FP32 kernel
+  const bool polb = (b.n_pol == 2);  // polarisation-resolved bank: its own h_imp
   if (!polb && !b.pol) return fail(DOTPE_E_INVALID, "bank %llu was loaded without polarisation factors (pol)",
                                    (unsigned long long)d->bank_id);
   if (d->i0 < 0 || d->i1 <= d->i0 || d->i1 > b.I)
@@ -1086,12 +1086,13 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
   if ((!rb && (!d->psd || !d->data)) || !d->t_grid) return fail(DOTPE_E_INVALID, "null input array");
   const int prec = d->precision;
-  if (polb && prec != DOTPE_PREC_FP32)
-    return fail(DOTPE_E_UNSUPPORTED, "a polarisation-resolved bank is pre-selected in FP32 only");
   if (polb && rb) return fail(DOTPE_E_UNSUPPORTED, "pre-selection of a polarisation-resolved bank with relative binning");
-  if (!polb && prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 &&
+  // a polarisation-resolved bank also runs in FP32 (CUDA cores); the tensor-core precisions serve both
+  const bool simt_pol = polb && prec == DOTPE_PREC_FP32;
+  if (!simt_pol && prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 &&
       prec != DOTPE_PREC_BF16X3)
-    return fail(DOTPE_E_INVALID, "pre-selection precision %d (FP16, FP16X3, BF16 or BF16X3)", prec);
+    return fail(DOTPE_E_INVALID, "pre-selection precision %d (FP16, FP16X3, BF16 or BF16X3%s)", prec,
+                polb ? ", or FP32" : "");
   if (d->flags != 0) return fail(DOTPE_E_INVALID, "flags must be 0");
   const int64_t NI = d->i1 - d->i0;
   if (NI >= (1ll << 31) / 2) return fail(DOTPE_E_UNSUPPORTED, "slice too large");
@@ -1120,7 +1121,10 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   const size_t o_G = c.take<float2>((size_t)MG * D * NTP * B);
   const size_t o_gmax = c.take<float>(1), o_gs = c.take<float>(1);
   const int rec = polb ? REC_P : REC;
-  const size_t o_pack = c.take<uint16_t>(polb ? 0 : (size_t)planes * MG * 2 * D * NTP * b.Kpad);
+  // operand rows per plane: (column, re/im) per mode group, or (column, polarisation, re/im)
+  const int64_t g_rows = polb ? (int64_t)4 * D * NTP : (int64_t)MG * 2 * D * NTP;
+  const size_t o_Gp = c.take<float2>((polb && !simt_pol) ? (size_t)4 * D * NTP * B : 0);
+  const size_t o_pack = c.take<uint16_t>(simt_pol ? 0 : (size_t)planes * g_rows * b.Kpad);
   const size_t o_mx = own_mx ? c.take<float>((size_t)NI * D * rec) : 0;
   const size_t o_keys = c.take<unsigned long long>((size_t)NI * D);
   const size_t o_ml = c.take<float>((size_t)NI * D), o_arg = c.take<int>((size_t)NI * D * 2);
@@ -1173,6 +1177,9 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   pa.gpack = scr + o_pack; pa.pack_kind = polb ? 0 : (bf ? 1 : 2); pa.pack_planes = planes;
   pa.gscale = (float *)(scr + o_gs); pa.status = status;
   launch_presel_prep(pa, st);
+  if (polb && !simt_pol)
+    launch_presel_pol_pack((int64_t)D * NTP, B, b.Kpad, pa.G32, (float2 *)(scr + o_Gp), pa.gmax, bf ? 1 : 2, planes,
+                           pa.gpack, pa.gscale, st);
 
   const float *mx = nullptr;
   if (x) {
@@ -1198,12 +1205,12 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   CUtensorMap mapG, mapBank;
   const int64_t a_rows = 2 * (int64_t)M * b.I;
   CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  if (polb) {
+  if (simt_pol) {
     // no tensor maps: the FP32 kernel reads the master and the FP32 operand
   } else if (a_rows >= (1ll << 31)) rc = fail(DOTPE_E_UNSUPPORTED, "bank too large for 32-bit TMA coordinates");
   else if (encode_tmap_kblocks(&mapBank, dt, bf ? (void *)b.bf : (void *)b.hf, a_rows, b.Kpad / 64,
                                (uint64_t)b.Kpad * 2, PS_TR, 1) ||
-           encode_tmap_kblocks(&mapG, dt, scr + o_pack, (uint64_t)planes * MG * 2 * D * NTP, b.Kpad / 64,
+           encode_tmap_kblocks(&mapG, dt, scr + o_pack, (uint64_t)planes * g_rows, b.Kpad / 64,
                                (uint64_t)b.Kpad * 2, 2 * PS_TC, 1))
     rc = fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (pre-selection)");
   PreselParams P;
@@ -1226,11 +1233,11 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     for (; ns < MAXM; ++ns) P.slot[ns] = 0;
   }
   P.n_itile = (int)((NI + PS_TR - 1) / PS_TR);
-  P.n_ctile = D * NTP / PS_TC;
+  P.n_ctile = D * NTP / (polb ? PS_TC / 2 : PS_TC);  // a polarisation-resolved tile holds 32 columns
   P.kb = b.Kpad / 64;
   P.a_plane_rows = M * (int)b.I;
   P.a_mode_rows = (int)b.I;
-  P.b_plane_rows = MG * 2 * D * NTP;
+  P.b_plane_rows = (int)g_rows;
   P.b_mode_rows = rb ? 2 * D * NTP : 0;
   P.pol = b.pol ? b.pol + (size_t)d->i0 * M * 2 : nullptr;
   P.mx = mx;
@@ -1242,7 +1249,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   P.wait_ns = 4000000000ull;
   if (rc == DOTPE_OK) {
     ck(cudaEventRecord(ev[1], st), "event record");
-    if (polb) {
+    if (simt_pol) {
       PreselPolArgs pp;
       memset(&pp, 0, sizeof(pp));
       pp.n_rows = NI; pp.row0 = d->i0; pp.bank_rows = b.I;
@@ -1257,7 +1264,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
       launch_presel_pol(pp, st);
       ck(cudaGetLastError(), "pre-selection kernel");
     } else {
-      ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, rb, ctx->n_sms, st), "pre-selection kernel");
+      ck((cudaError_t)launch_presel(mapG, mapBank, P, bf, split, rb, polb, ctx->n_sms, st), "pre-selection kernel");
     }
     ck(cudaEventRecord(ev[2], st), "event record");
     launch_presel_finish(NI, D, d->n_phi, d->delta, P.keys, (float *)(scr + o_ml), (int *)(scr + o_arg),

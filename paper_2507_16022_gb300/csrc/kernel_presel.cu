@@ -124,9 +124,10 @@ __device__ __forceinline__ void even_odd(const float4 &e01, const float4 &e23, c
 }  // namespace
 
 // One row of one column: best tagged ln L^ML over the thread's phases.
-// PAIR (n_phi % 4 == 0): base phases b = part, part + 2, ... < n_phi / 2 and
-// their partners b + n_phi / 2; otherwise phases o = part, part + 2, ...
-template <int NE, bool PAIR>
+// PAIR (n_phi % 4 == 0): base phases b = part, part + STEP, ... < n_phi / 2 and
+// their partners b + n_phi / 2; otherwise phases o = part, part + STEP, ...
+// (STEP lanes share one (row, time): 2, or 4 for a polarisation-resolved bank).
+template <int NE, bool PAIR, int STEP>
 __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const float (&yi)[MAXM][2],
                                           const float4 *__restrict__ hs_row, const QTail &T, int n_phi, int part) {
   float best = -1.f;
@@ -136,7 +137,7 @@ __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const floa
   if (PAIR) {
     const int half = n_phi >> 1;
 #pragma unroll 4
-    for (int b = part; b < half; b += 2) {
+    for (int b = part; b < half; b += STEP) {
       const float4 e01 = T.phm[b * 2], e23 = T.phm[b * 2 + 1];
       float Ep, Op, Ex, Ox;
       even_odd<NE>(e01, e23, yrp, yip, Ep, Op);
@@ -149,7 +150,7 @@ __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const floa
     }
   } else {
 #pragma unroll 2
-    for (int o = part; o < n_phi; o += 2) {
+    for (int o = part; o < n_phi; o += STEP) {
       const float4 e01 = T.phm[o * 2], e23 = T.phm[o * 2 + 1];
       float Ep, Op, Ex, Ox;
       even_odd<NE>(e01, e23, yrp, yip, Ep, Op);
@@ -168,7 +169,10 @@ __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const floa
 // parts swapped with the partner lane, Y = K Z (the accumulator scale is in
 // the [hh]^+ table), the best tagged ln L^ML over the thread's phases, the
 // warp maximum over its 16 times, one atomic per row.
-template <int NE, bool PAIR>
+// POL (polarisation-resolved bank): lanes 4c + 2p + part hold (Re, Im) of the
+// (mode, polarisation p) component of column c; the four lanes of a column
+// exchange their parts, take Y_{mp} = Z_{mp} (no factors) and a quarter of the phases each.
+template <int NE, bool PAIR, bool POL>
 __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T, uint32_t tbase, int rb, int j_first,
                                           int k, int t, int part, int lane, uint64_t *tempty) {
   const int M = P.n_modes;
@@ -197,33 +201,51 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
       const int j = j0 + jj;
       const int64_t i = (int64_t)rb * QTR + j;
       float zr[MAXM], zi[MAXM];
-#pragma unroll
-      for (int s = 0; s < MAXM; ++s) {
-        const float own = z[s][jj];
-        const float other = __shfl_xor_sync(0xffffffffu, own, 1);
-        zr[s] = part ? other : own;
-        zi[s] = part ? own : other;
-      }
-      if (i >= P.n_rows) continue;  // warp-uniform
       float yr[MAXM][2], yi[MAXM][2];
+      if constexpr (POL) {
+        const int pp = (lane >> 1) & 1;
 #pragma unroll
-      for (int s = 0; s < MAXM; ++s) {
-        float4 kv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (s < M) kv = __ldg(reinterpret_cast<const float4 *>(P.pol + (i * M + P.slot[s]) * 2));
-        yr[s][0] = kv.x * zr[s] - kv.y * zi[s];
-        yi[s][0] = kv.x * zi[s] + kv.y * zr[s];
-        yr[s][1] = kv.z * zr[s] - kv.w * zi[s];
-        yi[s][1] = kv.z * zi[s] + kv.w * zr[s];
+        for (int s = 0; s < MAXM; ++s) {
+          const float own = z[s][jj];
+          const float x1 = __shfl_xor_sync(0xffffffffu, own, 1);  // (p, other part)
+          const float x2 = __shfl_xor_sync(0xffffffffu, own, 2);  // (other p, this part)
+          const float x3 = __shfl_xor_sync(0xffffffffu, own, 3);  // (other p, other part)
+          const float r_own = part ? x1 : own, i_own = part ? own : x1;
+          const float r_oth = part ? x3 : x2, i_oth = part ? x2 : x3;
+          yr[s][0] = pp ? r_oth : r_own; yi[s][0] = pp ? i_oth : i_own;
+          yr[s][1] = pp ? r_own : r_oth; yi[s][1] = pp ? i_own : i_oth;
+        }
+        if (i >= P.n_rows) continue;  // warp-uniform
+      } else {
+#pragma unroll
+        for (int s = 0; s < MAXM; ++s) {
+          const float own = z[s][jj];
+          const float other = __shfl_xor_sync(0xffffffffu, own, 1);
+          zr[s] = part ? other : own;
+          zi[s] = part ? own : other;
+        }
+        if (i >= P.n_rows) continue;  // warp-uniform
+#pragma unroll
+        for (int s = 0; s < MAXM; ++s) {
+          float4 kv = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (s < M) kv = __ldg(reinterpret_cast<const float4 *>(P.pol + (i * M + P.slot[s]) * 2));
+          yr[s][0] = kv.x * zr[s] - kv.y * zi[s];
+          yi[s][0] = kv.x * zi[s] + kv.y * zr[s];
+          yr[s][1] = kv.z * zr[s] - kv.w * zi[s];
+          yi[s][1] = kv.z * zi[s] + kv.w * zr[s];
+        }
       }
-      const float best = row_best<NE, PAIR>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi, part);
-      // the warp's maximum over its 16 times: tagged values are distinct between
-      // partner lanes, so the lowest lane holding the maximum has the lowest time
+      const float best = row_best<NE, PAIR, POL ? 4 : 2>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi,
+                                                         POL ? (lane & 3) : part);
+      // the warp's maximum over its 16 (POL: 8) times: tagged values are distinct
+      // between the lanes of one time, so the lowest lane holding the maximum has
+      // the lowest time
       float m = tv ? best : -1.f;
 #pragma unroll
       for (int sh = 16; sh > 0; sh >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, sh));
       const unsigned hit = __ballot_sync(0xffffffffu, tv && best == m);
       if (lane == 0 && m >= -0.5f && hit) {
-        const int t_hit = t + ((__ffs(hit) - 1) >> 1);  // lane 0's time + half the lane offset
+        const int t_hit = t + ((__ffs(hit) - 1) >> (POL ? 2 : 1));  // lane 0's time + the lane offset's time
         const uint32_t o = 63u - (uint32_t)(__float_as_int(m) & 63);
         const unsigned long long key = ((unsigned long long)__float_as_uint(fmaxf(m, 0.f)) << 32) |
                                        (unsigned long long)(0xffffffffu - (uint32_t)(t_hit * P.n_phi + (int)o));
@@ -233,10 +255,14 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
   }
 }
 
-template <bool BF16, bool SPLIT, bool PERMODE>
+// VAR: 0 shared time-grid operand, 1 one per mode (relative binning), 2
+// polarisation-resolved bank (A rows 4c + 2p + part: 32 columns per tile).
+template <bool BF16, bool SPLIT, int VAR>
 __global__ void __launch_bounds__(QNT, 1)
     presel_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapBank,
                   const __grid_constant__ PreselParams P) {
+  constexpr bool PERMODE = (VAR == 1), POL = (VAR == 2);
+  constexpr int QCOLS = POL ? QTC / 2 : QTC;  // (detector, time) columns per tile
   using Pipe = QPipe<SPLIT, PERMODE>;
   constexpr int ST = Pipe::ST, NPL = Pipe::NPL;
   extern __shared__ uint8_t smem_raw[];
@@ -381,14 +407,44 @@ __global__ void __launch_bounds__(QNT, 1)
       const int b = u & 1;
       const uint32_t use = u >> 1;
       ++u;
-      const int c0 = ct * QTC;
+      const int c0 = ct * QCOLS;
       const int k = c0 / P.n_tpad;
       // ---- [hh]^+ / 2 of the tile's rows on every phase (thread = row, 4 phases)
       named_bar_sync(1, QEPT);  // the previous tile's readers are done with T.hs
       {
         const int j = etid >> 3, o0 = (etid & 7) * 4;
         const int64_t i = (int64_t)rb * QTR + j;
-        if (i < P.n_rows && o0 < P.n_phi) {
+        if (POL && i < P.n_rows && o0 < P.n_phi) {
+          // the row's records (grouped by delta = m - m'): hh_{++} = X0 + 2 Re sum X_d e^{i d phi},
+          // hh_{xx} = W0 + 2 Re sum W_d e^{i d phi}, hh_{+x} = Y0 / 2 + Re sum Y_d e^{i d phi}
+          const float *rec = P.mx + (i * P.n_det + k) * REC_P;
+          float rv[REC_POL];
+#pragma unroll
+          for (int q = 0; q < REC_POL; ++q) rv[q] = __ldg(rec + q);
+#pragma unroll
+          for (int oo = 0; oo < 4; ++oo) {
+            const int o = o0 + oo;
+            float A = rv[0], Bx = 0.5f * rv[1], C = rv[2];
+#pragma unroll
+            for (int dl = 0; dl < 3; ++dl) {
+              const float2 e = T.phd[o * 3 + dl];
+              A += 2.f * (rv[3 + 6 * dl] * e.x - rv[4 + 6 * dl] * e.y);
+              Bx += rv[5 + 6 * dl] * e.x - rv[6 + 6 * dl] * e.y;
+              C += 2.f * (rv[7 + 6 * dl] * e.x - rv[8 + 6 * dl] * e.y);
+            }
+            const float det = A * C - Bx * Bx;
+            float a = 0.f, bb = 0.f, c = 0.f;
+            if (det > P.rank_tol * A * C) {
+              const float inv = 0.5f / det;
+              a = C * inv; bb = -Bx * inv; c = A * inv;
+            } else if (A > 0.f || C > 0.f) {
+              const float sm = A + C;
+              const float inv = 0.5f / (sm * sm);
+              a = A * inv; bb = Bx * inv; c = C * inv;
+            }
+            T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, 0.f);
+          }
+        } else if (!POL && i < P.n_rows && o0 < P.n_phi) {
           float Kr[MAXM][2], Ki[MAXM][2], rec[REC];
 #pragma unroll
           for (int m = 0; m < MAXM; ++m) {
@@ -462,16 +518,16 @@ __global__ void __launch_bounds__(QNT, 1)
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, P.wait_ns)) break;
       tc_fence_after();
       // ---- the rows: this lane's column, the warp's 16 rows
-      const int t = c0 - k * P.n_tpad + (L >> 1);
+      const int t = c0 - k * P.n_tpad + (POL ? (L >> 2) : (L >> 1));
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * Q_BUF_COLS;
       const int j0 = sub * QJW;
       switch ((pair ? 8 : 0) + (pair ? P.n_even : 2)) {
-        case 8: tile_rows<0, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 9: tile_rows<1, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 10: tile_rows<2, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 11: tile_rows<3, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 12: tile_rows<4, true>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        default: tile_rows<2, false>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 8: tile_rows<0, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 9: tile_rows<1, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 10: tile_rows<2, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 11: tile_rows<3, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        case 12: tile_rows<4, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        default: tile_rows<2, false, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
       }
     }
   }
@@ -582,32 +638,33 @@ __global__ void presel_select_kernel(int64_t n, double delta, const double *__re
   }
 }
 
-template <bool BF16, bool SPLIT, bool PERMODE>
+template <bool BF16, bool SPLIT, int VAR>
 static cudaError_t launch_presel_variant(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p,
                                          int grid, cudaStream_t st) {
-  auto kern = presel_kernel<BF16, SPLIT, PERMODE>;
-  const size_t smem = q_smem_bytes<SPLIT, PERMODE>();
+  auto kern = presel_kernel<BF16, SPLIT, VAR>;
+  const size_t smem = q_smem_bytes<SPLIT, VAR == 1>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, QNT, smem, st>>>(mapG, mapBank, p);
   return cudaGetLastError();
 }
 
-template <bool PERMODE>
+template <int VAR>
 static cudaError_t launch_presel_pm(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p,
                                     bool bf16, bool split, int grid, cudaStream_t st) {
-  if (bf16) return split ? launch_presel_variant<true, true, PERMODE>(mapG, mapBank, p, grid, st)
-                         : launch_presel_variant<true, false, PERMODE>(mapG, mapBank, p, grid, st);
-  return split ? launch_presel_variant<false, true, PERMODE>(mapG, mapBank, p, grid, st)
-               : launch_presel_variant<false, false, PERMODE>(mapG, mapBank, p, grid, st);
+  if (bf16) return split ? launch_presel_variant<true, true, VAR>(mapG, mapBank, p, grid, st)
+                         : launch_presel_variant<true, false, VAR>(mapG, mapBank, p, grid, st);
+  return split ? launch_presel_variant<false, true, VAR>(mapG, mapBank, p, grid, st)
+               : launch_presel_variant<false, false, VAR>(mapG, mapBank, p, grid, st);
 }
 
 int launch_presel(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p, bool bf16, bool split,
-                  bool per_mode, int n_sms, cudaStream_t st) {
+                  bool per_mode, bool pol, int n_sms, cudaStream_t st) {
   const int total = p.n_itile * p.n_ctile;
   const int grid = total < n_sms ? (total > 0 ? total : 1) : n_sms;
-  const cudaError_t e = per_mode ? launch_presel_pm<true>(mapG, mapBank, p, bf16, split, grid, st)
-                                 : launch_presel_pm<false>(mapG, mapBank, p, bf16, split, grid, st);
+  const cudaError_t e = pol ? launch_presel_pm<2>(mapG, mapBank, p, bf16, split, grid, st)
+                            : per_mode ? launch_presel_pm<1>(mapG, mapBank, p, bf16, split, grid, st)
+                                       : launch_presel_pm<0>(mapG, mapBank, p, bf16, split, grid, st);
   return (int)e;
 }
 

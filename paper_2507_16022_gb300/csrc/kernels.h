@@ -242,8 +242,9 @@ struct PreselOut {
   long long arg_i, n_selected;
 };
 // returns a cudaError_t
+// pol: a polarisation-resolved bank (time-grid operand from launch_presel_pol_pack, 32 columns per tile)
 int launch_presel(const CUtensorMap &mapG, const CUtensorMap &mapBank, const PreselParams &p, bool bf16, bool split,
-                  bool per_mode, int n_sms, cudaStream_t st);
+                  bool per_mode, bool pol, int n_sms, cudaStream_t st);
 void launch_presel_finish(int64_t n, int D, int n_phi, double delta, const unsigned long long *keys, float *ml,
                           int *arg_ot, double *inco, unsigned long long *max_bits /*zeroed*/, int64_t *sel,
                           PreselOut *out, cudaStream_t st);
@@ -262,6 +263,12 @@ struct PreselPolArgs {
   unsigned long long *keys;  // [n_rows][n_det] out, zeroed
 };
 void launch_presel_pol(const PreselPolArgs &a, cudaStream_t st);
+// The tensor-core pre-selection's time-grid operand for a polarisation-resolved
+// bank: rows 4c + 2p + part (c = detector-time column), polarisation block p of
+// [Re | Im | Re | Im] along K holding the column's real-ified G, the other zero.
+// Gp: [2][2 n_cols][B] FP32 scratch; G32 [n_cols][B]; out and scale as launch_prep's pack.
+void launch_presel_pol_pack(int64_t n_cols, int B, int Kpad, const float2 *G32, float2 *Gp, const float *gmax,
+                            int kind, int planes, void *out, float *scale_out, cudaStream_t st);
 
 // Relative-binning weights (App. A): kernel_rb.cu.  w_dh [D][M][B], w_hh [D][M][M][B].
 void launch_rb_weights(int D, int M, int64_t N, const double *ff, const double *dff, const double *psd,

@@ -712,6 +712,32 @@ void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st) {
                                                          a.gpack, a.gscale);
 }
 
+// Gp[q][2c + p][b] = G32[c][b] if q == p, else 0: the polarisation-resolved
+// pre-selection's operand rows before packing (one row per (column, polarisation)).
+__global__ void presel_pol_spread_kernel(int64_t n_cols, int B, const float2 *__restrict__ G32,
+                                         float2 *__restrict__ Gp) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= 4 * n_cols * B) return;
+  const int b = (int)(k % B);
+  const int64_t r = k / B;                    // q * 2 n_cols + 2c + p
+  const int64_t e = r % (2 * n_cols), q = r / (2 * n_cols);
+  const int64_t c = e >> 1, p = e & 1;
+  Gp[k] = (q == p) ? G32[c * B + b] : make_float2(0.f, 0.f);
+}
+
+void launch_presel_pol_pack(int64_t n_cols, int B, int Kpad, const float2 *G32, float2 *Gp, const float *gmax,
+                            int kind, int planes, void *out, float *scale_out, cudaStream_t st) {
+  presel_pol_spread_kernel<<<nblk(4 * n_cols * B, 256), 256, 0, st>>>(n_cols, B, G32, Gp);
+  const int64_t E = 2 * n_cols;
+  const int pad = Kpad - 4 * B;
+  const int64_t n = E * (B > pad ? B : pad);
+  if (kind == 1)
+    pack_G_kernel<__nv_bfloat16><<<nblk(n, 256), 256, 0, st>>>(E, 1, B, Kpad, 2, Gp, gmax, 1, planes, out,
+                                                               scale_out);
+  else
+    pack_G_kernel<__half><<<nblk(n, 256), 256, 0, st>>>(E, 1, B, Kpad, 2, Gp, gmax, 2, planes, out, scale_out);
+}
+
 void launch_cross_terms(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
                         const float *master, const float *omega, const double2 *rb_hh, float *mx, int n_sms,
                         cudaStream_t st) {

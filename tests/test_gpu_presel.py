@@ -226,41 +226,44 @@ def test_invalid_requests_are_rejected(dpx):
 
 
 # ---------------------------------------------------------------------------
-# polarisation-resolved (precessing) bank: App. B with the bank's own h_imp,
-# the FP32 kernel
+# polarisation-resolved (precessing) bank: App. B with the bank's own h_imp
 # ---------------------------------------------------------------------------
-def test_polarisation_resolved_bank_fp32(dpx):
-    """All rows of a 700-row precessing bank (a ragged row block), 150 times
-    (two passes of the kernel's 128 time slots), against the oracle: the split
-    bound 2e-3 + 1e-4 ln L^ML (met with room by FP32), the (o, t) within it, the
-    kept set away from the threshold; a slice equals the whole-bank call (the
-    slice's own records against the bank's cached ones); the tensor-core
-    precisions are refused."""
-    dp, ctx = dpx
+@pytest.fixture(scope="module")
+def presw():
     import oracle
     wl = synth.make_precessing_workload(700, 4, 3, 4, 256, snr=15.0, seed=45, n_phi=32)
     n_t = 150
     t_grid = np.tile((np.arange(n_t) - n_t // 2) * 5e-4, (3, 1))
     P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h, None, wl.event.psd, wl.event.data,
                              t_grid, n_phi=32)
-    ref = P.run(delta=20.0)
+    return wl, t_grid, P, P.run(delta=20.0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "bf16x3", "fp16"])
+def test_polarisation_resolved_bank(dpx, presw, precision):
+    """All rows of a 700-row precessing bank (a ragged row block), 150 times
+    (FP32: two passes of its 128 time slots; tensor cores: 32-column tiles of
+    the (time, polarisation, part) operand rows), against the oracle: the split
+    bound 2e-3 + 1e-4 ln L^ML (FP32 and the split precisions; K = 4B here),
+    the single-pass bound for fp16; the (o, t) within it; the kept set away
+    from the threshold; a slice equals the whole-bank call (the slice's own
+    records against the bank's cached ones)."""
+    dp, ctx = dpx
+    wl, t_grid, P, ref = presw
+    n_t = t_grid.shape[1]
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
     try:
         part = dp.dotpe_preselect(ctx, bid, 150, 250, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,
-                                  precision="fp32")
+                                  precision=precision)
         r = dp.dotpe_preselect(ctx, bid, 0, 700, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,
-                               precision="fp32")
-        with pytest.raises(dp.DotpeError) as ei:
-            dp.dotpe_preselect(ctx, bid, 0, 700, wl.event.psd, wl.event.data, t_grid, n_phi=32,
-                               precision="fp16x3")
-        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+                               precision=precision)
     finally:
         dp.dotpe_bank_release(ctx, bid)
     assert r["device_status"] == 0
     ml_ref = ref["ml"]
-    tol = split_tol(ml_ref)
+    tol = fp16_tol(ml_ref, dd_per_detector(wl)[None, :]) if precision == "fp16" else split_tol(ml_ref)
     d = np.abs(r["lnl_ml"] - ml_ref)
-    print(f"presel precessing fp32: max |d ln L^ML_ik| {d.max():.3e} (ln L^ML up to {ml_ref.max():.1f})")
+    print(f"presel precessing {precision}: max |d ln L^ML_ik| {d.max():.3e} (ln L^ML up to {ml_ref.max():.1f})")
     assert np.all(d <= tol)
     tol_i = tol.sum(axis=1)
     assert np.all(np.abs(r["lnl_inco"] - ref["lnl_inco"]) <= tol_i)
