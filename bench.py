@@ -350,7 +350,10 @@ def bench_batch64(args, dp, ctx_factory, torch, dev, load_peaks_fn):
                      "peak_source": f"{peak_src} bf16_tflops_sustained"},
         "e2e": {"value": pairs * args.steps / (e2e_ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 96 * 64},
-        "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,
+        # per batch: each event's preparation (5) and reduction (6), the batch's fused
+        # launches (mixed: screen, 3 selection kernels, 2 gated refinement variants)
+        "gpu_launches": (64 * (5 + 6) + (6 if args.precision == "mixed" else 1)) * args.steps, "clocks": clocks,
+        "cpu_baseline": None,
     }
     dp.dotpe_bank_release(ctx, bid)
     dp.dotpe_destroy(ctx)
@@ -596,7 +599,10 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
                 "h2d_bytes_per_step": int(rw.f_fine.nbytes + rw.dff.nbytes + rw.psd_fine.nbytes + rw.data_fine.nbytes
                                           + rw.h0_fine.nbytes + rw.ext.t.nbytes + resp.nbytes + rw.ext.ln_w.nbytes),
                 "d2h_bytes_per_step": int(wdh.nbytes + whh.nbytes + 96)},
-        "gpu_launches": None, "clocks": clocks, "cpu_baseline": cpu,
+        # per step: the weights kernel; the event's preparation (prep_bins, rb_norm, prep_ext,
+        # build_G, pack_G), the fused launches (mixed: screen, 3 selection kernels, 2 gated
+        # refinement variants) and the reduction (6)
+        "gpu_launches": (1 + 5 + (6 if mixed else 1) + 6) * args.steps, "clocks": clocks, "cpu_baseline": cpu,
     }
     dp.dotpe_bank_release(ctx, bid)
     dp.dotpe_destroy(ctx)
@@ -778,6 +784,25 @@ def bench_samples(args, dp, ctx_factory, torch, dev):
     dp.dotpe_event_release(ctx, eid)
     dp.dotpe_bank_release(ctx, bid)
     dp.dotpe_destroy(ctx)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's resampling on a bounded sample: its FP64 grid of a 128-row slice of
+        # the bank against all 4,096 samples (not timed), then draws from it (timed)
+        import oracle
+        P = oracle.OracleProblem(wl.bank, wl.ext, wl.event, i_slice=slice(0, 128))
+        grid, _ = P.eval_grid(0.0)
+        oev = P.evidence(grid)
+        draws = rng.random((4000, 4))
+        tc = time.perf_counter()
+        oracle.posterior_samples(P, grid, oev, draws[:200])
+        per = (time.perf_counter() - tc) / 200
+        nd = int(min(4000, max(200, 10.0 / per)))
+        tc = time.perf_counter()
+        oracle.posterior_samples(P, grid, oev, draws[:nd])
+        dtc = time.perf_counter() - tc
+        cpu = {"value": nd / dtc, "unit": "samples/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nd} draws (row, sample, phase, distance) from the oracle's FP64 grid of rows 0-127 "
+                         f"x all {E} samples of the same event, {dtc:.1f} s (the grid itself not timed)"}
     return {
         "metric": "posterior samples/s", "value": n / dt, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -788,7 +813,7 @@ def bench_samples(args, dp, ctx_factory, torch, dev):
                                                  "copied between host and device inside)"},
         "roofline": None, "e2e": {"value": n / dt, "unit": "samples/s", "h2d_bytes_per_step": 32 * n,
                                   "d2h_bytes_per_step": 28 * n},
-        "gpu_launches": 2 * args.steps, "clocks": clocks, "cpu_baseline": None,
+        "gpu_launches": 2 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
     }
 
 
