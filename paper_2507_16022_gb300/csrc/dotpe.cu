@@ -508,6 +508,7 @@ static SelectEvent select_event_of(const EventRun &R) {
   v.sqrt_dd = R.pa.sqrt_dd;
   v.window = (R.P.cut_delta > 0.f) ? R.P.cut_delta : MIXED_FAR_WINDOW;
   v.margin_k = MIXED_MARGIN_K;
+  v.sep_ml = SEP_ML * (R.pa.Kpad > 1024 ? 1024.f / (float)R.pa.Kpad : 1.f);
   v.ml_refine = (float *)(R.scr + R.L.ml_refine);
   v.n_refined = (int *)(R.scr + R.L.n_list);
   return v;

@@ -384,7 +384,7 @@ __global__ void select_events_kernel(SelectBatch a) {
   const float mx = *v.ml_screen;
   *v.ml_refine = fmaxf(mx - screen_margin(mx, v.margin_k, *v.sqrt_dd), 0.f);
   *v.n_refined = 0;
-  if (a.sep) a.sep[k] = (mx > SEP_ML) ? 1 : 0;
+  if (a.sep) a.sep[k] = (mx > v.sep_ml) ? 1 : 0;
 }
 
 int select_count_blocks(int n_tiles) { return (n_tiles + SB - 1) / SB; }

@@ -119,7 +119,9 @@ struct TcLaunch {
 };
 // A refinement whose screened maximum ln L^ML exceeds this uses the separate
 // low-order accumulator: below it, one shared FP32 accumulator keeps the
-// tensor-core truncation floor (~7e-6 ln L^ML) under 1e-3.
+// tensor-core truncation floor (~7e-6 ln L^ML at Kpad = 1024) under 1e-3.  The
+// floor grows with the accumulation chain, so longer K lowers the threshold in
+// proportion (SEP_ML 1024 / Kpad for Kpad > 1024).
 constexpr float SEP_ML = 140.0f;
 // n <= TC_MAXB works; glist/glist_n non-null for list mode.  Returns a cudaError_t.
 int launch_tc(const TcLaunch &L, const TcWork *works, int n, const int2 *glist, const int *glist_n, cudaStream_t st);
@@ -136,6 +138,7 @@ struct SelectEvent {
   const float *sqrt_dd;    // sqrt<d|d>
   float window;            // tiles within window + 2 margins of the maximum are refined
   float margin_k;          // kappa*u of the screening precision
+  float sep_ml;            // screened maxima above this take the separate low-order accumulator
   float *ml_refine;        // out: screened maximum - margin (a lower bound of the exact maximum)
   int *n_refined;          // out: the event's refined tiles
 };

@@ -192,6 +192,7 @@ SHAPES = [  # I_bank, slice, E, D, M, B
     (400, (17, 350), 77, 2, 3, 96),
     (300, (5, 134), 33, 3, 4, 160),
     (150, (0, 150), 130, 3, 2, 40),
+    (140, (3, 140), 40, 2, 2, 2000),  # K = 4,000 -> 63 k-blocks of 64 (an odd count: a half-empty last box)
 ]
 
 

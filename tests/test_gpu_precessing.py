@@ -137,7 +137,8 @@ def test_tensor_core_precisions(dpx, pwl, precision):
         assert (ev["arg_i"], ev["arg_e"]) == ref["arg"][:2]
 
 
-@pytest.mark.parametrize("shape", [(300, 77, 2, 3, 128), (129, 33, 1, 1, 96), (200, 50, 3, 2, 200)])
+@pytest.mark.parametrize("shape", [(300, 77, 2, 3, 128), (129, 33, 1, 1, 96), (200, 50, 3, 2, 200),
+                                   (140, 36, 2, 2, 1000)])
 @pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
 def test_ragged_shapes_and_networks(dpx, shape, precision):
     """Ragged row and sample tiles, one to three detectors, one to three modes,
