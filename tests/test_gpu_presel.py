@@ -279,3 +279,22 @@ def test_polarisation_resolved_bank(dpx, presw, precision):
             assert g[o, t] >= g.max() - 2 * tol[i, k]
     np.testing.assert_array_equal(part["lnl_ml"], r["lnl_ml"][150:250])
     np.testing.assert_array_equal(part["arg_ot"], r["arg_ot"][150:250])
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+def test_long_bin_axis(dpx, precision):
+    """B = 2,000 bins (K = 4,000: 63 k-blocks, an odd count), two detectors,
+    two modes, 20 times, 200 rows: every row against the oracle."""
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=200, n_ext=4, n_det=2, n_modes=2, n_bins=2000, seed=47, snr=15.0)
+    ps = synth.make_presel_inputs(wl, n_t=20, dt=1e-3, seed=48)
+    _, ref = oracle_rows(wl, ps, np.arange(200), 16)
+    bid = load_bank(dp, ctx, wl, ps)
+    try:
+        r = dp.dotpe_preselect(ctx, bid, 0, 200, wl.event.psd, wl.event.data, ps.t_grid, n_phi=16, delta=20.0,
+                               precision=precision)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    d = np.abs(r["lnl_ml"] - ref["ml"])
+    print(f"presel B=2000 {precision}: max |d ln L^ML_ik| {d.max():.3e} (ln L^ML up to {ref['ml'].max():.1f})")
+    assert np.all(d <= split_tol(ref["ml"]))
