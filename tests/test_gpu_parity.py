@@ -242,6 +242,41 @@ def test_degenerate_cases(dpx, case, precision):
         assert np.all(got["ml"] == 0.0)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
+def test_ragged_block_streaming(dpx, precision):
+    """A 680-row slice streamed in 256-row blocks (256, 256, 168) against the
+    oracle, all pairs, cut off (block streaming then changes nothing but FP64
+    rounding); with the cut on, ln Z and the maximum equal the one-pass run's."""
+    import oracle
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=700, n_ext=70, n_det=3, n_modes=4, n_bins=128, snr=14.0, seed=91,
+                             ln_w="random", n_phi=16)
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event, i_slice=slice(20, 700))
+    grid, _ = P.eval_grid(0.0)
+    ref_ev = P.evidence(grid)
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    try:
+        out = {}
+        for cut, br in ((0.0, 256), (20.0, 256), (20.0, 0)):
+            eid = dp.dotpe_event_submit(ctx, bid, 20, 700, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                        wl.ext.ln_w, n_phi=16, u_min=wl.event.u_min, cut_delta=cut,
+                                        precision=precision, flags=dp.DOTPE_FLAG_STORE_LNL, block_rows=br)
+            dp.dotpe_event_wait(ctx, eid, 120.0)
+            out[(cut, br)] = dict(ev=dp.dotpe_evidence(ctx, eid),
+                                  lnl=dp.dotpe_lnl_blocks(ctx, eid, 0, 680, 0, 70),
+                                  ml=dp.dotpe_lnl_blocks(ctx, eid, 0, 680, 0, 70, what=dp.DOTPE_LNL_ML_MAX))
+            dp.dotpe_event_release(ctx, eid)
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    got = out[(0.0, 256)]
+    check_pairs(got, grid, precision, data_norm(wl))
+    assert abs(got["ev"]["ln_z"] - ref_ev["ln_z"]) <= 1e-2
+    assert got["ev"]["arg_i"] - 20 == ref_ev["arg"][0]
+    a, b = out[(20.0, 256)]["ev"], out[(20.0, 0)]["ev"]
+    assert abs(a["ln_z"] - b["ln_z"]) <= 1e-3
+    assert a["max_lnl_ml"] == b["max_lnl_ml"] and (a["arg_i"], a["arg_e"], a["arg_o"]) == (b["arg_i"], b["arg_e"], b["arg_o"])
+
+
 def test_noiseless_peak(dpx):
     dp, ctx = dpx
     wl = synth.make_workload(n_int=500, n_ext=96, n_det=3, n_modes=4, n_bins=128, snr=15.0, seed=5,
