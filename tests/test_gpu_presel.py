@@ -298,3 +298,34 @@ def test_long_bin_axis(dpx, precision):
     d = np.abs(r["lnl_ml"] - ref["ml"])
     print(f"presel B=2000 {precision}: max |d ln L^ML_ik| {d.max():.3e} (ln L^ML up to {ref['ml'].max():.1f})")
     assert np.all(d <= split_tol(ref["ml"]))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1, 1), (3, 2, 2, 3, 3)])
+@pytest.mark.parametrize("bank", ["modes", "precessing"])
+def test_degenerate_preselection(dpx, shape, bank):
+    """Tiny shapes: one row, one detector, one mode, one time and one phase;
+    three rows, two detectors and modes, three times and three phases (no
+    phase pairing), for a mode bank (fp16x3) and a polarisation-resolved bank
+    (fp16x3 and FP32), against the oracle."""
+    dp, ctx = dpx
+    import oracle
+    I, D, M, NT, NPH = shape
+    if bank == "modes":
+        wl = synth.make_workload(n_int=I, n_ext=2, n_det=D, n_modes=M, n_bins=48, seed=95, snr=12.0)
+        ps = synth.make_presel_inputs(wl, n_t=NT, dt=1e-3, seed=96)
+        pol, t_grid, precs = ps.pol, ps.t_grid, ("fp16x3",)
+    else:
+        wl = synth.make_precessing_workload(I, 2, D, M, 48, snr=12.0, seed=97, n_phi=NPH)
+        pol, t_grid, precs = None, np.tile((np.arange(NT) - NT // 2) * 1e-3, (D, 1)), ("fp16x3", "fp32")
+    P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h, pol, wl.event.psd, wl.event.data,
+                             t_grid, n_phi=NPH)
+    ref = P.run(delta=20.0)
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w, pol=pol)
+    try:
+        for prec in precs:
+            r = dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, t_grid, n_phi=NPH, delta=20.0,
+                                   precision=prec)
+            assert np.all(np.abs(r["lnl_ml"] - ref["ml"]) <= split_tol(ref["ml"])), prec
+            assert r["n_selected"] == int(ref["keep"].sum()) or I > 1
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
