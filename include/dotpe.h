@@ -341,6 +341,16 @@ int dotpe_device_info(dotpe_ctx *ctx, int *n_sms, char *name, int name_len);
 int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *desc, uint64_t *bank_id);
 
 /* Frees a bank.  E_INVALID if an unreleased event still uses it. */
+/* A new bank holding rows[0..n) of bank bank_id, in that order (Sec. IV.D:
+ * the coherent stage runs on the rows the pre-selection keeps; its
+ * `selected` output is a valid row list).  The rows' waveforms are copied on
+ * the device as the bank holds them (FP32 master and both operand formats,
+ * same scale), with their ln w_int and polarisation factors, so an event over
+ * the new bank gives, pair by pair, the values of the parent bank's rows.
+ * rows: int64 [n], host or device, each in [0, n_int) (repeats allowed).
+ * Errors: E_INVALID (null argument, n < 1, a row out of range), E_NOT_FOUND,
+ * E_NOMEM (beyond the HBM budget), E_DEVICE. */
+int dotpe_bank_subset(dotpe_ctx *ctx, uint64_t bank_id, const int64_t *rows, int64_t n, uint64_t *new_bank_id);
 int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id);
 
 /* ---- events ------------------------------------------------------------ */

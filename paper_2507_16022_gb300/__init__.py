@@ -44,7 +44,7 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
            "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit",
-           "dotpe_preselect", "dotpe_rb_weights", "dotpe_posterior_samples")
+           "dotpe_preselect", "dotpe_rb_weights", "dotpe_posterior_samples", "dotpe_bank_subset")
 
 
 class DotpeError(RuntimeError):
@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
                               ctypes.c_int),
         "dotpe_bank_load": ([vp, ctypes.POINTER(dotpe_bank_desc), u64p], ctypes.c_int),
         "dotpe_bank_release": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "dotpe_bank_subset": ([vp, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64, u64p], ctypes.c_int),
         "dotpe_event_submit": ([vp, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
         "dotpe_batch_submit": ([vp, ctypes.c_int, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
         "dotpe_event_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
@@ -247,6 +248,19 @@ def dotpe_bank_load(ctx, h, f, w_quad, mode_m, ln_w_int=None, pol=None):
                            hp, dtype, _ptr(lw), None if pl is None else _ptr(pl.view(np.float64)), n_pol)
     bid = ctypes.c_uint64()
     _check(L.dotpe_bank_load(ctx, ctypes.byref(desc), ctypes.byref(bid)))
+    return bid.value
+
+
+def dotpe_bank_subset(ctx, bank_id, rows):
+    """A new bank of the rows (int64, numpy host array or torch tensor on the device)
+    of bank_id, e.g. the pre-selection's `selected` rows."""
+    if hasattr(rows, "data_ptr"):
+        ptr, n = ctypes.c_void_p(rows.data_ptr()), int(rows.numel())
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        ptr, n = ctypes.c_void_p(rows.ctypes.data), int(rows.shape[0])
+    bid = ctypes.c_uint64()
+    _check(load().dotpe_bank_subset(ctx, ctypes.c_uint64(bank_id), ptr, n, ctypes.byref(bid)))
     return bid.value
 
 

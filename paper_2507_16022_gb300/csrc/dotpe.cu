@@ -1726,6 +1726,83 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   return DOTPE_OK;
 }
 
+int dotpe_bank_subset(dotpe_ctx *ctx, uint64_t bank_id, const int64_t *rows, int64_t n, uint64_t *new_bank_id) {
+  if (!ctx || !rows || !new_bank_id) return fail(DOTPE_E_INVALID, "null argument");
+  if (n < 1) return fail(DOTPE_E_INVALID, "n=%lld rows", (long long)n);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->banks.find(bank_id);
+  if (it == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)bank_id);
+  const Bank &s = *it->second;
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  // the row list on the host, checked
+  std::vector<int64_t> hr((size_t)n);
+  if (is_device_ptr(rows)) CUDA_OR_FAIL(cudaMemcpy(hr.data(), rows, (size_t)n * 8, cudaMemcpyDeviceToHost));
+  else memcpy(hr.data(), rows, (size_t)n * 8);
+  for (int64_t r = 0; r < n; ++r)
+    if (hr[r] < 0 || hr[r] >= s.I) return fail(DOTPE_E_INVALID, "rows[%lld]=%lld not in [0, %lld)", (long long)r,
+                                                (long long)hr[r], (long long)s.I);
+  Bank *b = new Bank();
+  b->I = n;
+  b->M = s.M;
+  b->B = s.B;
+  b->Kpad = s.Kpad;
+  b->n_pol = s.n_pol;
+  b->a_scale = s.a_scale;
+  for (int m = 0; m < MAXM; ++m) b->mode_m[m] = s.mode_m[m];
+  const size_t nel = (size_t)b->M * n * b->Kpad;
+  Carver c;
+  size_t o_f = c.take<double>(b->B), o_w = c.take<double>(b->B), o_lw = c.take<double>(s.lw ? n : 0);
+  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(2 * nel);
+  size_t o_pol = c.take<float2>(s.pol ? (size_t)n * b->M * 2 : 0);
+  size_t o_rows = c.take<int64_t>(n);
+  b->bytes = c.off;
+  if (ctx->used + b->bytes > ctx->budget) {
+    delete b;
+    return fail(DOTPE_E_NOMEM, "bank subset needs %zu bytes beyond the budget", c.off);
+  }
+  if (cudaMalloc(&b->block, b->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(DOTPE_E_NOMEM, "bank subset allocation of %zu bytes", c.off);
+  }
+  uint8_t *base = (uint8_t *)b->block;
+  b->f = (double *)(base + o_f);
+  b->w = (double *)(base + o_w);
+  b->lw = s.lw ? (double *)(base + o_lw) : nullptr;
+  b->master = (float *)(base + o_master);
+  b->bf = (__nv_bfloat16 *)(base + o_bf);
+  b->hf = (__half *)(base + o_hf);
+  b->pol = s.pol ? (float2 *)(base + o_pol) : nullptr;
+  int64_t *drows = (int64_t *)(base + o_rows);
+  cudaStream_t st = ctx->main_stream;
+  int rc = DOTPE_OK;
+  auto check = [&](cudaError_t x) {
+    if (x != cudaSuccess && rc == DOTPE_OK) rc = fail(DOTPE_E_DEVICE, "bank subset: %s", cudaGetErrorString(x));
+  };
+  check(cudaMemcpyAsync(drows, hr.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+  check(cudaMemcpyAsync(b->f, s.f, (size_t)b->B * 8, cudaMemcpyDeviceToDevice, st));
+  check(cudaMemcpyAsync(b->w, s.w, (size_t)b->B * 8, cudaMemcpyDeviceToDevice, st));
+  // the same operand values row by row (planes keep the parent's scale)
+  const int64_t kw = b->Kpad;  // words per master row; a plane row is Kpad 16-bit values = Kpad / 2 words
+  launch_gather_rows(b->M, s.I, n, kw, s.master, drows, b->master, st);
+  launch_gather_rows(2 * b->M, s.I, n, kw / 2, s.bf, drows, b->bf, st);
+  launch_gather_rows(2 * b->M, s.I, n, kw / 2, s.hf, drows, b->hf, st);
+  if (s.lw) launch_gather_rows(1, s.I, n, 2, s.lw, drows, b->lw, st);
+  if (s.pol) launch_gather_rows(1, s.I, n, 4 * b->M, s.pol, drows, b->pol, st);
+  check(cudaGetLastError());
+  check(cudaStreamSynchronize(st));
+  if (rc != DOTPE_OK) {
+    cudaFree(b->block);
+    delete b;
+    return rc;
+  }
+  b->id = ctx->next_id++;
+  ctx->banks[b->id] = b;
+  ctx->used += b->bytes;
+  *new_bank_id = b->id;
+  return DOTPE_OK;
+}
+
 int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id) {
   if (!ctx) return fail(DOTPE_E_INVALID, "ctx is null");
   std::lock_guard<std::mutex> lk(ctx->mu);

@@ -59,6 +59,9 @@ void launch_bank_to_master(int64_t rows, int64_t row0, int64_t I_bank, int M, in
 void launch_cross_terms_pol(int64_t n_rows, int64_t row0, int64_t I_bank, int M, int D, int B, int Kpad,
                             const int *mode_m, const float *master, const float *omega, const double2 *rb_hh,
                             float *mx, int n_sms, cudaStream_t st);
+// dst[o][r][:] = src[o][rows[r]][:], rows of row_words 32-bit words (device rows[n], in range)
+void launch_gather_rows(int64_t outer, int64_t src_rows, int64_t n, int64_t row_words, const void *src,
+                        const int64_t *rows, void *dst, cudaStream_t st);
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf /*[2][n]*/,
                              __half *hf /*[2][n]*/, float *scale_out, cudaStream_t st);
 void launch_build_dm_table(float4 *tab, cudaStream_t st);

@@ -792,6 +792,23 @@ void launch_cross_terms_pol(int64_t n_rows, int64_t row0, int64_t I_bank, int M,
                                                                     omega, nullptr, mx);
 }
 
+// dst[o][r][w] = src[o][rows[r]][w] (32-bit words): a bank's rows gathered into a new bank
+__global__ void gather_rows_kernel(int64_t outer, int64_t src_rows, int64_t n, int64_t row_words,
+                                   const uint32_t *__restrict__ src, const int64_t *__restrict__ rows,
+                                   uint32_t *__restrict__ dst) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= outer * n * row_words) return;
+  const int64_t w = k % row_words, orr = k / row_words;
+  const int64_t r = orr % n, o = orr / n;
+  dst[k] = src[(o * src_rows + rows[r]) * row_words + w];
+}
+
+void launch_gather_rows(int64_t outer, int64_t src_rows, int64_t n, int64_t row_words, const void *src,
+                        const int64_t *rows, void *dst, cudaStream_t st) {
+  gather_rows_kernel<<<nblk(outer * n * row_words, 256), 256, 0, st>>>(outer, src_rows, n, row_words,
+                                                                      (const uint32_t *)src, rows, (uint32_t *)dst);
+}
+
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf, __half *hf,
                              float *scale_out, cudaStream_t st) {
   master_to_planes_kernel<<<nblk(n, 256), 256, 0, st>>>(n, master, amax, bf, hf, scale_out);
