@@ -16,7 +16,7 @@ reduction.  The K timed events are submitted together; the runtime runs up to
 four at once.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload event|batch64|serve|presel|rb|samples|precessing]
+                  [--workload event|batch64|serve|presel|rb|samples|precessing|pipeline]
 
 --workload batch64: 64 events (extrinsic counts from {512, ..., 4096}, 2-3
 detectors, SNR 8-40) over one shared 262,144-row bank, submitted as one batch:
@@ -38,6 +38,9 @@ a step is one dotpe_posterior_samples call of 65,536 samples.
 --workload precessing: a polarisation-resolved bank (Sec. IV.A general case,
 h_{imp} with both polarisations, antenna patterns per sample) of 16,384 rows x
 4,096 samples, 3 detectors, 4 modes, 512 bins; a step is one event.
+--workload pipeline: the pre-selection of the 65,536-row bank, the kept rows
+gathered into a new bank, their coherent evaluation against the 4,096 samples;
+a step is one event through the three calls.
 
 Under torchrun (N > 1) every rank runs its own independent events on its own
 GPU (events do not share data: weak scaling, no collective on the data path);
@@ -751,6 +754,62 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     return line
 
 
+def bench_pipeline(args, dp, ctx_factory, torch, dev):
+    """The paper's two stages per event (Sec. IV.D then IV.B): the incoherent
+    pre-selection of the 65,536-row bank (fp16x3), the kept rows gathered into
+    a new bank (dotpe_bank_subset), and the coherent evaluation of the kept rows
+    against the 4,096 extrinsic samples (mixed, cut 20); a step is one event
+    through all three, wall clock of the synchronous calls."""
+    import synth
+    wl = synth.make_workload(**WORKLOAD, n_phi=N_PHI)
+    ps = synth.make_presel_inputs(wl)
+    I, E = WORKLOAD["n_int"], WORKLOAD["n_ext"]
+    ctx = ctx_factory()
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w, pol=ps.pol)
+
+    def step():
+        r = dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI,
+                               delta=CUT_DELTA, precision="fp16x3", outputs=("selected",))
+        sub = dp.dotpe_bank_subset(ctx, bid, r["selected"])
+        n = int(r["n_selected"])
+        eid = dp.dotpe_event_submit(ctx, sub, 0, n, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R, wl.ext.ln_w,
+                                    n_phi=N_PHI, u_min=wl.event.u_min, cut_delta=args.cut, precision="mixed")
+        dp.dotpe_event_wait(ctx, eid, 600.0)
+        ev = dp.dotpe_evidence(ctx, eid)
+        dp.dotpe_event_release(ctx, eid)
+        dp.dotpe_bank_release(ctx, sub)
+        return n, ev
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    t = time.perf_counter()
+    kept = []
+    for _ in range(args.steps):
+        n, ev = step()
+        kept.append(n)
+    dt = (time.perf_counter() - t) / args.steps
+    clocks = sampler.stop()
+    dp.dotpe_bank_release(ctx, bid)
+    dp.dotpe_destroy(ctx)
+    return {
+        "metric": "events/s through pre-selection and coherent evaluation", "value": 1.0 / dt, "unit": "events/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
+        "config": {"workload": f"pre-selection of {I} rows (D 3, N_t 128, N_phi {N_PHI}, window {CUT_DELTA:g}), "
+                               f"the kept rows x {E} extrinsic samples coherently (mixed, cut {args.cut:g})",
+                   "kept_rows": kept[-1], "ln_z": ev["ln_z"],
+                   "timing": "wall clock of the synchronous calls (inputs from host memory, results read back)"},
+        "roofline": None,
+        "e2e": {"value": 1.0 / dt, "unit": "events/s", "h2d_bytes_per_step": int(wl.event.psd.nbytes * 2
+                + wl.event.data.nbytes * 2 + ps.t_grid.nbytes + wl.ext.t.nbytes + wl.ext.R.nbytes
+                + wl.ext.ln_w.nbytes), "d2h_bytes_per_step": int(8 * kept[-1] + 96 + 64)},
+        # pre-selection 6, subset 3-5 gathers, coherent event 17 (mixed)
+        "gpu_launches": 28 * args.steps, "clocks": clocks, "cpu_baseline": None,
+    }
+
+
 def bench_samples(args, dp, ctx_factory, torch, dev):
     """Posterior samples of one stored 65,536 x 4,096 event; a step draws 65,536
     samples (the paper's N_s = N_eff/2 is reported beside it)."""
@@ -902,7 +961,7 @@ def main():
     ap.add_argument("--n-int", type=int, default=WORKLOAD["n_int"], help="bank rows (profiling runs)")
     ap.add_argument("--n-ext", type=int, default=WORKLOAD["n_ext"], help="extrinsic samples (profiling runs)")
     ap.add_argument("--workload", default="event",
-                    choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing"])
+                    choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing", "pipeline"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--precessing", action="store_true",
                     help="rb, presel: a polarisation-resolved bank (rb: weights per (mode, polarisation) "
@@ -945,6 +1004,8 @@ def main():
             line = bench_samples(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         elif args.workload == "precessing":
             line = bench_precessing(args, dp, lambda: dp.dotpe_create(local), torch, dev)
+        elif args.workload == "pipeline":
+            line = bench_pipeline(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         else:
             line = bench_serve(args, dp, lambda: dp.dotpe_create(local, max_batch=args.max_batch), torch, dev)
         print(json.dumps(line), flush=True)
