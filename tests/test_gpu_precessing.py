@@ -18,9 +18,11 @@ the polarisation index p and real antenna patterns F_{edp}).
   polarisation) component) match the oracle's resampling with the same
   uniforms: identical (i, e, o) except within the weights' tolerance of a
   cumulative boundary, distances to 2e-3.
-* Pre-selection and batches in a tensor-core precision are refused with
-  DOTPE_E_UNSUPPORTED; a missing F with DOTPE_E_INVALID.  (Relative binning
-  with component weights is tested with the other relative-binning cases.)
+* Pre-selection with relative binning and batches in a tensor-core precision
+  are refused with DOTPE_E_UNSUPPORTED; a missing F with DOTPE_E_INVALID.
+  (Relative binning of events with component weights is tested with the other
+  relative-binning cases, the pre-selection of such banks with the other
+  pre-selection cases.)
 """
 import numpy as np
 import pytest
@@ -252,9 +254,10 @@ def test_refusals(dpx, pwl):
         assert ei.value.status == dp.DOTPE_E_INVALID
         D, B = wl.event.psd.shape
         t_grid = np.zeros((D, 16))
+        rb = (np.ones((D, M, B), np.complex128), np.ones((D, M, M, B), np.complex128))
         with pytest.raises(dp.DotpeError) as ei:
-            dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, t_grid, n_phi=32, delta=20.0,
-                               precision="fp16x3")
+            dp.dotpe_preselect(ctx, bid, 0, I, None, None, t_grid, n_phi=32, delta=20.0, precision="fp16x3",
+                               rb=rb)
         assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
     finally:
         dp.dotpe_bank_release(ctx, bid)
