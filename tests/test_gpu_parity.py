@@ -383,6 +383,53 @@ def test_concurrent_events_equal_alone(dpx):
         dp.dotpe_bank_release(ctx, bid)
 
 
+def test_host_threads_share_one_context(dpx):
+    """Four host threads submit, wait for, read and release events on one
+    context at once (the ABI's calls are thread-safe on a context); each
+    thread's results equal the same events run one at a time, bit for bit."""
+    import threading
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=1536, n_ext=256, n_det=3, n_modes=4, n_bins=256, snr=12.0, seed=23)
+    rng = np.random.default_rng(4)
+    evs = [synth.make_event(rng, wl.bank, wl.ext, 3, snr=float(s)) for s in (9, 14, 22, 30)]
+    precs = ("fp32", "bf16x3", "fp16x3", "mixed")
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+
+    def one(ev, prec):
+        eid = dp.dotpe_event_submit(ctx, bid, 0, 1536, ev.psd, ev.data, wl.ext.t, wl.ext.R, n_phi=32,
+                                    u_min=ev.u_min, precision=prec)
+        dp.dotpe_event_wait(ctx, eid, 120.0)
+        r = dp.dotpe_evidence(ctx, eid)
+        dp.dotpe_event_release(ctx, eid)
+        return r
+
+    try:
+        alone = [one(evs[k], precs[k]) for k in range(4)]
+        got = [[None] * 3 for _ in range(4)]
+        errors = []
+
+        def worker(k):
+            try:
+                for rep in range(3):
+                    got[k][rep] = one(evs[k], precs[k])
+            except Exception as exc:  # reported below
+                errors.append(exc)
+
+        threads = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(300)
+        assert not errors, errors
+        for k in range(4):
+            for rep in range(3):
+                b, a = got[k][rep], alone[k]
+                assert b["ln_z"] == a["ln_z"] and b["n_eff"] == a["n_eff"], (k, rep)
+                assert (b["arg_i"], b["arg_e"], b["arg_o"]) == (a["arg_i"], a["arg_e"], a["arg_o"])
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+
+
 def test_served_mix_equal_alone(dpx):
     """Continuous batching: uneven events (bank slices, extrinsic counts, detector
     counts, SNR) in the served precision with the paper's cut, more events than
