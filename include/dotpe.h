@@ -351,6 +351,18 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *desc, uint64_t *bank_
  * Errors: E_INVALID (null argument, n < 1, a row out of range), E_NOT_FOUND,
  * E_NOMEM (beyond the HBM budget), E_DEVICE. */
 int dotpe_bank_subset(dotpe_ctx *ctx, uint64_t bank_id, const int64_t *rows, int64_t n, uint64_t *new_bank_id);
+
+/* Checkpoint / resume of a resident bank: dotpe_bank_save writes it to the
+ * file `path` (a header with the shapes, mode numbers and operand scale, then
+ * f, w_quad, ln w_int, the FP32 master rows and the polarisation factors, and
+ * an FNV-1a 64 checksum of them); dotpe_bank_open loads such a file as a new
+ * bank whose operands equal the saved bank's (the bf16/fp16 planes are
+ * rebuilt at the saved scale), so its events give the same values.  The file
+ * is in the host's byte order.  Errors: E_INVALID (null argument, unreadable
+ * or unwritable file, wrong magic or version, inconsistent header, truncated
+ * payload, checksum mismatch), E_NOT_FOUND, E_NOMEM, E_DEVICE. */
+int dotpe_bank_save(dotpe_ctx *ctx, uint64_t bank_id, const char *path);
+int dotpe_bank_open(dotpe_ctx *ctx, const char *path, uint64_t *bank_id);
 int dotpe_bank_release(dotpe_ctx *ctx, uint64_t bank_id);
 
 /* ---- events ------------------------------------------------------------ */

@@ -44,7 +44,8 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_event_submit", "dotpe_event_poll", "dotpe_event_wait", "dotpe_evidence",
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
            "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit",
-           "dotpe_preselect", "dotpe_rb_weights", "dotpe_posterior_samples", "dotpe_bank_subset")
+           "dotpe_preselect", "dotpe_rb_weights", "dotpe_posterior_samples", "dotpe_bank_subset",
+           "dotpe_bank_save", "dotpe_bank_open")
 
 
 class DotpeError(RuntimeError):
@@ -139,6 +140,8 @@ def load(path: str = LIB_PATH):
         "dotpe_bank_load": ([vp, ctypes.POINTER(dotpe_bank_desc), u64p], ctypes.c_int),
         "dotpe_bank_release": ([vp, ctypes.c_uint64], ctypes.c_int),
         "dotpe_bank_subset": ([vp, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64, u64p], ctypes.c_int),
+        "dotpe_bank_save": ([vp, ctypes.c_uint64, ctypes.c_char_p], ctypes.c_int),
+        "dotpe_bank_open": ([vp, ctypes.c_char_p, u64p], ctypes.c_int),
         "dotpe_event_submit": ([vp, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
         "dotpe_batch_submit": ([vp, ctypes.c_int, ctypes.POINTER(dotpe_event_desc), u64p], ctypes.c_int),
         "dotpe_event_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
@@ -261,6 +264,18 @@ def dotpe_bank_subset(ctx, bank_id, rows):
         ptr, n = ctypes.c_void_p(rows.ctypes.data), int(rows.shape[0])
     bid = ctypes.c_uint64()
     _check(load().dotpe_bank_subset(ctx, ctypes.c_uint64(bank_id), ptr, n, ctypes.byref(bid)))
+    return bid.value
+
+
+def dotpe_bank_save(ctx, bank_id, path):
+    """Write the bank to a file (checkpoint)."""
+    return _check(load().dotpe_bank_save(ctx, ctypes.c_uint64(bank_id), os.fsencode(path)))
+
+
+def dotpe_bank_open(ctx, path):
+    """Load a bank file written by dotpe_bank_save as a new bank; returns its id."""
+    bid = ctypes.c_uint64()
+    _check(load().dotpe_bank_open(ctx, os.fsencode(path), ctypes.byref(bid)))
     return bid.value
 
 

@@ -1726,6 +1726,188 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
   return DOTPE_OK;
 }
 
+}  // extern "C"
+
+// ---- bank files (checkpoint / resume) ----
+// Little-endian, host-native: the header, then the payload f [B], w [B],
+// ln w_int [I] (if present), the FP32 master [M][I][Kpad], the polarisation
+// factors [I][M][2] float2 (if present); FNV-1a 64 over the payload.  The
+// operand planes are rebuilt on open at the saved scale, so they equal the
+// saved bank's planes.
+struct BankFileHeader {
+  char magic[8];
+  uint32_t version, n_pol;
+  int64_t n_int;
+  int32_t n_modes, n_bins, kpad, has_lw, has_pol;
+  int32_t mode_m[MAXM];
+  float a_scale;
+  uint64_t payload_bytes, checksum;
+};
+static const char BANK_MAGIC[8] = {'D', 'O', 'T', 'P', 'E', 'B', 'K', '1'};
+
+static uint64_t fnv1a(uint64_t h, const uint8_t *p, size_t n) {
+  for (size_t k = 0; k < n; ++k) {
+    h ^= p[k];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// One allocation for a bank's arrays (the layout of dotpe_bank_load); pointers set, nothing copied.
+static int bank_alloc(dotpe_ctx *ctx, int64_t I, int M, int B, int Kpad, int n_pol, bool has_lw, bool has_pol,
+                      size_t extra_bytes, Bank **out, uint8_t **extra) {
+  Bank *b = new Bank();
+  b->I = I; b->M = M; b->B = B; b->Kpad = Kpad; b->n_pol = n_pol;
+  const size_t nel = (size_t)M * I * Kpad;
+  Carver c;
+  size_t o_f = c.take<double>(B), o_w = c.take<double>(B), o_lw = c.take<double>(has_lw ? I : 0);
+  size_t o_master = c.take<float>(nel), o_bf = c.take<__nv_bfloat16>(2 * nel), o_hf = c.take<__half>(2 * nel);
+  size_t o_pol = c.take<float2>(has_pol ? (size_t)I * M * 2 : 0);
+  size_t o_extra = c.take<uint8_t>(extra_bytes);
+  b->bytes = c.off;
+  if (ctx->used + b->bytes > ctx->budget) {
+    delete b;
+    return fail(DOTPE_E_NOMEM, "bank needs %zu bytes beyond the budget", c.off);
+  }
+  if (cudaMalloc(&b->block, b->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(DOTPE_E_NOMEM, "bank allocation of %zu bytes", c.off);
+  }
+  uint8_t *base = (uint8_t *)b->block;
+  b->f = (double *)(base + o_f);
+  b->w = (double *)(base + o_w);
+  b->lw = has_lw ? (double *)(base + o_lw) : nullptr;
+  b->master = (float *)(base + o_master);
+  b->bf = (__nv_bfloat16 *)(base + o_bf);
+  b->hf = (__half *)(base + o_hf);
+  b->pol = has_pol ? (float2 *)(base + o_pol) : nullptr;
+  if (extra) *extra = base + o_extra;
+  *out = b;
+  return DOTPE_OK;
+}
+
+extern "C" {
+
+int dotpe_bank_save(dotpe_ctx *ctx, uint64_t bank_id, const char *path) {
+  if (!ctx || !path) return fail(DOTPE_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->banks.find(bank_id);
+  if (it == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)bank_id);
+  const Bank &b = *it->second;
+  CUDA_OR_FAIL(cudaSetDevice(ctx->device));
+  CUDA_OR_FAIL(cudaDeviceSynchronize());
+  struct Part { const void *src; size_t n; };
+  const Part parts[5] = {{b.f, (size_t)b.B * 8}, {b.w, (size_t)b.B * 8}, {b.lw, b.lw ? (size_t)b.I * 8 : 0},
+                         {b.master, (size_t)b.M * b.I * b.Kpad * 4}, {b.pol, b.pol ? (size_t)b.I * b.M * 16 : 0}};
+  BankFileHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, BANK_MAGIC, 8);
+  h.version = 1;
+  h.n_pol = (uint32_t)b.n_pol;
+  h.n_int = b.I;
+  h.n_modes = b.M; h.n_bins = b.B; h.kpad = b.Kpad;
+  h.has_lw = b.lw != nullptr; h.has_pol = b.pol != nullptr;
+  for (int m = 0; m < MAXM; ++m) h.mode_m[m] = b.mode_m[m];
+  h.a_scale = b.a_scale;
+  for (const Part &p : parts) h.payload_bytes += p.n;
+  FILE *fp = fopen(path, "wb");
+  if (!fp) return fail(DOTPE_E_INVALID, "cannot open %s for writing", path);
+  const size_t chunk = (size_t)64 << 20;
+  std::vector<uint8_t> buf(chunk);
+  uint64_t sum = 1469598103934665603ull;
+  bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+  for (const Part &p : parts)
+    for (size_t o = 0; ok && o < p.n; o += chunk) {
+      const size_t n = std::min(chunk, p.n - o);
+      if (cudaMemcpy(buf.data(), (const uint8_t *)p.src + o, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        fclose(fp);
+        return fail(DOTPE_E_DEVICE, "bank save: copy from the device");
+      }
+      sum = fnv1a(sum, buf.data(), n);
+      ok = fwrite(buf.data(), 1, n, fp) == n;
+    }
+  h.checksum = sum;
+  ok = ok && fseek(fp, 0, SEEK_SET) == 0 && fwrite(&h, sizeof(h), 1, fp) == 1;
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? DOTPE_OK : fail(DOTPE_E_INVALID, "writing %s failed", path);
+}
+
+int dotpe_bank_open(dotpe_ctx *ctx, const char *path, uint64_t *bank_id) {
+  if (!ctx || !path || !bank_id) return fail(DOTPE_E_INVALID, "null argument");
+  FILE *fp = fopen(path, "rb");
+  if (!fp) return fail(DOTPE_E_INVALID, "cannot open %s", path);
+  BankFileHeader h;
+  if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, BANK_MAGIC, 8) != 0 || h.version != 1) {
+    fclose(fp);
+    return fail(DOTPE_E_INVALID, "%s is not a bank file of this version", path);
+  }
+  const int np = (h.n_pol == 2) ? 2 : 1;
+  const bool shape_ok = h.n_int >= 1 && h.n_modes >= 1 && h.n_modes <= MAXM && h.n_bins >= 2 &&
+                        h.kpad == (int)(((2 * np * (int64_t)h.n_bins + 63) / 64) * 64) && h.a_scale > 0.f;
+  const size_t want = (size_t)h.n_bins * 16 + (h.has_lw ? (size_t)h.n_int * 8 : 0) +
+                      (size_t)h.n_modes * h.n_int * h.kpad * 4 + (h.has_pol ? (size_t)h.n_int * h.n_modes * 16 : 0);
+  if (!shape_ok || h.payload_bytes != want) {
+    fclose(fp);
+    return fail(DOTPE_E_INVALID, "%s: inconsistent header", path);
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    fclose(fp);
+    return fail(DOTPE_E_DEVICE, "cudaSetDevice");
+  }
+  Bank *b = nullptr;
+  uint8_t *extra = nullptr;  // 16 bytes of device scratch: amax and the plane scale
+  int rc = bank_alloc(ctx, h.n_int, h.n_modes, h.n_bins, h.kpad, np, h.has_lw, h.has_pol, 16, &b, &extra);
+  if (rc != DOTPE_OK) {
+    fclose(fp);
+    return rc;
+  }
+  for (int m = 0; m < MAXM; ++m) b->mode_m[m] = h.mode_m[m];
+  b->a_scale = h.a_scale;
+  struct Part { void *dst; size_t n; };
+  const Part parts[5] = {{b->f, (size_t)b->B * 8}, {b->w, (size_t)b->B * 8}, {b->lw, b->lw ? (size_t)b->I * 8 : 0},
+                         {b->master, (size_t)b->M * b->I * b->Kpad * 4},
+                         {b->pol, b->pol ? (size_t)b->I * b->M * 16 : 0}};
+  const size_t chunk = (size_t)64 << 20;
+  std::vector<uint8_t> buf(chunk);
+  uint64_t sum = 1469598103934665603ull;
+  bool ok = true;
+  for (const Part &p : parts)
+    for (size_t o = 0; ok && o < p.n; o += chunk) {
+      const size_t n = std::min(chunk, p.n - o);
+      ok = fread(buf.data(), 1, n, fp) == n;
+      if (ok) {
+        sum = fnv1a(sum, buf.data(), n);
+        ok = cudaMemcpy((uint8_t *)p.dst + o, buf.data(), n, cudaMemcpyHostToDevice) == cudaSuccess;
+      }
+    }
+  fclose(fp);
+  if (!ok || sum != h.checksum) {
+    cudaFree(b->block);
+    delete b;
+    return fail(DOTPE_E_INVALID, "%s: %s", path, ok ? "checksum mismatch" : "truncated or unreadable payload");
+  }
+  // the operand planes at the saved scale: an amax whose power-of-two scale is a_scale
+  float *amax = (float *)extra;
+  const float am = 0.75f / b->a_scale;
+  cudaStream_t st = ctx->main_stream;
+  int64_t nel = (int64_t)b->M * b->I * b->Kpad;
+  bool dev_ok = cudaMemcpyAsync(amax, &am, 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  launch_master_to_planes(nel, b->master, amax, b->bf, b->hf, amax + 1, st);
+  dev_ok = dev_ok && cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  if (!dev_ok) {
+    cudaFree(b->block);
+    delete b;
+    return fail(DOTPE_E_DEVICE, "bank open: operand planes");
+  }
+  b->id = ctx->next_id++;
+  ctx->banks[b->id] = b;
+  ctx->used += b->bytes;
+  *bank_id = b->id;
+  return DOTPE_OK;
+}
+
 int dotpe_bank_subset(dotpe_ctx *ctx, uint64_t bank_id, const int64_t *rows, int64_t n, uint64_t *new_bank_id) {
   if (!ctx || !rows || !new_bank_id) return fail(DOTPE_E_INVALID, "null argument");
   if (n < 1) return fail(DOTPE_E_INVALID, "n=%lld rows", (long long)n);

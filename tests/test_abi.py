@@ -58,6 +58,8 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert L.dotpe_preselect(None, None, None, None, None, None, None) == dp.DOTPE_E_INVALID
     assert L.dotpe_rb_weights(None, None, None, None) == dp.DOTPE_E_INVALID
     assert L.dotpe_bank_subset(None, 1, None, 1, None) == dp.DOTPE_E_INVALID
+    assert L.dotpe_bank_save(None, 1, None) == dp.DOTPE_E_INVALID
+    assert L.dotpe_bank_open(None, None, None) == dp.DOTPE_E_INVALID
     assert "null" in L.dotpe_last_error_message().decode()
 
 
