@@ -34,17 +34,18 @@ typedef struct or_problem {
   const double *t;                   /* [E][D] */
   const double *ln_w_int, *ln_w_ext; /* [I], [E] (may be NULL: zeros) */
   double u_min;                      /* d_L^0 / d_max of pi(d_L) ~ d_L^2 */
-  /* relative binning (App. A), both or neither (NULL: plain quadrature with w):
-   * rb_dh complex [D][M][B] = W^{<d|h>}_{d m b}, rb_hh complex [D][M][M][B] =
-   * W^{<h|h>}_{d m m' b}; then <d|h_m>_d = sum_b W^{<d|h>}_{d m b} h_m^*(f_b) and
-   * <h_m|h_m'>_d = sum_b W^{<h|h>}_{d m m' b} h_m(f_b) h_m'^*(f_b) (Eqs. d_h, h_h).
-   * Route O2 only (the weights are per mode). */
+  /* relative binning (App. A), both or neither (NULL: plain quadrature with w),
+   * per component j (a mode, or the (mode, polarisation) pair j = m n_pol + p):
+   * rb_dh complex [D][J][B] = W^{<d|h>}_{d j b}, rb_hh complex [D][J][J][B] =
+   * W^{<h|h>}_{d j j' b} (J = M n_pol); then <d|h_j>_d = sum_b W^{<d|h>}_{d j b} h_j^*(f_b)
+   * and <h_j|h_j'>_d = sum_b W^{<h|h>}_{d j j' b} h_j(f_b) h_j'^*(f_b) (Eqs. dh_weights,
+   * hh_weights, d_h, h_h).  Route O2 only. */
   const double *rb_dh, *rb_hh;
   /* polarisation-resolved (precessing) bank (Sec. IV.A general case,
    * Eqs. dh_ieo, hh_ieo with the index p): n_pol = 2, h complex [I][M][2][B]
    * (h_{i m p}, p = +, x), F [E][D][2] real antenna patterns F_{e d p} replacing R:
    * the strain is sum_{m,p} F_{edp} h_{imp} e^{i m phi} T.  n_pol = 0 or 1: h [I][M][B]
-   * and R as above.  Relative binning applies to n_pol <= 1 only. */
+   * and R as above. */
   int n_pol;
   const double *F;
 } or_problem;

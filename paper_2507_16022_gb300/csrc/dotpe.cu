@@ -14,6 +14,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 namespace dotpe {
@@ -57,6 +59,13 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
 }
 
 // Carves one allocation into 256-byte aligned pieces.
+// NVTX range over a host scope (the enqueueing of one stage of an event or a
+// call); profilers that record NVTX show the stages by name.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 struct Carver {
   size_t off = 0;
   template <typename T>
@@ -697,12 +706,16 @@ static int psd_hash(int D, int B, const double *psd, uint64_t *out, const double
 
 // One event on its slot stream, its slice in bank blocks.
 static int run_event(dotpe_ctx *ctx, Event &e) {
+  NvtxRange nv("dotpe:event");
   cudaStream_t st = ctx->streams[e.slot];
   EventRun R;
   int rc = event_alloc(ctx, e, st, R);
   if (rc != DOTPE_OK) return rc;
-  if ((rc = xterms_acquire(ctx, e, R, st)) != DOTPE_OK) return rc;
-  if ((rc = event_begin(e, R, st)) != DOTPE_OK) return rc;
+  {
+    NvtxRange np("dotpe:prep");
+    if ((rc = xterms_acquire(ctx, e, R, st)) != DOTPE_OK) return rc;
+    if ((rc = event_begin(e, R, st)) != DOTPE_OK) return rc;
+  }
   const int64_t BR = R.L.block_rows;
   const int n_blocks = (int)((e.NI + BR - 1) / BR);
   for (int k = 0; k < n_blocks; ++k) {
@@ -710,9 +723,13 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
     event_block(ctx, e, R, r0, std::min<int64_t>(BR, e.NI - r0), st);
     if (k == 0 && ctx->autotune && (rc = autotune_band(ctx, e, R, st)) != DOTPE_OK) return rc;
     if (k == 0) CUDA_OR_FAIL(record(e.ev_k0, st));
-    if ((rc = event_fused(ctx, e, R, k == n_blocks - 1, st)) != DOTPE_OK) return rc;
+    {
+      NvtxRange nf("dotpe:fused");
+      if ((rc = event_fused(ctx, e, R, k == n_blocks - 1, st)) != DOTPE_OK) return rc;
+    }
     if (k == n_blocks - 1) CUDA_OR_FAIL(record(e.ev_k1, st));
     R.ra.first = (k == 0);
+    NvtxRange nr("dotpe:reduce");
     launch_reduce_block(R.ra, st);
   }
   if ((rc = event_end(ctx, e, R, st)) != DOTPE_OK) return rc;
@@ -795,6 +812,7 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
 // per-slot executable graph updated in place when the topology repeats.
 // ---------------------------------------------------------------------------
 static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) {
+  NvtxRange nv("dotpe:batch");
   cudaStream_t st = ctx->streams[slot];
   const int n = (int)evs.size();
   std::vector<EventRun> R(n);
@@ -1071,6 +1089,7 @@ static void free_event(dotpe_ctx *ctx, Event *e) {
 // ---------------------------------------------------------------------------
 static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *lnl_ml, int32_t *arg_ot,
                             double *lnl_inco, int64_t *selected, dotpe_presel_out *out) {
+  NvtxRange nv("dotpe:preselect");
   auto bit = ctx->banks.find(d->bank_id);
   if (bit == ctx->banks.end()) return fail(DOTPE_E_NOT_FOUND, "bank %llu", (unsigned long long)d->bank_id);
   Bank &b = *bit->second;
@@ -1312,6 +1331,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
 // Relative-binning weights (App. A)
 // ---------------------------------------------------------------------------
 static int rb_weights_locked(dotpe_ctx *ctx, const dotpe_rb_desc *d, double *w_dh, double *w_hh) {
+  NvtxRange nv("dotpe:rb_weights");
   if (d->n_det < 1 || d->n_det > MAXD) return fail(DOTPE_E_INVALID, "n_det=%d not in 1..%d", d->n_det, MAXD);
   if (d->n_modes < 1 || d->n_modes > 2 * MAXM)
     return fail(DOTPE_E_INVALID, "n_modes=%d components not in 1..%d", d->n_modes, 2 * MAXM);
@@ -1384,6 +1404,7 @@ static int rb_weights_locked(dotpe_ctx *ctx, const dotpe_rb_desc *d, double *w_d
 // ---------------------------------------------------------------------------
 static int samples_locked(dotpe_ctx *ctx, Event &e, int64_t n, const double *uniforms, int64_t *i_out,
                           int64_t *e_out, int32_t *o_out, double *d_out) {
+  NvtxRange nv("dotpe:posterior_samples");
   Bank &b = *e.bank;
   if (!(e.flags & DOTPE_FLAG_STORE_LNL))
     return fail(DOTPE_E_INVALID, "posterior samples need an event run with DOTPE_FLAG_STORE_LNL");
