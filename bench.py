@@ -818,14 +818,21 @@ def bench_samples(args, dp, ctx_factory, torch, dev):
     """Posterior samples of one stored 65,536 x 4,096 event; a step draws 65,536
     samples (the paper's N_s = N_eff/2 is reported beside it)."""
     import synth
-    wl = synth.make_workload(**WORKLOAD, n_phi=N_PHI)
-    I, E = WORKLOAD["n_int"], WORKLOAD["n_ext"]
+    pres = args.precessing  # a polarisation-resolved bank (16,384 rows): per-component pair recomputation
+    if pres:
+        I, E = 16384, WORKLOAD["n_ext"]
+        wl = synth.make_precessing_workload(I, E, WORKLOAD["n_det"], WORKLOAD["n_modes"], WORKLOAD["n_bins"],
+                                            snr=WORKLOAD["snr"], seed=8, n_phi=N_PHI)
+    else:
+        wl = synth.make_workload(**WORKLOAD, n_phi=N_PHI)
+        I, E = WORKLOAD["n_int"], WORKLOAD["n_ext"]
     ctx = ctx_factory()
     bank = wl.bank
     bid = dp.dotpe_bank_load(ctx, bank.h, bank.f, bank.w, bank.mode_m, bank.ln_w)
-    eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R, wl.ext.ln_w,
-                                n_phi=N_PHI, u_min=wl.event.u_min, cut_delta=args.cut, precision=args.precision,
-                                flags=dp.DOTPE_FLAG_STORE_LNL)
+    eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t,
+                                None if pres else wl.ext.R, wl.ext.ln_w, n_phi=N_PHI, u_min=wl.event.u_min,
+                                cut_delta=args.cut, precision=args.precision, flags=dp.DOTPE_FLAG_STORE_LNL,
+                                F=wl.ext.F if pres else None)
     dp.dotpe_event_wait(ctx, eid, 600.0)
     ev = dp.dotpe_evidence(ctx, eid)
     n = 65536
@@ -870,7 +877,9 @@ def bench_samples(args, dp, ctx_factory, torch, dev):
         "metric": "posterior samples/s", "value": n / dt, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"posterior samples of one stored event ({workload_name()}), 65,536 per call",
+        "config": {"workload": (f"posterior samples of one stored polarisation-resolved event ({I} x {E}, D 3, "
+                                f"M 4, B 512), 65,536 per call" if pres else
+                                f"posterior samples of one stored event ({workload_name()}), 65,536 per call"),
                    "precision": args.precision, "n_eff": ev["n_eff"], "n_s_paper": ns,
                    "ms_for_n_s": ns_ms, "timing": "wall clock of the synchronous call (uniforms and samples "
                                                  "copied between host and device inside)"},
