@@ -976,6 +976,8 @@ def main():
     ap.add_argument("--workload", default="event",
                     choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing", "pipeline"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--autotune", action="store_true",
+                    help="event: time candidate L2 bands on the first event (DOTPE_CONFIG_AUTOTUNE)")
     ap.add_argument("--precessing", action="store_true",
                     help="rb, presel: a polarisation-resolved bank (rb: weights per (mode, polarisation) "
                          "component; presel: the FP32 kernel)")
@@ -1033,7 +1035,7 @@ def main():
     events = [wl.event] + [synth.make_event(rng, wl.bank, wl.ext, D, snr=kw["snr"], n_phi=N_PHI)
                            for _ in range(args.events - 1)]
 
-    ctx = dp.dotpe_create(local)
+    ctx = dp.dotpe_create(local, flags=dp.DOTPE_CONFIG_AUTOTUNE if args.autotune else 0)
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
     dev = torch.device("cuda", local)
 
