@@ -440,7 +440,10 @@ int dotpe_lnl_blocks(dotpe_ctx *ctx, uint64_t event_id, int64_t i0, int64_t i1, 
 int dotpe_posterior_samples(dotpe_ctx *ctx, uint64_t event_id, int64_t n, const double *uniforms,
                             int64_t *i_out, int64_t *e_out, int32_t *o_out, double *dist_out);
 
-/* Frees an event's device state (waits for it if still running). */
+/* Frees an event's device state.  A RUNNING event is waited for first; a
+ * QUEUED event (not yet admitted to a slot) is cancelled: it never runs, and
+ * the events queued behind it are admitted in order.  The id is invalid
+ * afterwards (E_NOT_FOUND).  Errors: E_NOT_FOUND. */
 int dotpe_event_release(dotpe_ctx *ctx, uint64_t event_id);
 
 /* ---- relative binning -------------------------------------------------- */

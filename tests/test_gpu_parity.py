@@ -383,6 +383,45 @@ def test_concurrent_events_equal_alone(dpx):
         dp.dotpe_bank_release(ctx, bid)
 
 
+def test_release_cancels_a_queued_event():
+    """Releasing an event that still waits for a slot cancels it: it never
+    runs, its id is gone, and the events around it complete normally."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2507_16022_gb300 as dp
+    wl = synth.make_workload(n_int=1024, n_ext=128, n_det=2, n_modes=3, n_bins=128, snr=12.0, seed=25)
+    ctx = dp.dotpe_create(0, n_slots=1)
+    try:
+        bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+
+        def submit(stream=None):
+            return dp.dotpe_event_submit(ctx, bid, 0, 1024, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R,
+                                         n_phi=16, u_min=wl.event.u_min, precision="fp32", stream=stream)
+        ref = submit()
+        dp.dotpe_event_wait(ctx, ref, 60.0)
+        z_ref = dp.dotpe_evidence(ctx, ref)["ln_z"]
+        dp.dotpe_event_release(ctx, ref)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            torch.cuda._sleep(50_000_000)  # the first event's inputs wait behind this: it holds the slot
+        a = submit(stream=s)
+        b = submit()
+        assert dp.dotpe_event_poll(ctx, b)[0] == dp.DOTPE_STATE_QUEUED
+        dp.dotpe_event_release(ctx, b)  # cancelled before it ran
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_event_poll(ctx, b)
+        assert ei.value.status == dp.DOTPE_E_NOT_FOUND
+        c = submit()
+        for eid in (a, c):
+            dp.dotpe_event_wait(ctx, eid, 60.0)
+            assert dp.dotpe_evidence(ctx, eid)["ln_z"] == z_ref
+            dp.dotpe_event_release(ctx, eid)
+        dp.dotpe_bank_release(ctx, bid)
+    finally:
+        dp.dotpe_destroy(ctx)
+
+
 def test_host_threads_share_one_context(dpx):
     """Four host threads submit, wait for, read and release events on one
     context at once (the ABI's calls are thread-safe on a context); each
