@@ -243,12 +243,14 @@ class PreselProblem:
         self.t_grid = np.ascontiguousarray(t_grid, dtype=np.float64)
         I, M, B = self.h.shape[0], self.h.shape[1], self.h.shape[-1]
         D, NT = self.t_grid.shape
-        assert self.n_pol == 1 or (rb is None and self.h.shape[2] == 2)
+        assert self.n_pol == 1 or self.h.shape[2] == 2
         assert (self.n_pol == 2 or self.pol.shape == (I, M, 2)) and self.psd.shape == (D, B) \
             and self.data.shape == (D, B)
         self.shape = (I, D, M, B, NT)
         self.n_phi = int(n_phi)
         self.rb = None if rb is None else (_c128(rb[0]), _c128(rb[1]))
+        J = M * self.n_pol
+        assert rb is None or (self.rb[0].shape == (D, J, B) and self.rb[1].shape == (D, J, J, B))
         self.s = PreselStruct(I, D, M, B, NT, self.n_phi,
                               self.mode_m.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                               _dp(self.f), _dp(self.w), _dp(self.psd), _dp(self.data.view(np.float64)),

@@ -717,22 +717,28 @@ double or_quad_ml(double dp, double dx, double a, double b, double c) {
   return 0.5 * (a * dp * dp + 2.0 * b * dp * dx + c * dx * dx) / (s * s);
 }
 
-/* W_{m t b} = c_{k m b} T_{t k b} of one detector: [M][n_t][B] (Eq. dh_itop without the
- * waveform), c_{k m b} = 4 w_b d_k^*(f_b) / S_k(f_b), or (W^{<d|h>}_{k m b})^* with
- * relative binning (App. A; the polarisation factors cancel in Eq. dh_weights for a
- * reference waveform h0_{mp} = K_{mp} h0_m). */
+/* Number of data-weight components per mode: 2 with relative binning of a
+ * polarisation-resolved bank (one weight per (m, p), App. A's Eqs. dh_weights and
+ * hh_weights with the component index j = 2m + p), else 1. */
+static inline int presel_nw(const or_presel_problem *p) { return (p->rb_dh && p->n_pol == 2) ? 2 : 1; }
+
+/* W_{j t b} = c_{k j b} T_{t k b} of one detector: [M nw][n_t][B] (Eq. dh_itop without
+ * the waveform), c_{k j b} = 4 w_b d_k^*(f_b) / S_k(f_b) for every component, or
+ * (W^{<d|h>}_{k j b})^* with relative binning (App. A), j = m for a mode bank (the
+ * polarisation factors cancel in Eq. dh_weights for a reference h0_{mp} = K_{mp} h0_m)
+ * and j = 2m + p for a polarisation-resolved bank. */
 static cplx *presel_weights(const or_presel_problem *p, int k) {
-  const int B = p->n_bins, NT = p->n_t, M = p->n_modes;
+  const int B = p->n_bins, NT = p->n_t, J = p->n_modes * presel_nw(p);
   const int64_t kb = (int64_t)k * B;
-  cplx *W = malloc(sizeof(cplx) * (size_t)M * NT * B);
+  cplx *W = malloc(sizeof(cplx) * (size_t)J * NT * B);
   if (!W) return NULL;
-  for (int m = 0; m < M; ++m)
+  for (int j = 0; j < J; ++j)
     for (int t = 0; t < NT; ++t) {
       double tt = p->t_grid[(int64_t)k * NT + t];
       for (int b = 0; b < B; ++b) {
-        cplx c = p->rb_dh ? conj(ld_c(p->rb_dh, ((int64_t)k * M + m) * B + b))
+        cplx c = p->rb_dh ? conj(ld_c(p->rb_dh, ((int64_t)k * J + j) * B + b))
                           : (4.0 * p->w[b] / p->psd[kb + b]) * conj(ld_c(p->data, kb + b));
-        W[((int64_t)m * NT + t) * B + b] = c * cexp(-I * TWO_PI * p->f[b] * tt);
+        W[((int64_t)j * NT + t) * B + b] = c * cexp(-I * TWO_PI * p->f[b] * tt);
       }
     }
   return W;
@@ -740,6 +746,7 @@ static cplx *presel_weights(const or_presel_problem *p, int k) {
 
 static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, int k, double *ml_out) {
   const int M = p->n_modes, B = p->n_bins, NT = p->n_t, NP = p->n_phi;
+  const int nw = presel_nw(p), J = M * nw; /* weight component of (m, q): m nw + q (nw - 1) */
   const int64_t kb = (int64_t)k * B;
   cplx *hp = malloc(sizeof(cplx) * (size_t)2 * M * B); /* h_{i m p}(f_b): [p][m][b] */
   cplx *z = malloc(sizeof(cplx) * (size_t)2 * M);      /* [p][m]: sum_b W_{t b} h_{i m p}(f_b) */
@@ -767,7 +774,8 @@ static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, i
       for (int mp = 0; mp < M; ++mp) {
         cplx s = 0.0;
         for (int b = 0; b < B; ++b) {
-          cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)k * M + m) * M + mp) * B + b)
+          const int j = m * nw + pq[r][0] * (nw - 1), jp = mp * nw + pq[r][1] * (nw - 1);
+          cplx wgt = p->rb_hh ? ld_c(p->rb_hh, (((int64_t)k * J + j) * J + jp) * B + b)
                               : (cplx)(4.0 * p->w[b] / p->psd[kb + b]);
           s += wgt * hp[((int64_t)pq[r][0] * M + m) * B + b] * conj(hp[((int64_t)pq[r][1] * M + mp) * B + b]);
         }
@@ -786,7 +794,8 @@ static int presel_grid_w(const or_presel_problem *p, const cplx *W, int64_t i, i
     for (int q = 0; q < 2; ++q)
       for (int m = 0; m < M; ++m) {
         cplx acc = 0.0;
-        for (int b = 0; b < B; ++b) acc += W[((int64_t)m * NT + t) * B + b] * hp[((int64_t)q * M + m) * B + b];
+        const int j = m * nw + q * (nw - 1);
+        for (int b = 0; b < B; ++b) acc += W[((int64_t)j * NT + t) * B + b] * hp[((int64_t)q * M + m) * B + b];
         z[q * M + m] = acc;
       }
     for (int o = 0; o < NP; ++o) {

@@ -166,7 +166,9 @@ typedef struct or_presel {
   const double *h;                   /* complex [I][M][B], or [I][M][2][B] when n_pol = 2 */
   const double *pol;                 /* complex [I][M][2]: K_{i m +}, K_{i m x} (n_pol = 1) */
   const double *t_grid;              /* [D][n_t] arrival times at detector k (s) */
-  const double *rb_dh, *rb_hh;       /* relative binning as in or_problem, or NULL (n_pol = 1) */
+  const double *rb_dh, *rb_hh;       /* relative binning as in or_problem, or NULL: [D][J][B] and
+                                        [D][J][J][B] with J = M (mode bank) or 2M (n_pol = 2,
+                                        component j = 2m + p) */
   int n_pol;                         /* 2: polarisation-resolved bank, h_{i m p} read directly */
 } or_presel_problem;
 

@@ -66,15 +66,18 @@ static int run_rb_weights(void) {
   return rc;
 }
 
-static int run_presel(int n_pol) {
+static int run_presel(int n_pol, int with_rb) {
   const int I = 4, D = 2, M = 3, B = 20, NT = 5, NP = 6;
   int mode_m[3] = {1, 2, 4};
   double *f = arr(B, 20.0, 30.0), *w = arr(B, 1.0, 2.0), *psd = arr(D * B, 0.5, 2.0);
   for (int b = 1; b < B; ++b) f[b] = f[b - 1] + 12.0;
   double *data = arr(2 * D * B, -1.0, 1.0), *h = arr(2 * (size_t)I * M * 2 * B, -1.0, 1.0);
   double *pol = arr(2 * (size_t)I * M * 2, -1.0, 1.0), *tg = arr((size_t)D * NT, -0.01, 0.01);
+  const int J = M * (n_pol == 2 ? 2 : 1);
+  double *rbd = with_rb ? arr(2 * (size_t)D * J * B, -1.0, 1.0) : NULL;
+  double *rbh = with_rb ? arr(2 * (size_t)D * J * J * B, 0.1, 1.0) : NULL;
   or_presel_problem p = {I, D, M, B, NT, NP, mode_m, f, w, psd, data, h, n_pol == 2 ? NULL : pol, tg,
-                         NULL, NULL, n_pol};
+                         rbd, rbh, n_pol};
   double ml[4 * 2], inco[4], thr, g[6 * 5];
   int32_t arg[4 * 2 * 2];
   uint8_t keep[4];
@@ -82,7 +85,7 @@ static int run_presel(int n_pol) {
   int rc = or_presel_grid(&p, 1, 1, g);
   rc |= or_presel(&p, 20.0, 2, ml, arg, inco, keep, &thr, &arg_i);
   (void)or_quad_ml(1.0, 2.0, 1.0, 0.999, 1.0);
-  free(f); free(w); free(psd); free(data); free(h); free(pol); free(tg);
+  free(f); free(w); free(psd); free(data); free(h); free(pol); free(tg); free(rbd); free(rbh);
   return rc;
 }
 
@@ -98,8 +101,10 @@ int main(void) {
   rc |= run_problem(2, 0);
   rc |= run_problem(2, 1);
   rc |= run_rb_weights();
-  rc |= run_presel(1);
-  rc |= run_presel(2);
+  rc |= run_presel(1, 0);
+  rc |= run_presel(2, 0);
+  rc |= run_presel(1, 1);
+  rc |= run_presel(2, 1);
   rc |= or_default_threads() < 1;
   printf("oracle driver: rc=%d checksum=%.6g\n", rc, s);
   return rc != 0;

@@ -190,6 +190,32 @@ def test_polarisation_resolved_pipeline(rbp):
         assert np.max(np.abs(H - Ht)) <= 1e-10 * np.max(np.abs(Ht))
 
 
+def test_polarisation_resolved_preselection_uses_the_component_weights(rbp):
+    """Pre-selection of a precessing bank with the component weights, on the
+    reference row at the reference's arrival times: the fine-grid projection of
+    App. B onto the two real templates sum_m h_mp e^{i m phi_o} T_k, p = +, x."""
+    oracle, rw, (wdh, whh) = rbp
+    D = rw.psd_fine.shape[0]
+    hf = rw.rows_fine(0)[0]  # [M, 2, N]
+    M = hf.shape[0]
+    P = oracle.PreselProblem(rw.bank.f, rw.bank.w, rw.bank.mode_m, rw.bank.h, None, rw.event.psd,
+                             rw.event.data, rw.t0[:, None].copy(), n_phi=4, rb=(wdh, whh))
+    for k in range(D):
+        g = P.grid(0, k)
+        om = np.sqrt(4.0 * rw.dff / rw.psd_fine[k])
+        vd = np.concatenate([rw.data_fine[k].real * om, rw.data_fine[k].imag * om])
+        for o in range(4):
+            cols = []
+            for p in range(2):
+                tpl = sum(hf[m, p] * np.exp(1j * rw.bank.mode_m[m] * 2 * np.pi * o / 4) for m in range(M)) \
+                    * shift(rw, k)
+                cols.append(np.concatenate([tpl.real * om, tpl.imag * om]))
+            A = np.stack(cols, axis=1)
+            x, *_ = np.linalg.lstsq(A, vd, rcond=None)
+            res = vd - A @ x
+            assert g[o, 0] == pytest.approx(0.5 * (vd @ vd - res @ res), rel=1e-9)
+
+
 def test_fixed_inclination_components_reduce_to_mode_weights():
     """A reference whose polarisations are h0_mp = K_mp h0_m with constant K:
     the factor cancels in both ratios, so W_{k(m,p)b} = W_{kmb} and
