@@ -245,16 +245,19 @@ typedef struct dotpe_evidence_out {
  * the detector sum and the selection FP64.  A polarisation-resolved bank
  * (n_pol = 2) uses its own h_{imp} in place of K_{imp} h_{im} (App. B's
  * general form; pol is not needed): the tensor-core precisions as above, or
- * DOTPE_PREC_FP32 on the CUDA cores; relative binning returns
- * DOTPE_E_UNSUPPORTED for it.
+ * DOTPE_PREC_FP32 on the CUDA cores; with relative binning it runs in FP32
+ * only (other precisions return DOTPE_E_UNSUPPORTED), with the component
+ * weights rb_dh [n_det][2M][n_bins], rb_hh [n_det][2M][2M][n_bins] (j = 2m + p)
+ * and one time-grid operand per component.
  * Rows [i0, i1) of the bank.
  * psd [n_det][n_bins] (double) and data [n_det][n_bins] (complex): host or
  * device, as for events.  t_grid [n_det][n_t] (double, s; host or device):
  * the arrival times at each detector.  1 <= n_t <= 4096, 1 <= n_phi <= 32,
  * delta >= 0.  rb_dh / rb_hh as in dotpe_event_desc (relative binning, App. A;
  * the weights do not depend on the polarisation for a reference h0_{mp} =
- * K_{mp} h0_m, so the per-mode weights serve both polarisations); the time
- * grid operand is then one per mode.  Synchronous: returns when every output
+ * K_{mp} h0_m, so for a mode bank the per-mode weights serve both
+ * polarisations); the time grid operand is then one per mode (per component
+ * for a polarisation-resolved bank).  Synchronous: returns when every output
  * is written. */
 typedef struct dotpe_presel_desc {
   uint64_t bank_id;

@@ -1106,7 +1106,8 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   if (rb && !(d->rb_dh && d->rb_hh)) return fail(DOTPE_E_INVALID, "rb_dh and rb_hh go together");
   if ((!rb && (!d->psd || !d->data)) || !d->t_grid) return fail(DOTPE_E_INVALID, "null input array");
   const int prec = d->precision;
-  if (polb && rb) return fail(DOTPE_E_UNSUPPORTED, "pre-selection of a polarisation-resolved bank with relative binning");
+  if (polb && rb && prec != DOTPE_PREC_FP32)
+    return fail(DOTPE_E_UNSUPPORTED, "pre-selection of a polarisation-resolved bank with relative binning runs in FP32");
   // a polarisation-resolved bank also runs in FP32 (CUDA cores); the tensor-core precisions serve both
   const bool simt_pol = polb && prec == DOTPE_PREC_FP32;
   if (!simt_pol && prec != DOTPE_PREC_FP16 && prec != DOTPE_PREC_FP16X3 && prec != DOTPE_PREC_BF16 &&
@@ -1120,13 +1121,14 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   const int NTP = (NT + PS_TC - 1) / PS_TC * PS_TC;
   const bool bf = prec_bf16(prec), split = prec_split(prec);
   const int planes = split ? 2 : 1;
-  const int MG = rb ? M : 1;  // time-grid operands: one per mode with relative binning
+  const int J = M * (polb ? 2 : 1);  // data-weight components: (mode, polarisation) pairs j = 2m + p
+  const int MG = rb ? J : 1;          // time-grid operands: one per component with relative binning
   cudaStream_t st = ctx->main_stream;
 
   // cross-term records: the bank's cache entry for this PSD, a new one when the
   // slice is a large part of the bank, else the slice's own
   uint64_t key = 0;
-  int rc = rb ? psd_hash(D, B, nullptr, &key, d->rb_hh, (size_t)2 * D * M * M * B) : psd_hash(D, B, d->psd, &key);
+  int rc = rb ? psd_hash(D, B, nullptr, &key, d->rb_hh, (size_t)2 * D * J * J * B) : psd_hash(D, B, d->psd, &key);
   if (rc != DOTPE_OK) return rc;
   XEntry *x = xcache_find(b, key, D);
   const bool build_cache = !x && 4 * NI >= b.I;
@@ -1135,8 +1137,8 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   Carver c;
   const size_t o_psd = c.take<double>((size_t)D * B), o_data = c.take<double2>((size_t)D * B);
   const size_t o_tg = c.take<double>((size_t)D * NT);
-  const size_t o_rbd = c.take<double2>(rb ? (size_t)D * M * B : 0), o_rbh = c.take<double2>(rb ? (size_t)D * M * M * B : 0);
-  const size_t o_c = c.take<float2>((size_t)D * M * B), o_om = c.take<float>((size_t)D * B);
+  const size_t o_rbd = c.take<double2>(rb ? (size_t)D * J * B : 0), o_rbh = c.take<double2>(rb ? (size_t)D * J * J * B : 0);
+  const size_t o_c = c.take<float2>((size_t)D * J * B), o_om = c.take<float>((size_t)D * B);
   const size_t o_fh = c.take<float>(B), o_fl = c.take<float>(B);
   const size_t o_G = c.take<float2>((size_t)MG * D * NTP * B);
   const size_t o_gmax = c.take<float>(1), o_gs = c.take<float>(1);
@@ -1178,15 +1180,15 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   if (d->psd) ck(cudaMemcpyAsync(scr + o_psd, d->psd, (size_t)D * B * 8, cudaMemcpyDefault, st), "copying psd");
   if (d->data) ck(cudaMemcpyAsync(scr + o_data, d->data, (size_t)D * B * 16, cudaMemcpyDefault, st), "copying data");
   if (rb) {
-    ck(cudaMemcpyAsync(scr + o_rbd, d->rb_dh, (size_t)D * M * B * 16, cudaMemcpyDefault, st), "copying rb_dh");
-    ck(cudaMemcpyAsync(scr + o_rbh, d->rb_hh, (size_t)D * M * M * B * 16, cudaMemcpyDefault, st), "copying rb_hh");
+    ck(cudaMemcpyAsync(scr + o_rbd, d->rb_dh, (size_t)D * J * B * 16, cudaMemcpyDefault, st), "copying rb_dh");
+    ck(cudaMemcpyAsync(scr + o_rbh, d->rb_hh, (size_t)D * J * J * B * 16, cudaMemcpyDefault, st), "copying rb_hh");
   }
   ck(cudaMemcpyAsync(scr + o_tg, d->t_grid, (size_t)D * NT * 8, cudaMemcpyDefault, st), "copying t_grid");
   if (rc != DOTPE_OK) return finish(rc);
 
   PreselPrepArgs pa;
   memset(&pa, 0, sizeof(pa));
-  pa.D = D; pa.B = B; pa.M = M; pa.Kpad = b.Kpad; pa.n_t = NT; pa.n_tpad = NTP;
+  pa.D = D; pa.B = B; pa.M = rb ? J : M; pa.Kpad = b.Kpad; pa.n_t = NT; pa.n_tpad = NTP;
   pa.rb_dh = rb ? (const double2 *)(scr + o_rbd) : nullptr;
   const double2 *rb_hh = rb ? (const double2 *)(scr + o_rbh) : nullptr;
   pa.f = b.f; pa.w = b.w; pa.psd = (const double *)(scr + o_psd); pa.data = (const double2 *)(scr + o_data);
@@ -1209,7 +1211,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     if ((rc = xcache_build(ctx, b, key, D, pa.omega, rb_hh, st, &x)) != DOTPE_OK) return finish(rc);
     mx = x->mx + (size_t)d->i0 * D * rec;
   } else if (polb) {
-    launch_cross_terms_pol(NI, d->i0, b.I, M, D, B, b.Kpad, b.mode_m, b.master, pa.omega, nullptr,
+    launch_cross_terms_pol(NI, d->i0, b.I, M, D, B, b.Kpad, b.mode_m, b.master, pa.omega, rb_hh,
                            (float *)(scr + o_mx), ctx->n_sms, st);
     mx = (const float *)(scr + o_mx);
   } else {
@@ -1278,6 +1280,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
       for (int m = 0; m < MAXM; ++m) pp.mode_m[m] = m < M ? b.mode_m[m] : 0;
       pp.master = b.master;
       pp.G = pa.G32;
+      pp.n_gcomp = MG;
       pp.mx = mx;
       pp.rank_tol = PS_RANK_TOL;
       pp.keys = P.keys;

@@ -15,7 +15,9 @@
 // One block per (RPB rows, detector), one thread per time slot (time chunks of
 // PP_NT): the rows' components stream through shared memory in bin chunks and
 // each thread accumulates the RPB x M x 2 complex Z of its time; the time-grid
-// operand is the pre-selection's FP32 G [D][n_tpad][B].
+// operand is the pre-selection's FP32 G [D][n_tpad][B], or with relative
+// binning (App. A) one per (mode, polarisation) component j = 2m + p,
+// G [2M][D][n_tpad][B] from the component weights W^{<d|h>}_{k j b}.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -27,6 +29,7 @@ constexpr int PP_RPB = 4;    // bank rows per block
 constexpr int PP_BCH = 64;   // bins per shared-memory chunk
 }  // namespace
 
+template <bool RB>
 __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a) {
   __shared__ float2 hs[PP_RPB][MAXM][2][PP_BCH];
   __shared__ float4 tab[PP_RPB][PS_MAXPHI];    // (a, 2b, c): ln L^ML = a dp^2 + 2b dp dx + c dx^2
@@ -81,6 +84,7 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
 #pragma unroll
         for (int p = 0; p < 2; ++p) { zr[r][m][p] = 0.f; zi[r][m][p] = 0.f; }
     const float2 *g = a.G + ((int64_t)k * a.n_tpad + (tv ? t : 0)) * B;
+    const int64_t gstride = (int64_t)D * a.n_tpad * B;  // between components (relative binning)
     for (int b0 = 0; b0 < B; b0 += PP_BCH) {
       __syncthreads();  // the previous chunk is consumed (and, first time, the tables are written)
       for (int q = tid; q < PP_RPB * MAXM * 2 * PP_BCH; q += PP_NT) {
@@ -97,16 +101,27 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
       if (tv) {
         const int nb = min(PP_BCH, B - b0);
         for (int bb = 0; bb < nb; ++bb) {
-          const float2 gv = __ldg(g + b0 + bb);
+          float2 gv[MAXM][2];
+          if constexpr (RB) {
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m)
+#pragma unroll
+              for (int p = 0; p < 2; ++p)
+                gv[m][p] = m < M ? __ldg(g + (2 * m + p) * gstride + b0 + bb) : make_float2(0.f, 0.f);
+          } else {
+            const float2 g0 = __ldg(g + b0 + bb);
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) gv[m][0] = gv[m][1] = g0;
+          }
 #pragma unroll
           for (int r = 0; r < PP_RPB; ++r)
 #pragma unroll
             for (int m = 0; m < MAXM; ++m)
 #pragma unroll
               for (int p = 0; p < 2; ++p) {
-                const float2 h = hs[r][m][p][bb];
-                zr[r][m][p] = fmaf(gv.x, h.x, fmaf(-gv.y, h.y, zr[r][m][p]));
-                zi[r][m][p] = fmaf(gv.x, h.y, fmaf(gv.y, h.x, zi[r][m][p]));
+                const float2 h = hs[r][m][p][bb], gq = gv[m][p];
+                zr[r][m][p] = fmaf(gq.x, h.x, fmaf(-gq.y, h.y, zr[r][m][p]));
+                zi[r][m][p] = fmaf(gq.x, h.y, fmaf(gq.y, h.x, zi[r][m][p]));
               }
         }
       }
@@ -147,7 +162,10 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
 
 void launch_presel_pol(const PreselPolArgs &a, cudaStream_t st) {
   const dim3 grid((unsigned)((a.n_rows + PP_RPB - 1) / PP_RPB), (unsigned)a.n_det);
-  presel_pol_kernel<<<grid, PP_NT, 0, st>>>(a);
+  if (a.n_gcomp > 1)
+    presel_pol_kernel<true><<<grid, PP_NT, 0, st>>>(a);
+  else
+    presel_pol_kernel<false><<<grid, PP_NT, 0, st>>>(a);
 }
 
 }  // namespace dotpe

@@ -210,8 +210,9 @@ struct PreselPrepArgs {
   const double *f, *w, *psd;
   const double2 *data;
   const double *t_grid;  // [D][n_t]
-  const double2 *rb_dh;  // relative binning (App. A) or null: then G is per mode
-  float2 *c;             // [D][M][B] data weights of each mode
+  const double2 *rb_dh;  // relative binning (App. A) or null: then G is per weight component
+  float2 *c;             // [D][M][B] data weights of each component (M: modes, or the 2 n_modes
+                         // (mode, polarisation) components of a polarisation-resolved bank with rb_dh)
   float *omega, *fh, *fl;
   float2 *G32;           // [1 or M][D n_tpad][B] c_{kmb} e^{-2 pi i f_b t_{kt}} (0 on padding columns)
   float *gmax;           // 1 float, zeroed
@@ -263,7 +264,8 @@ struct PreselPolArgs {
   int n_det, n_t, n_tpad, n_phi, n_modes, n_bins, kpad;
   int mode_m[MAXM];
   const float *master;       // FP32 master [M][bank_rows][kpad], rows [Re h+ | Im h+ | Re hx | Im hx | 0]
-  const float2 *G;           // [n_det][n_tpad][n_bins] time-grid operand c_kb e^{-2 pi i f_b t_kt}
+  const float2 *G;           // [n_gcomp][n_det][n_tpad][n_bins] time-grid operand c_kjb e^{-2 pi i f_b t_kt}
+  int n_gcomp;               // 1 (one operand for every component), or 2 n_modes with relative binning (j = 2m + p)
   const float *mx;           // [n_rows][n_det][REC_P] overlap records (slice-relative)
   float rank_tol;
   unsigned long long *keys;  // [n_rows][n_det] out, zeroed

@@ -168,6 +168,54 @@ def test_component_weights_kernel_matches_oracle(dpx, rbp):
     assert np.max(np.abs(ghh - whh)) <= 1e-11 * np.max(np.abs(whh))
 
 
+def test_precessing_preselection_with_component_weights(dpx, rbp):
+    """Pre-selection of the 520-row precessing bank with the component weights
+    (one FP32 time-grid operand per (mode, polarisation) component, 150 times:
+    two passes of the kernel's 128 time slots) against the oracle with the same
+    weights: the split bound 2e-3 + 1e-4 ln L^ML per (row, detector), the
+    incoherent sums within the detectors' bounds, the kept set away from the
+    threshold, the (o, t) within the bound; a slice (its own records) equals
+    the whole-bank call (the cached records) bit for bit."""
+    dp, ctx = dpx
+    rw, (wdh, whh) = rbp
+    import oracle
+    I, D = rw.bank.h.shape[0], rw.psd_fine.shape[0]
+    t_grid = rw.t0[:, None] + (np.arange(150) - 75)[None, :] * 2.5e-4
+    P = oracle.PreselProblem(rw.bank.f, rw.bank.w, rw.bank.mode_m, rw.bank.h, None, rw.event.psd, rw.event.data,
+                             t_grid, n_phi=32, rb=(wdh, whh))
+    ref = P.run(delta=20.0)
+    bid = dp.dotpe_bank_load(ctx, rw.bank.h, rw.bank.f, rw.bank.w, rw.bank.mode_m, rw.bank.ln_w)
+    try:
+        part = dp.dotpe_preselect(ctx, bid, 100, 200, None, None, t_grid, n_phi=32, delta=20.0, precision="fp32",
+                                  rb=(wdh, whh))
+        r = dp.dotpe_preselect(ctx, bid, 0, I, None, None, t_grid, n_phi=32, delta=20.0, precision="fp32",
+                               rb=(wdh, whh))
+        with pytest.raises(dp.DotpeError) as ei:
+            dp.dotpe_preselect(ctx, bid, 0, I, None, None, t_grid, n_phi=32, delta=20.0, precision="bf16x3",
+                               rb=(wdh, whh))
+        assert ei.value.status == dp.DOTPE_E_UNSUPPORTED
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    assert r["device_status"] == 0
+    tol = 2e-3 + 1e-4 * np.abs(ref["ml"])
+    d = np.abs(r["lnl_ml"] - ref["ml"])
+    print(f"rb presel precessing fp32: max |d ln L^ML_ik| {d.max():.3e} (up to {ref['ml'].max():.1f})")
+    assert np.all(d <= tol), float(d.max())
+    tol_i = tol.sum(axis=1)
+    assert np.all(np.abs(r["lnl_inco"] - ref["lnl_inco"]) <= tol_i)
+    keep_gpu = np.zeros(I, bool)
+    keep_gpu[r["selected"]] = True
+    clear = np.abs(ref["lnl_inco"] - ref["threshold"]) > 2 * tol_i.max()
+    np.testing.assert_array_equal(keep_gpu[clear], ref["keep"][clear])
+    for i in (0, 259, I - 1, int(r["arg_i"])):
+        for k in range(D):
+            g = P.grid(i, k)
+            o, t = r["arg_ot"][i, k]
+            assert g[o, t] >= g.max() - 2 * tol[i, k]
+    np.testing.assert_array_equal(part["lnl_ml"], r["lnl_ml"][100:200])
+    np.testing.assert_array_equal(part["arg_ot"], r["arg_ot"][100:200])
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16x3", "mixed"])
 def test_precessing_event_with_component_weights(dpx, rbp, precision):
     """A polarisation-resolved event with relative binning against the
