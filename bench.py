@@ -363,7 +363,7 @@ def bench_batch64(args, dp, ctx_factory, torch, dev, load_peaks_fn):
     return line
 
 
-def presel_cpu_baseline(wl, ps, target_s=12.0):
+def presel_cpu_baseline(wl, ps, target_s=12.0, rb=None):
     """The FP64 oracle's pre-selection on a bounded random sample of the bank's
     rows (every detector, time and phase of each sampled row), all host cores."""
     import oracle
@@ -375,7 +375,7 @@ def presel_cpu_baseline(wl, ps, target_s=12.0):
         rows = np.sort(rng.choice(I, size=n, replace=False))
         P = oracle.PreselProblem(wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.h[rows],
                                  None if ps.pol is None else ps.pol[rows],
-                                 wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI)
+                                 wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI, rb=rb)
         t0 = time.perf_counter()
         P.run(n_threads=cores)
         return time.perf_counter() - t0
@@ -386,7 +386,8 @@ def presel_cpu_baseline(wl, ps, target_s=12.0):
     dt = run(n)
     return {"value": n / dt, "unit": "bank rows/s", "cores": cores, "kind": "oracle",
             "sample": f"{n} uniform random bank rows (seed 2468), all 3 detectors x 128 times x "
-                      f"{N_PHI} phases each, Eqs. dh_itop / single_det_ML in FP64, {dt:.1f} s"}
+                      f"{N_PHI} phases each, Eqs. dh_itop / single_det_ML in FP64"
+                      + (" with the relative-binning weights" if rb is not None else "") + f", {dt:.1f} s"}
 
 
 def bench_presel(args, dp, ctx_factory, torch, dev):
@@ -395,7 +396,17 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
     import synth
     I, D, M, B = args.n_int, WORKLOAD["n_det"], WORKLOAD["n_modes"], WORKLOAD["n_bins"]
     pres = args.precessing  # a polarisation-resolved bank: its own h_imp, the FP32 kernel
-    if pres:
+    rbw = None
+    if args.with_rb:
+        # relative binning (App. A): the bank on the 378 nodes, weights from the
+        # full-resolution data (per mode, or per (mode, polarisation) component)
+        B = 378
+        wl = synth.make_rb_workload(n_int=I, n_ext=4, n_det=D, n_modes=M, n_bins=B, n_fine=131072, snr=15.0,
+                                    seed=6, n_phi=N_PHI, precessing=pres)
+        t = wl.t0[:, None] + (np.arange(128) - 64)[None, :] * 5.0e-4
+        pol = None if pres else synth.row_polarisation_factors(wl.bank, np.random.default_rng(8).uniform(-1, 1, I))
+        ps = synth.PreselInputs(pol=pol, cos_iota=None, t_grid=t)
+    elif pres:
         wl = synth.make_precessing_workload(I, 4, D, M, B, snr=WORKLOAD["snr"], seed=9, n_phi=N_PHI)
         t = (np.arange(128) - 64) * 5.0e-4
         ps = synth.PreselInputs(pol=None, cos_iota=None, t_grid=np.tile(t, (D, 1)))
@@ -404,13 +415,18 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
         ps = synth.make_presel_inputs(wl)
     NT = ps.t_grid.shape[1]
     prec = args.precision if args.precision != "mixed" else "fp16x3"
+    if pres and args.with_rb and "--precision" not in sys.argv:
+        prec = "fp32"  # the only precision of a polarisation-resolved bank with relative binning
     simt = prec == "fp32"  # the FP32 kernel (polarisation-resolved banks only)
     ctx = ctx_factory()
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w, pol=ps.pol)
+    if args.with_rb:
+        rbw = dp.dotpe_rb_weights(ctx, wl.f_fine, wl.dff, wl.psd_fine, wl.data_fine, wl.h0_fine, wl.nodes, wl.t0)
 
     def call():
-        return dp.dotpe_preselect(ctx, bid, 0, I, wl.event.psd, wl.event.data, ps.t_grid, n_phi=N_PHI,
-                                  delta=CUT_DELTA, precision=prec, outputs=("lnl_inco", "selected"))
+        return dp.dotpe_preselect(ctx, bid, 0, I, None if rbw else wl.event.psd, None if rbw else wl.event.data,
+                                  ps.t_grid, n_phi=N_PHI, delta=CUT_DELTA, precision=prec,
+                                  outputs=("lnl_inco", "selected"), rb=rbw)
 
     for _ in range(args.warmup):
         call()
@@ -435,7 +451,7 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
     peak = FP32_SIMT_PEAK_TFLOPS if simt else sustained
     evals = I * D * NT * N_PHI
     dms = sum(dev_ms)
-    cpu = None if args.no_cpu_baseline else presel_cpu_baseline(wl, ps)
+    cpu = None if args.no_cpu_baseline else presel_cpu_baseline(wl, ps, rb=rbw)
     line = {
         "metric": "pre-selected bank rows/s", "value": I * args.steps / (dms * 1e-3), "unit": "rows/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dms / args.steps,
@@ -444,7 +460,9 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
         "config": {"workload": f"incoherent pre-selection of one event: I={I} "
                                + ("polarisation-resolved (precessing) " if pres else "")
                                + f"bank rows, D={D}, M={M}, B={B}, "
-                               f"N_t={NT} (0.5 ms grid), N_phi={N_PHI}, window {CUT_DELTA:g}",
+                               f"N_t={NT} (0.5 ms grid), N_phi={N_PHI}, window {CUT_DELTA:g}"
+                               + (", relative binning (one time-grid operand per weight component)"
+                                  if rbw else ""),
                    "precision": prec,
                    "l2": (f"inputs larger than L2 (FP32 bank {I * M * 4 * B * 4 / 1e9:.2f} GB per call)" if simt else
                           f"inputs larger than L2 (bank operand planes "
@@ -462,7 +480,8 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
                      "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if simt
                                      else f"{peak_src} bf16_tflops_sustained")},
         "e2e": {"value": I * args.steps / wall, "unit": "rows/s",
-                "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + ps.t_grid.nbytes),
+                "h2d_bytes_per_step": int((rbw[0].nbytes + rbw[1].nbytes) if rbw else
+                                          (wl.event.psd.nbytes + wl.event.data.nbytes)) + int(ps.t_grid.nbytes),
                 "d2h_bytes_per_step": int(8 * I + 8 * r["n_selected"] + 64)},
         "gpu_launches": 6 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
     }
@@ -981,6 +1000,8 @@ def main():
     ap.add_argument("--precessing", action="store_true",
                     help="rb, presel: a polarisation-resolved bank (rb: weights per (mode, polarisation) "
                          "component; presel: the FP32 kernel)")
+    ap.add_argument("--with-rb", action="store_true",
+                    help="presel: relative binning (weights from dotpe_rb_weights; with --precessing, FP32 only)")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
     args = ap.parse_args()
     if args.workload == "serve" and "--events" not in sys.argv:
