@@ -1146,6 +1146,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   // operand rows per plane: (column, re/im) per mode group, or (column, polarisation, re/im)
   const int64_t g_rows = polb ? (int64_t)4 * D * NTP : (int64_t)MG * 2 * D * NTP;
   const size_t o_Gp = c.take<float2>((polb && !simt_pol) ? (size_t)4 * D * NTP * B : 0);
+  const size_t o_GT = c.take<float2>(simt_pol ? (size_t)MG * D * NTP * B : 0);  // the FP32 kernel's layout
   const size_t o_pack = c.take<uint16_t>(simt_pol ? 0 : (size_t)planes * g_rows * b.Kpad);
   const size_t o_mx = own_mx ? c.take<float>((size_t)NI * D * rec) : 0;
   const size_t o_keys = c.take<unsigned long long>((size_t)NI * D);
@@ -1199,6 +1200,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
   pa.gpack = scr + o_pack; pa.pack_kind = polb ? 0 : (bf ? 1 : 2); pa.pack_planes = planes;
   pa.gscale = (float *)(scr + o_gs); pa.status = status;
   launch_presel_prep(pa, st);
+  if (simt_pol) launch_transpose_G((int64_t)MG * D, NTP, B, pa.G32, (float2 *)(scr + o_GT), st);
   if (polb && !simt_pol)
     launch_presel_pol_pack((int64_t)D * NTP, B, b.Kpad, pa.G32, (float2 *)(scr + o_Gp), pa.gmax, bf ? 1 : 2, planes,
                            pa.gpack, pa.gscale, st);
@@ -1279,7 +1281,7 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
       pp.kpad = b.Kpad;
       for (int m = 0; m < MAXM; ++m) pp.mode_m[m] = m < M ? b.mode_m[m] : 0;
       pp.master = b.master;
-      pp.G = pa.G32;
+      pp.G = (const float2 *)(scr + o_GT);
       pp.n_gcomp = MG;
       pp.mx = mx;
       pp.rank_tol = PS_RANK_TOL;

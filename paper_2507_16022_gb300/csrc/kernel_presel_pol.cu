@@ -15,9 +15,10 @@
 // One block per (RPB rows, detector), one thread per time slot (time chunks of
 // PP_NT): the rows' components stream through shared memory in bin chunks and
 // each thread accumulates the RPB x M x 2 complex Z of its time; the time-grid
-// operand is the pre-selection's FP32 G [D][n_tpad][B], or with relative
-// binning (App. A) one per (mode, polarisation) component j = 2m + p,
-// G [2M][D][n_tpad][B] from the component weights W^{<d|h>}_{k j b}.
+// operand is the pre-selection's FP32 G, transposed to [D][B][n_tpad] (times
+// innermost: a warp's loads are coalesced), or with relative binning (App. A)
+// one per (mode, polarisation) component j = 2m + p, [2M][D][B][n_tpad], from
+// the component weights W^{<d|h>}_{k j b}.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -83,8 +84,9 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
       for (int m = 0; m < MAXM; ++m)
 #pragma unroll
         for (int p = 0; p < 2; ++p) { zr[r][m][p] = 0.f; zi[r][m][p] = 0.f; }
-    const float2 *g = a.G + ((int64_t)k * a.n_tpad + (tv ? t : 0)) * B;
-    const int64_t gstride = (int64_t)D * a.n_tpad * B;  // between components (relative binning)
+    const int64_t TP = a.n_tpad;
+    const float2 *g = a.G + (int64_t)k * B * TP + (tv ? t : 0);
+    const int64_t gstride = (int64_t)D * B * TP;  // between components (relative binning)
     for (int b0 = 0; b0 < B; b0 += PP_BCH) {
       __syncthreads();  // the previous chunk is consumed (and, first time, the tables are written)
       for (int q = tid; q < PP_RPB * MAXM * 2 * PP_BCH; q += PP_NT) {
@@ -107,9 +109,9 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
             for (int m = 0; m < MAXM; ++m)
 #pragma unroll
               for (int p = 0; p < 2; ++p)
-                gv[m][p] = m < M ? __ldg(g + (2 * m + p) * gstride + b0 + bb) : make_float2(0.f, 0.f);
+                gv[m][p] = m < M ? __ldg(g + (2 * m + p) * gstride + (b0 + bb) * TP) : make_float2(0.f, 0.f);
           } else {
-            const float2 g0 = __ldg(g + b0 + bb);
+            const float2 g0 = __ldg(g + (b0 + bb) * TP);
 #pragma unroll
             for (int m = 0; m < MAXM; ++m) gv[m][0] = gv[m][1] = g0;
           }

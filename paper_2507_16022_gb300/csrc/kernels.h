@@ -264,7 +264,8 @@ struct PreselPolArgs {
   int n_det, n_t, n_tpad, n_phi, n_modes, n_bins, kpad;
   int mode_m[MAXM];
   const float *master;       // FP32 master [M][bank_rows][kpad], rows [Re h+ | Im h+ | Re hx | Im hx | 0]
-  const float2 *G;           // [n_gcomp][n_det][n_tpad][n_bins] time-grid operand c_kjb e^{-2 pi i f_b t_kt}
+  const float2 *G;           // [n_gcomp][n_det][n_bins][n_tpad] time-grid operand c_kjb e^{-2 pi i f_b t_kt},
+                             // times innermost so that a warp's threads (times) read consecutive words
   int n_gcomp;               // 1 (one operand for every component), or 2 n_modes with relative binning (j = 2m + p)
   const float *mx;           // [n_rows][n_det][REC_P] overlap records (slice-relative)
   float rank_tol;
@@ -275,6 +276,8 @@ void launch_presel_pol(const PreselPolArgs &a, cudaStream_t st);
 // bank: rows 4c + 2p + part (c = detector-time column), polarisation block p of
 // [Re | Im | Re | Im] along K holding the column's real-ified G, the other zero.
 // Gp: [2][2 n_cols][B] FP32 scratch; G32 [n_cols][B]; out and scale as launch_prep's pack.
+// GT [n_mat][B][T] = G [n_mat][T][B] transposed (the FP32 kernel's operand layout).
+void launch_transpose_G(int64_t n_mat, int T, int B, const float2 *G, float2 *GT, cudaStream_t st);
 void launch_presel_pol_pack(int64_t n_cols, int B, int Kpad, const float2 *G32, float2 *Gp, const float *gmax,
                             int kind, int planes, void *out, float *scale_out, cudaStream_t st);
 

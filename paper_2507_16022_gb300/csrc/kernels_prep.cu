@@ -712,6 +712,23 @@ void launch_presel_prep(const PreselPrepArgs &a, cudaStream_t st) {
                                                          a.gpack, a.gscale);
 }
 
+// GT[mat][b][t] = G[mat][t][b]: one thread per output element, t fastest, so
+// the writes are coalesced (the operand is a few MB: the strided reads stay in L2).
+__global__ void transpose_G_kernel(int64_t n_mat, int T, int B, const float2 *__restrict__ G,
+                                   float2 *__restrict__ GT) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n_mat * B * T) return;
+  const int t = (int)(k % T);
+  const int64_t mb = k / T;
+  const int b = (int)(mb % B);
+  const int64_t mat = mb / B;
+  GT[k] = G[(mat * T + t) * B + b];
+}
+
+void launch_transpose_G(int64_t n_mat, int T, int B, const float2 *G, float2 *GT, cudaStream_t st) {
+  transpose_G_kernel<<<nblk(n_mat * B * T, 256), 256, 0, st>>>(n_mat, T, B, G, GT);
+}
+
 // Gp[q][2c + p][b] = G32[c][b] if q == p, else 0: the polarisation-resolved
 // pre-selection's operand rows before packing (one row per (column, polarisation)).
 __global__ void presel_pol_spread_kernel(int64_t n_cols, int B, const float2 *__restrict__ G32,
