@@ -470,7 +470,10 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
                    "evaluations_per_s": evals * args.steps / (dms * 1e-3), "kept_rows": r["n_selected"],
                    "kernel_ms": kern, "device_ms_per_call": dms / args.steps},
         "roofline": {"bound": "alu" if simt else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     # DRAM bytes per launch from an ncu capture of the same kernel at 16,384 rows,
+                     # scaled by rows (every row is read once per detector)
+                     "traffic": (1.299212e9 / 16384 * I) if (simt and rbw is not None) else None,
                      "kernel": ("presel_pol_kernel (FP32 per-component <d|h> against the time grid + 2x2 ML)"
                                 if simt else
                                 "presel_kernel" + ("<VAR = 2> (per-component" if pres else " (per-mode")
