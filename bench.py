@@ -74,6 +74,21 @@ CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
 DRAM_BYTES_PER_PAIR = {"mixed": (308.76e6 + 14.37e6) / (16384 * 2048)}  # screening launch
 
 
+# DRAM bytes (read + write) per launch of the FP32 relative-binning pre-selection
+# of a polarisation-resolved bank (presel_pol_kernel<true>), from one ncu capture:
+# the build it was taken on, its shape and rows.  None = no capture of the current
+# kernel (the figure goes stale with any change to the kernel or its grid).
+PRESEL_TRAFFIC = {"bytes": None, "rows": 16384, "D": 3, "N_t": 128, "B": 378, "source": None}
+
+
+def presel_traffic(simt, rb, D, NT, B, I):
+    """Per-launch DRAM traffic scaled by rows from the capture, when the shape matches."""
+    t = PRESEL_TRAFFIC
+    if not (simt and rb) or t["bytes"] is None or (D, NT, B) != (t["D"], t["N_t"], t["B"]):
+        return None
+    return t["bytes"] / t["rows"] * I
+
+
 def rank_seed(base, rank):
     """Each rank draws its own events (independent problems: no data exchange)."""
     return base + 1000 * rank
@@ -106,6 +121,86 @@ def load_peaks():
         d = json.load(open(p))
         return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), d.get("hbm_gbs"), "measured"
     return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+class NvmlClockSampler:
+    """SM clock, power and clock-event reasons read through NVML (libnvidia-ml,
+    by ctypes) every `period_s` in a thread during the timed region: reads
+    only, no setting is changed.  Raises OSError where NVML is absent."""
+
+    # nvmlClocksEventReasons bits
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x40: "sw_thermal_slowdown", 0x80: "hw_thermal_slowdown"}
+
+    def __init__(self, device_index, period_s=0.01):
+        import ctypes
+        self.ct = ctypes
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None:
+            raise OSError("libnvidia-ml not found")
+        self.lib = lib
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(self.h)) != 0:
+            raise OSError("nvmlDeviceGetHandleByIndex failed")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        self.period = period_s
+        self.samples = []
+        self.stop_flag = threading.Event()
+
+    def _one(self):
+        ct = self.ct
+        sm, smax, pw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        ok = (self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(sm)) == 0 and
+              self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(smax)) == 0)
+        if not ok:
+            return None
+        p = float(pw.value) / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(pw)) == 0 else None
+        r = int(rs.value) if self.reasons_fn(self.h, ct.byref(rs)) == 0 else 0
+        return float(sm.value), float(smax.value), p, r
+
+    def _loop(self):
+        while not self.stop_flag.is_set():
+            x = self._one()
+            if x is not None:
+                self.samples.append(x)
+            self.stop_flag.wait(self.period)
+
+    def start(self):
+        self.samples.clear()
+        self.stop_flag.clear()
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        self.t.join(timeout=2)
+        x = self._one()  # at least one sample, taken at the end of the region
+        if x is not None and not self.samples:
+            self.samples.append(x)
+        sm = [a for a, _, _, _ in self.samples]
+        reasons = sorted({nm for *_, r in self.samples for bit, nm in self.BITS.items() if r & bit})
+        power = [p for _, _, p, _ in self.samples if p is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(b for _, b, _, _ in self.samples) if self.samples else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "period_ms": self.period * 1e3, "source": "nvml",
+                "reasons": reasons}
+
+
+def make_clock_sampler(device_index):
+    """NVML sampling every 10 ms where the library is present, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(device_index)
+    except (OSError, AttributeError):
+        return ClockSampler(device_index)
 
 
 class ClockSampler:
@@ -294,7 +389,7 @@ def bench_batch64(args, dp, ctx_factory, torch, dev, load_peaks_fn):
     for _ in range(args.warmup):
         finish(batch(d_specs))
     S = torch.cuda.Stream(device=dev)
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     torch.cuda.synchronize()
     sampler.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -430,7 +525,7 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
 
     for _ in range(args.warmup):
         call()
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     torch.cuda.synchronize()
     sampler.start()
     dev_ms, ker_ms = [], []
@@ -448,7 +543,7 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
     kern = statistics.median(ker_ms)
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops / (kern * 1e-3) / 1e12
-    peak = FP32_SIMT_PEAK_TFLOPS if simt else sustained
+    peak = FP32_SIMT_PEAK_TFLOPS if simt else burst
     evals = I * D * NT * N_PHI
     dms = sum(dev_ms)
     cpu = None if args.no_cpu_baseline else presel_cpu_baseline(wl, ps, rb=rbw)
@@ -471,9 +566,11 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
                    "kernel_ms": kern, "device_ms_per_call": dms / args.steps},
         "roofline": {"bound": "alu" if simt else "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     # DRAM bytes per launch from an ncu capture of the same kernel at 16,384 rows,
-                     # scaled by rows (every row is read once per detector)
-                     "traffic": (1.299212e9 / 16384 * I) if (simt and rbw is not None) else None,
+                     # DRAM bytes per launch from an ncu capture of the same kernel build and shape
+                     # (D, N_t, B) at fewer rows, scaled by rows; null when none matches
+                     "traffic": presel_traffic(simt, rbw is not None, D, NT, B, I),
+                     "traffic_source": PRESEL_TRAFFIC.get("source") if presel_traffic(
+                         simt, rbw is not None, D, NT, B, I) is not None else None,
                      "kernel": ("presel_pol_kernel (FP32 per-component <d|h> against the time grid + 2x2 ML)"
                                 if simt else
                                 "presel_kernel" + ("<VAR = 2> (per-component" if pres else " (per-mode")
@@ -481,7 +578,7 @@ def bench_presel(args, dp, ctx_factory, torch, dev):
                      "kernel_ms": kern, "flops_per_call": flops,
                      "issued_tflops": achieved * (3 if prec.endswith("x3") else 1),
                      "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if simt
-                                     else f"{peak_src} bf16_tflops_sustained")},
+                                     else f"{peak_src} bf16_tflops (burst: the kernel is timed one call at a time)")},
         "e2e": {"value": I * args.steps / wall, "unit": "rows/s",
                 "h2d_bytes_per_step": int((rbw[0].nbytes + rbw[1].nbytes) if rbw else
                                           (wl.event.psd.nbytes + wl.event.data.nbytes)) + int(ps.t_grid.nbytes),
@@ -548,7 +645,7 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
         weights()
     w_ms = (time.perf_counter() - tw) * 1e3 / args.steps
     S = torch.cuda.Stream(device=dev)
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     torch.cuda.synchronize()
     sampler.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -618,12 +715,12 @@ def bench_rb(args, dp, ctx_factory, torch, dev):
                    "fp32_path_ms": ref_st["device_ms"],
                    "l2": f"inputs larger than L2 (bank operand planes {I * M * kpad * 2 * 2 / 1e9:.2f} GB, "
                          "re-read every step)"},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
-                     "frac": achieved / sustained, "traffic": None,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": burst, "unit": "TFLOP/s",
+                     "frac": achieved / burst, "traffic": None,
                      "kernel": ("tc_fused_kernel screening pass" if mixed else f"tc_fused_kernel {prec} pass")
                                + " with relative-binning weights", "kernel_ms": dom_ms,
                      "flops_per_pair": fpp,
-                     "peak_source": f"{peak_src} bf16_tflops_sustained"},
+                     "peak_source": f"{peak_src} bf16_tflops (burst: the kernel is timed one event at a time)"},
         "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(rw.f_fine.nbytes + rw.dff.nbytes + rw.psd_fine.nbytes + rw.data_fine.nbytes
                                           + rw.h0_fine.nbytes + rw.ext.t.nbytes + resp.nbytes + rw.ext.ln_w.nbytes),
@@ -685,7 +782,7 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     for _ in range(args.warmup):
         one()
     S = torch.cuda.Stream(device=dev)
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     torch.cuda.synchronize()
     sampler.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -722,7 +819,7 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
     achieved = flops_per_pair * pairs / (dom_ms * 1e-3) / 1e12
     fp32 = args.precision == "fp32"
     burst, sustained, hbm, peak_src = load_peaks()
-    peak = FP32_SIMT_PEAK_TFLOPS if fp32 else sustained
+    peak = FP32_SIMT_PEAK_TFLOPS if fp32 else burst
     n_tiles = -(-I // 128) * -(-E // 32)
     cpu = None
     if not args.no_cpu_baseline:
@@ -765,7 +862,7 @@ def bench_precessing(args, dp, ctx_factory, torch, dev):
                                 + " (<d|h> GEMM over both polarisations, K = 4B)"),
                      "kernel_ms": dom_ms, "flops_per_pair": flops_per_pair,
                      "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz" if fp32
-                                     else f"{peak_src} bf16_tflops_sustained")},
+                                     else f"{peak_src} bf16_tflops (burst: the kernel is timed one call at a time)")},
         "e2e": {"value": pairs / e2e_s, "unit": "pairs/s",
                 "h2d_bytes_per_step": int(wl.event.psd.nbytes + wl.event.data.nbytes + wl.ext.t.nbytes
                                           + wl.ext.F.nbytes + wl.ext.ln_w.nbytes),
@@ -808,7 +905,7 @@ def bench_pipeline(args, dp, ctx_factory, torch, dev):
 
     for _ in range(args.warmup):
         step()
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     sampler.start()
     t = time.perf_counter()
     kept = []
@@ -866,7 +963,7 @@ def bench_samples(args, dp, ctx_factory, torch, dev):
     t = time.perf_counter()
     dp.dotpe_posterior_samples(ctx, eid, uni[:ns])
     ns_ms = (time.perf_counter() - t) * 1e3
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     sampler.start()
     t = time.perf_counter()
     for _ in range(args.steps):
@@ -925,7 +1022,7 @@ def bench_serve(args, dp, ctx_factory, torch, dev):
                                     precision=args.precision)
         dp.dotpe_event_wait(ctx, eid, 600.0)
         dp.dotpe_event_release(ctx, eid)
-    sampler = ClockSampler(dev.index or 0)
+    sampler = make_clock_sampler(dev.index or 0)
     sampler.start()
     pending, lat, pairs, done_ns = {}, [], 0, []
     t_start = time.perf_counter()
@@ -1107,7 +1204,7 @@ def main():
         one(args.precision, k)
 
     S = torch.cuda.Stream(device=dev)
-    sampler = ClockSampler(local)
+    sampler = make_clock_sampler(local)
 
     def barrier():
         torch.cuda.synchronize()
@@ -1198,6 +1295,11 @@ def main():
         flops_issued += (8 * B * M * 3 + hh_flops) * pairs * refined / n_tiles
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops_alg / (dom_ms * 1e-3) / 1e12
+    # algorithmic bytes of the dominant launch: one read of the bank's operand plane
+    # (M x I rows of Kpad 16-bit values) and of the extrinsic operand plane (M x 2E rows)
+    kpad = -(-2 * B // 64) * 64
+    alg_bytes = float(M * (I + 2 * E) * kpad * 2)
+    traffic = DRAM_BYTES_PER_PAIR[args.precision] * pairs if args.precision in DRAM_BYTES_PER_PAIR else None
     # prep (data norm, bins, extrinsic, G build, G pack), fused (mixed: screen, 3 selection
     # kernels, 2 gated refinement variants), reduction (2 line, 2 pass, merge, final);
     # cross terms are computed once per (bank, PSD) and reused
@@ -1249,17 +1351,20 @@ def main():
         "roofline": {
             "bound": "tensor",
             "achieved": achieved,
-            "peak": sustained,
+            "peak": burst,
             "unit": "TFLOP/s",
-            "frac": achieved / sustained,
-            "traffic": (DRAM_BYTES_PER_PAIR[args.precision] * pairs if args.precision in DRAM_BYTES_PER_PAIR
-                        else None),
-            "traffic_note": "bytes per launch, scaled by pairs from an ncu capture at 16,384 x 2,048",
+            "frac": achieved / burst,
+            "traffic": traffic,
+            "algorithmic_bytes": alg_bytes,
+            "traffic_ratio": (traffic / alg_bytes) if traffic is not None else None,
+            "traffic_note": ("bytes per launch, scaled by pairs from an ncu capture at 16,384 x 2,048; "
+                             "algorithmic bytes = one read of the bank's fp16 operand plane and of the "
+                             "event's extrinsic operand plane"),
             "kernel": ("tc_fused_kernel screening pass (fp16 <d|h> GEMM + <h|h> + ML over the phase grid)"
                        if mixed else "tc_fused_kernel (fused <d|h> GEMM + marginalisation)"),
             "kernel_ms": dom_ms,
             "flops_per_pair": algorithmic_flops_per_pair(B, M, D),
-            "peak_source": f"{peak_src} bf16_tflops_sustained",
+            "peak_source": f"{peak_src} bf16_tflops (burst: the kernel is timed one event at a time)",
         },
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": d2h_bytes, "wall_s": e2e_wall},

@@ -487,16 +487,18 @@ int dotpe_dist_marg_eval(dotpe_ctx *ctx, int64_t n, const float *dh, const float
 
 /* Allocation-free variant of dotpe_dist_marg_eval (the paper has no
  * counterpart; this is a library service).  Some callers cannot allocate
- * device memory at the point where they call: code running while a stream
- * is being captured into a CUDA graph (cudaMalloc is not allowed then),
- * hosts that hand the whole device to their own allocator, and latency-bound
- * loops that must not pay for cudaMalloc/cudaFree.  This entry point calls no
+ * device memory at the point where they call: hosts that hand the whole
+ * device to their own allocator (a framework's caching allocator that has
+ * reserved all free memory, so a cudaMalloc of ours would fail or fragment
+ * it), and latency-bound loops that must not pay for cudaMalloc/cudaFree and
+ * the synchronisation cudaFree implies.  This entry point calls no
  * cudaMalloc, cudaFree or other allocating routine.  Its scratch for the
  * inputs and the output is a static device array of 3 x 2^20 floats (12 MiB)
  * that every GPU loading the library holds until the process exits; the
  * array's device address is looked up with cudaGetSymbolAddress on the
- * first call on each device, so make that first call before any stream
- * capture.  n must not exceed 2^20 (1,048,576): larger n is rejected with
+ * first call on each device (and again after the device's context has been
+ * replaced, e.g. by cudaDeviceReset), so make that first call before any
+ * stream capture.  n must not exceed 2^20 (1,048,576): larger n is rejected with
  * DOTPE_E_INVALID and a message.  dh, hh, out: host or device float arrays
  * of length n, as for dotpe_dist_marg_eval.  All calls share the one scratch
  * array and are serialised on the context's stream; calls that overlap on

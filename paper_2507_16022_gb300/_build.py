@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["dotpe.cu", "kernels_prep.cu", "kernel_simt.cu", "kernel_tc.cu", "kernel_tc1.cu", "kernel_reduce.cu", "kernel_rb.cu", "kernel_sample.cu",
-           "kernel_presel_pol.cu", "kernel_presel_v1.cu", "kernel_presel_v2.cu",
+           "kernel_presel_pol.cu", "kernel_presel_permode.cu", "kernel_presel_polres.cu",
            "kernel_presel.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

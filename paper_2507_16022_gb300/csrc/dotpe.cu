@@ -1757,9 +1757,10 @@ int dotpe_bank_load(dotpe_ctx *ctx, const dotpe_bank_desc *d, uint64_t *bank_id)
 // ---- bank files (checkpoint / resume) ----
 // Little-endian, host-native: the header, then the payload f [B], w [B],
 // ln w_int [I] (if present), the FP32 master [M][I][Kpad], the polarisation
-// factors [I][M][2] float2 (if present); FNV-1a 64 over the payload.  The
-// operand planes are rebuilt on open at the saved scale, so they equal the
-// saved bank's planes.
+// factors [I][M][2] float2 (if present); FNV-1a 64 over the header (its
+// checksum field zeroed) and then the payload, so a damaged mode number, scale
+// or polarisation count is refused like a damaged payload.  The operand planes
+// are rebuilt on open at the saved scale, so they equal the saved bank's planes.
 struct BankFileHeader {
   char magic[8];
   uint32_t version, n_pol;
@@ -1770,6 +1771,7 @@ struct BankFileHeader {
   uint64_t payload_bytes, checksum;
 };
 static const char BANK_MAGIC[8] = {'D', 'O', 'T', 'P', 'E', 'B', 'K', '1'};
+static const uint32_t BANK_VERSION = 2;  // 2: the checksum covers the header
 
 static uint64_t fnv1a(uint64_t h, const uint8_t *p, size_t n) {
   for (size_t k = 0; k < n; ++k) {
@@ -1777,6 +1779,11 @@ static uint64_t fnv1a(uint64_t h, const uint8_t *p, size_t n) {
     h *= 1099511628211ull;
   }
   return h;
+}
+static uint64_t header_hash(const BankFileHeader &h) {
+  BankFileHeader z = h;
+  z.checksum = 0;
+  return fnv1a(1469598103934665603ull, reinterpret_cast<const uint8_t *>(&z), sizeof(z));
 }
 
 // One allocation for a bank's arrays (the layout of dotpe_bank_load); pointers set, nothing copied.
@@ -1829,7 +1836,7 @@ int dotpe_bank_save(dotpe_ctx *ctx, uint64_t bank_id, const char *path) {
   BankFileHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, BANK_MAGIC, 8);
-  h.version = 1;
+  h.version = BANK_VERSION;
   h.n_pol = (uint32_t)b.n_pol;
   h.n_int = b.I;
   h.n_modes = b.M; h.n_bins = b.B; h.kpad = b.Kpad;
@@ -1841,7 +1848,7 @@ int dotpe_bank_save(dotpe_ctx *ctx, uint64_t bank_id, const char *path) {
   if (!fp) return fail(DOTPE_E_INVALID, "cannot open %s for writing", path);
   const size_t chunk = (size_t)64 << 20;
   std::vector<uint8_t> buf(chunk);
-  uint64_t sum = 1469598103934665603ull;
+  uint64_t sum = header_hash(h);
   bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
   for (const Part &p : parts)
     for (size_t o = 0; ok && o < p.n; o += chunk) {
@@ -1864,13 +1871,23 @@ int dotpe_bank_open(dotpe_ctx *ctx, const char *path, uint64_t *bank_id) {
   FILE *fp = fopen(path, "rb");
   if (!fp) return fail(DOTPE_E_INVALID, "cannot open %s", path);
   BankFileHeader h;
-  if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, BANK_MAGIC, 8) != 0 || h.version != 1) {
+  if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, BANK_MAGIC, 8) != 0 || h.version != BANK_VERSION) {
     fclose(fp);
     return fail(DOTPE_E_INVALID, "%s is not a bank file of this version", path);
   }
-  const int np = (h.n_pol == 2) ? 2 : 1;
-  const bool shape_ok = h.n_int >= 1 && h.n_modes >= 1 && h.n_modes <= MAXM && h.n_bins >= 2 &&
-                        h.kpad == (int)(((2 * np * (int64_t)h.n_bins + 63) / 64) * 64) && h.a_scale > 0.f;
+  // the ranges dotpe_bank_load accepts: n_pol 1 or 2, increasing mode numbers in 1..4
+  bool modes_ok = h.n_modes >= 1 && h.n_modes <= MAXM;
+  for (int m = 0; modes_ok && m < MAXM; ++m) {
+    if (m < h.n_modes)
+      modes_ok = h.mode_m[m] >= 1 && h.mode_m[m] <= 4 && (m == 0 || h.mode_m[m] > h.mode_m[m - 1]);
+    else
+      modes_ok = h.mode_m[m] == 0;
+  }
+  const int np = (int)h.n_pol;
+  const bool shape_ok = modes_ok && (h.n_pol == 1 || h.n_pol == 2) && (h.has_lw == 0 || h.has_lw == 1) &&
+                        (h.has_pol == 0 || h.has_pol == 1) && h.n_int >= 1 && h.n_bins >= 2 &&
+                        h.kpad == (int)(((2 * np * (int64_t)h.n_bins + 63) / 64) * 64) && h.a_scale > 0.f &&
+                        std::isfinite(h.a_scale);
   const size_t want = (size_t)h.n_bins * 16 + (h.has_lw ? (size_t)h.n_int * 8 : 0) +
                       (size_t)h.n_modes * h.n_int * h.kpad * 4 + (h.has_pol ? (size_t)h.n_int * h.n_modes * 16 : 0);
   if (!shape_ok || h.payload_bytes != want) {
@@ -1897,7 +1914,7 @@ int dotpe_bank_open(dotpe_ctx *ctx, const char *path, uint64_t *bank_id) {
                          {b->pol, b->pol ? (size_t)b->I * b->M * 16 : 0}};
   const size_t chunk = (size_t)64 << 20;
   std::vector<uint8_t> buf(chunk);
-  uint64_t sum = 1469598103934665603ull;
+  uint64_t sum = header_hash(h);
   bool ok = true;
   for (const Part &p : parts)
     for (size_t o = 0; ok && o < p.n; o += chunk) {

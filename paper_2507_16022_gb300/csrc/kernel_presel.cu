@@ -1,6 +1,6 @@
 // Pre-selection kernels' host side and the finish kernels; the tensor-core
 // kernel is in kernel_presel.cuh, instantiated here for the shared time-grid
-// operand (VAR 0) and in kernel_presel_v1.cu / kernel_presel_v2.cu for the
+// operand (VAR 0) and in kernel_presel_permode.cu / kernel_presel_polres.cu for the
 // per-mode (relative binning) and polarisation-resolved operands, so that the
 // three instantiation sets compile in parallel.
 #include "kernel_presel.cuh"

@@ -36,8 +36,10 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
   __shared__ float4 tab[PP_RPB][PS_MAXPHI];    // (a, 2b, c): ln L^ML = a dp^2 + 2b dp dx + c dx^2
   __shared__ float2 ph[PS_MAXPHI][MAXM];       // e^{i m phi_o}
   const int tid = threadIdx.x;
-  const int k = blockIdx.y;
-  const int64_t r0 = (int64_t)blockIdx.x * PP_RPB;
+  // the detector is the fastest block index: the D blocks of one row group run
+  // together and share the rows' FP32 components in L2
+  const int k = (int)(blockIdx.x % (unsigned)a.n_det);
+  const int64_t r0 = (int64_t)(blockIdx.x / (unsigned)a.n_det) * PP_RPB;
   const int M = a.n_modes, B = a.n_bins, D = a.n_det, np = a.n_phi;
   // phase factors (angles reduced in integers first)
   for (int q = tid; q < PS_MAXPHI * MAXM; q += PP_NT) {
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
 }
 
 void launch_presel_pol(const PreselPolArgs &a, cudaStream_t st) {
-  const dim3 grid((unsigned)((a.n_rows + PP_RPB - 1) / PP_RPB), (unsigned)a.n_det);
+  const dim3 grid((unsigned)(((a.n_rows + PP_RPB - 1) / PP_RPB) * a.n_det));
   if (a.n_gcomp > 1)
     presel_pol_kernel<true><<<grid, PP_NT, 0, st>>>(a);
   else

@@ -856,10 +856,37 @@ size_t dm_table_elems() { return (size_t)DM_NY * DM_NS; }
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) float g_dm_noalloc_scratch[3 * DM_NOALLOC_MAX];
 
+// Identity of the current CUDA context (0 if the driver cannot tell): the
+// scratch array's address belongs to a context, so a device reset, which tears
+// the primary context down, must lead to a fresh look-up.
+static unsigned long long current_ctx_id() {
+  typedef CUresult (*GetCurrent)(CUcontext *);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f2;
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
+
 int dist_marg_eval_noalloc(int device, int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab,
                            float *out, cudaStream_t st, char *msg, size_t msg_len) {
   static std::mutex mu;
   static float *addr[64] = {nullptr};
+  static unsigned long long addr_ctx[64] = {0};
   if (n < 0 || n > DM_NOALLOC_MAX) {
     snprintf(msg, msg_len, "n=%lld exceeds the allocation-free limit of %lld evaluations per call", (long long)n,
              (long long)DM_NOALLOC_MAX);
@@ -873,8 +900,10 @@ int dist_marg_eval_noalloc(int device, int64_t n, const float *dh, const float *
   float *base = nullptr;
   {
     std::lock_guard<std::mutex> lk(mu);
-    if (!addr[device]) {
-      // first use on this device (the caller has made `device` current)
+    // the caller has made `device` current; its context has been set up by the runtime
+    const unsigned long long cid = current_ctx_id();
+    if (!addr[device] || cid == 0 || cid != addr_ctx[device]) {
+      // first use on this device (or in a new context of it)
       void *p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_dm_noalloc_scratch);
       if (e != cudaSuccess || p == nullptr) {
@@ -882,6 +911,7 @@ int dist_marg_eval_noalloc(int device, int64_t n, const float *dh, const float *
         return DOTPE_E_DEVICE;
       }
       addr[device] = (float *)p;
+      addr_ctx[device] = cid;
     }
     base = addr[device];
   }

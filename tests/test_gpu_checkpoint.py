@@ -4,9 +4,13 @@
   per-pair values bit for bit (FP32, split fp16 and the pre-selection), for a
   mode bank with polarisation factors and ln w_int and for a
   polarisation-resolved bank.
-* A damaged file is refused: a flipped payload byte (checksum), a truncated
-  payload, a wrong magic, a missing file.
+* A damaged file is refused: a flipped payload byte (checksum), a flipped
+  header byte (a mode number, the operand scale, the polarisation count: the
+  checksum covers the header too, and the header's ranges are checked), a
+  truncated payload, a wrong magic, a missing file.
 """
+import struct
+
 import numpy as np
 import pytest
 
@@ -80,8 +84,21 @@ def test_damaged_files_are_refused(dpx, tmp_path):
     finally:
         dp.dotpe_bank_release(ctx, a)
     raw = bytearray(path.read_bytes())
+
+    def flip(off, mask):
+        return raw[:off] + bytes([raw[off] ^ mask]) + raw[off + 1:]
+
+    # header: magic[8], version, n_pol (u32), n_int (i64), n_modes, n_bins, kpad,
+    # has_lw, has_pol (i32), mode_m[4] (i32) at byte 44, a_scale (f32) at 60
+    assert struct.unpack_from("<i", raw, 44)[0] == int(wl.bank.mode_m[0]) == 2
     damaged = {
-        "flipped": raw[:-100] + bytes([raw[-100] ^ 0x10]) + raw[-99:],
+        "flipped": flip(len(raw) - 100, 0x10),
+        # m = 2 -> 1: still increasing and in 1..4, so only the checksum refuses it
+        "mode_m in range": flip(44, int(wl.bank.mode_m[0]) ^ 1),
+        "mode_m out of range": flip(44, 0x40),
+        "second mode_m": flip(48, 0x04),
+        "a_scale": flip(62, 0x01),
+        "n_pol": flip(12, 0x02),
         "truncated": raw[:-1000],
         "magic": b"XXXXXXXX" + raw[8:],
     }

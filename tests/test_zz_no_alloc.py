@@ -1,9 +1,9 @@
 """The allocation-free entry point dotpe_dist_marg_eval_noalloc.
 
-Callers that cannot allocate device memory when they call (for example while
-a stream is being captured into a CUDA graph, or inside a host application
-whose own allocator owns the device) use this variant: its scratch is a
-static device array instead of cudaMalloc'ed memory.  The test calls it
+Callers that cannot allocate device memory when they call (a host
+application whose own caching allocator has reserved the device's memory, or
+a latency-bound loop that must not pay for cudaMalloc/cudaFree) use this
+variant: its scratch is a static device array instead of cudaMalloc'ed memory.  The test calls it
 through the C ABI and checks it against the allocating dotpe_dist_marg_eval,
 on two calls in a row with different inputs (so that a stale scratch array
 would show), and checks that an oversized request is refused.  It creates
