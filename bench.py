@@ -1103,6 +1103,8 @@ def main():
     ap.add_argument("--with-rb", action="store_true",
                     help="presel: relative binning (weights from dotpe_rb_weights; with --precessing, FP32 only)")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
+    ap.add_argument("--narrow-tiles", action="store_true",
+                    help="screening and GEMM-only launches in 32-sample tiles (DOTPE_CONFIG_NARROW_TILES)")
     args = ap.parse_args()
     if args.workload == "serve" and "--events" not in sys.argv:
         args.events = 2000
@@ -1156,7 +1158,8 @@ def main():
     events = [wl.event] + [synth.make_event(rng, wl.bank, wl.ext, D, snr=kw["snr"], n_phi=N_PHI)
                            for _ in range(args.events - 1)]
 
-    ctx = dp.dotpe_create(local, flags=dp.DOTPE_CONFIG_AUTOTUNE if args.autotune else 0)
+    ctx = dp.dotpe_create(local, flags=(dp.DOTPE_CONFIG_AUTOTUNE if args.autotune else 0)
+                          | (dp.DOTPE_CONFIG_NARROW_TILES if args.narrow_tiles else 0))
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
     dev = torch.device("cuda", local)
 

@@ -97,6 +97,11 @@ typedef struct dotpe_ctx dotpe_ctx;
 /* context flags */
 #define DOTPE_CONFIG_AUTOTUNE 0x1  /* time candidate L2 tile bands on the first event of each shape */
 #define DOTPE_CONFIG_NO_GRAPHS 0x2 /* launch batches directly instead of as captured CUDA graphs */
+/* Screening and GEMM-only launches of mode banks use 128 x 32-sample tiles
+ * (two TMEM accumulator sets) instead of the default 128 x 64-sample tiles (one
+ * set of N = 128 per mode, twice the MMA work per operand byte).  Results are
+ * the same either way; with DOTPE_CONFIG_AUTOTUNE the tuner times both. */
+#define DOTPE_CONFIG_NARROW_TILES 0x4
 
 typedef struct dotpe_config {
   int device;                /* CUDA ordinal */

@@ -179,6 +179,8 @@ struct dotpe_ctx {
   bool use_graphs = true;  // batches run as captured CUDA graphs
   bool autotune = false;   // time L2 band widths on first use of a shape
   std::unordered_map<std::string, int> band_cache;                        // shape key -> band
+  std::unordered_map<std::string, int> tev_cache;                         // shape key -> screening tile width
+  bool wide_tiles = true;  // 64-sample tiles for screening / GEMM-only launches of mode banks
   std::vector<std::unordered_map<std::string, cudaGraphExec_t>> graphs;  // per slot
   double l2_band_bytes = 0;  // extrinsic operand kept in L2 per sweep of the bank
   // completion callbacks -> admission worker
@@ -427,6 +429,10 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
     if (encode_tmap_kblocks(&W.mapB, dt, pa.gpack, b_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2, 2 * TC_TE,
                             tc_kblocks_per_stage()))
       return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (extrinsic operand)");
+    // 128-row boxes for 64-sample tiles (mode banks)
+    if (b.n_pol != 2 && encode_tmap_kblocks(&W.mapB64, dt, pa.gpack, b_rows, b.Kpad / 64, (uint64_t)b.Kpad * 2,
+                                            4 * TC_TE, tc_kblocks_per_stage()))
+      return fail(DOTPE_E_DEVICE, "cuTensorMapEncodeTiled failed (extrinsic operand, 128-row boxes)");
     W.n_etile = L.n_etile;
     W.band = event_band(ctx, e, L, prec_split(e.prec));
     W.b_plane_rows = b.M * 2 * (int)e.NE;
@@ -531,6 +537,19 @@ static EpiParams refine_params(const EventRun &R) {
   return Pf;
 }
 
+static std::string band_key(const Event &e, const ScratchLayout &L, bool split);
+
+// Tile width of a single-pass launch: 64-sample tiles where the launch writes
+// no marginal partials (a screening pass with the cut on, or GEMM-only) over a
+// mode bank, unless the context asks for 32-sample tiles; the autotuner's
+// choice for the shape where it has one.
+static int launch_tev(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, const EpiParams &P, bool split) {
+  if (!ctx->wide_tiles || split || e.bank->n_pol == 2 || P.lnl_tile) return 32;
+  if (!(P.gemm_only || P.screen_ml)) return 32;
+  auto it = ctx->tev_cache.find(band_key(e, L, prec_split(e.prec)));
+  return it != ctx->tev_cache.end() ? it->second : 64;
+}
+
 // The fused kernel(s) of the current block of one event (mixed: screen,
 // selection, refinement over the event's own list).
 static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, cudaStream_t st) {
@@ -551,14 +570,17 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
   TcWork W = R.W;
   if (!R.mixed) {
     W.P = R.P;
+    T.tev = launch_tev(ctx, e, R.L, W.P, T.split);
     int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
     if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
     return DOTPE_OK;
   }
   W.P = screen_params(R);
+  T.tev = launch_tev(ctx, e, R.L, W.P, false);
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
   if (last_block) CUDA_OR_FAIL(record(e.ev_ks, st));
+  T.tev = 32;
   SelectBatch sb;
   memset(&sb, 0, sizeof(sb));
   sb.ev[0] = select_event_of(R);
@@ -737,12 +759,14 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
 }
 
 // ---------------------------------------------------------------------------
-// L2 band autotuner.  The fused kernel walks the extrinsic tiles in bands: every
-// bank tile meets the band's extrinsic tiles before the next band starts, so the
-// band's operand stays in L2 while the bank streams once per band.  The best
-// band width depends on the operand sizes and on how the two L2 partitions
-// share lines; it is chosen per shape (precision class, modes, k-blocks,
-// extrinsic tiles) by timing candidate widths on the first event of that shape.
+// Tile-shape autotuner.  The fused kernel walks the extrinsic tiles in bands:
+// every bank tile meets the band's extrinsic tiles before the next band starts,
+// so the band's operand stays in L2 while the bank streams once per band.  The
+// best band width depends on the operand sizes and on how the two L2 partitions
+// share lines, and the best tile width (32 samples with two TMEM accumulator
+// sets, or 64 with one) on how much the epilogue costs against the MMAs; both
+// are chosen per shape (precision class, modes, k-blocks, extrinsic tiles) by
+// timing candidates on the first event of that shape.
 // ---------------------------------------------------------------------------
 static std::string band_key(const Event &e, const ScratchLayout &L, bool split) {
   char buf[96];
@@ -757,9 +781,11 @@ static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bo
   return tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, split, L.n_etile);
 }
 
-// Times the event's first fused launch at candidate band widths (the event's
-// own inputs, prepared on `st`); the results of these runs are overwritten by
-// the real launch that follows.  Blocks the calling thread once per shape.
+// Times the event's first fused launch at candidate (tile width, band width)
+// pairs (the event's own inputs, prepared on `st`): 32- and 64-sample tiles
+// where the launch may take either, band widths doubling from one extrinsic
+// tile to all of them.  The results of these runs are overwritten by the real
+// launch that follows.  Blocks the calling thread once per shape.
 static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
   const bool split_main = prec_split(e.prec) && e.prec != DOTPE_PREC_MIXED;
   const std::string key = band_key(e, R.L, prec_split(e.prec));
@@ -769,27 +795,37 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
   if (rc != DOTPE_OK) return rc;
   T.split = split_main;
   T.sep = split_main;
-  std::vector<int> cand;
-  for (int c = 1; c < R.W.n_etile; c *= 2) cand.push_back(c);
-  cand.push_back(R.W.n_etile);
-  const int dflt = tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, prec_split(e.prec), R.L.n_etile);
-  if (std::find(cand.begin(), cand.end(), dflt) == cand.end()) cand.push_back(dflt);
-  std::vector<cudaEvent_t> ev(cand.size() + 1);
-  for (auto &x : ev) CUDA_OR_FAIL(cudaEventCreate(&x));
   TcWork W = R.W;
   W.P = R.mixed ? screen_params(R) : R.P;
+  std::vector<int> tevs{32};
+  if (ctx->wide_tiles && !split_main && e.bank->n_pol != 2 && !W.P.lnl_tile && (W.P.gemm_only || W.P.screen_ml))
+    tevs.push_back(64);
+  const int dflt = tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, prec_split(e.prec), R.L.n_etile);
+  struct Cand { int tev, band; };
+  std::vector<Cand> cand;
+  for (int tv : tevs) {
+    std::vector<int> bands;
+    for (int c = 1; c < R.W.n_etile; c *= 2) bands.push_back(c);
+    bands.push_back(R.W.n_etile);
+    if (std::find(bands.begin(), bands.end(), dflt) == bands.end()) bands.push_back(dflt);
+    for (int c : bands) cand.push_back({tv, c});
+  }
+  std::vector<cudaEvent_t> ev(cand.size() + 1);
+  for (auto &x : ev) CUDA_OR_FAIL(cudaEventCreate(&x));
   // warm-up at the default width, then one timed launch per candidate
   W.band = dflt;
+  T.tev = tevs.back();
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   CUDA_OR_FAIL(cudaEventRecord(ev[0], st));
   for (size_t c = 0; c < cand.size() && r == 0; ++c) {
-    W.band = cand[c];
+    W.band = cand[c].band;
+    T.tev = cand[c].tev;
     r = launch_tc(T, &W, 1, nullptr, nullptr, st);
     CUDA_OR_FAIL(cudaEventRecord(ev[c + 1], st));
   }
   if (r != 0) return fail(DOTPE_E_DEVICE, "autotune launch failed: %s", cudaGetErrorString((cudaError_t)r));
   CUDA_OR_FAIL(cudaEventSynchronize(ev.back()));
-  int best = dflt;
+  Cand best{tevs.back(), dflt};
   float best_ms = 1e30f;
   for (size_t c = 0; c < cand.size(); ++c) {
     float ms = 0.f;
@@ -797,8 +833,9 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
     if (ms < best_ms) { best_ms = ms; best = cand[c]; }
   }
   for (auto &x : ev) cudaEventDestroy(x);
-  ctx->band_cache[key] = best;
-  R.W.band = best;
+  ctx->band_cache[key] = best.band;
+  ctx->tev_cache[key] = best.tev;
+  R.W.band = best.band;
   // the tuning runs raised the running maximum: start the real launch afresh
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
   return DOTPE_OK;
@@ -867,6 +904,10 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
         TcLaunch T1 = T;
         T1.split = prec_split(prec) && !mixed;
         T1.sep = T1.split;
+        // one tile width for the launch: 64 samples only if every event takes it
+        T1.tev = 64;
+        for (int k = k0; k < k0 + m; ++k)
+          T1.tev = std::min(T1.tev, launch_tev(ctx, *evs[k], R[k].L, W[k].P, T1.split));
         int r = launch_tc(T1, &W[k0], m, nullptr, nullptr, st);
         if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
       }
@@ -1544,6 +1585,7 @@ int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
   int ns = c.n_slots > 0 ? c.n_slots : 4;
   ctx->max_batch = c.max_batch > 1 ? c.max_batch : 1;
   ctx->autotune = (c.flags & DOTPE_CONFIG_AUTOTUNE) != 0;
+  ctx->wide_tiles = (c.flags & DOTPE_CONFIG_NARROW_TILES) == 0;
   ctx->use_graphs = (c.flags & DOTPE_CONFIG_NO_GRAPHS) == 0;
   ctx->graphs.resize(ns);
   ctx->streams.resize(ns);

@@ -43,13 +43,14 @@ int launch_tc_nb(const TcLaunch &L, const TcWork *works, int n, const int2 *glis
                  cudaStream_t st) {
   static_assert(sizeof(TcBatch<NB>) <= 32000, "kernel parameter space");
   if (n < 1 || n > NB) return (int)cudaErrorInvalidValue;
+  const int tev = L.tev == 64 ? 64 : 32;
   TcBatch<NB> *bt = new TcBatch<NB>();  // ~29 KB: off the host stack
   int total = 0;
   for (int k = 0; k < n; ++k) {
     bt->w[k] = works[k];
-    bt->mapB[k] = works[k].mapB;
+    bt->mapB[k] = (tev == 64) ? works[k].mapB64 : works[k].mapB;
     bt->begin[k] = total;
-    total += works[k].n_itile * works[k].n_etile;
+    total += tc_work_items(works[k], tev);
   }
   for (int k = n; k <= NB; ++k) bt->begin[k] = total;
   bt->n = n;

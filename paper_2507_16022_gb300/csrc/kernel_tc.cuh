@@ -11,11 +11,17 @@
 //               of the tile's extrinsic samples): tcgen05.ld of the accumulators,
 //               <h|h> coefficients, phase grid, ML cut, distance marginal,
 //               log-sum-exp partials
-// Tile = 128 bank rows x 32 extrinsic samples, all modes: accumulators for mode
-// m live in TMEM columns [buf*256 + 64 m, +64).  Per mode the GEMM is the
+// Tile = 128 bank rows x TEV extrinsic samples, all modes: accumulators for mode
+// m live in TMEM columns [buf * 4 * 2TEV + 2TEV m, +2TEV).  Per mode the GEMM is the
 // real-ified complex product of Eq. dh_ieo (K = 2B, padded to a multiple of 64).
-// Two buffers, so the epilogue of tile t overlaps the MMAs of tile t+1; split
-// precision adds the hi*lo and lo*hi passes into the same accumulator.  With
+// TEV = 32: two buffers, so the epilogue of tile t overlaps the MMAs of tile
+// t+1; split precision adds the hi*lo and lo*hi passes into the same
+// accumulator.  TEV = 64 (screening pass and GEMM-only runs): one buffer of
+// N = 128 per mode fills TMEM, so the epilogue and the next tile's MMAs take
+// turns, but every bank byte brought into shared memory feeds twice the MMA
+// work (64 instead of 43 flops per operand byte); a work tile then holds the
+// partial tiles (it, 2 wt) and (it, 2 wt + 1) of the 32-sample tile grid that
+// the outputs are indexed by.  With
 // SEP (split only) hi*hi accumulates in the first buffer and the small
 // hi*lo + lo*hi terms in the second, added in the epilogue: the tensor cores'
 // FP32 accumulation truncates at every step, and keeping the small terms out of
@@ -39,33 +45,39 @@
 namespace dotpe {
 
 namespace {
-constexpr int TI = TC_TI, TE = TC_TE, BN = 2 * TE, BK = 64;
+constexpr int TI = TC_TI, TE = TC_TE, BK = 64;
 constexpr int NEPI = 8;              // epilogue warps
 constexpr int NT = (2 + NEPI) * 32;  // 320 threads
 constexpr int EPT = NEPI * 32;       // epilogue threads
-constexpr int EHALF = TE / 2;        // extrinsic samples per epilogue thread and tile
-constexpr uint32_t A_BYTES = TI * BK * 2, B_BYTES = BN * BK * 2;  // one k-block
+constexpr uint32_t A_BYTES = TI * BK * 2;  // one k-block of the bank tile
 constexpr int KBX = 2;  // k-blocks per stage (one 3-D TMA box)
-// Pipeline: single pass = 4 stages of {A, B} x 2 k-blocks (48 KB); split
-// precision = 2 stages of {A_hi, A_lo, B_hi, B_lo} x 2 k-blocks (96 KB), whose
-// three MMA groups (hi*hi, hi*lo, lo*hi) share one load of each plane.
-template <bool SPLIT> struct Pipe {
+// Pipeline: single pass = 4 stages of {A, B} x 2 k-blocks (48 KB; 3 x 64 KB
+// with the 64-sample tile); split precision = 2 stages of {A_hi, A_lo, B_hi,
+// B_lo} x 2 k-blocks (96 KB), whose three MMA groups (hi*hi, hi*lo, lo*hi)
+// share one load of each plane.
+template <bool SPLIT, int TEV> struct Pipe {
+  static constexpr int BN = 2 * TEV;  // extrinsic operand rows of a tile: N of every MMA
   static constexpr int NPL = SPLIT ? 2 : 1;
-  static constexpr int ST = SPLIT ? 2 : 4;
+  static constexpr int ST = SPLIT ? 2 : (TEV == 64 ? 3 : 4);
+  static constexpr uint32_t B_BYTES = BN * BK * 2;  // one k-block
   static constexpr uint32_t A_ST = KBX * A_BYTES, B_ST = KBX * B_BYTES;  // per plane
   static constexpr uint32_t STAGE = NPL * (A_ST + B_ST);
+  static constexpr uint32_t BUF_COLS = MAXM * BN;  // TMEM columns of one accumulator set
 };
-constexpr uint32_t TMEM_COLS = 512, BUF_COLS = MAXM * BN;
-constexpr int XS_LD = TE + 1;
-static_assert(2 * BUF_COLS <= TMEM_COLS, "TMEM budget");
+constexpr uint32_t TMEM_COLS = 512;
+static_assert(2 * Pipe<false, 32>::BUF_COLS <= TMEM_COLS && Pipe<false, 64>::BUF_COLS <= TMEM_COLS, "TMEM budget");
 
-struct TcTail {
+// TEV = 32 carries the general epilogue (marginalisation, partial sums through
+// shared memory); TEV = 64 only the screening and GEMM-only epilogues.
+template <int TEV> struct TcTail {
+  static constexpr bool GEN = (TEV == 32);
+  static constexpr int XS_LD = TEV + 1;
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
-  float xs[TI * XS_LD];
-  alignas(16) float qs[TE * MAXD * REC];  // read as float4 records
-  double lwe[TE];
+  float xs[GEN ? TI * XS_LD : 1];
+  alignas(16) float qs[TEV * MAXD * REC];  // read as float4 records
+  double lwe[GEN ? TEV : 1];
   float2 ph[7 * MAXPHI];
-  float2 rowh[TI];  // second-half row partial of each row
+  float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
   float wm1[NEPI], ws1[NEPI], wm2[NEPI], ws2[NEPI], wml[NEPI];
   long long warg[NEPI];
   int wnp[NEPI];
@@ -73,11 +85,13 @@ struct TcTail {
   uint32_t tmem_slot;
   int abort_flag;
 };
-template <bool SPLIT>
+template <bool SPLIT, int TEV>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)Pipe<SPLIT>::ST * Pipe<SPLIT>::STAGE + sizeof(TcTail);
+  return 1024 + (size_t)Pipe<SPLIT, TEV>::ST * Pipe<SPLIT, TEV>::STAGE + sizeof(TcTail<TEV>);
 }
-static_assert(smem_bytes<true>() <= 232448 && smem_bytes<false>() <= 232448, "shared memory budget");
+static_assert(smem_bytes<true, 32>() <= 232448 && smem_bytes<false, 32>() <= 232448 &&
+                  smem_bytes<false, 64>() <= 232448,
+              "shared memory budget");
 }  // namespace
 
 // 32 lanes x 32-bit, 2 consecutive columns per thread.
@@ -91,8 +105,11 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
 // Work item w -> (event k, tile it, et): entry w of the device list, or the
 // event whose range [begin[k], begin[k+1]) holds w and, within it, the banded
 // order of super_tile.
-template <int NB>
+// With TEV = 64 the grid-mode items are 64-sample work tiles (et counts them):
+// ceil(n_etile / 2) per bank tile, banded in half as many of them.
+template <int NB, int TEV>
 __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, int &it, int &et) {
+  constexpr int RS = TEV / TE;  // 32-sample tiles per work tile
   if (Bt.glist) {
     const int2 q = Bt.glist[w];
     k = q.x;
@@ -111,16 +128,28 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
     k = lo;
   }
   const TcEvent &W = Bt.w[k];
-  super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
+  if (RS == 1) {
+    super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
+  } else {
+    const int nw = (W.n_etile + RS - 1) / RS, bw = W.band / RS;
+    super_tile(w - Bt.begin[k], W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
+  }
 }
 
-template <bool BF16, int HH, bool SPLIT, int NB, bool SEP>
+template <bool BF16, int HH, bool SPLIT, int NB, bool SEP, int TEV>
 __global__ void __launch_bounds__(NT, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcBatch<NB> Bt,
                     const TcCommon C) {
   static_assert(SPLIT || !SEP, "a separate low-order accumulator needs split operands");
-  constexpr int ST = Pipe<SPLIT>::ST, NPL = Pipe<SPLIT>::NPL;
-  constexpr uint32_t STAGE_BYTES = Pipe<SPLIT>::STAGE, A_ST = Pipe<SPLIT>::A_ST, B_ST = Pipe<SPLIT>::B_ST;
+  static_assert(TEV == 32 || (TEV == 64 && !SPLIT && HH != 2), "64-sample tiles: single-pass mode banks");
+  using PP = Pipe<SPLIT, TEV>;
+  using TcTail = dotpe::TcTail<TEV>;
+  constexpr int ST = PP::ST, NPL = PP::NPL, BN = PP::BN;
+  constexpr uint32_t STAGE_BYTES = PP::STAGE, A_ST = PP::A_ST, B_ST = PP::B_ST, B_BYTES = PP::B_BYTES;
+  constexpr uint32_t BUF_COLS = PP::BUF_COLS;
+  constexpr int EHALF = TEV / 2;  // extrinsic samples per epilogue thread and tile
+  constexpr int XS_LD = TcTail::XS_LD;
+  constexpr bool ONEBUF = SEP || TEV == 64;  // one accumulator set in flight
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s, plane p: A at sA + (s NPL + p) A_ST as [KBX][128 rows][64],
@@ -164,7 +193,7 @@ __global__ void __launch_bounds__(NT, 1)
       bool ok = !Bt.w[0].P.test_stall;
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
         int k, it, et;
-        work_tile(Bt, w, k, it, et);
+        work_tile<NB, TEV>(Bt, w, k, it, et);
         if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
         const TcEvent &W = Bt.w[k];
         for (int m = 0; m < M && ok; ++m) {
@@ -204,11 +233,11 @@ __global__ void __launch_bounds__(NT, 1)
     for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
       if (Bt.gate) {
         int k, it, et;
-        work_tile(Bt, w, k, it, et);
+        work_tile<NB, TEV>(Bt, w, k, it, et);
         if (Bt.gate[k] != Bt.gate_want) continue;
       }
-      const int b = SEP ? 0 : (u & 1);
-      const uint32_t use = SEP ? u : (u >> 1);
+      const int b = ONEBUF ? 0 : (u & 1);
+      const uint32_t use = ONEBUF ? u : (u >> 1);
       ++u;
       if (use > 0) ok = __all_sync(0xffffffffu, mbar_wait(&T.tempty[b], (use - 1) & 1, nullptr, abortp, wait_ns));
       if (!ok) break;
@@ -273,10 +302,10 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t u = 0;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
       int k, it, et;
-      work_tile(Bt, w, k, it, et);
+      work_tile<NB, TEV>(Bt, w, k, it, et);
       if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
-      const int b = SEP ? 0 : (u & 1);
-      const uint32_t use = SEP ? u : (u >> 1);
+      const int b = ONEBUF ? 0 : (u & 1);
+      const uint32_t use = ONEBUF ? u : (u >> 1);
       ++u;
       if (k != cur_k) {
         // the next event: its parameters and phase tables into shared memory
@@ -297,7 +326,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int t = it * Bt.w[k].n_etile + et;
       const int64_t i = (int64_t)it * TI + row;
       const bool vi = i < P.n_int;
-      const int64_t e0 = (int64_t)et * TE;
+      const int64_t e0 = (int64_t)et * TEV;
       if (it != cur_it) {
 #pragma unroll
         for (int k = 0; k < NREC; ++k) mrec[k] = 0.f;
@@ -329,15 +358,153 @@ __global__ void __launch_bounds__(NT, 1)
         lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
         cur_it = it;
       }
-      for (int k = etid; k < TE * P.n_det * REC; k += EPT) {
+      for (int k = etid; k < TEV * P.n_det * REC; k += EPT) {
         const int e = k / (P.n_det * REC), qq = k % (P.n_det * REC);
         T.qs[e * MAXD * REC + qq] = (e0 + e < P.n_ext) ? __ldg(P.qx + (e0 + e) * P.n_det * REC + qq) : 0.f;
       }
-      for (int k = etid; k < TE; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
+      if constexpr (TcTail::GEN)
+        for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
       named_bar_sync(1, EPT);
       const float thr = tile_threshold(P);
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
       tc_fence_after();
+
+      if constexpr (TEV == 64) {
+        // ---- 64-sample work tile: screening (or GEMM-only) of partial tiles 2 et + half ----
+        const int n_etile = Bt.w[k].n_etile;
+        const int pe = 2 * et + half;  // this thread's 32-sample partial tile
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16);
+        float best = -1.f;
+        long long barg = 0x7fffffffffffffffLL;
+        if (P.gemm_only) {
+          // the accumulators summed (keeps every TMEM read; the result is not valid)
+          float sx = 0.f;
+#pragma unroll 1
+          for (int j = 0; j < EHALF; ++j) {
+            float zr[MAXM], zi[MAXM];
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
+              else { zr[m] = 0.f; zi[m] = 0.f; }
+            }
+            tmem_ld_wait();
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) sx += zr[m] + zi[m];
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&T.tempty[0]);
+          best = (vi && sx == sx) ? fabsf(sx) : -1.f;
+        } else {
+          // Pass 1 bounds every pair of the thread (bounds in registers); pass 2
+          // evaluates pairs in decreasing bound order until the next bound lies
+          // below both the threshold and the best so far.
+          float bnd[EHALF];
+#pragma unroll
+          for (int j = 0; j < EHALF; ++j) {
+            const int64_t e = e0 + half * EHALF + j;
+            float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), Zr[m], Zi[m]);
+              else { Zr[m] = 0.f; Zi[m] = 0.f; }
+            }
+            tmem_ld_wait();
+            float bound = -INFINITY;
+            if (vi && e < P.n_ext) {
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) {
+                Zr[m] *= zs;
+                Zi[m] *= zs;
+              }
+              float C0, Cr[3], Ci[3];
+              hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
+              bound = pair_bound(Zr, Zi, C0, Cr, Ci);
+            }
+            bnd[j] = bound;
+          }
+#pragma unroll 1
+          while (true) {
+            int jm = 0;
+            float bm = bnd[0];
+#pragma unroll
+            for (int j = 1; j < EHALF; ++j)
+              if (bnd[j] > bm) { bm = bnd[j]; jm = j; }
+            // ties with the best are evaluated, so the lowest index wins them
+            const bool want = (bm >= thr) && !(bm < best);
+            if (!__any_sync(0xffffffffu, want)) break;
+#pragma unroll
+            for (int j = 0; j < EHALF; ++j)
+              if (want && j == jm) bnd[j] = -INFINITY;
+            float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) { Zr[m] = 0.f; Zi[m] = 0.f; }
+#pragma unroll 1
+            for (int j = 0; j < EHALF; ++j) {
+              if (!__any_sync(0xffffffffu, want && jm == j)) continue;
+              float zr[MAXM], zi[MAXM];
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) {
+                if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
+                else { zr[m] = 0.f; zi[m] = 0.f; }
+              }
+              tmem_ld_wait();
+              if (want && jm == j) {
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m) { Zr[m] = zr[m]; Zi[m] = zi[m]; }
+              }
+            }
+            if (want) {
+              const int el = half * EHALF + jm;
+              const int64_t e = e0 + el;
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) {
+                Zr[m] *= zs;
+                Zi[m] *= zs;
+              }
+              float C0, Cr[3], Ci[3];
+              hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+              int argo;
+              const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
+              const long long g = (i * P.n_ext + e) * (long long)P.n_phi + argo;
+              if (ml > best || (ml == best && g < barg)) {
+                best = ml;
+                barg = g;
+              }
+            }
+          }
+          // the accumulators are no longer needed: release the buffer to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&T.tempty[0]);
+        }
+        // outputs of the two partial tiles: empty marginal partials and each one's best ln L^ML
+        warp_argmax(best, barg);
+        if (lane == 0) {
+          T.wml[ew] = best;
+          T.warg[ew] = barg;
+        }
+        if (vi && pe < n_etile) P.row_part[(int64_t)pe * P.n_int + i] = make_float2(-INFINITY, 0.f);
+        if (etid < TEV && e0 + etid < P.n_ext)
+          P.col_part[(int64_t)it * P.n_ext + e0 + etid] = make_float2(-INFINITY, 0.f);
+        named_bar_sync(1, EPT);
+        if (etid < 2 && 2 * et + etid < n_etile) {
+          // warps 4 h .. 4 h + 3 hold partial tile 2 et + h
+          float bv = -1.f;
+          long long bi = 0x7fffffffffffffffLL;
+          for (int q = 4 * etid; q < 4 * etid + 4; ++q)
+            if (T.wml[q] > bv || (T.wml[q] == bv && T.warg[q] < bi)) { bv = T.wml[q]; bi = T.warg[q]; }
+          const int tp = it * n_etile + 2 * et + etid;
+          P.tile_part[tp] = make_float4(-INFINITY, 0.f, -INFINITY, 0.f);
+          P.tile_ml[tp] = bv;
+          P.tile_arg[tp] = bi;
+          P.tile_npass[tp] = 0;
+          if (bv > 0.f && P.track_max && !P.gemm_only) atomic_max_nonneg(P.ml_running, bv);
+        }
+        // the next tile's barrier (after its column records) orders these reads
+        // of T.wml before any thread writes it again
+        continue;
+      } else {
 
       Lse ra, rb;
       ra.init();
@@ -599,6 +766,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       // no trailing barrier: the next tile's barrier (after its column records)
       // orders these reads of the per-warp values before they are written again
+      }  // TEV == 32
     }
   }
   tc_fence_before();
@@ -611,31 +779,39 @@ __global__ void __launch_bounds__(NT, 1)
 
 // Launches one instantiation chosen by the run-time flags (the kernel's
 // parameter block is copied from *bt at launch).
-template <int NB, bool SPLIT, bool SEP>
+template <int NB, bool SPLIT, bool SEP, int TEV>
 cudaError_t launch_tc_variant(const TcLaunch &L, const TcBatch<NB> &bt, int grid, cudaStream_t st) {
   auto go = [&](auto kern) -> cudaError_t {
-    const size_t smem = smem_bytes<SPLIT>();
+    const size_t smem = smem_bytes<SPLIT, TEV>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, smem, st>>>(L.mapA, bt, L.C);
     return cudaGetLastError();
   };
   if (L.pol) {
-    // polarisation-resolved banks run one event per launch
-    if constexpr (NB == 1)
-      return L.bf16 ? go(tc_fused_kernel<true, 2, SPLIT, NB, SEP>) : go(tc_fused_kernel<false, 2, SPLIT, NB, SEP>);
+    // polarisation-resolved banks run one event per launch, in 32-sample tiles
+    if constexpr (NB == 1 && TEV == 32)
+      return L.bf16 ? go(tc_fused_kernel<true, 2, SPLIT, NB, SEP, TEV>)
+                    : go(tc_fused_kernel<false, 2, SPLIT, NB, SEP, TEV>);
     else
       return cudaErrorInvalidValue;
   }
-  if (L.bf16) return L.consec ? go(tc_fused_kernel<true, 1, SPLIT, NB, SEP>)
-                              : go(tc_fused_kernel<true, 0, SPLIT, NB, SEP>);
-  return L.consec ? go(tc_fused_kernel<false, 1, SPLIT, NB, SEP>) : go(tc_fused_kernel<false, 0, SPLIT, NB, SEP>);
+  if (L.bf16) return L.consec ? go(tc_fused_kernel<true, 1, SPLIT, NB, SEP, TEV>)
+                              : go(tc_fused_kernel<true, 0, SPLIT, NB, SEP, TEV>);
+  return L.consec ? go(tc_fused_kernel<false, 1, SPLIT, NB, SEP, TEV>)
+                  : go(tc_fused_kernel<false, 0, SPLIT, NB, SEP, TEV>);
 }
 
 template <int NB>
 cudaError_t launch_tc_any(const TcLaunch &L, const TcBatch<NB> &bt, int grid, cudaStream_t st) {
-  if (!L.split) return launch_tc_variant<NB, false, false>(L, bt, grid, st);
-  return L.sep ? launch_tc_variant<NB, true, true>(L, bt, grid, st) : launch_tc_variant<NB, true, false>(L, bt, grid, st);
+  if (L.tev == 64) {
+    // 64-sample work tiles: single pass, grid order only (no device list)
+    if (L.split || L.pol || bt.glist) return cudaErrorInvalidValue;
+    return launch_tc_variant<NB, false, false, 64>(L, bt, grid, st);
+  }
+  if (!L.split) return launch_tc_variant<NB, false, false, 32>(L, bt, grid, st);
+  return L.sep ? launch_tc_variant<NB, true, true, 32>(L, bt, grid, st)
+               : launch_tc_variant<NB, true, false, 32>(L, bt, grid, st);
 }
 
 }  // namespace dotpe

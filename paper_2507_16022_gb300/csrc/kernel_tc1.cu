@@ -5,11 +5,12 @@
 namespace dotpe {
 
 int launch_tc_single(const TcLaunch &L, const TcWork *works, const int2 *glist, const int *glist_n, cudaStream_t st) {
+  const int tev = L.tev == 64 ? 64 : 32;
   TcBatch<1> bt;
   bt.w[0] = works[0];
-  bt.mapB[0] = works[0].mapB;
+  bt.mapB[0] = (tev == 64) ? works[0].mapB64 : works[0].mapB;
   bt.begin[0] = 0;
-  bt.begin[1] = works[0].n_itile * works[0].n_etile;
+  bt.begin[1] = tc_work_items(works[0], tev);
   bt.n = 1;
   bt.glist = glist;
   bt.glist_n = glist_n;

@@ -91,8 +91,9 @@ struct TcEvent {             // one event of a launch (without its tensor map)
   int a_row0;                      // first bank row of the event's slice (block)
   int b_plane_rows, b_mode_rows;   // rows of one operand plane / one mode in mapB
 };
-struct TcWork : TcEvent {    // host-side record: the event and its map
-  CUtensorMap mapB;          // packed extrinsic operand planes [planes][M][2E][Kpad]
+struct TcWork : TcEvent {    // host-side record: the event and its maps
+  CUtensorMap mapB;          // packed extrinsic operand planes [planes][M][2E][Kpad], 64-row boxes
+  CUtensorMap mapB64;        // the same planes in 128-row boxes (64-sample tiles); zero if not encoded
 };
 template <int NB>
 struct TcBatch {
@@ -116,6 +117,7 @@ struct TcLaunch {
   bool bf16, split, consec;
   bool pol;          // polarisation-resolved bank (row records in registers, n_det <= POL_TC_MAXD)
   bool sep;          // split: hi*lo + lo*hi in their own accumulator (see kernel_tc.cuh)
+  int tev;           // extrinsic samples per work tile: 32, or 64 (single-pass mode banks, grid order)
   const int *gate;   // optional device words per event: event k's items run only if gate[k] == gate_want
   int gate_want;
   int n_sms;
@@ -313,6 +315,12 @@ struct SampleArgs {
 // cdf: n_int doubles of scratch; outputs may be null
 void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cdf, int64_t *i_out, int64_t *e_out,
                    int32_t *o_out, double *d_out, cudaStream_t st);
+
+// Work items of one event in a launch of tile width tev (grid order).
+inline int tc_work_items(const TcEvent &w, int tev) {
+  const int rs = tev / TC_TE;
+  return w.n_itile * ((w.n_etile + rs - 1) / rs);
+}
 
 // Tensor-map encoding through the driver entry point.
 int encode_tmap_kblocks(CUtensorMap *map, CUtensorMapDataType dt, void *base, uint64_t rows, uint64_t n_kb,

@@ -649,6 +649,43 @@ def test_lnl_blocks_recomputed_without_stored_tiles(dpx):
         dp.dotpe_bank_release(ctx, bid)
 
 
+@pytest.mark.parametrize("shape", SHAPES[:4] + [(600, (0, 600), 64 * 3 + 40, 3, 4, 256)],
+                         ids=lambda s: f"I{s[0]}E{s[2]}D{s[3]}M{s[4]}B{s[5]}")
+def test_screen_tile_widths_agree(dpx, shape):
+    """The served path's screening pass runs in 64-sample tiles by default and in
+    32-sample tiles under DOTPE_CONFIG_NARROW_TILES: both mark the same tiles for
+    refinement (an odd count of 32-sample tiles leaves the last 64-sample tile
+    half empty), so the events agree, and both keep ln Z between the oracle's cut
+    and uncut values (Eq. coherent_ML_selection)."""
+    import oracle
+    dp, ctx = dpx
+    I_bank, (i0, i1), E, D, M, B = shape
+    wl = synth.make_workload(n_int=I_bank, n_ext=E, n_det=D, n_modes=M, n_bins=B, snr=14.0, seed=I_bank + E,
+                             ln_w="random")
+    narrow = dp.dotpe_create(0, flags=dp.DOTPE_CONFIG_NARROW_TILES)
+    try:
+        res = []
+        for c in (ctx, narrow):
+            bid = dp.dotpe_bank_load(c, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+            try:
+                res.append(run(dp, c, wl, "mixed", bid=bid, i0=i0, i1=i1, cut=20.0, flags=0)["ev"])
+            finally:
+                dp.dotpe_bank_release(c, bid)
+    finally:
+        dp.dotpe_destroy(narrow)
+    wide, nar = res
+    assert wide["n_refined_tiles"] == nar["n_refined_tiles"]
+    assert (wide["arg_i"], wide["arg_e"], wide["arg_o"]) == (nar["arg_i"], nar["arg_e"], nar["arg_o"])
+    assert wide["ln_z"] == pytest.approx(nar["ln_z"], abs=1e-9)
+    assert wide["max_lnl_ml"] == nar["max_lnl_ml"]
+    P = oracle.OracleProblem(wl.bank, wl.ext, wl.event, i_slice=slice(i0, i1))
+    gcut, thr = P.eval_grid(20.0)
+    guncut, _ = P.eval_grid(0.0)
+    lo, hi = P.evidence(gcut)["ln_z"], P.evidence(guncut)["ln_z"]
+    assert lo - 1e-2 <= wide["ln_z"] <= hi + 1e-2
+    assert wide["max_lnl_ml"] == pytest.approx(float(guncut["lnl_ml_max"].max()), abs=1e-3)
+
+
 def test_gemm_only_diagnostic_runs(dpx):
     dp, ctx = dpx
     wl = synth.make_workload(n_int=1024, n_ext=256, n_det=3, n_modes=4, n_bins=256, seed=2)
