@@ -75,6 +75,8 @@ template <int TEV> struct TcTail {
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
   float xs[GEN ? TI * XS_LD : 1];
   alignas(16) float qs[TEV * MAXD * REC];  // read as float4 records
+  // sum_d |Q_d[e, ab]| of the off-diagonal column records (64-sample screening bound)
+  float qabs[GEN ? 1 : TEV * NPAIR];
   double lwe[GEN ? TEV : 1];
   float2 ph[7 * MAXPHI];
   float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
@@ -100,6 +102,36 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
   a = __uint_as_float(r0);
   b = __uint_as_float(r1);
+}
+
+// 32 lanes x 32-bit, 16 consecutive columns per thread (column a multiple of 16).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// One candidate of the 64-sample screen, out of line (the few pairs that pass
+// the cheap bound; keeps the registers of the hot pass free): the exact bound
+// of pair_bound, then max_o ln L^ML_o if that bound reaches both the threshold
+// and the thread's best so far.  Returns -2 when the pair is not evaluated.
+template <int HH>
+static __device__ __noinline__ float screen_candidate(float z0r, float z0i, float z1r, float z1i, float z2r,
+                                                      float z2i, float z3r, float z3i, const float *mrow,
+                                                      const float *qrec, const EpiParams &P, const float2 *ph,
+                                                      float thr, float best, int &argo) {
+  const float Zr[MAXM] = {z0r, z1r, z2r, z3r}, Zi[MAXM] = {z0i, z1i, z2i, z3i};
+  float C0, Cr[3], Ci[3];
+  hh_tile<HH>(mrow, qrec, P, C0, Cr, Ci);
+  const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
+  argo = 0;
+  if (!(bound >= thr) || bound < best) return -2.f;
+  return pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, ph, argo);
 }
 
 // Work item w -> (event k, tile it, et): entry w of the device list, or the
@@ -295,8 +327,11 @@ __global__ void __launch_bounds__(NT, 1)
     const EpiParams &P = (NB == 1) ? Bt.w[0].P : T.ep;
     bool store = false;
     float zs = 1.f;
-    constexpr int NREC = (HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC;  // row record floats in registers
+    // row record floats in registers (the 64-sample screen keeps only what its
+    // cheap bound needs: the diagonal overlaps and the off-diagonal moduli)
+    constexpr int NREC = (TEV == 64) ? 1 : ((HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC);
     float mrec[NREC];
+
     double lwi = 0.0;
     int cur_it = -1, cur_k = -1;
     uint32_t u = 0;
@@ -327,7 +362,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int64_t i = (int64_t)it * TI + row;
       const bool vi = i < P.n_int;
       const int64_t e0 = (int64_t)et * TEV;
-      if (it != cur_it) {
+      if (TEV == 32 && it != cur_it) {
 #pragma unroll
         for (int k = 0; k < NREC; ++k) mrec[k] = 0.f;
         if constexpr (HH == 2) {
@@ -345,7 +380,7 @@ __global__ void __launch_bounds__(NT, 1)
                   if (4 * v + c < REC_POL) mrec[d * REC_POL + 4 * v + c] = xs4[c];
               }
             }
-        } else {
+        } else if constexpr (TEV == 32) {
           const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
 #pragma unroll
           for (int k = 0; k < MAXD * REC / 4; ++k) {
@@ -364,8 +399,62 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if constexpr (TcTail::GEN)
         for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
+      if constexpr (!TcTail::GEN)
+        for (int k = etid; k < TEV * NPAIR; k += EPT) {
+          const int e = k / NPAIR, q = k % NPAIR;
+          float v = 0.f;
+          if (e0 + e < P.n_ext)
+            for (int d = 0; d < P.n_det; ++d) {
+              const float *src = P.qx + ((e0 + e) * P.n_det + d) * REC + 4 + 2 * q;
+              const float x = __ldg(src), y = __ldg(src + 1);
+              v += sqrtf(x * x + y * y);
+            }
+          T.qabs[e * NPAIR + q] = v;
+        }
       named_bar_sync(1, EPT);
-      const float thr = tile_threshold(P);
+      float thr = tile_threshold(P);
+      // 64-sample screen: a lower bound of <h|h> at every phase for each of the
+      // thread's pairs, formed while the MMAs of the tile run (Eq. hh_ieo):
+      // <h|h>(phi) >= C_0 - 2 sum_delta |C_delta|
+      //   >= sum_d sum_m <h_m|h_m>_d |R_dm|^2 - sum_{a>b} 2 max_d |<h_a|h_b>_d| sum_d |R_da R_db^*|
+      // (C_0 exact; the small off-diagonal overlaps bounded across detectors)
+      float hl[TEV == 64 ? TEV / 2 : 1];
+      if constexpr (TEV == 64) {
+        // the row's diagonal overlaps and off-diagonal maxima (read again for
+        // every tile, so that nothing of it stays live through the candidates)
+        float rdiag[MAXD * MAXM], uoff[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) uoff[q] = 0.f;
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+          const float *src = P.mx + (i * P.n_det + d) * REC;
+          const bool ok = vi && d < P.n_det;
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) rdiag[d * MAXM + m] = ok ? __ldg(src + m) : 0.f;
+#pragma unroll
+          for (int q = 0; q < NPAIR; ++q) {
+            const float x = ok ? __ldg(src + 4 + 2 * q) : 0.f, y = ok ? __ldg(src + 5 + 2 * q) : 0.f;
+            uoff[q] = fmaxf(uoff[q], 2.f * sqrtf(x * x + y * y));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < EHALF; ++j) {
+          const int el = half * EHALF + j;
+          float hd = 0.f, ho = 0.f;
+#pragma unroll
+          for (int d = 0; d < MAXD; ++d) {
+            if (d < P.n_det) {
+              const float4 q = *reinterpret_cast<const float4 *>(&T.qs[el * MAXD * REC + d * REC]);
+              hd = fmaf(rdiag[d * MAXM], q.x, fmaf(rdiag[d * MAXM + 1], q.y,
+                        fmaf(rdiag[d * MAXM + 2], q.z, fmaf(rdiag[d * MAXM + 3], q.w, hd))));
+            }
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < NPAIR; ++q2) ho = fmaf(uoff[q2], T.qabs[el * NPAIR + q2], ho);
+          // FP32 rounding of the sums: keep the bound below the exact value
+          hl[j] = hd - ho - 1e-5f * hd;
+        }
+      }
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
       tc_fence_after();
 
@@ -379,99 +468,88 @@ __global__ void __launch_bounds__(NT, 1)
         if (P.gemm_only) {
           // the accumulators summed (keeps every TMEM read; the result is not valid)
           float sx = 0.f;
-#pragma unroll 1
-          for (int j = 0; j < EHALF; ++j) {
-            float zr[MAXM], zi[MAXM];
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
-              else { zr[m] = 0.f; zi[m] = 0.f; }
-            }
-            tmem_ld_wait();
+          for (int g = 0; g < EHALF / 8; ++g)
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m) sx += zr[m] + zi[m];
-          }
+            for (int m = 0; m < MAXM; ++m)
+              if (m < M) {
+                float v[16];
+                tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) sx += v[q];
+              }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&T.tempty[0]);
           best = (vi && sx == sx) ? fabsf(sx) : -1.f;
         } else {
-          // Pass 1 bounds every pair of the thread (bounds in registers); pass 2
-          // evaluates pairs in decreasing bound order until the next bound lies
-          // below both the threshold and the best so far.
-          float bnd[EHALF];
+          // Pass 1 (the accumulators read 16 columns at a time): a pair can reach
+          // ln L^ML >= thr only if M sum_m |Z_m|^2 >= (sum_m |Z_m|)^2 >= dh^2 reaches
+          // 2 thr hl (Eq. bestfit_lnl with hl <= <h|h>); those are the candidates.
+          const float cm = (float)M * zs * zs * 1.0001f;
+          uint32_t cand = 0;
 #pragma unroll
-          for (int j = 0; j < EHALF; ++j) {
-            const int64_t e = e0 + half * EHALF + j;
+          for (int g = 0; g < EHALF / 8; ++g) {
+            float s2[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s2[q] = 0.f;
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m)
+              if (m < M) {
+                float v[16];
+                tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s2[q] = fmaf(v[2 * q], v[2 * q], fmaf(v[2 * q + 1], v[2 * q + 1], s2[q]));
+              }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int j = 8 * g + q;
+              const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
+              const bool reject = thr > 0.f && hl[j] > 0.f && cm * s2[q] < 2.f * thr * hl[j];
+              if (valid && !reject) cand |= 1u << j;
+            }
+          }
+          // Pass 2: candidates in index order (the warp takes the lowest pending
+          // pair of its lanes at a time): the exact bound of pair_bound, then the
+          // phase grid where it can still reach the threshold and the thread's
+          // best; the threshold follows the running maximum, raised by every pair
+          // evaluated here (a lower bound of the final threshold throughout).
+          const float *mrow = P.mx + i * P.n_det * REC;
+          float pushed = 0.f;
+#pragma unroll 1
+          while (__any_sync(0xffffffffu, cand != 0u)) {
+            const int jl = cand ? (__ffs(cand) - 1) : EHALF;
+            const int j = __reduce_min_sync(0xffffffffu, jl);
+            const bool mine = ((cand >> j) & 1u) != 0u;
+            cand &= ~(1u << j);
+            const int el = half * EHALF + j;
             float Zr[MAXM], Zi[MAXM];
 #pragma unroll
             for (int m = 0; m < MAXM; ++m) {
-              if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), Zr[m], Zi[m]);
+              if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
               else { Zr[m] = 0.f; Zi[m] = 0.f; }
             }
             tmem_ld_wait();
-            float bound = -INFINITY;
-            if (vi && e < P.n_ext) {
-#pragma unroll
-              for (int m = 0; m < MAXM; ++m) {
-                Zr[m] *= zs;
-                Zi[m] *= zs;
-              }
-              float C0, Cr[3], Ci[3];
-              hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
-              bound = pair_bound(Zr, Zi, C0, Cr, Ci);
-            }
-            bnd[j] = bound;
-          }
-#pragma unroll 1
-          while (true) {
-            int jm = 0;
-            float bm = bnd[0];
-#pragma unroll
-            for (int j = 1; j < EHALF; ++j)
-              if (bnd[j] > bm) { bm = bnd[j]; jm = j; }
-            // ties with the best are evaluated, so the lowest index wins them
-            const bool want = (bm >= thr) && !(bm < best);
-            if (!__any_sync(0xffffffffu, want)) break;
-#pragma unroll
-            for (int j = 0; j < EHALF; ++j)
-              if (want && j == jm) bnd[j] = -INFINITY;
-            float Zr[MAXM], Zi[MAXM];
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) { Zr[m] = 0.f; Zi[m] = 0.f; }
-#pragma unroll 1
-            for (int j = 0; j < EHALF; ++j) {
-              if (!__any_sync(0xffffffffu, want && jm == j)) continue;
-              float zr[MAXM], zi[MAXM];
-#pragma unroll
-              for (int m = 0; m < MAXM; ++m) {
-                if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
-                else { zr[m] = 0.f; zi[m] = 0.f; }
-              }
-              tmem_ld_wait();
-              if (want && jm == j) {
-#pragma unroll
-                for (int m = 0; m < MAXM; ++m) { Zr[m] = zr[m]; Zi[m] = zi[m]; }
-              }
-            }
-            if (want) {
-              const int el = half * EHALF + jm;
-              const int64_t e = e0 + el;
-#pragma unroll
-              for (int m = 0; m < MAXM; ++m) {
-                Zr[m] *= zs;
-                Zi[m] *= zs;
-              }
-              float C0, Cr[3], Ci[3];
-              hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+            if (mine) {
               int argo;
-              const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
-              const long long g = (i * P.n_ext + e) * (long long)P.n_phi + argo;
-              if (ml > best || (ml == best && g < barg)) {
-                best = ml;
-                barg = g;
+              const float ml = screen_candidate<HH>(Zr[0] * zs, Zi[0] * zs, Zr[1] * zs, Zi[1] * zs, Zr[2] * zs,
+                                                    Zi[2] * zs, Zr[3] * zs, Zi[3] * zs, mrow,
+                                                    &T.qs[el * MAXD * REC], P, T.ph, thr, best, argo);
+              if (ml > -2.f) {
+                const long long gidx = (i * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
+                if (ml > best || (ml == best && gidx < barg)) {
+                  best = ml;
+                  barg = gidx;
+                }
+                if (P.track_max && ml > pushed && ml > 0.f) {
+                  atomic_max_nonneg(P.ml_running, ml);
+                  pushed = ml;
+                }
               }
             }
+            thr = fmaxf(thr, tile_threshold(P));
           }
           // the accumulators are no longer needed: release the buffer to the MMA warp
           tc_fence_before();
