@@ -75,8 +75,10 @@ template <int TEV> struct TcTail {
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
   float xs[GEN ? TI * XS_LD : 1];
   alignas(16) float qs[TEV * MAXD * REC];  // read as float4 records
-  // sum_d |Q_d[e, ab]| of the off-diagonal column records (64-sample screening bound)
-  float qabs[GEN ? 1 : TEV * NPAIR];
+  // |Q_d[e, ab]| of the off-diagonal column records and sum_d sum_m |R_dm|^2
+  // (64-sample screening bound)
+  float qabs[GEN ? 1 : TEV * MAXD * NPAIR];
+  float qsum[GEN ? 1 : TEV];
   double lwe[GEN ? TEV : 1];
   float2 ph[7 * MAXPHI];
   float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
@@ -164,7 +166,15 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
     super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
   } else {
     const int nw = (W.n_etile + RS - 1) / RS, bw = W.band / RS;
-    super_tile(w - Bt.begin[k], W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
+    const int np = tc_pilot_tiles(W, TEV);
+    int local = w - Bt.begin[k];
+    if (local < np) {
+      // pilot tile: bank tiles evenly spread, extrinsic tiles scrambled
+      it = (int)(((long long)local * W.n_itile) / np);
+      et = (int)(((unsigned long long)local * 2654435761ull) % (unsigned long long)nw);
+      return;
+    }
+    super_tile(local - np, W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
   }
 }
 
@@ -400,60 +410,68 @@ __global__ void __launch_bounds__(NT, 1)
       if constexpr (TcTail::GEN)
         for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
       if constexpr (!TcTail::GEN)
-        for (int k = etid; k < TEV * NPAIR; k += EPT) {
-          const int e = k / NPAIR, q = k % NPAIR;
+        for (int k = etid; k < TEV * MAXD * NPAIR; k += EPT) {
+          const int e = k / (MAXD * NPAIR), r = k % (MAXD * NPAIR), d = r / NPAIR, q = r % NPAIR;
           float v = 0.f;
-          if (e0 + e < P.n_ext)
-            for (int d = 0; d < P.n_det; ++d) {
-              const float *src = P.qx + ((e0 + e) * P.n_det + d) * REC + 4 + 2 * q;
-              const float x = __ldg(src), y = __ldg(src + 1);
-              v += sqrtf(x * x + y * y);
-            }
-          T.qabs[e * NPAIR + q] = v;
+          if (e0 + e < P.n_ext && d < P.n_det) {
+            const float *src = P.qx + ((e0 + e) * P.n_det + d) * REC + 4 + 2 * q;
+            const float x = __ldg(src), y = __ldg(src + 1);
+            v = sqrtf(x * x + y * y);
+          }
+          T.qabs[k] = v;
+        }
+      if constexpr (!TcTail::GEN)
+        for (int k = etid; k < TEV; k += EPT) {
+          float v = 0.f;
+          if (e0 + k < P.n_ext)
+            for (int d = 0; d < P.n_det; ++d)
+              for (int m = 0; m < MAXM; ++m) v += __ldg(P.qx + ((e0 + k) * P.n_det + d) * REC + m);
+          T.qsum[k] = v;
         }
       named_bar_sync(1, EPT);
       float thr = tile_threshold(P);
       // 64-sample screen: a lower bound of <h|h> at every phase for each of the
       // thread's pairs, formed while the MMAs of the tile run (Eq. hh_ieo):
       // <h|h>(phi) >= C_0 - 2 sum_delta |C_delta|
-      //   >= sum_d sum_m <h_m|h_m>_d |R_dm|^2 - sum_{a>b} 2 max_d |<h_a|h_b>_d| sum_d |R_da R_db^*|
-      // (C_0 exact; the small off-diagonal overlaps bounded across detectors)
+      //   >= sum_d [sum_m <h_m|h_m>_d |R_dm|^2 - 2 sum_{a>b} |<h_a|h_b>_d| |R_da R_db^*|]
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
-        // the row's diagonal overlaps and off-diagonal maxima (read again for
-        // every tile, so that nothing of it stays live through the candidates)
-        float rdiag[MAXD * MAXM], uoff[NPAIR];
+        // detector by detector: the row's diagonal overlaps and off-diagonal
+        // moduli (read again for every tile, so that nothing of them stays live
+        // through the candidates), against every pair's column record
 #pragma unroll
-        for (int q = 0; q < NPAIR; ++q) uoff[q] = 0.f;
+        for (int j = 0; j < EHALF; ++j) hl[j] = 0.f;
+        float rmax = 0.f;
 #pragma unroll
         for (int d = 0; d < MAXD; ++d) {
-          const float *src = P.mx + (i * P.n_det + d) * REC;
-          const bool ok = vi && d < P.n_det;
+          if (d < P.n_det) {
+            const float *src = P.mx + (i * P.n_det + d) * REC;
+            float rd[MAXM], ro[NPAIR];
 #pragma unroll
-          for (int m = 0; m < MAXM; ++m) rdiag[d * MAXM + m] = ok ? __ldg(src + m) : 0.f;
+            for (int m = 0; m < MAXM; ++m) {
+              rd[m] = vi ? __ldg(src + m) : 0.f;
+              rmax = fmaxf(rmax, rd[m]);
+            }
 #pragma unroll
-          for (int q = 0; q < NPAIR; ++q) {
-            const float x = ok ? __ldg(src + 4 + 2 * q) : 0.f, y = ok ? __ldg(src + 5 + 2 * q) : 0.f;
-            uoff[q] = fmaxf(uoff[q], 2.f * sqrtf(x * x + y * y));
-          }
-        }
+            for (int q = 0; q < NPAIR; ++q) {
+              const float x = vi ? __ldg(src + 4 + 2 * q) : 0.f, y = vi ? __ldg(src + 5 + 2 * q) : 0.f;
+              ro[q] = -2.f * sqrtf(x * x + y * y);
+            }
 #pragma unroll
-        for (int j = 0; j < EHALF; ++j) {
-          const int el = half * EHALF + j;
-          float hd = 0.f, ho = 0.f;
-#pragma unroll
-          for (int d = 0; d < MAXD; ++d) {
-            if (d < P.n_det) {
+            for (int j = 0; j < EHALF; ++j) {
+              const int el = half * EHALF + j;
               const float4 q = *reinterpret_cast<const float4 *>(&T.qs[el * MAXD * REC + d * REC]);
-              hd = fmaf(rdiag[d * MAXM], q.x, fmaf(rdiag[d * MAXM + 1], q.y,
-                        fmaf(rdiag[d * MAXM + 2], q.z, fmaf(rdiag[d * MAXM + 3], q.w, hd))));
+              float h = fmaf(rd[0], q.x, fmaf(rd[1], q.y, fmaf(rd[2], q.z, fmaf(rd[3], q.w, hl[j]))));
+#pragma unroll
+              for (int q2 = 0; q2 < NPAIR; ++q2) h = fmaf(ro[q2], T.qabs[(el * MAXD + d) * NPAIR + q2], h);
+              hl[j] = h;
             }
           }
-#pragma unroll
-          for (int q2 = 0; q2 < NPAIR; ++q2) ho = fmaf(uoff[q2], T.qabs[el * NPAIR + q2], ho);
-          // FP32 rounding of the sums: keep the bound below the exact value
-          hl[j] = hd - ho - 1e-5f * hd;
         }
+        // FP32 rounding of the sums (terms up to rmax |R|^2 each): keep the bound
+        // below the exact value
+#pragma unroll
+        for (int j = 0; j < EHALF; ++j) hl[j] -= 1e-5f * rmax * T.qsum[half * EHALF + j];
       }
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
       tc_fence_after();
@@ -485,15 +503,15 @@ __global__ void __launch_bounds__(NT, 1)
           best = (vi && sx == sx) ? fabsf(sx) : -1.f;
         } else {
           // Pass 1 (the accumulators read 16 columns at a time): a pair can reach
-          // ln L^ML >= thr only if M sum_m |Z_m|^2 >= (sum_m |Z_m|)^2 >= dh^2 reaches
-          // 2 thr hl (Eq. bestfit_lnl with hl <= <h|h>); those are the candidates.
-          const float cm = (float)M * zs * zs * 1.0001f;
+          // ln L^ML >= thr only if (sum_m |Z_m|)^2 >= dh^2 reaches 2 thr hl
+          // (Eq. bestfit_lnl with hl <= <h|h>); those are the candidates.
+          const float cm = zs * zs * 1.0001f;
           uint32_t cand = 0;
 #pragma unroll
           for (int g = 0; g < EHALF / 8; ++g) {
-            float s2[8];
+            float a[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s2[q] = 0.f;
+            for (int q = 0; q < 8; ++q) a[q] = 0.f;
 #pragma unroll
             for (int m = 0; m < MAXM; ++m)
               if (m < M) {
@@ -501,13 +519,13 @@ __global__ void __launch_bounds__(NT, 1)
                 tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v);
                 tmem_ld_wait();
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s2[q] = fmaf(v[2 * q], v[2 * q], fmaf(v[2 * q + 1], v[2 * q + 1], s2[q]));
+                for (int q = 0; q < 8; ++q) a[q] += sqrtf(fmaf(v[2 * q], v[2 * q], v[2 * q + 1] * v[2 * q + 1]));
               }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int j = 8 * g + q;
               const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
-              const bool reject = thr > 0.f && hl[j] > 0.f && cm * s2[q] < 2.f * thr * hl[j];
+              const bool reject = thr > 0.f && hl[j] > 0.f && cm * a[q] * a[q] < 2.f * thr * hl[j];
               if (valid && !reject) cand |= 1u << j;
             }
           }

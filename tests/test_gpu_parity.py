@@ -649,14 +649,17 @@ def test_lnl_blocks_recomputed_without_stored_tiles(dpx):
         dp.dotpe_bank_release(ctx, bid)
 
 
-@pytest.mark.parametrize("shape", SHAPES[:4] + [(600, (0, 600), 64 * 3 + 40, 3, 4, 256)],
+@pytest.mark.parametrize("shape", SHAPES[:4] + [(600, (0, 600), 64 * 3 + 40, 3, 4, 256),
+                                                 (2048, (0, 2048), 24 * 32 + 5, 3, 4, 128)],
                          ids=lambda s: f"I{s[0]}E{s[2]}D{s[3]}M{s[4]}B{s[5]}")
 def test_screen_tile_widths_agree(dpx, shape):
     """The served path's screening pass runs in 64-sample tiles by default and in
     32-sample tiles under DOTPE_CONFIG_NARROW_TILES: both mark the same tiles for
     refinement (an odd count of 32-sample tiles leaves the last 64-sample tile
-    half empty), so the events agree, and both keep ln Z between the oracle's cut
-    and uncut values (Eq. coherent_ML_selection)."""
+    half empty; the largest shape has enough tiles for the pilot tiles that the
+    wide screen takes first), so the events agree, and both keep ln Z between
+    the oracle's cut and uncut values (Eq. coherent_ML_selection; the largest
+    shape against the plain FP32 path with the same cut)."""
     import oracle
     dp, ctx = dpx
     I_bank, (i0, i1), E, D, M, B = shape
@@ -678,6 +681,16 @@ def test_screen_tile_widths_agree(dpx, shape):
     assert (wide["arg_i"], wide["arg_e"], wide["arg_o"]) == (nar["arg_i"], nar["arg_e"], nar["arg_o"])
     assert wide["ln_z"] == pytest.approx(nar["ln_z"], abs=1e-9)
     assert wide["max_lnl_ml"] == nar["max_lnl_ml"]
+    if (i1 - i0) * E > 300000:
+        bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+        try:
+            ref = run(dp, ctx, wl, "fp32", bid=bid, i0=i0, i1=i1, cut=20.0, flags=0)["ev"]
+        finally:
+            dp.dotpe_bank_release(ctx, bid)
+        assert abs(wide["ln_z"] - ref["ln_z"]) <= 1e-2
+        assert wide["max_lnl_ml"] == pytest.approx(ref["max_lnl_ml"], abs=1e-3)
+        assert (wide["arg_i"], wide["arg_e"], wide["arg_o"]) == (ref["arg_i"], ref["arg_e"], ref["arg_o"])
+        return
     P = oracle.OracleProblem(wl.bank, wl.ext, wl.event, i_slice=slice(i0, i1))
     gcut, thr = P.eval_grid(20.0)
     guncut, _ = P.eval_grid(0.0)
