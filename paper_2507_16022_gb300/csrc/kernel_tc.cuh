@@ -75,10 +75,6 @@ template <int TEV> struct TcTail {
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
   float xs[GEN ? TI * XS_LD : 1];
   alignas(16) float qs[TEV * MAXD * REC];  // read as float4 records
-  // |Q_d[e, ab]| of the off-diagonal column records and sum_d sum_m |R_dm|^2
-  // (64-sample screening bound)
-  float qabs[GEN ? 1 : TEV * MAXD * NPAIR];
-  float qsum[GEN ? 1 : TEV];
   double lwe[GEN ? TEV : 1];
   float2 ph[7 * MAXPHI];
   float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
@@ -116,24 +112,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
       : "r"(taddr));
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-// One candidate of the 64-sample screen, out of line (the few pairs that pass
-// the cheap bound; keeps the registers of the hot pass free): the exact bound
-// of pair_bound, then max_o ln L^ML_o if that bound reaches both the threshold
-// and the thread's best so far.  Returns -2 when the pair is not evaluated.
-template <int HH>
-static __device__ __noinline__ float screen_candidate(float z0r, float z0i, float z1r, float z1i, float z2r,
-                                                      float z2i, float z3r, float z3i, const float *mrow,
-                                                      const float *qrec, const EpiParams &P, const float2 *ph,
-                                                      float thr, float best, int &argo) {
-  const float Zr[MAXM] = {z0r, z1r, z2r, z3r}, Zi[MAXM] = {z0i, z1i, z2i, z3i};
-  float C0, Cr[3], Ci[3];
-  hh_tile<HH>(mrow, qrec, P, C0, Cr, Ci);
-  const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
-  argo = 0;
-  if (!(bound >= thr) || bound < best) return -2.f;
-  return pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, ph, argo);
 }
 
 // Work item w -> (event k, tile it, et): entry w of the device list, or the
@@ -337,9 +315,7 @@ __global__ void __launch_bounds__(NT, 1)
     const EpiParams &P = (NB == 1) ? Bt.w[0].P : T.ep;
     bool store = false;
     float zs = 1.f;
-    // row record floats in registers (the 64-sample screen keeps only what its
-    // cheap bound needs: the diagonal overlaps and the off-diagonal moduli)
-    constexpr int NREC = (TEV == 64) ? 1 : ((HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC);
+    constexpr int NREC = (HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC;  // row record floats in registers
     float mrec[NREC];
 
     double lwi = 0.0;
@@ -372,7 +348,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int64_t i = (int64_t)it * TI + row;
       const bool vi = i < P.n_int;
       const int64_t e0 = (int64_t)et * TEV;
-      if (TEV == 32 && it != cur_it) {
+      if (it != cur_it) {
 #pragma unroll
         for (int k = 0; k < NREC; ++k) mrec[k] = 0.f;
         if constexpr (HH == 2) {
@@ -390,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1)
                   if (4 * v + c < REC_POL) mrec[d * REC_POL + 4 * v + c] = xs4[c];
               }
             }
-        } else if constexpr (TEV == 32) {
+        } else {
           const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
 #pragma unroll
           for (int k = 0; k < MAXD * REC / 4; ++k) {
@@ -409,69 +385,22 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if constexpr (TcTail::GEN)
         for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
-      if constexpr (!TcTail::GEN)
-        for (int k = etid; k < TEV * MAXD * NPAIR; k += EPT) {
-          const int e = k / (MAXD * NPAIR), r = k % (MAXD * NPAIR), d = r / NPAIR, q = r % NPAIR;
-          float v = 0.f;
-          if (e0 + e < P.n_ext && d < P.n_det) {
-            const float *src = P.qx + ((e0 + e) * P.n_det + d) * REC + 4 + 2 * q;
-            const float x = __ldg(src), y = __ldg(src + 1);
-            v = sqrtf(x * x + y * y);
-          }
-          T.qabs[k] = v;
-        }
-      if constexpr (!TcTail::GEN)
-        for (int k = etid; k < TEV; k += EPT) {
-          float v = 0.f;
-          if (e0 + k < P.n_ext)
-            for (int d = 0; d < P.n_det; ++d)
-              for (int m = 0; m < MAXM; ++m) v += __ldg(P.qx + ((e0 + k) * P.n_det + d) * REC + m);
-          T.qsum[k] = v;
-        }
       named_bar_sync(1, EPT);
       float thr = tile_threshold(P);
-      // 64-sample screen: a lower bound of <h|h> at every phase for each of the
-      // thread's pairs, formed while the MMAs of the tile run (Eq. hh_ieo):
-      // <h|h>(phi) >= C_0 - 2 sum_delta |C_delta|
-      //   >= sum_d [sum_m <h_m|h_m>_d |R_dm|^2 - 2 sum_{a>b} |<h_a|h_b>_d| |R_da R_db^*|]
+      // 64-sample screen: for each of the thread's pairs the lower bound of
+      // <h|h> at every phase that pair_bound uses, C_0 - 2 sum_delta |C_delta|
+      // (Eq. hh_ieo), formed while the MMAs of the tile run
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
-        // detector by detector: the row's diagonal overlaps and off-diagonal
-        // moduli (read again for every tile, so that nothing of them stays live
-        // through the candidates), against every pair's column record
 #pragma unroll
-        for (int j = 0; j < EHALF; ++j) hl[j] = 0.f;
-        float rmax = 0.f;
+        for (int j = 0; j < EHALF; ++j) {
+          float C0, Cr[3], Ci[3];
+          hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
+          float h = C0;
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-          if (d < P.n_det) {
-            const float *src = P.mx + (i * P.n_det + d) * REC;
-            float rd[MAXM], ro[NPAIR];
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              rd[m] = vi ? __ldg(src + m) : 0.f;
-              rmax = fmaxf(rmax, rd[m]);
-            }
-#pragma unroll
-            for (int q = 0; q < NPAIR; ++q) {
-              const float x = vi ? __ldg(src + 4 + 2 * q) : 0.f, y = vi ? __ldg(src + 5 + 2 * q) : 0.f;
-              ro[q] = -2.f * sqrtf(x * x + y * y);
-            }
-#pragma unroll
-            for (int j = 0; j < EHALF; ++j) {
-              const int el = half * EHALF + j;
-              const float4 q = *reinterpret_cast<const float4 *>(&T.qs[el * MAXD * REC + d * REC]);
-              float h = fmaf(rd[0], q.x, fmaf(rd[1], q.y, fmaf(rd[2], q.z, fmaf(rd[3], q.w, hl[j]))));
-#pragma unroll
-              for (int q2 = 0; q2 < NPAIR; ++q2) h = fmaf(ro[q2], T.qabs[(el * MAXD + d) * NPAIR + q2], h);
-              hl[j] = h;
-            }
-          }
+          for (int q = 0; q < 3; ++q) h -= 2.f * sqrtf(Cr[q] * Cr[q] + Ci[q] * Ci[q]);
+          hl[j] = h;
         }
-        // FP32 rounding of the sums (terms up to rmax |R|^2 each): keep the bound
-        // below the exact value
-#pragma unroll
-        for (int j = 0; j < EHALF; ++j) hl[j] -= 1e-5f * rmax * T.qsum[half * EHALF + j];
       }
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
       tc_fence_after();
@@ -502,10 +431,10 @@ __global__ void __launch_bounds__(NT, 1)
           if (lane == 0) mbar_arrive(&T.tempty[0]);
           best = (vi && sx == sx) ? fabsf(sx) : -1.f;
         } else {
-          // Pass 1 (the accumulators read 16 columns at a time): a pair can reach
-          // ln L^ML >= thr only if (sum_m |Z_m|)^2 >= dh^2 reaches 2 thr hl
-          // (Eq. bestfit_lnl with hl <= <h|h>); those are the candidates.
-          const float cm = zs * zs * 1.0001f;
+          // Pass 1 (the accumulators read 16 columns at a time): the bound of
+          // pair_bound, (sum_m |Z_m|)^2 / (2 hl), against the threshold; the
+          // pairs that reach it are the candidates.
+          const float cm = zs * zs * 1.000001f;
           uint32_t cand = 0;
 #pragma unroll
           for (int g = 0; g < EHALF / 8; ++g) {
@@ -525,16 +454,15 @@ __global__ void __launch_bounds__(NT, 1)
             for (int q = 0; q < 8; ++q) {
               const int j = 8 * g + q;
               const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
-              const bool reject = thr > 0.f && hl[j] > 0.f && cm * a[q] * a[q] < 2.f * thr * hl[j];
+              const bool reject = hl[j] > 0.f && cm * a[q] * a[q] < 2.f * thr * hl[j];
               if (valid && !reject) cand |= 1u << j;
             }
           }
           // Pass 2: candidates in index order (the warp takes the lowest pending
-          // pair of its lanes at a time): the exact bound of pair_bound, then the
-          // phase grid where it can still reach the threshold and the thread's
-          // best; the threshold follows the running maximum, raised by every pair
-          // evaluated here (a lower bound of the final threshold throughout).
-          const float *mrow = P.mx + i * P.n_det * REC;
+          // pair of its lanes at a time): the phase grid where the pair's bound
+          // still reaches the threshold and the thread's best.  The threshold
+          // follows the running maximum, raised by every pair evaluated here (a
+          // lower bound of the final threshold throughout).
           float pushed = 0.f;
 #pragma unroll 1
           while (__any_sync(0xffffffffu, cand != 0u)) {
@@ -551,11 +479,17 @@ __global__ void __launch_bounds__(NT, 1)
             }
             tmem_ld_wait();
             if (mine) {
-              int argo;
-              const float ml = screen_candidate<HH>(Zr[0] * zs, Zi[0] * zs, Zr[1] * zs, Zi[1] * zs, Zr[2] * zs,
-                                                    Zi[2] * zs, Zr[3] * zs, Zi[3] * zs, mrow,
-                                                    &T.qs[el * MAXD * REC], P, T.ph, thr, best, argo);
-              if (ml > -2.f) {
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) {
+                Zr[m] *= zs;
+                Zi[m] *= zs;
+              }
+              float C0, Cr[3], Ci[3];
+              hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+              const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
+              if (bound >= thr && !(bound < best)) {
+                int argo;
+                const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
                 const long long gidx = (i * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
                 if (ml > best || (ml == best && gidx < barg)) {
                   best = ml;
