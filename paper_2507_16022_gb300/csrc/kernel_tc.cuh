@@ -140,20 +140,16 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
     k = lo;
   }
   const TcEvent &W = Bt.w[k];
-  if (RS == 1) {
-    super_tile(w - Bt.begin[k], W.n_itile, W.n_etile, W.band, it, et);
-  } else {
-    const int nw = (W.n_etile + RS - 1) / RS, bw = W.band / RS;
-    const int np = tc_pilot_tiles(W, TEV);
-    int local = w - Bt.begin[k];
-    if (local < np) {
-      // pilot tile: bank tiles evenly spread, extrinsic tiles scrambled
-      it = (int)(((long long)local * W.n_itile) / np);
-      et = (int)(((unsigned long long)local * 2654435761ull) % (unsigned long long)nw);
-      return;
-    }
-    super_tile(local - np, W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
+  const int nw = (W.n_etile + RS - 1) / RS, bw = W.band / RS;
+  const int np = tc_pilot_tiles(W, TEV);
+  const int local = w - Bt.begin[k];
+  if (local < np) {
+    // pilot tile: bank tiles evenly spread, extrinsic tiles scrambled
+    it = (int)(((long long)local * W.n_itile) / np);
+    et = (int)(((unsigned long long)local * 2654435761ull) % (unsigned long long)nw);
+    return;
   }
+  super_tile(local - np, W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
 }
 
 template <bool BF16, int HH, bool SPLIT, int NB, bool SEP, int TEV>
@@ -390,9 +386,11 @@ __global__ void __launch_bounds__(NT, 1)
       // 64-sample screen: for each of the thread's pairs the lower bound of
       // <h|h> at every phase that pair_bound uses, C_0 - 2 sum_delta |C_delta|
       // (Eq. hh_ieo), formed while the MMAs of the tile run
+      // (a rolled loop into a per-thread array that lives in local memory: small
+      // code, no register pressure, read back once per pair in pass 1)
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < EHALF; ++j) {
           float C0, Cr[3], Ci[3];
           hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);

@@ -316,14 +316,15 @@ struct SampleArgs {
 void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cdf, int64_t *i_out, int64_t *e_out,
                    int32_t *o_out, double *d_out, cudaStream_t st);
 
-// Pilot tiles of a 64-sample screening launch (cut on): a spread-out 1/48 of
-// the event's work tiles is screened first, so that the running maximum, and
-// with it the cut's threshold, is near its final value before the bulk of the
-// tiles (which then skip almost every pair on the cheap bound) is screened.
+// Pilot tiles of a screening launch (cut on, grid order): a spread-out 1/48
+// of the event's work tiles is screened first, so that the running maximum,
+// and with it the cut's threshold, is near its final value before the bulk of
+// the tiles (which then skip almost every pair on their bounds) is screened.
 // The pilot tiles are screened again in their place in the band order.
 __host__ __device__ inline int tc_pilot_tiles(const TcEvent &w, int tev) {
-  if (tev != 64 || !w.P.screen_ml || w.P.gemm_only || w.P.cut_delta <= 0.f) return 0;
-  const int t = w.n_itile * ((w.n_etile + 1) / 2);
+  if (!w.P.screen_ml || w.P.gemm_only || w.P.cut_delta <= 0.f || w.P.lnl_tile) return 0;
+  const int rs = tev / TC_TE;
+  const int t = w.n_itile * ((w.n_etile + rs - 1) / rs);
   return t >= 96 ? t / 48 : 0;
 }
 
