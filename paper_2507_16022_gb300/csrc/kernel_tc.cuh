@@ -102,6 +102,12 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
   b = __uint_as_float(r1);
 }
 
+// An upper bound of sqrt(x) for x >= 0 from the approximate reciprocal square
+// root (a few ulp; the factor covers it): bounds only, never values.
+__device__ __forceinline__ float sqrt_up(float x) {
+  return x > 0.f ? x * rsqrtf(x) * 1.000002f : 0.f;
+}
+
 // 32 lanes x 32-bit, 16 consecutive columns per thread (column a multiple of 16).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -390,14 +396,16 @@ __global__ void __launch_bounds__(NT, 1)
       // code, no register pressure, read back once per pair in pass 1)
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
+        if (!P.gemm_only) {
 #pragma unroll 1
-        for (int j = 0; j < EHALF; ++j) {
-          float C0, Cr[3], Ci[3];
-          hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
-          float h = C0;
+          for (int j = 0; j < EHALF; ++j) {
+            float C0, Cr[3], Ci[3];
+            hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
+            float h = C0;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) h -= 2.f * sqrtf(Cr[q] * Cr[q] + Ci[q] * Ci[q]);
-          hl[j] = h;
+            for (int q = 0; q < 3; ++q) h -= 2.f * sqrt_up(Cr[q] * Cr[q] + Ci[q] * Ci[q]);
+            hl[j] = h;
+          }
         }
       }
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
@@ -440,14 +448,21 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
             for (int q = 0; q < 8; ++q) a[q] = 0.f;
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m)
-              if (m < M) {
-                float v[16];
-                tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v);
-                tmem_ld_wait();
+            for (int m0 = 0; m0 < MAXM; m0 += 2) {
+              // two modes per wait
+              float v[2][16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) a[q] += sqrtf(fmaf(v[2 * q], v[2 * q], v[2 * q + 1] * v[2 * q + 1]));
-              }
+              for (int m = m0; m < m0 + 2; ++m)
+                if (m < M) tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v[m - m0]);
+              tmem_ld_wait();
+#pragma unroll
+              for (int m = m0; m < m0 + 2; ++m)
+                if (m < M) {
+#pragma unroll
+                  for (int q = 0; q < 8; ++q)
+                    a[q] += sqrt_up(fmaf(v[m - m0][2 * q], v[m - m0][2 * q], v[m - m0][2 * q + 1] * v[m - m0][2 * q + 1]));
+                }
+            }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int j = 8 * g + q;
