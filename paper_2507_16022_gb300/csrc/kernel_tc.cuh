@@ -381,9 +381,16 @@ __global__ void __launch_bounds__(NT, 1)
         lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
         cur_it = it;
       }
-      for (int k = etid; k < TEV * P.n_det * REC; k += EPT) {
-        const int e = k / (P.n_det * REC), qq = k % (P.n_det * REC);
-        T.qs[e * MAXD * REC + qq] = (e0 + e < P.n_ext) ? __ldg(P.qx + (e0 + e) * P.n_det * REC + qq) : 0.f;
+      // column records of the tile's samples, a float4 at a time (compile-time
+      // divisors; detectors beyond n_det are never read)
+      for (int f = etid; f < TEV * MAXD * (REC / 4); f += EPT) {
+        const int e = f / (MAXD * (REC / 4)), r = f % (MAXD * (REC / 4)), d = r / (REC / 4), v = r % (REC / 4);
+        if (d < P.n_det) {
+          float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (e0 + e < P.n_ext)
+            x = __ldg(reinterpret_cast<const float4 *>(P.qx + ((e0 + e) * P.n_det + d) * REC) + v);
+          *reinterpret_cast<float4 *>(&T.qs[(e * MAXD + d) * REC + 4 * v]) = x;
+        }
       }
       if constexpr (TcTail::GEN)
         for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
