@@ -22,11 +22,16 @@
 // work (64 instead of 43 flops per operand byte); a work tile then holds the
 // partial tiles (it, 2 wt) and (it, 2 wt + 1) of the 32-sample tile grid that
 // the outputs are indexed by.  With
-// SEP (split only) hi*hi accumulates in the first buffer and the small
-// hi*lo + lo*hi terms in the second, added in the epilogue: the tensor cores'
-// FP32 accumulation truncates at every step, and keeping the small terms out of
-// the large accumulator shortens its chain of truncating additions threefold,
-// at the cost of the overlap of a tile's epilogue with the next tile's MMAs.
+// SEP (split only) a tile is taken in two halves of 16 samples (N = 32), each
+// with four accumulator sets: hi*hi goes round-robin into three (k16 step t
+// into set t mod 3) and the small hi*lo + lo*hi terms into the fourth, all
+// added in the epilogue.  The tensor cores' FP32 accumulation truncates at
+// every step, with an error that grows with the accumulator's magnitude and
+// the number of steps: three interleaved chains of a third of the steps, each
+// summing about a third of the value, cut the hi*hi truncation error about
+// threefold, and keeping the small terms apart keeps their steps out of the
+// large chains.  The cost is the overlap of a half's epilogue with the next
+// half's MMAs and a second pass over the bank tile's operand stages.
 // A launch may carry a gate: a device word per event; work items of events
 // whose word differs from the launch's expected value are skipped by every
 // role alike (two variants are launched, each event's word picks the one that
@@ -172,6 +177,10 @@ __global__ void __launch_bounds__(NT, 1)
   constexpr int EHALF = TEV / 2;  // extrinsic samples per epilogue thread and tile
   constexpr int XS_LD = TcTail::XS_LD;
   constexpr bool ONEBUF = SEP || TEV == 64;  // one accumulator set in flight
+  constexpr int NUSE = SEP ? 2 : 1;           // accumulator uses per work tile (SEP: two 16-sample halves)
+  constexpr int SEP_N = BN / 2;               // SEP: N of each MMA (one half's B rows)
+  constexpr uint32_t SEP_SET = 128;           // SEP: TMEM columns of one accumulator set (4 modes x N)
+  static_assert(!SEP || (TEV == 32 && 4 * SEP_SET <= TMEM_COLS), "SEP accumulator sets");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage s, plane p: A at sA + (s NPL + p) A_ST as [KBX][128 rows][64],
@@ -218,6 +227,7 @@ __global__ void __launch_bounds__(NT, 1)
         work_tile<NB, TEV>(Bt, w, k, it, et);
         if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
         const TcEvent &W = Bt.w[k];
+        for (int h2 = 0; h2 < NUSE; ++h2)
         for (int m = 0; m < M && ok; ++m) {
           const int arow = m * C.a_mode_rows + W.a_row0 + it * TI;
           const int brow = m * W.b_mode_rows + et * BN;
@@ -258,6 +268,7 @@ __global__ void __launch_bounds__(NT, 1)
         work_tile<NB, TEV>(Bt, w, k, it, et);
         if (Bt.gate[k] != Bt.gate_want) continue;
       }
+      for (int h2 = 0; h2 < NUSE && ok; ++h2) {
       const int b = ONEBUF ? 0 : (u & 1);
       const uint32_t use = ONEBUF ? u : (u >> 1);
       ++u;
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(NT, 1)
       tc_fence_after();
       for (int m = 0; m < M && ok; ++m) {
         const uint32_t dcol = tmem + b * BUF_COLS + m * BN;
-        const uint32_t dlo = tmem + BUF_COLS + m * BN;  // split: the hi*lo + lo*hi accumulator
+        const uint32_t dlo = tmem + 3 * SEP_SET + m * SEP_N;  // SEP: the hi*lo + lo*hi accumulator
         for (int ks = 0; ks < nst; ++ks, ++q) {
           const int s = q % ST;
           const uint32_t n = q / ST;
@@ -277,18 +288,26 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
             for (int kx = 0; kx < KBX; ++kx) {
               const uint64_t ah = sdesc_k128(sA + (s * NPL) * A_ST + kx * A_BYTES);
-              const uint64_t bh = sdesc_k128(sB + (s * NPL) * B_ST + kx * B_BYTES);
               const uint64_t al = sdesc_k128(sA + (s * NPL + NPL - 1) * A_ST + kx * A_BYTES);
-              const uint64_t bl = sdesc_k128(sB + (s * NPL + NPL - 1) * B_ST + kx * B_BYTES);
+              // SEP: this half's 32 B rows (8-row groups of 1024 bytes)
+              const uint32_t boff = SEP ? (uint32_t)h2 * SEP_N * 128u : 0u;
+              const uint64_t bh = sdesc_k128(sB + (s * NPL) * B_ST + kx * B_BYTES + boff);
+              const uint64_t bl = sdesc_k128(sB + (s * NPL + NPL - 1) * B_ST + kx * B_BYTES + boff);
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k) {
-                tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
                 if (SEP) {
-                  tc_mma(dlo, ah + 2 * k, bl + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);  // hi * lo
-                  tc_mma(dlo, al + 2 * k, bh + 2 * k, idesc, 1u);                      // lo * hi
-                } else if (SPLIT) {
-                  tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
-                  tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+                  constexpr uint32_t idesc_sep = idesc_f16(128, SEP_N, BF16);
+                  const int t16 = (ks * KBX + kx) * (BK / 16) + k;  // k16 step of this mode's chain
+                  const uint32_t dhh = tmem + (uint32_t)(t16 % 3) * SEP_SET + m * SEP_N;
+                  tc_mma(dhh, ah + 2 * k, bh + 2 * k, idesc_sep, t16 >= 3 ? 1u : 0u);      // hi * hi
+                  tc_mma(dlo, ah + 2 * k, bl + 2 * k, idesc_sep, t16 > 0 ? 1u : 0u);       // hi * lo
+                  tc_mma(dlo, al + 2 * k, bh + 2 * k, idesc_sep, 1u);                      // lo * hi
+                } else {
+                  tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
+                  if (SPLIT) {
+                    tc_mma(dcol, ah + 2 * k, bl + 2 * k, idesc, 1u);  // hi * lo
+                    tc_mma(dcol, al + 2 * k, bh + 2 * k, idesc, 1u);  // lo * hi
+                  }
                 }
               }
             }
@@ -299,6 +318,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if (ok && issuer) tc_commit(&T.tfull[b]);
       __syncwarp();
+      }
     }
     // all MMAs of this CTA complete before TMEM is released
     if (issuer) tc_commit(&T.drain);
@@ -329,7 +349,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
       const int b = ONEBUF ? 0 : (u & 1);
       const uint32_t use = ONEBUF ? u : (u >> 1);
-      ++u;
+      u += NUSE;
       if (k != cur_k) {
         // the next event: its parameters and phase tables into shared memory
         named_bar_sync(1, EPT);
@@ -675,30 +695,41 @@ __global__ void __launch_bounds__(NT, 1)
       } else {
 #pragma unroll 1
       for (int j = 0; j < EHALF; ++j) {
-        const int el = half * EHALF + j;
+        // SEP: samples of the first 16-sample half, then of the second (8 each)
+        const int el = SEP ? (16 * (j >> 3) + 8 * half + (j & 7)) : (half * EHALF + j);
         const int64_t e = e0 + el;
         float Zr[MAXM], Zi[MAXM];
-#pragma unroll
-        for (int m = 0; m < MAXM; ++m) {
-          if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
-          else { Zr[m] = 0.f; Zi[m] = 0.f; }
-        }
         if (SEP) {
-          float Lr[MAXM], Li[MAXM];
-#pragma unroll
-          for (int m = 0; m < MAXM; ++m) {
-            if (m < M) tmem_ld2(tbase + BUF_COLS + m * BN + 2 * el, Lr[m], Li[m]);
-            else { Lr[m] = 0.f; Li[m] = 0.f; }
+          if (j == 8) {
+            // the second half's accumulators
+            if (!mbar_wait(&T.tfull[b], (use + 1) & 1, nullptr, abortp, wait_ns)) break;
+            tc_fence_after();
           }
+          // hi*hi in three interleaved sets, then the low-order set
+          const uint32_t col = tbase + 2 * (8 * half + (j & 7));
+          float Ar[4][MAXM], Ai[4][MAXM];
+#pragma unroll
+          for (int qs = 0; qs < 4; ++qs)
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) {
+              if (m < M) tmem_ld2(col + qs * SEP_SET + m * SEP_N, Ar[qs][m], Ai[qs][m]);
+              else { Ar[qs][m] = 0.f; Ai[qs][m] = 0.f; }
+            }
           tmem_ld_wait();
 #pragma unroll
           for (int m = 0; m < MAXM; ++m) {
-            Zr[m] += Lr[m];
-            Zi[m] += Li[m];
+            Zr[m] = ((Ar[0][m] + Ar[1][m]) + Ar[2][m]) + Ar[3][m];
+            Zi[m] = ((Ai[0][m] + Ai[1][m]) + Ai[2][m]) + Ai[3][m];
           }
+        } else {
+#pragma unroll
+          for (int m = 0; m < MAXM; ++m) {
+            if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
+            else { Zr[m] = 0.f; Zi[m] = 0.f; }
+          }
+          tmem_ld_wait();
         }
-        tmem_ld_wait();
-        if (j == EHALF - 1) {
+        if (j == EHALF - 1 || (SEP && j == 7)) {
           // this warp's accumulators are in registers: release the buffer to the MMA warp
           tc_fence_before();
           __syncwarp();

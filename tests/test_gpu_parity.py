@@ -1,20 +1,22 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances (per pair, on ln Lbar_ie and max_o ln L^ML_ie):
-  fp32, bf16x3 : |d| <= 1e-3                       (the split-precision bound)
-  fp16, bf16   : |d| <= 2e-2 + 4 u max(ln L^ML, 0),  u = 2^-11 (fp16), 2^-9 (bf16)
-A single-pass format rounds both GEMM operands to precision u, so each product
+  fp32, bf16x3, fp16x3 : |d| <= 1e-3    (the split-precision bound)
+  mixed (the served path: fp16 screen + fp16x3 refinement): pairs within 30 of
+         the maximum ln L^ML (which lie in refined tiles) meet 1e-3, the others
+         the fp16 error model below; ln Z meets 1e-2.
+  ln Z : |d| <= 1e-2 for fp32, bf16x3, fp16x3 and mixed.
+Single pass (fp16, bf16: not served precisions).  A single-pass format rounds
+both GEMM operands to precision u (2^-11 fp16, 2^-9 bf16), so each product
 h G carries a relative error up to 2u and, by Cauchy-Schwarz,
 |d<d|h>| <= 2u sqrt(<h|h><d|d>).  ln L^ML = <d|h>^2 / 2<h|h> then moves by up to
 2u |x| sqrt(<d|d>) with |x| = sqrt(2 ln L^ML) (plus 4u ln L^ML when the
-products add coherently); the single-pass bound used is
-  2e-2 + 4u ln L^ML + 2u sqrt(2 ln L^ML + 1) sqrt(<d|d>).
-A flat 2e-2 is out of reach for bf16 at SNR 15: the noise power <d|d> ~ 2 B D
-enters every pair.
-ln Z: |d| <= 1e-2 for fp32, bf16x3 and fp16x3.
-mixed (fp16 screen + fp16x3 refinement): pairs within 30 of the maximum ln L^ML
-(which lie in refined tiles) meet the split bound, the others the fp16 bound;
-ln Z meets 1e-2.
+products add coherently).  These runs are checked against that error model,
+  2e-2 + 4u ln L^ML + 2u sqrt(2 ln L^ML + 1) sqrt(<d|d>),
+which is an error model and not a target: bf16 x 1 misses the flat 2e-2 per
+pair (and 1e-2 in ln Z) that the target sets for BF16 at SNR 15, because the
+noise power <d|d> ~ 2 B D enters every pair; test_bf16_single_pass_flat_bound
+records that miss (strict xfail), and no served path runs bf16 x 1.
 """
 import math
 
@@ -159,6 +161,24 @@ def test_config1_all_pairs(dpx, cfg1, precision):
     assert got["ev"]["n_marginalised"] == ref_ev["n_marginalised"]
 
 
+@pytest.mark.xfail(strict=True, reason="single-pass bf16 misses the flat 2e-2 per pair and 1e-2 in ln Z at "
+                                       "SNR 15 (operand rounding 2^-9 against <d|d> ~ 2 B D); not a served "
+                                       "precision")
+def test_bf16_single_pass_flat_bound(dpx, cfg1):
+    """The target's flat BF16 bound, |d ln L| <= 2e-2 per pair and |d ln Z| <= 1e-2,
+    applied to bf16 x 1 at configuration 1: expected to fail (see the module
+    docstring); the split and mixed paths are the ones that meet their bounds."""
+    dp, ctx = dpx
+    wl, P, grid, ref_ev = cfg1
+    got = run(dp, ctx, wl, "bf16")
+    d1 = np.abs(got["lnl"].astype(np.float64) - grid["lnl_marg"])
+    d2 = np.abs(got["ml"].astype(np.float64) - grid["lnl_ml_max"])
+    print(f"bf16 x 1 at configuration 1: max |d ln Lbar| {d1.max():.3e}, max |d ln L^ML| {d2.max():.3e}, "
+          f"|d ln Z| {abs(got['ev']['ln_z'] - ref_ev['ln_z']):.3e}")
+    assert d1.max() <= 2e-2 and d2.max() <= 2e-2
+    assert abs(got["ev"]["ln_z"] - ref_ev["ln_z"]) <= 1e-2
+
+
 def test_config1_ml_cut(dpx, cfg1):
     """Eq. coherent_ML_selection with the paper's delta = 20.  The device uses a
     running maximum, so it keeps a superset of the exact cut: its ln Z lies
@@ -297,30 +317,49 @@ def cfg2():
 
 
 def test_config2_sampled_pairs_and_evidence(dpx, cfg2):
+    """Configuration 2 against the oracle on a seeded 1% (i, e) subsample
+    (2,684,355 pairs, plus the peak pair), element by element, in every
+    precision."""
     import oracle
     dp, ctx = dpx
     wl = cfg2
     I, E = wl.bank.h.shape[0], wl.ext.t.shape[0]
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
     try:
-        pi, pe = synth.pair_subsample(2, I, E, n_max=12000)
+        pi, pe = synth.pair_subsample(2, I, E, frac=0.01)
+        assert pi.shape[0] == round(0.01 * I * E)
         # include the best pairs: the oracle's max must agree where it matters most
         P = oracle.OracleProblem(wl.bank, wl.ext, wl.event)
         res = {}
-        for precision in ("fp32", "bf16x3", "bf16", "mixed"):
-            res[precision] = run(dp, ctx, wl, precision, bid=bid)
-        i_s, e_s = res["bf16x3"]["ev"]["arg_i"], res["bf16x3"]["ev"]["arg_e"]
-        pi = np.concatenate([pi, [i_s]])
-        pe = np.concatenate([pe, [e_s]])
+        for precision in ("fp32", "bf16x3", "fp16x3", "bf16", "mixed"):
+            got = run(dp, ctx, wl, precision, bid=bid)
+            if precision == "fp32":
+                i_s, e_s = got["ev"]["arg_i"], got["ev"]["arg_e"]
+                pi = np.concatenate([pi, [i_s]])
+                pe = np.concatenate([pe, [e_s]])
+            # keep the sampled pairs only (the full [I][E] arrays are 1 GB each)
+            if precision == "bf16x3":
+                got["lnl_full"] = got["lnl"]
+            else:
+                got["lnl"] = got["lnl"][pi, pe]
+                got["ml"] = got["ml"][pi, pe]
+            res[precision] = got
         ref = P.eval_pairs(pi, pe)
         for precision, got in res.items():
-            sub = {"lnl": got["lnl"][pi, pe], "ml": got["ml"][pi, pe]}
+            if precision == "bf16x3":
+                sub = {"lnl": got["lnl"][pi, pe], "ml": got["ml"][pi, pe]}
+            else:
+                sub = {"lnl": got["lnl"], "ml": got["ml"]}
             check_pairs(sub, ref, precision, data_norm(wl))
+            if precision in ("fp32", "bf16x3", "fp16x3", "mixed"):
+                d = np.abs(sub["ml"].astype(np.float64) - ref["lnl_ml_max"])
+                print(f"config 2 {precision}: {pi.shape[0]} pairs, max |d ln L^ML| {d.max():.2e}")
         # evidence: served split precision against the plain FP32 path (same GPU)
         assert abs(res["bf16x3"]["ev"]["ln_z"] - res["fp32"]["ev"]["ln_z"]) <= 1e-2
         assert abs(res["mixed"]["ev"]["ln_z"] - res["fp32"]["ev"]["ln_z"]) <= 1e-2
+        assert abs(res["fp16x3"]["ev"]["ln_z"] - res["fp32"]["ev"]["ln_z"]) <= 1e-2
         # the FP64 reduction reproduces a direct FP64 log-sum-exp of the stored ln Lbar_ie
-        lnl = res["bf16x3"]["lnl"].astype(np.float64)
+        lnl = res["bf16x3"]["lnl_full"].astype(np.float64)
         lw = wl.bank.ln_w[:, None] + wl.ext.ln_w[None, :]
         x = (lnl + lw).ravel()
         m = x.max()
