@@ -266,10 +266,9 @@ def test_batch_with_cut_matches_oracle(omix):
         for rep in range(2):
             ids = dp.dotpe_batch_submit(ctx, [dict(bank_id=bid, precision="mixed", cut_delta=20.0, **sp)
                                               for sp in specs])
-            for ev, ref in zip(collect(dp, ctx, ids), refs):
+            for ev, ref, sp in zip(collect(dp, ctx, ids), refs, specs):
                 check_cut_against_oracle(ev, ref)
-                i0 = specs[refs.index(ref)]["i0"]
-                assert (ev["arg_i"] - i0, ev["arg_e"], ev["arg_o"]) == tuple(ref["ev"]["arg"])
+                assert (ev["arg_i"] - sp["i0"], ev["arg_e"], ev["arg_o"]) == tuple(ref["ev"]["arg"])
         dp.dotpe_bank_release(ctx, bid)
     finally:
         dp.dotpe_destroy(ctx)
