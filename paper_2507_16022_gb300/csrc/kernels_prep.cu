@@ -299,21 +299,27 @@ __global__ void pack_G_kernel(int64_t E, int M, int B, int Kpad, int NP, const f
   const int c = (int)(k % P);
   const int64_t me = k / P;  // m * E + e
   const int64_t m = me / E, e = me - m * E;
-  const int64_t re = (2 * me) * Kpad, im = (2 * me + 1) * Kpad;
+  // element (part, column) of sample me: the 16-bit planes keep the two rows
+  // [2 me][Kpad] and [2 me + 1][Kpad] (tensor-core B rows); the FP32 operand of
+  // the CUDA-core kernel interleaves them, [me][Kpad][2] = (re row, im row) per column
+  auto at = [&](int part, int64_t col) -> int64_t {
+    if constexpr (sizeof(T) == 4) return (me * Kpad + col) * 2 + part;
+    else return (2 * me + part) * Kpad + col;
+  };
   if (c < B) {
     for (int q = 0; q < NP; ++q) {
       const float2 g = G[((m * NP + q) * E + e) * B + c];
       const float gr = g.x * sc, gi = g.y * sc;
       const int o = 2 * q * B;
-      put<T>(out, total, re + o + c, gr, nplanes);
-      put<T>(out, total, re + o + B + c, -gi, nplanes);
-      put<T>(out, total, im + o + c, gi, nplanes);
-      put<T>(out, total, im + o + B + c, gr, nplanes);
+      put<T>(out, total, at(0, o + c), gr, nplanes);
+      put<T>(out, total, at(0, o + B + c), -gi, nplanes);
+      put<T>(out, total, at(1, o + c), gi, nplanes);
+      put<T>(out, total, at(1, o + B + c), gr, nplanes);
     }
   }
   if (c < pad) {
-    put<T>(out, total, re + 2 * NP * B + c, 0.f, nplanes);
-    put<T>(out, total, im + 2 * NP * B + c, 0.f, nplanes);
+    put<T>(out, total, at(0, 2 * NP * B + c), 0.f, nplanes);
+    put<T>(out, total, at(1, 2 * NP * B + c), 0.f, nplanes);
   }
 }
 
