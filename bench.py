@@ -440,7 +440,7 @@ def bench_batch64(args, dp, ctx_factory, torch, dev, load_peaks_fn):
                                f"E in {{512,1024,2048,4096}}, D in {{2,3}} (mean {D_mean:.2f}), SNR U[8,40], "
                                f"N_phi={N_PHI}", "precision": args.precision, "ml_cut_delta": args.cut,
                    "pairs_per_step": pairs, "dlnz_vs_fp32_4_events": dlnz,
-                   "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                   "latency_ms_p50": pctl(lat, 0.50), "latency_ms_p99": pctl(lat, 0.99),
                    "graph": "each batch captured and replayed through the slot's executable graph"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                      "frac": achieved / sustained, "traffic": None,
@@ -1008,23 +1008,14 @@ def bench_samples(args, dp, ctx_factory, torch, dev):
     }
 
 
-def bench_serve(args, dp, ctx_factory, torch, dev):
-    """Poisson arrivals against resident banks; continuous batching at admission."""
-    import synth
-    banks, stream = synth.make_serving_stream(n_events=args.events, rate=args.rate, seed=5)
-    ctx = ctx_factory()
-    bids = {B: dp.dotpe_bank_load(ctx, b.h, b.f, b.w, b.mode_m, b.ln_w) for B, b in banks.items()}
-    # one untimed event per bank: kernels loaded, tables warm
-    for B, b in banks.items():
-        a = next(x for x in stream if x.n_bins == B)
-        eid = dp.dotpe_event_submit(ctx, bids[B], a.i0, a.i1, a.event.psd, a.event.data, a.ext.t, a.ext.R,
-                                    a.ext.ln_w, n_phi=N_PHI, u_min=a.event.u_min, cut_delta=args.cut,
-                                    precision=args.precision)
-        dp.dotpe_event_wait(ctx, eid, 600.0)
-        dp.dotpe_event_release(ctx, eid)
-    sampler = make_clock_sampler(dev.index or 0)
-    sampler.start()
-    pending, lat, pairs, done_ns = {}, [], 0, []
+def run_stream(dp, ctx, bids, stream, precision, cut):
+    """Submits the stream's events at their arrival times (host inputs, copied
+    by each submission) and reaps them as they complete.  Returns per-event
+    latencies (completion - submission, ms, in stream order), the pairs, the
+    busy time (last completion - stream start, s), the wall time and the
+    evidence records."""
+    pending, lat, done_ns, evs = {}, {}, [], {}
+    pairs = 0
     t_start = time.perf_counter()
     t_start_ns = time.monotonic_ns()
 
@@ -1035,12 +1026,14 @@ def bench_serve(args, dp, ctx_factory, torch, dev):
                 if st not in (dp.DOTPE_STATE_DONE, dp.DOTPE_STATE_FAILED):
                     dp.dotpe_event_wait(ctx, eid, 600.0)
                     st, stats = dp.dotpe_event_poll(ctx, eid)
-                lat.append((stats["t_done_ns"] - stats["t_submit_ns"]) * 1e-6)
+                k = pending[eid]
+                lat[k] = (stats["t_done_ns"] - stats["t_submit_ns"]) * 1e-6
                 done_ns.append(stats["t_done_ns"])
+                evs[k] = dp.dotpe_evidence(ctx, eid)
                 dp.dotpe_event_release(ctx, eid)
                 del pending[eid]
 
-    for a in stream:
+    for k, a in enumerate(stream):
         while True:
             now = time.perf_counter() - t_start
             if now >= a.t:
@@ -1048,15 +1041,87 @@ def bench_serve(args, dp, ctx_factory, torch, dev):
             reap()
             time.sleep(min(0.002, a.t - now))
         eid = dp.dotpe_event_submit(ctx, bids[a.n_bins], a.i0, a.i1, a.event.psd, a.event.data, a.ext.t, a.ext.R,
-                                    a.ext.ln_w, n_phi=N_PHI, u_min=a.event.u_min, cut_delta=args.cut,
-                                    precision=args.precision)
-        pending[eid] = a
+                                    a.ext.ln_w, n_phi=N_PHI, u_min=a.event.u_min, cut_delta=cut,
+                                    precision=precision)
+        pending[eid] = k
         pairs += (a.i1 - a.i0) * a.ext.t.shape[0]
     reap(block=True)
     wall = time.perf_counter() - t_start
+    busy_s = (max(done_ns) - t_start_ns) * 1e-9
+    return [lat[k] for k in range(len(stream))], pairs, busy_s, wall, [evs[k] for k in range(len(stream))]
+
+
+def pctl(sorted_vals, q):
+    """The q-th percentile (nearest rank) of sorted values."""
+    return sorted_vals[min(len(sorted_vals) - 1, max(0, int(math.ceil(q * len(sorted_vals))) - 1))]
+
+
+def warm_banks(dp, ctx, bids, stream, precision, cut):
+    """One untimed event per bank: kernels loaded, tables warm."""
+    for B in bids:
+        a = next(x for x in stream if x.n_bins == B)
+        eid = dp.dotpe_event_submit(ctx, bids[B], a.i0, a.i1, a.event.psd, a.event.data, a.ext.t, a.ext.R,
+                                    a.ext.ln_w, n_phi=N_PHI, u_min=a.event.u_min, cut_delta=cut,
+                                    precision=precision)
+        dp.dotpe_event_wait(ctx, eid, 600.0)
+        dp.dotpe_event_release(ctx, eid)
+
+
+def served_leg(dp, create, n_events=120, rate=20.0, n_int=131072, n_fp32=20, cut=CUT_DELTA, max_batch=8):
+    """A bounded serving stream beside the single-event bench: Poisson arrivals
+    at `rate` per second, bank slices U[16K, n_int] of a resident n_int-row bank
+    per bin grid (B = 256 or 512), E U[1K, 8K], D in {2, 3}, SNR U[8, 50]
+    (the serving configuration's distributions with a smaller resident bank),
+    admitted by HBM footprint with continuous batching, in the served mixed
+    precision; then the first n_fp32 events of the same stream, with the same
+    arrival times, through the plain FP32 path."""
+    import synth
+    banks, stream = synth.make_serving_stream(n_events=n_events, rate=rate, seed=5, n_int=n_int,
+                                              slice_range=(16384, n_int))
+    ctx = create(max_batch)
+    try:
+        bids = {B: dp.dotpe_bank_load(ctx, b.h, b.f, b.w, b.mode_m, b.ln_w) for B, b in banks.items()}
+        warm_banks(dp, ctx, bids, stream, "mixed", cut)
+        lat, pairs, busy, wall, evs = run_stream(dp, ctx, bids, stream, "mixed", cut)
+        warm_banks(dp, ctx, bids, stream, "fp32", cut)
+        sub = stream[:n_fp32]
+        lat32, pairs32, busy32, _, evs32 = run_stream(dp, ctx, bids, sub, "fp32", cut)
+    finally:
+        dp.dotpe_destroy(ctx)
+    ls, ls32 = sorted(lat), sorted(lat32)
+    return {
+        "workload": f"{n_events} events, Poisson arrivals at {rate:g}/s, bank slices U[16K,{n_int // 1024}K] of a "
+                    f"resident {n_int // 1024}K-row bank per bin grid (B=256/512), E U[1K,8K], D in {{2,3}}, "
+                    f"SNR U[8,50], N_phi={N_PHI}, cut {cut:g}, continuous batching up to {max_batch}",
+        "precision": "mixed",
+        "pairs_per_s": pairs / busy,
+        "latency_ms_p50": pctl(ls, 0.50),
+        "latency_ms_p99": pctl(ls, 0.99),
+        "latency_ms_max": ls[-1],
+        "mean_pairs_per_event": pairs / len(stream),
+        "wall_s": wall,
+        "fp32_events": len(sub),
+        "fp32_pairs_per_s": pairs32 / busy32,
+        "fp32_latency_ms_p50": pctl(ls32, 0.50),
+        "fp32_latency_ms_p99": pctl(ls32, 0.99),
+        "mixed_latency_ms_p50_same_events": pctl(sorted(lat[:len(sub)]), 0.50),
+        "mixed_latency_ms_p99_same_events": pctl(sorted(lat[:len(sub)]), 0.99),
+        "dlnz_vs_fp32_max": max(abs(a["ln_z"] - b["ln_z"]) for a, b in zip(evs[:len(sub)], evs32)),
+    }
+
+
+def bench_serve(args, dp, ctx_factory, torch, dev):
+    """Poisson arrivals against resident banks; continuous batching at admission."""
+    import synth
+    banks, stream = synth.make_serving_stream(n_events=args.events, rate=args.rate, seed=5)
+    ctx = ctx_factory()
+    bids = {B: dp.dotpe_bank_load(ctx, b.h, b.f, b.w, b.mode_m, b.ln_w) for B, b in banks.items()}
+    warm_banks(dp, ctx, bids, stream, args.precision, args.cut)
+    sampler = make_clock_sampler(dev.index or 0)
+    sampler.start()
+    lat, pairs, busy_s, wall, _ = run_stream(dp, ctx, bids, stream, args.precision, args.cut)
     clocks = sampler.stop()
     lat.sort()
-    busy_s = (max(done_ns) - t_start_ns) * 1e-9
     mean_pairs = pairs / len(stream)
     line = {
         "metric": "(int x ext) lnL pairs/s", "value": pairs / busy_s, "unit": "pairs/s", "n_gpus": 1,
@@ -1067,7 +1132,7 @@ def bench_serve(args, dp, ctx_factory, torch, dev):
         "config": {"workload": f"serving loop: {len(stream)} events, Poisson arrivals at {args.rate:g}/s, bank slices "
                                f"U[16K,512K] of a resident 512K bank per bin grid (B=256/512), E U[1K,8K], D in {{2,3}}, "
                                f"SNR U[8,50], N_phi={N_PHI}", "precision": args.precision, "ml_cut_delta": args.cut,
-                   "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                   "latency_ms_p50": pctl(lat, 0.50), "latency_ms_p99": pctl(lat, 0.99),
                    "latency_ms_max": lat[-1], "mean_pairs_per_event": mean_pairs, "wall_s": wall,
                    "max_batch": args.max_batch, "slots": 4,
                    "note": "value = all pairs / (last completion - stream start); host inputs copied per event"},
@@ -1103,6 +1168,8 @@ def main():
     ap.add_argument("--with-rb", action="store_true",
                     help="presel: relative binning (weights from dotpe_rb_weights; with --precessing, FP32 only)")
     ap.add_argument("--max-batch", type=int, default=8, help="serve: continuous-batching limit")
+    ap.add_argument("--no-serve-leg", action="store_true",
+                    help="event: skip the bounded serving stream reported beside the single-event numbers")
     ap.add_argument("--narrow-tiles", action="store_true",
                     help="screening and GEMM-only launches in 32-sample tiles (DOTPE_CONFIG_NARROW_TILES)")
     args = ap.parse_args()
@@ -1316,6 +1383,9 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(wl)
+    served = None
+    if not args.no_serve_leg and world == 1:
+        served = served_leg(dp, lambda mb: dp.dotpe_create(local, max_batch=mb), cut=args.cut)
     lat_sorted = sorted(lat)
     line = {
         "metric": "(int x ext) lnL pairs/s",
@@ -1341,8 +1411,10 @@ def main():
             "fp32_path_ms_per_event": fp32_ms,
             "fp32_path_pairs_per_s": pairs / (fp32_ms * 1e-3),
             "latency_events": len(lat),
-            "latency_ms_p50": lat_sorted[len(lat) // 2],
-            "latency_ms_p99": lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "latency_ms_p50": pctl(lat_sorted, 0.50),
+            "latency_ms_p99": pctl(lat_sorted, 0.99),
+            "latency_note": "events submitted one after another from host memory, each waited for",
+            "served": served,
             "prep_ms": prep_ms,
             "fused_ms": fused_ms,
             "refine_ms": refine_ms if mixed else None,

@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define DOTPE_ABI_VERSION 5
+#define DOTPE_ABI_VERSION 6
 
 /* ---- status codes ------------------------------------------------------ */
 #define DOTPE_OK 0
@@ -481,6 +481,31 @@ int dotpe_rb_weights(dotpe_ctx *ctx, const dotpe_rb_desc *desc, double *w_dh, do
  * E_DEVICE. */
 int dotpe_preselect(dotpe_ctx *ctx, const dotpe_presel_desc *desc, float *lnl_ml, int32_t *arg_ot,
                     double *lnl_inco, int64_t *selected, dotpe_presel_out *out);
+
+/* ---- bank-sharded events ------------------------------------------------ */
+/* One event whose bank slice is split by rows into shards (e.g. one shard per
+ * GPU, each shard an event of its own over the same extrinsic samples): the
+ * paper's sums over i are plain sums (Eq. Z_sum; Eqs. posterior_element,
+ * int_ess, ext_ess), so the shards combine exactly, in FP64 on the host:
+ *   ln S1 = LSE_r [ln Z_r + ln(N_i,r N_e N_phi)],  ln Z = ln S1 - ln(N_i N_e N_phi),
+ *   sum p^2 and sum_i P_i^2 add over shards (recovered from each shard's N_eff
+ *   and N_eff,int), the per-sample marginals P_e add over shards (then
+ *   N_eff,ext = S1^2 / sum_e P_e^2), the maximum ln L^ML is the largest (lowest
+ *   (i, e, o) on ties).  Calls no CUDA function. */
+typedef struct dotpe_shard {
+  dotpe_evidence_out ev;   /* the shard's evidence (dotpe_evidence); arg_i in bank numbering */
+  int64_t n_int;           /* rows of the shard's slice */
+  const double *ln_p_ext;  /* [n_ext] host: the shard's per-sample marginals, ln sum_{i,o} w_i w_e Lbar_ieo
+                              (dotpe_lnl_blocks with DOTPE_COL_MARGINAL, widened to double) */
+} dotpe_shard;
+/* shards: n_shards >= 1 records over the same n_ext samples and n_phi phases.
+ * out: the event's evidence (n_marginalised and n_pairs summed; lnl_ml_threshold
+ * the largest of the shards'; device_status the first nonzero; n_refined_tiles
+ * summed, -1 if any shard has -1).  ln_p_ext_out: [n_ext] host or NULL, the
+ * event's per-sample marginals.  Errors: E_INVALID (null pointers, n_shards <
+ * 1, n_ext < 1, n_int < 1, n_phi < 1). */
+int dotpe_evidence_merge(int n_shards, const dotpe_shard *shards, int64_t n_ext, int n_phi,
+                         dotpe_evidence_out *out, double *ln_p_ext_out);
 
 /* ---- diagnostics ------------------------------------------------------- */
 /* Evaluates the device distance marginal ln Lbar(dh, hh) (Eq.

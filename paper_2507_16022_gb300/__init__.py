@@ -45,7 +45,7 @@ SYMBOLS = ("dotpe_create", "dotpe_destroy", "dotpe_strerror", "dotpe_last_error_
            "dotpe_lnl_blocks", "dotpe_event_release", "dotpe_dist_marg_eval",
            "dotpe_event_stream_wait", "dotpe_dist_marg_eval_noalloc", "dotpe_batch_submit",
            "dotpe_preselect", "dotpe_rb_weights", "dotpe_posterior_samples", "dotpe_bank_subset",
-           "dotpe_bank_save", "dotpe_bank_open")
+           "dotpe_bank_save", "dotpe_bank_open", "dotpe_evidence_merge")
 
 
 class DotpeError(RuntimeError):
@@ -117,6 +117,10 @@ class dotpe_evidence_out(ctypes.Structure):
                 ("n_refined_tiles", ctypes.c_int32)]
 
 
+class dotpe_shard(ctypes.Structure):
+    _fields_ = [("ev", dotpe_evidence_out), ("n_int", ctypes.c_int64), ("ln_p_ext", ctypes.POINTER(ctypes.c_double))]
+
+
 _lib = None
 
 
@@ -158,6 +162,8 @@ def load(path: str = LIB_PATH):
                              ctypes.POINTER(dotpe_presel_out)], ctypes.c_int),
         "dotpe_rb_weights": ([vp, ctypes.POINTER(dotpe_rb_desc), vp, vp], ctypes.c_int),
         "dotpe_posterior_samples": ([vp, ctypes.c_uint64, ctypes.c_int64, vp, vp, vp, vp, vp], ctypes.c_int),
+        "dotpe_evidence_merge": ([ctypes.c_int, ctypes.POINTER(dotpe_shard), ctypes.c_int64, ctypes.c_int,
+                                  ctypes.POINTER(dotpe_evidence_out), vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -355,6 +361,26 @@ def dotpe_evidence(ctx, event_id):
     o = dotpe_evidence_out()
     _check(load().dotpe_evidence(ctx, event_id, ctypes.byref(o)))
     return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def dotpe_evidence_merge(shards, n_phi):
+    """shards: list of (evidence dict as dotpe_evidence returns it, n_int, ln_p_ext [n_ext]),
+    one per bank-row shard of one event.  Returns (evidence dict, ln_p_ext [n_ext] float64)."""
+    n = len(shards)
+    keep = [np.ascontiguousarray(lp, dtype=np.float64) for _, _, lp in shards]
+    n_ext = keep[0].shape[0] if n else 0
+    arr = (dotpe_shard * max(n, 1))()
+    for k, (ev, n_int, _) in enumerate(shards):
+        e = dotpe_evidence_out()
+        for name, _ in e._fields_:
+            setattr(e, name, ev[name])
+        arr[k].ev = e
+        arr[k].n_int = int(n_int)
+        arr[k].ln_p_ext = keep[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o = dotpe_evidence_out()
+    out = np.zeros(max(n_ext, 1))
+    _check(load().dotpe_evidence_merge(n, arr, n_ext, int(n_phi), ctypes.byref(o), _ptr(out)))
+    return {k: getattr(o, k) for k, _ in o._fields_}, out[:n_ext]
 
 
 def dotpe_lnl_blocks(ctx, event_id, i0, i1, e0, e1, what=DOTPE_LNL_MARG, out=None):

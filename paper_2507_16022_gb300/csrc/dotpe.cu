@@ -2590,6 +2590,74 @@ int dotpe_dist_marg_eval(dotpe_ctx *ctx, int64_t n, const float *dh, const float
   return DOTPE_OK;
 }
 
+int dotpe_evidence_merge(int n_shards, const dotpe_shard *shards, int64_t n_ext, int n_phi,
+                         dotpe_evidence_out *out, double *ln_p_ext_out) {
+  if (!shards || !out) return fail(DOTPE_E_INVALID, "null argument");
+  if (n_shards < 1 || n_ext < 1 || n_phi < 1)
+    return fail(DOTPE_E_INVALID, "n_shards=%d n_ext=%lld n_phi=%d", n_shards, (long long)n_ext, n_phi);
+  for (int r = 0; r < n_shards; ++r)
+    if (shards[r].n_int < 1 || !shards[r].ln_p_ext) return fail(DOTPE_E_INVALID, "shard %d: n_int or ln_p_ext", r);
+  // log-sum-exp accumulator in FP64
+  struct L {
+    double m = -INFINITY, s = 0.0;
+    void add(double x) {
+      if (x == -INFINITY) return;
+      if (x > m) { s = s * std::exp(m - x) + 1.0; m = x; }
+      else s += std::exp(x - m);
+    }
+    double val() const { return s > 0.0 ? m + std::log(s) : -INFINITY; }
+  };
+  L s1, s2, spi;
+  int64_t n_int = 0;
+  dotpe_evidence_out o;
+  memset(&o, 0, sizeof(o));
+  o.max_lnl_ml = -INFINITY;
+  o.lnl_ml_threshold = -INFINITY;
+  bool refined = true;
+  for (int r = 0; r < n_shards; ++r) {
+    const dotpe_evidence_out &e = shards[r].ev;
+    const double ls1 = e.ln_z + std::log((double)shards[r].n_int) + std::log((double)n_ext) +
+                       std::log((double)n_phi);
+    if (ls1 != -INFINITY && e.n_eff > 0.0) {
+      s1.add(ls1);
+      s2.add(2.0 * ls1 - std::log(e.n_eff));             // sum p^2 of the shard
+      if (e.n_eff_int > 0.0) spi.add(2.0 * ls1 - std::log(e.n_eff_int));  // sum_i P_i^2
+    }
+    n_int += shards[r].n_int;
+    if (e.max_lnl_ml > o.max_lnl_ml ||
+        (e.max_lnl_ml == o.max_lnl_ml &&
+         (e.arg_i < o.arg_i || (e.arg_i == o.arg_i && (e.arg_e < o.arg_e || (e.arg_e == o.arg_e && e.arg_o < o.arg_o)))))) {
+      o.max_lnl_ml = e.max_lnl_ml;
+      o.arg_i = e.arg_i;
+      o.arg_e = e.arg_e;
+      o.arg_o = e.arg_o;
+    }
+    o.n_marginalised += e.n_marginalised;
+    o.n_pairs += e.n_pairs;
+    o.lnl_ml_threshold = std::max(o.lnl_ml_threshold, e.lnl_ml_threshold);
+    if (o.device_status == 0) o.device_status = e.device_status;
+    if (e.n_refined_tiles < 0) refined = false;
+    else o.n_refined_tiles += e.n_refined_tiles;
+  }
+  if (!refined) o.n_refined_tiles = -1;
+  // per-sample marginals: the shards' sums added, then sum_e P_e^2
+  L spe;
+  for (int64_t k = 0; k < n_ext; ++k) {
+    L pe;
+    for (int r = 0; r < n_shards; ++r) pe.add(shards[r].ln_p_ext[k]);
+    const double v = pe.val();
+    if (ln_p_ext_out) ln_p_ext_out[k] = v;
+    if (v != -INFINITY) spe.add(2.0 * v);
+  }
+  const double l1 = s1.val();
+  o.ln_z = l1 - std::log((double)n_int) - std::log((double)n_ext) - std::log((double)n_phi);
+  o.n_eff = (l1 == -INFINITY) ? 0.0 : std::exp(2.0 * l1 - s2.val());
+  o.n_eff_int = (l1 == -INFINITY) ? 0.0 : std::exp(2.0 * l1 - spi.val());
+  o.n_eff_ext = (l1 == -INFINITY) ? 0.0 : std::exp(2.0 * l1 - spe.val());
+  *out = o;
+  return DOTPE_OK;
+}
+
 int dotpe_dist_marg_eval_noalloc(dotpe_ctx *ctx, int64_t n, const float *dh, const float *hh, float u_min,
                                   float *out) {
   if (!ctx || (n > 0 && (!dh || !hh || !out))) return fail(DOTPE_E_INVALID, "null argument");

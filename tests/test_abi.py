@@ -42,7 +42,7 @@ def test_binding_lists_every_symbol():
 def test_strerror_and_version(lib):
     import paper_2507_16022_gb300 as dp
     L = dp.load()
-    assert L.dotpe_version() == 5
+    assert L.dotpe_version() == 6
     assert L.dotpe_strerror(dp.DOTPE_E_ADMISSION).decode() == "event can never fit the HBM budget"
     assert L.dotpe_strerror(12345).decode() == "unknown status"
 
@@ -60,6 +60,7 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert L.dotpe_bank_subset(None, 1, None, 1, None) == dp.DOTPE_E_INVALID
     assert L.dotpe_bank_save(None, 1, None) == dp.DOTPE_E_INVALID
     assert L.dotpe_bank_open(None, None, None) == dp.DOTPE_E_INVALID
+    assert L.dotpe_evidence_merge(0, None, 1, 32, None, None) == dp.DOTPE_E_INVALID
     assert "null" in L.dotpe_last_error_message().decode()
 
 
@@ -81,9 +82,9 @@ def test_ctypes_struct_sizes_match_header(lib):
     code = r'''
 #include <stdio.h>
 #include "dotpe.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dotpe_config), sizeof(dotpe_bank_desc),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dotpe_config), sizeof(dotpe_bank_desc),
  sizeof(dotpe_event_desc), sizeof(dotpe_event_stats), sizeof(dotpe_evidence_out),
- sizeof(dotpe_presel_desc), sizeof(dotpe_presel_out), sizeof(dotpe_rb_desc));return 0;}
+ sizeof(dotpe_presel_desc), sizeof(dotpe_presel_out), sizeof(dotpe_rb_desc), sizeof(dotpe_shard));return 0;}
 '''
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "s.c")
@@ -94,4 +95,4 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dotpe_config),
     assert sizes == [ctypes.sizeof(c) for c in (dp.dotpe_config, dp.dotpe_bank_desc,
                                                dp.dotpe_event_desc, dp.dotpe_event_stats,
                                                dp.dotpe_evidence_out, dp.dotpe_presel_desc,
-                                               dp.dotpe_presel_out, dp.dotpe_rb_desc)]
+                                               dp.dotpe_presel_out, dp.dotpe_rb_desc, dp.dotpe_shard)]

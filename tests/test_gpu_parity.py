@@ -738,6 +738,37 @@ def test_screen_tile_widths_agree(dpx, shape):
     assert wide["max_lnl_ml"] == pytest.approx(float(guncut["lnl_ml_max"].max()), abs=1e-3)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_bank_shards_merge_to_one_pass(dpx, precision):
+    """A bank-sharded event on one GPU: the slice's rows in two shards (each an
+    event of its own), merged by dotpe_evidence_merge, give the one-pass
+    event's ln Z, N_eff, N_eff,int, N_eff,ext, per-sample marginals and maximum
+    (the shards' tiles are the one-pass event's, so the FP32 tile partials are
+    the same; the per-sample marginals arrive as float32)."""
+    dp, ctx = dpx
+    wl = synth.make_workload(n_int=600, n_ext=90, n_det=3, n_modes=4, n_bins=128, snr=14.0, seed=71,
+                             ln_w="random")
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+    try:
+        one = run(dp, ctx, wl, precision, bid=bid, i0=0, i1=600, flags=0)
+        shards = []
+        for a, b in ((0, 256), (256, 600)):
+            got = run(dp, ctx, wl, precision, bid=bid, i0=a, i1=b, flags=0)
+            shards.append((got["ev"], b - a, got["col"].astype(np.float64)))
+    finally:
+        dp.dotpe_bank_release(ctx, bid)
+    merged, lpe = dp.dotpe_evidence_merge(shards, wl.event.n_phi)
+    ev = one["ev"]
+    assert merged["ln_z"] == pytest.approx(ev["ln_z"], abs=1e-9)
+    assert merged["n_eff"] == pytest.approx(ev["n_eff"], rel=1e-9)
+    assert merged["n_eff_int"] == pytest.approx(ev["n_eff_int"], rel=1e-9)
+    assert merged["n_eff_ext"] == pytest.approx(ev["n_eff_ext"], rel=1e-5)
+    np.testing.assert_allclose(lpe, one["col"].astype(np.float64), rtol=0, atol=1e-5)
+    assert merged["max_lnl_ml"] == ev["max_lnl_ml"]
+    assert (merged["arg_i"], merged["arg_e"], merged["arg_o"]) == (ev["arg_i"], ev["arg_e"], ev["arg_o"])
+    assert merged["n_marginalised"] == ev["n_marginalised"] and merged["n_pairs"] == ev["n_pairs"]
+
+
 def test_gemm_only_diagnostic_runs(dpx):
     dp, ctx = dpx
     wl = synth.make_workload(n_int=1024, n_ext=256, n_det=3, n_modes=4, n_bins=256, seed=2)
