@@ -1145,6 +1145,52 @@ def bench_serve(args, dp, ctx_factory, torch, dev):
     return line
 
 
+def bench_gemm(args, dp, ctx_factory, torch, dev):
+    """The <d|h> GEMM mainloop alone (diagnostic): events with DOTPE_FLAG_GEMM_ONLY
+    (the fused kernel's epilogue reduced to reading and summing the
+    accumulators; the results are not valid), one fp16 pass over every pair."""
+    import synth
+    kw = dict(WORKLOAD)
+    kw["n_int"], kw["n_ext"] = args.n_int, args.n_ext
+    wl = synth.make_workload(**kw, n_phi=N_PHI)
+    I, E, M, B = kw["n_int"], kw["n_ext"], kw["n_modes"], kw["n_bins"]
+    ctx = ctx_factory()
+    bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
+
+    def one():
+        eid = dp.dotpe_event_submit(ctx, bid, 0, I, wl.event.psd, wl.event.data, wl.ext.t, wl.ext.R, wl.ext.ln_w,
+                                    n_phi=N_PHI, u_min=wl.event.u_min, cut_delta=0.0, precision="fp16",
+                                    flags=dp.DOTPE_FLAG_GEMM_ONLY)
+        dp.dotpe_event_wait(ctx, eid, 600.0)
+        st = dp.dotpe_event_poll(ctx, eid)[1]
+        dp.dotpe_event_release(ctx, eid)
+        return st
+
+    for _ in range(args.warmup):
+        one()
+    sampler = make_clock_sampler(dev.index or 0)
+    sampler.start()
+    stats = [one() for _ in range(args.steps)]
+    clocks = sampler.stop()
+    ms = statistics.median(s["fused_ms"] for s in stats)
+    flops = 8 * B * M * I * E
+    burst, sustained, hbm, peak_src = load_peaks()
+    tf = flops / (ms * 1e-3) / 1e12
+    dp.dotpe_destroy(ctx)
+    return {
+        "metric": "<d|h> GEMM TFLOP/s (diagnostic)", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
+        "config": {"workload": f"GEMM-only pass, I={I} x E={E}, M={M}, B={B}",
+                   "tiles": "32-sample" if args.narrow_tiles else "64-sample (default)",
+                   "note": "median of the fused launch's device time over the steps; results not valid"},
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": burst, "unit": "TFLOP/s", "frac": tf / burst,
+                     "traffic": None, "kernel": "tc_fused_kernel, GEMM-only epilogue", "kernel_ms": ms,
+                     "peak_source": f"{peak_src} bf16_tflops (burst; fp16 has the same dense rate)"},
+        "e2e": None, "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1158,7 +1204,8 @@ def main():
     ap.add_argument("--n-int", type=int, default=WORKLOAD["n_int"], help="bank rows (profiling runs)")
     ap.add_argument("--n-ext", type=int, default=WORKLOAD["n_ext"], help="extrinsic samples (profiling runs)")
     ap.add_argument("--workload", default="event",
-                    choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing", "pipeline"])
+                    choices=["event", "batch64", "serve", "presel", "rb", "samples", "precessing", "pipeline",
+                             "gemm"])
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--autotune", action="store_true",
                     help="event: time candidate L2 bands on the first event (DOTPE_CONFIG_AUTOTUNE)")
@@ -1211,6 +1258,9 @@ def main():
             line = bench_precessing(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         elif args.workload == "pipeline":
             line = bench_pipeline(args, dp, lambda: dp.dotpe_create(local), torch, dev)
+        elif args.workload == "gemm":
+            line = bench_gemm(args, dp, lambda: dp.dotpe_create(
+                local, flags=dp.DOTPE_CONFIG_NARROW_TILES if args.narrow_tiles else 0), torch, dev)
         else:
             line = bench_serve(args, dp, lambda: dp.dotpe_create(local, max_batch=args.max_batch), torch, dev)
         print(json.dumps(line), flush=True)
