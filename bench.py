@@ -68,10 +68,10 @@ WORKLOAD = dict(n_int=65536, n_ext=4096, n_det=3, n_modes=4, n_bins=512, snr=15.
 N_PHI = 32
 CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
 # DRAM bytes (read + write) per (i,e) pair of the dominant launch, from one ncu
-# capture of a 16,384 x 2,048 event (the traffic grows with I*E: the bank is
-# re-read once per L2 band), keyed by precision; absent = not measured for the
-# current kernel version.
-DRAM_BYTES_PER_PAIR = {"mixed": (308.76e6 + 14.37e6) / (16384 * 2048)}  # screening launch
+# capture of a 16,384 x 2,048 event (profiles/screen64_16384x2048_ncu_full.md;
+# the traffic grows with I*E: the bank is re-read once per L2 band), keyed by
+# precision; absent = not measured for the current kernel version.
+DRAM_BYTES_PER_PAIR = {"mixed": (411.714816e6 + 19.353088e6) / (16384 * 2048)}  # 64-sample screening launch
 
 
 # DRAM bytes (read + write) per launch of the FP32 relative-binning pre-selection
