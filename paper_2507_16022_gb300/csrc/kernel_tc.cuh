@@ -80,6 +80,9 @@ template <int TEV> struct TcTail {
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
   float xs[GEN ? TI * XS_LD : 1];
   alignas(16) float qs[TEV * MAXD * REC];  // read as float4 records
+  // 64-sample screen: |Q_d[e, ab]| of the off-diagonal column entries, 8 per
+  // detector (6 used), read as float4
+  alignas(16) float qabs[GEN ? 4 : TEV * MAXD * 8];
   double lwe[GEN ? TEV : 1];
   float2 ph[7 * MAXPHI];
   float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
@@ -414,24 +417,62 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if constexpr (TcTail::GEN)
         for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
+      if constexpr (!TcTail::GEN)
+        for (int f = etid; f < TEV * MAXD * 8; f += EPT) {
+          const int e = f / (MAXD * 8), d = (f / 8) % MAXD, q = f % 8;
+          float v = 0.f;
+          if (q < NPAIR && d < P.n_det && e0 + e < P.n_ext) {
+            const float *src = P.qx + ((e0 + e) * P.n_det + d) * REC + 4 + 2 * q;
+            const float x = __ldg(src), y = __ldg(src + 1);
+            v = sqrt_up(x * x + y * y);
+          }
+          T.qabs[f] = v;
+        }
       named_bar_sync(1, EPT);
       float thr = tile_threshold(P);
-      // 64-sample screen: for each of the thread's pairs the lower bound of
-      // <h|h> at every phase that pair_bound uses, C_0 - 2 sum_delta |C_delta|
-      // (Eq. hh_ieo), formed while the MMAs of the tile run
-      // (a rolled loop into a per-thread array that lives in local memory: small
-      // code, no register pressure, read back once per pair in pass 1)
+      // 64-sample screen: for each of the thread's pairs a lower bound of
+      // <h|h> at every phase (Eq. hh_ieo), formed while the MMAs of the tile run:
+      //   <h|h>(phi) >= C_0 - 2 sum_delta |C_delta|
+      //             >= sum_d [sum_m <h_m|h_m>_d |R_dm|^2 - 2 sum_{a>b} |<h_a|h_b>_d| |R_da R_db^*|]
+      // (C_0 exact, the small off-diagonal terms by the triangle inequality per
+      // detector and mode pair; a rolled loop into a per-thread array that
+      // lives in local memory: small code, read back once per pair in pass 1)
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
         if (!P.gemm_only) {
+          float ro[MAXD][8];  // 2 |<h_a|h_b>_d|, 6 used per detector
+          float rmax = 0.f;
+#pragma unroll
+          for (int d = 0; d < MAXD; ++d) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float x = q < NPAIR ? mrec[d * REC + 4 + 2 * q] : 0.f;
+              const float y = q < NPAIR ? mrec[d * REC + 5 + 2 * q] : 0.f;
+              ro[d][q] = 2.f * sqrt_up(x * x + y * y);
+            }
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) rmax = fmaxf(rmax, mrec[d * REC + m]);
+          }
 #pragma unroll 1
           for (int j = 0; j < EHALF; ++j) {
-            float C0, Cr[3], Ci[3];
-            hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
-            float h = C0;
+            const int el = half * EHALF + j;
+            float hd = 0.f, ho = 0.f, cs = 0.f;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) h -= 2.f * sqrt_up(Cr[q] * Cr[q] + Ci[q] * Ci[q]);
-            hl[j] = h;
+            for (int d = 0; d < MAXD; ++d) {
+              if (d < P.n_det) {
+                const float4 q = *reinterpret_cast<const float4 *>(&T.qs[(el * MAXD + d) * REC]);
+                hd = fmaf(mrec[d * REC], q.x, fmaf(mrec[d * REC + 1], q.y,
+                          fmaf(mrec[d * REC + 2], q.z, fmaf(mrec[d * REC + 3], q.w, hd))));
+                cs += (q.x + q.y) + (q.z + q.w);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&T.qabs[(el * MAXD + d) * 8]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&T.qabs[(el * MAXD + d) * 8 + 4]);
+                ho = fmaf(ro[d][0], a0.x, fmaf(ro[d][1], a0.y, fmaf(ro[d][2], a0.z, fmaf(ro[d][3], a0.w, ho))));
+                ho = fmaf(ro[d][4], a1.x, fmaf(ro[d][5], a1.y, ho));
+              }
+            }
+            // FP32 rounding of the sums (terms up to rmax |R|^2 each): keep the
+            // bound below the exact value
+            hl[j] = hd - ho * 1.00001f - 1e-5f * rmax * cs;
           }
         }
       }
