@@ -80,9 +80,6 @@ template <int TEV> struct TcTail {
   EpiParams ep;  // parameters of the event whose tile the epilogue is on
   float xs[GEN ? TI * XS_LD : 1];
   alignas(16) float qs[TEV * MAXD * REC];  // read as float4 records
-  // 64-sample screen: |Q_d[e, ab]| of the off-diagonal column entries, 8 per
-  // detector (6 used), read as float4
-  alignas(16) float qabs[GEN ? 4 : TEV * MAXD * 8];
   double lwe[GEN ? TEV : 1];
   float2 ph[7 * MAXPHI];
   float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
@@ -340,8 +337,7 @@ __global__ void __launch_bounds__(NT, 1)
     const EpiParams &P = (NB == 1) ? Bt.w[0].P : T.ep;
     bool store = false;
     float zs = 1.f;
-    // row record floats in registers (the 64-sample screen reads them through the cache)
-    constexpr int NREC = (TEV == 64) ? 1 : ((HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC);
+    constexpr int NREC = (HH == 2) ? POL_TC_MAXD * REC_POL : MAXD * REC;  // row record floats in registers
     float mrec[NREC];
 
     double lwi = 0.0;
@@ -374,7 +370,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int64_t i = (int64_t)it * TI + row;
       const bool vi = i < P.n_int;
       const int64_t e0 = (int64_t)et * TEV;
-      if (TEV == 32 && it != cur_it) {
+      if (it != cur_it) {
 #pragma unroll
         for (int k = 0; k < NREC; ++k) mrec[k] = 0.f;
         if constexpr (HH == 2) {
@@ -392,7 +388,7 @@ __global__ void __launch_bounds__(NT, 1)
                   if (4 * v + c < REC_POL) mrec[d * REC_POL + 4 * v + c] = xs4[c];
               }
             }
-        } else if constexpr (TEV == 32) {
+        } else {
           const float4 *src = reinterpret_cast<const float4 *>(P.mx + i * P.n_det * REC);
 #pragma unroll
           for (int k = 0; k < MAXD * REC / 4; ++k) {
@@ -418,74 +414,24 @@ __global__ void __launch_bounds__(NT, 1)
       }
       if constexpr (TcTail::GEN)
         for (int k = etid; k < TEV; k += EPT) T.lwe[k] = (P.lw_ext && e0 + k < P.n_ext) ? P.lw_ext[e0 + k] : 0.0;
-      if constexpr (!TcTail::GEN)
-        for (int f = etid; f < TEV * MAXD * 8; f += EPT) {
-          const int e = f / (MAXD * 8), d = (f / 8) % MAXD, q = f % 8;
-          float v = 0.f;
-          if (q < NPAIR && d < P.n_det && e0 + e < P.n_ext) {
-            const float *src = P.qx + ((e0 + e) * P.n_det + d) * REC + 4 + 2 * q;
-            const float x = __ldg(src), y = __ldg(src + 1);
-            v = sqrt_up(x * x + y * y);
-          }
-          T.qabs[f] = v;
-        }
       named_bar_sync(1, EPT);
       float thr = tile_threshold(P);
-      // 64-sample screen: for each of the thread's pairs a lower bound of
-      // <h|h> at every phase (Eq. hh_ieo), formed while the MMAs of the tile run:
-      //   <h|h>(phi) >= C_0 - 2 sum_delta |C_delta|
-      //             >= sum_d [sum_m <h_m|h_m>_d |R_dm|^2 - 2 sum_{a>b} |<h_a|h_b>_d| |R_da R_db^*|]
-      // (C_0 exact, the small off-diagonal terms by the triangle inequality per
-      // detector and mode pair; a rolled loop into a per-thread array that
-      // lives in local memory: small code, read back once per pair in pass 1)
+      // 64-sample screen: for each of the thread's pairs the lower bound of
+      // <h|h> at every phase that pair_bound uses, C_0 - 2 sum_delta |C_delta|
+      // (Eq. hh_ieo), formed while the MMAs of the tile run
+      // (a rolled loop into a per-thread array that lives in local memory: small
+      // code, no register pressure, read back once per pair in pass 1)
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
         if (!P.gemm_only) {
-          // the row's records (read through the cache for every tile, so that
-          // nothing of them stays live through pass 1)
-          float rd[MAXD][MAXM], ro[MAXD][8];  // <h_m|h_m>_d; 2 |<h_a|h_b>_d|, 6 used per detector
-          float rmax = 0.f;
-#pragma unroll
-          for (int d = 0; d < MAXD; ++d) {
-            const float4 *src = reinterpret_cast<const float4 *>(P.mx + (i * P.n_det + d) * REC);
-            const bool ok = vi && d < P.n_det;
-            float r16[REC];
-#pragma unroll
-            for (int v4 = 0; v4 < REC / 4; ++v4) {
-              const float4 x = ok ? __ldg(src + v4) : make_float4(0.f, 0.f, 0.f, 0.f);
-              r16[4 * v4] = x.x; r16[4 * v4 + 1] = x.y; r16[4 * v4 + 2] = x.z; r16[4 * v4 + 3] = x.w;
-            }
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              rd[d][m] = r16[m];
-              rmax = fmaxf(rmax, r16[m]);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float x = q < NPAIR ? r16[4 + 2 * q] : 0.f;
-              const float y = q < NPAIR ? r16[5 + 2 * q] : 0.f;
-              ro[d][q] = 2.f * sqrt_up(x * x + y * y);
-            }
-          }
 #pragma unroll 1
           for (int j = 0; j < EHALF; ++j) {
-            const int el = half * EHALF + j;
-            float hd = 0.f, ho = 0.f, cs = 0.f;
+            float C0, Cr[3], Ci[3];
+            hh_tile<HH>(mrec, &T.qs[(half * EHALF + j) * MAXD * REC], P, C0, Cr, Ci);
+            float h = C0;
 #pragma unroll
-            for (int d = 0; d < MAXD; ++d) {
-              if (d < P.n_det) {
-                const float4 q = *reinterpret_cast<const float4 *>(&T.qs[(el * MAXD + d) * REC]);
-                hd = fmaf(rd[d][0], q.x, fmaf(rd[d][1], q.y, fmaf(rd[d][2], q.z, fmaf(rd[d][3], q.w, hd))));
-                cs += (q.x + q.y) + (q.z + q.w);
-                const float4 a0 = *reinterpret_cast<const float4 *>(&T.qabs[(el * MAXD + d) * 8]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&T.qabs[(el * MAXD + d) * 8 + 4]);
-                ho = fmaf(ro[d][0], a0.x, fmaf(ro[d][1], a0.y, fmaf(ro[d][2], a0.z, fmaf(ro[d][3], a0.w, ho))));
-                ho = fmaf(ro[d][4], a1.x, fmaf(ro[d][5], a1.y, ho));
-              }
-            }
-            // FP32 rounding of the sums (terms up to rmax |R|^2 each): keep the
-            // bound below the exact value
-            hl[j] = hd - ho * 1.00001f - 1e-5f * rmax * cs;
+            for (int q = 0; q < 3; ++q) h -= 2.f * sqrt_up(Cr[q] * Cr[q] + Ci[q] * Ci[q]);
+            hl[j] = h;
           }
         }
       }
@@ -518,108 +464,89 @@ __global__ void __launch_bounds__(NT, 1)
           if (lane == 0) mbar_arrive(&T.tempty[0]);
           best = (vi && sx == sx) ? fabsf(sx) : -1.f;
         } else {
-          // Pass 1 (the accumulators read 16 columns at a time, 8 pairs x 4 modes
-          // per wait): a pair can reach ln L^ML >= thr only if (sum_m |Z_m|)^2,
-          // a bound of dh^2 at every phase, reaches 2 thr hl (Eq. bestfit_lnl
-          // with hl <= <h|h>); those are the candidates.  Each lane keeps its
-          // first candidate's accumulators in registers.
+          // Pass 1 (the accumulators read 16 columns at a time): the bound of
+          // pair_bound, (sum_m |Z_m|)^2 / (2 hl), against the threshold; the
+          // pairs that reach it are the candidates.
           const float cm = zs * zs * 1.000001f;
           uint32_t cand = 0;
-          int sj = -1;
-          float sr[MAXM], si[MAXM];
-#pragma unroll
-          for (int m = 0; m < MAXM; ++m) { sr[m] = 0.f; si[m] = 0.f; }
 #pragma unroll
           for (int g = 0; g < EHALF / 8; ++g) {
-            float v[MAXM][16];
+            float a[8];
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              if (m < M) tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v[m]);
-              else {
+            for (int q = 0; q < 8; ++q) a[q] = 0.f;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) v[m][q] = 0.f;
-              }
-            }
-            tmem_ld_wait();
-            uint32_t cg = 0;
+            for (int m0 = 0; m0 < MAXM; m0 += 2) {
+              // two modes per wait
+              float v[2][16];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              float a = 0.f;
+              for (int m = m0; m < m0 + 2; ++m)
+                if (m < M) tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v[m - m0]);
+              tmem_ld_wait();
 #pragma unroll
-              for (int m = 0; m < MAXM; ++m) a += sqrt_up(fmaf(v[m][2 * q], v[m][2 * q], v[m][2 * q + 1] * v[m][2 * q + 1]));
-              const int j = 8 * g + q;
-              const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
-              const bool reject = hl[j] > 0.f && cm * a * a < 2.f * thr * hl[j];
-              if (valid && !reject) cg |= 1u << q;
-            }
-            cand |= cg << (8 * g);
-            if (__any_sync(0xffffffffu, cg != 0u && sj < 0)) {
+              for (int m = m0; m < m0 + 2; ++m)
+                if (m < M) {
 #pragma unroll
-              for (int q = 0; q < 8; ++q)
-                if (sj < 0 && ((cg >> q) & 1u)) {
-                  sj = 8 * g + q;
-#pragma unroll
-                  for (int m = 0; m < MAXM; ++m) { sr[m] = v[m][2 * q]; si[m] = v[m][2 * q + 1]; }
+                  for (int q = 0; q < 8; ++q)
+                    a[q] += sqrt_up(fmaf(v[m - m0][2 * q], v[m - m0][2 * q], v[m - m0][2 * q + 1] * v[m - m0][2 * q + 1]));
                 }
             }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int j = 8 * g + q;
+              const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
+              const bool reject = hl[j] > 0.f && cm * a[q] * a[q] < 2.f * thr * hl[j];
+              if (valid && !reject) cand |= 1u << j;
+            }
           }
-          if (sj >= 0) cand &= ~(1u << sj);
-          // The exact bound of pair_bound, then the phase grid where it can
-          // still reach the threshold and the thread's best; the threshold
+          // Pass 2: candidates in index order (the warp takes the lowest pending
+          // pair of its lanes at a time): the phase grid where the pair's bound
+          // still reaches the threshold and the thread's best.  The threshold
           // follows the running maximum, raised by every pair evaluated here (a
           // lower bound of the final threshold throughout).
-          const float *mrow = P.mx + i * P.n_det * REC;
           float pushed = 0.f;
-          auto evaluate = [&](const float (&zr)[MAXM], const float (&zi)[MAXM], int j) {
-            const int el = half * EHALF + j;
-            float Zr[MAXM], Zi[MAXM];
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              Zr[m] = zr[m] * zs;
-              Zi[m] = zi[m] * zs;
-            }
-            float C0, Cr[3], Ci[3];
-            hh_tile<HH>(mrow, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
-            const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
-            if (bound >= thr && !(bound < best)) {
-              int argo;
-              const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
-              const long long gidx = (i * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
-              if (ml > best || (ml == best && gidx < barg)) {
-                best = ml;
-                barg = gidx;
-              }
-              if (P.track_max && ml > pushed && ml > 0.f) {
-                atomic_max_nonneg(P.ml_running, ml);
-                pushed = ml;
-              }
-            }
-          };
-          // further candidates of a lane (rare once the threshold is near its
-          // final value): the warp takes the lowest pending pair of its lanes at
-          // a time and reads its columns from TMEM
 #pragma unroll 1
           while (__any_sync(0xffffffffu, cand != 0u)) {
             const int jl = cand ? (__ffs(cand) - 1) : EHALF;
             const int j = __reduce_min_sync(0xffffffffu, jl);
             const bool mine = ((cand >> j) & 1u) != 0u;
             cand &= ~(1u << j);
-            float zr[MAXM], zi[MAXM];
+            const int el = half * EHALF + j;
+            float Zr[MAXM], Zi[MAXM];
 #pragma unroll
             for (int m = 0; m < MAXM; ++m) {
-              if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
-              else { zr[m] = 0.f; zi[m] = 0.f; }
+              if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
+              else { Zr[m] = 0.f; Zi[m] = 0.f; }
             }
             tmem_ld_wait();
-            if (mine) evaluate(zr, zi, j);
+            if (mine) {
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) {
+                Zr[m] *= zs;
+                Zi[m] *= zs;
+              }
+              float C0, Cr[3], Ci[3];
+              hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+              const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
+              if (bound >= thr && !(bound < best)) {
+                int argo;
+                const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
+                const long long gidx = (i * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
+                if (ml > best || (ml == best && gidx < barg)) {
+                  best = ml;
+                  barg = gidx;
+                }
+                if (P.track_max && ml > pushed && ml > 0.f) {
+                  atomic_max_nonneg(P.ml_running, ml);
+                  pushed = ml;
+                }
+              }
+            }
             thr = fmaxf(thr, tile_threshold(P));
           }
           // the accumulators are no longer needed: release the buffer to the MMA warp
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&T.tempty[0]);
-          // each lane's first candidate, from its registers, while the next tile's MMAs run
-          if (sj >= 0) evaluate(sr, si, sj);
         }
         // outputs of the two partial tiles: empty marginal partials and each one's best ln L^ML
         warp_argmax(best, barg);
