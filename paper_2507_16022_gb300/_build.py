@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libdotpe.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["dotpe.cu", "kernels_prep.cu", "kernel_simt.cu", "kernel_tc.cu", "kernel_tc1.cu", "kernel_reduce.cu", "kernel_rb.cu", "kernel_sample.cu",
+SOURCES = ["dotpe.cu", "kernels_prep.cu", "kernel_simt.cu", "kernel_tc.cu", "kernel_tc1.cu", "kernel_hh.cu", "kernel_reduce.cu", "kernel_rb.cu", "kernel_sample.cu",
            "kernel_presel_pol.cu", "kernel_presel_permode.cu", "kernel_presel_polres.cu",
            "kernel_presel.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]

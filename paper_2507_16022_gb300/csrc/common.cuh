@@ -65,6 +65,10 @@ struct EpiParams {
   int n_pol;                // 2: polarisation-resolved bank (row records REC_P, column records F_p F_p')
   int test_stall;           // producer withholds its first stage (failure-path test)
   unsigned long long wait_ns;  // bound of every mbarrier wait
+  // screening: a lower bound of <h|h> at every phase per pair, bf16 [n_int][hmin_ld]
+  // (slice-relative rows), or null (the screen forms it itself)
+  const __nv_bfloat16 *hmin;
+  int64_t hmin_ld;
 };
 
 // Error allowance of a single-pass (one rounding of each operand, unit roundoff u)

@@ -217,7 +217,8 @@ static void CUDART_CB mark_done(void *p) {
 struct ScratchLayout {
   size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, sqrt_dd, gpack, mx, tile_part, tile_ml, tile_arg,
       tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, n_list_total, sel_counts, sep, acc,
-      acc_col, status, red, total;
+      acc_col, status, red, hb, total;
+  size_t hb_bytes;     // scratch of the tensor-core <h|h> bound (0: the screen forms it itself)
   int64_t block_rows;  // bank rows per streamed block (the whole slice when not streamed)
   int n_itile, n_etile, pack_kind, pack_planes, TI, TE;  // n_itile: tiles of one block
 };
@@ -231,7 +232,12 @@ static const float MIXED_MARGIN_K = 2.0f * 0.00048828125f;
 // maximum keep their screened values (their share of Z is below e^-30 each).
 static const float MIXED_FAR_WINDOW = 30.0f;
 
-static ScratchLayout scratch_layout(const Event &e) {
+// The screening pass of a single (not batched) mixed event with the cut on
+// reads a per-pair bound of <h|h> from the tensor-core pass when its buffer
+// (2 bytes per pair of a bank block) stays under this size.
+static const size_t HB_MAX_BYTES = (size_t)3 << 29;
+
+static ScratchLayout scratch_layout(const Event &e, bool want_hmin = false) {
   ScratchLayout L{};
   const Bank &b = *e.bank;
   const int64_t D = e.D, B = b.B, M = b.M, E = e.NE, Kp = b.Kpad;
@@ -279,6 +285,12 @@ static ScratchLayout scratch_layout(const Event &e) {
   L.acc_col = c.take<double2>(E);
   L.status = c.take<int>(1);
   L.red = c.take<uint8_t>(reduce_scratch_bytes());
+  L.hb_bytes = 0;
+  if (want_hmin && e.prec == DOTPE_PREC_MIXED && e.cut > 0 && !(e.flags & DOTPE_FLAG_STORE_LNL) && b.n_pol == 1) {
+    const size_t hb = hb_scratch_bytes(NI, E);
+    if (hb <= HB_MAX_BYTES) L.hb_bytes = hb;
+  }
+  L.hb = c.take<uint8_t>(L.hb_bytes);
   L.total = c.off;
   return L;
 }
@@ -334,9 +346,9 @@ static int tc_launch_of(dotpe_ctx *ctx, const Bank &b, int prec, TcLaunch &T) {
 static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bool split);
 
 // Device allocations of an event and every pointer of its plan (no launches).
-static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
+static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R, bool single = false) {
   Bank &b = *e.bank;
-  R.L = scratch_layout(e);
+  R.L = scratch_layout(e, single && ctx->wide_tiles);
   const ScratchLayout &L = R.L;
   e.scratch_bytes = L.total;
   CUDA_OR_FAIL(cudaStreamWaitEvent(st, e.ev_inputs, 0));
@@ -577,6 +589,17 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
   }
   W.P = screen_params(R);
   T.tev = launch_tev(ctx, e, R.L, W.P, false);
+  if (T.tev == 64 && R.L.hb_bytes > 0) {
+    // the <h|h> bound of every pair of the block on the tensor cores, read by the screen
+    HbDelta dl;
+    for (int p = 0; p < NPAIR; ++p) dl.pdelta[p] = R.P.pdelta[p];
+    __nv_bfloat16 *hmin = nullptr;
+    if (launch_hh_bound(R.P.n_int, e.NE, e.D, dl, R.P.mx, R.pa.qx, R.scr + R.L.hb, &hmin, ctx->n_sms,
+                        R.P.status, st) != 0)
+      return fail(DOTPE_E_DEVICE, "<h|h> bound launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    W.P.hmin = hmin;
+    W.P.hmin_ld = hb_ld(e.NE);
+  }
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
   if (last_block) CUDA_OR_FAIL(record(e.ev_ks, st));
@@ -731,7 +754,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   NvtxRange nv("dotpe:event");
   cudaStream_t st = ctx->streams[e.slot];
   EventRun R;
-  int rc = event_alloc(ctx, e, st, R);
+  int rc = event_alloc(ctx, e, st, R, true);
   if (rc != DOTPE_OK) return rc;
   {
     NvtxRange np("dotpe:prep");

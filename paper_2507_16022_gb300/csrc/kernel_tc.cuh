@@ -423,7 +423,21 @@ __global__ void __launch_bounds__(NT, 1)
       // code, no register pressure, read back once per pair in pass 1)
       float hl[TEV == 64 ? TEV / 2 : 1];
       if constexpr (TEV == 64) {
-        if (!P.gemm_only) {
+        if (!P.gemm_only && P.hmin) {
+          // the bound from the tensor-core <h|h> pass (bf16, rounded down)
+          const int64_t ib = vi ? i : 0;
+          const uint4 *src = reinterpret_cast<const uint4 *>(P.hmin + ib * P.hmin_ld + e0 + half * EHALF);
+#pragma unroll
+          for (int v4 = 0; v4 < EHALF / 8; ++v4) {
+            const uint4 w = __ldg(src + v4);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              hl[8 * v4 + 2 * c] = __uint_as_float(ws[c] << 16);
+              hl[8 * v4 + 2 * c + 1] = __uint_as_float(ws[c] & 0xffff0000u);
+            }
+          }
+        } else if (!P.gemm_only) {
 #pragma unroll 1
           for (int j = 0; j < EHALF; ++j) {
             float C0, Cr[3], Ci[3];

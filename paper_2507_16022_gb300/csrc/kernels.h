@@ -133,6 +133,28 @@ int launch_tc(const TcLaunch &L, const TcWork *works, int n, const int2 *glist, 
 // extrinsic tiles per L2 band: the band's operand planes fill about l2_band_bytes
 int tc_band(double l2_band_bytes, int kb, int n_modes, bool split, int n_etile);
 
+// K4 on the tensor cores (kernel_hh.cu): a lower bound of <h|h> at every phase
+// for every pair of a bank block and an event, C_0 - 2 sum_delta |C_delta| less
+// 2^-8 C_0, as bf16 rounded down [rows][hb_ld(E)]; the screening pass reads it.
+struct HbDelta {
+  int pdelta[NPAIR];  // m_a - m_b of mode pair p (a > b), 1..3; 0 for pairs beyond the modes
+};
+struct HbArgs {
+  int64_t n_rows;
+  int n_itile, n_etile;           // 128-row tiles, 32-sample tiles
+  int a_plane_rows, b_plane_rows; // rows of one bf16 plane of the row records / sample matrix
+  __nv_bfloat16 *out;             // [n_rows][ld]
+  int64_t ld;
+  int *status;
+};
+int64_t hb_ld(int64_t E);
+// device scratch of launch_hh_bound (record planes and the bound itself)
+size_t hb_scratch_bytes(int64_t rows, int64_t E);
+// mx [rows][D][REC] row records of the block, qx [E][D][REC] column records; *out set to
+// the bound inside `scratch`.  Returns 0, or < 0 if a launch or a tensor map failed.
+int launch_hh_bound(int64_t rows, int64_t E, int D, const HbDelta &dl, const float *mx, const float *qx,
+                    void *scratch, __nv_bfloat16 **out, int n_sms, int *status, cudaStream_t st);
+
 // Refinement selection after a screening pass, over a batch of events: the
 // tiles whose screened best ln L^ML can reach the cut, in banded tile order,
 // written as (event, tile) work items.
