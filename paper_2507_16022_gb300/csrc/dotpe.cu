@@ -152,6 +152,7 @@ struct Event {
   ReduceOut *d_out = nullptr;
   ReduceOut *h_out = nullptr;  // pinned
   size_t scratch_bytes = 0;
+  bool want_hb = false;  // admitted with room for the tensor-core <h|h> bound of its screen
   int slot = -1;
   int64_t t_submit = 0, t_admit = 0;
   volatile int64_t t_done = 0;
@@ -348,7 +349,7 @@ static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bo
 // Device allocations of an event and every pointer of its plan (no launches).
 static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R, bool single = false) {
   Bank &b = *e.bank;
-  R.L = scratch_layout(e, single && ctx->wide_tiles);
+  R.L = scratch_layout(e, single && e.want_hb);
   const ScratchLayout &L = R.L;
   e.scratch_bytes = L.total;
   CUDA_OR_FAIL(cudaStreamWaitEvent(st, e.ev_inputs, 0));
@@ -1053,7 +1054,7 @@ static void progress(dotpe_ctx *ctx) {
           e.xent->refs--;
           e.xent = nullptr;
         }
-        ctx->used -= e.scratch_bytes;
+        ctx->used = (ctx->used >= e.scratch_bytes) ? ctx->used - e.scratch_bytes : 0;
         e.scratch_bytes = 0;
         if (e.in_stage) {
           cudaFreeHost(e.in_stage);
@@ -1107,6 +1108,15 @@ static void progress(dotpe_ctx *ctx) {
       }
     }
     if (ctx->used + need > ctx->budget) break;
+    // a single event's screen reads the <h|h> bound from its own scratch when that fits too
+    e.want_hb = false;
+    if (grp.size() == 1 && e.group == 0 && ctx->wide_tiles) {
+      const size_t with = scratch_layout(e, true).total + keep_bytes_of(e);
+      if (with > need && ctx->used + with <= ctx->budget) {
+        need = with;
+        e.want_hb = true;
+      }
+    }
     for (size_t q = 0; q < grp.size(); ++q) ctx->queue.pop_front();
     ctx->used += need;
     const int64_t t_admit = now_ns();
@@ -2332,7 +2342,7 @@ static void fill_stats(const Event &e, dotpe_event_stats *s) {
   s->t_admit_ns = e.t_admit;
   s->t_done_ns = e.t_done;
   s->n_pairs = e.NI * e.NE;
-  s->footprint_bytes = (int64_t)(e.keep_bytes + scratch_layout(e).total + e.in_bytes);
+  s->footprint_bytes = (int64_t)(e.keep_bytes + scratch_layout(e, e.want_hb).total + e.in_bytes);
   s->device_ms = e.device_ms;
   s->prep_ms = e.prep_ms;
   s->fused_ms = e.fused_ms;
