@@ -66,9 +66,10 @@ __device__ __forceinline__ void hh_coeffs_pol(const float *__restrict__ mrow, co
   }
 }
 
-template <bool CONSEC>
-__device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const float *__restrict__ qrec,
-                                          const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
+// Row-record entry k of detector d through `mr(k)` (registers, memory or another lane).
+template <bool CONSEC, class Row>
+__device__ __forceinline__ void hh_coeffs_by(Row mr_at, const float *__restrict__ qrec, const EpiParams &P,
+                                             float &C0, float Cr[3], float Ci[3]) {
   float c0[MAXD], cr[MAXD][3], ci[MAXD][3];
 #pragma unroll
   for (int d = 0; d < MAXD; ++d) {
@@ -80,7 +81,7 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
 #pragma unroll
   for (int d = 0; d < MAXD; ++d) {
     if (d >= nd) break;
-    const float *mr = mrec + d * REC;
+    auto mr = [&](int k) { return mr_at(d * REC + k); };
     const float4 *q4 = reinterpret_cast<const float4 *>(qrec + d * REC);
     float qr[REC];
 #pragma unroll
@@ -89,13 +90,13 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
       qr[4 * v] = x.x; qr[4 * v + 1] = x.y; qr[4 * v + 2] = x.z; qr[4 * v + 3] = x.w;
     }
 #pragma unroll
-    for (int m = 0; m < MAXM; ++m) c0[d] = fmaf(mr[m], qr[m], c0[d]);
+    for (int m = 0; m < MAXM; ++m) c0[d] = fmaf(mr(m), qr[m], c0[d]);
     int p = 0;
 #pragma unroll
     for (int a = 1; a < MAXM; ++a)
 #pragma unroll
       for (int b = 0; b < a; ++b, ++p) {
-        const float ar = mr[4 + 2 * p], ai = mr[5 + 2 * p];
+        const float ar = mr(4 + 2 * p), ai = mr(5 + 2 * p);
         const float br = qr[4 + 2 * p], bi = qr[5 + 2 * p];
         if (CONSEC) {
           const int k = a - b - 1;
@@ -119,6 +120,21 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
     Cr[k] = (cr[0][k] + cr[1][k]) + cr[2][k];
     Ci[k] = (ci[0][k] + ci[1][k]) + ci[2][k];
   }
+}
+
+template <bool CONSEC>
+__device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const float *__restrict__ qrec,
+                                          const EpiParams &P, float &C0, float Cr[3], float Ci[3]) {
+  hh_coeffs_by<CONSEC>([&](int k) { return mrec[k]; }, qrec, P, C0, Cr, Ci);
+}
+
+// The same coefficients for the row record held in registers mrec of lane
+// `src` of the warp (every lane of the warp calls it, each with its own src).
+template <bool CONSEC>
+__device__ __forceinline__ void hh_coeffs_lane(const float (&mrec)[MAXD * REC], int src,
+                                               const float *__restrict__ qrec, const EpiParams &P, float &C0,
+                                               float Cr[3], float Ci[3]) {
+  hh_coeffs_by<CONSEC>([&](int k) { return __shfl_sync(0xffffffffu, mrec[k], src); }, qrec, P, C0, Cr, Ci);
 }
 
 // Polarisation-resolved bank, row records held in registers (tensor-core

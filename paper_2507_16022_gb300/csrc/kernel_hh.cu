@@ -16,7 +16,8 @@
 //   hmin = C_0 - 2 sum_delta |C_delta| - 2^-8 C_0
 // (the last term covers the split products' rounding many times over: the
 // off-diagonal terms of a Gram matrix are bounded by the diagonal ones), and
-// stores it rounded down to bf16 (0 where not positive).
+// stores it as bf16 truncated (rounded down where positive; a value that is
+// not positive stays so, and the screen then rejects nothing on it).
 //
 // Persistent, warp-specialised like the fused kernel: warp 0 loads the tiles
 // with TMA (the sample tile once per work unit of up to 64 bank tiles, the bank
@@ -54,7 +55,12 @@ struct HbSmem {
 constexpr size_t HB_SMEM = 1024 + sizeof(HbSmem);
 static_assert(HB_SMEM <= 232448, "shared memory budget");
 
-__device__ __forceinline__ float hb_sqrt_up(float x) { return x > 0.f ? x * rsqrtf(x) * 1.000002f : 0.f; }
+// x rsqrt(x) for x >= 0, never below sqrt(x) once scaled by 1 + 2e-6 (the
+// approximate reciprocal square root is within a few ulp; the floor keeps 0 finite)
+__device__ __forceinline__ float hb_sqrt_lo(float x) {
+  x = fmaxf(x, 1e-30f);
+  return x * rsqrtf(x);
+}
 
 __device__ __forceinline__ void hb_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -204,12 +210,14 @@ __global__ void __launch_bounds__(HB_NT, 1)
           const uint32_t d = tmem + b * HB_BUF;
           const uint64_t ah = sdesc_k128(S.A[s][0]), al = sdesc_k128(S.A[s][1]);
           const uint64_t bh = sdesc_k128(S.B[0]), bl = sdesc_k128(S.B[1]);
+          // K steps beyond the detectors hold zeros in both operands
 #pragma unroll
-          for (int k = 0; k < HB_K / 16; ++k) {
-            tc_mma(d, ah + 2 * k, bh + 2 * k, idesc, k ? 1u : 0u);  // hi * hi
-            tc_mma(d, ah + 2 * k, bl + 2 * k, idesc, 1u);          // hi * lo
-            tc_mma(d, al + 2 * k, bh + 2 * k, idesc, 1u);          // lo * hi
-          }
+          for (int k = 0; k < HB_K / 16; ++k)
+            if (k < a.n_kstep) {
+              tc_mma(d, ah + 2 * k, bh + 2 * k, idesc, k ? 1u : 0u);  // hi * hi
+              tc_mma(d, ah + 2 * k, bl + 2 * k, idesc, 1u);          // hi * lo
+              tc_mma(d, al + 2 * k, bh + 2 * k, idesc, 1u);          // lo * hi
+            }
           tc_commit(&S.empty[s]);
           tc_commit(&S.tfull[b]);
         }
@@ -249,17 +257,21 @@ __global__ void __launch_bounds__(HB_NT, 1)
         // column 16 g + x of this thread's range holds sample (16 g + x) / 7, output (16 g + x) % 7
         uint32_t o[8];
 #pragma unroll
-        for (int sm = 0; sm < 16; ++sm) {
-          float cc[HB_NC];
+        for (int sm = 0; sm < 16; sm += 2) {
+          float h2[2];
 #pragma unroll
-          for (int k = 0; k < HB_NC; ++k) cc[k] = v[(sm * HB_NC + k) / 16][(sm * HB_NC + k) % 16];
-          float h = cc[0] * (1.f - 0.00390625f);
+          for (int t = 0; t < 2; ++t) {
+            float cc[HB_NC];
 #pragma unroll
-          for (int dl = 0; dl < 3; ++dl)
-            h -= 2.f * hb_sqrt_up(cc[1 + 2 * dl] * cc[1 + 2 * dl] + cc[2 + 2 * dl] * cc[2 + 2 * dl]);
-          const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rd(h > 0.f ? h : 0.f));
-          if (sm & 1) o[sm >> 1] |= bits << 16;
-          else o[sm >> 1] = bits;
+            for (int k = 0; k < HB_NC; ++k) cc[k] = v[((sm + t) * HB_NC + k) / 16][((sm + t) * HB_NC + k) % 16];
+            float h = cc[0] * (1.f - 0.00390625f);
+#pragma unroll
+            for (int dl = 0; dl < 3; ++dl)
+              h = fmaf(-2.000004f, hb_sqrt_lo(fmaf(cc[1 + 2 * dl], cc[1 + 2 * dl], cc[2 + 2 * dl] * cc[2 + 2 * dl])), h);
+            h2[t] = h;
+          }
+          // the upper halves of the two floats: bf16 truncated, sample sm in the low half
+          o[sm >> 1] = __byte_perm(__float_as_uint(h2[0]), __float_as_uint(h2[1]), 0x7632);
         }
         const int64_t i = (int64_t)it * HB_TI + row;
         if (i < a.n_rows) {
@@ -291,6 +303,7 @@ int64_t hb_ld(int64_t E) { return (E + 63) / 64 * 64; }
 
 int launch_hh_bound(int64_t rows, int64_t E, int D, const HbDelta &dl, const float *mx, const float *qx,
                     void *scratch, __nv_bfloat16 **out, int n_sms, int *status, cudaStream_t st) {
+  if (D < 1 || D > MAXD || rows < 1 || E < 1) return -4;
   const int64_t rows_pad = (rows + HB_TI - 1) / HB_TI * HB_TI;
   const int n_itile = (int)(rows_pad / HB_TI), n_etile = (int)((E + HB_TE - 1) / HB_TE);
   uint8_t *p = (uint8_t *)scratch;
@@ -313,6 +326,7 @@ int launch_hh_bound(int64_t rows, int64_t E, int D, const HbDelta &dl, const flo
   a.n_etile = n_etile;
   a.a_plane_rows = (int)rows_pad;
   a.b_plane_rows = n_etile * HB_BN;
+  a.n_kstep = D;
   a.out = *out;
   a.ld = hb_ld(E);
   a.status = status;

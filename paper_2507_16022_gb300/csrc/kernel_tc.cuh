@@ -74,6 +74,7 @@ static_assert(2 * Pipe<false, 32>::BUF_COLS <= TMEM_COLS && Pipe<false, 64>::BUF
 
 // TEV = 32 carries the general epilogue (marginalisation, partial sums through
 // shared memory); TEV = 64 only the screening and GEMM-only epilogues.
+constexpr int CAND_POOL = 32;  // candidate pairs per epilogue warp and 64-sample tile kept in shared memory
 template <int TEV> struct TcTail {
   static constexpr bool GEN = (TEV == 32);
   static constexpr int XS_LD = TEV + 1;
@@ -84,6 +85,10 @@ template <int TEV> struct TcTail {
   float2 ph[7 * MAXPHI];
   float2 rowh[GEN ? TI : 1];  // second-half row partial of each row
   float wm1[NEPI], ws1[NEPI], wm2[NEPI], ws2[NEPI], wml[NEPI];
+  // 64-sample screen: per-warp pool of candidate pairs taken out of TMEM
+  // (Z_m of every mode, and the owner lane and sample of the pair)
+  alignas(16) float pz[TEV == 64 ? NEPI * CAND_POOL * 2 * MAXM : 1];
+  int ptag[TEV == 64 ? NEPI * CAND_POOL : 1];
   long long warg[NEPI];
   int wnp[NEPI];
   uint64_t full[4], empty[4], tfull[2], tempty[2], drain;
@@ -480,18 +485,25 @@ __global__ void __launch_bounds__(NT, 1)
         } else {
           // Pass 1 (the accumulators read 16 columns at a time): the bound of
           // pair_bound, (sum_m |Z_m|)^2 / (2 hl), against the threshold; the
-          // pairs that reach it are the candidates.
+          // pairs that reach it are the candidates.  Each candidate's Z_m go to
+          // the warp's pool in shared memory as soon as its group of 8 samples is
+          // tested, so the buffer can be released before any candidate is
+          // evaluated; candidates beyond the pool stay in `cand`.
           const float cm = zs * zs * 1.000001f;
           uint32_t cand = 0;
+          int npool = 0;  // warp-uniform
+          float *pz = &T.pz[ew * CAND_POOL * 2 * MAXM];
+          int *ptag = &T.ptag[ew * CAND_POOL];
+          const int mlast = M > 2 ? 2 : 0;  // first mode of the pair left in v after the mode loop
 #pragma unroll
           for (int g = 0; g < EHALF / 8; ++g) {
             float a[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) a[q] = 0.f;
+            float v[2][16];
 #pragma unroll
             for (int m0 = 0; m0 < MAXM; m0 += 2) {
               // two modes per wait
-              float v[2][16];
 #pragma unroll
               for (int m = m0; m < m0 + 2; ++m)
                 if (m < M) tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v[m - m0]);
@@ -504,63 +516,148 @@ __global__ void __launch_bounds__(NT, 1)
                     a[q] += sqrt_up(fmaf(v[m - m0][2 * q], v[m - m0][2 * q], v[m - m0][2 * q + 1] * v[m - m0][2 * q + 1]));
                 }
             }
+            uint32_t gc = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int j = 8 * g + q;
               const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
               const bool reject = hl[j] > 0.f && cm * a[q] * a[q] < 2.f * thr * hl[j];
-              if (valid && !reject) cand |= 1u << j;
+              if (valid && !reject) gc |= 1u << q;
+            }
+            if (__any_sync(0xffffffffu, gc != 0u)) {
+              // pool slots: exclusive prefix of the lanes' candidate counts
+              const int cnt = __popc(gc);
+              int incl = cnt;
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+              }
+              const int total = __shfl_sync(0xffffffffu, incl, 31);
+              int slot = npool + incl - cnt;
+              uint32_t kept = 0;
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                if ((gc >> q) & 1u) {
+                  if (slot < CAND_POOL) {
+                    ptag[slot] = (lane << 8) | (half * EHALF + 8 * g + q);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+                      if (mlast + m < M)
+                        *reinterpret_cast<float2 *>(&pz[slot * 2 * MAXM + 2 * (mlast + m)]) =
+                            make_float2(v[m][2 * q], v[m][2 * q + 1]);
+                    kept |= 1u << q;
+                  } else {
+                    cand |= 1u << (8 * g + q);
+                  }
+                  ++slot;
+                }
+              if (mlast > 0) {
+                // modes 0 and 1 of the group once more
+#pragma unroll
+                for (int m = 0; m < 2; ++m) tmem_ld16(tbase + m * BN + 2 * (half * EHALF + 8 * g), v[m]);
+                tmem_ld_wait();
+                int sl = npool + incl - cnt;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  if ((kept >> q) & 1u) {
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+                      *reinterpret_cast<float2 *>(&pz[sl * 2 * MAXM + 2 * m]) = make_float2(v[m][2 * q], v[m][2 * q + 1]);
+                    ++sl;
+                  }
+              }
+              npool = min(CAND_POOL, npool + total);
             }
           }
-          // Pass 2: candidates in index order (the warp takes the lowest pending
-          // pair of its lanes at a time): the phase grid where the pair's bound
-          // still reaches the threshold and the thread's best.  The threshold
-          // follows the running maximum, raised by every pair evaluated here (a
-          // lower bound of the final threshold throughout).
+          // Pass 2: the pool, one candidate per lane at a time (the owner lane's
+          // row record by shuffle): the phase grid where the pair's bound still
+          // reaches the threshold and the thread's best.  While candidates remain
+          // in TMEM beyond the pool, the buffer is kept and the pool refilled
+          // from it (the warp takes the lowest pending sample of its lanes at a
+          // time); after the last refill the buffer goes back to the MMA warp
+          // and the pool is evaluated while the next tile's MMAs run.  The
+          // threshold follows the running maximum, raised by every pair
+          // evaluated here (a lower bound of the final threshold throughout).
           float pushed = 0.f;
+          bool held = true;
 #pragma unroll 1
-          while (__any_sync(0xffffffffu, cand != 0u)) {
-            const int jl = cand ? (__ffs(cand) - 1) : EHALF;
-            const int j = __reduce_min_sync(0xffffffffu, jl);
-            const bool mine = ((cand >> j) & 1u) != 0u;
-            cand &= ~(1u << j);
-            const int el = half * EHALF + j;
-            float Zr[MAXM], Zi[MAXM];
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) {
-              if (m < M) tmem_ld2(tbase + m * BN + 2 * el, Zr[m], Zi[m]);
-              else { Zr[m] = 0.f; Zi[m] = 0.f; }
+          while (true) {
+            const bool more = __any_sync(0xffffffffu, cand != 0u);
+            if (!more && held) {
+              // the accumulators are no longer needed: release the buffer to the MMA warp
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&T.tempty[0]);
+              held = false;
             }
-            tmem_ld_wait();
-            if (mine) {
+#pragma unroll 1
+            for (int k0 = 0; k0 < npool; k0 += 32) {
+              const int kk = k0 + lane;
+              const bool act = kk < npool;
+              const int tag = act ? ptag[kk] : (lane << 8);
+              const int owner = tag >> 8, el = tag & 255;
+              float C0, Cr[3], Ci[3];
+              hh_coeffs_lane<HH == 1>(mrec, owner, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
+              if (act) {
+                float Zr[MAXM], Zi[MAXM];
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m) {
+                  if (m < M) {
+                    const float2 z = *reinterpret_cast<const float2 *>(&pz[kk * 2 * MAXM + 2 * m]);
+                    Zr[m] = z.x * zs;
+                    Zi[m] = z.y * zs;
+                  } else {
+                    Zr[m] = 0.f;
+                    Zi[m] = 0.f;
+                  }
+                }
+                const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
+                if (bound >= thr && !(bound < best)) {
+                  int argo;
+                  const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
+                  const int64_t io = (int64_t)it * TI + quad * 32 + owner;
+                  const long long gidx = (io * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
+                  if (ml > best || (ml == best && gidx < barg)) {
+                    best = ml;
+                    barg = gidx;
+                  }
+                  if (P.track_max && ml > pushed && ml > 0.f) {
+                    atomic_max_nonneg(P.ml_running, ml);
+                    pushed = ml;
+                  }
+                }
+              }
+              thr = fmaxf(thr, tile_threshold(P));
+            }
+            __syncwarp();
+            npool = 0;
+            if (!more) break;
+#pragma unroll 1
+            while (npool < CAND_POOL && __any_sync(0xffffffffu, cand != 0u)) {
+              const int jl = cand ? (__ffs(cand) - 1) : EHALF;
+              const int j = __reduce_min_sync(0xffffffffu, jl);
+              const bool mine = ((cand >> j) & 1u) != 0u;
+              float zr[MAXM], zi[MAXM];
 #pragma unroll
               for (int m = 0; m < MAXM; ++m) {
-                Zr[m] *= zs;
-                Zi[m] *= zs;
+                if (m < M) tmem_ld2(tbase + m * BN + 2 * (half * EHALF + j), zr[m], zi[m]);
+                else { zr[m] = 0.f; zi[m] = 0.f; }
               }
-              float C0, Cr[3], Ci[3];
-              hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
-              const float bound = pair_bound(Zr, Zi, C0, Cr, Ci);
-              if (bound >= thr && !(bound < best)) {
-                int argo;
-                const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
-                const long long gidx = (i * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
-                if (ml > best || (ml == best && gidx < barg)) {
-                  best = ml;
-                  barg = gidx;
-                }
-                if (P.track_max && ml > pushed && ml > 0.f) {
-                  atomic_max_nonneg(P.ml_running, ml);
-                  pushed = ml;
-                }
+              tmem_ld_wait();
+              const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+              const int slot = npool + __popc(bal & ((1u << lane) - 1u));
+              if (mine && slot < CAND_POOL) {
+                ptag[slot] = (lane << 8) | (half * EHALF + j);
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m)
+                  *reinterpret_cast<float2 *>(&pz[slot * 2 * MAXM + 2 * m]) = make_float2(zr[m], zi[m]);
+                cand &= ~(1u << j);
               }
+              npool = min(CAND_POOL, npool + __popc(bal));
             }
-            thr = fmaxf(thr, tile_threshold(P));
+            __syncwarp();
           }
-          // the accumulators are no longer needed: release the buffer to the MMA warp
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&T.tempty[0]);
         }
         // outputs of the two partial tiles: empty marginal partials and each one's best ln L^ML
         warp_argmax(best, barg);

@@ -143,6 +143,7 @@ struct HbArgs {
   int64_t n_rows;
   int n_itile, n_etile;           // 128-row tiles, 32-sample tiles
   int a_plane_rows, b_plane_rows; // rows of one bf16 plane of the row records / sample matrix
+  int n_kstep;                    // 16-entry K steps that hold record entries (one per detector)
   __nv_bfloat16 *out;             // [n_rows][ld]
   int64_t ld;
   int *status;
