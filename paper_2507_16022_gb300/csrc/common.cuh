@@ -203,6 +203,20 @@ __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Approximate reciprocal square root (PTX rsqrt.approx, relative error below
+// 2^-22 for normal inputs; subnormal inputs flush to zero).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// x rsqrt(x) with x floored at 1e-30: within a few ulp of sqrt(x) for x >= 1e-30
+// and above it below, so (1 + 2e-6) times it is never below sqrt(x) (bounds only).
+__device__ __forceinline__ float sqrt_near(float x) {
+  x = fmaxf(x, 1e-30f);
+  return x * rsqrt_ftz(x);
+}
+
 // Order-preserving float max for values >= 0.
 __device__ __forceinline__ void atomic_max_nonneg(float *addr, float v) {
   atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v));

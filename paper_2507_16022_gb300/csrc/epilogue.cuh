@@ -128,15 +128,6 @@ __device__ __forceinline__ void hh_coeffs(const float *__restrict__ mrec, const 
   hh_coeffs_by<CONSEC>([&](int k) { return mrec[k]; }, qrec, P, C0, Cr, Ci);
 }
 
-// The same coefficients for the row record held in registers mrec of lane
-// `src` of the warp (every lane of the warp calls it, each with its own src).
-template <bool CONSEC>
-__device__ __forceinline__ void hh_coeffs_lane(const float (&mrec)[MAXD * REC], int src,
-                                               const float *__restrict__ qrec, const EpiParams &P, float &C0,
-                                               float Cr[3], float Ci[3]) {
-  hh_coeffs_by<CONSEC>([&](int k) { return __shfl_sync(0xffffffffu, mrec[k], src); }, qrec, P, C0, Cr, Ci);
-}
-
 // Polarisation-resolved bank, row records held in registers (tensor-core
 // epilogue): mrec [POL_TC_MAXD][REC_POL] as hh_coeffs_pol reads them from
 // memory, the column record's (F+^2, F+ Fx, Fx^2) as one float4 per detector.

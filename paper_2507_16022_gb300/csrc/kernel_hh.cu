@@ -22,8 +22,8 @@
 // Persistent, warp-specialised like the fused kernel: warp 0 loads the tiles
 // with TMA (the sample tile once per work unit of up to 64 bank tiles, the bank
 // tiles through a 3-stage ring), warp 1 allocates TMEM and issues the MMAs
-// into two accumulator buffers of 224 columns, warps 2-9 read the
-// accumulators (two warps per TMEM lane quadrant, 16 samples each), form the
+// into two accumulator buffers of 224 columns, warps 2-17 read the
+// accumulators (four warps per TMEM lane quadrant, 8 samples each), form the
 // bounds and store them.  Every wait is bounded.
 #include "common.cuh"
 #include "kernels.h"
@@ -37,7 +37,7 @@ constexpr int HB_NC = 7;                 // outputs per sample: C_0, Re/Im C_1..
 constexpr int HB_BN = HB_TE * HB_NC;     // 224 B rows per tile: N of each MMA
 constexpr int HB_K = 64;                 // K: 3 detectors x 16 record entries, padded
 constexpr int HB_ST = 3;                 // bank-tile stages
-constexpr int HB_NEPI = 8;               // epilogue warps
+constexpr int HB_NEPI = 16;              // epilogue warps (four per TMEM lane quadrant, 8 samples each)
 constexpr int HB_NT = (2 + HB_NEPI) * 32;
 constexpr int HB_CHUNK = 64;             // bank tiles per work unit
 constexpr uint32_t HB_A_BYTES = HB_TI * HB_K * 2;  // one plane of a bank tile (16 KB)
@@ -55,22 +55,15 @@ struct HbSmem {
 constexpr size_t HB_SMEM = 1024 + sizeof(HbSmem);
 static_assert(HB_SMEM <= 232448, "shared memory budget");
 
-// x rsqrt(x) for x >= 0, never below sqrt(x) once scaled by 1 + 2e-6 (the
-// approximate reciprocal square root is within a few ulp; the floor keeps 0 finite)
-__device__ __forceinline__ float hb_sqrt_lo(float x) {
-  x = fmaxf(x, 1e-30f);
-  return x * rsqrtf(x);
-}
 
-__device__ __forceinline__ void hb_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// 32 lanes x 32-bit, 8 consecutive columns per thread.
+__device__ __forceinline__ void hb_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 }  // namespace
 
@@ -232,8 +225,8 @@ __global__ void __launch_bounds__(HB_NT, 1)
     volatile int no_abort = 0;
     mbar_wait(&S.drain, 0, nullptr, &no_abort, 500000000ull);
   } else {
-    // ---------------- epilogue: one row, 16 samples per thread ----------------
-    const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
+    // ---------------- epilogue: one row, 8 samples per thread ----------------
+    const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
     const int row = quad * 32 + lane;
     uint32_t u2 = 0;
     bool ok = true;
@@ -245,40 +238,37 @@ __global__ void __launch_bounds__(HB_NT, 1)
         const uint32_t use = u2 >> 1;
         if (!(ok = mbar_wait(&S.tfull[b], use & 1, nullptr, abortp, wait_ns))) break;
         tc_fence_after();
-        // this thread's 16 samples x 7 outputs: columns [112 half, +112)
-        float v[HB_NC][16];
-        const uint32_t t0 = tmem + ((uint32_t)(quad * 32) << 16) + b * HB_BUF + 112 * half;
+        // this thread's 8 samples x 7 outputs: columns [56 part, +56)
+        float v[HB_NC][8];
+        const uint32_t t0 = tmem + ((uint32_t)(quad * 32) << 16) + b * HB_BUF + 56 * part;
 #pragma unroll
-        for (int g = 0; g < HB_NC; ++g) hb_ld16(t0 + 16 * g, v[g]);
+        for (int g = 0; g < HB_NC; ++g) hb_ld8(t0 + 8 * g, v[g]);
         tmem_ld_wait();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.tempty[b]);
-        // column 16 g + x of this thread's range holds sample (16 g + x) / 7, output (16 g + x) % 7
-        uint32_t o[8];
+        // column 8 g + x of this thread's range holds sample (8 g + x) / 7, output (8 g + x) % 7
+        uint32_t o[4];
 #pragma unroll
-        for (int sm = 0; sm < 16; sm += 2) {
+        for (int sm = 0; sm < 8; sm += 2) {
           float h2[2];
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             float cc[HB_NC];
 #pragma unroll
-            for (int k = 0; k < HB_NC; ++k) cc[k] = v[((sm + t) * HB_NC + k) / 16][((sm + t) * HB_NC + k) % 16];
+            for (int k = 0; k < HB_NC; ++k) cc[k] = v[((sm + t) * HB_NC + k) / 8][((sm + t) * HB_NC + k) % 8];
             float h = cc[0] * (1.f - 0.00390625f);
 #pragma unroll
             for (int dl = 0; dl < 3; ++dl)
-              h = fmaf(-2.000004f, hb_sqrt_lo(fmaf(cc[1 + 2 * dl], cc[1 + 2 * dl], cc[2 + 2 * dl] * cc[2 + 2 * dl])), h);
+              h = fmaf(-2.000004f, sqrt_near(fmaf(cc[1 + 2 * dl], cc[1 + 2 * dl], cc[2 + 2 * dl] * cc[2 + 2 * dl])), h);
             h2[t] = h;
           }
           // the upper halves of the two floats: bf16 truncated, sample sm in the low half
           o[sm >> 1] = __byte_perm(__float_as_uint(h2[0]), __float_as_uint(h2[1]), 0x7632);
         }
         const int64_t i = (int64_t)it * HB_TI + row;
-        if (i < a.n_rows) {
-          uint4 *dst = reinterpret_cast<uint4 *>(a.out + i * a.ld + (int64_t)et * HB_TE + 16 * half);
-          dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-          dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-        }
+        if (i < a.n_rows)
+          *reinterpret_cast<uint4 *>(a.out + i * a.ld + (int64_t)et * HB_TE + 8 * part) = make_uint4(o[0], o[1], o[2], o[3]);
       }
     }
   }

@@ -375,7 +375,9 @@ __global__ void __launch_bounds__(NT, 1)
       const int64_t i = (int64_t)it * TI + row;
       const bool vi = i < P.n_int;
       const int64_t e0 = (int64_t)et * TEV;
-      if (it != cur_it) {
+      // the row record of this thread's bank row into registers (64-sample tiles:
+      // only where it is used, so that it holds no registers through pass 1)
+      auto load_mrec = [&]() {
 #pragma unroll
         for (int k = 0; k < NREC; ++k) mrec[k] = 0.f;
         if constexpr (HH == 2) {
@@ -403,6 +405,9 @@ __global__ void __launch_bounds__(NT, 1)
             }
           }
         }
+      };
+      if (it != cur_it) {
+        if constexpr (TEV == 32) load_mrec();
         lwi = (vi && P.lw_int) ? P.lw_int[i] : 0.0;
         cur_it = it;
       }
@@ -443,6 +448,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
           }
         } else if (!P.gemm_only) {
+          load_mrec();
 #pragma unroll 1
           for (int j = 0; j < EHALF; ++j) {
             float C0, Cr[3], Ci[3];
@@ -489,7 +495,9 @@ __global__ void __launch_bounds__(NT, 1)
           // the warp's pool in shared memory as soon as its group of 8 samples is
           // tested, so the buffer can be released before any candidate is
           // evaluated; candidates beyond the pool stay in `cand`.
-          const float cm = zs * zs * 1.000001f;
+          // (the sum of sqrt_near is within a factor 1 + 2e-6 of the sum of |Z_m|)
+          const float cm = zs * zs * 1.000006f;
+          const float thr2 = 2.f * thr;
           uint32_t cand = 0;
           int npool = 0;  // warp-uniform
           float *pz = &T.pz[ew * CAND_POOL * 2 * MAXM];
@@ -513,7 +521,7 @@ __global__ void __launch_bounds__(NT, 1)
                 if (m < M) {
 #pragma unroll
                   for (int q = 0; q < 8; ++q)
-                    a[q] += sqrt_up(fmaf(v[m - m0][2 * q], v[m - m0][2 * q], v[m - m0][2 * q + 1] * v[m - m0][2 * q + 1]));
+                    a[q] += sqrt_near(fmaf(v[m - m0][2 * q], v[m - m0][2 * q], v[m - m0][2 * q + 1] * v[m - m0][2 * q + 1]));
                 }
             }
             uint32_t gc = 0;
@@ -521,7 +529,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int q = 0; q < 8; ++q) {
               const int j = 8 * g + q;
               const bool valid = vi && (e0 + half * EHALF + j < P.n_ext);
-              const bool reject = hl[j] > 0.f && cm * a[q] * a[q] < 2.f * thr * hl[j];
+              const bool reject = hl[j] > 0.f && cm * a[q] * a[q] < thr2 * hl[j];
               if (valid && !reject) gc |= 1u << q;
             }
             if (__any_sync(0xffffffffu, gc != 0u)) {
@@ -570,8 +578,8 @@ __global__ void __launch_bounds__(NT, 1)
               npool = min(CAND_POOL, npool + total);
             }
           }
-          // Pass 2: the pool, one candidate per lane at a time (the owner lane's
-          // row record by shuffle): the phase grid where the pair's bound still
+          // Pass 2: the pool, one candidate per lane at a time (the owner's row
+          // record read through the cache): the phase grid where the pair's bound still
           // reaches the threshold and the thread's best.  While candidates remain
           // in TMEM beyond the pool, the buffer is kept and the pool refilled
           // from it (the warp takes the lowest pending sample of its lanes at a
@@ -597,9 +605,11 @@ __global__ void __launch_bounds__(NT, 1)
               const bool act = kk < npool;
               const int tag = act ? ptag[kk] : (lane << 8);
               const int owner = tag >> 8, el = tag & 255;
-              float C0, Cr[3], Ci[3];
-              hh_coeffs_lane<HH == 1>(mrec, owner, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
               if (act) {
+                const int64_t io = (int64_t)it * TI + quad * 32 + owner;
+                const float *mrow = P.mx + io * P.n_det * REC;
+                float C0, Cr[3], Ci[3];
+                hh_coeffs_by<HH == 1>([&](int q) { return __ldg(mrow + q); }, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
                 float Zr[MAXM], Zi[MAXM];
 #pragma unroll
                 for (int m = 0; m < MAXM; ++m) {
@@ -616,7 +626,6 @@ __global__ void __launch_bounds__(NT, 1)
                 if (bound >= thr && !(bound < best)) {
                   int argo;
                   const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
-                  const int64_t io = (int64_t)it * TI + quad * 32 + owner;
                   const long long gidx = (io * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
                   if (ml > best || (ml == best && gidx < barg)) {
                     best = ml;
