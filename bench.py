@@ -67,11 +67,12 @@ import numpy as np
 WORKLOAD = dict(n_int=65536, n_ext=4096, n_det=3, n_modes=4, n_bins=512, snr=15.0, seed=2)
 N_PHI = 32
 CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
-# DRAM bytes (read + write) per (i,e) pair of the dominant launch, from one ncu
-# capture of a 16,384 x 2,048 event (profiles/screen64_16384x2048_ncu_full.md;
-# the traffic grows with I*E: the bank is re-read once per L2 band), keyed by
-# precision; absent = not measured for the current kernel version.
-DRAM_BYTES_PER_PAIR = {"mixed": (411.714816e6 + 19.353088e6) / (16384 * 2048)}  # 64-sample screening launch
+# DRAM bytes (read + write) of the screening step of one mixed event (the
+# tensor-core <h|h> bound pass and the 64-sample screen launch) from one ncu
+# capture of the DRAM counters at the workload's own size (the bound's 2 bytes
+# per pair stay in L2 at small sizes, so a small capture does not scale):
+# the shape it was taken on.  None = no capture of the current kernels.
+SCREEN_TRAFFIC = {"bytes": None, "n_int": 65536, "n_ext": 4096, "source": None}
 
 
 # DRAM bytes (read + write) per launch of the FP32 relative-binning pre-selection
@@ -1412,18 +1413,24 @@ def main():
     hh_flops = D * (2 * M + 4 * M * (M - 1))
     flops_issued = (8 * B * M * passes + hh_flops) * pairs
     if mixed:
+        # the <h|h> bound pass: 7 outputs per pair, 16 record entries per detector, 3 split products
+        flops_issued += 2 * 7 * 16 * D * 3 * pairs
         flops_issued += (8 * B * M * 3 + hh_flops) * pairs * refined / n_tiles
+    n_cand = statistics.mean(ev["n_screen_candidates"] for ev in evs) if mixed else None
+    n_eval = statistics.mean(ev["n_screen_evaluated"] for ev in evs) if mixed else None
     burst, sustained, hbm, peak_src = load_peaks()
     achieved = flops_alg / (dom_ms * 1e-3) / 1e12
     # algorithmic bytes of the dominant launch: one read of the bank's operand plane
     # (M x I rows of Kpad 16-bit values) and of the extrinsic operand plane (M x 2E rows)
     kpad = -(-2 * B // 64) * 64
     alg_bytes = float(M * (I + 2 * E) * kpad * 2)
-    traffic = DRAM_BYTES_PER_PAIR[args.precision] * pairs if args.precision in DRAM_BYTES_PER_PAIR else None
-    # prep (data norm, bins, extrinsic, G build, G pack), fused (mixed: screen, 3 selection
-    # kernels, 2 gated refinement variants), reduction (2 line, 2 pass, merge, final);
-    # cross terms are computed once per (bank, PSD) and reused
-    launches_per_event = 5 + (6 if mixed else 1) + 6
+    traffic = (SCREEN_TRAFFIC["bytes"] if mixed and SCREEN_TRAFFIC["bytes"] is not None
+               and (I, E) == (SCREEN_TRAFFIC["n_int"], SCREEN_TRAFFIC["n_ext"]) else None)
+    # prep (data norm, bins, extrinsic, G build, G pack), fused (mixed: <h|h> bound
+    # pass of 3 kernels, screen, 3 selection kernels, 2 gated refinement variants),
+    # reduction (2 line, 2 pass, merge, final); cross terms are computed once per
+    # (bank, PSD) and reused
+    launches_per_event = 5 + (9 if mixed else 1) + 6
     dlnz = max(abs(evs[k]["ln_z"] - ref_fp32[k % len(events)][0]["ln_z"]) for k in range(len(evs)))
     if rank != 0:
         if dist is not None:
@@ -1469,6 +1476,8 @@ def main():
             "fused_ms": fused_ms,
             "refine_ms": refine_ms if mixed else None,
             "refined_tile_fraction": refined / n_tiles if mixed else None,
+            "screen_candidates_per_pair": n_cand / pairs if mixed and n_cand >= 0 else None,
+            "screen_evaluated_per_pair": n_eval / pairs if mixed and n_eval >= 0 else None,
             "issued_tflops": flops_issued / (fused_ms * 1e-3) / 1e12,
             "gemm_only_ms": gemm_only_ms,
             "gemm_only_tflops": 8 * B * M * pairs / (gemm_only_ms * 1e-3) / 1e12,
@@ -1482,10 +1491,11 @@ def main():
             "traffic": traffic,
             "algorithmic_bytes": alg_bytes,
             "traffic_ratio": (traffic / alg_bytes) if traffic is not None else None,
-            "traffic_note": ("bytes per launch, scaled by pairs from an ncu capture at 16,384 x 2,048; "
-                             "algorithmic bytes = one read of the bank's fp16 operand plane and of the "
-                             "event's extrinsic operand plane"),
-            "kernel": ("tc_fused_kernel screening pass (fp16 <d|h> GEMM + <h|h> + ML over the phase grid)"
+            "traffic_note": ("DRAM bytes of the screening step (hb_bound_kernel + the screen launch) from "
+                             "one ncu capture at this size; algorithmic bytes = one read of the bank's fp16 "
+                             "operand plane and of the event's extrinsic operand plane"),
+            "kernel": ("screening step: hb_bound_kernel (<h|h> lower bound on the tensor cores) + "
+                       "tc_fused_kernel screen (fp16 <d|h> GEMM + bound + ML over the phase grid)"
                        if mixed else "tc_fused_kernel (fused <d|h> GEMM + marginalisation)"),
             "kernel_ms": dom_ms,
             "flops_per_pair": algorithmic_flops_per_pair(B, M, D),

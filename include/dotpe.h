@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define DOTPE_ABI_VERSION 6
+#define DOTPE_ABI_VERSION 7
 
 /* ---- status codes ------------------------------------------------------ */
 #define DOTPE_OK 0
@@ -227,6 +227,11 @@ typedef struct dotpe_evidence_out {
   double lnl_ml_threshold;  /* the cut applied (running maximum - cut_delta), -inf when off */
   int32_t device_status;    /* 0, or a DOTPE_E_* raised inside a kernel */
   int32_t n_refined_tiles;  /* MIXED: tiles recomputed in split precision; else -1 */
+  /* MIXED: pairs that passed the screening pass's first bound (64-sample tiles:
+   * sum_m |Z_m| against the <h|h> lower bound; 32-sample tiles: the pairs taken
+   * for evaluation), and pairs whose ln L^ML the screen evaluated over the phase
+   * grid; else -1.  Diagnostics of the screen's selectivity, not of the result. */
+  int64_t n_screen_candidates, n_screen_evaluated;
 } dotpe_evidence_out;
 
 /* Incoherent single-detector pre-selection of bank rows (Sec. IV.D, App. B).

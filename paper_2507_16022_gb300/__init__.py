@@ -114,7 +114,8 @@ class dotpe_evidence_out(ctypes.Structure):
                 ("arg_e", ctypes.c_int64), ("arg_o", ctypes.c_int64),
                 ("n_marginalised", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("lnl_ml_threshold", ctypes.c_double), ("device_status", ctypes.c_int32),
-                ("n_refined_tiles", ctypes.c_int32)]
+                ("n_refined_tiles", ctypes.c_int32),
+                ("n_screen_candidates", ctypes.c_int64), ("n_screen_evaluated", ctypes.c_int64)]
 
 
 class dotpe_shard(ctypes.Structure):
@@ -373,7 +374,8 @@ def dotpe_evidence_merge(shards, n_phi):
     for k, (ev, n_int, _) in enumerate(shards):
         e = dotpe_evidence_out()
         for name, _ in e._fields_:
-            setattr(e, name, ev[name])
+            # the screening counters are diagnostics: -1 (not counted) when absent
+            setattr(e, name, ev.get(name, -1) if name.startswith("n_screen") else ev[name])
         arr[k].ev = e
         arr[k].n_int = int(n_int)
         arr[k].ln_p_ext = keep[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))

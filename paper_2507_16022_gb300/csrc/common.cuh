@@ -69,6 +69,9 @@ struct EpiParams {
   // (slice-relative rows), or null (the screen forms it itself)
   const __nv_bfloat16 *hmin;
   int64_t hmin_ld;
+  // screening statistics (null: not counted): [0] pairs that passed the first
+  // bound, [1] pairs evaluated over the phase grid
+  unsigned long long *n_cand;
 };
 
 // Error allowance of a single-pass (one rounding of each operand, unit roundoff u)

@@ -217,7 +217,7 @@ static void CUDART_CB mark_done(void *p) {
 // ---------------------------------------------------------------------------
 struct ScratchLayout {
   size_t c, omega, fh, fl, th, tl, Rf, qx, G32, gmax, gscale, sqrt_dd, gpack, mx, tile_part, tile_ml, tile_arg,
-      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, n_list_total, sel_counts, sep, acc,
+      tile_npass, row_part, col_part, ml_running, ml_refine, list, n_list, n_list_total, sel_counts, sep, n_cand, acc,
       acc_col, status, red, hb, total;
   size_t hb_bytes;     // scratch of the tensor-core <h|h> bound (0: the screen forms it itself)
   int64_t block_rows;  // bank rows per streamed block (the whole slice when not streamed)
@@ -281,6 +281,7 @@ static ScratchLayout scratch_layout(const Event &e, bool want_hmin = false) {
   L.n_list = c.take<int>(1);
   L.n_list_total = c.take<int>(1);
   L.sep = c.take<int>(1);
+  L.n_cand = c.take<unsigned long long>(2);
   L.sel_counts = c.take<int>(mixed ? select_count_blocks((int)T) : 0);
   L.acc = c.take<EvAcc>(1);
   L.acc_col = c.take<double2>(E);
@@ -477,6 +478,7 @@ static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R, b
   ra.scratch = scr + L.red;
   ra.out = e.d_out;
   ra.n_refined = R.mixed ? (const int *)(scr + L.n_list) : nullptr;
+  ra.n_cand = R.mixed ? (const unsigned long long *)(scr + L.n_cand) : nullptr;
   return DOTPE_OK;
 }
 
@@ -488,6 +490,7 @@ static int event_begin(Event &e, EventRun &R, cudaStream_t st) {
   else
     CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.status, 0, 4, st));
+  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.n_cand, 0, 16, st));
   CUDA_OR_FAIL(record(e.ev_start, st));
   launch_prep(R.pa, st);
   return DOTPE_OK;
@@ -523,6 +526,7 @@ static EpiParams screen_params(const EventRun &R) {
   Ps.track_max = 1;
   Ps.screen_ml = (R.P.cut_delta > 0.f) ? 1 : 0;
   Ps.margin_k = MIXED_MARGIN_K;
+  Ps.n_cand = (unsigned long long *)(R.scr + R.L.n_cand);
   return Ps;
 }
 
@@ -860,8 +864,9 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
   ctx->band_cache[key] = best.band;
   ctx->tev_cache[key] = best.tev;
   R.W.band = best.band;
-  // the tuning runs raised the running maximum: start the real launch afresh
+  // the tuning runs raised the running maximum and the counters: start the real launch afresh
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
+  CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.n_cand, 0, 16, st));
   return DOTPE_OK;
 }
 
@@ -2434,6 +2439,8 @@ int dotpe_evidence(dotpe_ctx *ctx, uint64_t event_id, dotpe_evidence_out *out) {
   out->lnl_ml_threshold = r.threshold;
   out->device_status = r.status;
   out->n_refined_tiles = r.n_refined;
+  out->n_screen_candidates = r.n_cand;
+  out->n_screen_evaluated = r.n_eval;
   if (r.status == DEV_E_NONFINITE) return fail(DOTPE_E_INVALID, "non-finite or non-positive event input");
   if (r.status == DEV_E_TIMEOUT) return fail(DOTPE_E_TIMEOUT, "device wait timed out");
   if (r.status != 0) return fail(DOTPE_E_DEVICE, "device status %d", r.status);
@@ -2646,7 +2653,7 @@ int dotpe_evidence_merge(int n_shards, const dotpe_shard *shards, int64_t n_ext,
   memset(&o, 0, sizeof(o));
   o.max_lnl_ml = -INFINITY;
   o.lnl_ml_threshold = -INFINITY;
-  bool refined = true;
+  bool refined = true, screened = true;
   for (int r = 0; r < n_shards; ++r) {
     const dotpe_evidence_out &e = shards[r].ev;
     const double ls1 = e.ln_z + std::log((double)shards[r].n_int) + std::log((double)n_ext) +
@@ -2671,8 +2678,12 @@ int dotpe_evidence_merge(int n_shards, const dotpe_shard *shards, int64_t n_ext,
     if (o.device_status == 0) o.device_status = e.device_status;
     if (e.n_refined_tiles < 0) refined = false;
     else o.n_refined_tiles += e.n_refined_tiles;
+    if (e.n_screen_candidates < 0 || e.n_screen_evaluated < 0) screened = false;
+    o.n_screen_candidates += e.n_screen_candidates;
+    o.n_screen_evaluated += e.n_screen_evaluated;
   }
   if (!refined) o.n_refined_tiles = -1;
+  if (!screened) o.n_screen_candidates = o.n_screen_evaluated = -1;
   // per-sample marginals: the shards' sums added, then sum_e P_e^2
   L spe;
   for (int64_t k = 0; k < n_ext; ++k) {

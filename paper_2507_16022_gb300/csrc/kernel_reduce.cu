@@ -272,6 +272,8 @@ __global__ void __launch_bounds__(1024) reduce_final_kernel(ReduceArgs a) {
   o.threshold = (a.cut_delta > 0.f) ? (double)(*a.ml_running) - (double)a.cut_delta : -INFINITY;
   o.status = *a.status;
   o.n_refined = a.n_refined ? *a.n_refined : -1;
+  o.n_cand = a.n_cand ? (long long)a.n_cand[0] : -1;
+  o.n_eval = a.n_cand ? (long long)a.n_cand[1] : -1;
   *a.out = o;
 }
 

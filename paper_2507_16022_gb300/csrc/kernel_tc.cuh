@@ -500,6 +500,8 @@ __global__ void __launch_bounds__(NT, 1)
           const float thr2 = 2.f * thr;
           uint32_t cand = 0;
           int npool = 0;  // warp-uniform
+          int ncand = 0;  // the warp's candidates (warp-uniform)
+          int neval = 0;  // this lane's evaluations over the phase grid
           float *pz = &T.pz[ew * CAND_POOL * 2 * MAXM];
           int *ptag = &T.ptag[ew * CAND_POOL];
           const int mlast = M > 2 ? 2 : 0;  // first mode of the pair left in v after the mode loop
@@ -542,6 +544,7 @@ __global__ void __launch_bounds__(NT, 1)
                 if (lane >= o) incl += y;
               }
               const int total = __shfl_sync(0xffffffffu, incl, 31);
+              ncand += total;
               int slot = npool + incl - cnt;
               uint32_t kept = 0;
 #pragma unroll
@@ -626,6 +629,7 @@ __global__ void __launch_bounds__(NT, 1)
                 if (bound >= thr && !(bound < best)) {
                   int argo;
                   const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
+                  ++neval;
                   const long long gidx = (io * P.n_ext + e0 + el) * (long long)P.n_phi + argo;
                   if (ml > best || (ml == best && gidx < barg)) {
                     best = ml;
@@ -666,6 +670,13 @@ __global__ void __launch_bounds__(NT, 1)
               npool = min(CAND_POOL, npool + __popc(bal));
             }
             __syncwarp();
+          }
+          if (P.n_cand) {
+            const int ne = __reduce_add_sync(0xffffffffu, neval);
+            if (lane == 0 && ncand > 0) {
+              atomicAdd(&P.n_cand[0], (unsigned long long)ncand);
+              atomicAdd(&P.n_cand[1], (unsigned long long)ne);
+            }
           }
         }
         // outputs of the two partial tiles: empty marginal partials and each one's best ln L^ML
@@ -735,6 +746,7 @@ __global__ void __launch_bounds__(NT, 1)
         // Rounds: each lane picks its highest remaining bound; the warp reads the
         // accumulator columns its lanes picked (tcgen05.ld takes one column for the
         // whole warp), then each lane evaluates its own pick.
+        int neval = 0;
 #pragma unroll 1
         while (true) {
           int jm = 0;
@@ -778,11 +790,20 @@ __global__ void __launch_bounds__(NT, 1)
             hh_tile<HH>(mrec, &T.qs[el * MAXD * REC], P, C0, Cr, Ci);
             int argo;
             const float ml = pair_ml(Zr, Zi, C0, Cr, Ci, thr, false, P, T.ph, argo);
+            ++neval;
             const long long g = (i * P.n_ext + e) * (long long)P.n_phi + argo;
             if (ml > best || (ml == best && g < barg)) {
               best = ml;
               barg = g;
             }
+          }
+        }
+        if (P.n_cand) {
+          // here every pair taken is evaluated: both counters alike
+          const int ne = __reduce_add_sync(0xffffffffu, neval);
+          if (lane == 0 && ne > 0) {
+            atomicAdd(&P.n_cand[0], (unsigned long long)ne);
+            atomicAdd(&P.n_cand[1], (unsigned long long)ne);
           }
         }
         // the accumulators are no longer needed: release the buffer to the MMA warp

@@ -191,6 +191,7 @@ struct ReduceOut {
   double threshold;
   int status;
   int n_refined;  // tiles refined in split precision (mixed), else -1
+  long long n_cand, n_eval;  // screening statistics (mixed), else -1
 };
 // FP64 accumulators across bank blocks: (m, s) pairs with s = 0 meaning empty.
 struct EvAcc {
@@ -219,6 +220,7 @@ struct ReduceArgs {
   void *scratch;     // reduce_scratch_bytes() of device memory
   const int *status;
   const int *n_refined;  // optional
+  const unsigned long long *n_cand;  // optional: the screen's two counters
   ReduceOut *out;
 };
 void launch_reduce_block(const ReduceArgs &a, cudaStream_t st);

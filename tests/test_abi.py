@@ -42,7 +42,7 @@ def test_binding_lists_every_symbol():
 def test_strerror_and_version(lib):
     import paper_2507_16022_gb300 as dp
     L = dp.load()
-    assert L.dotpe_version() == 6
+    assert L.dotpe_version() == 7
     assert L.dotpe_strerror(dp.DOTPE_E_ADMISSION).decode() == "event can never fit the HBM budget"
     assert L.dotpe_strerror(12345).decode() == "unknown status"
 
