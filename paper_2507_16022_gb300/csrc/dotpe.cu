@@ -569,6 +569,21 @@ static int launch_tev(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, co
 
 // The fused kernel(s) of the current block of one event (mixed: screen,
 // selection, refinement over the event's own list).
+// The <h|h> bound of every pair of the current bank block on the tensor cores,
+// for the 64-sample screen P (when the event's scratch has room for it).
+static int hh_bound_pass(dotpe_ctx *ctx, const Event &e, EventRun &R, EpiParams &P, cudaStream_t st) {
+  if (R.L.hb_bytes == 0) return DOTPE_OK;
+  HbDelta dl;
+  for (int p = 0; p < NPAIR; ++p) dl.pdelta[p] = R.P.pdelta[p];
+  __nv_bfloat16 *hmin = nullptr;
+  if (launch_hh_bound(R.P.n_int, e.NE, e.D, dl, R.P.mx, R.pa.qx, R.scr + R.L.hb, &hmin, ctx->n_sms, R.P.status,
+                      st) != 0)
+    return fail(DOTPE_E_DEVICE, "<h|h> bound launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+  P.hmin = hmin;
+  P.hmin_ld = hb_ld(e.NE);
+  return DOTPE_OK;
+}
+
 static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, cudaStream_t st) {
   Bank &b = *e.bank;
   if (e.prec == DOTPE_PREC_FP32) {
@@ -594,17 +609,7 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
   }
   W.P = screen_params(R);
   T.tev = launch_tev(ctx, e, R.L, W.P, false);
-  if (T.tev == 64 && R.L.hb_bytes > 0) {
-    // the <h|h> bound of every pair of the block on the tensor cores, read by the screen
-    HbDelta dl;
-    for (int p = 0; p < NPAIR; ++p) dl.pdelta[p] = R.P.pdelta[p];
-    __nv_bfloat16 *hmin = nullptr;
-    if (launch_hh_bound(R.P.n_int, e.NE, e.D, dl, R.P.mx, R.pa.qx, R.scr + R.L.hb, &hmin, ctx->n_sms,
-                        R.P.status, st) != 0)
-      return fail(DOTPE_E_DEVICE, "<h|h> bound launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-    W.P.hmin = hmin;
-    W.P.hmin_ld = hb_ld(e.NE);
-  }
+  if (T.tev == 64 && (rc = hh_bound_pass(ctx, e, R, W.P, st)) != DOTPE_OK) return rc;
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
   if (last_block) CUDA_OR_FAIL(record(e.ev_ks, st));
@@ -828,6 +833,8 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
   std::vector<int> tevs{32};
   if (ctx->wide_tiles && !split_main && e.bank->n_pol != 2 && !W.P.lnl_tile && (W.P.gemm_only || W.P.screen_ml))
     tevs.push_back(64);
+  // the 64-sample candidates timed as they run: with the <h|h> bound where the event has it
+  if (R.mixed && tevs.back() == 64 && (rc = hh_bound_pass(ctx, e, R, W.P, st)) != DOTPE_OK) return rc;
   const int dflt = tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, prec_split(e.prec), R.L.n_etile);
   struct Cand { int tev, band; };
   std::vector<Cand> cand;

@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(HB_NT, 1)
         }
         const int64_t i = (int64_t)it * HB_TI + row;
         if (i < a.n_rows)
-          *reinterpret_cast<uint4 *>(a.out + i * a.ld + (int64_t)et * HB_TE + 8 * part) = make_uint4(o[0], o[1], o[2], o[3]);
+          __stcs(reinterpret_cast<uint4 *>(a.out + i * a.ld + (int64_t)et * HB_TE + 8 * part),
+                 make_uint4(o[0], o[1], o[2], o[3]));  // streamed: read once by the screen
       }
     }
   }

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(NT, 1)
           const uint4 *src = reinterpret_cast<const uint4 *>(P.hmin + ib * P.hmin_ld + e0 + half * EHALF);
 #pragma unroll
           for (int v4 = 0; v4 < EHALF / 8; ++v4) {
-            const uint4 w = __ldg(src + v4);
+            const uint4 w = __ldcs(src + v4);  // read once: evict first, keep the operand band in L2
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
