@@ -567,8 +567,6 @@ static int launch_tev(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, co
   return it != ctx->tev_cache.end() ? it->second : 64;
 }
 
-// The fused kernel(s) of the current block of one event (mixed: screen,
-// selection, refinement over the event's own list).
 // The <h|h> bound of every pair of the current bank block on the tensor cores,
 // for the 64-sample screen P (when the event's scratch has room for it).
 static int hh_bound_pass(dotpe_ctx *ctx, const Event &e, EventRun &R, EpiParams &P, cudaStream_t st) {
@@ -584,6 +582,8 @@ static int hh_bound_pass(dotpe_ctx *ctx, const Event &e, EventRun &R, EpiParams 
   return DOTPE_OK;
 }
 
+// The fused kernel(s) of the current block of one event (mixed: screen,
+// selection, refinement over the event's own list).
 static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, cudaStream_t st) {
   Bank &b = *e.bank;
   if (e.prec == DOTPE_PREC_FP32) {

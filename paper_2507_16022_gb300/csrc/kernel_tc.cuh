@@ -160,9 +160,11 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
   const int np = tc_pilot_tiles(W, TEV);
   const int local = w - Bt.begin[k];
   if (local < np) {
-    // pilot tile: bank tiles evenly spread, extrinsic tiles scrambled
-    it = (int)(((long long)local * W.n_itile) / np);
-    et = (int)(((unsigned long long)local * 2654435761ull) % (unsigned long long)nw);
+    // pilot tile: row a of the grid of spread bank tiles, column c of the spread extrinsic tiles
+    const int nc = min(nw, TC_PILOT_COLS), nr = (np + nc - 1) / nc;
+    const int a = local / nc, c = local - a * nc;
+    it = (int)(((long long)a * W.n_itile) / nr);
+    et = (int)(((2ll * c + 1) * nw) / (2 * nc));
     return;
   }
   super_tile(local - np, W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);

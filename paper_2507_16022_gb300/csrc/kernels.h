@@ -345,7 +345,11 @@ void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cd
 // of the event's work tiles is screened first, so that the running maximum,
 // and with it the cut's threshold, is near its final value before the bulk of
 // the tiles (which then skip almost every pair on their bounds) is screened.
-// The pilot tiles are screened again in their place in the band order.
+// They form a grid of evenly spread bank tiles by up to TC_PILOT_COLS evenly
+// spread extrinsic tiles, the bank tile slowest, so that each operand tile
+// the pilots read comes from memory once.  The pilot tiles are screened again
+// in their place in the band order.
+constexpr int TC_PILOT_COLS = 8;
 __host__ __device__ inline int tc_pilot_tiles(const TcEvent &w, int tev) {
   if (!w.P.screen_ml || w.P.gemm_only || w.P.cut_delta <= 0.f || w.P.lnl_tile) return 0;
   const int rs = tev / TC_TE;
