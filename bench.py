@@ -90,6 +90,18 @@ def presel_traffic(simt, rb, D, NT, B, I):
     return t["bytes"] / t["rows"] * I
 
 
+def tile_flags(dp, args):
+    """Context flags of the tile options on the command line."""
+    return ((dp.DOTPE_CONFIG_NARROW_TILES if args.narrow_tiles else 0)
+            | (dp.DOTPE_CONFIG_SINGLE_CTA_TILES if args.single_cta_tiles else 0))
+
+
+def tile_name(args):
+    if args.narrow_tiles:
+        return "128 x 32-sample tiles"
+    return "128 x 64-sample tiles, one SM each" if args.single_cta_tiles else "256 x 64-sample tiles on CTA pairs (default)"
+
+
 def rank_seed(base, rank):
     """Each rank draws its own events (independent problems: no data exchange)."""
     return base + 1000 * rank
@@ -1183,7 +1195,7 @@ def bench_gemm(args, dp, ctx_factory, torch, dev):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
         "config": {"workload": f"GEMM-only pass, I={I} x E={E}, M={M}, B={B}",
-                   "tiles": "32-sample" if args.narrow_tiles else "64-sample (default)",
+                   "tiles": tile_name(args),
                    "note": "median of the fused launch's device time over the steps; results not valid"},
         "roofline": {"bound": "tensor", "achieved": tf, "peak": burst, "unit": "TFLOP/s", "frac": tf / burst,
                      "traffic": None, "kernel": "tc_fused_kernel, GEMM-only epilogue", "kernel_ms": ms,
@@ -1220,6 +1232,8 @@ def main():
                     help="event: skip the bounded serving stream reported beside the single-event numbers")
     ap.add_argument("--narrow-tiles", action="store_true",
                     help="screening and GEMM-only launches in 32-sample tiles (DOTPE_CONFIG_NARROW_TILES)")
+    ap.add_argument("--single-cta-tiles", action="store_true",
+                    help="64-sample tiles on one SM each, not CTA pairs (DOTPE_CONFIG_SINGLE_CTA_TILES)")
     args = ap.parse_args()
     if args.workload == "serve" and "--events" not in sys.argv:
         args.events = 2000
@@ -1260,8 +1274,7 @@ def main():
         elif args.workload == "pipeline":
             line = bench_pipeline(args, dp, lambda: dp.dotpe_create(local), torch, dev)
         elif args.workload == "gemm":
-            line = bench_gemm(args, dp, lambda: dp.dotpe_create(
-                local, flags=dp.DOTPE_CONFIG_NARROW_TILES if args.narrow_tiles else 0), torch, dev)
+            line = bench_gemm(args, dp, lambda: dp.dotpe_create(local, flags=tile_flags(dp, args)), torch, dev)
         else:
             line = bench_serve(args, dp, lambda: dp.dotpe_create(local, max_batch=args.max_batch), torch, dev)
         print(json.dumps(line), flush=True)
@@ -1276,8 +1289,7 @@ def main():
     events = [wl.event] + [synth.make_event(rng, wl.bank, wl.ext, D, snr=kw["snr"], n_phi=N_PHI)
                            for _ in range(args.events - 1)]
 
-    ctx = dp.dotpe_create(local, flags=(dp.DOTPE_CONFIG_AUTOTUNE if args.autotune else 0)
-                          | (dp.DOTPE_CONFIG_NARROW_TILES if args.narrow_tiles else 0))
+    ctx = dp.dotpe_create(local, flags=(dp.DOTPE_CONFIG_AUTOTUNE if args.autotune else 0) | tile_flags(dp, args))
     bid = dp.dotpe_bank_load(ctx, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
     dev = torch.device("cuda", local)
 

@@ -102,6 +102,9 @@ typedef struct dotpe_ctx dotpe_ctx;
  * set of N = 128 per mode, twice the MMA work per operand byte).  Results are
  * the same either way; with DOTPE_CONFIG_AUTOTUNE the tuner times both. */
 #define DOTPE_CONFIG_NARROW_TILES 0x4
+/* 64-sample tiles on one SM each instead of CTA pairs (two SMs sharing each
+ * MMA, cta_group::2, each loading half of the extrinsic operand tile) */
+#define DOTPE_CONFIG_SINGLE_CTA_TILES 0x8
 
 typedef struct dotpe_config {
   int device;                /* CUDA ordinal */

@@ -30,6 +30,7 @@ DOTPE_E_UNSUPPORTED = -8
 DOTPE_PREC_FP32, DOTPE_PREC_BF16, DOTPE_PREC_FP16, DOTPE_PREC_BF16X3 = 0, 1, 2, 3
 DOTPE_PREC_FP16X3, DOTPE_PREC_MIXED = 4, 5
 DOTPE_CONFIG_AUTOTUNE, DOTPE_CONFIG_NO_GRAPHS, DOTPE_CONFIG_NARROW_TILES = 0x1, 0x2, 0x4
+DOTPE_CONFIG_SINGLE_CTA_TILES = 0x8
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4, "mixed": 5}
 DOTPE_C128, DOTPE_C64 = 0, 1
 DOTPE_FLAG_STORE_LNL = 0x1

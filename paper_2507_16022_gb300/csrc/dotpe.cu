@@ -182,6 +182,7 @@ struct dotpe_ctx {
   std::unordered_map<std::string, int> band_cache;                        // shape key -> band
   std::unordered_map<std::string, int> tev_cache;                         // shape key -> screening tile width
   bool wide_tiles = true;  // 64-sample tiles for screening / GEMM-only launches of mode banks
+  bool pair_tiles = true;  // those tiles on CTA pairs (single events)
   std::vector<std::unordered_map<std::string, cudaGraphExec_t>> graphs;  // per slot
   double l2_band_bytes = 0;  // extrinsic operand kept in L2 per sweep of the bank
   // completion callbacks -> admission worker
@@ -336,6 +337,7 @@ static int tc_launch_of(dotpe_ctx *ctx, const Bank &b, int prec, TcLaunch &T) {
   T.bf16 = bf;
   T.split = prec_split(prec) && prec != DOTPE_PREC_MIXED;
   T.sep = T.split;  // full split runs keep the low-order terms apart (precision first)
+  T.pair = ctx->pair_tiles;  // taken by single-event launches of 64-sample tiles
   T.consec = true;
   for (int m = 1; m < b.M; ++m)
     if (b.mode_m[m] != b.mode_m[m - 1] + 1) T.consec = false;
@@ -1631,6 +1633,7 @@ int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
   ctx->max_batch = c.max_batch > 1 ? c.max_batch : 1;
   ctx->autotune = (c.flags & DOTPE_CONFIG_AUTOTUNE) != 0;
   ctx->wide_tiles = (c.flags & DOTPE_CONFIG_NARROW_TILES) == 0;
+  ctx->pair_tiles = (c.flags & DOTPE_CONFIG_SINGLE_CTA_TILES) == 0;
   ctx->use_graphs = (c.flags & DOTPE_CONFIG_NO_GRAPHS) == 0;
   ctx->graphs.resize(ns);
   ctx->streams.resize(ns);

@@ -57,14 +57,15 @@ constexpr int EPT = NEPI * 32;       // epilogue threads
 constexpr uint32_t A_BYTES = TI * BK * 2;  // one k-block of the bank tile
 constexpr int KBX = 2;  // k-blocks per stage (one 3-D TMA box)
 // Pipeline: single pass = 4 stages of {A, B} x 2 k-blocks (48 KB; 3 x 64 KB
-// with the 64-sample tile); split precision = 2 stages of {A_hi, A_lo, B_hi,
-// B_lo} x 2 k-blocks (96 KB), whose three MMA groups (hi*hi, hi*lo, lo*hi)
-// share one load of each plane.
-template <bool SPLIT, int TEV> struct Pipe {
+// with the 64-sample tile, 4 x 48 KB when a CTA pair shares it); split
+// precision = 2 stages of {A_hi, A_lo, B_hi, B_lo} x 2 k-blocks (96 KB), whose
+// three MMA groups (hi*hi, hi*lo, lo*hi) share one load of each plane.
+template <bool SPLIT, int TEV, bool PAIR = false> struct Pipe {
   static constexpr int BN = 2 * TEV;  // extrinsic operand rows of a tile: N of every MMA
   static constexpr int NPL = SPLIT ? 2 : 1;
-  static constexpr int ST = SPLIT ? 2 : (TEV == 64 ? 3 : 4);
-  static constexpr uint32_t B_BYTES = BN * BK * 2;  // one k-block
+  static constexpr int ST = SPLIT ? 2 : (PAIR ? 4 : (TEV == 64 ? 3 : 4));
+  // one k-block of the extrinsic operand in this CTA (a pair: half of the N rows each)
+  static constexpr uint32_t B_BYTES = (PAIR ? BN / 2 : BN) * BK * 2;
   static constexpr uint32_t A_ST = KBX * A_BYTES, B_ST = KBX * B_BYTES;  // per plane
   static constexpr uint32_t STAGE = NPL * (A_ST + B_ST);
   static constexpr uint32_t BUF_COLS = MAXM * BN;  // TMEM columns of one accumulator set
@@ -95,12 +96,12 @@ template <int TEV> struct TcTail {
   uint32_t tmem_slot;
   int abort_flag;
 };
-template <bool SPLIT, int TEV>
+template <bool SPLIT, int TEV, bool PAIR = false>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)Pipe<SPLIT, TEV>::ST * Pipe<SPLIT, TEV>::STAGE + sizeof(TcTail<TEV>);
+  return 1024 + (size_t)Pipe<SPLIT, TEV, PAIR>::ST * Pipe<SPLIT, TEV, PAIR>::STAGE + sizeof(TcTail<TEV>);
 }
 static_assert(smem_bytes<true, 32>() <= 232448 && smem_bytes<false, 32>() <= 232448 &&
-                  smem_bytes<false, 64>() <= 232448,
+                  smem_bytes<false, 64>() <= 232448 && smem_bytes<false, 64, true>() <= 232448,
               "shared memory budget");
 }  // namespace
 
@@ -135,8 +136,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // order of super_tile.
 // With TEV = 64 the grid-mode items are 64-sample work tiles (et counts them):
 // ceil(n_etile / 2) per bank tile, banded in half as many of them.
-template <int NB, int TEV>
-__device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, int &it, int &et) {
+// PAIR: the item is a 256-row pair tile; CTA `rank` of the pair takes its bank tile 2 it + rank.
+template <int NB, int TEV, bool PAIR = false>
+__device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, int &it, int &et,
+                                          uint32_t rank = 0) {
   constexpr int RS = TEV / TE;  // 32-sample tiles per work tile
   if (Bt.glist) {
     const int2 q = Bt.glist[w];
@@ -156,27 +159,34 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
     k = lo;
   }
   const TcEvent &W = Bt.w[k];
+  const int ni = PAIR ? (W.n_itile + 1) / 2 : W.n_itile;  // bank tiles (pair tiles) of the event
   const int nw = (W.n_etile + RS - 1) / RS, bw = W.band / RS;
-  const int np = tc_pilot_tiles(W, TEV);
+  const int np = tc_pilot_tiles(W, TEV, PAIR);
   const int local = w - Bt.begin[k];
   if (local < np) {
     // pilot tile: row a of the grid of spread bank tiles, column c of the spread extrinsic tiles
     const int nc = min(nw, TC_PILOT_COLS), nr = (np + nc - 1) / nc;
     const int a = local / nc, c = local - a * nc;
-    it = (int)(((long long)a * W.n_itile) / nr);
+    it = (int)(((long long)a * ni) / nr);
     et = (int)(((2ll * c + 1) * nw) / (2 * nc));
-    return;
+  } else {
+    super_tile(local - np, ni, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
   }
-  super_tile(local - np, W.n_itile, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
+  if (PAIR) it = 2 * it + (int)rank;
 }
 
-template <bool BF16, int HH, bool SPLIT, int NB, bool SEP, int TEV>
+// PAIR: launched in clusters of two CTAs that run each MMA as one (cta_group::2,
+// M = 256): each CTA loads its own 128 bank rows and half of the tile's N
+// extrinsic rows, the even CTA issues the MMAs and commits them to both, and
+// each CTA's epilogue reads its own rows' accumulators from its own TMEM.
+template <bool BF16, int HH, bool SPLIT, int NB, bool SEP, int TEV, bool PAIR = false>
 __global__ void __launch_bounds__(NT, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcBatch<NB> Bt,
                     const TcCommon C) {
   static_assert(SPLIT || !SEP, "a separate low-order accumulator needs split operands");
   static_assert(TEV == 32 || (TEV == 64 && !SPLIT && HH != 2), "64-sample tiles: single-pass mode banks");
-  using PP = Pipe<SPLIT, TEV>;
+  static_assert(!PAIR || (TEV == 64 && NB == 1), "CTA pairs: 64-sample tiles of one event");
+  using PP = Pipe<SPLIT, TEV, PAIR>;
   using TcTail = dotpe::TcTail<TEV>;
   constexpr int ST = PP::ST, NPL = PP::NPL, BN = PP::BN;
   constexpr uint32_t STAGE_BYTES = PP::STAGE, A_ST = PP::A_ST, B_ST = PP::B_ST, B_BYTES = PP::B_BYTES;
@@ -200,6 +210,10 @@ __global__ void __launch_bounds__(NT, 1)
   const int n_work = Bt.glist ? *Bt.glist_n : Bt.begin[Bt.n];
   const int nst = (C.kb + KBX - 1) / KBX;  // stages per mode (an odd last k-block is zero-filled)
   const unsigned long long wait_ns = Bt.w[0].P.wait_ns;
+  // work items: per CTA, or per CTA pair (consecutive blocks form a cluster)
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const int w0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int wstep = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(&T.full[s], 1);
@@ -207,7 +221,7 @@ __global__ void __launch_bounds__(NT, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&T.tfull[b], 1);
-      mbar_init(&T.tempty[b], NEPI);
+      mbar_init(&T.tempty[b], PAIR ? 2 * NEPI : NEPI);  // a pair: both CTAs' epilogue warps
     }
     mbar_init(&T.drain, 1);
     T.abort_flag = 0;
@@ -217,41 +231,66 @@ __global__ void __launch_bounds__(NT, 1)
     tma_prefetch_desc(&mapA);
     tma_prefetch_desc(&Bt.mapB[0]);
   }
-  if (warp == 1) tmem_alloc(&T.tmem_slot, TMEM_COLS);
+  if (warp == 1) {
+    if constexpr (PAIR) tmem_alloc_pair(&T.tmem_slot, TMEM_COLS);
+    else tmem_alloc(&T.tmem_slot, TMEM_COLS);
+  }
   tc_fence_before();
   __syncthreads();
+  // a pair: the peer's barriers are initialised before any copy or arrival reaches them
+  if constexpr (PAIR) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = T.tmem_slot;
   volatile int *abortp = &T.abort_flag;
+  // this CTA's epilogue warps hand the accumulator set back (a pair: to the even CTA's barrier)
+  auto release_acc = [&](int b) {
+    if (PAIR && rank != 0) mbar_arrive_remote(peer_addr(smem_u32(&T.tempty[b]), 0));
+    else mbar_arrive(&T.tempty[b]);
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       uint32_t q = 0;
       bool ok = !Bt.w[0].P.test_stall;
-      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+      for (int w = w0; w < n_work && ok; w += wstep) {
         int k, it, et;
-        work_tile<NB, TEV>(Bt, w, k, it, et);
+        work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank);
         if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
         const TcEvent &W = Bt.w[k];
         for (int h2 = 0; h2 < NUSE; ++h2)
         for (int m = 0; m < M && ok; ++m) {
           const int arow = m * C.a_mode_rows + W.a_row0 + it * TI;
-          const int brow = m * W.b_mode_rows + et * BN;
+          // a pair: this CTA's half of the tile's extrinsic rows
+          const int brow = m * W.b_mode_rows + et * BN + (PAIR ? (int)rank * (BN / 2) : 0);
           for (int ks = 0; ks < nst; ++ks, ++q) {
             const int s = q % ST;
             const uint32_t n = q / ST;
             if (n > 0 && !(ok = mbar_wait(&T.empty[s], (n - 1) & 1, nullptr, abortp, wait_ns))) break;
-            mbar_expect_tx(&T.full[s], STAGE_BYTES);
+            if constexpr (PAIR) {
+              // both CTAs' copies complete on the even CTA's barrier, which expects them all
+              if (rank == 0) mbar_expect_tx(&T.full[s], 2 * STAGE_BYTES);
+              const uint32_t fb = peer_addr(smem_u32(&T.full[s]), 0);
+              tma_load_3d_pair(sA + s * A_ST, &mapA, fb, 0, arow, ks * KBX);
+              tma_load_3d_pair(sB + s * B_ST, &Bt.mapB[k], fb, 0, brow, ks * KBX);
+            } else {
+              mbar_expect_tx(&T.full[s], STAGE_BYTES);
 #pragma unroll
-            for (int pl = 0; pl < NPL; ++pl) {
-              tma_load_3d(sA + (s * NPL + pl) * A_ST, &mapA, &T.full[s], 0, pl * C.a_plane_rows + arow, ks * KBX);
-              tma_load_3d(sB + (s * NPL + pl) * B_ST, &Bt.mapB[k], &T.full[s], 0, pl * W.b_plane_rows + brow, ks * KBX);
+              for (int pl = 0; pl < NPL; ++pl) {
+                tma_load_3d(sA + (s * NPL + pl) * A_ST, &mapA, &T.full[s], 0, pl * C.a_plane_rows + arow, ks * KBX);
+                tma_load_3d(sB + (s * NPL + pl) * B_ST, &Bt.mapB[k], &T.full[s], 0, pl * W.b_plane_rows + brow,
+                            ks * KBX);
+              }
             }
           }
         }
       }
-      if (!ok) {
+      if (PAIR && rank != 0 && !ok) {
+        // the odd CTA's copies complete on the even CTA's barrier: give those in flight time to land
+        const uint64_t t0 = global_ns();
+        while (global_ns() - t0 < 2000000ull) {
+        }
+      } else if (!ok) {
         // let copies already in flight land before the CTA exits
         uint32_t first = q > (uint32_t)ST ? q - ST : 0;
         for (uint32_t j = first; j < q; ++j) {
@@ -265,14 +304,16 @@ __global__ void __launch_bounds__(NT, 1)
     // The whole warp walks the schedule (so descriptors and addresses stay
     // warp-uniform); lane 0 issues every MMA and commit (a commit tracks the
     // MMAs of the thread that issues it).
-    constexpr uint32_t idesc = idesc_f16(128, BN, BF16);
+    // (a pair: the even CTA issues M = 256 MMAs over both CTAs' operands; the
+    // odd CTA's MMA warp only holds its TMEM until they are done)
+    constexpr uint32_t idesc = idesc_f16(PAIR ? 256 : 128, BN, BF16);
     const bool issuer = (lane == 0);
     uint32_t q = 0, u = 0;
-    bool ok = true;
-    for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+    bool ok = !(PAIR && rank != 0);
+    for (int w = w0; w < n_work && ok; w += wstep) {
       if (Bt.gate) {
         int k, it, et;
-        work_tile<NB, TEV>(Bt, w, k, it, et);
+        work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank);
         if (Bt.gate[k] != Bt.gate_want) continue;
       }
       for (int h2 = 0; h2 < NUSE && ok; ++h2) {
@@ -309,6 +350,8 @@ __global__ void __launch_bounds__(NT, 1)
                   tc_mma(dhh, ah + 2 * k, bh + 2 * k, idesc_sep, t16 >= 3 ? 1u : 0u);      // hi * hi
                   tc_mma(dlo, ah + 2 * k, bl + 2 * k, idesc_sep, t16 > 0 ? 1u : 0u);       // hi * lo
                   tc_mma(dlo, al + 2 * k, bh + 2 * k, idesc_sep, 1u);                      // lo * hi
+                } else if (PAIR) {
+                  tc_mma_pair(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
                 } else {
                   tc_mma(dcol, ah + 2 * k, bh + 2 * k, idesc, (ks | kx | k) ? 1u : 0u);
                   if (SPLIT) {
@@ -318,20 +361,32 @@ __global__ void __launch_bounds__(NT, 1)
                 }
               }
             }
-            tc_commit(&T.empty[s]);
+            if (PAIR) tc_commit_pair(&T.empty[s], 0x3);
+            else tc_commit(&T.empty[s]);
           }
           __syncwarp();
         }
       }
-      if (ok && issuer) tc_commit(&T.tfull[b]);
+      if (ok && issuer) {
+        if (PAIR) tc_commit_pair(&T.tfull[b], 0x3);
+        else tc_commit(&T.tfull[b]);
+      }
       __syncwarp();
       }
     }
-    // all MMAs of this CTA complete before TMEM is released
-    if (issuer) tc_commit(&T.drain);
-    __syncwarp();
+    // all MMAs of this CTA (a pair: of the even CTA, on both) complete before TMEM is released
     volatile int no_abort = 0;
-    mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
+    if (PAIR && rank != 0) {
+      // the even CTA commits the drain once its work is issued: wait for it over the whole launch
+      mbar_wait(&T.drain, 0, nullptr, &no_abort, 20000000000ull);
+    } else {
+      if (issuer) {
+        if (PAIR) tc_commit_pair(&T.drain, 0x3);
+        else tc_commit(&T.drain);
+      }
+      __syncwarp();
+      mbar_wait(&T.drain, 0, nullptr, &no_abort, 500000000ull);
+    }
   } else {
     // ---------------- epilogue (256 threads: one tile row, half the samples each) ----------------
     const int ew = warp - 2;      // 0..7
@@ -350,9 +405,9 @@ __global__ void __launch_bounds__(NT, 1)
     double lwi = 0.0;
     int cur_it = -1, cur_k = -1;
     uint32_t u = 0;
-    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+    for (int w = w0; w < n_work; w += wstep) {
       int k, it, et;
-      work_tile<NB, TEV>(Bt, w, k, it, et);
+      work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank);
       if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
       const int b = ONEBUF ? 0 : (u & 1);
       const uint32_t use = ONEBUF ? u : (u >> 1);
@@ -488,7 +543,7 @@ __global__ void __launch_bounds__(NT, 1)
               }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&T.tempty[0]);
+          if (lane == 0) release_acc(0);
           best = (vi && sx == sx) ? fabsf(sx) : -1.f;
         } else {
           // Pass 1 (the accumulators read 16 columns at a time): the bound of
@@ -601,7 +656,7 @@ __global__ void __launch_bounds__(NT, 1)
               // the accumulators are no longer needed: release the buffer to the MMA warp
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(&T.tempty[0]);
+              if (lane == 0) release_acc(0);
               held = false;
             }
 #pragma unroll 1
@@ -687,11 +742,13 @@ __global__ void __launch_bounds__(NT, 1)
           T.wml[ew] = best;
           T.warg[ew] = barg;
         }
+        // (a pair's odd CTA past the last bank tile has no outputs: all its rows are invalid)
+        const bool tv = it < Bt.w[k].n_itile;
         if (vi && pe < n_etile) P.row_part[(int64_t)pe * P.n_int + i] = make_float2(-INFINITY, 0.f);
-        if (etid < TEV && e0 + etid < P.n_ext)
+        if (tv && etid < TEV && e0 + etid < P.n_ext)
           P.col_part[(int64_t)it * P.n_ext + e0 + etid] = make_float2(-INFINITY, 0.f);
         named_bar_sync(1, EPT);
-        if (etid < 2 && 2 * et + etid < n_etile) {
+        if (tv && etid < 2 && 2 * et + etid < n_etile) {
           // warps 4 h .. 4 h + 3 hold partial tile 2 et + h
           float bv = -1.f;
           long long bi = 0x7fffffffffffffffLL;
@@ -811,7 +868,7 @@ __global__ void __launch_bounds__(NT, 1)
         // the accumulators are no longer needed: release the buffer to the MMA warp
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&T.tempty[b]);
+        if (lane == 0) release_acc(b);
         // tile outputs of a screen: empty marginal partials and the tile's best ln L^ML
         warp_argmax(best, barg);
         if (lane == 0) {
@@ -876,7 +933,7 @@ __global__ void __launch_bounds__(NT, 1)
           // this warp's accumulators are in registers: release the buffer to the MMA warp
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&T.tempty[b]);
+          if (lane == 0) release_acc(b);
         }
         float x = -INFINITY, x2 = -INFINITY;
         if (vi && e < P.n_ext) {
@@ -995,7 +1052,12 @@ __global__ void __launch_bounds__(NT, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+  // a pair: neither CTA leaves while the other may still signal its barriers
+  if constexpr (PAIR) cluster_sync_all();
+  if (warp == 1) {
+    if constexpr (PAIR) tmem_dealloc_pair(tmem, TMEM_COLS);
+    else tmem_dealloc(tmem, TMEM_COLS);
+  }
   // a wait that ran out leaves this CTA's tiles of every event unfinished
   if (threadIdx.x == 0 && T.abort_flag)
     for (int k = 0; k < Bt.n; ++k) atomicCAS(Bt.w[k].P.status, 0, DEV_E_TIMEOUT);
@@ -1019,6 +1081,48 @@ cudaError_t launch_tc_variant(const TcLaunch &L, const TcBatch<NB> &bt, int grid
                     : go(tc_fused_kernel<false, 2, SPLIT, NB, SEP, TEV>);
     else
       return cudaErrorInvalidValue;
+  }
+  if constexpr (NB == 1 && TEV == 64 && !SPLIT) {
+    if (L.pair) {
+      // clusters of two CTAs (grid even)
+      auto go2 = [&](auto kern) -> cudaError_t {
+        const size_t smem = smem_bytes<false, 64, true>();
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid, 1, 1);
+        cfg.blockDim = dim3(NT, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        // no more pairs than can be resident at once (a persistent grid: a pair that
+        // waited for another to finish would add its whole share to the tail)
+        static int max_pairs = 0;
+        if (max_pairs == 0) {
+          int mc = 0;
+          if (cudaOccupancyMaxActiveClusters(&mc, kern, &cfg) != cudaSuccess || mc < 1) {
+            cudaGetLastError();
+            mc = grid / 2;
+          }
+          max_pairs = mc;
+        }
+        if (grid / 2 > max_pairs) cfg.gridDim.x = 2u * (unsigned)max_pairs;
+        e = cudaLaunchKernelEx(&cfg, kern, L.mapA, bt, L.C);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+      };
+      if (grid % 2 != 0) return cudaErrorInvalidValue;
+      if (L.bf16) return L.consec ? go2(tc_fused_kernel<true, 1, false, 1, false, 64, true>)
+                                  : go2(tc_fused_kernel<true, 0, false, 1, false, 64, true>);
+      return L.consec ? go2(tc_fused_kernel<false, 1, false, 1, false, 64, true>)
+                      : go2(tc_fused_kernel<false, 0, false, 1, false, 64, true>);
+    }
   }
   if (L.bf16) return L.consec ? go(tc_fused_kernel<true, 1, SPLIT, NB, SEP, TEV>)
                               : go(tc_fused_kernel<true, 0, SPLIT, NB, SEP, TEV>);

@@ -118,6 +118,7 @@ struct TcLaunch {
   bool pol;          // polarisation-resolved bank (row records in registers, n_det <= POL_TC_MAXD)
   bool sep;          // split: hi*lo + lo*hi in their own accumulator (see kernel_tc.cuh)
   int tev;           // extrinsic samples per work tile: 32, or 64 (single-pass mode banks, grid order)
+  bool pair;         // 64-sample tiles of one event: CTA pairs (cta_group::2, M = 256)
   const int *gate;   // optional device words per event: event k's items run only if gate[k] == gate_want
   int gate_want;
   int n_sms;
@@ -350,17 +351,18 @@ void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cd
 // the pilots read comes from memory once.  The pilot tiles are screened again
 // in their place in the band order.
 constexpr int TC_PILOT_COLS = 8;
-__host__ __device__ inline int tc_pilot_tiles(const TcEvent &w, int tev) {
+// pair: the work items are 256-row pair tiles of a CTA pair.
+__host__ __device__ inline int tc_pilot_tiles(const TcEvent &w, int tev, bool pair = false) {
   if (!w.P.screen_ml || w.P.gemm_only || w.P.cut_delta <= 0.f || w.P.lnl_tile) return 0;
   const int rs = tev / TC_TE;
-  const int t = w.n_itile * ((w.n_etile + rs - 1) / rs);
+  const int t = (pair ? (w.n_itile + 1) / 2 : w.n_itile) * ((w.n_etile + rs - 1) / rs);
   return t >= 96 ? t / 48 : 0;
 }
 
 // Work items of one event in a launch of tile width tev (grid order).
-__host__ __device__ inline int tc_work_items(const TcEvent &w, int tev) {
+__host__ __device__ inline int tc_work_items(const TcEvent &w, int tev, bool pair = false) {
   const int rs = tev / TC_TE;
-  return tc_pilot_tiles(w, tev) + w.n_itile * ((w.n_etile + rs - 1) / rs);
+  return tc_pilot_tiles(w, tev, pair) + (pair ? (w.n_itile + 1) / 2 : w.n_itile) * ((w.n_etile + rs - 1) / rs);
 }
 
 // Tensor-map encoding through the driver entry point.

@@ -692,22 +692,25 @@ def test_lnl_blocks_recomputed_without_stored_tiles(dpx):
                                                  (2048, (0, 2048), 24 * 32 + 5, 3, 4, 128)],
                          ids=lambda s: f"I{s[0]}E{s[2]}D{s[3]}M{s[4]}B{s[5]}")
 def test_screen_tile_widths_agree(dpx, shape):
-    """The served path's screening pass runs in 64-sample tiles by default and in
-    32-sample tiles under DOTPE_CONFIG_NARROW_TILES: both mark the same tiles for
-    refinement (an odd count of 32-sample tiles leaves the last 64-sample tile
-    half empty; the largest shape has enough tiles for the pilot tiles that the
-    wide screen takes first), so the events agree, and both keep ln Z between
-    the oracle's cut and uncut values (Eq. coherent_ML_selection; the largest
-    shape against the plain FP32 path with the same cut)."""
+    """The served path's screening pass runs in 64-sample tiles on CTA pairs by
+    default, in 64-sample tiles on one CTA each under DOTPE_CONFIG_SINGLE_CTA_TILES
+    and in 32-sample tiles under DOTPE_CONFIG_NARROW_TILES: all mark the same
+    tiles for refinement (an odd count of 32-sample tiles leaves the last
+    64-sample tile half empty, an odd count of bank tiles the last pair tile;
+    the largest shape has enough tiles for the pilot tiles that the wide screen
+    takes first), so the events agree, and all keep ln Z between the oracle's
+    cut and uncut values (Eq. coherent_ML_selection; the largest shape against
+    the plain FP32 path with the same cut)."""
     import oracle
     dp, ctx = dpx
     I_bank, (i0, i1), E, D, M, B = shape
     wl = synth.make_workload(n_int=I_bank, n_ext=E, n_det=D, n_modes=M, n_bins=B, snr=14.0, seed=I_bank + E,
                              ln_w="random")
     narrow = dp.dotpe_create(0, flags=dp.DOTPE_CONFIG_NARROW_TILES)
+    single = dp.dotpe_create(0, flags=dp.DOTPE_CONFIG_SINGLE_CTA_TILES)
     try:
         res = []
-        for c in (ctx, narrow):
+        for c in (ctx, narrow, single):
             bid = dp.dotpe_bank_load(c, wl.bank.h, wl.bank.f, wl.bank.w, wl.bank.mode_m, wl.bank.ln_w)
             try:
                 res.append(run(dp, c, wl, "mixed", bid=bid, i0=i0, i1=i1, cut=20.0, flags=0)["ev"])
@@ -715,7 +718,10 @@ def test_screen_tile_widths_agree(dpx, shape):
                 dp.dotpe_bank_release(c, bid)
     finally:
         dp.dotpe_destroy(narrow)
-    wide, nar = res
+        dp.dotpe_destroy(single)
+    wide, nar, one = res
+    for k in ("n_refined_tiles", "arg_i", "arg_e", "arg_o", "ln_z", "max_lnl_ml", "n_eff", "n_marginalised"):
+        assert wide[k] == one[k], k
     assert wide["n_refined_tiles"] == nar["n_refined_tiles"]
     assert (wide["arg_i"], wide["arg_e"], wide["arg_o"]) == (nar["arg_i"], nar["arg_e"], nar["arg_o"])
     assert wide["ln_z"] == pytest.approx(nar["ln_z"], abs=1e-9)
