@@ -36,11 +36,6 @@ __device__ __forceinline__ void fill_phase_tables(float2 *ph, const EpiParams &P
   }
 }
 
-// <h|h> coefficients for one pair from the row record (mrec) and column record (qrec):
-// C_0 = sum_d sum_m M_d[m,m] Q_d[m,m];  C_delta = sum_d sum_{a>b, m_a-m_b=delta} M_d[a,b] Q_d[a,b].
-// CONSEC: the modes' azimuthal numbers are consecutive, so pair (a, b) has delta = a - b.
-// Each detector accumulates into its own partial sums (independent FMA chains),
-// added at the end; records of detectors d >= n_det are zero.
 // <h|h> coefficients for a polarisation-resolved bank (Eqs. hh_ieo with the
 // polarisation index): H_{mm'} = sum_d sum_{pp'} F_p F_p' <h_{mp}|h_{m'p'}>_d.
 // The row record of detector d (mrow + d REC_P, read through the cache) holds
@@ -66,7 +61,12 @@ __device__ __forceinline__ void hh_coeffs_pol(const float *__restrict__ mrow, co
   }
 }
 
-// Row-record entry k of detector d through `mr(k)` (registers, memory or another lane).
+// <h|h> coefficients for one pair from the row record (mrec) and column record (qrec):
+// C_0 = sum_d sum_m M_d[m,m] Q_d[m,m];  C_delta = sum_d sum_{a>b, m_a-m_b=delta} M_d[a,b] Q_d[a,b].
+// CONSEC: the modes' azimuthal numbers are consecutive, so pair (a, b) has delta = a - b.
+// Each detector accumulates into its own partial sums (independent FMA chains),
+// added at the end; records of detectors d >= n_det are zero.
+// The row record's entry k of detector d is mr_at(d REC + k) (registers or memory).
 template <bool CONSEC, class Row>
 __device__ __forceinline__ void hh_coeffs_by(Row mr_at, const float *__restrict__ qrec, const EpiParams &P,
                                              float &C0, float Cr[3], float Ci[3]) {

@@ -93,6 +93,7 @@ template <int TEV> struct TcTail {
   long long warg[NEPI];
   int wnp[NEPI];
   uint64_t full[4], empty[4], tfull[2], tempty[2], drain;
+  uint64_t mfull;  // 64-sample tiles: the accumulators of modes 0 and 1 are complete
   uint32_t tmem_slot;
   int abort_flag;
 };
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(NT, 1)
       mbar_init(&T.tempty[b], PAIR ? 2 * NEPI : NEPI);  // a pair: both CTAs' epilogue warps
     }
     mbar_init(&T.drain, 1);
+    mbar_init(&T.mfull, 1);
     T.abort_flag = 0;
     mbar_fence_init();
   }
@@ -366,6 +368,13 @@ __global__ void __launch_bounds__(NT, 1)
           }
           __syncwarp();
         }
+        if (TEV == 64 && m == 1 && M >= 3 && ok && issuer) {
+          // modes 0 and 1 are issued (the MMAs run mode after mode): the screen's
+          // epilogue reads them while the other modes' MMAs run
+          if (PAIR) tc_commit_pair(&T.mfull, 0x3);
+          else tc_commit(&T.mfull);
+        }
+        __syncwarp();
       }
       if (ok && issuer) {
         if (PAIR) tc_commit_pair(&T.tfull[b], 0x3);
@@ -517,6 +526,31 @@ __global__ void __launch_bounds__(NT, 1)
           }
         }
       }
+      // 64-sample screen with three or four modes: modes 0 and 1 complete first;
+      // their share of sum_m |Z_m| per pair is read while the other modes' MMAs run
+      const bool early = TEV == 64 && !P.gemm_only && M >= 3;
+      float a01[TEV == 64 ? EHALF : 1];
+      if constexpr (TEV == 64) {
+        if (early) {
+          if (!mbar_wait(&T.mfull, use & 1, nullptr, abortp, wait_ns)) break;
+          tc_fence_after();
+          const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+          for (int g = 0; g < EHALF / 8; ++g) {
+            float v[2][16];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) tmem_ld16(tb + m * BN + 2 * (half * EHALF + 8 * g), v[m]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              float s = 0.f;
+#pragma unroll
+              for (int m = 0; m < 2; ++m) s += sqrt_near(fmaf(v[m][2 * q], v[m][2 * q], v[m][2 * q + 1] * v[m][2 * q + 1]));
+              a01[8 * g + q] = s;
+            }
+          }
+        }
+      }
       if (!mbar_wait(&T.tfull[b], use & 1, nullptr, abortp, wait_ns)) break;
       tc_fence_after();
 
@@ -566,10 +600,11 @@ __global__ void __launch_bounds__(NT, 1)
           for (int g = 0; g < EHALF / 8; ++g) {
             float a[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = 0.f;
+            for (int q = 0; q < 8; ++q) a[q] = early ? a01[8 * g + q] : 0.f;
             float v[2][16];
 #pragma unroll
             for (int m0 = 0; m0 < MAXM; m0 += 2) {
+              if (early && m0 == 0) continue;  // modes 0 and 1 are in a01
               // two modes per wait
 #pragma unroll
               for (int m = m0; m < m0 + 2; ++m)
