@@ -200,8 +200,15 @@ def test_config1_ml_cut(dpx, cfg1):
             # the frozen threshold lies at most two margins below the exact one
             assert thr - 3.0 <= ev["lnl_ml_threshold"] <= thr + 1e-3
             assert 0 < ev["n_refined_tiles"] < (1024 // 128) * (256 // 32)
+            # the screen's counters: every pair whose exact ln L^ML reaches the final
+            # threshold passes its first bound (bounds never fall below ln L^ML, the
+            # threshold only rises to it), and it evaluates a subset of what passes
+            above = int(np.sum(gcut["lnl_ml_max"] >= ev["lnl_ml_threshold"] + 1e-3))
+            assert above <= ev["n_screen_candidates"] <= ev["n_pairs"]
+            assert 1 <= ev["n_screen_evaluated"] <= ev["n_screen_candidates"]
         else:
             assert ev["n_refined_tiles"] == -1
+            assert ev["n_screen_candidates"] == -1 and ev["n_screen_evaluated"] == -1
 
 
 # ---------------------------------------------------------------------------

@@ -135,3 +135,19 @@ def test_evidence_merge_of_one_shard_is_identity():
     assert got["n_eff_ext"] == pytest.approx(s1 ** 2 / np.sum(np.exp(2 * lpe)), rel=1e-12)
     np.testing.assert_allclose(out, lpe, atol=1e-15)
     assert (got["arg_i"], got["n_refined_tiles"], got["lnl_ml_threshold"]) == (3, 7, -8.0)
+
+
+def test_evidence_merge_adds_screen_counters():
+    """The screening counters of row shards add up; a shard without them (-1, or a
+    record that does not carry them) leaves the merged counters unknown (-1)."""
+    import numpy as np
+    import paper_2507_16022_gb300 as dp
+    base = dict(ln_z=-1.0, n_eff=2.0, n_eff_int=2.0, n_eff_ext=2.0, max_lnl_ml=5.0, arg_i=0, arg_e=0, arg_o=0,
+                n_marginalised=10, n_pairs=40, lnl_ml_threshold=-15.0, device_status=0, n_refined_tiles=1)
+    lpe = np.log(np.array([0.5, 1.5]))
+    a = dict(base, n_screen_candidates=30, n_screen_evaluated=4)
+    b = dict(base, arg_i=20, n_screen_candidates=12, n_screen_evaluated=3)
+    got, _ = dp.dotpe_evidence_merge([(a, 20, lpe), (b, 20, lpe)], 8)
+    assert (got["n_screen_candidates"], got["n_screen_evaluated"]) == (42, 7)
+    got, _ = dp.dotpe_evidence_merge([(a, 20, lpe), (base, 20, lpe)], 8)
+    assert (got["n_screen_candidates"], got["n_screen_evaluated"]) == (-1, -1)
