@@ -72,7 +72,8 @@ CUT_DELTA = 20.0  # Eq. coherent_ML_selection, the paper's value
 # capture of the DRAM counters at the workload's own size (the bound's 2 bytes
 # per pair stay in L2 at small sizes, so a small capture does not scale):
 # the shape it was taken on.  None = no capture of the current kernels.
-SCREEN_TRAFFIC = {"bytes": None, "n_int": 65536, "n_ext": 4096, "source": None}
+SCREEN_TRAFFIC = {"bytes": 0.504e9 + 3.688e9, "n_int": 65536, "n_ext": 4096,
+                  "source": "profiles/mixed_65536x4096_launch_list.md"}
 
 
 # DRAM bytes (read + write) per launch of the FP32 relative-binning pre-selection
