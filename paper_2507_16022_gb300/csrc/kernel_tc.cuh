@@ -138,8 +138,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // With TEV = 64 the grid-mode items are 64-sample work tiles (et counts them):
 // ceil(n_etile / 2) per bank tile, banded in half as many of them.
 // PAIR: the item is a 256-row pair tile; CTA `rank` of the pair takes its bank tile 2 it + rank.
+// Returns false for a band-order item that a pilot tile has already screened
+// (every role of the kernel skips it: the pilot pass wrote all its outputs,
+// with a threshold no higher than the band-order pass would use).
 template <int NB, int TEV, bool PAIR = false>
-__device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, int &it, int &et,
+__device__ __forceinline__ bool work_tile(const TcBatch<NB> &Bt, int w, int &k, int &it, int &et,
                                           uint32_t rank = 0) {
   constexpr int RS = TEV / TE;  // 32-sample tiles per work tile
   if (Bt.glist) {
@@ -147,7 +150,7 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
     k = q.x;
     it = q.y / Bt.w[k].n_etile;
     et = q.y - it * Bt.w[k].n_etile;
-    return;
+    return true;
   }
   k = 0;
   if (NB > 1) {
@@ -164,16 +167,29 @@ __device__ __forceinline__ void work_tile(const TcBatch<NB> &Bt, int w, int &k, 
   const int nw = (W.n_etile + RS - 1) / RS, bw = W.band / RS;
   const int np = tc_pilot_tiles(W, TEV, PAIR);
   const int local = w - Bt.begin[k];
+  const int nc = min(nw, TC_PILOT_COLS), nr = (np + nc - 1) / nc;
+  bool run = true;
   if (local < np) {
     // pilot tile: row a of the grid of spread bank tiles, column c of the spread extrinsic tiles
-    const int nc = min(nw, TC_PILOT_COLS), nr = (np + nc - 1) / nc;
     const int a = local / nc, c = local - a * nc;
     it = (int)(((long long)a * ni) / nr);
     et = (int)(((2ll * c + 1) * nw) / (2 * nc));
   } else {
     super_tile(local - np, ni, nw, bw < 1 ? 1 : (bw > nw ? nw : bw), it, et);
+    if (np > 0) {
+      // a pilot tile again: the (a, c) of the grid that maps to (it, et), if any
+      // (column spacing nw / nc >= 1 and row spacing ni / nr >= 1: at most one)
+      const int c0 = (int)(((long long)et * nc) / nw);
+      for (int c = max(0, c0 - 1); c <= min(nc - 1, c0 + 1); ++c)
+        if ((int)(((2ll * c + 1) * nw) / (2 * nc)) == et) {
+          const int a0 = (int)(((long long)it * nr) / ni);
+          for (int a = max(0, a0 - 1); a <= a0 + 1; ++a)
+            if (a < nr && (int)(((long long)a * ni) / nr) == it && a * nc + c < np) run = false;
+        }
+    }
   }
   if (PAIR) it = 2 * it + (int)rank;
+  return run;
 }
 
 // PAIR: launched in clusters of two CTAs that run each MMA as one (cta_group::2,
@@ -257,7 +273,7 @@ __global__ void __launch_bounds__(NT, 1)
       bool ok = !Bt.w[0].P.test_stall;
       for (int w = w0; w < n_work && ok; w += wstep) {
         int k, it, et;
-        work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank);
+        if (!work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank)) continue;
         if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
         const TcEvent &W = Bt.w[k];
         for (int h2 = 0; h2 < NUSE; ++h2)
@@ -313,10 +329,10 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t q = 0, u = 0;
     bool ok = !(PAIR && rank != 0);
     for (int w = w0; w < n_work && ok; w += wstep) {
-      if (Bt.gate) {
+      {
         int k, it, et;
-        work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank);
-        if (Bt.gate[k] != Bt.gate_want) continue;
+        if (!work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank)) continue;
+        if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
       }
       for (int h2 = 0; h2 < NUSE && ok; ++h2) {
       const int b = ONEBUF ? 0 : (u & 1);
@@ -416,7 +432,7 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t u = 0;
     for (int w = w0; w < n_work; w += wstep) {
       int k, it, et;
-      work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank);
+      if (!work_tile<NB, TEV, PAIR>(Bt, w, k, it, et, rank)) continue;
       if (Bt.gate && Bt.gate[k] != Bt.gate_want) continue;
       const int b = ONEBUF ? 0 : (u & 1);
       const uint32_t use = ONEBUF ? u : (u >> 1);

@@ -348,8 +348,8 @@ void launch_sample(const SampleArgs &a, int64_t n, const double *uni, double *cd
 // the tiles (which then skip almost every pair on their bounds) is screened.
 // They form a grid of evenly spread bank tiles by up to TC_PILOT_COLS evenly
 // spread extrinsic tiles, the bank tile slowest, so that each operand tile
-// the pilots read comes from memory once.  The pilot tiles are screened again
-// in their place in the band order.
+// the pilots read comes from memory once.  The band-order sweep skips them
+// (their first pass wrote every output, with a lower threshold).
 constexpr int TC_PILOT_COLS = 8;
 // pair: the work items are 256-row pair tiles of a CTA pair.
 __host__ __device__ inline int tc_pilot_tiles(const TcEvent &w, int tev, bool pair = false) {
