@@ -179,9 +179,9 @@ __device__ __forceinline__ bool work_tile(const TcBatch<NB> &Bt, int w, int &k, 
     if (np > 0) {
       // a pilot tile again: the (a, c) of the grid that maps to (it, et), if any
       // (column spacing nw / nc >= 1 and row spacing ni / nr >= 1: at most one)
-      const int c0 = (int)(((long long)et * nc) / nw);
+      const int c0 = et * nc / nw;  // et < nw, nc <= TC_PILOT_COLS: no overflow
       for (int c = max(0, c0 - 1); c <= min(nc - 1, c0 + 1); ++c)
-        if ((int)(((2ll * c + 1) * nw) / (2 * nc)) == et) {
+        if ((2 * c + 1) * nw / (2 * nc) == et) {
           const int a0 = (int)(((long long)it * nr) / ni);
           for (int a = max(0, a0 - 1); a <= a0 + 1; ++a)
             if (a < nr && (int)(((long long)a * ni) / nr) == it && a * nc + c < np) run = false;
