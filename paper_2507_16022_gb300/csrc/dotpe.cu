@@ -350,9 +350,9 @@ static int tc_launch_of(dotpe_ctx *ctx, const Bank &b, int prec, TcLaunch &T) {
 static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bool split);
 
 // Device allocations of an event and every pointer of its plan (no launches).
-static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R, bool single = false) {
+static int event_alloc(dotpe_ctx *ctx, Event &e, cudaStream_t st, EventRun &R) {
   Bank &b = *e.bank;
-  R.L = scratch_layout(e, single && e.want_hb);
+  R.L = scratch_layout(e, e.want_hb);
   const ScratchLayout &L = R.L;
   e.scratch_bytes = L.total;
   CUDA_OR_FAIL(cudaStreamWaitEvent(st, e.ev_inputs, 0));
@@ -766,7 +766,7 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
   NvtxRange nv("dotpe:event");
   cudaStream_t st = ctx->streams[e.slot];
   EventRun R;
-  int rc = event_alloc(ctx, e, st, R, true);
+  int rc = event_alloc(ctx, e, st, R);
   if (rc != DOTPE_OK) return rc;
   {
     NvtxRange np("dotpe:prep");
@@ -946,6 +946,11 @@ static int run_batch(dotpe_ctx *ctx, const std::vector<Event *> &evs, int slot) 
         T1.tev = 64;
         for (int k = k0; k < k0 + m; ++k)
           T1.tev = std::min(T1.tev, launch_tev(ctx, *evs[k], R[k].L, W[k].P, T1.split));
+        if (mixed && T1.tev == 64)
+          for (int k = k0; k < k0 + m; ++k) {
+            int rb = hh_bound_pass(ctx, *evs[k], R[k], W[k].P, st);
+            if (rb != DOTPE_OK) return rb;
+          }
         int r = launch_tc(T1, &W[k0], m, nullptr, nullptr, st);
         if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 batch launch failed: %s", cudaGetErrorString((cudaError_t)r));
       }
@@ -1122,13 +1127,15 @@ static void progress(dotpe_ctx *ctx) {
       }
     }
     if (ctx->used + need > ctx->budget) break;
-    // a single event's screen reads the <h|h> bound from its own scratch when that fits too
-    e.want_hb = false;
-    if (grp.size() == 1 && e.group == 0 && ctx->wide_tiles) {
-      const size_t with = scratch_layout(e, true).total + keep_bytes_of(e);
+    // the screens read the <h|h> bound from the events' own scratch when, for
+    // the whole launch unit, that fits too
+    for (Event *x : grp) x->want_hb = false;
+    if (ctx->wide_tiles) {
+      size_t with = 0;
+      for (Event *x : grp) with += scratch_layout(*x, true).total + keep_bytes_of(*x);
       if (with > need && ctx->used + with <= ctx->budget) {
         need = with;
-        e.want_hb = true;
+        for (Event *x : grp) x->want_hb = true;
       }
     }
     for (size_t q = 0; q < grp.size(); ++q) ctx->queue.pop_front();
