@@ -234,10 +234,11 @@ static const float MIXED_MARGIN_K = 2.0f * 0.00048828125f;
 // maximum keep their screened values (their share of Z is below e^-30 each).
 static const float MIXED_FAR_WINDOW = 30.0f;
 
-// The screening pass of a single (not batched) mixed event with the cut on
-// reads a per-pair bound of <h|h> from the tensor-core pass when its buffer
-// (2 bytes per pair of a bank block) stays under this size.
-static const size_t HB_MAX_BYTES = (size_t)3 << 29;
+// The screening pass of a mixed event with the cut on reads a per-pair bound
+// of <h|h> from the tensor-core pass when its buffer (2 bytes per pair of a
+// bank block) stays under this size (and the launch unit's scratch with the
+// bounds fits the HBM budget).
+static const size_t HB_MAX_BYTES = (size_t)8 << 30;
 
 static ScratchLayout scratch_layout(const Event &e, bool want_hmin = false) {
   ScratchLayout L{};
