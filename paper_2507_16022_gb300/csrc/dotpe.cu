@@ -181,6 +181,7 @@ struct dotpe_ctx {
   bool autotune = false;   // time L2 band widths on first use of a shape
   std::unordered_map<std::string, int> band_cache;                        // shape key -> band
   std::unordered_map<std::string, int> tev_cache;                         // shape key -> screening tile width
+  std::unordered_map<std::string, bool> pair_cache;                       // shape key -> 64-sample tiles on CTA pairs
   bool wide_tiles = true;  // 64-sample tiles for screening / GEMM-only launches of mode banks
   bool pair_tiles = true;  // those tiles on CTA pairs (single events)
   std::vector<std::unordered_map<std::string, cudaGraphExec_t>> graphs;  // per slot
@@ -570,6 +571,14 @@ static int launch_tev(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, co
   return it != ctx->tev_cache.end() ? it->second : 64;
 }
 
+// Whether a single event's 64-sample tiles run on CTA pairs: the autotuner's
+// choice for the shape where it has one, else the context's default.
+static bool launch_pair(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L) {
+  if (!ctx->pair_tiles) return false;
+  auto it = ctx->pair_cache.find(band_key(e, L, prec_split(e.prec)));
+  return it != ctx->pair_cache.end() ? it->second : true;
+}
+
 // The <h|h> bound of every pair of the current bank block on the tensor cores,
 // for the 64-sample screen P (when the event's scratch has room for it).
 static int hh_bound_pass(dotpe_ctx *ctx, const Event &e, EventRun &R, EpiParams &P, cudaStream_t st) {
@@ -606,12 +615,14 @@ static int event_fused(dotpe_ctx *ctx, Event &e, EventRun &R, bool last_block, c
   if (!R.mixed) {
     W.P = R.P;
     T.tev = launch_tev(ctx, e, R.L, W.P, T.split);
+    T.pair = launch_pair(ctx, e, R.L);
     int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
     if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
     return DOTPE_OK;
   }
   W.P = screen_params(R);
   T.tev = launch_tev(ctx, e, R.L, W.P, false);
+  T.pair = launch_pair(ctx, e, R.L);
   if (T.tev == 64 && (rc = hh_bound_pass(ctx, e, R, W.P, st)) != DOTPE_OK) return rc;
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   if (r != 0) return fail(DOTPE_E_DEVICE, "tcgen05 kernel launch failed: %s", cudaGetErrorString((cudaError_t)r));
@@ -799,10 +810,13 @@ static int run_event(dotpe_ctx *ctx, Event &e) {
 // every bank tile meets the band's extrinsic tiles before the next band starts,
 // so the band's operand stays in L2 while the bank streams once per band.  The
 // best band width depends on the operand sizes and on how the two L2 partitions
-// share lines, and the best tile width (32 samples with two TMEM accumulator
-// sets, or 64 with one) on how much the epilogue costs against the MMAs; both
-// are chosen per shape (precision class, modes, k-blocks, extrinsic tiles) by
-// timing candidates on the first event of that shape.
+// share lines, the best tile width (32 samples with two TMEM accumulator sets,
+// or 64 with one) on how much the epilogue costs against the MMAs, and whether
+// 64-sample tiles run on CTA pairs (cta_group::2, M = 256: each SM loads half
+// of the tile's extrinsic rows) or on one SM each on how the mainloop's
+// shared-memory ingress weighs against the pair's tail; all three are chosen
+// per shape (precision class, modes, k-blocks, extrinsic tiles) by timing
+// candidates on the first event of that shape.
 // ---------------------------------------------------------------------------
 static std::string band_key(const Event &e, const ScratchLayout &L, bool split) {
   char buf[96];
@@ -817,10 +831,11 @@ static int event_band(dotpe_ctx *ctx, const Event &e, const ScratchLayout &L, bo
   return tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, split, L.n_etile);
 }
 
-// Times the event's first fused launch at candidate (tile width, band width)
-// pairs (the event's own inputs, prepared on `st`): 32- and 64-sample tiles
-// where the launch may take either, band widths doubling from one extrinsic
-// tile to all of them.  The results of these runs are overwritten by the real
+// Times the event's first fused launch at candidate (tile form, band width)
+// pairs (the event's own inputs, prepared on `st`): 32-sample tiles, and where
+// the launch may take them 64-sample tiles on one SM each and on CTA pairs
+// (unless the context keeps one SM per tile), band widths doubling from one
+// extrinsic tile to all of them.  The results of these runs are overwritten by the real
 // launch that follows.  Blocks the calling thread once per shape.
 static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st) {
   const bool split_main = prec_split(e.prec) && e.prec != DOTPE_PREC_MIXED;
@@ -839,31 +854,36 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
   // the 64-sample candidates timed as they run: with the <h|h> bound where the event has it
   if (R.mixed && tevs.back() == 64 && (rc = hh_bound_pass(ctx, e, R, W.P, st)) != DOTPE_OK) return rc;
   const int dflt = tc_band(ctx->l2_band_bytes, e.bank->Kpad / 64, e.bank->M, prec_split(e.prec), R.L.n_etile);
-  struct Cand { int tev, band; };
+  struct Cand { int tev; bool pair; int band; };
   std::vector<Cand> cand;
   for (int tv : tevs) {
     std::vector<int> bands;
     for (int c = 1; c < R.W.n_etile; c *= 2) bands.push_back(c);
     bands.push_back(R.W.n_etile);
     if (std::find(bands.begin(), bands.end(), dflt) == bands.end()) bands.push_back(dflt);
-    for (int c : bands) cand.push_back({tv, c});
+    std::vector<bool> forms{false};
+    if (tv == 64 && ctx->pair_tiles) forms.push_back(true);
+    for (bool pr : forms)
+      for (int c : bands) cand.push_back({tv, pr, c});
   }
   std::vector<cudaEvent_t> ev(cand.size() + 1);
   for (auto &x : ev) CUDA_OR_FAIL(cudaEventCreate(&x));
   // warm-up at the default width, then one timed launch per candidate
   W.band = dflt;
   T.tev = tevs.back();
+  T.pair = ctx->pair_tiles;
   int r = launch_tc(T, &W, 1, nullptr, nullptr, st);
   CUDA_OR_FAIL(cudaEventRecord(ev[0], st));
   for (size_t c = 0; c < cand.size() && r == 0; ++c) {
     W.band = cand[c].band;
     T.tev = cand[c].tev;
+    T.pair = cand[c].pair;
     r = launch_tc(T, &W, 1, nullptr, nullptr, st);
     CUDA_OR_FAIL(cudaEventRecord(ev[c + 1], st));
   }
   if (r != 0) return fail(DOTPE_E_DEVICE, "autotune launch failed: %s", cudaGetErrorString((cudaError_t)r));
   CUDA_OR_FAIL(cudaEventSynchronize(ev.back()));
-  Cand best{tevs.back(), dflt};
+  Cand best{tevs.back(), ctx->pair_tiles && tevs.back() == 64, dflt};
   float best_ms = 1e30f;
   for (size_t c = 0; c < cand.size(); ++c) {
     float ms = 0.f;
@@ -873,6 +893,7 @@ static int autotune_band(dotpe_ctx *ctx, Event &e, EventRun &R, cudaStream_t st)
   for (auto &x : ev) cudaEventDestroy(x);
   ctx->band_cache[key] = best.band;
   ctx->tev_cache[key] = best.tev;
+  ctx->pair_cache[key] = best.pair;
   R.W.band = best.band;
   // the tuning runs raised the running maximum and the counters: start the real launch afresh
   CUDA_OR_FAIL(cudaMemsetAsync(R.scr + R.L.ml_running, 0, 4, st));
@@ -1351,6 +1372,27 @@ static int preselect_locked(dotpe_ctx *ctx, const dotpe_presel_desc *d, float *l
     for (int m = 0; m < M; ++m)
       if (b.mode_m[m] % 2 != 0) P.slot[ns++] = m;
     for (; ns < MAXM; ++ns) P.slot[ns] = 0;
+    P.slot_mask = (1u << M) - 1u;
+    // quarter turns: e^{i m (phi + pi/2)} = i^m e^{i m phi}, so with one mode per
+    // class m mod 4 (slot order 0, 2, 1, 3; a mode bank's m are distinct in 1..4)
+    // four phases share one rotation; otherwise every phase is rotated on its own
+    if (!polb && d->n_phi % 4 == 0) {
+      static const int cls_slot[4] = {0, 2, 1, 3};  // class -> slot
+      int qs[MAXM] = {0, 0, 0, 0};
+      unsigned qm = 0;
+      bool ok = true;
+      for (int m = 0; m < M && ok; ++m) {
+        const int c = ((b.mode_m[m] % 4) + 4) % 4, sl = cls_slot[c];
+        if (qm & (1u << sl)) ok = false;
+        qm |= 1u << sl;
+        qs[sl] = m;
+      }
+      if (ok) {
+        P.quad = 1;
+        P.slot_mask = qm;
+        for (int q = 0; q < MAXM; ++q) P.slot[q] = qs[q];
+      }
+    }
   }
   P.n_itile = (int)((NI + PS_TR - 1) / PS_TR);
   P.n_ctile = D * NTP / (polb ? PS_TC / 2 : PS_TC);  // a polarisation-resolved tile holds 32 columns
@@ -1655,18 +1697,16 @@ int dotpe_create(const dotpe_config *cfg, dotpe_ctx **out) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
-  cudaError_t e = cudaMalloc(&ctx->dm_table, dm_table_elems() * sizeof(float4));
-  if (e != cudaSuccess) {
-    delete ctx;
-    return fail(DOTPE_E_NOMEM, "table allocation: %s", cudaGetErrorString(e));
-  }
-  launch_build_dm_table(ctx->dm_table, ctx->main_stream);
-  e = cudaStreamSynchronize(ctx->main_stream);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    cudaFree(ctx->dm_table);
-    delete ctx;
-    return fail(DOTPE_E_DEVICE, "table build: %s", cudaGetErrorString(e));
+  {
+    char msg[160];
+    const int trc = shared_dm_table(c.device, ctx->main_stream, &ctx->dm_table, msg, sizeof(msg));
+    if (trc != DOTPE_OK) {
+      for (auto s : ctx->streams) cudaStreamDestroy(s);
+      cudaStreamDestroy(ctx->main_stream);
+      cudaStreamDestroy(ctx->input_stream);
+      delete ctx;
+      return fail(trc, "%s", msg);
+    }
   }
   // admission worker: admits queued events as earlier ones complete
   ctx->worker = std::thread([ctx]() {
@@ -1705,7 +1745,6 @@ int dotpe_destroy(dotpe_ctx *ctx) {
     ctx->banks.clear();
   }
   cudaDeviceSynchronize();
-  cudaFree(ctx->dm_table);
   for (auto &m : ctx->graphs)
     for (auto &kv : m) cudaGraphExecDestroy(kv.second);
   for (auto s : ctx->streams) cudaStreamDestroy(s);

@@ -31,17 +31,25 @@
 // multiple of 64 columns, so a tile lies in one detector.
 //
 // Epilogue.  Per tile the 512 epilogue threads first tabulate [hh]^+ / 2 of the
-// tile's 64 rows on every phase in shared memory (one (row, 4 phases) each).
-// Then each thread takes its lane's column (one arrival time, Re or Im part)
-// and its warp's 16 rows: it reads the mode components from TMEM, swaps parts
-// with the partner lane (so both hold Z), forms Y_{mp} = K_{mp} Z_m and
-// evaluates half of the phases, the partner the other half.  With n_phi a
-// multiple of 4 the phases are taken in pairs (phi, phi + pi): with the modes
-// ordered even m first, e^{i m (phi + pi)} = +-e^{i m phi} gives both <d|h>
-// from one rotation.  The row's best (ln L^ML, o) over the warp's 16 times is
-// a warp reduction, merged across tiles with a 64-bit atomic maximum.  The
-// phase index rides in the low 6 mantissa bits of ln L^ML (a change of at
-// most 2^-17 of the value), so the inner maximum is one FMNMX.
+// tile's 64 rows on every phase in shared memory: for a mode bank 192 threads
+// (row, polarisation pair) form the row's phase-independent coefficients of
+// <h|h>_{pp'}(phi) once, then every thread evaluates one (row, 4 phases).
+// Then each lane takes its column (one arrival time; its TMEM lane holds the
+// Re or the Im part) and the warp's 16 rows: it reads the mode components from
+// TMEM and, for a mode bank, swaps with the partner lane the parts of two rows
+// so that it holds the whole Z of every other row (the partner the rest), forms
+// Y_{mp} = K_{mp} Z_m and evaluates all phases of its rows.  (A polarisation-
+// resolved bank keeps four lanes per column, each with a quarter of the
+// phases.)  With n_phi a multiple of 4 one rotation serves several phases: a
+// mode bank (distinct m in 1..4, one per class m mod 4) takes them in
+// quadruples (phi + k pi / 2, k = 0..3) from e^{i m (phi + pi / 2)} =
+// i^m e^{i m phi}; a polarisation-resolved bank in pairs (phi, phi + pi), with
+// the modes ordered even m first, from e^{i m (phi + pi)} = +-e^{i m phi}.
+// The row's best (ln L^ML, o) over
+// the warp's 16 times is a warp reduction, merged across tiles with a 64-bit
+// atomic maximum.  The phase index rides in the low 6 mantissa bits of
+// ln L^ML (a change of at most 2^-17 of the value), so the inner maximum is one
+// FMNMX.
 #pragma once
 #include "common.cuh"
 #include "kernels.h"
@@ -122,20 +130,53 @@ __device__ __forceinline__ void even_odd(const float4 &e01, const float4 &e23, c
   else if (NE == 3) { E = (r0 + r1) + r2; O = r3; }
   else { E = (r0 + r1) + (r2 + r3); O = 0.f; }
 }
+
+// Re sum_s Y_s e^{i m_s (phi + k pi / 2)}, k = 0..3, for one polarisation, the
+// slots holding the classes m mod 4 = 0, 2, 1, 3 (i^m = 1, -1, i, -i):
+// with R_c = Re(Y e^{i m phi}) and P_c = Y e^{i m phi} of class c,
+//   d0 = (R_0 + R_2) + (Re P_1 + Re P_3),   d1 = (R_0 - R_2) + (Im P_3 - Im P_1),
+//   d2 = (R_0 + R_2) - (Re P_1 + Re P_3),   d3 = (R_0 - R_2) - (Im P_3 - Im P_1).
+__device__ __forceinline__ void quarter_turns(const float4 &e01, const float4 &e23, const float *yr, const float *yi,
+                                              float (&d)[4]) {
+  const float r0 = e01.x * yr[0] - e01.y * yi[0];
+  const float r2 = e01.z * yr[1] - e01.w * yi[1];
+  const float p1r = e23.x * yr[2] - e23.y * yi[2], p1i = e23.x * yi[2] + e23.y * yr[2];
+  const float p3r = e23.z * yr[3] - e23.w * yi[3], p3i = e23.z * yi[3] + e23.w * yr[3];
+  const float a = r0 + r2, b = r0 - r2, c = p1r + p3r, e = p3i - p1i;
+  d[0] = a + c; d[1] = b + e; d[2] = a - c; d[3] = b - e;
+}
 }  // namespace
 
 // One row of one column: best tagged ln L^ML over the thread's phases.
-// PAIR (n_phi % 4 == 0): base phases b = part, part + STEP, ... < n_phi / 2 and
-// their partners b + n_phi / 2; otherwise phases o = part, part + STEP, ...
-// (STEP lanes share one (row, time): 2, or 4 for a polarisation-resolved bank).
-template <int NE, bool PAIR, int STEP>
+// PH 2 (quarter turns; n_phi % 4 == 0, slots by class m mod 4): base phases
+// b = part, part + STEP, ... < n_phi / 4 and b + k n_phi / 4; PH 1 (pairs;
+// n_phi % 4 == 0): base phases b < n_phi / 2 and their partners b + n_phi / 2;
+// PH 0: phases o = part, part + STEP, ...  (STEP lanes share one (row, time):
+// 1 for a mode bank, 4 for a polarisation-resolved bank.)
+template <int NE, int PH, int STEP>
 __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const float (&yi)[MAXM][2],
                                           const float4 *__restrict__ hs_row, const QTail &T, int n_phi, int part) {
   float best = -1.f;
   float yrp[MAXM], yip[MAXM], yrx[MAXM], yix[MAXM];
 #pragma unroll
   for (int s = 0; s < MAXM; ++s) { yrp[s] = yr[s][0]; yip[s] = yi[s][0]; yrx[s] = yr[s][1]; yix[s] = yi[s][1]; }
-  if (PAIR) {
+  if (PH == 2) {
+    const int qn = n_phi >> 2;
+#pragma unroll 2
+    for (int b = part; b < qn; b += STEP) {
+      const float4 e01 = T.phm[b * 2], e23 = T.phm[b * 2 + 1];
+      float dp[4], dx[4];
+      quarter_turns(e01, e23, yrp, yip, dp);
+      quarter_turns(e01, e23, yrx, yix, dx);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int o = b + k * qn;
+        const float4 h = hs_row[o];
+        const float q = fmaf(dp[k], fmaf(h.y, dx[k], h.x * dp[k]), h.z * dx[k] * dx[k]);
+        best = fmaxf(best, tag(q, 63 - o));
+      }
+    }
+  } else if (PH == 1) {
     const int half = n_phi >> 1;
 #pragma unroll 4
     for (int b = part; b < half; b += STEP) {
@@ -165,17 +206,16 @@ __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const floa
   return best;
 }
 
-// The warp's 16 rows of one tile for the thread's column t (Re or Im part):
-// mode components from TMEM (the buffer is released after the last read),
-// parts swapped with the partner lane, Y = K Z (the accumulator scale is in
-// the [hh]^+ table), the best tagged ln L^ML over the thread's phases, the
-// warp maximum over its 16 times, one atomic per row.
-// POL (polarisation-resolved bank): lanes 4c + 2p + part hold (Re, Im) of the
-// (mode, polarisation p) component of column c; the four lanes of a column
-// exchange their parts, take Y_{mp} = Z_{mp} (no factors) and a quarter of the phases each.
-template <int NE, bool PAIR, bool POL>
-__device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T, uint32_t tbase, int rb, int j_first,
-                                          int k, int t, int part, int lane, uint64_t *tempty) {
+// The warp's 16 rows of one tile of a mode bank for the lane's column t: mode
+// components from TMEM (the buffer is released after the last read); of each
+// two rows the Re lane (part 0) takes the first and the Im lane the second,
+// the two swapping the parts each lacks, so each lane holds the whole Z of its
+// rows; Y = K Z (the accumulator scale is in the [hh]^+ table), the best tagged
+// ln L^ML over every phase, the maximum over the warp's 16 times (the lanes of
+// one part), one atomic per row.
+template <int PH>
+__device__ __forceinline__ void tile_rows_modes(const PreselParams &P, const QTail &T, uint32_t tbase, int rb,
+                                                int j_first, int k, int t, int part, int lane, uint64_t *tempty) {
   const int M = P.n_modes;
   const bool tv = t < P.n_t;
 #pragma unroll 1
@@ -184,7 +224,81 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
     float z[MAXM][QJC];
 #pragma unroll
     for (int s = 0; s < MAXM; ++s) {
-      if (s < M) tmem_ld8(tbase + P.slot[s] * QTR + j0, z[s]);
+      if ((P.slot_mask >> s) & 1u) tmem_ld8(tbase + P.slot[s] * QTR + j0, z[s]);
+      else {
+#pragma unroll
+        for (int q = 0; q < QJC; ++q) z[s][q] = 0.f;
+      }
+    }
+    tmem_ld_wait();
+    if (jc == QJW / QJC - 1) {
+      // this warp's last read of the buffer: release it to the MMA warp
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+#pragma unroll
+    for (int r = 0; r < QJC / 2; ++r) {
+      const int j = j0 + 2 * r + part;  // this lane's row
+      const int64_t i = (int64_t)rb * QTR + j;
+      const bool rv = i < P.n_rows;
+      float zr[MAXM], zi[MAXM];
+#pragma unroll
+      for (int s = 0; s < MAXM; ++s) {
+        // the Re lane holds Re of rows 2r, 2r + 1, the Im lane their Im: each
+        // sends the part of the partner's row
+        const float send = part ? z[s][2 * r] : z[s][2 * r + 1];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+        zr[s] = part ? recv : z[s][2 * r];
+        zi[s] = part ? z[s][2 * r + 1] : recv;
+      }
+      float yr[MAXM][2], yi[MAXM][2];
+#pragma unroll
+      for (int s = 0; s < MAXM; ++s) {
+        float4 kv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rv && ((P.slot_mask >> s) & 1u))
+          kv = __ldg(reinterpret_cast<const float4 *>(P.pol + (i * M + P.slot[s]) * 2));
+        yr[s][0] = kv.x * zr[s] - kv.y * zi[s];
+        yi[s][0] = kv.x * zi[s] + kv.y * zr[s];
+        yr[s][1] = kv.z * zr[s] - kv.w * zi[s];
+        yi[s][1] = kv.z * zi[s] + kv.w * zr[s];
+      }
+      const float best = row_best<0, PH, 1>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi, 0);
+      // the maximum over the warp's 16 times of this lane's row (lanes of the
+      // same part): tagged values are distinct between the phases of one time, so
+      // the lowest lane holding the maximum has the lowest time
+      const bool ok = tv && rv;
+      float m = ok ? best : -1.f;
+#pragma unroll
+      for (int sh = 16; sh > 1; sh >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, sh));
+      const unsigned hit = __ballot_sync(0xffffffffu, ok && best == m) & (part ? 0xAAAAAAAAu : 0x55555555u);
+      if (lane < 2 && m >= -0.5f && hit) {
+        const int t_hit = t + ((__ffs(hit) - 1) >> 1);  // lane 0's (= lane 1's) time + the lane offset's time
+        const uint32_t o = 63u - (uint32_t)(__float_as_int(m) & 63);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(fmaxf(m, 0.f)) << 32) |
+                                       (unsigned long long)(0xffffffffu - (uint32_t)(t_hit * P.n_phi + (int)o));
+        atomicMax(P.keys + i * P.n_det + k, key);
+      }
+    }
+  }
+}
+
+// The warp's 16 rows of one tile of a polarisation-resolved bank: lanes
+// 4c + 2p + part hold (Re, Im) of the (mode, polarisation p) component of
+// column c; the four lanes of a column exchange their parts, take
+// Y_{mp} = Z_{mp} (no factors) and a quarter of the phases each, then the warp
+// maximum over its 8 times and one atomic per row.
+template <int NE, int PH>
+__device__ __forceinline__ void tile_rows_pol(const PreselParams &P, const QTail &T, uint32_t tbase, int rb,
+                                              int j_first, int k, int t, int part, int lane, uint64_t *tempty) {
+  const bool tv = t < P.n_t;
+#pragma unroll 1
+  for (int jc = 0; jc < QJW / QJC; ++jc) {
+    const int j0 = j_first + jc * QJC;
+    float z[MAXM][QJC];
+#pragma unroll
+    for (int s = 0; s < MAXM; ++s) {
+      if ((P.slot_mask >> s) & 1u) tmem_ld8(tbase + P.slot[s] * QTR + j0, z[s]);
       else {
 #pragma unroll
         for (int q = 0; q < QJC; ++q) z[s][q] = 0.f;
@@ -201,52 +315,30 @@ __device__ __forceinline__ void tile_rows(const PreselParams &P, const QTail &T,
     for (int jj = 0; jj < QJC; ++jj) {
       const int j = j0 + jj;
       const int64_t i = (int64_t)rb * QTR + j;
-      float zr[MAXM], zi[MAXM];
       float yr[MAXM][2], yi[MAXM][2];
-      if constexpr (POL) {
-        const int pp = (lane >> 1) & 1;
+      const int pp = (lane >> 1) & 1;
 #pragma unroll
-        for (int s = 0; s < MAXM; ++s) {
-          const float own = z[s][jj];
-          const float x1 = __shfl_xor_sync(0xffffffffu, own, 1);  // (p, other part)
-          const float x2 = __shfl_xor_sync(0xffffffffu, own, 2);  // (other p, this part)
-          const float x3 = __shfl_xor_sync(0xffffffffu, own, 3);  // (other p, other part)
-          const float r_own = part ? x1 : own, i_own = part ? own : x1;
-          const float r_oth = part ? x3 : x2, i_oth = part ? x2 : x3;
-          yr[s][0] = pp ? r_oth : r_own; yi[s][0] = pp ? i_oth : i_own;
-          yr[s][1] = pp ? r_own : r_oth; yi[s][1] = pp ? i_own : i_oth;
-        }
-        if (i >= P.n_rows) continue;  // warp-uniform
-      } else {
-#pragma unroll
-        for (int s = 0; s < MAXM; ++s) {
-          const float own = z[s][jj];
-          const float other = __shfl_xor_sync(0xffffffffu, own, 1);
-          zr[s] = part ? other : own;
-          zi[s] = part ? own : other;
-        }
-        if (i >= P.n_rows) continue;  // warp-uniform
-#pragma unroll
-        for (int s = 0; s < MAXM; ++s) {
-          float4 kv = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (s < M) kv = __ldg(reinterpret_cast<const float4 *>(P.pol + (i * M + P.slot[s]) * 2));
-          yr[s][0] = kv.x * zr[s] - kv.y * zi[s];
-          yi[s][0] = kv.x * zi[s] + kv.y * zr[s];
-          yr[s][1] = kv.z * zr[s] - kv.w * zi[s];
-          yi[s][1] = kv.z * zi[s] + kv.w * zr[s];
-        }
+      for (int s = 0; s < MAXM; ++s) {
+        const float own = z[s][jj];
+        const float x1 = __shfl_xor_sync(0xffffffffu, own, 1);  // (p, other part)
+        const float x2 = __shfl_xor_sync(0xffffffffu, own, 2);  // (other p, this part)
+        const float x3 = __shfl_xor_sync(0xffffffffu, own, 3);  // (other p, other part)
+        const float r_own = part ? x1 : own, i_own = part ? own : x1;
+        const float r_oth = part ? x3 : x2, i_oth = part ? x2 : x3;
+        yr[s][0] = pp ? r_oth : r_own; yi[s][0] = pp ? i_oth : i_own;
+        yr[s][1] = pp ? r_own : r_oth; yi[s][1] = pp ? i_own : i_oth;
       }
-      const float best = row_best<NE, PAIR, POL ? 4 : 2>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi,
-                                                         POL ? (lane & 3) : part);
-      // the warp's maximum over its 16 (POL: 8) times: tagged values are distinct
-      // between the lanes of one time, so the lowest lane holding the maximum has
-      // the lowest time
+      if (i >= P.n_rows) continue;  // warp-uniform
+      const float best = row_best<NE, PH, 4>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi, lane & 3);
+      // the warp's maximum over its 8 times: tagged values are distinct between
+      // the lanes of one time, so the lowest lane holding the maximum has the
+      // lowest time
       float m = tv ? best : -1.f;
 #pragma unroll
       for (int sh = 16; sh > 0; sh >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, sh));
       const unsigned hit = __ballot_sync(0xffffffffu, tv && best == m);
       if (lane == 0 && m >= -0.5f && hit) {
-        const int t_hit = t + ((__ffs(hit) - 1) >> (POL ? 2 : 1));  // lane 0's time + the lane offset's time
+        const int t_hit = t + ((__ffs(hit) - 1) >> 2);  // lane 0's time + the lane offset's time
         const uint32_t o = 63u - (uint32_t)(__float_as_int(m) & 63);
         const unsigned long long key = ((unsigned long long)__float_as_uint(fmaxf(m, 0.f)) << 32) |
                                        (unsigned long long)(0xffffffffu - (uint32_t)(t_hit * P.n_phi + (int)o));
@@ -295,7 +387,7 @@ __global__ void __launch_bounds__(QNT, 1)
     const int o = q >> 2, s = q & 3;
     float c = 1.f, sn = 0.f, c2 = 1.f, s2 = 0.f;
     if (o < P.n_phi) {
-      const int mm = s < M ? P.mode_m[P.slot[s]] : 0;
+      const int mm = ((P.slot_mask >> s) & 1u) ? P.mode_m[P.slot[s]] : 0;
       sincospif(2.0f * (float)((mm * o) % P.n_phi) / (float)P.n_phi, &sn, &c);
       sincospif(2.0f * (float)((s * o) % P.n_phi) / (float)P.n_phi, &s2, &c2);
     }
@@ -445,73 +537,97 @@ __global__ void __launch_bounds__(QNT, 1)
             }
             T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, 0.f);
           }
-        } else if (!POL && i < P.n_rows && o0 < P.n_phi) {
-          float Kr[MAXM][2], Ki[MAXM][2], rec[REC];
+        }
+        if constexpr (!POL) {
+          // <h|h>_{pp'}(phi) = Dc_r + sum_delta Re(Q_r[delta] e^{i delta phi}), r = (++, +x, xx):
+          // (a) one thread per (row, r) forms the row's coefficients (Dc_r, Re Q_r, Im Q_r)
+          // into the row's own part of T.hs (rows of one warp 8 words apart, so that
+          // the reads of (b) meet distinct banks)
+          if (etid < QTR * 3) {
+            const int ja = etid / 3, r = etid - 3 * ja;
+            const int64_t ia = (int64_t)rb * QTR + ja;
+            if (ia < P.n_rows) {
+              // K_{mp} and K_{mp'} of the thread's polarisation pair (p, p')
+              const bool p1 = r == 2, pp1 = r != 0;
+              float Kpr[MAXM], Kpi[MAXM], Kqr[MAXM], Kqi[MAXM], rec[REC];
 #pragma unroll
-          for (int m = 0; m < MAXM; ++m) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (m < M) v = __ldg(reinterpret_cast<const float4 *>(P.pol + (i * M + m) * 2));
-            Kr[m][0] = v.x; Ki[m][0] = v.y; Kr[m][1] = v.z; Ki[m][1] = v.w;
-          }
-          const float4 *src = reinterpret_cast<const float4 *>(P.mx + (i * P.n_det + k) * REC);
-#pragma unroll
-          for (int q = 0; q < REC / 4; ++q) {
-            const float4 v = __ldg(src + q);
-            rec[4 * q] = v.x; rec[4 * q + 1] = v.y; rec[4 * q + 2] = v.z; rec[4 * q + 3] = v.w;
-          }
-          // <h|h>_{pp'}(phi) = Dc_r + sum_delta Re(Q_r[delta] e^{i delta phi}), r = (++, +x, xx)
-          float Dc[3], Qr[3][3], Qi[3][3];
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const int p = r == 2 ? 1 : 0, pp = r == 0 ? 0 : 1;
-            float d = 0.f;
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) d += rec[m] * (Kr[m][p] * Kr[m][pp] + Ki[m][p] * Ki[m][pp]);
-            Dc[r] = d;
-#pragma unroll
-            for (int dl = 0; dl < 3; ++dl) { Qr[r][dl] = 0.f; Qi[r][dl] = 0.f; }
-            int pr = 0;
-#pragma unroll
-            for (int a = 1; a < MAXM; ++a)
-#pragma unroll
-              for (int c = 0; c < a; ++c, ++pr) {
-                if (a >= M) continue;
-                // X = K_ap K_cp'^* + K_ap' K_cp^*, times <h_a|h_c>
-                const float xr = Kr[a][p] * Kr[c][pp] + Ki[a][p] * Ki[c][pp] + Kr[a][pp] * Kr[c][p] + Ki[a][pp] * Ki[c][p];
-                const float xi = Ki[a][p] * Kr[c][pp] - Kr[a][p] * Ki[c][pp] + Ki[a][pp] * Kr[c][p] - Kr[a][pp] * Ki[c][p];
-                const float hr = rec[4 + 2 * pr], hi = rec[5 + 2 * pr];
-                const int dl = P.pdelta[pr] - 1;
-                const float qr = hr * xr - hi * xi, qi = hr * xi + hi * xr;
-#pragma unroll
-                for (int z = 0; z < 3; ++z)
-                  if (z == dl) { Qr[r][z] += qr; Qi[r][z] += qi; }
+              for (int m = 0; m < MAXM; ++m) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (m < M) v = __ldg(reinterpret_cast<const float4 *>(P.pol + (ia * M + m) * 2));
+                Kpr[m] = p1 ? v.z : v.x; Kpi[m] = p1 ? v.w : v.y;
+                Kqr[m] = pp1 ? v.z : v.x; Kqi[m] = pp1 ? v.w : v.y;
               }
+              const float4 *src = reinterpret_cast<const float4 *>(P.mx + (ia * P.n_det + k) * REC);
+#pragma unroll
+              for (int q = 0; q < REC / 4; ++q) {
+                const float4 v = __ldg(src + q);
+                rec[4 * q] = v.x; rec[4 * q + 1] = v.y; rec[4 * q + 2] = v.z; rec[4 * q + 3] = v.w;
+              }
+              float Dc = 0.f, Qr[3] = {0.f, 0.f, 0.f}, Qi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) Dc += rec[m] * (Kpr[m] * Kqr[m] + Kpi[m] * Kqi[m]);
+              int pr = 0;
+#pragma unroll
+              for (int a = 1; a < MAXM; ++a)
+#pragma unroll
+                for (int c = 0; c < a; ++c, ++pr) {
+                  if (a >= M) continue;
+                  // X = K_ap K_cp'^* + K_ap' K_cp^*, times <h_a|h_c>
+                  const float xr = Kpr[a] * Kqr[c] + Kpi[a] * Kqi[c] + Kqr[a] * Kpr[c] + Kqi[a] * Kpi[c];
+                  const float xi = Kpi[a] * Kqr[c] - Kpr[a] * Kqi[c] + Kqi[a] * Kpr[c] - Kqr[a] * Kpi[c];
+                  const float hr = rec[4 + 2 * pr], hi = rec[5 + 2 * pr];
+                  const int dl = P.pdelta[pr] - 1;
+                  const float qr = hr * xr - hi * xi, qi = hr * xi + hi * xr;
+#pragma unroll
+                  for (int z = 0; z < 3; ++z)
+                    if (z == dl) { Qr[z] += qr; Qi[z] += qi; }
+                }
+              float4 *cf = &T.hs[ja * PS_MAXPHI + (ja & 3) * 2 + r * 2];
+              cf[0] = make_float4(Dc, Qr[0], Qr[1], Qr[2]);
+              cf[1] = make_float4(Qi[0], Qi[1], Qi[2], 0.f);
+            }
           }
+          named_bar_sync(1, QEPT);
+          // (b) every thread: its row's coefficients, then [hh]^+ / 2 on its 4 phases
+          const bool act = i < P.n_rows && o0 < P.n_phi;
+          float Dc[3] = {0.f, 0.f, 0.f}, Qr[3][3] = {}, Qi[3][3] = {};
+          if (act) {
+            const float4 *cf = &T.hs[j * PS_MAXPHI + (j & 3) * 2];
 #pragma unroll
-          for (int oo = 0; oo < 4; ++oo) {
-            const int o = o0 + oo;
-            float hh[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) hh[r] = Dc[r];
-#pragma unroll
-            for (int dl = 0; dl < 3; ++dl) {
-              const float2 e = T.phd[o * 3 + dl];
-#pragma unroll
-              for (int r = 0; r < 3; ++r) hh[r] += Qr[r][dl] * e.x - Qi[r][dl] * e.y;
+            for (int r = 0; r < 3; ++r) {
+              const float4 u0 = cf[2 * r], u1 = cf[2 * r + 1];
+              Dc[r] = u0.x; Qr[r][0] = u0.y; Qr[r][1] = u0.z; Qr[r][2] = u0.w;
+              Qi[r][0] = u1.x; Qi[r][1] = u1.y; Qi[r][2] = u1.z;
             }
-            const float A = hh[0], B = hh[1], C = hh[2];
-            const float det = A * C - B * B;
-            float a = 0.f, bb = 0.f, c = 0.f;
-            if (det > P.rank_tol * A * C) {
-              const float inv = 0.5f / det;
-              a = C * inv; bb = -B * inv; c = A * inv;
-            } else if (A > 0.f || C > 0.f) {
-              const float sm = A + C;
-              const float inv = 0.5f / (sm * sm);
-              a = A * inv; bb = B * inv; c = C * inv;
+          }
+          named_bar_sync(1, QEPT);  // every row's coefficients read before T.hs is overwritten
+          if (act) {
+#pragma unroll
+            for (int oo = 0; oo < 4; ++oo) {
+              const int o = o0 + oo;
+              float hh[3];
+#pragma unroll
+              for (int r = 0; r < 3; ++r) hh[r] = Dc[r];
+#pragma unroll
+              for (int dl = 0; dl < 3; ++dl) {
+                const float2 e = T.phd[o * 3 + dl];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) hh[r] += Qr[r][dl] * e.x - Qi[r][dl] * e.y;
+              }
+              const float A = hh[0], B = hh[1], C = hh[2];
+              const float det = A * C - B * B;
+              float a = 0.f, bb = 0.f, c = 0.f;
+              if (det > P.rank_tol * A * C) {
+                const float inv = 0.5f / det;
+                a = C * inv; bb = -B * inv; c = A * inv;
+              } else if (A > 0.f || C > 0.f) {
+                const float sm = A + C;
+                const float inv = 0.5f / (sm * sm);
+                a = A * inv; bb = B * inv; c = C * inv;
+              }
+              // the accumulators' scale enters ln L^ML squared: fold it into the table
+              T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, 0.f);
             }
-            // the accumulators' scale enters ln L^ML squared: fold it into the table
-            T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, 0.f);
           }
         }
       }
@@ -522,13 +638,20 @@ __global__ void __launch_bounds__(QNT, 1)
       const int t = c0 - k * P.n_tpad + (POL ? (L >> 2) : (L >> 1));
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + b * Q_BUF_COLS;
       const int j0 = sub * QJW;
-      switch ((pair ? 8 : 0) + (pair ? P.n_even : 2)) {
-        case 8: tile_rows<0, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 9: tile_rows<1, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 10: tile_rows<2, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 11: tile_rows<3, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        case 12: tile_rows<4, true, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
-        default: tile_rows<2, false, POL>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+      if constexpr (POL) {
+        switch ((pair ? 8 : 0) + (pair ? P.n_even : 2)) {
+          case 8: tile_rows_pol<0, 1>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+          case 9: tile_rows_pol<1, 1>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+          case 10: tile_rows_pol<2, 1>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+          case 11: tile_rows_pol<3, 1>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+          case 12: tile_rows_pol<4, 1>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+          default: tile_rows_pol<2, 0>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]); break;
+        }
+      } else {
+        // a mode bank's azimuthal numbers are distinct in 1..4, one per class m mod 4:
+        // quarter turns whenever n_phi % 4 == 0, else every phase on its own
+        if (P.quad) tile_rows_modes<2>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]);
+        else tile_rows_modes<0>(P, T, tbase, rb, j0, k, t, part, lane, &T.tempty[b]);
       }
     }
   }

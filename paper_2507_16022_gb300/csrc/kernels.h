@@ -65,6 +65,10 @@ void launch_gather_rows(int64_t outer, int64_t src_rows, int64_t n, int64_t row_
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf /*[2][n]*/,
                              __half *hf /*[2][n]*/, float *scale_out, cudaStream_t st);
 void launch_build_dm_table(float4 *tab, cudaStream_t st);
+// The device's distance-marginal table (static device memory), built on `st`
+// on first use in the current CUDA context of `device` (which must be current);
+// later calls return the same address.  DOTPE_OK, or an error code with `msg`.
+int shared_dm_table(int device, cudaStream_t st, float4 **tab, char *msg, size_t msg_len);
 void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
                            cudaStream_t st);
 size_t dm_table_elems();
@@ -257,8 +261,11 @@ struct PreselParams {
   int n_det, n_t, n_tpad, n_phi, n_modes;
   int mode_m[MAXM];
   int pdelta[NPAIR];     // m_a - m_b of mode pair p (a > b), 1..3
-  int slot[MAXM];        // epilogue mode slots: bank mode index, even m first
+  int slot[MAXM];        // epilogue mode slots: bank mode index (even m first, or by m mod 4 when quad)
   int n_even;            // modes with even m
+  int quad;              // mode bank, n_phi % 4 == 0, one mode per class m mod 4: slot s holds class
+                         // (0, 2, 1, 3)[s] and the phases are taken four at a time (phi + k pi / 2)
+  unsigned slot_mask;    // slots that hold a mode (the others are empty)
   int n_itile, n_ctile;  // 64-row tiles, 64-column tiles
   int kb;                // k-blocks of 64 per mode
   int a_plane_rows, a_mode_rows, b_plane_rows;

@@ -841,6 +841,46 @@ void launch_build_dm_table(float4 *tab, cudaStream_t st) {
   build_dm_table_kernel<<<nblk((int64_t)DM_NY * DM_NS, 64), 64, 0, st>>>(tab);
 }
 
+// The distance-marginal table is a constant of the method, the same for every
+// context: it lives in this static device array (3.2 MB, held by every GPU
+// that loads the library until the process exits) and is built once per CUDA
+// context of a device, by the first dotpe context created there, instead of
+// once per dotpe context.
+static __device__ __align__(256) float4 g_dm_table[DM_NY * DM_NS];
+
+static unsigned long long current_ctx_id();
+
+int shared_dm_table(int device, cudaStream_t st, float4 **tab, char *msg, size_t msg_len) {
+  static std::mutex mu;
+  static float4 *addr[64] = {nullptr};
+  static unsigned long long addr_ctx[64] = {0};
+  if (device < 0 || device >= 64) {
+    snprintf(msg, msg_len, "device %d out of range", device);
+    return DOTPE_E_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  // the caller has made `device` current
+  const unsigned long long cid = current_ctx_id();
+  if (!addr[device] || cid == 0 || cid != addr_ctx[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dm_table);
+    if (e == cudaSuccess && p == nullptr) e = cudaErrorInvalidSymbol;
+    if (e == cudaSuccess) {
+      build_dm_table_kernel<<<nblk((int64_t)DM_NY * DM_NS, 64), 64, 0, st>>>((float4 *)p);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      snprintf(msg, msg_len, "table build: %s", cudaGetErrorString(e));
+      return DOTPE_E_DEVICE;
+    }
+    addr[device] = (float4 *)p;
+    addr_ctx[device] = cid;
+  }
+  *tab = addr[device];
+  return DOTPE_OK;
+}
+
 void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
                            cudaStream_t st) {
   dist_marg_eval_kernel<<<nblk(n, 256), 256, 0, st>>>(n, dh, hh, u_min, tab, out);

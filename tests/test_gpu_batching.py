@@ -152,7 +152,10 @@ def test_batch_admission_errors(mix):
 
 
 def test_autotuned_band_gives_the_same_result(mix):
-    """The autotuner changes only the order of the tiles (the L2 band width)."""
+    """The autotuner changes only the order of the tiles (the L2 band width),
+    the screen's tile width (32 or 64 samples) and whether 64-sample tiles run
+    on CTA pairs or one SM each: the refined tiles, hence the events, stay the
+    same."""
     dp, wl, specs = mix
     ref_ctx = dp.dotpe_create(0)
     ctx = dp.dotpe_create(0, flags=dp.DOTPE_CONFIG_AUTOTUNE)
