@@ -152,28 +152,47 @@ __device__ __forceinline__ void quarter_turns(const float4 &e01, const float4 &e
 // b = part, part + STEP, ... < n_phi / 4 and b + k n_phi / 4; PH 1 (pairs;
 // n_phi % 4 == 0): base phases b < n_phi / 2 and their partners b + n_phi / 2;
 // PH 0: phases o = part, part + STEP, ...  (STEP lanes share one (row, time):
-// 1 for a mode bank, 4 for a polarisation-resolved bank.)
+// 1 for a mode bank, 4 for a polarisation-resolved bank; PH 2 takes every
+// phase.)  With PH 2 and n_phi / 4 even the base phases go in pairs, in the
+// order (c + sw, c + 1 - sw): the lanes of a warp that read two rows at once
+// (512 bytes apart in the table) with sw = 0 and 1 then read different
+// phases, in different shared-memory banks.
 template <int NE, int PH, int STEP>
 __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const float (&yi)[MAXM][2],
-                                          const float4 *__restrict__ hs_row, const QTail &T, int n_phi, int part) {
+                                          const float4 *__restrict__ hs_row, const QTail &T, int n_phi, int part,
+                                          int sw = 0) {
   float best = -1.f;
   float yrp[MAXM], yip[MAXM], yrx[MAXM], yix[MAXM];
 #pragma unroll
   for (int s = 0; s < MAXM; ++s) { yrp[s] = yr[s][0]; yip[s] = yi[s][0]; yrx[s] = yr[s][1]; yix[s] = yi[s][1]; }
   if (PH == 2) {
     const int qn = n_phi >> 2;
-#pragma unroll 2
-    for (int b = part; b < qn; b += STEP) {
-      const float4 e01 = T.phm[b * 2], e23 = T.phm[b * 2 + 1];
+    // one base phase b: <d|h> of both polarisations at b + k qn, k = 0..3, from one
+    // rotation; ph = the phase table at b, hq = the row's table entry at b, code0 = 63 - b
+    auto quad_step = [&](const float4 *ph, const float4 *hq, int code0) {
+      const float4 e01 = ph[0], e23 = ph[1];
       float dp[4], dx[4];
       quarter_turns(e01, e23, yrp, yip, dp);
       quarter_turns(e01, e23, yrx, yix, dx);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const int o = b + k * qn;
-        const float4 h = hs_row[o];
+        const float4 h = hq[k * qn];
         const float q = fmaf(dp[k], fmaf(h.y, dx[k], h.x * dp[k]), h.z * dx[k] * dx[k]);
-        best = fmaxf(best, tag(q, 63 - o));
+        best = fmaxf(best, tag(q, code0 - k * qn));
+      }
+    };
+    if (qn & 1) {
+#pragma unroll 2
+      for (int b = 0; b < qn; ++b) quad_step(T.phm + 2 * b, hs_row + b, 63 - b);
+    } else {
+      // base phases in pairs (c + sw, c + 1 - sw): the per-lane offset sw is folded
+      // into the pointers, so the swizzle costs nothing inside the loop
+      const float4 *pA = T.phm + 2 * sw, *pB = T.phm + 2 * (1 - sw);
+      const float4 *hA = hs_row + sw, *hB = hs_row + (1 - sw);
+#pragma unroll 1
+      for (int c = 0; c < qn; c += 2) {
+        quad_step(pA + 2 * c, hA + c, 63 - sw - c);
+        quad_step(pB + 2 * c, hB + c, 62 + sw - c);
       }
     }
   } else if (PH == 1) {
@@ -216,8 +235,8 @@ __device__ __forceinline__ float row_best(const float (&yr)[MAXM][2], const floa
 template <int PH>
 __device__ __forceinline__ void tile_rows_modes(const PreselParams &P, const QTail &T, uint32_t tbase, int rb,
                                                 int j_first, int k, int t, int part, int lane, uint64_t *tempty) {
-  const int M = P.n_modes;
   const bool tv = t < P.n_t;
+  const int sw = ((P.n_phi >> 2) & 1) ? 0 : part;  // phase order of the odd rows (see row_best)
 #pragma unroll 1
   for (int jc = 0; jc < QJW / QJC; ++jc) {
     const int j0 = j_first + jc * QJC;
@@ -252,18 +271,19 @@ __device__ __forceinline__ void tile_rows_modes(const PreselParams &P, const QTa
         zr[s] = part ? recv : z[s][2 * r];
         zi[s] = part ? z[s][2 * r + 1] : recv;
       }
+      // the row's polarisation factors from the fourth words of its table
+      // entries 4 s + c + (j & 1) (zero for empty slots)
+      const float *kw = reinterpret_cast<const float *>(&T.hs[j * PS_MAXPHI + part]) + 3;
       float yr[MAXM][2], yi[MAXM][2];
 #pragma unroll
       for (int s = 0; s < MAXM; ++s) {
-        float4 kv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (rv && ((P.slot_mask >> s) & 1u))
-          kv = __ldg(reinterpret_cast<const float4 *>(P.pol + (i * M + P.slot[s]) * 2));
+        const float4 kv = make_float4(kw[16 * s], kw[16 * s + 4], kw[16 * s + 8], kw[16 * s + 12]);
         yr[s][0] = kv.x * zr[s] - kv.y * zi[s];
         yi[s][0] = kv.x * zi[s] + kv.y * zr[s];
         yr[s][1] = kv.z * zr[s] - kv.w * zi[s];
         yi[s][1] = kv.z * zi[s] + kv.w * zr[s];
       }
-      const float best = row_best<0, PH, 1>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi, 0);
+      const float best = row_best<0, PH, 1>(yr, yi, &T.hs[j * PS_MAXPHI], T, P.n_phi, 0, sw);
       // the maximum over the warp's 16 times of this lane's row (lanes of the
       // same part): tagged values are distinct between the phases of one time, so
       // the lowest lane holding the maximum has the lowest time
@@ -588,8 +608,22 @@ __global__ void __launch_bounds__(QNT, 1)
             }
           }
           named_bar_sync(1, QEPT);
-          // (b) every thread: its row's coefficients, then [hh]^+ / 2 on its 4 phases
-          const bool act = i < P.n_rows && o0 < P.n_phi;
+          // (b) every thread: its row's coefficients, then [hh]^+ / 2 on its 4 phases.
+          // The entries' fourth words carry the row's polarisation factors for the
+          // row pass: K_{s, c} (slot s, component c of (Re K+, Im K+, Re Kx, Im Kx))
+          // in entry 4 s + c + (j & 1), so that the two rows a warp reads at once
+          // (j even and odd) sit in different banks.
+          const bool rowv = i < P.n_rows;
+          const bool act = rowv && o0 < P.n_phi;
+          float kw[4] = {0.f, 0.f, 0.f, 0.f};
+          if (rowv) {
+#pragma unroll
+            for (int oo = 0; oo < 4; ++oo) {
+              const int q = o0 + oo - (j & 1);
+              if (q >= 0 && q < 4 * MAXM && ((P.slot_mask >> (q >> 2)) & 1u))
+                kw[oo] = __ldg(reinterpret_cast<const float *>(P.pol) + (i * M + P.slot[q >> 2]) * 4 + (q & 3));
+            }
+          }
           float Dc[3] = {0.f, 0.f, 0.f}, Qr[3][3] = {}, Qi[3][3] = {};
           if (act) {
             const float4 *cf = &T.hs[j * PS_MAXPHI + (j & 3) * 2];
@@ -601,10 +635,14 @@ __global__ void __launch_bounds__(QNT, 1)
             }
           }
           named_bar_sync(1, QEPT);  // every row's coefficients read before T.hs is overwritten
-          if (act) {
+          if (rowv) {
 #pragma unroll
             for (int oo = 0; oo < 4; ++oo) {
               const int o = o0 + oo;
+              if (!act) {
+                T.hs[j * PS_MAXPHI + o] = make_float4(0.f, 0.f, 0.f, kw[oo]);
+                continue;
+              }
               float hh[3];
 #pragma unroll
               for (int r = 0; r < 3; ++r) hh[r] = Dc[r];
@@ -626,7 +664,7 @@ __global__ void __launch_bounds__(QNT, 1)
                 a = A * inv; bb = B * inv; c = C * inv;
               }
               // the accumulators' scale enters ln L^ML squared: fold it into the table
-              T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, 0.f);
+              T.hs[j * PS_MAXPHI + o] = make_float4(a * zs2, 2.f * bb * zs2, c * zs2, kw[oo]);
             }
           }
         }

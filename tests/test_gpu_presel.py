@@ -300,12 +300,15 @@ def test_long_bin_axis(dpx, precision):
     assert np.all(d <= split_tol(ref["ml"]))
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1, 1, 1), (3, 2, 2, 3, 3)])
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1, 1), (3, 2, 2, 3, 3), (4, 3, 3, 2, 4), (5, 2, 4, 5, 12),
+                                   (70, 2, 4, 3, 24)])
 @pytest.mark.parametrize("bank", ["modes", "precessing"])
 def test_degenerate_preselection(dpx, shape, bank):
     """Tiny shapes: one row, one detector, one mode, one time and one phase;
     three rows, two detectors and modes, three times and three phases (no
-    phase pairing), for a mode bank (fp16x3) and a polarisation-resolved bank
+    phase pairing); 4 and 12 phases (an odd number of quarter-turn base
+    phases) and 24 phases over 70 rows (base phases in pairs, a ragged second
+    row tile), for a mode bank (fp16x3) and a polarisation-resolved bank
     (fp16x3 and FP32), against the oracle."""
     dp, ctx = dpx
     import oracle
