@@ -32,7 +32,7 @@ constexpr int PP_BCH = 64;   // bins per shared-memory chunk
 
 template <bool RB>
 __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a) {
-  __shared__ float2 hs[PP_RPB][MAXM][2][PP_BCH];
+  __shared__ __align__(16) float2 hs[PP_RPB][MAXM][2][PP_BCH];
   __shared__ float4 tab[PP_RPB][PS_MAXPHI];    // (a, 2b, c): ln L^ML = a dp^2 + 2b dp dx + c dx^2
   __shared__ float2 ph[PS_MAXPHI][MAXM];       // e^{i m phi_o}
   const int tid = threadIdx.x;
@@ -104,18 +104,27 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
       __syncthreads();
       if (tv) {
         const int nb = min(PP_BCH, B - b0);
-        for (int bb = 0; bb < nb; ++bb) {
-          float2 gv[MAXM][2];
-          if constexpr (RB) {
+        // two bins per step: the rows' components of both in one 16-byte shared
+        // load (bins past the chunk's end hold zeros), the operand's of both
+        // loaded before either is used
+        for (int bb = 0; bb < nb; bb += 2) {
+          const bool two = bb + 1 < nb;
+          float2 gv[2][MAXM][2];
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m)
+          for (int u = 0; u < 2; ++u) {
+            const bool in = u == 0 || two;
+            if constexpr (RB) {
 #pragma unroll
-              for (int p = 0; p < 2; ++p)
-                gv[m][p] = m < M ? __ldg(g + (2 * m + p) * gstride + (b0 + bb) * TP) : make_float2(0.f, 0.f);
-          } else {
-            const float2 g0 = __ldg(g + (b0 + bb) * TP);
+              for (int m = 0; m < MAXM; ++m)
 #pragma unroll
-            for (int m = 0; m < MAXM; ++m) gv[m][0] = gv[m][1] = g0;
+                for (int p = 0; p < 2; ++p)
+                  gv[u][m][p] = (m < M && in) ? __ldg(g + (2 * m + p) * gstride + (b0 + bb + u) * TP)
+                                              : make_float2(0.f, 0.f);
+            } else {
+              const float2 g0 = in ? __ldg(g + (b0 + bb + u) * TP) : make_float2(0.f, 0.f);
+#pragma unroll
+              for (int m = 0; m < MAXM; ++m) gv[u][m][0] = gv[u][m][1] = g0;
+            }
           }
 #pragma unroll
           for (int r = 0; r < PP_RPB; ++r)
@@ -123,9 +132,12 @@ __global__ void __launch_bounds__(PP_NT) presel_pol_kernel(const PreselPolArgs a
             for (int m = 0; m < MAXM; ++m)
 #pragma unroll
               for (int p = 0; p < 2; ++p) {
-                const float2 h = hs[r][m][p][bb], gq = gv[m][p];
-                zr[r][m][p] = fmaf(gq.x, h.x, fmaf(-gq.y, h.y, zr[r][m][p]));
-                zi[r][m][p] = fmaf(gq.x, h.y, fmaf(gq.y, h.x, zi[r][m][p]));
+                const float4 h2 = *reinterpret_cast<const float4 *>(&hs[r][m][p][bb]);
+                const float2 g0 = gv[0][m][p], g1 = gv[1][m][p];
+                zr[r][m][p] = fmaf(g0.x, h2.x, fmaf(-g0.y, h2.y, zr[r][m][p]));
+                zi[r][m][p] = fmaf(g0.x, h2.y, fmaf(g0.y, h2.x, zi[r][m][p]));
+                zr[r][m][p] = fmaf(g1.x, h2.z, fmaf(-g1.y, h2.w, zr[r][m][p]));
+                zi[r][m][p] = fmaf(g1.x, h2.w, fmaf(g1.y, h2.z, zi[r][m][p]));
               }
         }
       }
