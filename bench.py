@@ -80,7 +80,7 @@ SCREEN_TRAFFIC = {"bytes": 0.504e9 + 3.688e9, "n_int": 65536, "n_ext": 4096,
 # of a polarisation-resolved bank (presel_pol_kernel<true>), from one ncu capture:
 # the build it was taken on, its shape and rows.  None = no capture of the current
 # kernel (the figure goes stale with any change to the kernel or its grid).
-PRESEL_TRAFFIC = {"bytes": 1.644e9 + 0.017e9, "rows": 65536, "D": 3, "N_t": 128, "B": 378,
+PRESEL_TRAFFIC = {"bytes": 1.643e9 + 0.017e9, "rows": 65536, "D": 3, "N_t": 128, "B": 378,
                   "source": "profiles/presel_pol_rb_fp32_65536x3x128x32.md"}
 
 
