@@ -95,7 +95,9 @@ enum {
 typedef struct dotpe_ctx dotpe_ctx;
 
 /* context flags */
-#define DOTPE_CONFIG_AUTOTUNE 0x1  /* time candidate L2 tile bands on the first event of each shape */
+/* time candidate tile forms (32-sample tiles; 64-sample tiles on one SM or on
+ * CTA pairs) and L2 bands on the first event of each shape, keep the fastest */
+#define DOTPE_CONFIG_AUTOTUNE 0x1
 #define DOTPE_CONFIG_NO_GRAPHS 0x2 /* launch batches directly instead of as captured CUDA graphs */
 /* Screening and GEMM-only launches of mode banks use 128 x 32-sample tiles
  * (two TMEM accumulator sets) instead of the default 128 x 64-sample tiles (one
@@ -103,7 +105,8 @@ typedef struct dotpe_ctx dotpe_ctx;
  * the same either way; with DOTPE_CONFIG_AUTOTUNE the tuner times both. */
 #define DOTPE_CONFIG_NARROW_TILES 0x4
 /* 64-sample tiles on one SM each instead of CTA pairs (two SMs sharing each
- * MMA, cta_group::2, each loading half of the extrinsic operand tile) */
+ * MMA, cta_group::2, each loading half of the extrinsic operand tile); the
+ * autotuner then times no CTA pairs */
 #define DOTPE_CONFIG_SINGLE_CTA_TILES 0x8
 
 typedef struct dotpe_config {
