@@ -64,14 +64,12 @@ void launch_gather_rows(int64_t outer, int64_t src_rows, int64_t n, int64_t row_
                         const int64_t *rows, void *dst, cudaStream_t st);
 void launch_master_to_planes(int64_t n, const float *master, const float *amax, __nv_bfloat16 *bf /*[2][n]*/,
                              __half *hf /*[2][n]*/, float *scale_out, cudaStream_t st);
-void launch_build_dm_table(float4 *tab, cudaStream_t st);
 // The device's distance-marginal table (static device memory), built on `st`
 // on first use in the current CUDA context of `device` (which must be current);
 // later calls return the same address.  DOTPE_OK, or an error code with `msg`.
 int shared_dm_table(int device, cudaStream_t st, float4 **tab, char *msg, size_t msg_len);
 void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab, float *out,
                            cudaStream_t st);
-size_t dm_table_elems();
 constexpr int64_t DM_NOALLOC_MAX = 1 << 20;  // evaluations per allocation-free call
 int dist_marg_eval_noalloc(int device, int64_t n, const float *dh, const float *hh, float u_min, const float4 *tab,
                            float *out, cudaStream_t st, char *msg, size_t msg_len);

@@ -837,10 +837,6 @@ void launch_master_to_planes(int64_t n, const float *master, const float *amax, 
   master_to_planes_kernel<<<nblk(n, 256), 256, 0, st>>>(n, master, amax, bf, hf, scale_out);
 }
 
-void launch_build_dm_table(float4 *tab, cudaStream_t st) {
-  build_dm_table_kernel<<<nblk((int64_t)DM_NY * DM_NS, 64), 64, 0, st>>>(tab);
-}
-
 // The distance-marginal table is a constant of the method, the same for every
 // context: it lives in this static device array (3.2 MB, held by every GPU
 // that loads the library until the process exits) and is built once per CUDA
@@ -886,7 +882,6 @@ void launch_dist_marg_eval(int64_t n, const float *dh, const float *hh, float u_
   dist_marg_eval_kernel<<<nblk(n, 256), 256, 0, st>>>(n, dh, hh, u_min, tab, out);
 }
 
-size_t dm_table_elems() { return (size_t)DM_NY * DM_NS; }
 
 // ---------------------------------------------------------------------------
 // Allocation-free distance-marginal evaluation.
